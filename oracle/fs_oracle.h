@@ -1,0 +1,110 @@
+/*
+ * fs_oracle.h -- plain, slow, single-threaded CPU oracle for the renewal
+ * (age-dependent hazard) Bernoulli tau-leaping step of SIR/SEIR on a CSR
+ * contact graph (FlashSpread, arXiv 2604.22092, Sections 3 and 5, Algorithm 3).
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing in the product library links, loads or
+ * calls this code: it exists so that tests, the smoke check and the CPU
+ * baseline leg of the benchmark can compare the CUDA path with an independent
+ * restatement of the method. It shares no source with the CUDA path.
+ *
+ * Conventions (shared with the C ABI only through their definitions):
+ *   compartments  S = 0, E = 1, I = 2, R = 3 (SIR leaves E empty)
+ *   CSR           row i lists the in-neighbours j of node i (Section 3, Eq. 3;
+ *                 Appendix D.1): row_ptr int64[n+1], col_ind int32[E]
+ *   ages          stored as the float value of the storage type (f32, f16 or
+ *                 bf16 values are all exactly representable in a float)
+ *   uniforms      u = (w >> 8) * 2^-24, w = word (rep mod 4) of
+ *                 Philox4x32-10(counter = (node, step, rep / 4, 0),
+ *                               key = (seed_lo32, seed_hi32))
+ */
+#ifndef FS_ORACLE_H
+#define FS_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { FSO_S = 0, FSO_E = 1, FSO_I = 2, FSO_R = 3 };
+enum { FSO_SIR = 0, FSO_SEIR = 1 };
+enum { FSO_LAW_NONE = 0, FSO_LAW_EXP = 1, FSO_LAW_LOGNORMAL = 2,
+       FSO_LAW_WEIBULL = 3, FSO_LAW_ERLANG = 4 };
+enum { FSO_AGE_F32 = 0, FSO_AGE_F16 = 1, FSO_AGE_BF16 = 2 };
+
+/* Holding-time law.  EXP: a = rate.  LOGNORMAL: a = mu, b = sigma (log-days).
+ * WEIBULL: a = shape k, b = scale s.  ERLANG: k = stages, a = rate per stage. */
+typedef struct {
+    int32_t kind;
+    int32_t k;
+    double a, b;
+} fso_law;
+
+typedef struct {
+    int32_t model;          /* FSO_SIR or FSO_SEIR                          */
+    int32_t age_dtype;      /* FSO_AGE_F32 / F16 / BF16                      */
+    fso_law latent;         /* E -> I (SEIR only)                            */
+    fso_law infectious;     /* I -> R                                        */
+    double beta;            /* per infectious in-neighbour hazard (1/day)    */
+    double dt;              /* fixed step (days)                             */
+    uint64_t seed;          /* Philox key                                    */
+    uint32_t rep;           /* realisation index inside the key's stream     */
+    int32_t pad_;
+} fso_params;
+
+/* ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) ------------------ */
+void fso_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+/* The 24-bit uniform of (seed, rep, step, node), as a double in [0, 1). */
+double fso_uniform(uint64_t seed, uint32_t rep, int64_t step, int64_t node);
+
+/* ---- hazards in double precision (Section 5.1, Proposition 1) ----------- */
+double fso_erfcx(double z);
+double fso_hazard(const fso_law* law, double tau);
+
+/* ---- storage rounding (Section 5.7: fp32 math, cast on store) ----------- */
+uint16_t fso_f32_to_f16_bits(float x);
+float    fso_f16_bits_to_f32(uint16_t h);
+uint16_t fso_f32_to_bf16_bits(float x);
+float    fso_bf16_bits_to_f32(uint16_t h);
+float    fso_store_age(float x, int32_t age_dtype);
+/* renewal age update of a node that did not fire and is in E or I */
+float    fso_age_next(float age, double dt, int32_t age_dtype);
+
+/* ---- the tau-leaping step (Algorithm 3 with a fixed step) --------------- */
+/* Initial condition: every node S with age 0, listed nodes in index_state
+ * with age 0. Returns 0, or -1 on a bad index list. */
+int fso_init(int64_t n, const int32_t* index_nodes, int64_t n_index,
+             int32_t index_state, uint8_t* X, float* A);
+
+void fso_counts(int64_t n, const uint8_t* X, uint32_t counts[4]);
+
+/* One synchronous step k: reads (X, A), writes (Xn, An). When margin is not
+ * NULL, margin[i] = u_i - p_i for every node with p_i > 0 and +inf elsewhere.
+ * When lambda_out is not NULL it receives lambda_i. Returns 0 or -1. */
+int fso_step(int64_t n, const int64_t* row_ptr, const int32_t* col_ind,
+             const fso_params* prm, int64_t k,
+             const uint8_t* X, const float* A, uint8_t* Xn, float* An,
+             double* margin, double* lambda_out);
+
+/* steps consecutive steps k0 .. k0+steps-1, in place on (X, A);
+ * counts[(steps+1)*4], row 0 = the input state. */
+int fso_run(int64_t n, const int64_t* row_ptr, const int32_t* col_ind,
+            const fso_params* prm, int64_t k0, int64_t steps,
+            uint8_t* X, float* A, uint32_t* counts);
+
+/* ---- exact continuous-time simulator for tiny graphs -------------------- */
+/* Event-driven simulation of the same compartmental process without time
+ * discretisation: S -> E (SIR: S -> I) at rate beta * (#infectious
+ * in-neighbours), piecewise constant between events; E and I holding times
+ * drawn at entry from their laws. Uses its own splitmix64 stream (not
+ * Philox). counts_grid[(n_grid)*4] receives the counts at t = g * grid_dt. */
+int fso_exact_run(int64_t n, const int64_t* row_ptr, const int32_t* col_ind,
+                  const fso_params* prm, const int32_t* index_nodes,
+                  int64_t n_index, int32_t index_state, uint64_t rng_seed,
+                  int64_t n_grid, double grid_dt, uint32_t* counts_grid);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

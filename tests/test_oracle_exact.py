@@ -1,0 +1,110 @@
+"""Pins of the exact event-driven simulator and of the tau-leap scheme
+against it (the paper validates against an exact non-Markovian Gillespie:
+Section 6 "validation", Appendix C).
+
+The exact simulator is pinned to closed forms: isolated nodes leave their
+compartment following the law's survival function; an S-I pair is infected
+with probability integral beta exp(-beta t) S_I(t) dt (beta/(beta+gamma) for
+an exponential infectious period). The tau-leap oracle is then compared with
+it on the paper's validation benchmark, within the bias floor the paper
+states (about 6% of N on peak I and 7% on final R, Appendix C), and with the
+paper's printed tau-leap values (tests/golden/epsilon_sweep.txt).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.integrate
+import scipy.stats
+
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "epsilon_sweep.txt")
+
+
+def _golden():
+    rows = {}
+    for line in open(GOLDEN):
+        if line.startswith("#") or not line.strip():
+            continue
+        f = line.split()
+        rows[f[0]] = tuple(float(x) for x in f[1:])
+    return rows
+
+
+def test_exact_isolated_nodes_follow_survival(oracle_mod):
+    om = oracle_mod
+    n = 3000
+    g = W.empty_graph(n)
+    prm = om.params(om.SEIR, om.law("weibull", 2.0, 4.0), om.law("lognormal", math.log(6), 0.6), 0.25, 0.1, seed=0)
+    grid = om.exact_run(g.row_ptr, g.col_ind, prm, np.arange(n), om.E, rng_seed=5, n_grid=121, grid_dt=0.25)
+    wb = scipy.stats.weibull_min(c=2.0, scale=4.0)
+    for gi in (4, 12, 20, 40, 80):
+        t = gi * 0.25
+        q = wb.sf(t)
+        z = (grid[gi, 1] - n * q) / math.sqrt(n * q * (1 - q) + 1e-12)
+        assert abs(z) < 5
+    assert (grid.sum(axis=1) == n).all()
+    prm2 = om.params(om.SIR, None, om.law("lognormal", math.log(5), 0.5), 0.3, 0.1, seed=0)
+    grid = om.exact_run(g.row_ptr, g.col_ind, prm2, np.arange(n), om.I, rng_seed=6, n_grid=61, grid_dt=0.5)
+    ln = scipy.stats.lognorm(s=0.5, scale=5.0)
+    for gi in (2, 8, 12, 20, 40):
+        q = ln.sf(gi * 0.5)
+        z = (grid[gi, 2] - n * q) / math.sqrt(n * q * (1 - q) + 1e-12)
+        assert abs(z) < 5
+
+
+@pytest.mark.parametrize("law", ["exp", "lognormal"])
+def test_exact_si_pair_infection_probability(oracle_mod, law):
+    om = oracle_mod
+    pairs = 2000
+    n = 2 * pairs
+    u = np.arange(0, n, 2, dtype=np.int64)
+    g = W.csr_from_edges(n, u, u + 1)
+    beta = 0.2
+    if law == "exp":
+        lw = om.law("exp", 0.3)
+        expect = beta / (beta + 0.3)
+    else:
+        lw = om.law("lognormal", math.log(5), 0.5)
+        ln = scipy.stats.lognorm(s=0.5, scale=5.0)
+        expect = scipy.integrate.quad(lambda t: beta * math.exp(-beta * t) * ln.sf(t), 0, np.inf)[0]
+    prm = om.params(om.SIR, None, lw, beta, 0.1, seed=0)
+    grid = om.exact_run(g.row_ptr, g.col_ind, prm, u.astype(np.int32), om.I, rng_seed=11, n_grid=2, grid_dt=500.0)
+    infected = pairs - int(grid[-1, 0])
+    z = (infected - pairs * expect) / math.sqrt(pairs * expect * (1 - expect))
+    assert abs(z) < 5, (infected, pairs * expect)
+
+
+@pytest.mark.slow
+def test_tau_leap_within_bias_floor_of_exact_on_validation_benchmark(oracle_mod):
+    """ER N=1000 d=8, beta=0.25, log-normal E->I (mean 5, median 4) and I->R
+    (mean 7.5, median 5), 10 index E, T=50, 100 runs (Section 6 validation)."""
+    om = oracle_mod
+    g = W.erdos_renyi(1000, 8, seed=0)
+    sE = math.sqrt(2 * math.log(5 / 4))
+    sI = math.sqrt(2 * math.log(7.5 / 5))
+    prm = om.params(om.SEIR, om.law("lognormal", math.log(4), sE), om.law("lognormal", math.log(5), sI),
+                    0.25, 0.1, seed=1)
+    pk_e, R_e, pk_t, R_t = [], [], [], []
+    for r in range(100):
+        idx = W.index_nodes(g.n, 10, seed=100 + r)
+        cg = om.exact_run(g.row_ptr, g.col_ind, prm, idx, om.E, rng_seed=1000 + r, n_grid=501, grid_dt=0.1)
+        pk_e.append(cg[:, 2].max() / g.n)
+        R_e.append(cg[-1, 3] / g.n)
+        prm.seed = 5000 + r
+        X, A = om.init(g.n, idx, om.E)
+        cnt, _, _ = om.run(g.row_ptr, g.col_ind, prm, 0, 500, X, A)
+        pk_t.append(cnt[:, 2].max() / g.n)
+        R_t.append(cnt[-1, 3] / g.n)
+    ci = lambda x: 1.96 * np.std(x) / math.sqrt(len(x))
+    d_pk = abs(np.mean(pk_t) - np.mean(pk_e))
+    d_R = abs(np.mean(R_t) - np.mean(R_e))
+    assert d_pk <= 0.065 + ci(pk_t) + ci(pk_e)
+    assert d_R <= 0.07 + ci(R_t) + ci(R_e)
+    # the paper's printed tau-leap ensemble at eps = 0.03 (fixed dt = 0.1 here
+    # equals its tau_max), within three of its 95% half-widths
+    gold = _golden()["0.03"]
+    assert abs(np.mean(pk_t) - gold[0]) <= 3 * gold[1] + ci(pk_t)
+    assert abs(np.mean(R_t) - gold[2]) <= 3 * gold[3] + ci(R_t)
