@@ -1,0 +1,413 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused renewal tau-leaping step (GNUPS = N * steps / time).
+
+One benchmark step is one whole run of the SEIR workload on a random
+10-regular graph with N = 10^6 (Weibull(2, 4 d) latent period, log-normal
+(ln 6, 0.6) infectious period, beta = 0.25/day, 100 uniformly chosen index
+cases, dt = 0.1 d, 1,000 steps, FP32 ages, the step loop replayed as CUDA
+Graphs of 50 steps): graph ingest from the CSR already resident in HBM,
+state initialisation and the 1,000 fused steps, timed with CUDA events on the
+launching stream. The L2 is flushed between benchmark steps. The same metric
+is also measured end to end through the C ABI with host buffers (pinned
+CSR upload, counts download), and for the Barabasi-Albert (m = 5) graph of
+the same size as a secondary figure.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl flashstep|reference]
+Under torchrun every rank runs an independent replica (no data-path
+collective): "replicas only" scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "GNUPS at N=1e6 (regular/BA); served-ensemble GNUPS + p50/p99 vs plain"
+UNIT = "GNUPS"
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "fused_step_regular_n1e6.md")
+KERNEL_SOURCES = ["paper_2604_22092_gb300/csrc/fs_step.cu", "paper_2604_22092_gb300/csrc/fs_device.cuh",
+                  "paper_2604_22092_gb300/csrc/fs_internal.h"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["flashstep", "reference"], default="flashstep")
+    ap.add_argument("--n", type=int, default=1_000_000, help="nodes (the headline workload uses 10^6)")
+    ap.add_argument("--sim-steps", type=int, default=1000)
+    ap.add_argument("--graph-steps", type=int, default=50)
+    ap.add_argument("--no-secondary", action="store_true", help="skip the Barabasi-Albert figure")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ workload
+def workload(kind: str, n: int):
+    if kind == "regular":
+        g = W.random_regular(n, 10, seed=0)
+        idx = W.index_nodes(g.n, 100, seed=1)
+        name = f"seir-regular10-n{n:.0e}".replace("+0", "")
+    else:
+        g = W.barabasi_albert(n, 5, seed=0)
+        idx = W.index_nodes(g.n, 100, seed=1, allowed=W.non_hub_nodes(g))
+        name = f"seir-ba-m5-n{n:.0e}".replace("+0", "")
+    return g, idx, name
+
+
+def params(fs, seed: int, replicate: int = 0):
+    return fs.sim_params(fs.FS_SEIR, fs.law("lognormal", math.log(6.0), 0.6), 0.25, 0.1, seed,
+                         latent=fs.law("weibull", 2.0, 4.0), replicate=replicate)
+
+
+def bytes_model(n: int, steps: int, s_node_sum: int, s_degree_sum: int, b_state=1, b_age=4) -> float:
+    """Algorithmic bytes of `steps` steps of the pull formulation: every node
+    reads and writes its state and age and writes its bitmap bit; every S node
+    reads its row offset (4 B), and per in-edge a column index (4 B) and one
+    bitmap bit."""
+    return (n * steps * (2 * b_state + 2 * b_age + 1 / 8) + 4.0 * s_node_sum
+            + (4.0 + 1 / 8) * s_degree_sum)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    if it was taken on the current kernel source."""
+    try:
+        text = open(PROFILE_TRAFFIC).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    k = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
+    if not m or not k or k.group(1) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+def measured_peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(g, idx, budget_s=12.0, max_steps=400):
+    """The oracle, as it stands (single thread), on the first steps of the
+    same workload from its initial state."""
+    import oracle
+    om = oracle
+    om.build()
+    prm = om.params(om.SEIR, om.law("weibull", 2.0, 4.0), om.law("lognormal", math.log(6.0), 0.6),
+                    0.25, 0.1, seed=1)
+    X, A = om.init(g.n, idx, om.E)
+    t0 = time.perf_counter()
+    k = 0
+    while k < max_steps:
+        X, A, _, _ = om.step(g.row_ptr, g.col_ind, prm, k, X, A)
+        k += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": g.n * k / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {k} steps of the {g.n}-node run from its initial state (single-threaded C oracle)",
+            "seconds": round(dt, 3)}
+
+
+# ------------------------------------------------------------------ arms
+def run_flashstep(args, rank, world, local_rank):
+    import torch
+    import paper_2604_22092_gb300 as fs
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    fs.load()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    g, idx, wname = workload("regular", args.n)
+    stream = torch.cuda.Stream(device=dev)
+    d_rp = torch.from_numpy(g.row_ptr).to(dev)
+    d_col = torch.from_numpy(g.col_ind).to(dev)
+    counts_dev = torch.zeros((args.sim_steps + 1) * 4, dtype=torch.int32, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    prm = params(fs, seed=1 + rank, replicate=0)
+    opts = fs.graph_opts(device_input=True)
+
+    def one_step():
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        gh = fs.fs_graph_create(g.n, d_rp, d_col, opts=opts, stream=stream)
+        sh = fs.fs_sim_init(gh, prm, idx, stream=stream)
+        replay_ms = fs.fs_sim_run_timed(sh, args.sim_steps, args.graph_steps, counts_dev)
+        ev1.record(stream)
+        ev1.synchronize()
+        work = fs.fs_sim_work(sh)
+        fs.fs_sim_destroy(sh)
+        fs.fs_graph_destroy(gh)
+        return ev0.elapsed_time(ev1), replay_ms, work
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        one_step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank) if rank == 0 else None
+    times, kern_ms, bytes_alg = [], [], []
+    launches0 = fs.fs_kernel_launches()
+    if clocks:
+        clocks.start()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        ms, replay_ms, work = one_step()
+        torch.cuda.synchronize()
+        times.append(ms)
+        K = args.graph_steps
+        full = args.sim_steps // K
+        kern_ms.append(float(np.sum(replay_ms[:full])))
+        steps_in_graphs = full * K
+        # bytes of the steps inside the timed graph replays (all steps when K divides them)
+        bytes_alg.append(bytes_model(g.n, args.sim_steps, work["s_node_sum"], work["s_degree_sum"])
+                         * steps_in_graphs / args.sim_steps)
+    clock_info = clocks.stop() if clocks else None
+    launches = (fs.fs_kernel_launches() - launches0) // max(args.steps, 1)
+    total_ms = float(np.sum(times))
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    node_updates = g.n * args.sim_steps * args.steps * world
+    value = node_updates / (total_ms * 1e-3) / 1e9
+    # roofline of the dominant kernel (the fused step): algorithmic bytes of the
+    # steps / their event-timed graph replays (which include launch gaps and the
+    # per-replay epilogue, so this is a lower bound on the kernel's own rate)
+    peak, peak_kind = measured_peak_hbm()
+    per_step_bytes = float(np.sum(bytes_alg)) / (args.steps * (args.sim_steps // args.graph_steps) * args.graph_steps)
+    per_step_ms = float(np.sum(kern_ms)) / (args.steps * (args.sim_steps // args.graph_steps) * args.graph_steps)
+    achieved = per_step_bytes / (per_step_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": profiled_traffic(),
+                "peak_source": peak_kind, "kernel": "fused_step_kernel",
+                "algorithmic_bytes_per_launch": round(per_step_bytes),
+                "avg_launch_us": round(per_step_ms * 1e3, 3)}
+    out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": wname, "model": "SEIR renewal", "graph": "random 10-regular (configuration model, seed 0)",
+                      "n": g.n, "sim_steps": args.sim_steps, "graph_steps": args.graph_steps,
+                      "age_storage": "f32", "state_storage": "u8", "parallelism": f"replicas{world}",
+                      "l2_flush": "512 MB write between timed steps",
+                      "timed": "device-resident CSR -> ingest + init + all steps (CUDA events)"},
+           "roofline": roofline, "gpu_launches": int(launches)}
+    if clock_info:
+        out["clocks"] = clock_info
+    # end to end through the C ABI with host buffers (rank 0 only)
+    if rank == 0 and not args.no_e2e:
+        out["e2e"] = e2e(fs, torch, g, idx, prm, args, stream)
+    if rank == 0 and not args.no_secondary:
+        out["secondary"] = secondary_ba(fs, torch, args, stream, flush)
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline(g, idx)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out if rank == 0 else None
+
+
+def e2e(fs, torch, g, idx, prm, args, stream):
+    rp_h = torch.from_numpy(g.row_ptr).pin_memory()
+    col_h = torch.from_numpy(g.col_ind).pin_memory()
+    idx_h = np.ascontiguousarray(idx, dtype=np.int32)
+    times = []
+    for it in range(args.warmup + args.steps):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        gh = fs.fs_graph_create(g.n, rp_h.data_ptr(), col_h.data_ptr(), stream=stream)
+        sh = fs.fs_sim_init(gh, prm, idx_h, stream=stream)
+        counts = fs.fs_sim_run(sh, args.sim_steps, args.graph_steps)
+        ev1.record(stream)
+        ev1.synchronize()
+        if it >= args.warmup:
+            times.append(ev0.elapsed_time(ev1))
+        fs.fs_sim_destroy(sh)
+        fs.fs_graph_destroy(gh)
+    assert counts.sum(axis=1).max() == g.n
+    ms = float(np.mean(times))
+    return {"value": round(g.n * args.sim_steps / (ms * 1e-3) / 1e9, 3), "unit": UNIT,
+            "h2d_bytes_per_step": int(g.row_ptr.nbytes + g.col_ind.nbytes + idx_h.nbytes),
+            "d2h_bytes_per_step": int((args.sim_steps + 1) * 16), "ms_per_step": round(ms, 3)}
+
+
+def secondary_ba(fs, torch, args, stream, flush):
+    g, idx, wname = workload("ba", args.n)
+    dev = flush.device
+    d_rp = torch.from_numpy(g.row_ptr).to(dev)
+    d_col = torch.from_numpy(g.col_ind).to(dev)
+    prm = params(fs, seed=1)
+    opts = fs.graph_opts(device_input=True)
+    times = []
+    info = None
+    for it in range(args.warmup + args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        gh = fs.fs_graph_create(g.n, d_rp, d_col, opts=opts, stream=stream)
+        sh = fs.fs_sim_init(gh, prm, idx, stream=stream)
+        fs.fs_sim_run_async(sh, args.sim_steps, args.graph_steps)
+        fs.fs_sim_sync(sh)
+        ev1.record(stream)
+        ev1.synchronize()
+        if it >= args.warmup:
+            times.append(ev0.elapsed_time(ev1))
+        info = fs.fs_graph_info_get(gh)
+        fs.fs_sim_destroy(sh)
+        fs.fs_graph_destroy(gh)
+    ms = float(np.mean(times))
+    return {"workload": wname, "value": round(g.n * args.sim_steps / (ms * 1e-3) / 1e9, 3), "unit": UNIT,
+            "ms_per_step": round(ms, 3), "d_max": info["d_max"], "rho": round(info["rho"], 1),
+            "thread_class_nodes": info["n_thread"], "merge_class_nodes": info["n_merge"]}
+
+
+def run_reference(args, rank, world):
+    """The oracle timed on the host cores on bounded samples of the workload."""
+    if rank != 0:
+        return None
+    import oracle as om
+    om.build()
+    g, idx, wname = workload("regular", args.n)
+    prm = om.params(om.SEIR, om.law("weibull", 2.0, 4.0), om.law("lognormal", math.log(6.0), 0.6),
+                    0.25, 0.1, seed=1)
+    X, A = om.init(g.n, idx, om.E)
+    per_step = 10   # oracle steps per benchmark step (a bounded sample)
+    k = 0
+    times = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        for _ in range(per_step):
+            X, A, _, _ = om.step(g.row_ptr, g.col_ind, prm, k, X, A)
+            k += 1
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+    total = float(np.sum(times))
+    value = g.n * per_step * args.steps / total / 1e9
+    sample = (f"{per_step} consecutive oracle steps per benchmark step, steps {args.warmup * per_step} to "
+              f"{k - 1} of the {g.n}-node run")
+    return {"metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(total / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": wname, "model": "SEIR renewal", "n": g.n, "sim_steps": args.sim_steps,
+                       "parallelism": "host", "l2_flush": "n/a (CPU)"},
+            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1 and "LOCAL_RANK" in os.environ:
+        # one visible GPU per replica, so that every CUDA runtime in the
+        # process (torch's and the library's) addresses the same device
+        os.environ["CUDA_VISIBLE_DEVICES"] = os.environ["LOCAL_RANK"]
+        os.environ["LOCAL_RANK"] = "0"
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_flashstep(args, rank, world, local_rank)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,228 @@
+/*
+ * fs.h -- C ABI of libflashstep: the renewal (age-dependent hazard) Bernoulli
+ * tau-leaping step of SIR/SEIR on a CSR contact graph, on one GB300 GPU
+ * (sm_103a). Method: FlashSpread, arXiv 2604.22092 -- Section 3 (Eqs. 1-3:
+ * state (X, tau), rate decomposition, inducer influence), Section 5.1
+ * (Proposition 1: stable log-normal hazard), Section 5.2 (Bernoulli
+ * tau-leap), Section 5.4 (Algorithm 3: the fused step; Algorithm 2: capture
+ * of b steps in a CUDA Graph), Section 5.5 (degree-aware traversal),
+ * Section 5.7 (storage precision).
+ *
+ * General rules for every entry point
+ *   - Every function returns an fs_status; FS_OK is 0. On any other value
+ *     fs_last_error() returns a message (thread-local, valid until the next
+ *     call on the same thread). No C++ exception crosses this boundary.
+ *   - Argument errors are detected on the host before any device work and
+ *     leave every handle unchanged (FS_EINVAL).
+ *   - Host arrays passed in are read during the call only; the caller keeps
+ *     ownership. Device memory is allocated and owned by the library.
+ *   - A CUDA error moves the handle to a failed state: the call returns
+ *     FS_ECUDA and later calls on that handle return FS_ESTATE.
+ *   - Handles are not thread-safe; use one handle from one thread at a time.
+ *   - Node ids are the caller's (original) ids everywhere in this API. The
+ *     library may relabel nodes internally; random numbers are always keyed
+ *     by original ids, so results never depend on the internal layout.
+ *
+ * Conventions
+ *   compartments: FS_S = 0, FS_E = 1, FS_I = 2, FS_R = 3 (SIR leaves E empty)
+ *   CSR: row i lists the in-neighbours j of node i (each j -> i edge once);
+ *        row_ptr int64[n+1] nondecreasing with row_ptr[0] = 0,
+ *        col_ind int32[row_ptr[n]] with 0 <= col_ind[e] < n.
+ *        Undirected graphs list every edge in both rows.
+ *   uniforms: u = (w >> 8) * 2^-24 with w = word (replicate mod 4) of
+ *        Philox4x32-10(counter = (node, step, replicate / 4, 0),
+ *                      key = (seed mod 2^32, seed / 2^32)); a node fires
+ *        when u < p, p = 1 - exp(-lambda * dt) computed in FP32.
+ */
+#ifndef FLASHSTEP_FS_H
+#define FLASHSTEP_FS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FS_OK = 0,
+    FS_EINVAL = 1,        /* invalid argument (detected before device work)   */
+    FS_ENOMEM = 2,        /* device or host allocation failed / over budget   */
+    FS_ECUDA = 3,         /* a CUDA call or kernel failed                      */
+    FS_ETIMEOUT = 4,      /* a bounded device wait ran out                     */
+    FS_EBUSY = 5,         /* the object is still referenced                    */
+    FS_ESTATE = 6,        /* the handle is in a failed state                   */
+    FS_EUNSUPPORTED = 7   /* valid request this build does not implement       */
+} fs_status;
+
+enum { FS_S = 0, FS_E = 1, FS_I = 2, FS_R = 3 };
+enum { FS_SIR = 0, FS_SEIR = 1 };
+enum { FS_AGE_F32 = 0, FS_AGE_F16 = 1, FS_AGE_BF16 = 2 };
+enum { FS_DISPATCH_AUTO = 0, FS_DISPATCH_THREAD = 1, FS_DISPATCH_MERGE = 2 };
+
+/* Holding-time law of a nodal transition (Section 5.1; hazard h = f/S).
+ *   FS_LAW_EXP:       a = rate gamma                  h = gamma
+ *   FS_LAW_LOGNORMAL: a = mu, b = sigma (log-days)    h = sqrt(2/pi)/(tau sigma erfcx(z)),
+ *                                                     z = (ln tau - mu)/(sigma sqrt 2)
+ *   FS_LAW_WEIBULL:   a = shape k >= 1, b = scale s   h = (k/s)(tau/s)^(k-1)
+ *   FS_LAW_ERLANG:    k = stages >= 1, a = rate r     h = r (r tau)^(k-1)/(k-1)! / sum_{n<k} (r tau)^n/n!
+ * Hazards are evaluated in FP32 at the begin-of-step age; h(0) = 0 for the
+ * log-normal, for Weibull with k > 1 and for Erlang with k > 1. */
+typedef enum {
+    FS_LAW_NONE = 0, FS_LAW_EXP = 1, FS_LAW_LOGNORMAL = 2, FS_LAW_WEIBULL = 3, FS_LAW_ERLANG = 4
+} fs_law_kind;
+
+typedef struct {
+    int32_t kind;        /* fs_law_kind */
+    int32_t k;           /* Erlang stages */
+    double a, b;
+} fs_law;
+
+/* One realisation (Section 3; Algorithm 3 with a fixed step dt). */
+typedef struct {
+    int32_t model;       /* FS_SIR or FS_SEIR                                     */
+    int32_t age_dtype;   /* FS_AGE_F32, FS_AGE_F16 or FS_AGE_BF16 (age storage)    */
+    fs_law latent;       /* E -> I law (SEIR only; ignored for SIR)                */
+    fs_law infectious;   /* I -> R law                                             */
+    double beta;         /* hazard per infectious in-neighbour (1/day) > 0         */
+    double dt;           /* fixed step (days) > 0                                  */
+    uint64_t seed;       /* Philox key                                             */
+    uint32_t replicate;  /* realisation index in the key's stream                  */
+    int32_t index_state; /* compartment of the index cases: FS_E (SEIR) or FS_I    */
+    int32_t flags;       /* reserved, must be 0                                    */
+    int32_t reserved_;   /* must be 0                                              */
+} fs_sim_params;
+
+/* Graph construction options (all fields may be 0 for the defaults). */
+typedef struct {
+    int32_t dispatch;        /* FS_DISPATCH_*: AUTO picks the class split from the
+                                degree profile (Section 5.5 auto-dispatch)        */
+    int32_t thread_max_deg;  /* rows of degree <= this go to the one-thread-per-node
+                                class; larger rows go to the edge-partitioned
+                                merge class. 0 = chosen by the tuner; >= 31        */
+    int32_t device_input;    /* 1: row_ptr/col_ind are device pointers             */
+    int32_t reserved_;
+} fs_graph_opts;
+
+typedef struct {
+    int64_t n, nnz, d_max;
+    double d_avg, rho;        /* rho = d_max / d_avg (Section 5.5)                 */
+    int64_t n_thread;         /* nodes in the one-thread-per-node (SELL-32) class  */
+    int64_t n_merge;          /* nodes in the edge-partitioned merge class         */
+    int64_t sell_entries;     /* SELL-32 column entries incl. padding              */
+    int64_t merge_chunks;     /* edge chunks of the merge class per step           */
+    int32_t thread_max_deg;   /* class threshold in use                            */
+    int32_t identity_layout;  /* 1 when internal ids equal original ids            */
+    int64_t device_bytes;     /* device memory held by the graph                   */
+} fs_graph_info;
+
+typedef struct fs_graph fs_graph;
+typedef struct fs_sim fs_sim;
+
+/* Library version string, e.g. "flashstep 0.1 sm_103a". Never NULL. */
+const char* fs_version(void);
+/* Message for the last non-OK status on this thread ("" if none). */
+const char* fs_last_error(void);
+
+/* ---------------------------------------------------------------------------
+ * fs_graph_create -- ingest a CSR graph (Appendix D.1 layout; Section 5.5
+ * degree inspection). Copies the CSR to the device (or reads it there when
+ * opts->device_input = 1), computes degrees, d_max, rho, splits the nodes
+ * into the thread class and the merge class, relabels nodes by degree
+ * (stable), and builds the SELL-32 column blocks of the thread class and the
+ * chunk tables of the merge class. Runs on `stream` (a cudaStream_t, NULL =
+ * a library stream) and returns after the ingest has completed.
+ *   n        number of nodes, 1 <= n < 2^31
+ *   row_ptr  int64[n+1] (see CSR above)
+ *   col_ind  int32[row_ptr[n]]
+ *   weights  must be NULL (unit edge weights; other weights: FS_EUNSUPPORTED)
+ *   opts     NULL for the defaults
+ *   out      receives the handle; destroy with fs_graph_destroy
+ * Errors: FS_EINVAL (bad sizes, non-monotone row_ptr, col_ind out of range,
+ *         checked on the host for host input and on the device for device
+ *         input), FS_ENOMEM, FS_ECUDA, FS_EUNSUPPORTED.
+ * ------------------------------------------------------------------------- */
+fs_status fs_graph_create(int64_t n, const int64_t* row_ptr, const int32_t* col_ind,
+                          const float* weights, const fs_graph_opts* opts,
+                          void* stream, fs_graph** out);
+fs_status fs_graph_info_get(const fs_graph* g, fs_graph_info* out);
+/* FS_EBUSY while a simulation created on the graph is alive. */
+fs_status fs_graph_destroy(fs_graph* g);
+
+/* ---------------------------------------------------------------------------
+ * fs_sim_init -- one realisation on a graph (Algorithm 2: persistent state
+ * X, tau and the step counter). Every node starts in S with age 0; the
+ * listed index nodes start in params->index_state with age 0; the step
+ * counter starts at 0.
+ *   index_nodes  host int32[n_index] of distinct original ids in [0, n)
+ *   stream       cudaStream_t used by every later call on the sim (NULL = a
+ *                library-owned non-blocking stream)
+ * Errors: FS_EINVAL (bad params: model, laws, beta, dt, dtype, index list),
+ *         FS_ENOMEM, FS_ECUDA.
+ * ------------------------------------------------------------------------- */
+fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params,
+                      const int32_t* index_nodes, int64_t n_index, void* stream,
+                      fs_sim** out);
+
+/* One fused step (Algorithm 3); counts_out (host uint32[4], may be NULL)
+ * receives [S, E, I, R] after the step. Synchronous. */
+fs_status fs_sim_step(fs_sim* s, uint32_t* counts_out);
+
+/* `steps` fused steps; the step loop runs as replays of a CUDA Graph of
+ * `graph_steps` steps (Algorithm 2; captured on first use, 0 = 50) plus
+ * directly launched remainder steps. counts_out: host uint32[(steps+1)*4],
+ * row 0 = the counts before the first step, row t = after step t. May be
+ * NULL. Synchronous. */
+fs_status fs_sim_run(fs_sim* s, int64_t steps, int32_t graph_steps, uint32_t* counts_out);
+
+/* Asynchronous form of fs_sim_run for callers that keep results on the
+ * device: enqueues the steps on the sim's stream and returns. counts_dev:
+ * device uint32[(steps+1)*4] written when the stream reaches it, or NULL.
+ * Call fs_sim_sync before reading results or issuing host calls that read
+ * the state. */
+fs_status fs_sim_run_async(fs_sim* s, int64_t steps, int32_t graph_steps, uint32_t* counts_dev);
+/* Waits for the sim's stream and reports device-side errors. */
+fs_status fs_sim_sync(fs_sim* s);
+
+/* fs_sim_run_async + fs_sim_sync with CUDA events recorded on the sim's
+ * stream around every graph replay: replay_ms (host float[steps/K + 1])
+ * receives the duration of each K-step replay (step kernels, the launch gaps
+ * between them and the replay's epilogue) and, last, of the directly
+ * launched remainder (0 if none); *n_replays = steps/K + 1. */
+fs_status fs_sim_run_timed(fs_sim* s, int64_t steps, int32_t graph_steps, uint32_t* counts_dev,
+                           float* replay_ms, int64_t* n_replays);
+
+/* Number of kernels enqueued so far by step loops of this process (graph
+ * replays count their kernels). */
+fs_status fs_kernel_launches(uint64_t* count);
+
+/* Host copies of the state in original node order: state uint8[n], age
+ * (float / binary16 / bfloat16 bits per age_dtype)[n], step (next step
+ * index). Any pointer may be NULL. Synchronous. */
+fs_status fs_sim_get_state(fs_sim* s, uint8_t* state, void* age, int64_t* step);
+/* Replace the state (resume from a checkpoint; original node order). The
+ * ages must be storage values of the sim's age dtype; S and R ages must be
+ * 0. Synchronous. */
+fs_status fs_sim_set_state(fs_sim* s, const uint8_t* state, const void* age, int64_t step);
+
+/* Work accounting for the roofline model: the sum over all steps run so far
+ * of sum_{i in S at step start} deg(i), and of |S at step start|. */
+fs_status fs_sim_work(const fs_sim* s, uint64_t* s_degree_sum, uint64_t* s_node_sum, int64_t* steps_run);
+
+fs_status fs_sim_destroy(fs_sim* s);
+
+/* ---------------------------------------------------------------------------
+ * Diagnostics that run the same device functions the step uses.
+ * fs_eval_hazard: h_dev[i] = hazard(law, tau_dev[i]) in FP32, device arrays
+ * of n floats, on `stream` (asynchronous).
+ * fs_eval_uniforms: u_dev[i] = the step's uniform for (seed, replicate,
+ * step, nodes_dev[i]) as a float, device arrays (asynchronous).
+ * ------------------------------------------------------------------------- */
+fs_status fs_eval_hazard(const fs_law* law, const float* tau_dev, float* h_dev, int64_t n, void* stream);
+fs_status fs_eval_uniforms(uint64_t seed, uint32_t replicate, int64_t step, const int32_t* nodes_dev,
+                           float* u_dev, int64_t n, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,211 @@
+"""flashstep: the renewal (age-dependent hazard) Bernoulli tau-leaping step of
+SIR/SEIR on a CSR contact graph, as hand-written CUDA for GB300 (sm_103a),
+after FlashSpread (arXiv 2604.22092).
+
+This module is a thin binding of the C ABI in include/fs.h: every function
+has the name of the C entry point it calls and only marshals arguments
+(numpy arrays for host buffers, torch CUDA tensors or raw integers for device
+buffers and streams). All computation runs in libflashstep.so; if the library
+is missing the import of any entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+
+import numpy as np
+
+from . import _abi
+from ._abi import (FS_AGE_BF16, FS_AGE_F16, FS_AGE_F32, FS_DISPATCH_AUTO, FS_DISPATCH_MERGE,
+                   FS_DISPATCH_THREAD, FS_E, FS_I, FS_LAW_ERLANG, FS_LAW_EXP, FS_LAW_LOGNORMAL,
+                   FS_LAW_NONE, FS_LAW_WEIBULL, FS_R, FS_S, FS_SEIR, FS_SIR, FsError, check)
+
+__all__ = [
+    "fs_version", "fs_last_error", "fs_graph_create", "fs_graph_info_get", "fs_graph_destroy",
+    "fs_sim_init", "fs_sim_step", "fs_sim_run", "fs_sim_run_async", "fs_sim_sync", "fs_sim_run_timed",
+    "fs_kernel_launches",
+    "fs_sim_get_state", "fs_sim_set_state", "fs_sim_work", "fs_sim_destroy", "fs_eval_hazard",
+    "fs_eval_uniforms", "law", "sim_params", "graph_opts", "FsError", "load",
+    "FS_S", "FS_E", "FS_I", "FS_R", "FS_SIR", "FS_SEIR", "FS_AGE_F32", "FS_AGE_F16", "FS_AGE_BF16",
+    "FS_DISPATCH_AUTO", "FS_DISPATCH_THREAD", "FS_DISPATCH_MERGE",
+]
+
+
+def load():
+    """Load (building if stale) libflashstep.so; returns the ctypes library."""
+    return _abi.load()
+
+
+def _addr(x):
+    """Address of a buffer: numpy array (host), torch tensor (device/host), int or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s or None
+    return s.cuda_stream or None
+
+
+# --------------------------------------------------------------- parameters
+def law(kind: str, a: float = 0.0, b: float = 0.0, k: int = 0) -> _abi.fs_law:
+    """Holding-time law: exp(rate), lognormal(mu, sigma), weibull(shape, scale),
+    erlang(rate, k=stages), none."""
+    code = {"none": FS_LAW_NONE, "exp": FS_LAW_EXP, "lognormal": FS_LAW_LOGNORMAL,
+            "weibull": FS_LAW_WEIBULL, "erlang": FS_LAW_ERLANG}[kind]
+    return _abi.fs_law(code, int(k), float(a), float(b))
+
+
+def lognormal_from_mean_median(mean: float, median: float) -> _abi.fs_law:
+    """mu = ln(median), sigma = sqrt(2 ln(mean/median)) (the paper's parametrisation)."""
+    return law("lognormal", math.log(median), math.sqrt(2.0 * math.log(mean / median)))
+
+
+def sim_params(model: int, infectious: _abi.fs_law, beta: float, dt: float, seed: int,
+               latent: _abi.fs_law | None = None, replicate: int = 0, index_state: int | None = None,
+               age_dtype: int = FS_AGE_F32) -> _abi.fs_sim_params:
+    if index_state is None:
+        index_state = FS_E if model == FS_SEIR else FS_I
+    return _abi.fs_sim_params(int(model), int(age_dtype), latent if latent is not None else law("none"),
+                              infectious, float(beta), float(dt), int(seed), int(replicate),
+                              int(index_state), 0, 0)
+
+
+def graph_opts(dispatch: int = FS_DISPATCH_AUTO, thread_max_deg: int = 0,
+               device_input: bool = False) -> _abi.fs_graph_opts:
+    return _abi.fs_graph_opts(int(dispatch), int(thread_max_deg), 1 if device_input else 0, 0)
+
+
+# --------------------------------------------------------------- entry points
+def fs_version() -> str:
+    return load().fs_version().decode()
+
+
+def fs_last_error() -> str:
+    return load().fs_last_error().decode(errors="replace")
+
+
+def fs_graph_create(n: int, row_ptr, col_ind, weights=None, opts: _abi.fs_graph_opts | None = None,
+                    stream=None) -> int:
+    """Returns an opaque graph handle. row_ptr/col_ind: numpy int64/int32 on the
+    host, or torch CUDA tensors with opts.device_input = 1."""
+    L = load()
+    if isinstance(row_ptr, np.ndarray):
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        col_ind = np.ascontiguousarray(col_ind, dtype=np.int32)
+    h = ctypes.c_void_p()
+    st = L.fs_graph_create(int(n), _addr(row_ptr), _addr(col_ind), _addr(weights),
+                           ctypes.byref(opts) if opts is not None else None, _stream(stream),
+                           ctypes.byref(h))
+    check(st, "fs_graph_create")
+    return h.value
+
+
+def fs_graph_info_get(g: int) -> dict:
+    info = _abi.fs_graph_info()
+    check(load().fs_graph_info_get(g, ctypes.byref(info)), "fs_graph_info_get")
+    return {name: getattr(info, name) for name, _ in info._fields_}
+
+
+def fs_graph_destroy(g: int) -> None:
+    check(load().fs_graph_destroy(g), "fs_graph_destroy")
+
+
+def fs_sim_init(g: int, params: _abi.fs_sim_params, index_nodes, stream=None) -> int:
+    idx = np.ascontiguousarray(index_nodes, dtype=np.int32)
+    h = ctypes.c_void_p()
+    st = load().fs_sim_init(g, ctypes.byref(params), _addr(idx) if idx.size else None, idx.size,
+                            _stream(stream), ctypes.byref(h))
+    check(st, "fs_sim_init")
+    return h.value
+
+
+def fs_sim_step(s: int) -> np.ndarray:
+    c = np.zeros(4, dtype=np.uint32)
+    check(load().fs_sim_step(s, _addr(c)), "fs_sim_step")
+    return c
+
+
+def fs_sim_run(s: int, steps: int, graph_steps: int = 0, want_counts: bool = True):
+    c = np.zeros((steps + 1, 4), dtype=np.uint32) if want_counts else None
+    check(load().fs_sim_run(s, int(steps), int(graph_steps), _addr(c)), "fs_sim_run")
+    return c
+
+
+def fs_sim_run_async(s: int, steps: int, graph_steps: int = 0, counts_dev=None) -> None:
+    check(load().fs_sim_run_async(s, int(steps), int(graph_steps), _addr(counts_dev)), "fs_sim_run_async")
+
+
+def fs_sim_sync(s: int) -> None:
+    check(load().fs_sim_sync(s), "fs_sim_sync")
+
+
+def fs_sim_run_timed(s: int, steps: int, graph_steps: int = 0, counts_dev=None) -> np.ndarray:
+    """Runs `steps` steps and returns the event-timed ms of every graph replay
+    (and, last, of the directly launched remainder)."""
+    K = graph_steps or 50
+    ms = np.zeros(steps // K + 1, dtype=np.float32)
+    n = ctypes.c_int64()
+    check(load().fs_sim_run_timed(s, int(steps), int(graph_steps), _addr(counts_dev), _addr(ms),
+                                  ctypes.byref(n)), "fs_sim_run_timed")
+    return ms[:n.value]
+
+
+def fs_kernel_launches() -> int:
+    c = ctypes.c_uint64()
+    check(load().fs_kernel_launches(ctypes.byref(c)), "fs_kernel_launches")
+    return c.value
+
+
+_AGE_NP = {FS_AGE_F32: np.float32, FS_AGE_F16: np.uint16, FS_AGE_BF16: np.uint16}
+
+
+def fs_sim_get_state(s: int, n: int, age_dtype: int = FS_AGE_F32):
+    """(state uint8[n], age[n] (float32, or the raw 16-bit storage), step)."""
+    X = np.zeros(n, dtype=np.uint8)
+    A = np.zeros(n, dtype=_AGE_NP[age_dtype])
+    step = ctypes.c_int64()
+    check(load().fs_sim_get_state(s, _addr(X), _addr(A), ctypes.byref(step)), "fs_sim_get_state")
+    return X, A, step.value
+
+
+def fs_sim_set_state(s: int, state, age, step: int) -> None:
+    X = np.ascontiguousarray(state, dtype=np.uint8)
+    A = np.ascontiguousarray(age)
+    check(load().fs_sim_set_state(s, _addr(X), _addr(A), int(step)), "fs_sim_set_state")
+
+
+def fs_sim_work(s: int) -> dict:
+    ds, sn, k = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int64()
+    check(load().fs_sim_work(s, ctypes.byref(ds), ctypes.byref(sn), ctypes.byref(k)), "fs_sim_work")
+    return {"s_degree_sum": ds.value, "s_node_sum": sn.value, "steps": k.value}
+
+
+def fs_sim_destroy(s: int) -> None:
+    check(load().fs_sim_destroy(s), "fs_sim_destroy")
+
+
+def fs_eval_hazard(lw: _abi.fs_law, tau_dev, h_dev, stream=None) -> None:
+    n = tau_dev.numel()
+    check(load().fs_eval_hazard(ctypes.byref(lw), _addr(tau_dev), _addr(h_dev), n, _stream(stream)),
+          "fs_eval_hazard")
+
+
+def fs_eval_uniforms(seed: int, replicate: int, step: int, nodes_dev, u_dev, stream=None) -> None:
+    n = nodes_dev.numel()
+    check(load().fs_eval_uniforms(int(seed), int(replicate), int(step), _addr(nodes_dev), _addr(u_dev), n,
+                                  _stream(stream)), "fs_eval_uniforms")

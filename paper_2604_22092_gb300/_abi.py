@@ -1,0 +1,113 @@
+"""ctypes mirror of include/fs.h (structures, enums and prototypes).
+
+Argument marshalling only: every computation happens in libflashstep.so.
+Loading fails loudly when the library has not been built; there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import _build_lib
+
+FS_OK, FS_EINVAL, FS_ENOMEM, FS_ECUDA, FS_ETIMEOUT, FS_EBUSY, FS_ESTATE, FS_EUNSUPPORTED = range(8)
+STATUS_NAMES = {0: "FS_OK", 1: "FS_EINVAL", 2: "FS_ENOMEM", 3: "FS_ECUDA", 4: "FS_ETIMEOUT",
+                5: "FS_EBUSY", 6: "FS_ESTATE", 7: "FS_EUNSUPPORTED"}
+FS_S, FS_E, FS_I, FS_R = 0, 1, 2, 3
+FS_SIR, FS_SEIR = 0, 1
+FS_AGE_F32, FS_AGE_F16, FS_AGE_BF16 = 0, 1, 2
+FS_DISPATCH_AUTO, FS_DISPATCH_THREAD, FS_DISPATCH_MERGE = 0, 1, 2
+FS_LAW_NONE, FS_LAW_EXP, FS_LAW_LOGNORMAL, FS_LAW_WEIBULL, FS_LAW_ERLANG = 0, 1, 2, 3, 4
+
+
+class fs_law(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("a", ctypes.c_double), ("b", ctypes.c_double)]
+
+
+class fs_sim_params(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("age_dtype", ctypes.c_int32),
+                ("latent", fs_law), ("infectious", fs_law),
+                ("beta", ctypes.c_double), ("dt", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("replicate", ctypes.c_uint32),
+                ("index_state", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("reserved_", ctypes.c_int32)]
+
+
+class fs_graph_opts(ctypes.Structure):
+    _fields_ = [("dispatch", ctypes.c_int32), ("thread_max_deg", ctypes.c_int32),
+                ("device_input", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
+
+
+class fs_graph_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("d_max", ctypes.c_int64),
+                ("d_avg", ctypes.c_double), ("rho", ctypes.c_double),
+                ("n_thread", ctypes.c_int64), ("n_merge", ctypes.c_int64),
+                ("sell_entries", ctypes.c_int64), ("merge_chunks", ctypes.c_int64),
+                ("thread_max_deg", ctypes.c_int32), ("identity_layout", ctypes.c_int32),
+                ("device_bytes", ctypes.c_int64)]
+
+
+VP = ctypes.c_void_p
+P = ctypes.POINTER
+
+# name -> (restype, argtypes); the exported C ABI
+PROTOTYPES = {
+    "fs_version": (ctypes.c_char_p, []),
+    "fs_last_error": (ctypes.c_char_p, []),
+    "fs_graph_create": (ctypes.c_int, [ctypes.c_int64, VP, VP, VP, P(fs_graph_opts), VP, P(VP)]),
+    "fs_graph_info_get": (ctypes.c_int, [VP, P(fs_graph_info)]),
+    "fs_graph_destroy": (ctypes.c_int, [VP]),
+    "fs_sim_init": (ctypes.c_int, [VP, P(fs_sim_params), VP, ctypes.c_int64, VP, P(VP)]),
+    "fs_sim_step": (ctypes.c_int, [VP, VP]),
+    "fs_sim_run": (ctypes.c_int, [VP, ctypes.c_int64, ctypes.c_int32, VP]),
+    "fs_sim_run_async": (ctypes.c_int, [VP, ctypes.c_int64, ctypes.c_int32, VP]),
+    "fs_sim_sync": (ctypes.c_int, [VP]),
+    "fs_sim_run_timed": (ctypes.c_int, [VP, ctypes.c_int64, ctypes.c_int32, VP, VP, P(ctypes.c_int64)]),
+    "fs_kernel_launches": (ctypes.c_int, [P(ctypes.c_uint64)]),
+    "fs_sim_get_state": (ctypes.c_int, [VP, VP, VP, P(ctypes.c_int64)]),
+    "fs_sim_set_state": (ctypes.c_int, [VP, VP, VP, ctypes.c_int64]),
+    "fs_sim_work": (ctypes.c_int, [VP, P(ctypes.c_uint64), P(ctypes.c_uint64), P(ctypes.c_int64)]),
+    "fs_sim_destroy": (ctypes.c_int, [VP]),
+    "fs_eval_hazard": (ctypes.c_int, [P(fs_law), VP, VP, ctypes.c_int64, VP]),
+    "fs_eval_uniforms": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64, VP, VP,
+                                        ctypes.c_int64, VP]),
+}
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build_lib.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libflashstep.so (building it first if asked and stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not _build_lib.is_fresh():
+        _build_lib.build()
+    path = _build_lib.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libflashstep.so is not built ({path}); run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    for name, (res, args) in PROTOTYPES.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+class FsError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {message}")
+
+
+def check(status: int, where: str) -> None:
+    if status != FS_OK:
+        msg = load().fs_last_error().decode(errors="replace")
+        raise FsError(status, where, msg)

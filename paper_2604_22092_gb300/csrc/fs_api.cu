@@ -1,0 +1,904 @@
+// fs_api.cu -- the C ABI of libflashstep (declared in include/fs.h): graph
+// ingest orchestration, simulation state, and the step loop as CUDA Graph
+// replays (FlashSpread, arXiv 2604.22092, Algorithm 2: capture of b steps with
+// a persistent device step counter; Algorithm 3: the fused step).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fs.h"
+#include "fs_launch.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+fs_status fail(fs_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+}  // namespace
+
+#define FS_CUDA(obj, expr)                                                                     \
+    do {                                                                                       \
+        cudaError_t e_ = (expr);                                                               \
+        if (e_ != cudaSuccess) {                                                               \
+            if (obj)                                                                           \
+                (obj)->failed = true;                                                          \
+            return fail(e_ == cudaErrorMemoryAllocation ? FS_ENOMEM : FS_ECUDA, "%s: %s (%s:%d)", #expr, \
+                        cudaGetErrorString(e_), __FILE__, __LINE__);                           \
+        }                                                                                      \
+    } while (0)
+
+struct fs_graph {
+    int64_t n = 0, nnz = 0;
+    int32_t dmax = 0;
+    int32_t t1 = 0;
+    int32_t n_thr = 0, n_m = 0, n_slices = 0, n_chunks = 0;
+    int64_t e_m = 0, sell_entries = 0;
+    bool identity = true;
+    int32_t* d_perm = nullptr;     // internal -> original
+    int32_t* d_inv = nullptr;      // original -> internal
+    int32_t* d_deg = nullptr;      // degree by internal id
+    int64_t* d_sell_off = nullptr;
+    int32_t* d_sell_col = nullptr;
+    int64_t* d_m_ptr = nullptr;
+    int32_t* d_m_col = nullptr;
+    int32_t* d_m_warp_row = nullptr;
+    int32_t* d_m_chunk_last = nullptr;
+    int64_t bytes = 0;
+    int refs = 0;
+    bool failed = false;
+};
+
+struct fs_sim {
+    fs_graph* g = nullptr;
+    fs_sim_params p{};
+    fs::ModelF M{};
+    int age_bytes = 4;
+    uint8_t* d_X = nullptr;
+    void* d_A = nullptr;
+    uint32_t* d_bm[2] = {nullptr, nullptr};
+    int32_t* d_m_cnt = nullptr;
+    uint32_t* d_m_tkt = nullptr;
+    fs::DevCtl* d_ctl = nullptr;
+    unsigned long long* d_deltas = nullptr;
+    uint32_t* d_counts = nullptr;
+    int64_t counts_cap = 0;
+    cudaGraphExec_t gexec = nullptr;
+    int gK = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    bool failed = false;
+};
+
+namespace {
+
+template <typename T>
+cudaError_t dev_alloc(T** p, size_t count, int64_t* bytes)
+{
+    const size_t b = sizeof(T) * std::max<size_t>(count, 1);
+    cudaError_t e = cudaMalloc((void**)p, b);
+    if (e == cudaSuccess && bytes)
+        *bytes += (int64_t)b;
+    return e;
+}
+
+void free_graph(fs_graph* g)
+{
+    if (!g)
+        return;
+    cudaFree(g->d_perm);
+    cudaFree(g->d_inv);
+    cudaFree(g->d_deg);
+    cudaFree(g->d_sell_off);
+    cudaFree(g->d_sell_col);
+    cudaFree(g->d_m_ptr);
+    cudaFree(g->d_m_col);
+    cudaFree(g->d_m_warp_row);
+    cudaFree(g->d_m_chunk_last);
+    delete g;
+}
+
+void free_sim(fs_sim* s)
+{
+    if (!s)
+        return;
+    if (s->gexec)
+        cudaGraphExecDestroy(s->gexec);
+    cudaFree(s->d_X);
+    cudaFree(s->d_A);
+    cudaFree(s->d_bm[0]);
+    cudaFree(s->d_bm[1]);
+    cudaFree(s->d_m_cnt);
+    cudaFree(s->d_m_tkt);
+    cudaFree(s->d_ctl);
+    cudaFree(s->d_deltas);
+    cudaFree(s->d_counts);
+    if (s->own_stream && s->stream)
+        cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+bool finite(double v) { return std::isfinite(v); }
+
+fs_status check_law(const fs_law& L, const char* what, bool allow_none)
+{
+    switch (L.kind) {
+    case FS_LAW_NONE:
+        if (!allow_none)
+            return fail(FS_EINVAL, "%s law: kind NONE is not allowed here", what);
+        return FS_OK;
+    case FS_LAW_EXP:
+        if (!finite(L.a) || L.a < 0)
+            return fail(FS_EINVAL, "%s law: exponential rate must be finite and >= 0", what);
+        return FS_OK;
+    case FS_LAW_LOGNORMAL:
+        if (!finite(L.a) || !finite(L.b) || !(L.b > 0))
+            return fail(FS_EINVAL, "%s law: log-normal needs finite mu and sigma > 0", what);
+        return FS_OK;
+    case FS_LAW_WEIBULL:
+        if (!finite(L.a) || !finite(L.b) || !(L.a >= 1.0) || !(L.b > 0))
+            return fail(FS_EINVAL, "%s law: Weibull needs shape >= 1 and scale > 0", what);
+        return FS_OK;
+    case FS_LAW_ERLANG:
+        if (L.k < 1 || L.k > 64 || !finite(L.a) || !(L.a > 0))
+            return fail(FS_EINVAL, "%s law: Erlang needs 1 <= k <= 64 and rate > 0", what);
+        return FS_OK;
+    default:
+        return fail(FS_EINVAL, "%s law: unknown kind %d", what, L.kind);
+    }
+}
+
+fs::LawF to_lawf(const fs_law& L)
+{
+    fs::LawF f{};
+    f.kind = L.kind;
+    f.k = L.k;
+    switch (L.kind) {
+    case FS_LAW_EXP:
+        f.p0 = (float)L.a;
+        break;
+    case FS_LAW_LOGNORMAL: {
+        const double inv = 1.0 / (L.b * std::sqrt(2.0));
+        f.p0 = (float)L.a;
+        f.p3 = (float)(L.a - (double)f.p0);
+        f.p1 = (float)inv;
+        f.p4 = (float)(inv - (double)f.p1);
+        f.p2 = (float)(std::sqrt(2.0 / M_PI) / L.b);
+        break;
+    }
+    case FS_LAW_WEIBULL:
+        f.p0 = (float)(L.a / L.b);
+        f.p1 = (float)(1.0 / L.b);
+        f.p2 = (float)(L.a - 1.0);
+        break;
+    case FS_LAW_ERLANG:
+        f.p0 = (float)L.a;
+        break;
+    default:
+        break;
+    }
+    return f;
+}
+
+fs_status check_params(const fs_sim_params* p)
+{
+    if (!p)
+        return fail(FS_EINVAL, "params is NULL");
+    if (p->model != FS_SIR && p->model != FS_SEIR)
+        return fail(FS_EINVAL, "model must be FS_SIR or FS_SEIR");
+    if (p->age_dtype < FS_AGE_F32 || p->age_dtype > FS_AGE_BF16)
+        return fail(FS_EINVAL, "age_dtype must be FS_AGE_F32, FS_AGE_F16 or FS_AGE_BF16");
+    if (!finite(p->beta) || p->beta < 0)
+        return fail(FS_EINVAL, "beta must be finite and >= 0");
+    if (!finite(p->dt) || !(p->dt > 0))
+        return fail(FS_EINVAL, "dt must be finite and > 0");
+    if (p->flags != 0 || p->reserved_ != 0)
+        return fail(FS_EINVAL, "flags and reserved fields must be 0");
+    fs_status st = check_law(p->infectious, "infectious", false);
+    if (st != FS_OK)
+        return st;
+    if (p->model == FS_SEIR) {
+        st = check_law(p->latent, "latent", false);
+        if (st != FS_OK)
+            return st;
+        if (p->index_state != FS_E && p->index_state != FS_I)
+            return fail(FS_EINVAL, "SEIR index_state must be FS_E or FS_I");
+    } else if (p->index_state != FS_I) {
+        return fail(FS_EINVAL, "SIR index_state must be FS_I");
+    }
+    return FS_OK;
+}
+
+fs::ModelF to_model(const fs_sim_params& p)
+{
+    fs::ModelF M{};
+    M.model = p.model;
+    M.beta = (float)p.beta;
+    M.dt = (float)p.dt;
+    M.key0 = (uint32_t)(p.seed & 0xffffffffu);
+    M.key1 = (uint32_t)(p.seed >> 32);
+    M.rep = p.replicate;
+    M.lat = to_lawf(p.latent);
+    M.inf = to_lawf(p.infectious);
+    return M;
+}
+
+fs::StepArgs step_args(const fs_sim* s, int j)
+{
+    const fs_graph* g = s->g;
+    fs::StepArgs a{};
+    a.X = s->d_X;
+    a.A = s->d_A;
+    a.bm[0] = s->d_bm[0];
+    a.bm[1] = s->d_bm[1];
+    a.sell_off = g->d_sell_off;
+    a.sell_col = g->d_sell_col;
+    a.n_thr = g->n_thr;
+    a.n_slices = g->n_slices;
+    a.sentinel = (int32_t)g->n;
+    a.m_base = g->n_thr;
+    a.n_m = g->n_m;
+    a.n_chunks = g->n_chunks;
+    a.n_sell_ctas = (g->n_slices + fs::kSellSlicesPerCta - 1) / fs::kSellSlicesPerCta;
+    a.m_ptr = g->d_m_ptr;
+    a.m_col = g->d_m_col;
+    a.m_warp_row = g->d_m_warp_row;
+    a.m_chunk_last = g->d_m_chunk_last;
+    a.e_m = g->e_m;
+    a.m_cnt = s->d_m_cnt;
+    a.m_tkt = s->d_m_tkt;
+    a.perm = g->d_perm;
+    a.M = s->M;
+    a.ctl = s->d_ctl;
+    a.deltas = s->d_deltas;
+    a.j = j;
+    a.n = (int32_t)g->n;
+    return a;
+}
+
+fs_status check_device_error(fs_sim* s)
+{
+    fs::DevCtl c;
+    FS_CUDA(s, cudaMemcpy(&c, s->d_ctl, sizeof(c), cudaMemcpyDeviceToHost));
+    if (c.error) {
+        s->failed = true;
+        if (c.error == fs::kErrTmaTimeout)
+            return fail(FS_ETIMEOUT, "a bounded device wait ran out (error word %d)", c.error);
+        return fail(FS_ECUDA, "device error word %d", c.error);
+    }
+    return FS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fs_version(void) { return "flashstep 0.1 sm_103a"; }
+
+const char* fs_last_error(void) { return g_err.c_str(); }
+
+fs_status fs_graph_create(int64_t n, const int64_t* row_ptr, const int32_t* col_ind, const float* weights,
+                          const fs_graph_opts* opts, void* stream, fs_graph** out)
+{
+    g_err.clear();
+    if (!out)
+        return fail(FS_EINVAL, "out is NULL");
+    *out = nullptr;
+    fs_graph_opts o{};
+    if (opts)
+        o = *opts;
+    if (weights)
+        return fail(FS_EUNSUPPORTED, "edge weights are not supported (unit weights only)");
+    if (n < 1 || n >= (int64_t)INT32_MAX)
+        return fail(FS_EINVAL, "n must be in [1, 2^31 - 1)");
+    if (!row_ptr)
+        return fail(FS_EINVAL, "row_ptr is NULL");
+    if (o.dispatch < FS_DISPATCH_AUTO || o.dispatch > FS_DISPATCH_MERGE)
+        return fail(FS_EINVAL, "unknown dispatch %d", o.dispatch);
+    if (o.thread_max_deg != 0 && (o.thread_max_deg < 31 || o.thread_max_deg > fs::kMaxThreadDeg))
+        return fail(FS_EINVAL, "thread_max_deg must be 0 or in [31, %d]", fs::kMaxThreadDeg);
+    if (o.device_input != 0 && o.device_input != 1)
+        return fail(FS_EINVAL, "device_input must be 0 or 1");
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool dev_in = o.device_input == 1;
+    int64_t nnz = 0;
+    if (!dev_in) {
+        if (row_ptr[0] != 0)
+            return fail(FS_EINVAL, "row_ptr[0] must be 0");
+        for (int64_t i = 0; i < n; ++i)
+            if (row_ptr[i + 1] < row_ptr[i])
+                return fail(FS_EINVAL, "row_ptr decreases at %lld", (long long)i);
+        nnz = row_ptr[n];
+        if (nnz > 0 && !col_ind)
+            return fail(FS_EINVAL, "col_ind is NULL");
+        for (int64_t e = 0; e < nnz; ++e)
+            if (col_ind[e] < 0 || col_ind[e] >= n)
+                return fail(FS_EINVAL, "col_ind[%lld] = %d out of range", (long long)e, col_ind[e]);
+    } else {
+        cudaError_t e = cudaMemcpy(&nnz, row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess)
+            return fail(FS_ECUDA, "reading row_ptr[n]: %s", cudaGetErrorString(e));
+        if (nnz < 0)
+            return fail(FS_EINVAL, "row_ptr[n] < 0");
+        if (nnz > 0 && !col_ind)
+            return fail(FS_EINVAL, "col_ind is NULL");
+    }
+
+    fs_graph* g = new fs_graph();
+    g->n = n;
+    g->nnz = nnz;
+    fs_status rc = FS_OK;
+    const int ni = (int)n;
+    int64_t* d_rp = nullptr;
+    int32_t* d_col = nullptr;
+    uint16_t* d_key = nullptr;
+    fs::IngestFlags* d_flags = nullptr;
+    int64_t* d_tmp = nullptr;
+    fs::IngestFlags fl{};
+    auto cleanup = [&]() {
+        if (!dev_in) {
+            cudaFree(d_rp);
+            cudaFree(d_col);
+        }
+        cudaFree(d_key);
+        cudaFree(d_flags);
+        cudaFree(d_tmp);
+    };
+#define G_CUDA(expr)                                                                                  \
+    do {                                                                                              \
+        cudaError_t e_ = (expr);                                                                      \
+        if (e_ != cudaSuccess) {                                                                      \
+            rc = fail(e_ == cudaErrorMemoryAllocation ? FS_ENOMEM : FS_ECUDA, "%s: %s", #expr,       \
+                      cudaGetErrorString(e_));                                                        \
+            goto done;                                                                                \
+        }                                                                                             \
+    } while (0)
+    {
+        if (dev_in) {
+            d_rp = const_cast<int64_t*>(row_ptr);
+            d_col = const_cast<int32_t*>(col_ind);
+        } else {
+            G_CUDA(dev_alloc(&d_rp, (size_t)n + 1, nullptr));
+            G_CUDA(dev_alloc(&d_col, (size_t)nnz, nullptr));
+            G_CUDA(cudaMemcpyAsync(d_rp, row_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st));
+            if (nnz)
+                G_CUDA(cudaMemcpyAsync(d_col, col_ind, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, st));
+        }
+        G_CUDA(dev_alloc(&g->d_deg, (size_t)n, &g->bytes));
+        G_CUDA(dev_alloc(&d_key, (size_t)n, nullptr));
+        G_CUDA(dev_alloc(&d_flags, 1, nullptr));
+        // pass 1: degrees, d_max, validity
+        G_CUDA(cudaMemsetAsync(d_flags, 0, sizeof(fs::IngestFlags), st));
+        G_CUDA(fs::launch_degrees(d_rp, ni, fs::kMaxThreadDeg, g->d_deg, d_key, d_flags, st));
+        if (dev_in)
+            G_CUDA(fs::launch_check_cols(d_col, nnz, ni, d_flags, st));
+        G_CUDA(cudaMemcpyAsync(&fl, d_flags, sizeof(fl), cudaMemcpyDeviceToHost, st));
+        G_CUDA(cudaStreamSynchronize(st));
+        if (fl.error) {
+            rc = fail(FS_EINVAL, fl.error == 2 ? "col_ind out of range" : "row_ptr is not a valid CSR row pointer");
+            goto done;
+        }
+        g->dmax = fl.dmax;
+        // class threshold (Section 5.5 auto-dispatch, adapted: a degree split)
+        bool all_thread = false;
+        if (o.dispatch == FS_DISPATCH_THREAD) {
+            all_thread = true;
+        } else if (o.dispatch == FS_DISPATCH_MERGE) {
+            g->t1 = fs::kMinMergeDegree - 1;
+        } else if (o.thread_max_deg > 0) {
+            g->t1 = o.thread_max_deg;
+        } else {
+            g->t1 = (g->dmax <= 64) ? g->dmax : 63;
+        }
+        if (all_thread) {
+            g->t1 = g->dmax;
+            g->n_thr = ni;
+            g->identity = true;
+        } else {
+            G_CUDA(cudaMemsetAsync(d_flags, 0, sizeof(fs::IngestFlags), st));
+            G_CUDA(fs::launch_degrees(d_rp, ni, g->t1, g->d_deg, d_key, d_flags, st));
+            G_CUDA(cudaMemcpyAsync(&fl, d_flags, sizeof(fl), cudaMemcpyDeviceToHost, st));
+            G_CUDA(cudaStreamSynchronize(st));
+            g->n_thr = fl.n_thr;
+            g->identity = fl.unsorted == 0;
+        }
+        g->n_m = ni - g->n_thr;
+        if (!g->identity) {
+            int32_t* deg_int = nullptr;
+            G_CUDA(dev_alloc(&g->d_perm, (size_t)n, &g->bytes));
+            G_CUDA(dev_alloc(&g->d_inv, (size_t)n, &g->bytes));
+            G_CUDA(dev_alloc(&deg_int, (size_t)n, nullptr));
+            G_CUDA(fs::stable_sort_by_key(d_key, g->d_deg, ni, g->t1 + 2, g->d_perm, g->d_inv, deg_int, st));
+            G_CUDA(cudaStreamSynchronize(st));
+            cudaFree(g->d_deg);
+            g->d_deg = deg_int;
+        }
+        // SELL-32 blocks of the thread class
+        g->n_slices = (g->n_thr + 31) / 32;
+        G_CUDA(dev_alloc(&g->d_sell_off, (size_t)g->n_slices + 1, &g->bytes));
+        G_CUDA(dev_alloc(&d_tmp, (size_t)std::max(g->n_slices, g->n_m) + 1, nullptr));
+        G_CUDA(fs::launch_sell_widths(g->d_deg, g->n_thr, g->n_slices, d_tmp, st));
+        G_CUDA(fs::exclusive_scan_i64(d_tmp, g->d_sell_off, g->n_slices, st));
+        G_CUDA(cudaMemcpyAsync(&g->sell_entries, g->d_sell_off + g->n_slices, sizeof(int64_t),
+                               cudaMemcpyDeviceToHost, st));
+        G_CUDA(cudaStreamSynchronize(st));
+        G_CUDA(dev_alloc(&g->d_sell_col, (size_t)g->sell_entries, &g->bytes));
+        G_CUDA(fs::launch_sell_fill(d_rp, d_col, g->d_perm, g->d_inv, g->d_deg, g->n_thr, g->n_slices,
+                                    g->d_sell_off, (int)n, g->d_sell_col, st));
+        // CSR and chunk tables of the merge class
+        if (g->n_m > 0) {
+            G_CUDA(dev_alloc(&g->d_m_ptr, (size_t)g->n_m + 1, &g->bytes));
+            G_CUDA(fs::launch_merge_degrees(g->d_deg, g->n_thr, g->n_m, d_tmp, st));
+            G_CUDA(fs::exclusive_scan_i64(d_tmp, g->d_m_ptr, g->n_m, st));
+            G_CUDA(cudaMemcpyAsync(&g->e_m, g->d_m_ptr + g->n_m, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+            G_CUDA(cudaStreamSynchronize(st));
+            const int64_t chunks = (g->e_m + fs::kMergeEPB - 1) / fs::kMergeEPB;
+            if (chunks >= INT32_MAX) {
+                rc = fail(FS_EUNSUPPORTED, "too many merge chunks");
+                goto done;
+            }
+            g->n_chunks = (int32_t)chunks;
+            const int64_t padded = chunks * fs::kMergeEPB;
+            G_CUDA(dev_alloc(&g->d_m_col, (size_t)padded, &g->bytes));
+            G_CUDA(fs::launch_merge_fill(d_rp, d_col, g->d_perm, g->d_inv, g->n_thr, g->n_m, g->d_m_ptr, g->e_m,
+                                         padded, (int)n, g->d_m_col, st));
+            G_CUDA(dev_alloc(&g->d_m_warp_row, (size_t)chunks * fs::kStepWarps, &g->bytes));
+            G_CUDA(dev_alloc(&g->d_m_chunk_last, (size_t)chunks, &g->bytes));
+            G_CUDA(fs::launch_merge_tables(g->d_m_ptr, g->n_m, g->e_m, g->n_chunks, g->d_m_warp_row,
+                                           g->d_m_chunk_last, st));
+        }
+        G_CUDA(cudaStreamSynchronize(st));
+    }
+done:
+#undef G_CUDA
+    cleanup();
+    if (rc != FS_OK) {
+        free_graph(g);
+        return rc;
+    }
+    *out = g;
+    return FS_OK;
+}
+
+fs_status fs_graph_info_get(const fs_graph* g, fs_graph_info* out)
+{
+    if (!g || !out)
+        return fail(FS_EINVAL, "NULL argument");
+    fs_graph_info i{};
+    i.n = g->n;
+    i.nnz = g->nnz;
+    i.d_max = g->dmax;
+    i.d_avg = g->n ? (double)g->nnz / (double)g->n : 0.0;
+    i.rho = i.d_avg > 0 ? (double)g->dmax / i.d_avg : 0.0;
+    i.n_thread = g->n_thr;
+    i.n_merge = g->n_m;
+    i.sell_entries = g->sell_entries;
+    i.merge_chunks = g->n_chunks;
+    i.thread_max_deg = g->t1;
+    i.identity_layout = g->identity ? 1 : 0;
+    i.device_bytes = g->bytes;
+    *out = i;
+    return FS_OK;
+}
+
+fs_status fs_graph_destroy(fs_graph* g)
+{
+    if (!g)
+        return fail(FS_EINVAL, "graph is NULL");
+    if (g->refs > 0)
+        return fail(FS_EBUSY, "%d simulation(s) still use this graph", g->refs);
+    free_graph(g);
+    return FS_OK;
+}
+
+fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* index_nodes, int64_t n_index,
+                      void* stream, fs_sim** out)
+{
+    g_err.clear();
+    if (!g || !out)
+        return fail(FS_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (g->failed)
+        return fail(FS_ESTATE, "graph is in a failed state");
+    fs_status st = check_params(params);
+    if (st != FS_OK)
+        return st;
+    if (n_index < 0 || n_index > g->n || (n_index > 0 && !index_nodes))
+        return fail(FS_EINVAL, "bad index list size");
+    {
+        std::vector<int32_t> v(index_nodes, index_nodes + n_index);
+        std::sort(v.begin(), v.end());
+        for (int64_t q = 0; q < n_index; ++q) {
+            if (v[q] < 0 || v[q] >= g->n)
+                return fail(FS_EINVAL, "index node %d out of range", v[q]);
+            if (q && v[q] == v[q - 1])
+                return fail(FS_EINVAL, "index node %d repeated", v[q]);
+        }
+    }
+    fs_sim* s = new fs_sim();
+    s->g = g;
+    s->p = *params;
+    s->M = to_model(*params);
+    s->age_bytes = params->age_dtype == FS_AGE_F32 ? 4 : 2;
+    const int64_t n = g->n;
+    int32_t* d_idx = nullptr;
+    auto bail = [&](fs_status rc) {
+        cudaFree(d_idx);
+        free_sim(s);
+        return rc;
+    };
+#define S_CUDA(expr)                                                                                  \
+    do {                                                                                              \
+        cudaError_t e_ = (expr);                                                                      \
+        if (e_ != cudaSuccess)                                                                        \
+            return bail(fail(e_ == cudaErrorMemoryAllocation ? FS_ENOMEM : FS_ECUDA, "%s: %s", #expr, \
+                             cudaGetErrorString(e_)));                                                \
+    } while (0)
+    if (stream) {
+        s->stream = (cudaStream_t)stream;
+    } else {
+        S_CUDA(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+        s->own_stream = true;
+    }
+    cudaStream_t cs = s->stream;
+    const size_t words = (size_t)(n >> 5) + 1;
+    S_CUDA(dev_alloc(&s->d_X, (size_t)n, nullptr));
+    S_CUDA(cudaMalloc(&s->d_A, (size_t)n * s->age_bytes));
+    S_CUDA(dev_alloc(&s->d_bm[0], words, nullptr));
+    S_CUDA(dev_alloc(&s->d_bm[1], words, nullptr));
+    S_CUDA(dev_alloc(&s->d_m_cnt, (size_t)std::max(g->n_m, 1), nullptr));
+    S_CUDA(dev_alloc(&s->d_m_tkt, (size_t)std::max(g->n_m, 1), nullptr));
+    S_CUDA(dev_alloc(&s->d_ctl, 1, nullptr));
+    S_CUDA(dev_alloc(&s->d_deltas, (size_t)fs::kMaxGraphSteps * fs::kDeltaFields, nullptr));
+    S_CUDA(cudaMemsetAsync(s->d_X, 0, (size_t)n, cs));
+    S_CUDA(cudaMemsetAsync(s->d_A, 0, (size_t)n * s->age_bytes, cs));
+    S_CUDA(cudaMemsetAsync(s->d_bm[0], 0, words * 4, cs));
+    S_CUDA(cudaMemsetAsync(s->d_bm[1], 0, words * 4, cs));
+    S_CUDA(cudaMemsetAsync(s->d_m_cnt, 0, sizeof(int32_t) * std::max(g->n_m, 1), cs));
+    S_CUDA(cudaMemsetAsync(s->d_m_tkt, 0, sizeof(uint32_t) * std::max(g->n_m, 1), cs));
+    S_CUDA(cudaMemsetAsync(s->d_ctl, 0, sizeof(fs::DevCtl), cs));
+    S_CUDA(cudaMemsetAsync(s->d_deltas, 0, sizeof(unsigned long long) * fs::kMaxGraphSteps * fs::kDeltaFields, cs));
+    if (n_index > 0) {
+        S_CUDA(dev_alloc(&d_idx, (size_t)n_index, nullptr));
+        S_CUDA(cudaMemcpyAsync(d_idx, index_nodes, sizeof(int32_t) * n_index, cudaMemcpyHostToDevice, cs));
+        S_CUDA(fs::launch_set_index(s->d_X, d_idx, n_index, g->d_inv, params->index_state, cs));
+    }
+    S_CUDA(fs::launch_refresh(s->d_X, (int)n, g->d_deg, s->d_bm[0], s->d_bm[1], s->d_ctl, cs));
+    S_CUDA(cudaStreamSynchronize(cs));
+#undef S_CUDA
+    cudaFree(d_idx);
+    g->refs += 1;
+    *out = s;
+    return FS_OK;
+}
+
+static fs_status ensure_graph(fs_sim* s, int K)
+{
+    if (s->gexec && s->gK == K)
+        return FS_OK;
+    if (s->gexec) {
+        cudaGraphExecDestroy(s->gexec);
+        s->gexec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    FS_CUDA(s, cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int j = 0; j < K && e == cudaSuccess; ++j)
+        e = fs::launch_step(step_args(s, j), s->p.age_dtype, s->stream);
+    if (e == cudaSuccess)
+        e = fs::launch_run_epilogue(s->d_ctl, s->d_deltas, K, s->p.model, s->stream);
+    cudaError_t e2 = cudaStreamEndCapture(s->stream, &graph);
+    FS_CUDA(s, e);
+    FS_CUDA(s, e2);
+    e = cudaGraphInstantiate(&s->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    FS_CUDA(s, e);
+    s->gK = K;
+    return FS_OK;
+}
+
+static fs_status run_enqueue(fs_sim* s, int64_t steps, int32_t graph_steps, uint32_t* counts_dev,
+                             cudaEvent_t* replay_ev)
+{
+    if (!s)
+        return fail(FS_EINVAL, "sim is NULL");
+    if (s->failed)
+        return fail(FS_ESTATE, "sim is in a failed state");
+    if (steps < 0)
+        return fail(FS_EINVAL, "steps must be >= 0");
+    const int K = graph_steps == 0 ? 50 : graph_steps;
+    if (K < 1 || K > fs::kMaxGraphSteps)
+        return fail(FS_EINVAL, "graph_steps must be in [1, %d]", fs::kMaxGraphSteps);
+    FS_CUDA(s, fs::launch_run_begin(s->d_ctl, counts_dev, s->stream));
+    const int64_t full = steps / K;
+    const int rem = (int)(steps % K);
+    if (full > 0) {
+        fs_status st = ensure_graph(s, K);
+        if (st != FS_OK)
+            return st;
+        for (int64_t r = 0; r < full; ++r) {
+            if (replay_ev)
+                FS_CUDA(s, cudaEventRecord(replay_ev[r], s->stream));
+            FS_CUDA(s, cudaGraphLaunch(s->gexec, s->stream));
+        }
+        fs::g_launch_count += (unsigned long long)full * (K + 1);
+    }
+    if (replay_ev)
+        FS_CUDA(s, cudaEventRecord(replay_ev[full], s->stream));
+    if (rem > 0) {
+        for (int j = 0; j < rem; ++j)
+            FS_CUDA(s, fs::launch_step(step_args(s, j), s->p.age_dtype, s->stream));
+        FS_CUDA(s, fs::launch_run_epilogue(s->d_ctl, s->d_deltas, rem, s->p.model, s->stream));
+    }
+    if (replay_ev)
+        FS_CUDA(s, cudaEventRecord(replay_ev[full + 1], s->stream));
+    return FS_OK;
+}
+
+fs_status fs_sim_run_async(fs_sim* s, int64_t steps, int32_t graph_steps, uint32_t* counts_dev)
+{
+    return run_enqueue(s, steps, graph_steps, counts_dev, nullptr);
+}
+
+fs_status fs_sim_run_timed(fs_sim* s, int64_t steps, int32_t graph_steps, uint32_t* counts_dev,
+                            float* replay_ms, int64_t* n_replays)
+{
+    if (!s || !replay_ms || !n_replays)
+        return fail(FS_EINVAL, "NULL argument");
+    const int K = graph_steps == 0 ? 50 : graph_steps;
+    if (K < 1 || K > fs::kMaxGraphSteps || steps < 0)
+        return fail(FS_EINVAL, "bad steps or graph_steps");
+    const int64_t full = steps / K;
+    std::vector<cudaEvent_t> ev((size_t)full + 2, nullptr);
+    for (auto& e : ev)
+        FS_CUDA(s, cudaEventCreate(&e));
+    fs_status st = run_enqueue(s, steps, graph_steps, counts_dev, ev.data());
+    if (st == FS_OK)
+        st = fs_sim_sync(s);
+    if (st == FS_OK) {
+        for (int64_t r = 0; r < full; ++r)
+            cudaEventElapsedTime(&replay_ms[r], ev[r], ev[r + 1]);
+        cudaEventElapsedTime(&replay_ms[full], ev[full], ev[full + 1]);
+        *n_replays = full + 1;
+    }
+    for (auto& e : ev)
+        cudaEventDestroy(e);
+    return st;
+}
+
+fs_status fs_kernel_launches(uint64_t* count)
+{
+    if (!count)
+        return fail(FS_EINVAL, "NULL argument");
+    *count = fs::g_launch_count.load();
+    return FS_OK;
+}
+
+fs_status fs_sim_sync(fs_sim* s)
+{
+    if (!s)
+        return fail(FS_EINVAL, "sim is NULL");
+    if (s->failed)
+        return fail(FS_ESTATE, "sim is in a failed state");
+    FS_CUDA(s, cudaStreamSynchronize(s->stream));
+    return check_device_error(s);
+}
+
+fs_status fs_sim_run(fs_sim* s, int64_t steps, int32_t graph_steps, uint32_t* counts_out)
+{
+    if (!s)
+        return fail(FS_EINVAL, "sim is NULL");
+    if (s->failed)
+        return fail(FS_ESTATE, "sim is in a failed state");
+    if (steps < 0)
+        return fail(FS_EINVAL, "steps must be >= 0");
+    uint32_t* dc = nullptr;
+    if (counts_out) {
+        const int64_t need = (steps + 1) * 4;
+        if (need > s->counts_cap) {
+            cudaFree(s->d_counts);
+            s->d_counts = nullptr;
+            s->counts_cap = 0;
+            FS_CUDA(s, cudaMalloc(&s->d_counts, sizeof(uint32_t) * need));
+            s->counts_cap = need;
+        }
+        dc = s->d_counts;
+    }
+    fs_status st = fs_sim_run_async(s, steps, graph_steps, dc);
+    if (st != FS_OK)
+        return st;
+    if (counts_out)
+        FS_CUDA(s, cudaMemcpyAsync(counts_out, dc, sizeof(uint32_t) * (steps + 1) * 4, cudaMemcpyDeviceToHost,
+                                   s->stream));
+    return fs_sim_sync(s);
+}
+
+fs_status fs_sim_step(fs_sim* s, uint32_t* counts_out)
+{
+    uint32_t c[8];
+    fs_status st = fs_sim_run(s, 1, 1, c);
+    if (st == FS_OK && counts_out)
+        memcpy(counts_out, c + 4, sizeof(uint32_t) * 4);
+    return st;
+}
+
+fs_status fs_sim_get_state(fs_sim* s, uint8_t* state, void* age, int64_t* step)
+{
+    if (!s)
+        return fail(FS_EINVAL, "sim is NULL");
+    if (s->failed)
+        return fail(FS_ESTATE, "sim is in a failed state");
+    const fs_graph* g = s->g;
+    const int n = (int)g->n;
+    FS_CUDA(s, cudaStreamSynchronize(s->stream));
+    if (step) {
+        fs::DevCtl c;
+        FS_CUDA(s, cudaMemcpy(&c, s->d_ctl, sizeof(c), cudaMemcpyDeviceToHost));
+        *step = c.step;
+    }
+    if (!state && !age)
+        return FS_OK;
+    void* tmp = nullptr;
+    if (!g->identity)
+        FS_CUDA(s, cudaMalloc(&tmp, (size_t)n * 4));
+    fs_status rc = FS_OK;
+    auto copy_out = [&](const void* dsrc, void* hdst, int eb) -> cudaError_t {
+        if (g->identity)
+            return cudaMemcpy(hdst, dsrc, (size_t)n * eb, cudaMemcpyDeviceToHost);
+        cudaError_t e = fs::launch_to_original(dsrc, tmp, eb, g->d_perm, n, s->stream);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(s->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(hdst, tmp, (size_t)n * eb, cudaMemcpyDeviceToHost);
+        return e;
+    };
+    cudaError_t e = cudaSuccess;
+    if (state)
+        e = copy_out(s->d_X, state, 1);
+    if (e == cudaSuccess && age)
+        e = copy_out(s->d_A, age, s->age_bytes);
+    if (e != cudaSuccess) {
+        s->failed = true;
+        rc = fail(FS_ECUDA, "get_state: %s", cudaGetErrorString(e));
+    }
+    cudaFree(tmp);
+    return rc;
+}
+
+// storage value of an age: S and R ages must be +-0, E and I ages finite and >= 0
+static bool age_ok(const void* age, int dtype, int64_t i, bool must_be_zero)
+{
+    if (dtype == FS_AGE_F32) {
+        const float v = ((const float*)age)[i];
+        return must_be_zero ? (v == 0.0f) : (std::isfinite(v) && v >= 0.0f);
+    }
+    const uint16_t b = ((const uint16_t*)age)[i];
+    if ((b & 0x7fffu) == 0)
+        return true;
+    if (must_be_zero || (b & 0x8000u))
+        return false;
+    if (dtype == FS_AGE_F16)
+        return ((b >> 10) & 0x1fu) != 0x1fu;
+    return ((b >> 7) & 0xffu) != 0xffu;
+}
+
+fs_status fs_sim_set_state(fs_sim* s, const uint8_t* state, const void* age, int64_t step)
+{
+    if (!s || !state || !age)
+        return fail(FS_EINVAL, "NULL argument");
+    if (s->failed)
+        return fail(FS_ESTATE, "sim is in a failed state");
+    if (step < 0 || step >= ((int64_t)1 << 32))
+        return fail(FS_EINVAL, "step must be in [0, 2^32)");
+    const fs_graph* g = s->g;
+    const int n = (int)g->n;
+    for (int64_t i = 0; i < n; ++i) {
+        const int x = state[i];
+        if (x > FS_R || (s->p.model == FS_SIR && x == FS_E))
+            return fail(FS_EINVAL, "state[%lld] = %d is not a compartment of the model", (long long)i, x);
+        if (!age_ok(age, s->p.age_dtype, i, x == FS_S || x == FS_R))
+            return fail(FS_EINVAL, "age[%lld] invalid (S/R ages must be 0; E/I ages finite and >= 0)",
+                        (long long)i);
+    }
+    FS_CUDA(s, cudaStreamSynchronize(s->stream));
+    void* tmp = nullptr;
+    if (!g->identity)
+        FS_CUDA(s, cudaMalloc(&tmp, (size_t)n * 4));
+    cudaError_t e = cudaSuccess;
+    auto copy_in = [&](const void* hsrc, void* ddst, int eb) -> cudaError_t {
+        if (g->identity)
+            return cudaMemcpy(ddst, hsrc, (size_t)n * eb, cudaMemcpyHostToDevice);
+        cudaError_t e2 = cudaMemcpy(tmp, hsrc, (size_t)n * eb, cudaMemcpyHostToDevice);
+        if (e2 == cudaSuccess)
+            e2 = fs::launch_from_original(tmp, ddst, eb, g->d_inv, n, s->stream);
+        if (e2 == cudaSuccess)
+            e2 = cudaStreamSynchronize(s->stream);
+        return e2;
+    };
+    e = copy_in(state, s->d_X, 1);
+    if (e == cudaSuccess)
+        e = copy_in(age, s->d_A, s->age_bytes);
+    cudaFree(tmp);
+    if (e != cudaSuccess) {
+        s->failed = true;
+        return fail(FS_ECUDA, "set_state: %s", cudaGetErrorString(e));
+    }
+    fs::DevCtl c{};
+    c.step = step;
+    FS_CUDA(s, cudaMemcpy(s->d_ctl, &c, sizeof(c), cudaMemcpyHostToDevice));
+    FS_CUDA(s, fs::launch_refresh(s->d_X, n, g->d_deg, s->d_bm[0], s->d_bm[1], s->d_ctl, s->stream));
+    FS_CUDA(s, cudaStreamSynchronize(s->stream));
+    return FS_OK;
+}
+
+fs_status fs_sim_work(const fs_sim* s, uint64_t* s_degree_sum, uint64_t* s_node_sum, int64_t* steps_run)
+{
+    if (!s)
+        return fail(FS_EINVAL, "sim is NULL");
+    fs::DevCtl c;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(&c, s->d_ctl, sizeof(c), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+        return fail(FS_ECUDA, "fs_sim_work: %s", cudaGetErrorString(e));
+    if (s_degree_sum)
+        *s_degree_sum = c.ds_total;
+    if (s_node_sum)
+        *s_node_sum = c.s_total;
+    if (steps_run)
+        *steps_run = c.step;
+    return FS_OK;
+}
+
+fs_status fs_sim_destroy(fs_sim* s)
+{
+    if (!s)
+        return fail(FS_EINVAL, "sim is NULL");
+    cudaStreamSynchronize(s->stream);
+    s->g->refs -= 1;
+    free_sim(s);
+    return FS_OK;
+}
+
+fs_status fs_eval_hazard(const fs_law* law, const float* tau_dev, float* h_dev, int64_t n, void* stream)
+{
+    if (!law || n < 0 || (n > 0 && (!tau_dev || !h_dev)))
+        return fail(FS_EINVAL, "bad argument");
+    fs_status st = check_law(*law, "eval", false);
+    if (st != FS_OK)
+        return st;
+    cudaError_t e = fs::launch_eval_hazard(to_lawf(*law), tau_dev, h_dev, n, (cudaStream_t)stream);
+    if (e != cudaSuccess)
+        return fail(FS_ECUDA, "fs_eval_hazard: %s", cudaGetErrorString(e));
+    return FS_OK;
+}
+
+fs_status fs_eval_uniforms(uint64_t seed, uint32_t replicate, int64_t step, const int32_t* nodes_dev, float* u_dev,
+                           int64_t n, void* stream)
+{
+    if (n < 0 || (n > 0 && (!nodes_dev || !u_dev)) || step < 0 || step >= ((int64_t)1 << 32))
+        return fail(FS_EINVAL, "bad argument");
+    cudaError_t e = fs::launch_eval_uniforms((uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), replicate,
+                                             (uint32_t)step, nodes_dev, u_dev, n, (cudaStream_t)stream);
+    if (e != cudaSuccess)
+        return fail(FS_ECUDA, "fs_eval_uniforms: %s", cudaGetErrorString(e));
+    return FS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,184 @@
+// fs_device.cuh -- device building blocks of the fused renewal step:
+// Philox4x32-10 uniforms, FP32 hazards, and the per-node tail (hazard ->
+// Bernoulli -> transition -> renewal age) of FlashSpread (arXiv 2604.22092),
+// Algorithm 3 at a fixed step.
+#pragma once
+
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "fs_internal.h"
+
+namespace fs {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the
+// multiply-xor bijection on a 128-bit counter under a 64-bit key bumped by
+// the two Weyl constants between rounds. Replaces the paper's
+// tl.rand(seed + step_id, node_id) (Appendix A) with a draw keyed by
+// (seed, replicate, step, node) so that every traversal class, packing and
+// batching draws the same number for the same node-step.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+    constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    constexpr uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += W0;
+            k1 += W1;
+        }
+        const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+        const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// u = (w >> 8) * 2^-24, exactly representable in FP32.
+__device__ __forceinline__ float uniform24(uint32_t key0, uint32_t key1, uint32_t rep,
+                                           uint32_t step, uint32_t node)
+{
+    const uint4 w = philox4x32_10(make_uint4(node, step, rep >> 2, 0u), key0, key1);
+    const uint32_t sel = rep & 3u;
+    const uint32_t word = sel == 0 ? w.x : sel == 1 ? w.y : sel == 2 ? w.z : w.w;
+    return (float)(word >> 8) * 5.9604644775390625e-08f;
+}
+
+// ---------------------------------------------------------------------------
+// Hazards in FP32 (Section 5.1; Proposition 1 for the log-normal).
+//
+// The log-normal hazard h = sqrt(2/pi) / (tau sigma erfcx(z)) is
+// exponentially sensitive to z when z << 0 (young ages): its relative error
+// is about 2|z| times the absolute error of z. So z = (ln tau - mu) /
+// (sigma sqrt 2) is formed as an unevaluated float pair (error-free sums and
+// fma products; ln tau = e ln2 + log1p(m - 1) with ln2 split in two), and for
+// z < -2 the hazard is evaluated as sqrt(2/pi)/sigma * e^{-z^2} / (tau
+// erfc(z)) with z^2 split exactly, erfc(z) = 2 - erfc(-z). For z >= -2 the
+// CUDA erfcxf of the rounded z is accurate enough. Every operation is FP32.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ float hazard_lognormal(const LawF& L, float tau)
+{
+    if (!(tau > 0.0f))
+        return 0.0f;
+    constexpr float kLn2Hi = 0.693145751953125f;          // ln 2 to 16 bits (e * kLn2Hi is exact)
+    constexpr float kLn2Lo = 1.4286067653302226e-06f;     // ln 2 - kLn2Hi
+    int e;
+    float m = frexpf(tau, &e);                            // tau = m 2^e, m in [0.5, 1)
+    if (m < 0.70710678f) {
+        m = m * 2.0f;
+        e -= 1;
+    }
+    const float lm = log1pf(__fsub_rn(m, 1.0f));          // m - 1 is exact
+    float a_hi, a_lo;
+    two_sum(__fmul_rn((float)e, kLn2Hi), lm, a_hi, a_lo);
+    a_lo = __fadd_rn(a_lo, __fmul_rn((float)e, kLn2Lo));
+    float d_hi, d_lo;
+    two_sum(a_hi, -L.p0, d_hi, d_lo);                     // ln tau - mu
+    d_lo = __fadd_rn(d_lo, __fsub_rn(a_lo, L.p3));
+    const float z_hi = __fmul_rn(d_hi, L.p1);
+    const float z_lo = __fadd_rn(__fmaf_rn(d_hi, L.p1, -z_hi),
+                                 __fadd_rn(__fmul_rn(d_hi, L.p4), __fmul_rn(d_lo, L.p1)));
+    const float zh = __fadd_rn(z_hi, z_lo);
+    const float zl = __fsub_rn(z_lo, __fsub_rn(zh, z_hi));
+    if (zh < -2.0f) {
+        const float s_hi = __fmul_rn(zh, zh);
+        const float s_lo = __fadd_rn(__fmaf_rn(zh, zh, -s_hi), __fmul_rn(__fmul_rn(2.0f, zh), zl));
+        const float ez = __fmul_rn(expf(-s_hi), __fsub_rn(1.0f, s_lo));   // e^{-z^2}
+        const float erfc_z = __fsub_rn(2.0f, erfcf(-zh));
+        return __fdiv_rn(__fmul_rn(L.p2, ez), __fmul_rn(tau, erfc_z));
+    }
+    return __fdiv_rn(L.p2, __fmul_rn(tau, erfcxf(zh)));
+}
+
+__device__ __forceinline__ float hazard(const LawF& L, float tau)
+{
+    switch (L.kind) {
+    case kLawExp:
+        return L.p0;
+    case kLawLogNormal:
+        return hazard_lognormal(L, tau);
+    case kLawWeibull:
+        // h = (k/s) (tau/s)^(k-1); powf(0, 0) = 1 gives h(0) = 1/s for k = 1
+        return L.p0 * powf(tau * L.p1, L.p2);
+    case kLawErlang: {
+        // h = r (r tau)^(k-1)/(k-1)! / sum_{n<k} (r tau)^n / n!
+        const float r = L.p0;
+        const float x = r * tau;
+        if (x <= 1.0f) {
+            float t = 1.0f, s = 1.0f;
+            for (int n = 1; n < L.k; ++n) {
+                t *= x / (float)n;
+                s += t;
+            }
+            return r * t / s;
+        }
+        // same ratio divided through by x^(k-1)/(k-1)!: r / sum_j (k-1)!/(k-1-j)! x^-j
+        const float y = 1.0f / x;
+        float s = 1.0f;
+        for (int m = 1; m < L.k; ++m)
+            s = 1.0f + (float)m * y * s;
+        return r / s;
+    }
+    default:
+        return 0.0f;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Age storage: FP32 math, round-to-nearest-even on the store (Section 5.7).
+// ---------------------------------------------------------------------------
+template <typename AgeT> struct AgeIO;
+template <> struct AgeIO<float> {
+    static __device__ __forceinline__ float load(float v) { return v; }
+    static __device__ __forceinline__ float store(float v) { return v; }
+};
+template <> struct AgeIO<__half> {
+    static __device__ __forceinline__ float load(__half v) { return __half2float(v); }
+    static __device__ __forceinline__ __half store(float v) { return __float2half_rn(v); }
+};
+template <> struct AgeIO<__nv_bfloat16> {
+    static __device__ __forceinline__ float load(__nv_bfloat16 v) { return __bfloat162float(v); }
+    static __device__ __forceinline__ __nv_bfloat16 store(float v) { return __float2bfloat16_rn(v); }
+};
+
+struct TailResult {
+    int x;        // new compartment
+    float age;    // new age (FP32 value, rounded on store by the caller)
+    bool fired;
+};
+
+// Bounded wait on an mbarrier phase (TMA completion). Returns false when the
+// iteration limit runs out; the caller records an error and skips the data.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar_smem, uint32_t phase, uint32_t limit)
+{
+    for (uint32_t it = 0; it < limit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 1000;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(mbar_smem), "r"(phase)
+            : "memory");
+        if (done)
+            return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+}  // namespace fs

@@ -1,0 +1,99 @@
+// fs_internal.h -- definitions shared by the CUDA translation units of
+// libflashstep (not part of the public C ABI in include/fs.h).
+#pragma once
+
+#include <cstdint>
+
+namespace fs {
+
+enum { kS = 0, kE = 1, kI = 2, kR = 3 };
+enum { kSIR = 0, kSEIR = 1 };
+enum { kLawNone = 0, kLawExp = 1, kLawLogNormal = 2, kLawWeibull = 3, kLawErlang = 4 };
+enum { kAgeF32 = 0, kAgeF16 = 1, kAgeBF16 = 2 };
+
+// FP32 law constants prepared on the host (double -> float once):
+//   EXP:       p0 = rate
+//   LOGNORMAL: mu = p0 + p3 and 1/(sigma sqrt 2) = p1 + p4 (hi/lo float
+//              pairs), p2 = sqrt(2/pi)/sigma
+//   WEIBULL:   p0 = k/s, p1 = 1/s, p2 = k - 1
+//   ERLANG:    p0 = rate, k = stages
+struct LawF {
+    int32_t kind;
+    int32_t k;
+    float p0, p1, p2, p3, p4;
+};
+
+struct ModelF {
+    int32_t model;
+    float beta;
+    float dt;
+    uint32_t key0, key1, rep;
+    LawF lat, inf;
+};
+
+constexpr int kWarp = 32;
+constexpr int kStepThreads = 256;                 // 8 warps per CTA
+constexpr int kStepWarps = kStepThreads / kWarp;
+constexpr int kSellSlicesPerCta = kStepWarps;     // one 32-node SELL slice per warp
+constexpr int kMergeWindowsPerWarp = 16;          // 16 x 32-edge windows per warp
+constexpr int kMergeEdgesPerWarp = kMergeWindowsPerWarp * kWarp;   // 512
+constexpr int kMergeEPB = kMergeEdgesPerWarp * kStepWarps;         // 4096 edges per CTA
+constexpr int kMinMergeDegree = 32;               // keeps <= 18 rows per warp range
+constexpr int kMergeMaxRows = kMergeEPB / kMinMergeDegree + 2;     // rows one chunk can touch
+constexpr int kMaxThreadDeg = 255;                // bucket cap of the degree sort
+constexpr uint32_t kWaitLimit = 1u << 20;         // bounded mbarrier waits
+constexpr int kMaxGraphSteps = 256;              // steps per captured graph / epilogue
+
+// Device-resident control block of one simulation (the persistent scalars of
+// Algorithm 2: step counter; plus running counts and work accounting).
+struct DevCtl {
+    int64_t step;                 // index of the next step
+    int64_t row;                  // next row of the counts output
+    uint32_t* out;                // counts output ((steps+1) x 4) or null
+    unsigned long long ds_cur;    // sum of degrees of the current S nodes
+    unsigned long long ds_total;  // sum over run steps of ds at step start
+    unsigned long long s_total;   // sum over run steps of |S| at step start
+    uint32_t counts[4];           // counts of the current state
+    int32_t error;                // device error word (0 = ok)
+    int32_t pad_;
+};
+
+enum { kErrNone = 0, kErrTmaTimeout = 1, kErrBadState = 2, kErrBadGraph = 3 };
+
+// Per-step deltas accumulated by the step kernel (atomics, skipped when 0):
+// [0] nodes that left S, [1] E -> I, [2] I -> R, [3] sum of degrees of the
+// nodes that left S.
+constexpr int kDeltaFields = 4;
+
+// Everything the fused step kernel reads, passed by value.
+struct StepArgs {
+    uint8_t* X;                   // compartments, internal order
+    void* A;                      // ages (f32/f16/bf16), internal order
+    uint32_t* bm[2];              // infectious bitmaps; step k reads bm[k&1]
+    // one-thread-per-node class: SELL-32 over internal ids [0, n_thr)
+    const int64_t* sell_off;      // [n_slices + 1] entry offsets
+    const int32_t* sell_col;      // column-major 32-wide blocks, padding = sentinel
+    int32_t n_thr;
+    int32_t n_slices;
+    int32_t sentinel;             // id whose bitmap bit is always 0 (= n)
+    // merge class: internal ids [m_base, m_base + n_m), CSR rows relative
+    int32_t m_base;
+    int32_t n_m;
+    int32_t n_chunks;             // kMergeEPB-edge chunks
+    int32_t n_sell_ctas;
+    const int64_t* m_ptr;         // [n_m + 1], m_ptr[0] = 0
+    const int32_t* m_col;         // [n_chunks * kMergeEPB], padded with sentinel
+    const int32_t* m_warp_row;    // [n_chunks * kStepWarps] row of each warp range start
+    const int32_t* m_chunk_last;  // [n_chunks] row containing the chunk's last edge
+    int64_t e_m;                  // edges of the merge class
+    int32_t* m_cnt;               // [n_m] cross-chunk partial counts (scratch)
+    uint32_t* m_tkt;              // [n_m] cross-chunk tickets (scratch)
+    const int32_t* perm;          // internal -> original id, null = identity
+    ModelF M;
+    DevCtl* ctl;
+    unsigned long long* deltas;   // [K][kDeltaFields]
+    int32_t j;                    // step offset within the launch sequence
+    int32_t n;
+};
+
+}  // namespace fs

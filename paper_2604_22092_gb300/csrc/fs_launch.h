@@ -1,0 +1,57 @@
+// fs_launch.h -- host-side launchers of the kernels in fs_step.cu and
+// fs_ingest.cu (internal to libflashstep).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+
+#include "fs_internal.h"
+
+namespace fs {
+
+// kernels enqueued by this library (graph replays add their node count)
+extern std::atomic<unsigned long long> g_launch_count;
+
+// fs_step.cu
+cudaError_t launch_step(const StepArgs& a, int age_dtype, cudaStream_t s);
+cudaError_t launch_run_begin(DevCtl* ctl, uint32_t* out, cudaStream_t s);
+cudaError_t launch_run_epilogue(DevCtl* ctl, unsigned long long* deltas, int K, int model, cudaStream_t s);
+cudaError_t launch_refresh(const uint8_t* X, int n, const int32_t* deg, uint32_t* bm0, uint32_t* bm1, DevCtl* ctl,
+                           cudaStream_t s);
+cudaError_t launch_set_index(uint8_t* X, const int32_t* idx, int64_t n_idx, const int32_t* inv, int state,
+                             cudaStream_t s);
+cudaError_t launch_to_original(const void* in, void* out, int elem_bytes, const int32_t* perm, int n, cudaStream_t s);
+cudaError_t launch_from_original(const void* in, void* out, int elem_bytes, const int32_t* inv, int n,
+                                 cudaStream_t s);
+cudaError_t launch_eval_hazard(const LawF& L, const float* tau, float* h, int64_t n, cudaStream_t s);
+cudaError_t launch_eval_uniforms(uint32_t key0, uint32_t key1, uint32_t rep, uint32_t step, const int32_t* nodes,
+                                 float* u, int64_t n, cudaStream_t s);
+
+// fs_ingest.cu
+struct IngestFlags {
+    int32_t dmax;
+    int32_t unsorted;     // 1 when the class keys are not nondecreasing
+    int32_t error;        // 1 = bad row_ptr, 2 = col_ind out of range
+    int32_t n_thr;        // nodes with degree <= thread_max_deg
+};
+cudaError_t launch_degrees(const int64_t* row_ptr, int n, int t1, int32_t* deg, uint16_t* key, IngestFlags* flags,
+                           cudaStream_t s);
+cudaError_t launch_check_cols(const int32_t* col, int64_t nnz, int n, IngestFlags* flags, cudaStream_t s);
+// stable counting sort of nodes by key (keys < n_buckets): perm[pos] = i, inv[i] = pos, deg_int[pos] = deg[i]
+cudaError_t stable_sort_by_key(const uint16_t* key, const int32_t* deg, int n, int n_buckets, int32_t* perm,
+                               int32_t* inv, int32_t* deg_int, cudaStream_t s);
+// out[0..n] = exclusive prefix sums of in[0..n-1] (out[n] = total)
+cudaError_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
+cudaError_t launch_sell_widths(const int32_t* deg_int, int n_thr, int n_slices, int64_t* width32, cudaStream_t s);
+cudaError_t launch_sell_fill(const int64_t* row_ptr, const int32_t* col, const int32_t* perm, const int32_t* inv,
+                             const int32_t* deg_int, int n_thr, int n_slices, const int64_t* sell_off, int sentinel,
+                             int32_t* sell_col, cudaStream_t s);
+cudaError_t launch_merge_degrees(const int32_t* deg_int, int m_base, int n_m, int64_t* out, cudaStream_t s);
+cudaError_t launch_merge_fill(const int64_t* row_ptr, const int32_t* col, const int32_t* perm, const int32_t* inv,
+                              int m_base, int n_m, const int64_t* m_ptr, int64_t e_m, int64_t padded, int sentinel,
+                              int32_t* m_col, cudaStream_t s);
+cudaError_t launch_merge_tables(const int64_t* m_ptr, int n_m, int64_t e_m, int n_chunks, int32_t* warp_row,
+                                int32_t* chunk_last, cudaStream_t s);
+
+}  // namespace fs

@@ -1,0 +1,570 @@
+// fs_step.cu -- the fused renewal tau-leaping step (FlashSpread, arXiv
+// 2604.22092, Algorithm 3 at a fixed step) for one realisation, plus the
+// small kernels around it (run begin/epilogue, state refresh, relabelling,
+// diagnostics).
+//
+// One launch performs one whole step for every node. The grid has two kinds
+// of CTA (Section 5.5, degree-aware traversal):
+//   * merge CTAs (blockIdx < n_chunks): one 4096-edge chunk of the merge
+//     class (rows of degree > thread_max_deg). The chunk's column block is
+//     staged in shared memory by one bulk TMA copy; each warp counts the
+//     infectious in-neighbours of the rows overlapping its 512 edges with
+//     ballots over 32-edge windows; rows that span chunks combine integer
+//     partial counts with an atomic ticket (the last chunk runs the tail), so
+//     the result is exact and independent of scheduling.
+//   * SELL CTAs: eight 32-node slices of the one-thread-per-node class stored
+//     as SELL-32 (column-major 32-wide blocks), one lane per node.
+// Only S nodes read their row; the neighbour infectivity is a 1-bit
+// infectious bitmap (Eq. 8 with s = 1), read through the read-only path and
+// double-buffered by step parity; the next bitmap is written with warp
+// ballots. States and ages are updated in place (each node has one owner).
+#include <cuda_runtime.h>
+
+#include "fs_device.cuh"
+#include "fs_launch.h"
+
+namespace fs {
+
+std::atomic<unsigned long long> g_launch_count{0};
+
+constexpr uint32_t kFull = 0xffffffffu;
+
+__device__ __forceinline__ void record_error(DevCtl* ctl, int code)
+{
+    atomicCAS(&ctl->error, 0, code);
+}
+
+__device__ __forceinline__ uint32_t orig_id(const int32_t* perm, int i)
+{
+    return perm ? (uint32_t)__ldg(perm + i) : (uint32_t)i;
+}
+
+// rate, Bernoulli and transition for one node; the original id is looked
+// up only when a uniform is needed (p > 0)
+__device__ __forceinline__ TailResult tail_at(const ModelF& M, int x, float age, uint32_t c,
+                                              const int32_t* perm, int i, uint32_t step)
+{
+    float lambda = 0.0f;
+    if (x == kS)
+        lambda = M.beta * (float)c;
+    else if (x == kE)
+        lambda = hazard(M.lat, age);
+    else if (x == kI)
+        lambda = hazard(M.inf, age);
+    bool fired = false;
+    if (lambda > 0.0f) {
+        const float p = -expm1f(-lambda * M.dt);
+        if (p > 0.0f)
+            fired = uniform24(M.key0, M.key1, M.rep, step, orig_id(perm, i)) < p;
+    }
+    TailResult r;
+    if (fired) {
+        r.x = (x == kS) ? (M.model == kSEIR ? kE : kI) : (x + 1);
+        r.age = 0.0f;
+    } else {
+        r.x = x;
+        r.age = (x == kE || x == kI) ? __fadd_rn(age, M.dt) : 0.0f;
+    }
+    r.fired = fired;
+    return r;
+}
+
+// warp-level delta accumulation into the CTA's shared counters
+__device__ __forceinline__ void warp_deltas(unsigned long long* s_delta, bool firedS, bool firedE,
+                                            bool firedI, uint32_t deg_if_firedS)
+{
+    const uint32_t a = __popc(__ballot_sync(kFull, firedS));
+    const uint32_t b = __popc(__ballot_sync(kFull, firedE));
+    const uint32_t c = __popc(__ballot_sync(kFull, firedI));
+    const uint32_t d = __reduce_add_sync(kFull, deg_if_firedS);
+    if ((threadIdx.x & 31) == 0) {
+        if (a) atomicAdd(&s_delta[0], (unsigned long long)a);
+        if (b) atomicAdd(&s_delta[1], (unsigned long long)b);
+        if (c) atomicAdd(&s_delta[2], (unsigned long long)c);
+        if (d) atomicAdd(&s_delta[3], (unsigned long long)d);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// One-thread-per-node class: one warp per 32-node SELL slice.
+// ---------------------------------------------------------------------------
+template <typename AgeT>
+__device__ __forceinline__ void sell_slice(const StepArgs& a, uint32_t step, const uint32_t* __restrict__ bm,
+                                           uint32_t* __restrict__ bmn, int slice, unsigned long long* s_delta)
+{
+    const int lane = threadIdx.x & 31;
+    const int i = slice * 32 + lane;
+    const bool valid = i < a.n_thr;
+    AgeT* __restrict__ A = static_cast<AgeT*>(a.A);
+    const int x = valid ? (int)a.X[i] : kR;
+    float age = 0.0f;
+    if (x == kE || x == kI)
+        age = AgeIO<AgeT>::load(A[i]);
+    uint32_t c = 0, deg = 0;
+    if (x == kS) {
+        const int64_t off = __ldg(a.sell_off + slice);
+        const int w = (int)((__ldg(a.sell_off + slice + 1) - off) >> 5);
+        const int32_t* __restrict__ p = a.sell_col + off + lane;
+        const int sentinel = a.sentinel;
+        for (int t0 = 0; t0 < w; t0 += 8) {
+            int32_t jj[8];
+            uint32_t ww[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                jj[u] = (t0 + u < w) ? __ldg(p + 32 * (t0 + u)) : sentinel;
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                ww[u] = (jj[u] != sentinel) ? __ldg(bm + (jj[u] >> 5)) : 0u;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                c += (ww[u] >> (jj[u] & 31)) & 1u;
+                deg += (jj[u] != sentinel);
+            }
+        }
+    }
+    const TailResult r = tail_at(a.M, x, age, c, a.perm, i, step);
+    if (valid) {
+        if (r.x != x)
+            a.X[i] = (uint8_t)r.x;
+        if (r.fired || x == kE || x == kI)
+            A[i] = AgeIO<AgeT>::store(r.age);
+    }
+    const uint32_t word = __ballot_sync(kFull, valid && r.x == kI);
+    const uint32_t vmask = __ballot_sync(kFull, valid);
+    if (lane == 0) {
+        if (vmask == kFull) {
+            bmn[slice] = word;
+        } else {
+            // the slice shares its word with merge-class nodes: touch own bits only
+            if (word) atomicOr(bmn + slice, word);
+            atomicAnd(bmn + slice, word | ~vmask);
+        }
+    }
+    warp_deltas(s_delta, r.fired && x == kS, r.fired && x == kE, r.fired && x == kI,
+                (r.fired && x == kS) ? deg : 0u);
+}
+
+// ---------------------------------------------------------------------------
+// Merge class: one 4096-edge chunk per CTA.
+// ---------------------------------------------------------------------------
+struct MergeSmem {
+    int32_t col[kMergeEPB];                 // staged column block (TMA destination)
+    int64_t rp[kMergeMaxRows + 1];          // row bounds of the rows touched
+    int32_t xs[kMergeMaxRows];              // their compartments
+    uint32_t cnt[kMergeMaxRows];            // chunk-local infectious counts
+    uint32_t wset[8], wclr[8];              // bitmap bits to set / clear
+    unsigned long long mbar;
+};
+
+template <typename AgeT>
+__device__ __forceinline__ void merge_chunk(const StepArgs& a, uint32_t step, const uint32_t* __restrict__ bm,
+                                            uint32_t* __restrict__ bmn, int chunk, unsigned long long* s_delta)
+{
+    __shared__ __align__(128) MergeSmem sm;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t e0 = (int64_t)chunk * kMergeEPB;
+    const int64_t e1 = min(e0 + (int64_t)kMergeEPB, a.e_m);
+    const int R0 = __ldg(a.m_warp_row + (int64_t)chunk * kStepWarps);
+    const int R1 = __ldg(a.m_chunk_last + chunk);
+    const int nrows = R1 - R0 + 1;           // <= kMergeMaxRows by construction
+    AgeT* __restrict__ A = static_cast<AgeT*>(a.A);
+
+    for (int t = tid; t <= nrows; t += kStepThreads)
+        sm.rp[t] = __ldg(a.m_ptr + R0 + t);
+    if (tid < 8) {
+        sm.wset[tid] = 0u;
+        sm.wclr[tid] = 0u;
+    }
+    int xrow = kR;
+    if (tid < nrows) {
+        xrow = a.X[a.m_base + R0 + tid];
+        sm.xs[tid] = xrow;
+        sm.cnt[tid] = 0u;
+    }
+    const int anyS = __syncthreads_or(xrow == kS);
+
+    if (anyS) {
+        const uint32_t mbar = smem_addr(&sm.mbar);
+        const uint32_t bytes = kMergeEPB * 4u;
+        if (tid == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes)
+                         : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    smem_addr(sm.col)),
+                "l"(a.m_col + e0), "r"(bytes), "r"(mbar)
+                : "memory");
+        }
+        __syncthreads();
+        bool ok = mbar_wait(mbar, 0u, kWaitLimit);
+        if (!ok) {
+            record_error(a.ctl, kErrTmaTimeout);
+            ok = mbar_wait(mbar, 0u, kWaitLimit);   // let an in-flight copy land before leaving
+        }
+        const int64_t s0 = e0 + (int64_t)warp * kMergeEdgesPerWarp;
+        if (ok && s0 < e1) {
+            const int64_t s1 = min(s0 + (int64_t)kMergeEdgesPerWarp, e1);
+            const int rw = __ldg(a.m_warp_row + (int64_t)chunk * kStepWarps + warp);
+            const int r = rw + lane;
+            int64_t lo = 0, hi = 0;
+            bool isS = false;
+            if (r <= R1) {
+                lo = max(sm.rp[r - R0], s0);
+                hi = min(sm.rp[r - R0 + 1], s1);
+                isS = sm.xs[r - R0] == kS;
+            }
+            const int32_t* cb = sm.col + (s0 - e0);
+            uint32_t cnt = 0;
+#pragma unroll
+            for (int m = 0; m < kMergeWindowsPerWarp; ++m) {
+                const int64_t base = s0 + 32 * m;
+                const int l0 = (int)max((int64_t)0, min((int64_t)32, lo - base));
+                const int h0 = (int)max((int64_t)0, min((int64_t)32, hi - base));
+                uint32_t rm = 0u;
+                if (h0 > l0)
+                    rm = ((h0 == 32) ? kFull : ((1u << h0) - 1u)) & ~((1u << l0) - 1u);
+                const uint32_t act = __reduce_or_sync(kFull, isS ? rm : 0u);
+                uint32_t bit = 0u;
+                if ((act >> lane) & 1u) {
+                    const int32_t col = cb[32 * m + lane];
+                    bit = (__ldg(bm + (col >> 5)) >> (col & 31)) & 1u;
+                }
+                cnt += __popc(__ballot_sync(kFull, bit != 0u) & rm);
+            }
+            if (r <= R1 && isS && lo < hi && cnt)
+                atomicAdd(&sm.cnt[r - R0], cnt);
+        }
+    }
+    __syncthreads();
+
+    bool fS = false, fE = false, fI = false;
+    uint32_t dS = 0;
+    if (tid < nrows) {
+        const int r = R0 + tid;
+        const int64_t rlo = sm.rp[tid], rhi = sm.rp[tid + 1];
+        const int x = sm.xs[tid];
+        bool do_tail = false;
+        uint32_t count = 0;
+        if (x == kS) {
+            if (rlo >= e0 && rhi <= e1) {
+                do_tail = true;
+                count = sm.cnt[tid];
+            } else {
+                const uint32_t nch = (uint32_t)((rhi - 1) / kMergeEPB - rlo / kMergeEPB + 1);
+                const uint32_t part = sm.cnt[tid];
+                if (part)
+                    atomicAdd(reinterpret_cast<unsigned int*>(a.m_cnt + r), part);
+                __threadfence();
+                const uint32_t tk = atomicAdd(a.m_tkt + r, 1u);
+                if (tk == nch - 1u) {
+                    __threadfence();
+                    count = atomicExch(reinterpret_cast<unsigned int*>(a.m_cnt + r), 0u);
+                    atomicExch(a.m_tkt + r, 0u);
+                    do_tail = true;
+                }
+            }
+        } else {
+            do_tail = rlo >= e0;   // the chunk that holds the row's first edge
+        }
+        if (do_tail) {
+            const int gi = a.m_base + r;
+            float age = 0.0f;
+            if (x == kE || x == kI)
+                age = AgeIO<AgeT>::load(A[gi]);
+            const TailResult t = tail_at(a.M, x, age, count, a.perm, gi, step);
+            if (t.x != x)
+                a.X[gi] = (uint8_t)t.x;
+            if (t.fired || x == kE || x == kI)
+                A[gi] = AgeIO<AgeT>::store(t.age);
+            const int wofs = (gi >> 5) - ((a.m_base + R0) >> 5);
+            const uint32_t bit = 1u << (gi & 31);
+            if (t.x == kI)
+                atomicOr(&sm.wset[wofs], bit);
+            else
+                atomicOr(&sm.wclr[wofs], bit);
+            fS = t.fired && x == kS;
+            fE = t.fired && x == kE;
+            fI = t.fired && x == kI;
+            dS = fS ? (uint32_t)(rhi - rlo) : 0u;
+        }
+    }
+    warp_deltas(s_delta, fS, fE, fI, dS);
+    __syncthreads();
+    if (tid < 8) {
+        const int w = ((a.m_base + R0) >> 5) + tid;
+        if (sm.wset[tid])
+            atomicOr(bmn + w, sm.wset[tid]);
+        if (sm.wclr[tid])
+            atomicAnd(bmn + w, ~sm.wclr[tid]);
+    }
+}
+
+template <typename AgeT, bool HAS_MERGE>
+__global__ void __launch_bounds__(kStepThreads) fused_step_kernel(const __grid_constant__ StepArgs a)
+{
+    __shared__ unsigned long long s_delta[kDeltaFields];
+    if (threadIdx.x < kDeltaFields)
+        s_delta[threadIdx.x] = 0ull;
+    const int64_t k = a.ctl->step + a.j;
+    const uint32_t par = (uint32_t)(k & 1);
+    const uint32_t* __restrict__ bm = a.bm[par];
+    uint32_t* __restrict__ bmn = a.bm[par ^ 1u];
+    __syncthreads();
+    if constexpr (HAS_MERGE) {
+        if ((int)blockIdx.x < a.n_chunks) {
+            merge_chunk<AgeT>(a, (uint32_t)k, bm, bmn, (int)blockIdx.x, s_delta);
+        } else {
+            const int slice = ((int)blockIdx.x - a.n_chunks) * kSellSlicesPerCta + (int)(threadIdx.x >> 5);
+            if (slice < a.n_slices)
+                sell_slice<AgeT>(a, (uint32_t)k, bm, bmn, slice, s_delta);
+        }
+    } else {
+        const int slice = (int)blockIdx.x * kSellSlicesPerCta + (int)(threadIdx.x >> 5);
+        if (slice < a.n_slices)
+            sell_slice<AgeT>(a, (uint32_t)k, bm, bmn, slice, s_delta);
+    }
+    __syncthreads();
+    if (threadIdx.x < kDeltaFields) {
+        const unsigned long long v = s_delta[threadIdx.x];
+        if (v)
+            atomicAdd(a.deltas + (int64_t)a.j * kDeltaFields + threadIdx.x, v);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Run bookkeeping: begin (row 0 of the counts output) and the epilogue that
+// integrates K steps of deltas into counts (one launch per K steps).
+// ---------------------------------------------------------------------------
+__global__ void run_begin_kernel(DevCtl* ctl, uint32_t* out)
+{
+    if (threadIdx.x == 0) {
+        ctl->out = out;
+        ctl->row = 0;
+        if (out) {
+            for (int t = 0; t < 4; ++t)
+                out[t] = ctl->counts[t];
+            ctl->row = 1;
+        }
+    }
+}
+
+__global__ void run_epilogue_kernel(DevCtl* ctl, unsigned long long* deltas, int K, int model)
+{
+    __shared__ unsigned long long d[kMaxGraphSteps][kDeltaFields];
+    for (int t = threadIdx.x; t < K * kDeltaFields; t += blockDim.x) {
+        d[t / kDeltaFields][t % kDeltaFields] = deltas[t];
+        deltas[t] = 0ull;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t c0 = ctl->counts[0], c1 = ctl->counts[1], c2 = ctl->counts[2], c3 = ctl->counts[3];
+        unsigned long long ds = ctl->ds_cur, dst = ctl->ds_total, st = ctl->s_total;
+        uint32_t* out = ctl->out;
+        const int64_t row = ctl->row;
+        for (int j = 0; j < K; ++j) {
+            st += c0;
+            dst += ds;
+            const uint32_t l = (uint32_t)d[j][0], ei = (uint32_t)d[j][1], ir = (uint32_t)d[j][2];
+            c0 -= l;
+            if (model == kSEIR) {
+                c1 += l - ei;
+                c2 += ei - ir;
+            } else {
+                c2 += l - ir;
+            }
+            c3 += ir;
+            ds -= d[j][3];
+            if (out) {
+                uint32_t* o = out + (row + j) * 4;
+                o[0] = c0; o[1] = c1; o[2] = c2; o[3] = c3;
+            }
+        }
+        ctl->counts[0] = c0; ctl->counts[1] = c1; ctl->counts[2] = c2; ctl->counts[3] = c3;
+        ctl->ds_cur = ds;
+        ctl->ds_total = dst;
+        ctl->s_total = st;
+        ctl->step += K;
+        if (out)
+            ctl->row = row + K;
+    }
+}
+
+// Rebuild the infectious bitmap of the current step parity, the counts and
+// the S-degree sum from the state (after init or set_state).
+__global__ void refresh_kernel(const uint8_t* __restrict__ X, int n, const int32_t* __restrict__ deg,
+                               uint32_t* bm0, uint32_t* bm1, DevCtl* ctl)
+{
+    const int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    const int i = w * 32 + lane;
+    const int x = (i < n) ? (int)X[i] : -1;
+    const uint32_t word = __ballot_sync(kFull, x == kI);
+    const unsigned long long dS = (x == kS) ? (unsigned long long)deg[i] : 0ull;
+    uint32_t cs[4];
+    for (int c = 0; c < 4; ++c)
+        cs[c] = __popc(__ballot_sync(kFull, x == c));
+    unsigned long long dsum = dS;
+    for (int o = 16; o > 0; o >>= 1)
+        dsum += __shfl_xor_sync(kFull, dsum, o);
+    if (lane == 0 && w * 32 < n) {
+        const uint32_t par = (uint32_t)(ctl->step & 1);
+        (par ? bm1 : bm0)[w] = word;
+        for (int c = 0; c < 4; ++c)
+            if (cs[c])
+                atomicAdd(&ctl->counts[c], cs[c]);
+        if (dsum)
+            atomicAdd(&ctl->ds_cur, dsum);
+    }
+}
+
+__global__ void set_index_kernel(uint8_t* X, const int32_t* idx, int64_t n_idx, const int32_t* inv, int state)
+{
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q < n_idx) {
+        const int o = idx[q];
+        X[inv ? inv[o] : o] = (uint8_t)state;
+    }
+}
+
+// out[perm[i]] = in[i] (internal -> original order), elements of `bytes`
+template <typename T>
+__global__ void to_original_kernel(const T* __restrict__ in, T* __restrict__ out, const int32_t* perm, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n)
+        out[perm[i]] = in[i];
+}
+
+template <typename T>
+__global__ void from_original_kernel(const T* __restrict__ in, T* __restrict__ out, const int32_t* inv, int n)
+{
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o < n)
+        out[inv[o]] = in[o];
+}
+
+__global__ void eval_hazard_kernel(LawF L, const float* tau, float* h, int64_t n)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n)
+        h[i] = hazard(L, tau[i]);
+}
+
+__global__ void eval_uniform_kernel(uint32_t key0, uint32_t key1, uint32_t rep, uint32_t step,
+                                    const int32_t* nodes, float* u, int64_t n)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n)
+        u[i] = uniform24(key0, key1, rep, step, (uint32_t)nodes[i]);
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+template <typename AgeT>
+static cudaError_t launch_step_t(const StepArgs& a, cudaStream_t s)
+{
+    const int grid = a.n_chunks + a.n_sell_ctas;
+    if (grid == 0)
+        return cudaSuccess;
+    if (a.n_chunks > 0)
+        fused_step_kernel<AgeT, true><<<grid, kStepThreads, 0, s>>>(a);
+    else
+        fused_step_kernel<AgeT, false><<<grid, kStepThreads, 0, s>>>(a);
+    g_launch_count += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step(const StepArgs& a, int age_dtype, cudaStream_t s)
+{
+    switch (age_dtype) {
+    case kAgeF16: return launch_step_t<__half>(a, s);
+    case kAgeBF16: return launch_step_t<__nv_bfloat16>(a, s);
+    default: return launch_step_t<float>(a, s);
+    }
+}
+
+cudaError_t launch_run_begin(DevCtl* ctl, uint32_t* out, cudaStream_t s)
+{
+    run_begin_kernel<<<1, 32, 0, s>>>(ctl, out);
+    g_launch_count += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_run_epilogue(DevCtl* ctl, unsigned long long* deltas, int K, int model, cudaStream_t s)
+{
+    run_epilogue_kernel<<<1, 256, 0, s>>>(ctl, deltas, K, model);
+    g_launch_count += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refresh(const uint8_t* X, int n, const int32_t* deg, uint32_t* bm0, uint32_t* bm1, DevCtl* ctl,
+                           cudaStream_t s)
+{
+    const int words = (n + 31) / 32;
+    const int threads = 256;
+    const int blocks = (int)(((int64_t)words * 32 + threads - 1) / threads);
+    refresh_kernel<<<blocks, threads, 0, s>>>(X, n, deg, bm0, bm1, ctl);
+    g_launch_count += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_index(uint8_t* X, const int32_t* idx, int64_t n_idx, const int32_t* inv, int state,
+                             cudaStream_t s)
+{
+    if (n_idx == 0)
+        return cudaSuccess;
+    set_index_kernel<<<(unsigned)((n_idx + 255) / 256), 256, 0, s>>>(X, idx, n_idx, inv, state);
+    g_launch_count += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_original(const void* in, void* out, int elem_bytes, const int32_t* perm, int n, cudaStream_t s)
+{
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    if (elem_bytes == 1)
+        to_original_kernel<uint8_t><<<blocks, 256, 0, s>>>((const uint8_t*)in, (uint8_t*)out, perm, n);
+    else if (elem_bytes == 2)
+        to_original_kernel<uint16_t><<<blocks, 256, 0, s>>>((const uint16_t*)in, (uint16_t*)out, perm, n);
+    else
+        to_original_kernel<uint32_t><<<blocks, 256, 0, s>>>((const uint32_t*)in, (uint32_t*)out, perm, n);
+    g_launch_count += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_from_original(const void* in, void* out, int elem_bytes, const int32_t* inv, int n,
+                                 cudaStream_t s)
+{
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    if (elem_bytes == 1)
+        from_original_kernel<uint8_t><<<blocks, 256, 0, s>>>((const uint8_t*)in, (uint8_t*)out, inv, n);
+    else if (elem_bytes == 2)
+        from_original_kernel<uint16_t><<<blocks, 256, 0, s>>>((const uint16_t*)in, (uint16_t*)out, inv, n);
+    else
+        from_original_kernel<uint32_t><<<blocks, 256, 0, s>>>((const uint32_t*)in, (uint32_t*)out, inv, n);
+    g_launch_count += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eval_hazard(const LawF& L, const float* tau, float* h, int64_t n, cudaStream_t s)
+{
+    if (n == 0)
+        return cudaSuccess;
+    eval_hazard_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L, tau, h, n);
+    g_launch_count += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eval_uniforms(uint32_t key0, uint32_t key1, uint32_t rep, uint32_t step, const int32_t* nodes,
+                                 float* u, int64_t n, cudaStream_t s)
+{
+    if (n == 0)
+        return cudaSuccess;
+    eval_uniform_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(key0, key1, rep, step, nodes, u, n);
+    g_launch_count += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace fs
