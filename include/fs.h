@@ -222,6 +222,48 @@ fs_status fs_eval_hazard(const fs_law* law, const float* tau_dev, float* h_dev, 
 fs_status fs_eval_uniforms(uint64_t seed, uint32_t replicate, int64_t step, const int32_t* nodes_dev,
                            float* u_dev, int64_t n, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * fs_step_noalloc -- one fused step that allocates no device memory. The
+ * paper has no counterpart: this entry point exists for callers that cannot
+ * call cudaMalloc while they step -- code running inside CUDA stream capture
+ * (where cudaMalloc is not allowed), and applications whose device memory is
+ * owned by their own pool or arena and must not be grown behind its back. The
+ * graph is created beforehand with fs_graph_create (which does allocate); the
+ * caller owns and passes every other buffer.
+ *
+ * The step's only scratch -- the merge class's cross-chunk partial counts and
+ * tickets, and a 256-byte control block -- lives in one fixed array inside
+ * the library, sized for at most 65,536 merge-class rows (512 KiB + 256 B,
+ * held on every GPU that loads the library until the process exits). A graph
+ * with more merge-class rows is rejected with FS_EINVAL.
+ *   g               graph from fs_graph_create. The buffers below are in the
+ *                   graph's internal node order, which is the caller's order
+ *                   when fs_graph_info_get reports identity_layout = 1.
+ *   params          the realisation, as for fs_sim_init (index_state unused)
+ *   step            step index k (keys the uniforms), 0 <= k < 2^32
+ *   state_dev       device uint8[n], read and updated in place
+ *   age_dev         device ages[n] of params->age_dtype, updated in place
+ *   bitmap_cur_dev  device uint32[n/32 + 1]: bit i = (state[i] == FS_I) at
+ *                   the start of the step, other bits 0
+ *   bitmap_next_dev device uint32[n/32 + 1], receives that bitmap after the
+ *                   step (must not alias bitmap_cur_dev)
+ *   deltas_dev      device uint64[5], receives [nodes that left S, E -> I,
+ *                   I -> R, sum of degrees of the nodes that left S, device
+ *                   error word (0 = ok)]
+ *   stream          cudaStream_t (NULL = the legacy default stream); the call
+ *                   only enqueues work and returns
+ * Set-up: the first call on each device looks up the device address of the
+ * scratch array (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture. Every call shares the one array and
+ * clears what must start at zero; calls that overlap on the GPU (other
+ * streams, other threads) race on it and must be serialised by the caller.
+ * Errors: FS_EINVAL (NULL pointers, bad params or step, too many merge-class
+ * rows), FS_ESTATE, FS_ECUDA.
+ * ------------------------------------------------------------------------- */
+fs_status fs_step_noalloc(const fs_graph* g, const fs_sim_params* params, int64_t step,
+                          uint8_t* state_dev, void* age_dev, const uint32_t* bitmap_cur_dev,
+                          uint32_t* bitmap_next_dev, uint64_t* deltas_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

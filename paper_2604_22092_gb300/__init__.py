@@ -25,7 +25,7 @@ __all__ = [
     "fs_sim_init", "fs_sim_step", "fs_sim_run", "fs_sim_run_async", "fs_sim_sync", "fs_sim_run_timed",
     "fs_kernel_launches",
     "fs_sim_get_state", "fs_sim_set_state", "fs_sim_work", "fs_sim_destroy", "fs_eval_hazard",
-    "fs_eval_uniforms", "law", "sim_params", "graph_opts", "FsError", "load",
+    "fs_eval_uniforms", "fs_step_noalloc", "law", "sim_params", "graph_opts", "FsError", "load",
     "FS_S", "FS_E", "FS_I", "FS_R", "FS_SIR", "FS_SEIR", "FS_AGE_F32", "FS_AGE_F16", "FS_AGE_BF16",
     "FS_DISPATCH_AUTO", "FS_DISPATCH_THREAD", "FS_DISPATCH_MERGE",
 ]
@@ -209,3 +209,13 @@ def fs_eval_uniforms(seed: int, replicate: int, step: int, nodes_dev, u_dev, str
     n = nodes_dev.numel()
     check(load().fs_eval_uniforms(int(seed), int(replicate), int(step), _addr(nodes_dev), _addr(u_dev), n,
                                   _stream(stream)), "fs_eval_uniforms")
+
+
+def fs_step_noalloc(g: int, params: _abi.fs_sim_params, step: int, state_dev, age_dev, bitmap_cur_dev,
+                    bitmap_next_dev, deltas_dev, stream=None) -> None:
+    """One step on caller-owned device buffers that allocates no device
+    memory (for callers that may not call cudaMalloc, e.g. under stream
+    capture or inside their own memory pool). Enqueues only; see fs.h."""
+    check(load().fs_step_noalloc(g, ctypes.byref(params), int(step), _addr(state_dev), _addr(age_dev),
+                                 _addr(bitmap_cur_dev), _addr(bitmap_next_dev), _addr(deltas_dev),
+                                 _stream(stream)), "fs_step_noalloc")

@@ -73,6 +73,7 @@ PROTOTYPES = {
     "fs_eval_hazard": (ctypes.c_int, [P(fs_law), VP, VP, ctypes.c_int64, VP]),
     "fs_eval_uniforms": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64, VP, VP,
                                         ctypes.c_int64, VP]),
+    "fs_step_noalloc": (ctypes.c_int, [VP, P(fs_sim_params), ctypes.c_int64, VP, VP, VP, VP, VP, VP]),
 }
 
 _lib = None

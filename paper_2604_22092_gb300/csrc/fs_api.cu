@@ -10,6 +10,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -902,3 +903,148 @@ fs_status fs_eval_uniforms(uint64_t seed, uint32_t replicate, int64_t step, cons
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// fs_step_noalloc: one fused step that allocates nothing. Its scratch (the
+// merge class's cross-chunk partial counts and tickets, and the control block
+// the step kernel reads its step index from and writes its error word to)
+// lives in one file-scope device array, looked up once per device.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNoAllocMaxMergeRows = 65536;
+constexpr size_t kNoAllocCtlBytes = 256;
+constexpr size_t kNoAllocBytes = kNoAllocCtlBytes + (size_t)kNoAllocMaxMergeRows * 8;
+static_assert(sizeof(fs::DevCtl) <= kNoAllocCtlBytes, "control block does not fit");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// device address of g_noalloc_scratch on the current device (set-up on the
+// first call per device; host code may not use the symbol's host stand-in)
+fs_status noalloc_scratch_addr(unsigned char** out)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return fail(FS_ECUDA, "fs_step_noalloc: cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kNoAllocMaxDevices)
+        return fail(FS_EUNSUPPORTED, "fs_step_noalloc: device ordinal %d beyond %d", dev, kNoAllocMaxDevices);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(FS_ECUDA, "fs_step_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        g_noalloc_addr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+    return FS_OK;
+}
+
+// clears the scratch rows in use, sets the step index, clears the caller's
+// delta outputs (everything the step expects to start at zero)
+__global__ void noalloc_prepare_kernel(fs::DevCtl* ctl, int32_t* cnt, uint32_t* tkt, int n_m, int64_t step,
+                                       unsigned long long* deltas)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (int64_t i = t; i < n_m; i += (int64_t)gridDim.x * blockDim.x) {
+        cnt[i] = 0;
+        tkt[i] = 0u;
+    }
+    if (t == 0) {
+        ctl->step = step;
+        ctl->error = 0;
+    }
+    if (t < 5)
+        deltas[t] = 0ull;
+}
+
+__global__ void noalloc_finish_kernel(const fs::DevCtl* ctl, unsigned long long* deltas)
+{
+    if (threadIdx.x == 0)
+        deltas[4] = (unsigned long long)(unsigned)ctl->error;
+}
+
+}  // namespace
+
+extern "C" fs_status fs_step_noalloc(const fs_graph* g, const fs_sim_params* params, int64_t step,
+                                     uint8_t* state_dev, void* age_dev, const uint32_t* bitmap_cur_dev,
+                                     uint32_t* bitmap_next_dev, uint64_t* deltas_dev, void* stream)
+{
+    g_err.clear();
+    if (!g || !state_dev || !age_dev || !bitmap_cur_dev || !bitmap_next_dev || !deltas_dev)
+        return fail(FS_EINVAL, "fs_step_noalloc: NULL argument");
+    if (g->failed)
+        return fail(FS_ESTATE, "fs_step_noalloc: graph is in a failed state");
+    if (!params)
+        return fail(FS_EINVAL, "fs_step_noalloc: params is NULL");
+    fs_sim_params pv = *params;                     // index_state does not apply to one step
+    pv.index_state = pv.model == FS_SEIR ? FS_E : FS_I;
+    fs_status st = check_params(&pv);
+    if (st != FS_OK)
+        return st;
+    if (step < 0 || step >= ((int64_t)1 << 32))
+        return fail(FS_EINVAL, "fs_step_noalloc: step must be in [0, 2^32)");
+    if (g->n_m > kNoAllocMaxMergeRows)
+        return fail(FS_EINVAL,
+                    "fs_step_noalloc: the graph has %d merge-class rows; the allocation-free step supports at "
+                    "most %d (raise thread_max_deg when creating the graph, or use fs_sim_*)",
+                    g->n_m, kNoAllocMaxMergeRows);
+    unsigned char* base = nullptr;
+    st = noalloc_scratch_addr(&base);
+    if (st != FS_OK)
+        return st;
+    fs::DevCtl* ctl = reinterpret_cast<fs::DevCtl*>(base);
+    int32_t* cnt = reinterpret_cast<int32_t*>(base + kNoAllocCtlBytes);
+    uint32_t* tkt = reinterpret_cast<uint32_t*>(base + kNoAllocCtlBytes + (size_t)kNoAllocMaxMergeRows * 4);
+    cudaStream_t cs = (cudaStream_t)stream;
+    unsigned long long* deltas = reinterpret_cast<unsigned long long*>(deltas_dev);
+
+    const int prep_blocks = std::max(1, std::min(64, (g->n_m + 255) / 256));
+    noalloc_prepare_kernel<<<prep_blocks, 256, 0, cs>>>(ctl, cnt, tkt, g->n_m, step, deltas);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return fail(FS_ECUDA, "fs_step_noalloc: prepare: %s", cudaGetErrorString(e));
+    fs::g_launch_count += 1;
+
+    fs::StepArgs a{};
+    a.X = state_dev;
+    a.A = age_dev;
+    a.bm[step & 1] = const_cast<uint32_t*>(bitmap_cur_dev);
+    a.bm[(step + 1) & 1] = bitmap_next_dev;
+    a.sell_off = g->d_sell_off;
+    a.sell_col = g->d_sell_col;
+    a.n_thr = g->n_thr;
+    a.n_slices = g->n_slices;
+    a.sentinel = (int32_t)g->n;
+    a.m_base = g->n_thr;
+    a.n_m = g->n_m;
+    a.n_chunks = g->n_chunks;
+    a.n_sell_ctas = (g->n_slices + fs::kSellSlicesPerCta - 1) / fs::kSellSlicesPerCta;
+    a.m_ptr = g->d_m_ptr;
+    a.m_col = g->d_m_col;
+    a.m_warp_row = g->d_m_warp_row;
+    a.m_chunk_last = g->d_m_chunk_last;
+    a.e_m = g->e_m;
+    a.m_cnt = cnt;
+    a.m_tkt = tkt;
+    a.perm = g->d_perm;
+    a.M = to_model(pv);
+    a.ctl = ctl;
+    a.deltas = deltas;
+    a.j = 0;
+    a.n = (int32_t)g->n;
+    e = fs::launch_step(a, pv.age_dtype, cs);
+    if (e != cudaSuccess)
+        return fail(FS_ECUDA, "fs_step_noalloc: step: %s", cudaGetErrorString(e));
+    noalloc_finish_kernel<<<1, 32, 0, cs>>>(ctl, deltas);
+    e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return fail(FS_ECUDA, "fs_step_noalloc: finish: %s", cudaGetErrorString(e));
+    fs::g_launch_count += 1;
+    return FS_OK;
+}
