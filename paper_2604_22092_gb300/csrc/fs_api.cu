@@ -62,6 +62,11 @@ struct fs_graph {
     int32_t* d_m_warp_row = nullptr;
     int32_t* d_m_chunk_last = nullptr;
     int64_t bytes = 0;
+    int32_t num_sms = 152;
+    int32_t spw = 1;               // SELL slices per warp (one wave of step CTAs)
+    uint32_t bm_bytes = 0;         // infectious bitmap bytes, rounded up to 16
+    bool smem_path = false;        // bitmap small enough to be staged in shared memory
+    uint32_t smem_min_s = 0;       // S count from which staging pays off
     int refs = 0;
     bool failed = false;
 };
@@ -78,6 +83,8 @@ struct fs_sim {
     uint32_t* d_m_tkt = nullptr;
     fs::DevCtl* d_ctl = nullptr;
     unsigned long long* d_deltas = nullptr;
+    float2* d_ptab = nullptr;
+    float* d_ps = nullptr;
     uint32_t* d_counts = nullptr;
     int64_t counts_cap = 0;
     cudaGraphExec_t gexec = nullptr;
@@ -129,6 +136,8 @@ void free_sim(fs_sim* s)
     cudaFree(s->d_m_tkt);
     cudaFree(s->d_ctl);
     cudaFree(s->d_deltas);
+    cudaFree(s->d_ptab);
+    cudaFree(s->d_ps);
     cudaFree(s->d_counts);
     if (s->own_stream && s->stream)
         cudaStreamDestroy(s->stream);
@@ -232,6 +241,7 @@ fs::ModelF to_model(const fs_sim_params& p)
     M.model = p.model;
     M.beta = (float)p.beta;
     M.dt = (float)p.dt;
+    M.inv_dt = (float)(1.0 / p.dt);
     M.key0 = (uint32_t)(p.seed & 0xffffffffu);
     M.key1 = (uint32_t)(p.seed >> 32);
     M.rep = p.replicate;
@@ -256,7 +266,6 @@ fs::StepArgs step_args(const fs_sim* s, int j)
     a.m_base = g->n_thr;
     a.n_m = g->n_m;
     a.n_chunks = g->n_chunks;
-    a.n_sell_ctas = (g->n_slices + fs::kSellSlicesPerCta - 1) / fs::kSellSlicesPerCta;
     a.m_ptr = g->d_m_ptr;
     a.m_col = g->d_m_col;
     a.m_warp_row = g->d_m_warp_row;
@@ -265,6 +274,13 @@ fs::StepArgs step_args(const fs_sim* s, int j)
     a.m_cnt = s->d_m_cnt;
     a.m_tkt = s->d_m_tkt;
     a.perm = g->d_perm;
+    a.deg = g->d_deg;
+    a.ptab = s->d_ptab;
+    a.ps = s->d_ps;
+    a.spw = g->spw;
+    a.n_sell_ctas = (g->n_slices + fs::kSellSlicesPerCta * g->spw - 1) / (fs::kSellSlicesPerCta * g->spw);
+    a.bm_bytes = g->bm_bytes;
+    a.smem_min_s = g->smem_min_s;
     a.M = s->M;
     a.ctl = s->d_ctl;
     a.deltas = s->d_deltas;
@@ -430,8 +446,24 @@ fs_status fs_graph_create(int64_t n, const int64_t* row_ptr, const int32_t* col_
             cudaFree(g->d_deg);
             g->d_deg = deg_int;
         }
-        // SELL-32 blocks of the thread class
+        // SELL-32 blocks of the thread class; slices per warp so that the
+        // step grid is about one wave of resident CTAs
         g->n_slices = (g->n_thr + 31) / 32;
+        {
+            int dev = 0, sms = 0;
+            if (cudaGetDevice(&dev) == cudaSuccess &&
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+                g->num_sms = sms;
+            const int64_t wave_warps = (int64_t)g->num_sms * fs::kStepCtasPerSm * fs::kStepWarps;
+            g->spw = (int32_t)std::max<int64_t>(1, (g->n_slices + wave_warps - 1) / wave_warps);
+            // shared-memory bitmap path: the whole bitmap fits one CTA's shared
+            // memory; it pays off once the S nodes' gathers outweigh one copy of
+            // the bitmap per SM (about 4 gathers per node, measured)
+            g->bm_bytes = (uint32_t)((((n >> 5) + 1) * 4 + 15) / 16 * 16);
+            g->smem_path = g->n_slices > 0 && g->bm_bytes <= fs::kSmemBitmapMaxBytes;
+            const double d_avg = n ? (double)nnz / (double)n : 0.0;
+            g->smem_min_s = (uint32_t)std::min<double>((double)n, 4.0 * (double)n / std::max(d_avg, 1.0));
+        }
         G_CUDA(dev_alloc(&g->d_sell_off, (size_t)g->n_slices + 1, &g->bytes));
         G_CUDA(dev_alloc(&d_tmp, (size_t)std::max(g->n_slices, g->n_m) + 1, nullptr));
         G_CUDA(fs::launch_sell_widths(g->d_deg, g->n_thr, g->n_slices, d_tmp, st));
@@ -558,7 +590,7 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
         s->own_stream = true;
     }
     cudaStream_t cs = s->stream;
-    const size_t words = (size_t)(n >> 5) + 1;
+    const size_t words = ((size_t)(n >> 5) + 1 + 3) / 4 * 4;
     S_CUDA(dev_alloc(&s->d_X, (size_t)n, nullptr));
     S_CUDA(cudaMalloc(&s->d_A, (size_t)n * s->age_bytes));
     S_CUDA(dev_alloc(&s->d_bm[0], words, nullptr));
@@ -567,6 +599,10 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
     S_CUDA(dev_alloc(&s->d_m_tkt, (size_t)std::max(g->n_m, 1), nullptr));
     S_CUDA(dev_alloc(&s->d_ctl, 1, nullptr));
     S_CUDA(dev_alloc(&s->d_deltas, (size_t)fs::kMaxGraphSteps * fs::kDeltaFields, nullptr));
+    S_CUDA(dev_alloc(&s->d_ptab, (size_t)2 * fs::kPTableN, nullptr));
+    S_CUDA(dev_alloc(&s->d_ps, (size_t)fs::kPSTableN, nullptr));
+    S_CUDA(cudaMemsetAsync(s->d_ptab, 0xff, sizeof(float2) * 2 * fs::kPTableN, cs));   // NaN ages: no entry
+    S_CUDA(fs::launch_build_ptables(s->M, params->age_dtype, s->d_ptab, s->d_ps, cs));
     S_CUDA(cudaMemsetAsync(s->d_X, 0, (size_t)n, cs));
     S_CUDA(cudaMemsetAsync(s->d_A, 0, (size_t)n * s->age_bytes, cs));
     S_CUDA(cudaMemsetAsync(s->d_bm[0], 0, words * 4, cs));
@@ -589,6 +625,16 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
     return FS_OK;
 }
 
+// one fused step: the shared-memory-bitmap grids when the bitmap fits, else
+// the single mixed grid
+static cudaError_t launch_one_step(fs_sim* s, int j)
+{
+    const fs::StepArgs a = step_args(s, j);
+    if (s->g->smem_path)
+        return fs::launch_step_smem(a, s->p.age_dtype, s->stream, s->g->num_sms);
+    return fs::launch_step(a, s->p.age_dtype, s->stream, false);
+}
+
 static fs_status ensure_graph(fs_sim* s, int K)
 {
     if (s->gexec && s->gK == K)
@@ -601,7 +647,7 @@ static fs_status ensure_graph(fs_sim* s, int K)
     FS_CUDA(s, cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     for (int j = 0; j < K && e == cudaSuccess; ++j)
-        e = fs::launch_step(step_args(s, j), s->p.age_dtype, s->stream);
+        e = launch_one_step(s, j);
     if (e == cudaSuccess)
         e = fs::launch_run_epilogue(s->d_ctl, s->d_deltas, K, s->p.model, s->stream);
     cudaError_t e2 = cudaStreamEndCapture(s->stream, &graph);
@@ -644,7 +690,7 @@ static fs_status run_enqueue(fs_sim* s, int64_t steps, int32_t graph_steps, uint
         FS_CUDA(s, cudaEventRecord(replay_ev[full], s->stream));
     if (rem > 0) {
         for (int j = 0; j < rem; ++j)
-            FS_CUDA(s, fs::launch_step(step_args(s, j), s->p.age_dtype, s->stream));
+            FS_CUDA(s, launch_one_step(s, j));
         FS_CUDA(s, fs::launch_run_epilogue(s->d_ctl, s->d_deltas, rem, s->p.model, s->stream));
     }
     if (replay_ev)
@@ -1024,7 +1070,8 @@ extern "C" fs_status fs_step_noalloc(const fs_graph* g, const fs_sim_params* par
     a.m_base = g->n_thr;
     a.n_m = g->n_m;
     a.n_chunks = g->n_chunks;
-    a.n_sell_ctas = (g->n_slices + fs::kSellSlicesPerCta - 1) / fs::kSellSlicesPerCta;
+    a.spw = g->spw;
+    a.n_sell_ctas = (g->n_slices + fs::kSellSlicesPerCta * g->spw - 1) / (fs::kSellSlicesPerCta * g->spw);
     a.m_ptr = g->d_m_ptr;
     a.m_col = g->d_m_col;
     a.m_warp_row = g->d_m_warp_row;
@@ -1033,12 +1080,13 @@ extern "C" fs_status fs_step_noalloc(const fs_graph* g, const fs_sim_params* par
     a.m_cnt = cnt;
     a.m_tkt = tkt;
     a.perm = g->d_perm;
+    a.deg = g->d_deg;
     a.M = to_model(pv);
     a.ctl = ctl;
     a.deltas = deltas;
     a.j = 0;
     a.n = (int32_t)g->n;
-    e = fs::launch_step(a, pv.age_dtype, cs);
+    e = fs::launch_step(a, pv.age_dtype, cs, false);
     if (e != cudaSuccess)
         return fail(FS_ECUDA, "fs_step_noalloc: step: %s", cudaGetErrorString(e));
     noalloc_finish_kernel<<<1, 32, 0, cs>>>(ctl, deltas);

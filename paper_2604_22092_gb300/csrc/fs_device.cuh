@@ -109,25 +109,25 @@ __device__ __forceinline__ float hazard(const LawF& L, float tau)
         return hazard_lognormal(L, tau);
     case kLawWeibull:
         // h = (k/s) (tau/s)^(k-1); powf(0, 0) = 1 gives h(0) = 1/s for k = 1
-        return L.p0 * powf(tau * L.p1, L.p2);
+        return __fmul_rn(L.p0, powf(__fmul_rn(tau, L.p1), L.p2));
     case kLawErlang: {
         // h = r (r tau)^(k-1)/(k-1)! / sum_{n<k} (r tau)^n / n!
         const float r = L.p0;
-        const float x = r * tau;
+        const float x = __fmul_rn(r, tau);
         if (x <= 1.0f) {
             float t = 1.0f, s = 1.0f;
             for (int n = 1; n < L.k; ++n) {
-                t *= x / (float)n;
-                s += t;
+                t = __fmul_rn(t, __fdiv_rn(x, (float)n));
+                s = __fadd_rn(s, t);
             }
-            return r * t / s;
+            return __fdiv_rn(__fmul_rn(r, t), s);
         }
         // same ratio divided through by x^(k-1)/(k-1)!: r / sum_j (k-1)!/(k-1-j)! x^-j
-        const float y = 1.0f / x;
+        const float y = __fdiv_rn(1.0f, x);
         float s = 1.0f;
         for (int m = 1; m < L.k; ++m)
-            s = 1.0f + (float)m * y * s;
-        return r / s;
+            s = __fadd_rn(1.0f, __fmul_rn(__fmul_rn((float)m, y), s));
+        return __fdiv_rn(r, s);
     }
     default:
         return 0.0f;
@@ -150,6 +150,23 @@ template <> struct AgeIO<__nv_bfloat16> {
     static __device__ __forceinline__ float load(__nv_bfloat16 v) { return __bfloat162float(v); }
     static __device__ __forceinline__ __nv_bfloat16 store(float v) { return __float2bfloat16_rn(v); }
 };
+
+// Bernoulli probability of a rate over the step: p = 1 - exp(-lambda dt)
+__device__ __forceinline__ float p_of_rate(const ModelF& M, float lambda)
+{
+    return lambda > 0.0f ? -expm1f(-__fmul_rn(lambda, M.dt)) : 0.0f;
+}
+
+// the age after one more step in storage: one FP32 add, round to storage
+__device__ __forceinline__ float age_step_stored(float age, float dt, int age_dtype)
+{
+    const float v = __fadd_rn(age, dt);
+    if (age_dtype == kAgeF16)
+        return __half2float(__float2half_rn(v));
+    if (age_dtype == kAgeBF16)
+        return __bfloat162float(__float2bfloat16_rn(v));
+    return v;
+}
 
 struct TailResult {
     int x;        // new compartment

@@ -27,6 +27,7 @@ struct ModelF {
     int32_t model;
     float beta;
     float dt;
+    float inv_dt;                 // (float)(1/dt): age -> table index
     uint32_t key0, key1, rep;
     LawF lat, inf;
 };
@@ -43,6 +44,11 @@ constexpr int kMergeMaxRows = kMergeEPB / kMinMergeDegree + 2;     // rows one c
 constexpr int kMaxThreadDeg = 255;                // bucket cap of the degree sort
 constexpr uint32_t kWaitLimit = 1u << 20;         // bounded mbarrier waits
 constexpr int kMaxGraphSteps = 256;              // steps per captured graph / epilogue
+constexpr int kPTableN = 4096;                    // age-indexed p entries per law
+constexpr int kPSTableN = 256;                    // p of an S node by infectious count
+constexpr int kStepCtasPerSm = 5;                 // resident step CTAs per SM (256 thr, <= 48 regs)
+constexpr int kSmemThreads = 1024;                // one CTA per SM holding the bitmap in shared memory
+constexpr uint32_t kSmemBitmapMaxBytes = 200u * 1024u;   // bitmap sizes staged in shared memory
 
 // Device-resident control block of one simulation (the persistent scalars of
 // Algorithm 2: step counter; plus running counts and work accounting).
@@ -89,6 +95,16 @@ struct StepArgs {
     int32_t* m_cnt;               // [n_m] cross-chunk partial counts (scratch)
     uint32_t* m_tkt;              // [n_m] cross-chunk tickets (scratch)
     const int32_t* perm;          // internal -> original id, null = identity
+    const int32_t* deg;           // degree by internal id (work accounting of fired S nodes)
+    // Bernoulli probabilities memoised per sim (bit-identical to direct
+    // evaluation): ptab[law * kPTableN + n] = (age, p) for the ages of the
+    // fixed-step sequence (law 0 = latent, 1 = infectious); ps[c] = p of an S
+    // node with c infectious in-neighbours
+    const float2* ptab;
+    const float* ps;
+    int32_t spw;                  // SELL slices per warp
+    uint32_t bm_bytes;            // bitmap bytes copied to shared memory (multiple of 16)
+    uint32_t smem_min_s;          // stage the bitmap when at least this many nodes are S
     ModelF M;
     DevCtl* ctl;
     unsigned long long* deltas;   // [K][kDeltaFields]

@@ -14,7 +14,12 @@ namespace fs {
 extern std::atomic<unsigned long long> g_launch_count;
 
 // fs_step.cu
-cudaError_t launch_step(const StepArgs& a, int age_dtype, cudaStream_t s);
+// pdl: launch with programmatic stream serialization (overlaps the launch
+// with the previous kernel; the kernel waits for it before reading anything)
+cudaError_t launch_step(const StepArgs& a, int age_dtype, cudaStream_t s, bool pdl);
+// one step as the shared-memory-bitmap SELL grid plus, if present, the merge grid
+cudaError_t launch_step_smem(const StepArgs& a, int age_dtype, cudaStream_t s, int num_sms);
+cudaError_t launch_build_ptables(const ModelF& M, int age_dtype, float2* tab, float* ps, cudaStream_t s);
 cudaError_t launch_run_begin(DevCtl* ctl, uint32_t* out, cudaStream_t s);
 cudaError_t launch_run_epilogue(DevCtl* ctl, unsigned long long* deltas, int K, int model, cudaStream_t s);
 cudaError_t launch_refresh(const uint8_t* X, int n, const int32_t* deg, uint32_t* bm0, uint32_t* bm1, DevCtl* ctl,

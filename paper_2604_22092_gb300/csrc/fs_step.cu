@@ -20,6 +20,8 @@
 // ballots. States and ages are updated in place (each node has one owner).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "fs_device.cuh"
 #include "fs_launch.h"
 
@@ -39,31 +41,55 @@ __device__ __forceinline__ uint32_t orig_id(const int32_t* perm, int i)
     return perm ? (uint32_t)__ldg(perm + i) : (uint32_t)i;
 }
 
-// rate, Bernoulli and transition for one node; the original id is looked
-// up only when a uniform is needed (p > 0)
-__device__ __forceinline__ TailResult tail_at(const ModelF& M, int x, float age, uint32_t c,
-                                              const int32_t* perm, int i, uint32_t step)
+// direct evaluation (rare path: ages off the tabulated sequence); kept out of
+// line so that its registers do not weigh on the common path
+__device__ __noinline__ float p_direct(const ModelF& M, int x, float age)
 {
-    float lambda = 0.0f;
-    if (x == kS)
-        lambda = M.beta * (float)c;
-    else if (x == kE)
-        lambda = hazard(M.lat, age);
-    else if (x == kI)
-        lambda = hazard(M.inf, age);
-    bool fired = false;
-    if (lambda > 0.0f) {
-        const float p = -expm1f(-lambda * M.dt);
-        if (p > 0.0f)
-            fired = uniform24(M.key0, M.key1, M.rep, step, orig_id(perm, i)) < p;
+    return p_of_rate(M, hazard(x == kE ? M.lat : M.inf, age));
+}
+
+// Bernoulli probability of one node this step (Section 5.2): S nodes from
+// beta * c, E/I nodes from the hazard at their begin-of-step age. Both come
+// from per-sim tables built by the same FP32 code at init (identical bits);
+// ages off the fixed-step sequence, counts beyond the S table, and launches
+// without tables (null pointers) are evaluated directly.
+__device__ __forceinline__ float node_p(const StepArgs& a, int x, float age, uint32_t c)
+{
+    if (x == kS) {
+        if (c == 0u)
+            return 0.0f;
+        if (a.ps && c < (uint32_t)kPSTableN)
+            return __ldg(a.ps + c);
+        return p_of_rate(a.M, __fmul_rn(a.M.beta, (float)c));
     }
+    if (x == kE || x == kI) {
+        const int n = __float2int_rn(__fmul_rn(age, a.M.inv_dt));
+        if (a.ptab && (unsigned)n < (unsigned)kPTableN) {
+            const float2 e = __ldg(a.ptab + (x == kI ? kPTableN : 0) + n);
+            if (e.x == age)
+                return e.y;
+        }
+        return p_direct(a.M, x, age);
+    }
+    return 0.0f;
+}
+
+// Bernoulli decision and transition for one node (Algorithm 3); the original
+// id is looked up only when a uniform is needed (p > 0)
+__device__ __forceinline__ TailResult tail_at(const StepArgs& a, int x, float age, uint32_t c, int i,
+                                              uint32_t step)
+{
+    const float p = node_p(a, x, age, c);
+    bool fired = false;
+    if (p > 0.0f)
+        fired = uniform24(a.M.key0, a.M.key1, a.M.rep, step, orig_id(a.perm, i)) < p;
     TailResult r;
     if (fired) {
-        r.x = (x == kS) ? (M.model == kSEIR ? kE : kI) : (x + 1);
+        r.x = (x == kS) ? (a.M.model == kSEIR ? kE : kI) : (x + 1);
         r.age = 0.0f;
     } else {
         r.x = x;
-        r.age = (x == kE || x == kI) ? __fadd_rn(age, M.dt) : 0.0f;
+        r.age = (x == kE || x == kI) ? __fadd_rn(age, a.M.dt) : 0.0f;
     }
     r.fired = fired;
     return r;
@@ -86,43 +112,61 @@ __device__ __forceinline__ void warp_deltas(unsigned long long* s_delta, bool fi
 }
 
 // ---------------------------------------------------------------------------
-// One-thread-per-node class: one warp per 32-node SELL slice.
+// One-thread-per-node class: a warp owns `spw` consecutive 32-node SELL
+// slices; the states of four slices are loaded together so that their
+// latencies overlap, then each slice is processed with one lane per node.
 // ---------------------------------------------------------------------------
-template <typename AgeT>
+struct LaneDeltas {
+    uint32_t fS = 0, fE = 0, fI = 0, dS = 0;
+};
+
+template <typename AgeT, bool SMEM_BM>
 __device__ __forceinline__ void sell_slice(const StepArgs& a, uint32_t step, const uint32_t* __restrict__ bm,
-                                           uint32_t* __restrict__ bmn, int slice, unsigned long long* s_delta)
+                                           uint32_t* __restrict__ bmn, int slice, int x, LaneDeltas& ld,
+                                           uint32_t mbar = 0u, bool* ready = nullptr)
 {
+    constexpr int B = 12;                        // column loads in flight per lane
     const int lane = threadIdx.x & 31;
     const int i = slice * 32 + lane;
     const bool valid = i < a.n_thr;
     AgeT* __restrict__ A = static_cast<AgeT*>(a.A);
-    const int x = valid ? (int)a.X[i] : kR;
     float age = 0.0f;
     if (x == kE || x == kI)
         age = AgeIO<AgeT>::load(A[i]);
-    uint32_t c = 0, deg = 0;
+    uint32_t c = 0;
     if (x == kS) {
+        // padding entries hold the sentinel id n, whose bitmap bit is always
+        // 0, so every gathered bit is added without a test
         const int64_t off = __ldg(a.sell_off + slice);
         const int w = (int)((__ldg(a.sell_off + slice + 1) - off) >> 5);
         const int32_t* __restrict__ p = a.sell_col + off + lane;
         const int sentinel = a.sentinel;
-        for (int t0 = 0; t0 < w; t0 += 8) {
-            int32_t jj[8];
-            uint32_t ww[8];
+        for (int t0 = 0; t0 < w; t0 += B) {
+            int32_t jj[B];
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
+            for (int u = 0; u < B; ++u)
                 jj[u] = (t0 + u < w) ? __ldg(p + 32 * (t0 + u)) : sentinel;
+            if constexpr (SMEM_BM) {
+                // the shared copy of the bitmap is awaited only now, after
+                // this lane's first column loads are in flight
+                if (!*ready) {
+                    if (!mbar_wait(mbar, 0u, kWaitLimit))
+                        record_error(a.ctl, kErrTmaTimeout);
+                    *ready = true;
+                }
+            }
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                ww[u] = (jj[u] != sentinel) ? __ldg(bm + (jj[u] >> 5)) : 0u;
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                c += (ww[u] >> (jj[u] & 31)) & 1u;
-                deg += (jj[u] != sentinel);
+            for (int u = 0; u < B; ++u) {
+                uint32_t word;
+                if constexpr (SMEM_BM)
+                    word = bm[jj[u] >> 5];
+                else
+                    word = __ldg(bm + (jj[u] >> 5));
+                c += __funnelshift_r(word, 0u, (uint32_t)jj[u]) & 1u;   // bit jj mod 32
             }
         }
     }
-    const TailResult r = tail_at(a.M, x, age, c, a.perm, i, step);
+    const TailResult r = tail_at(a, x, age, c, i, step);
     if (valid) {
         if (r.x != x)
             a.X[i] = (uint8_t)r.x;
@@ -130,18 +174,55 @@ __device__ __forceinline__ void sell_slice(const StepArgs& a, uint32_t step, con
             A[i] = AgeIO<AgeT>::store(r.age);
     }
     const uint32_t word = __ballot_sync(kFull, valid && r.x == kI);
-    const uint32_t vmask = __ballot_sync(kFull, valid);
-    if (lane == 0) {
-        if (vmask == kFull) {
+    if ((slice + 1) * 32 <= a.n_thr) {
+        if (lane == 0)
             bmn[slice] = word;
-        } else {
-            // the slice shares its word with merge-class nodes: touch own bits only
-            if (word) atomicOr(bmn + slice, word);
+    } else {
+        // the last slice shares its word with merge-class nodes: own bits only
+        const uint32_t vmask = __ballot_sync(kFull, valid);
+        if (lane == 0) {
+            if (word)
+                atomicOr(bmn + slice, word);
             atomicAnd(bmn + slice, word | ~vmask);
         }
     }
-    warp_deltas(s_delta, r.fired && x == kS, r.fired && x == kE, r.fired && x == kI,
-                (r.fired && x == kS) ? deg : 0u);
+    if (r.fired) {
+        ld.fS += x == kS;
+        ld.fE += x == kE;
+        ld.fI += x == kI;
+        if (x == kS)
+            ld.dS += (uint32_t)__ldg(a.deg + i);
+    }
+}
+
+template <typename AgeT>
+__device__ __forceinline__ void sell_warp(const StepArgs& a, uint32_t step, const uint32_t* __restrict__ bm,
+                                          uint32_t* __restrict__ bmn, int s_begin, int s_end, LaneDeltas& ld)
+{
+    const int lane = threadIdx.x & 31;
+    for (int s0 = s_begin; s0 < s_end; s0 += 4) {
+        uint32_t xs = 0;                       // four states, one byte each
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = (s0 + u) * 32 + lane;
+            const uint32_t x = (s0 + u < s_end && i < a.n_thr) ? (uint32_t)a.X[i] : (uint32_t)kR;
+            xs |= x << (8 * u);
+        }
+#pragma unroll 1
+        for (int u = 0; u < 4; ++u) {
+            const int slice = s0 + u;
+            if (slice >= s_end)
+                break;
+            const int x = (int)((xs >> (8 * u)) & 0xffu);
+            // absorbed slice: every node R, next-bitmap word 0, nothing else to do
+            if (__all_sync(kFull, x == kR) && (slice + 1) * 32 <= a.n_thr) {
+                if (lane == 0)
+                    bmn[slice] = 0u;
+                continue;
+            }
+            sell_slice<AgeT, false>(a, step, bm, bmn, slice, x, ld);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -273,7 +354,7 @@ __device__ __forceinline__ void merge_chunk(const StepArgs& a, uint32_t step, co
             float age = 0.0f;
             if (x == kE || x == kI)
                 age = AgeIO<AgeT>::load(A[gi]);
-            const TailResult t = tail_at(a.M, x, age, count, a.perm, gi, step);
+            const TailResult t = tail_at(a, x, age, count, gi, step);
             if (t.x != x)
                 a.X[gi] = (uint8_t)t.x;
             if (t.fired || x == kE || x == kI)
@@ -302,8 +383,14 @@ __device__ __forceinline__ void merge_chunk(const StepArgs& a, uint32_t step, co
 }
 
 template <typename AgeT, bool HAS_MERGE>
-__global__ void __launch_bounds__(kStepThreads) fused_step_kernel(const __grid_constant__ StepArgs a)
+__global__ void __launch_bounds__(kStepThreads, kStepCtasPerSm) fused_step_kernel(const __grid_constant__ StepArgs a)
 {
+    // Programmatic dependent launch: this grid may start while the previous
+    // step drains; nothing it reads is touched before the previous grid has
+    // completed and flushed (griddepcontrol.wait), and the next step may be
+    // scheduled as soon as every CTA of this one has started.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
     __shared__ unsigned long long s_delta[kDeltaFields];
     if (threadIdx.x < kDeltaFields)
         s_delta[threadIdx.x] = 0ull;
@@ -312,18 +399,27 @@ __global__ void __launch_bounds__(kStepThreads) fused_step_kernel(const __grid_c
     const uint32_t* __restrict__ bm = a.bm[par];
     uint32_t* __restrict__ bmn = a.bm[par ^ 1u];
     __syncthreads();
-    if constexpr (HAS_MERGE) {
-        if ((int)blockIdx.x < a.n_chunks) {
+    LaneDeltas ld;
+    bool merge_cta = false;
+    if constexpr (HAS_MERGE)
+        merge_cta = (int)blockIdx.x < a.n_chunks;
+    if (merge_cta) {
+        if constexpr (HAS_MERGE)
             merge_chunk<AgeT>(a, (uint32_t)k, bm, bmn, (int)blockIdx.x, s_delta);
-        } else {
-            const int slice = ((int)blockIdx.x - a.n_chunks) * kSellSlicesPerCta + (int)(threadIdx.x >> 5);
-            if (slice < a.n_slices)
-                sell_slice<AgeT>(a, (uint32_t)k, bm, bmn, slice, s_delta);
-        }
     } else {
-        const int slice = (int)blockIdx.x * kSellSlicesPerCta + (int)(threadIdx.x >> 5);
-        if (slice < a.n_slices)
-            sell_slice<AgeT>(a, (uint32_t)k, bm, bmn, slice, s_delta);
+        const int cta = (int)blockIdx.x - (HAS_MERGE ? a.n_chunks : 0);
+        const int s_begin = (cta * kStepWarps + (int)(threadIdx.x >> 5)) * a.spw;
+        const int s_end = min(s_begin + a.spw, a.n_slices);
+        if (s_begin < s_end)
+            sell_warp<AgeT>(a, (uint32_t)k, bm, bmn, s_begin, s_end, ld);
+        const uint32_t fs_ = __reduce_add_sync(kFull, ld.fS), fe = __reduce_add_sync(kFull, ld.fE);
+        const uint32_t fi = __reduce_add_sync(kFull, ld.fI), ds = __reduce_add_sync(kFull, ld.dS);
+        if ((threadIdx.x & 31) == 0) {
+            if (fs_) atomicAdd(&s_delta[0], (unsigned long long)fs_);
+            if (fe) atomicAdd(&s_delta[1], (unsigned long long)fe);
+            if (fi) atomicAdd(&s_delta[2], (unsigned long long)fi);
+            if (ds) atomicAdd(&s_delta[3], (unsigned long long)ds);
+        }
     }
     __syncthreads();
     if (threadIdx.x < kDeltaFields) {
@@ -331,6 +427,128 @@ __global__ void __launch_bounds__(kStepThreads) fused_step_kernel(const __grid_c
         if (v)
             atomicAdd(a.deltas + (int64_t)a.j * kDeltaFields + threadIdx.x, v);
     }
+}
+
+// ---------------------------------------------------------------------------
+// SELL class with the bitmap in shared memory: one 1024-thread CTA per SM.
+// While many nodes are S (the gather-heavy phase), every CTA copies the
+// whole current bitmap into shared memory with one bulk TMA copy, overlapped
+// with its first state and column loads, and the S lanes' random bit
+// gathers hit shared memory instead of L1/L2. Otherwise the gathers read the
+// bitmap through the read-only path. Warps take slices round-robin and load
+// the next slice's states one iteration ahead.
+// ---------------------------------------------------------------------------
+template <typename AgeT>
+__global__ void __launch_bounds__(kSmemThreads, 1) sell_smem_kernel(const __grid_constant__ StepArgs a)
+{
+    extern __shared__ __align__(128) uint32_t sbm[];
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ unsigned long long s_delta[kDeltaFields];
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < kDeltaFields)
+        s_delta[tid] = 0ull;
+    const int64_t k = a.ctl->step + a.j;
+    const uint32_t par = (uint32_t)(k & 1);
+    const uint32_t* __restrict__ bm = a.bm[par];
+    uint32_t* __restrict__ bmn = a.bm[par ^ 1u];
+    const bool use_smem = a.ctl->counts[0] >= a.smem_min_s;
+    const uint32_t mb = smem_addr(&mbar);
+    if (use_smem && tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(a.bm_bytes) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         smem_addr(sbm)),
+                     "l"(bm), "r"(a.bm_bytes), "r"(mb)
+                     : "memory");
+    }
+    __syncthreads();
+    LaneDeltas ld;
+    bool ready = !use_smem;
+    const int W = (int)gridDim.x * (kSmemThreads / 32);
+    const int first = (int)blockIdx.x * (kSmemThreads / 32) + warp;
+    // states of the slices first + (4g + u) W, u = 0..3, packed one byte each
+    auto load_group = [&](int base) -> uint32_t {
+        uint32_t xs = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int sl = base + u * W;
+            const int i = sl * 32 + lane;
+            const uint32_t x = (sl < a.n_slices && i < a.n_thr) ? (uint32_t)a.X[i] : (uint32_t)kR;
+            xs |= x << (8 * u);
+        }
+        return xs;
+    };
+    uint32_t xs_next = load_group(first);
+    for (int base = first; base < a.n_slices; base += 4 * W) {
+        const uint32_t xs = xs_next;
+        if (base + 4 * W < a.n_slices)
+            xs_next = load_group(base + 4 * W);
+#pragma unroll 1
+        for (int u = 0; u < 4; ++u) {
+            const int slice = base + u * W;
+            if (slice >= a.n_slices)
+                break;
+            const int x = (int)((xs >> (8 * u)) & 0xffu);
+            if (__all_sync(kFull, x == kR) && (slice + 1) * 32 <= a.n_thr) {
+                if (lane == 0)
+                    bmn[slice] = 0u;
+                continue;
+            }
+            if (use_smem)
+                sell_slice<AgeT, true>(a, (uint32_t)k, sbm, bmn, slice, x, ld, mb, &ready);
+            else
+                sell_slice<AgeT, false>(a, (uint32_t)k, bm, bmn, slice, x, ld);
+        }
+    }
+    // the copy into this CTA's shared memory must have landed before it exits
+    if (!ready && !mbar_wait(mb, 0u, kWaitLimit))
+        record_error(a.ctl, kErrTmaTimeout);
+    const uint32_t fs_ = __reduce_add_sync(kFull, ld.fS), fe = __reduce_add_sync(kFull, ld.fE);
+    const uint32_t fi = __reduce_add_sync(kFull, ld.fI), ds = __reduce_add_sync(kFull, ld.dS);
+    if (lane == 0) {
+        if (fs_) atomicAdd(&s_delta[0], (unsigned long long)fs_);
+        if (fe) atomicAdd(&s_delta[1], (unsigned long long)fe);
+        if (fi) atomicAdd(&s_delta[2], (unsigned long long)fi);
+        if (ds) atomicAdd(&s_delta[3], (unsigned long long)ds);
+    }
+    __syncthreads();
+    if (tid < kDeltaFields) {
+        const unsigned long long v = s_delta[tid];
+        if (v)
+            atomicAdd(a.deltas + (int64_t)a.j * kDeltaFields + tid, v);
+    }
+}
+
+// Memoised Bernoulli probabilities of one sim: the fixed-step age sequence
+// a_0 = 0, a_{n+1} = store(a_n + dt) is generated by one thread (it is
+// sequential), then every entry is evaluated in parallel with the step's own
+// hazard code and placed at the index the step computes from the age. Ages
+// that share an index with an earlier, different age keep the earlier one
+// (the step then evaluates them directly). Unfilled entries hold NaN ages.
+__global__ void build_ptables_kernel(ModelF M, int age_dtype, float2* __restrict__ tab, float* __restrict__ ps)
+{
+    __shared__ float ages[kPTableN];
+    if (threadIdx.x == 0) {
+        float v = 0.0f;
+        for (int n = 0; n < kPTableN; ++n) {
+            ages[n] = v;
+            v = age_step_stored(v, M.dt, age_dtype);
+        }
+    }
+    __syncthreads();
+    for (int n = threadIdx.x; n < kPTableN; n += blockDim.x) {
+        const float v = ages[n];
+        const int idx = __float2int_rn(__fmul_rn(v, M.inv_dt));
+        const bool first = n == 0 || __float2int_rn(__fmul_rn(ages[n - 1], M.inv_dt)) != idx;
+        if (first && idx >= 0 && idx < kPTableN) {
+            tab[idx] = make_float2(v, p_of_rate(M, hazard(M.lat, v)));
+            tab[kPTableN + idx] = make_float2(v, p_of_rate(M, hazard(M.inf, v)));
+        }
+    }
+    for (int c = threadIdx.x; c < kPSTableN; c += blockDim.x)
+        ps[c] = p_of_rate(M, __fmul_rn(M.beta, (float)c));
 }
 
 // ---------------------------------------------------------------------------
@@ -464,26 +682,75 @@ __global__ void eval_uniform_kernel(uint32_t key0, uint32_t key1, uint32_t rep, 
 // host launchers
 // ---------------------------------------------------------------------------
 template <typename AgeT>
-static cudaError_t launch_step_t(const StepArgs& a, cudaStream_t s)
+static cudaError_t launch_step_t(const StepArgs& a, cudaStream_t s, bool pdl)
 {
     const int grid = a.n_chunks + a.n_sell_ctas;
     if (grid == 0)
         return cudaSuccess;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kStepThreads);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cudaError_t e;
     if (a.n_chunks > 0)
-        fused_step_kernel<AgeT, true><<<grid, kStepThreads, 0, s>>>(a);
+        e = cudaLaunchKernelEx(&cfg, fused_step_kernel<AgeT, true>, a);
     else
-        fused_step_kernel<AgeT, false><<<grid, kStepThreads, 0, s>>>(a);
+        e = cudaLaunchKernelEx(&cfg, fused_step_kernel<AgeT, false>, a);
     g_launch_count += 1;
-    return cudaGetLastError();
+    return e;
 }
 
-cudaError_t launch_step(const StepArgs& a, int age_dtype, cudaStream_t s)
+cudaError_t launch_step(const StepArgs& a, int age_dtype, cudaStream_t s, bool pdl)
 {
     switch (age_dtype) {
-    case kAgeF16: return launch_step_t<__half>(a, s);
-    case kAgeBF16: return launch_step_t<__nv_bfloat16>(a, s);
-    default: return launch_step_t<float>(a, s);
+    case kAgeF16: return launch_step_t<__half>(a, s, pdl);
+    case kAgeBF16: return launch_step_t<__nv_bfloat16>(a, s, pdl);
+    default: return launch_step_t<float>(a, s, pdl);
     }
+}
+
+template <typename AgeT>
+static cudaError_t launch_step_smem_t(const StepArgs& a, cudaStream_t s, int num_sms)
+{
+    static thread_local int configured = 0;   // dynamic shared memory limit set once per thread
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(sell_smem_kernel<AgeT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kSmemBitmapMaxBytes);
+        if (e != cudaSuccess)
+            return e;
+        configured = 1;
+    }
+    const int grid = std::max(1, std::min(num_sms, (a.n_slices + 31) / 32));
+    sell_smem_kernel<AgeT><<<grid, kSmemThreads, a.bm_bytes, s>>>(a);
+    g_launch_count += 1;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || a.n_chunks == 0)
+        return e;
+    // merge class of the same step (independent of the SELL class) in a second grid
+    StepArgs m = a;
+    m.n_sell_ctas = 0;
+    return launch_step_t<AgeT>(m, s, false);
+}
+
+cudaError_t launch_step_smem(const StepArgs& a, int age_dtype, cudaStream_t s, int num_sms)
+{
+    switch (age_dtype) {
+    case kAgeF16: return launch_step_smem_t<__half>(a, s, num_sms);
+    case kAgeBF16: return launch_step_smem_t<__nv_bfloat16>(a, s, num_sms);
+    default: return launch_step_smem_t<float>(a, s, num_sms);
+    }
+}
+
+cudaError_t launch_build_ptables(const ModelF& M, int age_dtype, float2* tab, float* ps, cudaStream_t s)
+{
+    build_ptables_kernel<<<1, 256, 0, s>>>(M, age_dtype, tab, ps);
+    g_launch_count += 1;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_run_begin(DevCtl* ctl, uint32_t* out, cudaStream_t s)
