@@ -223,6 +223,50 @@ fs_status fs_eval_uniforms(uint64_t seed, uint32_t replicate, int64_t step, cons
                            float* u_dev, int64_t n, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Packed ensembles and batches (the fused step of Algorithm 3 applied to many
+ * realisations at once). An ensemble holds 1..32 realisations of one graph
+ * stored node-major (the state of replicate r of node i next to the other
+ * replicates of node i), so every column read and neighbour-mask gather of a
+ * step serves all of them. Each realisation keeps its own parameters (beta,
+ * laws, seed, replicate index), so it draws exactly the uniforms it would
+ * draw alone: an ensemble's results are identical to running each
+ * realisation on its own with fs_sim_*. A batch (the segment table) steps
+ * every live ensemble added to it with one kernel launch per step;
+ * ensembles may join and leave between launches.
+ * ------------------------------------------------------------------------- */
+typedef struct fs_ens fs_ens;
+typedef struct fs_batch fs_batch;
+
+/* params[n_real]: every entry must share model, age_dtype and index_state;
+ * the index nodes (host int32[n_index], distinct original ids) are the same
+ * for every realisation. Errors: FS_EINVAL, FS_ENOMEM, FS_ECUDA. */
+fs_status fs_ens_create(fs_graph* g, const fs_sim_params* params, int32_t n_real, const int32_t* index_nodes,
+                        int64_t n_index, fs_ens** out);
+/* Runs the ensemble alone for `steps` steps (a batch of one).
+ * counts_out: host uint32[(steps+1)][n_real][4] or NULL. Synchronous. */
+fs_status fs_ens_run(fs_ens* e, int64_t steps, int32_t graph_steps, uint32_t* counts_out);
+/* Host copies of realisation r's state (original node order) and the number
+ * of steps the ensemble has run. Synchronous. */
+fs_status fs_ens_get_state(fs_ens* e, int32_t r, uint8_t* state, void* age, int64_t* step);
+/* FS_EBUSY while the ensemble is a live member of a batch. */
+fs_status fs_ens_destroy(fs_ens* e);
+
+/* A batch steps ensembles of one age storage type together. stream: a
+ * cudaStream_t or NULL for a library stream. */
+fs_status fs_batch_create(int32_t age_dtype, int32_t max_members, void* stream, fs_batch** out);
+/* Adds an ensemble that will run `steps` further steps, starting at the
+ * batch's next launch. counts_out: host uint32[(steps+1)][n_real][4] or NULL,
+ * written when the member completes (row 0 = counts when it joins). */
+fs_status fs_batch_add(fs_batch* b, fs_ens* e, int64_t steps, uint32_t* counts_out);
+/* Launches `launches` steps of every live member (replays of a captured
+ * graph of graph_steps launches; 0 = 50), then retires the members that have
+ * completed (their counts are copied out). Synchronous. */
+fs_status fs_batch_run(fs_batch* b, int64_t launches, int32_t graph_steps);
+/* Live members and the launches still needed to complete all of them. */
+fs_status fs_batch_status(const fs_batch* b, int32_t* live, int64_t* launches_to_finish);
+fs_status fs_batch_destroy(fs_batch* b);
+
+/* ---------------------------------------------------------------------------
  * fs_step_noalloc -- one fused step that allocates no device memory. The
  * paper has no counterpart: this entry point exists for callers that cannot
  * call cudaMalloc while they step -- code running inside CUDA stream capture

@@ -25,7 +25,9 @@ __all__ = [
     "fs_sim_init", "fs_sim_step", "fs_sim_run", "fs_sim_run_async", "fs_sim_sync", "fs_sim_run_timed",
     "fs_kernel_launches",
     "fs_sim_get_state", "fs_sim_set_state", "fs_sim_work", "fs_sim_destroy", "fs_eval_hazard",
-    "fs_eval_uniforms", "fs_step_noalloc", "law", "sim_params", "graph_opts", "FsError", "load",
+    "fs_eval_uniforms", "fs_step_noalloc", "fs_ens_create", "fs_ens_run", "fs_ens_get_state",
+    "fs_ens_destroy", "fs_batch_create", "fs_batch_add", "fs_batch_run", "fs_batch_status", "fs_batch_destroy",
+    "law", "sim_params", "graph_opts", "FsError", "load",
     "FS_S", "FS_E", "FS_I", "FS_R", "FS_SIR", "FS_SEIR", "FS_AGE_F32", "FS_AGE_F16", "FS_AGE_BF16",
     "FS_DISPATCH_AUTO", "FS_DISPATCH_THREAD", "FS_DISPATCH_MERGE",
 ]
@@ -219,3 +221,59 @@ def fs_step_noalloc(g: int, params: _abi.fs_sim_params, step: int, state_dev, ag
     check(load().fs_step_noalloc(g, ctypes.byref(params), int(step), _addr(state_dev), _addr(age_dev),
                                  _addr(bitmap_cur_dev), _addr(bitmap_next_dev), _addr(deltas_dev),
                                  _stream(stream)), "fs_step_noalloc")
+
+
+# --------------------------------------------------------------- ensembles
+def fs_ens_create(g: int, params, index_nodes) -> int:
+    """params: a sequence of fs_sim_params (1..32 realisations of graph g)."""
+    arr = (_abi.fs_sim_params * len(params))(*params)
+    idx = np.ascontiguousarray(index_nodes, dtype=np.int32)
+    h = ctypes.c_void_p()
+    check(load().fs_ens_create(g, arr, len(params), _addr(idx) if idx.size else None, idx.size, ctypes.byref(h)),
+          "fs_ens_create")
+    return h.value
+
+
+def fs_ens_run(e: int, steps: int, n_real: int, graph_steps: int = 0, want_counts: bool = True):
+    c = np.zeros((steps + 1, n_real, 4), dtype=np.uint32) if want_counts else None
+    check(load().fs_ens_run(e, int(steps), int(graph_steps), _addr(c)), "fs_ens_run")
+    return c
+
+
+def fs_ens_get_state(e: int, r: int, n: int, age_dtype: int = FS_AGE_F32):
+    X = np.zeros(n, dtype=np.uint8)
+    A = np.zeros(n, dtype=_AGE_NP[age_dtype])
+    step = ctypes.c_int64()
+    check(load().fs_ens_get_state(e, int(r), _addr(X), _addr(A), ctypes.byref(step)), "fs_ens_get_state")
+    return X, A, step.value
+
+
+def fs_ens_destroy(e: int) -> None:
+    check(load().fs_ens_destroy(e), "fs_ens_destroy")
+
+
+def fs_batch_create(age_dtype: int = FS_AGE_F32, max_members: int = 1024, stream=None) -> int:
+    h = ctypes.c_void_p()
+    check(load().fs_batch_create(int(age_dtype), int(max_members), _stream(stream), ctypes.byref(h)),
+          "fs_batch_create")
+    return h.value
+
+
+def fs_batch_add(b: int, e: int, steps: int, counts_out=None) -> None:
+    """counts_out: None or a host uint32 array of shape (steps+1, n_real, 4),
+    written when the member completes."""
+    check(load().fs_batch_add(b, e, int(steps), _addr(counts_out)), "fs_batch_add")
+
+
+def fs_batch_run(b: int, launches: int, graph_steps: int = 0) -> None:
+    check(load().fs_batch_run(b, int(launches), int(graph_steps)), "fs_batch_run")
+
+
+def fs_batch_status(b: int):
+    live, need = ctypes.c_int32(), ctypes.c_int64()
+    check(load().fs_batch_status(b, ctypes.byref(live), ctypes.byref(need)), "fs_batch_status")
+    return live.value, need.value
+
+
+def fs_batch_destroy(b: int) -> None:
+    check(load().fs_batch_destroy(b), "fs_batch_destroy")

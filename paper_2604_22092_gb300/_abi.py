@@ -74,6 +74,15 @@ PROTOTYPES = {
     "fs_eval_uniforms": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64, VP, VP,
                                         ctypes.c_int64, VP]),
     "fs_step_noalloc": (ctypes.c_int, [VP, P(fs_sim_params), ctypes.c_int64, VP, VP, VP, VP, VP, VP]),
+    "fs_ens_create": (ctypes.c_int, [VP, P(fs_sim_params), ctypes.c_int32, VP, ctypes.c_int64, P(VP)]),
+    "fs_ens_run": (ctypes.c_int, [VP, ctypes.c_int64, ctypes.c_int32, VP]),
+    "fs_ens_get_state": (ctypes.c_int, [VP, ctypes.c_int32, VP, VP, P(ctypes.c_int64)]),
+    "fs_ens_destroy": (ctypes.c_int, [VP]),
+    "fs_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, VP, P(VP)]),
+    "fs_batch_add": (ctypes.c_int, [VP, VP, ctypes.c_int64, VP]),
+    "fs_batch_run": (ctypes.c_int, [VP, ctypes.c_int64, ctypes.c_int32]),
+    "fs_batch_status": (ctypes.c_int, [VP, P(ctypes.c_int32), P(ctypes.c_int64)]),
+    "fs_batch_destroy": (ctypes.c_int, [VP]),
 }
 
 _lib = None

@@ -113,3 +113,53 @@ struct StepArgs {
 };
 
 }  // namespace fs
+
+namespace fs {
+
+// ---------------------------------------------------------------------------
+// Packed ensembles: up to 32 realisations of one graph stored node-major
+// (state[i * R_pad + r]), stepped together so that one column read serves
+// every replicate. A batch steps many such segments in one launch per step
+// through a device segment table.
+// ---------------------------------------------------------------------------
+constexpr int kPackMaxR = 32;
+
+struct PackScen {           // one realisation of a segment
+    ModelF M;               // M.rep = the realisation's replicate index (Philox)
+    const float2* ptab;     // [2][kPTableN] memoised probabilities of its laws
+    const float* ps;        // [kPSTableN]
+};
+
+struct PackSeg {            // one row of the segment table
+    // graph in internal node order (shared with single-realisation sims)
+    const int64_t* sell_off;
+    const int32_t* sell_col;
+    const int64_t* m_ptr;   // merge-class (hub) rows, relative to m_base = n_thr
+    const int32_t* m_col;
+    const int32_t* perm;    // internal -> original id (null = identity)
+    int32_t n, n_thr, n_slices, n_m, sentinel;
+    int32_t R_pad;          // 8, 16 or 32 lanes per node
+    int32_t R;              // live realisations (r >= R are inert padding, state R)
+    int32_t model;
+    // packed state
+    uint8_t* X;             // [n][R_pad]
+    void* A;                // [n][R_pad] ages of the batch's storage type
+    void* mask[2];          // [n + 1] R_pad-bit infectious masks by local step parity
+    const PackScen* scen;   // [R_pad]
+    int64_t join;           // the segment's step index at global step G is k = G - join
+    int64_t kmin, kend;     // it runs steps kmin .. kend-1; counts row k - kmin after step k-1
+    unsigned long long* deltas;   // [2][R_pad][3] per-replicate transitions by local step parity
+    uint32_t* counts;       // [R_pad][4] running counts
+    uint32_t* out;          // [(steps + 1)][R_pad][4] counts after each step, or null
+};
+
+struct PackArgs {
+    const PackSeg* seg;       // segment table
+    const int64_t* thr_pre;   // [n_seg + 1] exclusive prefix of SELL work items
+    const int64_t* hub_pre;   // [n_seg + 1] exclusive prefix of hub rows
+    const int32_t* n_seg;     // number of table rows (device, updated between launches)
+    DevCtl* ctl;              // global step counter and error word
+    int32_t j;                // step offset within the launch sequence
+};
+
+}  // namespace fs

@@ -33,6 +33,13 @@ cudaError_t launch_eval_hazard(const LawF& L, const float* tau, float* h, int64_
 cudaError_t launch_eval_uniforms(uint32_t key0, uint32_t key1, uint32_t rep, uint32_t step, const int32_t* nodes,
                                  float* u, int64_t n, cudaStream_t s);
 
+// fs_pack.cu
+cudaError_t launch_pack_step(const PackArgs& a, int age_dtype, int grid, cudaStream_t s);
+cudaError_t launch_pack_init(uint8_t* X, int n, int R_pad, int R, const int32_t* idx, int64_t n_idx,
+                             const int32_t* inv, int state, void* mask, cudaStream_t s);
+int pack_grid(int num_sms);   // persistent grid of the packed step kernel
+cudaError_t launch_pack_advance(DevCtl* ctl, int K, cudaStream_t s);   // global step += K
+
 // fs_ingest.cu
 struct IngestFlags {
     int32_t dmax;

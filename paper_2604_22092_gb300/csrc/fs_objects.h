@@ -1,0 +1,79 @@
+// fs_objects.h -- host-side definitions of the opaque handles of include/fs.h
+// (internal to libflashstep; shared by the C-ABI translation units).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "fs.h"
+#include "fs_internal.h"
+
+struct fs_graph {
+    int64_t n = 0, nnz = 0;
+    int32_t dmax = 0;
+    int32_t t1 = 0;
+    int32_t n_thr = 0, n_m = 0, n_slices = 0, n_chunks = 0;
+    int64_t e_m = 0, sell_entries = 0;
+    bool identity = true;
+    int32_t* d_perm = nullptr;     // internal -> original
+    int32_t* d_inv = nullptr;      // original -> internal
+    int32_t* d_deg = nullptr;      // degree by internal id
+    int64_t* d_sell_off = nullptr;
+    int32_t* d_sell_col = nullptr;
+    int64_t* d_m_ptr = nullptr;
+    int32_t* d_m_col = nullptr;
+    int32_t* d_m_warp_row = nullptr;
+    int32_t* d_m_chunk_last = nullptr;
+    int64_t bytes = 0;
+    int32_t num_sms = 152;
+    int32_t spw = 1;               // SELL slices per warp (one wave of step CTAs)
+    uint32_t bm_bytes = 0;         // infectious bitmap bytes, rounded up to 16
+    bool smem_path = false;        // bitmap small enough to be staged in shared memory
+    uint32_t smem_min_s = 0;       // S count from which staging pays off
+    int refs = 0;
+    bool failed = false;
+};
+
+struct fs_sim {
+    fs_graph* g = nullptr;
+    fs_sim_params p{};
+    fs::ModelF M{};
+    int age_bytes = 4;
+    uint8_t* d_X = nullptr;
+    void* d_A = nullptr;
+    uint32_t* d_bm[2] = {nullptr, nullptr};
+    int32_t* d_m_cnt = nullptr;
+    uint32_t* d_m_tkt = nullptr;
+    fs::DevCtl* d_ctl = nullptr;
+    unsigned long long* d_deltas = nullptr;
+    float2* d_ptab = nullptr;
+    float* d_ps = nullptr;
+    uint32_t* d_counts = nullptr;
+    int64_t counts_cap = 0;
+    cudaGraphExec_t gexec = nullptr;
+    int gK = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    bool failed = false;
+};
+
+
+// helpers of the C-ABI translation units (fs_api.cu)
+namespace fsapi {
+extern thread_local std::string g_err;
+fs_status fail(fs_status st, const char* fmt, ...);
+// cudaMalloc of count elements (at least one), adding the bytes to *bytes
+template <typename T>
+inline cudaError_t dev_alloc(T** p, size_t count, int64_t* bytes)
+{
+    const size_t b = sizeof(T) * (count > 0 ? count : 1);
+    cudaError_t e = cudaMalloc((void**)p, b);
+    if (e == cudaSuccess && bytes)
+        *bytes += (int64_t)b;
+    return e;
+}
+fs_status check_params(const fs_sim_params* p);
+fs::ModelF to_model(const fs_sim_params& p);
+}  // namespace fsapi

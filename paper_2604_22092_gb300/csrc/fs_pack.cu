@@ -1,0 +1,386 @@
+// fs_pack.cu -- packed ensembles: one launch advances every live segment of
+// a batch by one step of the fused renewal tau-leap (FlashSpread, arXiv
+// 2604.22092, Algorithm 3 at a fixed step), with up to 32 realisations of a
+// graph packed node-major so that each column read and each neighbour-mask
+// gather serves all of them.
+//
+// Work items, taken by warps round-robin over the whole grid:
+//   * hub rows first (merge-class rows, degree > thread_max_deg): one warp per
+//     row; 32 edges per window, each lane loads one neighbour's R-bit mask and
+//     one ballot per S replicate counts that replicate's infectious
+//     neighbours; lane r then runs replicate r's tail;
+//   * SELL items: 32/R_pad nodes of a 32-node slice x R_pad replicates, lane =
+//     (node, replicate); lanes of the same node read the same columns
+//     (broadcast) and extract their own bit of each neighbour's mask.
+// At the start of a launch one warp per segment integrates the previous
+// step's per-replicate deltas into the running counts and writes that row of
+// the segment's counts output (deltas are double-buffered by local step
+// parity, so the integration never races the step that is running).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "fs_device.cuh"
+#include "fs_launch.h"
+
+namespace fs {
+
+namespace {
+
+constexpr uint32_t kFullP = 0xffffffffu;
+
+template <int L> struct MaskOf;
+template <> struct MaskOf<8> { using T = uint8_t; };
+template <> struct MaskOf<16> { using T = uint16_t; };
+template <> struct MaskOf<32> { using T = uint32_t; };
+
+__device__ __noinline__ float pack_p_direct(const ModelF& M, int x, float age)
+{
+    return p_of_rate(M, hazard(x == kE ? M.lat : M.inf, age));
+}
+
+// Bernoulli probability of one (node, replicate), as in the single step
+__device__ __forceinline__ float pack_p(const PackScen& S, int x, float age, uint32_t c)
+{
+    if (x == kS) {
+        if (c == 0u)
+            return 0.0f;
+        if (c < (uint32_t)kPSTableN)
+            return __ldg(S.ps + c);
+        return p_of_rate(S.M, __fmul_rn(S.M.beta, (float)c));
+    }
+    if (x == kE || x == kI) {
+        const int n = __float2int_rn(__fmul_rn(age, S.M.inv_dt));
+        if ((unsigned)n < (unsigned)kPTableN) {
+            const float2 e = __ldg(S.ptab + (x == kI ? kPTableN : 0) + n);
+            if (e.x == age)
+                return e.y;
+        }
+        return pack_p_direct(S.M, x, age);
+    }
+    return 0.0f;
+}
+
+struct PackTail {
+    int x;
+    float age;
+    bool fired;
+};
+
+// the original id is read only when a uniform is drawn (p > 0 implies a
+// valid node: padding and absorbed lanes have p = 0)
+__device__ __forceinline__ PackTail pack_tail(const PackScen& S, int model, int x, float age, uint32_t c,
+                                              const int32_t* perm, int i, uint32_t step)
+{
+    const float p = pack_p(S, x, age, c);
+    bool fired = false;
+    if (p > 0.0f) {
+        const uint32_t orig = perm ? (uint32_t)__ldg(perm + i) : (uint32_t)i;
+        fired = uniform24(S.M.key0, S.M.key1, S.M.rep, step, orig) < p;
+    }
+    PackTail t;
+    if (fired) {
+        t.x = (x == kS) ? (model == kSEIR ? kE : kI) : (x + 1);
+        t.age = 0.0f;
+    } else {
+        t.x = x;
+        t.age = (x == kE || x == kI) ? __fadd_rn(age, S.M.dt) : 0.0f;
+    }
+    t.fired = fired;
+    return t;
+}
+
+// per-replicate transitions of this step: [S->, E->I, I->R]
+__device__ __forceinline__ void add_deltas(const PackSeg& g, int64_t k, int r, uint32_t dS, uint32_t dE,
+                                           uint32_t dI)
+{
+    unsigned long long* d = g.deltas + ((k & 1) * g.R_pad + r) * 3;
+    if (dS) atomicAdd(d + 0, (unsigned long long)dS);
+    if (dE) atomicAdd(d + 1, (unsigned long long)dE);
+    if (dI) atomicAdd(d + 2, (unsigned long long)dI);
+}
+
+// SELL item: nodes slice*32 + round*G + q (q < G = 32/L) x replicates r < L
+template <typename AgeT, int L>
+__device__ __forceinline__ void pack_sell_item(const PackSeg& g, int64_t k, int slice, int round)
+{
+    using MT = typename MaskOf<L>::T;
+    constexpr int G = 32 / L;
+    constexpr int B = 12;
+    const int lane = threadIdx.x & 31;
+    const int q = lane / L, r = lane % L;
+    const int col_lane = round * G + q;            // position of the node inside its slice
+    const int i = slice * 32 + col_lane;
+    const bool valid = i < g.n_thr;
+    const int64_t off_state = (int64_t)i * L + r;
+    AgeT* __restrict__ A = static_cast<AgeT*>(g.A);
+    const MT* __restrict__ mk = static_cast<const MT*>(g.mask[k & 1]);
+    MT* __restrict__ mkn = static_cast<MT*>(g.mask[(k + 1) & 1]);
+    const int x = valid ? (int)g.X[off_state] : kR;
+    if (__all_sync(kFullP, x == kR)) {               // absorbed (or padding) replicates only
+        if (valid && r == 0)
+            mkn[i] = (MT)0;
+        return;
+    }
+    float age = 0.0f;
+    if (x == kE || x == kI)
+        age = AgeIO<AgeT>::load(A[off_state]);
+    uint32_t c = 0;
+    if (x == kS) {
+        const int64_t off = __ldg(g.sell_off + slice);
+        const int w = (int)((__ldg(g.sell_off + slice + 1) - off) >> 5);
+        const int32_t* __restrict__ p = g.sell_col + off + col_lane;
+        for (int t0 = 0; t0 < w; t0 += B) {
+            int32_t jj[B];
+#pragma unroll
+            for (int u = 0; u < B; ++u)
+                jj[u] = (t0 + u < w) ? __ldg(p + 32 * (t0 + u)) : g.sentinel;
+#pragma unroll
+            for (int u = 0; u < B; ++u)                // the sentinel's mask is always 0
+                c += ((uint32_t)__ldg(mk + jj[u]) >> r) & 1u;
+        }
+    }
+    const PackScen& S = g.scen[r];
+    const PackTail t = pack_tail(S, g.model, x, age, c, g.perm, i, (uint32_t)k);
+    if (valid) {
+        if (t.x != x)
+            g.X[off_state] = (uint8_t)t.x;
+        if (t.fired || x == kE || x == kI)
+            A[off_state] = AgeIO<AgeT>::store(t.age);
+    }
+    const uint32_t b = __ballot_sync(kFullP, valid && t.x == kI);
+    if (valid && r == 0)
+        mkn[i] = (MT)((b >> (q * L)) & (L == 32 ? kFullP : ((1u << L) - 1u)));
+    // per-replicate sums over the G nodes of this item
+    uint32_t dS = t.fired && x == kS, dE = t.fired && x == kE, dI = t.fired && x == kI;
+#pragma unroll
+    for (int o = L; o < 32; o <<= 1) {
+        dS += __shfl_xor_sync(kFullP, dS, o);
+        dE += __shfl_xor_sync(kFullP, dE, o);
+        dI += __shfl_xor_sync(kFullP, dI, o);
+    }
+    if (q == 0)
+        add_deltas(g, k, r, dS, dE, dI);
+}
+
+// hub row: one warp, lane r < L is replicate r; 32 edges per window
+template <typename AgeT, int L>
+__device__ __forceinline__ void pack_hub_row(const PackSeg& g, int64_t k, int row)
+{
+    using MT = typename MaskOf<L>::T;
+    constexpr int U = 4;                             // windows in flight
+    const int lane = threadIdx.x & 31;
+    const int i = g.n_thr + row;
+    const bool mine = lane < L;
+    const int64_t off_state = (int64_t)i * L + lane;
+    AgeT* __restrict__ A = static_cast<AgeT*>(g.A);
+    const MT* __restrict__ mk = static_cast<const MT*>(g.mask[k & 1]);
+    MT* __restrict__ mkn = static_cast<MT*>(g.mask[(k + 1) & 1]);
+    const int x = mine ? (int)g.X[off_state] : kR;
+    float age = 0.0f;
+    if (x == kE || x == kI)
+        age = AgeIO<AgeT>::load(A[off_state]);
+    const uint32_t sm = __ballot_sync(kFullP, x == kS);
+    uint32_t c = 0;
+    if (sm) {
+        const int64_t e0 = __ldg(g.m_ptr + row), e1 = __ldg(g.m_ptr + row + 1);
+        for (int64_t w0 = e0; w0 < e1; w0 += 32 * U) {
+            uint32_t m[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t e = w0 + 32 * u + lane;
+                const int32_t col = e < e1 ? __ldg(g.m_col + e) : g.sentinel;
+                m[u] = (uint32_t)__ldg(mk + col);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                uint32_t todo = sm;
+                while (todo) {                        // one ballot per S replicate
+                    const int rr = __ffs(todo) - 1;
+                    todo &= todo - 1u;
+                    const uint32_t bal = __ballot_sync(kFullP, (m[u] >> rr) & 1u);
+                    if (lane == rr)
+                        c += __popc(bal);
+                }
+            }
+        }
+    }
+    const PackScen& S = g.scen[mine ? lane : 0];
+    PackTail t{x, 0.0f, false};
+    if (mine)
+        t = pack_tail(S, g.model, x, age, c, g.perm, i, (uint32_t)k);
+    if (mine) {
+        if (t.x != x)
+            g.X[off_state] = (uint8_t)t.x;
+        if (t.fired || x == kE || x == kI)
+            A[off_state] = AgeIO<AgeT>::store(t.age);
+    }
+    const uint32_t b = __ballot_sync(kFullP, mine && t.x == kI);
+    if (lane == 0)
+        mkn[i] = (MT)b;
+    if (mine)
+        add_deltas(g, k, lane, t.fired && x == kS, t.fired && x == kE, t.fired && x == kI);
+}
+
+// integrate the deltas of the segment's previous step and write its row
+__device__ __forceinline__ void pack_integrate(const PackSeg& g, int64_t k)
+{
+    const int lane = threadIdx.x & 31;
+    if (k <= g.kmin || k > g.kend || lane >= g.R_pad)
+        return;
+    unsigned long long* d = g.deltas + (((k - 1) & 1) * g.R_pad + lane) * 3;
+    const uint32_t l = (uint32_t)d[0], ei = (uint32_t)d[1], ir = (uint32_t)d[2];
+    d[0] = 0ull;
+    d[1] = 0ull;
+    d[2] = 0ull;
+    uint32_t* cnt = g.counts + lane * 4;
+    uint32_t c0 = cnt[0], c1 = cnt[1], c2 = cnt[2], c3 = cnt[3];
+    c0 -= l;
+    if (g.model == kSEIR) {
+        c1 += l - ei;
+        c2 += ei - ir;
+    } else {
+        c2 += l - ir;
+    }
+    c3 += ir;
+    cnt[0] = c0; cnt[1] = c1; cnt[2] = c2; cnt[3] = c3;
+    if (g.out) {
+        uint32_t* o = g.out + ((k - g.kmin) * g.R_pad + lane) * 4;
+        o[0] = c0; o[1] = c1; o[2] = c2; o[3] = c3;
+    }
+}
+
+}  // namespace
+
+template <typename AgeT>
+__global__ void __launch_bounds__(256) pack_step_kernel(const __grid_constant__ PackArgs a)
+{
+    const int64_t G = a.ctl->step + a.j;
+    const int nseg = *a.n_seg;
+    const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    // counts of the previous step, one warp per segment
+    for (int64_t s = gw; s < nseg; s += W) {
+        const PackSeg& g = a.seg[s];
+        pack_integrate(g, G - g.join);
+    }
+    // hub rows (long rows start first), then SELL items
+    const int64_t n_hub = __ldg(a.hub_pre + nseg), n_thr = __ldg(a.thr_pre + nseg);
+    int s = 0;
+    for (int64_t it = gw; it < n_hub; it += W) {
+        while (__ldg(a.hub_pre + s + 1) <= it)
+            ++s;
+        const PackSeg& g = a.seg[s];
+        const int64_t k = G - g.join;
+        if (k < g.kmin || k >= g.kend)
+            continue;
+        const int row = (int)(it - __ldg(a.hub_pre + s));
+        if (g.R_pad == 8)
+            pack_hub_row<AgeT, 8>(g, k, row);
+        else if (g.R_pad == 16)
+            pack_hub_row<AgeT, 16>(g, k, row);
+        else
+            pack_hub_row<AgeT, 32>(g, k, row);
+    }
+    s = 0;
+    for (int64_t it = gw; it < n_thr; it += W) {
+        while (__ldg(a.thr_pre + s + 1) <= it)
+            ++s;
+        const PackSeg& g = a.seg[s];
+        const int64_t k = G - g.join;
+        if (k < g.kmin || k >= g.kend)
+            continue;
+        const int64_t local = it - __ldg(a.thr_pre + s);
+        // L items per slice
+        if (g.R_pad == 8)
+            pack_sell_item<AgeT, 8>(g, k, (int)(local >> 3), (int)(local & 7));
+        else if (g.R_pad == 16)
+            pack_sell_item<AgeT, 16>(g, k, (int)(local >> 4), (int)(local & 15));
+        else
+            pack_sell_item<AgeT, 32>(g, k, (int)(local >> 5), (int)(local & 31));
+    }
+}
+
+// initial packed state of a segment: replicates r < R start in S with the
+// index nodes in `index_state`; padding replicates are absorbed (R)
+__global__ void pack_init_kernel(uint8_t* X, int n, int R_pad, int R)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < (int64_t)n * R_pad)
+        X[t] = (uint8_t)((t % R_pad) < R ? kS : kR);
+}
+
+__global__ void pack_index_kernel(uint8_t* X, const int32_t* idx, int64_t n_idx, const int32_t* inv, int R_pad, int R,
+                                  int state, uint32_t* mask32, uint16_t* mask16, uint8_t* mask8)
+{
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= n_idx)
+        return;
+    const int o = idx[q];
+    const int i = inv ? inv[o] : o;
+    for (int r = 0; r < R; ++r)
+        X[(int64_t)i * R_pad + r] = (uint8_t)state;
+    if (state == kI) {
+        const uint32_t bits = R == 32 ? 0xffffffffu : ((1u << R) - 1u);
+        if (mask32) mask32[i] = bits;
+        if (mask16) mask16[i] = (uint16_t)bits;
+        if (mask8) mask8[i] = (uint8_t)bits;
+    }
+}
+
+__global__ void pack_advance_kernel(DevCtl* ctl, int K)
+{
+    if (threadIdx.x == 0)
+        ctl->step += K;
+}
+
+cudaError_t launch_pack_advance(DevCtl* ctl, int K, cudaStream_t s)
+{
+    pack_advance_kernel<<<1, 32, 0, s>>>(ctl, K);
+    g_launch_count += 1;
+    return cudaGetLastError();
+}
+
+template <typename AgeT>
+static cudaError_t launch_pack_t(const PackArgs& a, int grid, cudaStream_t s)
+{
+    pack_step_kernel<AgeT><<<grid, 256, 0, s>>>(a);
+    g_launch_count += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_step(const PackArgs& a, int age_dtype, int grid, cudaStream_t s)
+{
+    switch (age_dtype) {
+    case kAgeF16: return launch_pack_t<__half>(a, grid, s);
+    case kAgeBF16: return launch_pack_t<__nv_bfloat16>(a, grid, s);
+    default: return launch_pack_t<float>(a, grid, s);
+    }
+}
+
+cudaError_t launch_pack_init(uint8_t* X, int n, int R_pad, int R, const int32_t* idx, int64_t n_idx,
+                             const int32_t* inv, int state, void* mask, cudaStream_t s)
+{
+    const int64_t total = (int64_t)n * R_pad;
+    pack_init_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(X, n, R_pad, R);
+    g_launch_count += 1;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || n_idx == 0)
+        return e;
+    pack_index_kernel<<<(unsigned)((n_idx + 255) / 256), 256, 0, s>>>(
+        X, idx, n_idx, inv, R_pad, R, state, R_pad == 32 ? (uint32_t*)mask : nullptr,
+        R_pad == 16 ? (uint16_t*)mask : nullptr, R_pad == 8 ? (uint8_t*)mask : nullptr);
+    g_launch_count += 1;
+    return cudaGetLastError();
+}
+
+int pack_grid(int num_sms)
+{
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pack_step_kernel<float>, 256, 0) != cudaSuccess ||
+        occ < 1)
+        occ = 4;
+    return num_sms * occ;
+}
+
+}  // namespace fs
