@@ -267,6 +267,54 @@ fs_status fs_batch_status(const fs_batch* b, int32_t* live, int64_t* launches_to
 fs_status fs_batch_destroy(fs_batch* b);
 
 /* ---------------------------------------------------------------------------
+ * Serving: continuous batching of forecast ensembles. A server owns a batch
+ * and a host thread. A request asks for n_scen x replicates realisations of
+ * one resident graph (realisation (s, r) uses scenarios[s] with replicate
+ * index scenarios[s].replicate + r), run for `steps` steps. Requests are
+ * admitted first come, first served while their device memory fits the
+ * budget; admitted requests join the running batch at the next quantum of
+ * `quantum` launches, so work of requests that arrive while others run
+ * overlaps on the device; finished requests leave the batch and free their
+ * memory. Results are identical to running each realisation alone.
+ * Graphs must outlive the requests that use them.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int64_t hbm_budget_bytes;  /* device memory for request state; 0 = 80% of free memory */
+    int32_t max_members;       /* ensembles in flight (segment table rows); 0 = 4096        */
+    int32_t quantum;           /* launches between admissions and retirements; 0 = 10      */
+    int32_t age_dtype;         /* age storage of every request                               */
+    int32_t reserved_;         /* must be 0                                                  */
+} fs_server_cfg;
+
+typedef struct {
+    int64_t submitted, completed, queued, running;
+    int64_t launches;          /* step launches so far                                       */
+    int64_t node_updates;      /* realisation-node-steps completed                           */
+    int64_t device_bytes;      /* request state held on the device now                       */
+    double busy_seconds;       /* time with at least one request in flight                   */
+} fs_server_stats;
+
+typedef struct fs_server fs_server;
+
+fs_status fs_server_create(const fs_server_cfg* cfg, fs_server** out);
+/* Validates and queues a request (host arrays are copied). FS_EINVAL for bad
+ * arguments, FS_ENOMEM if the request alone exceeds the budget. */
+fs_status fs_server_submit(fs_server* s, fs_graph* g, const fs_sim_params* scenarios, int32_t n_scen,
+                           int32_t replicates, const int32_t* index_nodes, int64_t n_index, int64_t steps,
+                           uint64_t* request_id);
+/* *done = 1 when the request has finished; then counts_out (host uint32
+ * [(steps+1)][n_scen*replicates][4], may be NULL) receives its counts and
+ * *seconds (may be NULL) its time from submission to completion. */
+fs_status fs_server_poll(fs_server* s, uint64_t request_id, int32_t* done, uint32_t* counts_out,
+                         double* seconds);
+/* Blocks until every submitted request has finished or `timeout_s` passes
+ * (FS_ETIMEOUT). */
+fs_status fs_server_drain(fs_server* s, double timeout_s);
+fs_status fs_server_stats_get(fs_server* s, fs_server_stats* out);
+/* Stops the thread (finishing nothing further) and frees everything. */
+fs_status fs_server_destroy(fs_server* s);
+
+/* ---------------------------------------------------------------------------
  * fs_step_noalloc -- one fused step that allocates no device memory. The
  * paper has no counterpart: this entry point exists for callers that cannot
  * call cudaMalloc while they step -- code running inside CUDA stream capture

@@ -27,6 +27,8 @@ __all__ = [
     "fs_sim_get_state", "fs_sim_set_state", "fs_sim_work", "fs_sim_destroy", "fs_eval_hazard",
     "fs_eval_uniforms", "fs_step_noalloc", "fs_ens_create", "fs_ens_run", "fs_ens_get_state",
     "fs_ens_destroy", "fs_batch_create", "fs_batch_add", "fs_batch_run", "fs_batch_status", "fs_batch_destroy",
+    "fs_server_create", "fs_server_submit", "fs_server_poll", "fs_server_drain", "fs_server_stats_get",
+    "fs_server_destroy",
     "law", "sim_params", "graph_opts", "FsError", "load",
     "FS_S", "FS_E", "FS_I", "FS_R", "FS_SIR", "FS_SEIR", "FS_AGE_F32", "FS_AGE_F16", "FS_AGE_BF16",
     "FS_DISPATCH_AUTO", "FS_DISPATCH_THREAD", "FS_DISPATCH_MERGE",
@@ -277,3 +279,45 @@ def fs_batch_status(b: int):
 
 def fs_batch_destroy(b: int) -> None:
     check(load().fs_batch_destroy(b), "fs_batch_destroy")
+
+
+# --------------------------------------------------------------- serving
+def fs_server_create(hbm_budget_bytes: int = 0, max_members: int = 0, quantum: int = 0,
+                     age_dtype: int = FS_AGE_F32) -> int:
+    cfg = _abi.fs_server_cfg(int(hbm_budget_bytes), int(max_members), int(quantum), int(age_dtype), 0)
+    h = ctypes.c_void_p()
+    check(load().fs_server_create(ctypes.byref(cfg), ctypes.byref(h)), "fs_server_create")
+    return h.value
+
+
+def fs_server_submit(srv: int, g: int, scenarios, replicates: int, index_nodes, steps: int) -> int:
+    arr = (_abi.fs_sim_params * len(scenarios))(*scenarios)
+    idx = np.ascontiguousarray(index_nodes, dtype=np.int32)
+    rid = ctypes.c_uint64()
+    check(load().fs_server_submit(srv, g, arr, len(scenarios), int(replicates), _addr(idx) if idx.size else None,
+                                  idx.size, int(steps), ctypes.byref(rid)), "fs_server_submit")
+    return rid.value
+
+
+def fs_server_poll(srv: int, request_id: int, steps: int = 0, n_real: int = 0):
+    """(done, counts[(steps+1), n_real, 4] or None, seconds)."""
+    done = ctypes.c_int32()
+    sec = ctypes.c_double()
+    c = np.zeros((steps + 1, n_real, 4), dtype=np.uint32) if n_real else None
+    check(load().fs_server_poll(srv, int(request_id), ctypes.byref(done), _addr(c), ctypes.byref(sec)),
+          "fs_server_poll")
+    return bool(done.value), (c if done.value else None), sec.value
+
+
+def fs_server_drain(srv: int, timeout_s: float = 600.0) -> None:
+    check(load().fs_server_drain(srv, float(timeout_s)), "fs_server_drain")
+
+
+def fs_server_stats_get(srv: int) -> dict:
+    st = _abi.fs_server_stats()
+    check(load().fs_server_stats_get(srv, ctypes.byref(st)), "fs_server_stats_get")
+    return {name: getattr(st, name) for name, _ in st._fields_}
+
+
+def fs_server_destroy(srv: int) -> None:
+    check(load().fs_server_destroy(srv), "fs_server_destroy")

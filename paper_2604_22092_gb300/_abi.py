@@ -49,6 +49,17 @@ class fs_graph_info(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64)]
 
 
+class fs_server_cfg(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_members", ctypes.c_int32),
+                ("quantum", ctypes.c_int32), ("age_dtype", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
+
+
+class fs_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("queued", ctypes.c_int64),
+                ("running", ctypes.c_int64), ("launches", ctypes.c_int64), ("node_updates", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("busy_seconds", ctypes.c_double)]
+
+
 VP = ctypes.c_void_p
 P = ctypes.POINTER
 
@@ -83,6 +94,13 @@ PROTOTYPES = {
     "fs_batch_run": (ctypes.c_int, [VP, ctypes.c_int64, ctypes.c_int32]),
     "fs_batch_status": (ctypes.c_int, [VP, P(ctypes.c_int32), P(ctypes.c_int64)]),
     "fs_batch_destroy": (ctypes.c_int, [VP]),
+    "fs_server_create": (ctypes.c_int, [P(fs_server_cfg), P(VP)]),
+    "fs_server_submit": (ctypes.c_int, [VP, VP, P(fs_sim_params), ctypes.c_int32, ctypes.c_int32, VP,
+                                        ctypes.c_int64, ctypes.c_int64, P(ctypes.c_uint64)]),
+    "fs_server_poll": (ctypes.c_int, [VP, ctypes.c_uint64, P(ctypes.c_int32), VP, P(ctypes.c_double)]),
+    "fs_server_drain": (ctypes.c_int, [VP, ctypes.c_double]),
+    "fs_server_stats_get": (ctypes.c_int, [VP, P(fs_server_stats)]),
+    "fs_server_destroy": (ctypes.c_int, [VP]),
 }
 
 _lib = None

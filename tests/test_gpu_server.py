@@ -1,0 +1,121 @@
+"""Continuous batching (fs_server_*): requests that arrive while others run
+join the running batch, and every request's counts equal its realisations
+run alone through fs_sim_*. Also: a short request submitted after a long one
+finishes first (their work overlaps on the device), admission by the device
+memory budget queues what does not fit and rejects what never can.
+"""
+import math
+import time
+
+import numpy as np
+import pytest
+
+import paper_2604_22092_gb300 as fs
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def graphs():
+    import torch
+    assert torch.cuda.is_available()
+    fs.load()
+    gs = [W.random_regular(15_000, 8, seed=31), W.barabasi_albert(20_000, 4, seed=32),
+          W.erdos_renyi(12_000, 8, seed=33)]
+    hs = [fs.fs_graph_create(g.n, g.row_ptr, g.col_ind) for g in gs]
+    yield gs, hs
+    for h in hs:
+        fs.fs_graph_destroy(h)
+
+
+def scen(k, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for s in range(k):
+        out.append(fs.sim_params(fs.FS_SEIR, fs.law("lognormal", math.log(6.0), float(rng.uniform(0.3, 1.0))),
+                                 float(rng.uniform(0.1, 0.5)), 0.1, seed=seed * 1000 + s,
+                                 latent=fs.law("erlang", 0.75, k=3) if s % 2 else fs.law("weibull", 2.0, 4.0),
+                                 replicate=0))
+    return out
+
+
+def alone_counts(gh, p, idx, steps, replicate):
+    q = fs.sim_params(p.model, p.infectious, p.beta, p.dt, p.seed, latent=p.latent,
+                      replicate=p.replicate + replicate, age_dtype=p.age_dtype)
+    s = fs.fs_sim_init(gh, q, idx)
+    c = fs.fs_sim_run(s, steps)
+    fs.fs_sim_destroy(s)
+    return c
+
+
+def test_requests_in_the_mix_equal_alone_and_overlap(graphs):
+    gs, hs = graphs
+    srv = fs.fs_server_create(quantum=8)
+    reqs = []
+    # a long request first; the other two are submitted once it is running
+    plan = [(0, 2, 20, 3000), (1, 3, 5, 60), (2, 1, 37, 120)]
+    for n, (gi, k, reps, steps) in enumerate(plan):
+        idx = W.index_nodes(gs[gi].n, 25, seed=40 + n)
+        sc = scen(k, seed=50 + n)
+        rid = fs.fs_server_submit(srv, hs[gi], sc, reps, idx, steps)
+        reqs.append((rid, gi, sc, reps, idx, steps))
+        if n == 0:
+            t0 = time.time()
+            while fs.fs_server_stats_get(srv)["running"] < 1:
+                assert time.time() - t0 < 60
+    saw_overlap = False
+    t0 = time.time()
+    while fs.fs_server_stats_get(srv)["completed"] < len(plan):
+        if fs.fs_server_stats_get(srv)["running"] >= 2:
+            saw_overlap = True
+        assert time.time() - t0 < 300
+        time.sleep(0.002)
+    fs.fs_server_drain(srv, 60)
+    results = []
+    for rid, gi, sc, reps, idx, steps in reqs:
+        done, c, sec = fs.fs_server_poll(srv, rid, steps, len(sc) * reps)
+        assert done
+        results.append((c, sec))
+        for s, p in enumerate(sc):
+            for r in range(reps):
+                ref = alone_counts(hs[gi], p, idx, steps, r)
+                np.testing.assert_array_equal(c[:, s * reps + r, :], ref, err_msg=f"request {rid} scen {s} rep {r}")
+    assert saw_overlap
+    # the short request submitted after the long one finished before it
+    assert results[1][1] < results[0][1]
+    st = fs.fs_server_stats_get(srv)
+    assert st["node_updates"] == sum(gs[gi].n * k * reps * steps for gi, k, reps, steps in plan)
+    assert st["device_bytes"] == 0
+    fs.fs_server_destroy(srv)
+
+
+def test_budget_queues_and_rejects(graphs):
+    gs, hs = graphs
+    idx = W.index_nodes(gs[0].n, 10, seed=7)
+    sc = scen(1, seed=70)
+    # a budget that fits one 32-replicate request at a time
+    one = 15_000 * 32 * 5 + 2 * 15_001 * 4 + 32 * (2 * 4096 * 8 + 1024) + 101 * 32 * 16 + 4096
+    srv = fs.fs_server_create(hbm_budget_bytes=int(one * 1.5), quantum=5)
+    ids = [fs.fs_server_submit(srv, hs[0], sc, 32, idx, 100) for _ in range(3)]
+    with pytest.raises(fs.FsError) as e:
+        fs.fs_server_submit(srv, hs[0], sc, 96, idx, 100)       # never fits
+    assert e.value.status == 2
+    max_running = 0
+    while fs.fs_server_stats_get(srv)["completed"] < 3:
+        max_running = max(max_running, fs.fs_server_stats_get(srv)["running"])
+        time.sleep(0.001)
+    assert max_running <= 1
+    outs = [fs.fs_server_poll(srv, rid, 100, 32)[1] for rid in ids]
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o, outs[0])       # same scenario, same replicates
+    for r in (0, 17, 31):
+        np.testing.assert_array_equal(outs[0][:, r, :], alone_counts(hs[0], sc[0], idx, 100, r))
+    with pytest.raises(fs.FsError) as e:
+        fs.fs_server_submit(srv, hs[0], sc, 0, idx, 10)
+    assert e.value.status == 1
+    bad = scen(1, seed=71)
+    bad[0].age_dtype = fs.FS_AGE_F16
+    with pytest.raises(fs.FsError):
+        fs.fs_server_submit(srv, hs[0], bad, 4, idx, 10)
+    fs.fs_server_destroy(srv)
