@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--no-secondary", action="store_true", help="skip the Barabasi-Albert figure")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-served", action="store_true", help="skip the served-vs-plain block")
+    ap.add_argument("--workload", choices=["regular", "ensemble", "serving"], default="regular",
+                    help="regular: the headline line; ensemble / serving: full-size packed and served runs")
+    ap.add_argument("--age", choices=["f32", "f16"], default="f32", help="age storage of ensemble/serving runs")
     return ap.parse_args()
 
 
@@ -195,6 +199,126 @@ def cpu_baseline(g, idx, budget_s=12.0, max_steps=400):
             "seconds": round(dt, 3)}
 
 
+# ------------------------------------------------------------------ ensembles and serving
+def scen_params(fs, sc, replicate: int, age_dtype: int):
+    latent = fs.law("erlang", 0.75, k=3) if sc.latent == "erlang" else fs.law("weibull", 2.0, 4.0)
+    return fs.sim_params(fs.FS_SEIR, fs.law("lognormal", math.log(6.0), float(sc.sigma_inf)), float(sc.beta), 0.1,
+                         int(sc.seed), latent=latent, replicate=replicate, age_dtype=age_dtype)
+
+
+def index_for(g, count=100, seed=1):
+    allowed = W.non_hub_nodes(g) if g.name.startswith("ba") else None
+    pool = g.n if allowed is None else allowed.size
+    return W.index_nodes(g.n, min(count, max(1, pool // 2)), seed=seed, allowed=allowed)
+
+
+def plain_seconds(fs, gh, p, idx, steps):
+    """One realisation through the one-run-per-launch engine, wall time."""
+    t0 = time.perf_counter()
+    s = fs.fs_sim_init(gh, p, idx)
+    fs.fs_sim_run(s, steps, 50, want_counts=True)
+    fs.fs_sim_destroy(s)
+    return time.perf_counter() - t0
+
+
+def ensemble_bench(fs, torch, n_graphs, n_lo, n_hi, steps, age_dtype, reps=3):
+    """Packed batch of 8 scenarios x n_graphs mixed graphs in one launch per
+    step, against each realisation run alone (a sample: scenario 0 of every
+    graph, whose cost stands for the other scenarios of that graph)."""
+    graphs = [W.mixed_graph(q, n_lo, n_hi, seed=2026) for q in range(n_graphs)]
+    ghs = [fs.fs_graph_create(g.n, g.row_ptr, g.col_ind) for g in graphs]
+    idxs = [index_for(g, seed=q + 1) for q, g in enumerate(graphs)]
+    scen = [W.scenarios(8, seed=1000 + q) for q in range(n_graphs)]
+    stream = torch.cuda.Stream()
+    times = []
+    for it in range(reps):
+        ens = [fs.fs_ens_create(ghs[q], [scen_params(fs, sc, s, age_dtype) for s, sc in enumerate(scen[q])], idxs[q])
+               for q in range(n_graphs)]
+        b = fs.fs_batch_create(age_dtype, n_graphs + 1, stream=stream)
+        for e in ens:
+            fs.fs_batch_add(b, e, steps)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        fs.fs_batch_run(b, steps + 1, 50)
+        ev1.record(stream)
+        ev1.synchronize()
+        times.append(ev0.elapsed_time(ev1) * 1e-3)
+        fs.fs_batch_destroy(b)
+        for e in ens:
+            fs.fs_ens_destroy(e)
+    served_s = float(np.median(times))
+    updates = sum(g.n for g in graphs) * 8 * steps
+    for warm in (True, False):   # the first pass captures each sim's graph and warms caches
+        plain = [plain_seconds(fs, ghs[q], scen_params(fs, scen[q][0], 0, age_dtype), idxs[q], steps)
+                 for q in range(n_graphs)]
+    plain_s = 8 * float(np.sum(plain))
+    for gh in ghs:
+        fs.fs_graph_destroy(gh)
+    return {"workload": f"packed-{n_graphs}graphs-x8scen-n{n_lo:.0e}-{n_hi:.0e}-{steps}steps".replace("+0", ""),
+            "realisations": 8 * n_graphs, "nodes_total": int(sum(g.n for g in graphs)),
+            "age_storage": "f16" if age_dtype == fs.FS_AGE_F16 else "f32",
+            "served_gnups": round(updates / served_s / 1e9, 3), "served_seconds": round(served_s, 4),
+            "plain_gnups": round(updates / plain_s / 1e9, 3), "plain_seconds_estimated": round(plain_s, 3),
+            "speedup": round(plain_s / served_s, 2),
+            "plain_sample": "scenario 0 of every graph run alone through fs_sim_run, x8 for the other scenarios"}
+
+
+def serving_bench(fs, torch, n_requests, n_pool, n_hi, steps, rep_lo, rep_hi, window_s, age_dtype):
+    """Poisson stream of requests against the server, then the same stream
+    through the plain engine (each realisation alone, FIFO); the plain
+    queue is replayed on measured service times."""
+    pool = [W.mixed_graph(q, 1e4, n_hi, seed=77) for q in range(n_pool)]
+    ghs = [fs.fs_graph_create(g.n, g.row_ptr, g.col_ind) for g in pool]
+    idxs = [index_for(g, seed=q + 5) for q, g in enumerate(pool)]
+    reqs = W.request_stream(n_requests, n_requests / window_s, n_pool, seed=99, steps=steps, rep_lo=rep_lo,
+                            rep_hi=rep_hi)
+    srv = fs.fs_server_create(quantum=10, age_dtype=age_dtype)
+    # warm the server's graph capture on a tiny request
+    wid = fs.fs_server_submit(srv, ghs[0], [scen_params(fs, W.scenarios(1, 5)[0], 0, age_dtype)], 1, idxs[0], 5)
+    fs.fs_server_drain(srv, 120)
+    t0 = time.perf_counter()
+    ids = []
+    for r in reqs:
+        while time.perf_counter() - t0 < r.arrival:
+            time.sleep(0.0002)
+        sc = W.scenarios(r.n_scen, seed=r.seed)
+        ids.append(fs.fs_server_submit(srv, ghs[r.graph], [scen_params(fs, c, 0, age_dtype) for c in sc],
+                                       r.replicates, idxs[r.graph], r.steps))
+    fs.fs_server_drain(srv, 3600)
+    makespan = time.perf_counter() - t0
+    lat = np.array([fs.fs_server_poll(srv, rid)[2] for rid in ids])
+    fs.fs_server_destroy(srv)
+    updates = sum(pool[r.graph].n * r.n_scen * r.replicates * r.steps for r in reqs)
+    # plain engine: service time of a request = its realisations one by one
+    # (one realisation per graph and scenario count is timed and scaled)
+    svc = {}
+    clock, plain_lat = 0.0, []
+    for r in reqs:
+        key = r.graph
+        if key not in svc:
+            p = scen_params(fs, W.scenarios(1, seed=r.seed)[0], 0, age_dtype)
+            plain_seconds(fs, ghs[r.graph], p, idxs[r.graph], r.steps)
+            svc[key] = plain_seconds(fs, ghs[r.graph], p, idxs[r.graph], r.steps)
+        service = svc[key] * r.n_scen * r.replicates
+        start = max(clock, r.arrival)
+        clock = start + service
+        plain_lat.append(clock - r.arrival)
+    plain_lat = np.array(plain_lat)
+    for gh in ghs:
+        fs.fs_graph_destroy(gh)
+    return {"workload": f"serving-{n_requests}req-pool{n_pool}-n1e4-{n_hi:.0e}-{steps}steps-rep{rep_lo}-{rep_hi}".replace("+0", ""),
+            "arrival_rate_per_s": round(n_requests / window_s, 2),
+            "served_gnups": round(updates / makespan / 1e9, 3), "served_makespan_s": round(makespan, 3),
+            "served_p50_s": round(float(np.percentile(lat, 50)), 4), "served_p99_s": round(float(np.percentile(lat, 99)), 4),
+            "plain_gnups": round(updates / clock / 1e9, 3), "plain_makespan_s": round(clock, 3),
+            "plain_p50_s": round(float(np.percentile(plain_lat, 50)), 4),
+            "plain_p99_s": round(float(np.percentile(plain_lat, 99)), 4),
+            "speedup": round(clock / makespan, 2), "node_updates": int(updates),
+            "plain_engine": "each realisation alone through fs_sim_run (CUDA Graph step loop), FIFO; service times "
+                            "measured per graph and scaled by realisations; queue replayed on them"}
+
+
 # ------------------------------------------------------------------ arms
 def run_flashstep(args, rank, world, local_rank):
     import torch
@@ -291,6 +415,9 @@ def run_flashstep(args, rank, world, local_rank):
         out["e2e"] = e2e(fs, torch, g, idx, prm, args, stream)
     if rank == 0 and not args.no_secondary:
         out["secondary"] = secondary_ba(fs, torch, args, stream, flush)
+    if rank == 0 and not args.no_served:
+        out["served"] = serving_bench(fs, torch, n_requests=24, n_pool=8, n_hi=2e5, steps=200, rep_lo=16,
+                                      rep_hi=64, window_s=0.25, age_dtype=fs.FS_AGE_F32)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(g, idx)
     if dist:
@@ -391,8 +518,25 @@ def run_reference(args, rank, world):
             "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_extra(args):
+    """Full-size packed-ensemble or serving runs (their own JSON line)."""
+    import torch
+    import paper_2604_22092_gb300 as fs
+    fs.load()
+    age = fs.FS_AGE_F16 if args.age == "f16" else fs.FS_AGE_F32
+    if args.workload == "ensemble":
+        res = ensemble_bench(fs, torch, n_graphs=64, n_lo=1e4, n_hi=2e6, steps=500, age_dtype=age)
+    else:
+        res = serving_bench(fs, torch, n_requests=200, n_pool=24, n_hi=1e6, steps=500, rep_lo=16, rep_hi=256,
+                            window_s=2.0, age_dtype=age)
+    print(json.dumps({"metric": METRIC, "unit": UNIT, "impl": "flashstep", "data": "synthetic", **res}), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload != "regular":
+        run_extra(args)
+        return
     if int(os.environ.get("WORLD_SIZE", "1")) > 1 and "LOCAL_RANK" in os.environ:
         # one visible GPU per replica, so that every CUDA runtime in the
         # process (torch's and the library's) addresses the same device

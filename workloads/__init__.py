@@ -268,3 +268,66 @@ def non_hub_nodes(g: Graph) -> np.ndarray:
     """Nodes of degree at most ceil(mean degree)."""
     deg = g.degree
     return np.flatnonzero(deg <= math.ceil(deg.mean())).astype(np.int64)
+
+
+# ---------------------------------------------------------------- ensembles
+@dataclass
+class Scenario:
+    """Parameters of one realisation drawn for the ensemble and serving
+    workloads: beta ~ U[0.1, 0.5]; infectious log-normal with mu = ln 6 and
+    sigma ~ U[0.3, 1.0]; latent Erlang(3, rate 0.75/d, mean 4 d) for even
+    scenario indices and Weibull(2, 4 d) for odd ones."""
+    beta: float
+    sigma_inf: float
+    latent: str            # "erlang" or "weibull"
+    seed: int
+
+
+def scenarios(count: int, seed: int) -> list[Scenario]:
+    u = uniform01(seed, 2 * count, stream=91)
+    return [Scenario(0.1 + 0.4 * u[2 * s], 0.3 + 0.7 * u[2 * s + 1], "erlang" if s % 2 == 0 else "weibull",
+                     int(seed * 1_000_003 + s) & 0xFFFFFFFFFFFF) for s in range(count)]
+
+
+def mixed_graph(q: int, n_lo: float, n_hi: float, seed: int) -> Graph:
+    """Graph q of a mixed ensemble: N log-uniform in [n_lo, n_hi]; the family
+    cycles random-regular (k uniform in 4..20), Erdos-Renyi (mean degree 8)
+    and Barabasi-Albert (m uniform in 2..8); graph seed q."""
+    u = uniform01(seed, 3, stream=300 + q)
+    n = int(round(math.exp(math.log(n_lo) + u[0] * (math.log(n_hi) - math.log(n_lo)))))
+    fam = q % 3
+    if fam == 0:
+        k = 4 + int(u[1] * 17)
+        if (n * k) % 2:
+            n += 1
+        return random_regular(n, k, seed=q)
+    if fam == 1:
+        return erdos_renyi(n, 8.0, seed=q)
+    m = 2 + int(u[2] * 7)
+    return barabasi_albert(n, m, seed=q)
+
+
+@dataclass
+class Request:
+    arrival: float         # seconds after the start
+    graph: int             # index into the graph pool
+    n_scen: int
+    replicates: int
+    steps: int
+    seed: int
+
+
+def request_stream(count: int, rate_per_s: float, n_graphs: int, seed: int, steps: int = 200,
+                   rep_lo: int = 16, rep_hi: int = 256) -> list[Request]:
+    """Poisson arrivals (exponential gaps at `rate_per_s`); each request picks
+    a pooled graph uniformly, 1..4 scenarios and a replicate count
+    log-uniform in [rep_lo, rep_hi]."""
+    u = uniform01(seed, 4 * count, stream=404)
+    t = 0.0
+    out = []
+    for r in range(count):
+        t += -math.log(max(u[4 * r], 1e-12)) / rate_per_s
+        reps = int(round(math.exp(math.log(rep_lo) + u[4 * r + 1] * (math.log(rep_hi) - math.log(rep_lo)))))
+        out.append(Request(t, int(u[4 * r + 2] * n_graphs), 1 + int(u[4 * r + 3] * 4), reps, steps,
+                           seed * 7919 + r))
+    return out
