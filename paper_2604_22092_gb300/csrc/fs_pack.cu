@@ -100,67 +100,212 @@ __device__ __forceinline__ void add_deltas(const PackSeg& g, int64_t k, int r, u
     if (dI) atomicAdd(d + 2, (unsigned long long)dI);
 }
 
-// SELL item: nodes slice*32 + round*G + q (q < G = 32/L) x replicates r < L
-template <typename AgeT, int L>
-__device__ __forceinline__ void pack_sell_item(const PackSeg& g, int64_t k, int slice, int round)
+// Ages of 8 consecutive replicates of one node, as one or two 16-byte loads
+template <typename AgeT> struct AgeVec8;
+template <> struct AgeVec8<float> {
+    float v[8];
+    __device__ __forceinline__ void load(const float* p)
+    {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+        const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    }
+    __device__ __forceinline__ void store(float* p) const
+    {
+        reinterpret_cast<float4*>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
+        reinterpret_cast<float4*>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+    }
+};
+template <typename H> struct AgeVec8H {
+    float v[8];
+    __device__ __forceinline__ void load(const H* p)
+    {
+        const uint4 a = __ldg(reinterpret_cast<const uint4*>(p));
+        const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            H lo, hi;
+            const uint16_t l16 = (uint16_t)(w[q] & 0xffffu), h16 = (uint16_t)(w[q] >> 16);
+            memcpy(&lo, &l16, 2);
+            memcpy(&hi, &h16, 2);
+            v[2 * q] = AgeIO<H>::load(lo);
+            v[2 * q + 1] = AgeIO<H>::load(hi);
+        }
+    }
+    __device__ __forceinline__ void store(H* p) const
+    {
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const H lo = AgeIO<H>::store(v[2 * q]), hi = AgeIO<H>::store(v[2 * q + 1]);
+            uint16_t l16, h16;
+            memcpy(&l16, &lo, 2);
+            memcpy(&h16, &hi, 2);
+            w[q] = (uint32_t)l16 | ((uint32_t)h16 << 16);
+        }
+        *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+};
+template <> struct AgeVec8<__half> : AgeVec8H<__half> {};
+template <> struct AgeVec8<__nv_bfloat16> : AgeVec8H<__nv_bfloat16> {};
+
+// true when any byte of v equals b (b < 128)
+__device__ __forceinline__ bool has_byte(uint64_t v, uint32_t b)
 {
-    using MT = typename MaskOf<L>::T;
-    constexpr int G = 32 / L;
+    const uint64_t x = v ^ (0x0101010101010101ull * b);
+    return ((x - 0x0101010101010101ull) & ~x & 0x8080808080808080ull) != 0ull;
+}
+
+// SELL slice: lane = node, each lane carries all RP replicates of its node.
+// One column load and one RP-bit mask load per edge serve every replicate;
+// the mask bits are spread into byte counters (8 per 64-bit word) through a
+// 256-entry table in shared memory. Replicates are then processed in groups
+// of 8 with vector loads and stores of their states and ages; one Philox
+// call serves the replicates that share a key and a counter (rep / 4).
+template <typename AgeT, int RP>
+__device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slice, const uint64_t* __restrict__ lut)
+{
+    using MT = typename MaskOf<RP>::T;
+    constexpr int NB = RP / 8;
     constexpr int B = 12;
     const int lane = threadIdx.x & 31;
-    const int q = lane / L, r = lane % L;
-    const int col_lane = round * G + q;            // position of the node inside its slice
-    const int i = slice * 32 + col_lane;
+    const int i = slice * 32 + lane;
     const bool valid = i < g.n_thr;
-    const int64_t off_state = (int64_t)i * L + r;
-    AgeT* __restrict__ A = static_cast<AgeT*>(g.A);
     const MT* __restrict__ mk = static_cast<const MT*>(g.mask[k & 1]);
     MT* __restrict__ mkn = static_cast<MT*>(g.mask[(k + 1) & 1]);
-    const int x = valid ? (int)g.X[off_state] : kR;
-    if (__all_sync(kFullP, x == kR)) {               // absorbed (or padding) replicates only
-        if (valid && r == 0)
+    uint64_t xs[NB];
+    const uint64_t* xp = reinterpret_cast<const uint64_t*>(g.X + (int64_t)i * RP);
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+        xs[b] = valid ? xp[b] : 0x0303030303030303ull;
+    bool allR = true, anyS = false;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        allR &= xs[b] == 0x0303030303030303ull;
+        anyS |= has_byte(xs[b], (uint32_t)kS);
+    }
+    if (__all_sync(kFullP, allR)) {
+        if (valid)
             mkn[i] = (MT)0;
         return;
     }
-    float age = 0.0f;
-    if (x == kE || x == kI)
-        age = AgeIO<AgeT>::load(A[off_state]);
-    uint32_t c = 0;
-    if (x == kS) {
+    uint64_t cnt[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+        cnt[b] = 0ull;
+    if (anyS) {
         const int64_t off = __ldg(g.sell_off + slice);
         const int w = (int)((__ldg(g.sell_off + slice + 1) - off) >> 5);
-        const int32_t* __restrict__ p = g.sell_col + off + col_lane;
+        const int32_t* __restrict__ p = g.sell_col + off + lane;
         for (int t0 = 0; t0 < w; t0 += B) {
             int32_t jj[B];
 #pragma unroll
             for (int u = 0; u < B; ++u)
                 jj[u] = (t0 + u < w) ? __ldg(p + 32 * (t0 + u)) : g.sentinel;
 #pragma unroll
-            for (int u = 0; u < B; ++u)                // the sentinel's mask is always 0
-                c += ((uint32_t)__ldg(mk + jj[u]) >> r) & 1u;
+            for (int u = 0; u < B; ++u) {
+                const uint32_t m = (uint32_t)__ldg(mk + jj[u]);   // the sentinel's mask is always 0
+#pragma unroll
+                for (int b = 0; b < NB; ++b)
+                    cnt[b] += lut[(m >> (8 * b)) & 0xffu];
+            }
         }
     }
-    const PackScen& S = g.scen[r];
-    const PackTail t = pack_tail(S, g.model, x, age, c, g.perm, i, (uint32_t)k);
-    if (valid) {
-        if (t.x != x)
-            g.X[off_state] = (uint8_t)t.x;
-        if (t.fired || x == kE || x == kI)
-            A[off_state] = AgeIO<AgeT>::store(t.age);
-    }
-    const uint32_t b = __ballot_sync(kFullP, valid && t.x == kI);
-    if (valid && r == 0)
-        mkn[i] = (MT)((b >> (q * L)) & (L == 32 ? kFullP : ((1u << L) - 1u)));
-    // per-replicate sums over the G nodes of this item
-    uint32_t dS = t.fired && x == kS, dE = t.fired && x == kE, dI = t.fired && x == kI;
+    AgeT* __restrict__ Abase = static_cast<AgeT*>(g.A) + (int64_t)i * RP;
+    uint8_t* Xb = g.X + (int64_t)i * RP;
+    uint32_t newmask = 0;
+    // Philox cache: counter word 2 and key of the last draw
+    uint4 ph = make_uint4(0u, 0u, 0u, 0u);
+    uint32_t ph_k0 = 0u, ph_k1 = 0u, ph_c2 = 0xffffffffu;
+    bool ph_ok = false;
+    const uint32_t orig = (valid && g.perm) ? (uint32_t)__ldg(g.perm + i) : (uint32_t)i;
+    // groups are taken from xs[0] / cnt[0], the arrays shifted down after each
+    // one (static indices keep them in registers)
+#pragma unroll 1
+    for (int b = 0; b < NB; ++b) {
+        if (b * 8 >= g.R)
+            break;
+        const uint64_t xv = xs[0];
+        const uint64_t cb = cnt[0];
 #pragma unroll
-    for (int o = L; o < 32; o <<= 1) {
-        dS += __shfl_xor_sync(kFullP, dS, o);
-        dE += __shfl_xor_sync(kFullP, dE, o);
-        dI += __shfl_xor_sync(kFullP, dI, o);
+        for (int t = 0; t + 1 < NB; ++t) {
+            xs[t] = xs[t + 1];
+            cnt[t] = cnt[t + 1];
+        }
+        const bool ageful = valid && (has_byte(xv, (uint32_t)kE) || has_byte(xv, (uint32_t)kI));
+        AgeVec8<AgeT> ag;
+        if (ageful)
+            ag.load(Abase + b * 8);
+        uint64_t xnew = xv;
+        bool age_dirty = false;
+        uint32_t fS = 0, fE = 0, fI = 0;     // bit q: replicate b*8+q fired from S / E / I
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int r = b * 8 + q;
+            const int x = (int)((xv >> (8 * q)) & 0xffu);
+            const float age = ageful ? ag.v[q] : 0.0f;
+            const uint32_t c = (uint32_t)((cb >> (8 * q)) & 0xffu);
+            const PackScen& S = g.scen[r];
+            const float pr = (x == kR) ? 0.0f : pack_p(S, x, age, c);
+            bool fired = false;
+            if (pr > 0.0f) {
+                const uint32_t k0 = S.M.key0, k1 = S.M.key1, rep = S.M.rep;
+                if (!ph_ok || k0 != ph_k0 || k1 != ph_k1 || (rep >> 2) != ph_c2) {
+                    ph = philox4x32_10(make_uint4(orig, (uint32_t)k, rep >> 2, 0u), k0, k1);
+                    ph_k0 = k0;
+                    ph_k1 = k1;
+                    ph_c2 = rep >> 2;
+                    ph_ok = true;
+                }
+                const uint32_t sel = rep & 3u;
+                const uint32_t word = sel == 0 ? ph.x : sel == 1 ? ph.y : sel == 2 ? ph.z : ph.w;
+                fired = (float)(word >> 8) * 5.9604644775390625e-08f < pr;
+            }
+            int xn = x;
+            float an = 0.0f;
+            if (fired) {
+                xn = (x == kS) ? (g.model == kSEIR ? kE : kI) : (x + 1);
+                an = 0.0f;
+                fS |= (uint32_t)(x == kS) << q;
+                fE |= (uint32_t)(x == kE) << q;
+                fI |= (uint32_t)(x == kI) << q;
+            } else if (x == kE || x == kI) {
+                an = __fadd_rn(age, S.M.dt);
+            }
+            if (fired || x == kE || x == kI) {
+                ag.v[q] = an;
+                age_dirty = true;
+            }
+            xnew = (xnew & ~(0xffull << (8 * q))) | ((uint64_t)xn << (8 * q));
+            newmask |= (uint32_t)(xn == kI) << r;
+        }
+        if (valid) {
+            if (xnew != xv)
+                reinterpret_cast<uint64_t*>(Xb)[b] = xnew;
+            if (age_dirty) {
+                if (!ageful) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)   // only replicates that fired from S hold a non-zero age slot
+                        if (!((fS >> q) & 1u))
+                            ag.v[q] = 0.0f;
+                }
+                ag.store(Abase + b * 8);
+            }
+        }
+        // per-replicate transitions of this group, summed over the warp
+        if (!__any_sync(kFullP, (fS | fE | fI) != 0u))
+            continue;
+#pragma unroll 1
+        for (int q = 0; q < 8; ++q) {
+            const uint32_t a = __popc(__ballot_sync(kFullP, (fS >> q) & 1u));
+            const uint32_t e = __popc(__ballot_sync(kFullP, (fE >> q) & 1u));
+            const uint32_t h = __popc(__ballot_sync(kFullP, (fI >> q) & 1u));
+            if (lane == 0 && (a | e | h))
+                add_deltas(g, k, b * 8 + q, a, e, h);
+        }
     }
-    if (q == 0)
-        add_deltas(g, k, r, dS, dE, dI);
+    if (valid)
+        mkn[i] = (MT)newmask;
 }
 
 // hub row: one warp, lane r < L is replicate r; 32 edges per window
@@ -255,6 +400,15 @@ __device__ __forceinline__ void pack_integrate(const PackSeg& g, int64_t k)
 template <typename AgeT>
 __global__ void __launch_bounds__(256) pack_step_kernel(const __grid_constant__ PackArgs a)
 {
+    // byte r of lut[m] is bit r of m: spreads an 8-replicate mask into byte counters
+    __shared__ uint64_t lut[256];
+    for (int m = threadIdx.x; m < 256; m += blockDim.x) {
+        uint64_t v = 0;
+        for (int r = 0; r < 8; ++r)
+            v |= (uint64_t)((m >> r) & 1) << (8 * r);
+        lut[m] = v;
+    }
+    __syncthreads();
     const int64_t G = a.ctl->step + a.j;
     const int nseg = *a.n_seg;
     const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -290,14 +444,13 @@ __global__ void __launch_bounds__(256) pack_step_kernel(const __grid_constant__ 
         const int64_t k = G - g.join;
         if (k < g.kmin || k >= g.kend)
             continue;
-        const int64_t local = it - __ldg(a.thr_pre + s);
-        // L items per slice
+        const int slice = (int)(it - __ldg(a.thr_pre + s));   // one item per 32-node slice
         if (g.R_pad == 8)
-            pack_sell_item<AgeT, 8>(g, k, (int)(local >> 3), (int)(local & 7));
+            pack_slice<AgeT, 8>(g, k, slice, lut);
         else if (g.R_pad == 16)
-            pack_sell_item<AgeT, 16>(g, k, (int)(local >> 4), (int)(local & 15));
+            pack_slice<AgeT, 16>(g, k, slice, lut);
         else
-            pack_sell_item<AgeT, 32>(g, k, (int)(local >> 5), (int)(local & 31));
+            pack_slice<AgeT, 32>(g, k, slice, lut);
     }
 }
 

@@ -407,7 +407,7 @@ static fs_status upload_table(fs_batch* b)
         const Member& m = b->members[q];
         b->h_seg[q] = segment_of(m);
         const fs_graph* g = m.e->g;
-        b->h_thr[q + 1] = b->h_thr[q] + (int64_t)g->n_slices * m.e->R_pad;
+        b->h_thr[q + 1] = b->h_thr[q] + (int64_t)g->n_slices;
         b->h_hub[q + 1] = b->h_hub[q] + g->n_m;
     }
     *b->h_nseg = ns;
