@@ -123,11 +123,17 @@ namespace fs {
 // through a device segment table.
 // ---------------------------------------------------------------------------
 constexpr int kPackMaxR = 32;
+constexpr int kPackThreads = 128;       // threads per block of the packed step
 
-struct PackScen {           // one realisation of a segment
-    ModelF M;               // M.rep = the realisation's replicate index (Philox)
+struct __align__(16) PackScen {   // one realisation of a segment
+    // what the step reads per replicate, as three 16-byte words
     const float2* ptab;     // [2][kPTableN] memoised probabilities of its laws
     const float* ps;        // [kPSTableN]
+    uint32_t key0, key1, rep;   // copies of M.key0, M.key1, M.rep (Philox key and replicate index)
+    float dt;               // copy of M.dt
+    float beta, inv_dt;     // copies of M.beta, M.inv_dt
+    int32_t pad_[2];
+    ModelF M;               // all parameters (direct evaluation when a table misses)
 };
 
 struct PackSeg {            // one row of the segment table

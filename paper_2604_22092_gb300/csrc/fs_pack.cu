@@ -173,6 +173,12 @@ __device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slic
     const bool valid = i < g.n_thr;
     const MT* __restrict__ mk = static_cast<const MT*>(g.mask[k & 1]);
     MT* __restrict__ mkn = static_cast<MT*>(g.mask[(k + 1) & 1]);
+    const PackScen* __restrict__ scen = g.scen;
+    const int model = g.model;
+    // independent loads first: slice offsets, original id, states
+    const int64_t off = __ldg(g.sell_off + slice);
+    const int64_t off_end = __ldg(g.sell_off + slice + 1);
+    const uint32_t orig = (valid && g.perm) ? (uint32_t)__ldg(g.perm + i) : (uint32_t)i;
     uint64_t xs[NB];
     const uint64_t* xp = reinterpret_cast<const uint64_t*>(g.X + (int64_t)i * RP);
 #pragma unroll
@@ -189,13 +195,27 @@ __device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slic
             mkn[i] = (MT)0;
         return;
     }
+    AgeT* __restrict__ Abase = static_cast<AgeT*>(g.A) + (int64_t)i * RP;
+    uint8_t* Xb = g.X + (int64_t)i * RP;
+    // ages are read and written only for groups holding an E or I
+    // replicate: the age slot of S and R replicates is always 0, and a
+    // transition from S leaves it at 0. The first group's ages are issued
+    // before the neighbour gather so that the two overlap.
+    bool ageful = valid && (has_byte(xs[0], (uint32_t)kE) || has_byte(xs[0], (uint32_t)kI));
+    AgeVec8<AgeT> ag;
+    if (ageful)
+        ag.load(Abase);
+    else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            ag.v[q] = 0.0f;
+    }
     uint64_t cnt[NB];
 #pragma unroll
     for (int b = 0; b < NB; ++b)
         cnt[b] = 0ull;
     if (anyS) {
-        const int64_t off = __ldg(g.sell_off + slice);
-        const int w = (int)((__ldg(g.sell_off + slice + 1) - off) >> 5);
+        const int w = (int)((off_end - off) >> 5);
         const int32_t* __restrict__ p = g.sell_col + off + lane;
         for (int t0 = 0; t0 < w; t0 += B) {
             int32_t jj[B];
@@ -211,14 +231,11 @@ __device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slic
             }
         }
     }
-    AgeT* __restrict__ Abase = static_cast<AgeT*>(g.A) + (int64_t)i * RP;
-    uint8_t* Xb = g.X + (int64_t)i * RP;
     uint32_t newmask = 0;
     // Philox cache: counter word 2 and key of the last draw
     uint4 ph = make_uint4(0u, 0u, 0u, 0u);
     uint32_t ph_k0 = 0u, ph_k1 = 0u, ph_c2 = 0xffffffffu;
     bool ph_ok = false;
-    const uint32_t orig = (valid && g.perm) ? (uint32_t)__ldg(g.perm + i) : (uint32_t)i;
     // groups are taken from xs[0] / cnt[0], the arrays shifted down after each
     // one (static indices keep them in registers)
 #pragma unroll 1
@@ -232,24 +249,65 @@ __device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slic
             xs[t] = xs[t + 1];
             cnt[t] = cnt[t + 1];
         }
-        const bool ageful = valid && (has_byte(xv, (uint32_t)kE) || has_byte(xv, (uint32_t)kI));
-        AgeVec8<AgeT> ag;
-        if (ageful)
-            ag.load(Abase + b * 8);
-        uint64_t xnew = xv;
-        bool age_dirty = false;
-        uint32_t fS = 0, fE = 0, fI = 0;     // bit q: replicate b*8+q fired from S / E / I
+        if (b > 0) {
+            ageful = valid && (has_byte(xv, (uint32_t)kE) || has_byte(xv, (uint32_t)kI));
+            if (ageful)
+                ag.load(Abase + b * 8);
+            else {
 #pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    ag.v[q] = 0.0f;
+            }
+        }
+        // probabilities of the 8 replicates: table loads are issued four at a
+        // time, then resolved (a miss falls back to direct evaluation)
+        float pv[8];
+#pragma unroll
+        for (int h = 0; h < 8; h += 4) {
+            float sp[8];                    // entries h..h+3 used
+            float2 et[8];
+#pragma unroll
+            for (int q = h; q < h + 4; ++q) {
+                const int x = (int)((xv >> (8 * q)) & 0xffu);
+                const uint32_t c = (uint32_t)((cb >> (8 * q)) & 0xffu);
+                const uint4 h0 = __ldg(reinterpret_cast<const uint4*>(scen + b * 8 + q));
+                const float inv_dt = __uint_as_float(__ldg(reinterpret_cast<const uint32_t*>(scen + b * 8 + q) + 9));
+                const float* ps = reinterpret_cast<const float*>(((uint64_t)h0.w << 32) | h0.z);
+                const float2* pt = reinterpret_cast<const float2*>(((uint64_t)h0.y << 32) | h0.x);
+                const int n = __float2int_rn(__fmul_rn(ag.v[q], inv_dt));
+                sp[q] = (x == kS && c != 0u) ? __ldg(ps + c) : 0.0f;      // c < 256 = kPSTableN
+                et[q] = ((x == kE || x == kI) && (unsigned)n < (unsigned)kPTableN)
+                            ? __ldg(pt + (x == kI ? kPTableN : 0) + n)
+                            : make_float2(-1.0f, 0.0f);
+            }
+#pragma unroll
+            for (int q = h; q < h + 4; ++q) {
+                const int x = (int)((xv >> (8 * q)) & 0xffu);
+                if (x == kE || x == kI)
+                    pv[q] = (et[q].x == ag.v[q]) ? et[q].y : pack_p_direct(scen[b * 8 + q].M, x, ag.v[q]);
+                else
+                    pv[q] = sp[q];
+            }
+        }
+        uint64_t xr = xv, xnew = 0;
+        uint32_t fS = 0, fE = 0, fI = 0;     // bit q: replicate b*8+q fired from S / E / I
+        // replicate q of the group is taken from the low byte of xr, pv[0] and
+        // ag.v[0]; its results are shifted in at the top (one copy of the
+        // replicate body keeps the register count down)
+#pragma unroll 1
         for (int q = 0; q < 8; ++q) {
             const int r = b * 8 + q;
-            const int x = (int)((xv >> (8 * q)) & 0xffu);
-            const float age = ageful ? ag.v[q] : 0.0f;
-            const uint32_t c = (uint32_t)((cb >> (8 * q)) & 0xffu);
-            const PackScen& S = g.scen[r];
-            const float pr = (x == kR) ? 0.0f : pack_p(S, x, age, c);
+            const int x = (int)(xr & 0xffu);
+            xr >>= 8;
+            const float age = ag.v[0];
+            const float pr = pv[0];
+#pragma unroll
+            for (int t = 0; t < 7; ++t)
+                pv[t] = pv[t + 1];
             bool fired = false;
+            const uint4 h1 = __ldg(reinterpret_cast<const uint4*>(scen + r) + 1);   // key0, key1, rep, dt
             if (pr > 0.0f) {
-                const uint32_t k0 = S.M.key0, k1 = S.M.key1, rep = S.M.rep;
+                const uint32_t k0 = h1.x, k1 = h1.y, rep = h1.z;
                 if (!ph_ok || k0 != ph_k0 || k1 != ph_k1 || (rep >> 2) != ph_c2) {
                     ph = philox4x32_10(make_uint4(orig, (uint32_t)k, rep >> 2, 0u), k0, k1);
                     ph_k0 = k0;
@@ -262,35 +320,28 @@ __device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slic
                 fired = (float)(word >> 8) * 5.9604644775390625e-08f < pr;
             }
             int xn = x;
-            float an = 0.0f;
+            float an = age;
             if (fired) {
-                xn = (x == kS) ? (g.model == kSEIR ? kE : kI) : (x + 1);
+                xn = (x == kS) ? (model == kSEIR ? kE : kI) : (x + 1);
                 an = 0.0f;
                 fS |= (uint32_t)(x == kS) << q;
                 fE |= (uint32_t)(x == kE) << q;
                 fI |= (uint32_t)(x == kI) << q;
             } else if (x == kE || x == kI) {
-                an = __fadd_rn(age, S.M.dt);
+                an = __fadd_rn(age, __uint_as_float(h1.w));
             }
-            if (fired || x == kE || x == kI) {
-                ag.v[q] = an;
-                age_dirty = true;
-            }
-            xnew = (xnew & ~(0xffull << (8 * q))) | ((uint64_t)xn << (8 * q));
+#pragma unroll
+            for (int t = 0; t < 7; ++t)
+                ag.v[t] = ag.v[t + 1];
+            ag.v[7] = an;
+            xnew = (xnew >> 8) | ((uint64_t)xn << 56);
             newmask |= (uint32_t)(xn == kI) << r;
         }
         if (valid) {
             if (xnew != xv)
                 reinterpret_cast<uint64_t*>(Xb)[b] = xnew;
-            if (age_dirty) {
-                if (!ageful) {
-#pragma unroll
-                    for (int q = 0; q < 8; ++q)   // only replicates that fired from S hold a non-zero age slot
-                        if (!((fS >> q) & 1u))
-                            ag.v[q] = 0.0f;
-                }
+            if (ageful)
                 ag.store(Abase + b * 8);
-            }
         }
         // per-replicate transitions of this group, summed over the warp
         if (!__any_sync(kFullP, (fS | fE | fI) != 0u))
@@ -398,7 +449,7 @@ __device__ __forceinline__ void pack_integrate(const PackSeg& g, int64_t k)
 }  // namespace
 
 template <typename AgeT>
-__global__ void __launch_bounds__(256) pack_step_kernel(const __grid_constant__ PackArgs a)
+__global__ void __launch_bounds__(kPackThreads) pack_step_kernel(const __grid_constant__ PackArgs a)
 {
     // byte r of lut[m] is bit r of m: spreads an 8-replicate mask into byte counters
     __shared__ uint64_t lut[256];
@@ -497,7 +548,7 @@ cudaError_t launch_pack_advance(DevCtl* ctl, int K, cudaStream_t s)
 template <typename AgeT>
 static cudaError_t launch_pack_t(const PackArgs& a, int grid, cudaStream_t s)
 {
-    pack_step_kernel<AgeT><<<grid, 256, 0, s>>>(a);
+    pack_step_kernel<AgeT><<<grid, kPackThreads, 0, s>>>(a);
     g_launch_count += 1;
     return cudaGetLastError();
 }
@@ -530,7 +581,7 @@ cudaError_t launch_pack_init(uint8_t* X, int n, int R_pad, int R, const int32_t*
 int pack_grid(int num_sms)
 {
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pack_step_kernel<float>, 256, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pack_step_kernel<float>, kPackThreads, 0) != cudaSuccess ||
         occ < 1)
         occ = 4;
     return num_sms * occ;

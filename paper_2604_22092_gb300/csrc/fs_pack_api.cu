@@ -238,6 +238,12 @@ fs_status fs_ens_create(fs_graph* g, const fs_sim_params* params, int32_t n_real
         sc.M = fsapi::to_model(params[r]);
         sc.ptab = e->d_ptab + (size_t)r * 2 * fs::kPTableN;
         sc.ps = e->d_ps + (size_t)r * fs::kPSTableN;
+        sc.key0 = sc.M.key0;
+        sc.key1 = sc.M.key1;
+        sc.rep = sc.M.rep;
+        sc.dt = sc.M.dt;
+        sc.beta = sc.M.beta;
+        sc.inv_dt = sc.M.inv_dt;
         C_TRY(fs::launch_build_ptables(sc.M, e->age_dtype, const_cast<float2*>(sc.ptab), const_cast<float*>(sc.ps),
                                        cs));
         scen[r] = sc;
