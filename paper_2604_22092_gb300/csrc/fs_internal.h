@@ -159,11 +159,13 @@ struct PackSeg {            // one row of the segment table
     uint32_t* out;          // [(steps + 1)][R_pad][4] counts after each step, or null
 };
 
+// The segment table is ordered by replicate width (R_pad 8, 16, 32); each
+// width is stepped by its own kernel instance, whose register budget suits it.
 struct PackArgs {
     const PackSeg* seg;       // segment table
     const int64_t* thr_pre;   // [n_seg + 1] exclusive prefix of SELL work items
     const int64_t* hub_pre;   // [n_seg + 1] exclusive prefix of hub rows
-    const int32_t* n_seg;     // number of table rows (device, updated between launches)
+    const int32_t* cls;       // [4] rows [cls[c], cls[c+1]) have R_pad = 8 << c (device, updated between launches)
     DevCtl* ctl;              // global step counter and error word
     int32_t j;                // step offset within the launch sequence
 };

@@ -34,10 +34,11 @@ cudaError_t launch_eval_uniforms(uint32_t key0, uint32_t key1, uint32_t rep, uin
                                  float* u, int64_t n, cudaStream_t s);
 
 // fs_pack.cu
-cudaError_t launch_pack_step(const PackArgs& a, int age_dtype, int grid, cudaStream_t s);
+// one step of the segments of replicate-width class cls (R_pad = 8 << cls)
+cudaError_t launch_pack_step(const PackArgs& a, int cls, int age_dtype, int grid, cudaStream_t s);
 cudaError_t launch_pack_init(uint8_t* X, int n, int R_pad, int R, const int32_t* idx, int64_t n_idx,
                              const int32_t* inv, int state, void* mask, cudaStream_t s);
-int pack_grid(int num_sms);   // persistent grid of the packed step kernel
+int pack_grid(int num_sms, int cls);   // persistent grid of the packed step kernel of class cls
 cudaError_t launch_pack_advance(DevCtl* ctl, int K, cudaStream_t s);   // global step += K
 
 // fs_ingest.cu

@@ -163,7 +163,8 @@ __device__ __forceinline__ bool has_byte(uint64_t v, uint32_t b)
 // of 8 with vector loads and stores of their states and ages; one Philox
 // call serves the replicates that share a key and a counter (rep / 4).
 template <typename AgeT, int RP>
-__device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slice, const uint64_t* __restrict__ lut)
+__device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slice, const uint64_t* __restrict__ lut,
+                                           float* __restrict__ spv)
 {
     using MT = typename MaskOf<RP>::T;
     constexpr int NB = RP / 8;
@@ -260,8 +261,9 @@ __device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slic
             }
         }
         // probabilities of the 8 replicates: table loads are issued four at a
-        // time, then resolved (a miss falls back to direct evaluation)
-        float pv[8];
+        // time, then resolved (a miss falls back to direct evaluation); they
+        // go to this lane's column of spv, and bit q of act marks p > 0
+        uint32_t act = 0;
 #pragma unroll
         for (int h = 0; h < 8; h += 4) {
             float sp[8];                    // entries h..h+3 used
@@ -283,59 +285,53 @@ __device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slic
 #pragma unroll
             for (int q = h; q < h + 4; ++q) {
                 const int x = (int)((xv >> (8 * q)) & 0xffu);
+                float pq = sp[q];
                 if (x == kE || x == kI)
-                    pv[q] = (et[q].x == ag.v[q]) ? et[q].y : pack_p_direct(scen[b * 8 + q].M, x, ag.v[q]);
-                else
-                    pv[q] = sp[q];
+                    pq = (et[q].x == ag.v[q]) ? et[q].y : pack_p_direct(scen[b * 8 + q].M, x, ag.v[q]);
+                spv[q * 32 + lane] = pq;
+                act |= (uint32_t)(pq > 0.0f) << q;
             }
         }
-        uint64_t xr = xv, xnew = 0;
-        uint32_t fS = 0, fE = 0, fI = 0;     // bit q: replicate b*8+q fired from S / E / I
-        // replicate q of the group is taken from the low byte of xr, pv[0] and
-        // ag.v[0]; its results are shifted in at the top (one copy of the
-        // replicate body keeps the register count down)
-#pragma unroll 1
+        // E and I replicates age by their dt (one that fires restarts at 0 below)
+#pragma unroll
         for (int q = 0; q < 8; ++q) {
-            const int r = b * 8 + q;
-            const int x = (int)(xr & 0xffu);
-            xr >>= 8;
-            const float age = ag.v[0];
-            const float pr = pv[0];
-#pragma unroll
-            for (int t = 0; t < 7; ++t)
-                pv[t] = pv[t + 1];
-            bool fired = false;
-            const uint4 h1 = __ldg(reinterpret_cast<const uint4*>(scen + r) + 1);   // key0, key1, rep, dt
-            if (pr > 0.0f) {
-                const uint32_t k0 = h1.x, k1 = h1.y, rep = h1.z;
-                if (!ph_ok || k0 != ph_k0 || k1 != ph_k1 || (rep >> 2) != ph_c2) {
-                    ph = philox4x32_10(make_uint4(orig, (uint32_t)k, rep >> 2, 0u), k0, k1);
-                    ph_k0 = k0;
-                    ph_k1 = k1;
-                    ph_c2 = rep >> 2;
-                    ph_ok = true;
-                }
-                const uint32_t sel = rep & 3u;
-                const uint32_t word = sel == 0 ? ph.x : sel == 1 ? ph.y : sel == 2 ? ph.z : ph.w;
-                fired = (float)(word >> 8) * 5.9604644775390625e-08f < pr;
+            const int x = (int)((xv >> (8 * q)) & 0xffu);
+            if (x == kE || x == kI)
+                ag.v[q] = __fadd_rn(ag.v[q], __uint_as_float(__ldg(reinterpret_cast<const uint32_t*>(scen + b * 8 + q) + 7)));
+        }
+        // uniforms only for the replicates with p > 0; bit q of F: fired
+        uint32_t F = 0;
+        for (uint32_t todo = act; todo != 0u; todo &= todo - 1u) {
+            const int q = __ffs(todo) - 1;
+            const uint4 h1 = __ldg(reinterpret_cast<const uint4*>(scen + b * 8 + q) + 1);   // key0, key1, rep, dt
+            const uint32_t k0 = h1.x, k1 = h1.y, rep = h1.z;
+            if (!ph_ok || k0 != ph_k0 || k1 != ph_k1 || (rep >> 2) != ph_c2) {
+                ph = philox4x32_10(make_uint4(orig, (uint32_t)k, rep >> 2, 0u), k0, k1);
+                ph_k0 = k0;
+                ph_k1 = k1;
+                ph_c2 = rep >> 2;
+                ph_ok = true;
             }
-            int xn = x;
-            float an = age;
+            const uint32_t sel = rep & 3u;
+            const uint32_t word = sel == 0 ? ph.x : sel == 1 ? ph.y : sel == 2 ? ph.z : ph.w;
+            F |= (uint32_t)((float)(word >> 8) * 5.9604644775390625e-08f < spv[q * 32 + lane]) << q;
+        }
+        // transitions: S -> E (SEIR) or I (SIR), E -> I, I -> R
+        uint64_t xnew = xv;
+        uint32_t fS = 0, fE = 0, fI = 0;     // bit q: replicate b*8+q fired from S / E / I
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int x = (int)((xv >> (8 * q)) & 0xffu);
+            const bool fired = (F >> q) & 1u;
+            const int xn = !fired ? x : (x == kS) ? (model == kSEIR ? kE : kI) : (x + 1);
             if (fired) {
-                xn = (x == kS) ? (model == kSEIR ? kE : kI) : (x + 1);
-                an = 0.0f;
-                fS |= (uint32_t)(x == kS) << q;
-                fE |= (uint32_t)(x == kE) << q;
-                fI |= (uint32_t)(x == kI) << q;
-            } else if (x == kE || x == kI) {
-                an = __fadd_rn(age, __uint_as_float(h1.w));
+                ag.v[q] = 0.0f;
+                xnew = (xnew & ~(0xffull << (8 * q))) | ((uint64_t)xn << (8 * q));
             }
-#pragma unroll
-            for (int t = 0; t < 7; ++t)
-                ag.v[t] = ag.v[t + 1];
-            ag.v[7] = an;
-            xnew = (xnew >> 8) | ((uint64_t)xn << 56);
-            newmask |= (uint32_t)(xn == kI) << r;
+            fS |= (uint32_t)(fired && x == kS) << q;
+            fE |= (uint32_t)(fired && x == kE) << q;
+            fI |= (uint32_t)(fired && x == kI) << q;
+            newmask |= (uint32_t)(xn == kI) << (b * 8 + q);
         }
         if (valid) {
             if (xnew != xv)
@@ -448,11 +444,18 @@ __device__ __forceinline__ void pack_integrate(const PackSeg& g, int64_t k)
 
 }  // namespace
 
-template <typename AgeT>
-__global__ void __launch_bounds__(kPackThreads) pack_step_kernel(const __grid_constant__ PackArgs a)
+// Minimum resident blocks per SM of the packed step, by replicate width: the
+// register budget that measured fastest for each (80 and 96 registers).
+template <int RP> struct PackOcc { static constexpr int kMinBlocks = RP == 8 ? 6 : 5; };
+
+template <typename AgeT, int RP>
+__global__ void __launch_bounds__(kPackThreads, PackOcc<RP>::kMinBlocks) pack_step_kernel(const __grid_constant__ PackArgs a)
 {
     // byte r of lut[m] is bit r of m: spreads an 8-replicate mask into byte counters
     __shared__ uint64_t lut[256];
+    // per warp: the probabilities of one 8-replicate group, [q][lane]
+    __shared__ float s_pv[kPackThreads / 32][8 * 32];
+    float* spv = s_pv[threadIdx.x >> 5];
     for (int m = threadIdx.x; m < 256; m += blockDim.x) {
         uint64_t v = 0;
         for (int r = 0; r < 8; ++r)
@@ -460,48 +463,38 @@ __global__ void __launch_bounds__(kPackThreads) pack_step_kernel(const __grid_co
         lut[m] = v;
     }
     __syncthreads();
+    constexpr int c = RP == 8 ? 0 : RP == 16 ? 1 : 2;
     const int64_t G = a.ctl->step + a.j;
-    const int nseg = *a.n_seg;
+    const int s0 = a.cls[c], s1 = a.cls[c + 1];
     const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     // counts of the previous step, one warp per segment
-    for (int64_t s = gw; s < nseg; s += W) {
+    for (int64_t s = s0 + gw; s < s1; s += W) {
         const PackSeg& g = a.seg[s];
         pack_integrate(g, G - g.join);
     }
     // hub rows (long rows start first), then SELL items
-    const int64_t n_hub = __ldg(a.hub_pre + nseg), n_thr = __ldg(a.thr_pre + nseg);
-    int s = 0;
-    for (int64_t it = gw; it < n_hub; it += W) {
+    const int64_t hub0 = __ldg(a.hub_pre + s0), n_hub = __ldg(a.hub_pre + s1);
+    const int64_t thr0 = __ldg(a.thr_pre + s0), n_thr = __ldg(a.thr_pre + s1);
+    int s = s0;
+    for (int64_t it = hub0 + gw; it < n_hub; it += W) {
         while (__ldg(a.hub_pre + s + 1) <= it)
             ++s;
         const PackSeg& g = a.seg[s];
         const int64_t k = G - g.join;
         if (k < g.kmin || k >= g.kend)
             continue;
-        const int row = (int)(it - __ldg(a.hub_pre + s));
-        if (g.R_pad == 8)
-            pack_hub_row<AgeT, 8>(g, k, row);
-        else if (g.R_pad == 16)
-            pack_hub_row<AgeT, 16>(g, k, row);
-        else
-            pack_hub_row<AgeT, 32>(g, k, row);
+        pack_hub_row<AgeT, RP>(g, k, (int)(it - __ldg(a.hub_pre + s)));
     }
-    s = 0;
-    for (int64_t it = gw; it < n_thr; it += W) {
+    s = s0;
+    for (int64_t it = thr0 + gw; it < n_thr; it += W) {
         while (__ldg(a.thr_pre + s + 1) <= it)
             ++s;
         const PackSeg& g = a.seg[s];
         const int64_t k = G - g.join;
         if (k < g.kmin || k >= g.kend)
             continue;
-        const int slice = (int)(it - __ldg(a.thr_pre + s));   // one item per 32-node slice
-        if (g.R_pad == 8)
-            pack_slice<AgeT, 8>(g, k, slice, lut);
-        else if (g.R_pad == 16)
-            pack_slice<AgeT, 16>(g, k, slice, lut);
-        else
-            pack_slice<AgeT, 32>(g, k, slice, lut);
+        pack_slice<AgeT, RP>(g, k, (int)(it - __ldg(a.thr_pre + s)), lut, spv);   // one item per 32-node slice
     }
 }
 
@@ -546,19 +539,23 @@ cudaError_t launch_pack_advance(DevCtl* ctl, int K, cudaStream_t s)
 }
 
 template <typename AgeT>
-static cudaError_t launch_pack_t(const PackArgs& a, int grid, cudaStream_t s)
+static cudaError_t launch_pack_t(const PackArgs& a, int cls, int grid, cudaStream_t s)
 {
-    pack_step_kernel<AgeT><<<grid, kPackThreads, 0, s>>>(a);
+    switch (cls) {
+    case 0: pack_step_kernel<AgeT, 8><<<grid, kPackThreads, 0, s>>>(a); break;
+    case 1: pack_step_kernel<AgeT, 16><<<grid, kPackThreads, 0, s>>>(a); break;
+    default: pack_step_kernel<AgeT, 32><<<grid, kPackThreads, 0, s>>>(a); break;
+    }
     g_launch_count += 1;
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack_step(const PackArgs& a, int age_dtype, int grid, cudaStream_t s)
+cudaError_t launch_pack_step(const PackArgs& a, int cls, int age_dtype, int grid, cudaStream_t s)
 {
     switch (age_dtype) {
-    case kAgeF16: return launch_pack_t<__half>(a, grid, s);
-    case kAgeBF16: return launch_pack_t<__nv_bfloat16>(a, grid, s);
-    default: return launch_pack_t<float>(a, grid, s);
+    case kAgeF16: return launch_pack_t<__half>(a, cls, grid, s);
+    case kAgeBF16: return launch_pack_t<__nv_bfloat16>(a, cls, grid, s);
+    default: return launch_pack_t<float>(a, cls, grid, s);
     }
 }
 
@@ -578,11 +575,13 @@ cudaError_t launch_pack_init(uint8_t* X, int n, int R_pad, int R, const int32_t*
     return cudaGetLastError();
 }
 
-int pack_grid(int num_sms)
+int pack_grid(int num_sms, int cls)
 {
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pack_step_kernel<float>, kPackThreads, 0) != cudaSuccess ||
-        occ < 1)
+    cudaError_t e = cls == 0   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pack_step_kernel<float, 8>, kPackThreads, 0)
+                    : cls == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pack_step_kernel<float, 16>, kPackThreads, 0)
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pack_step_kernel<float, 32>, kPackThreads, 0);
+    if (e != cudaSuccess || occ < 1)
         occ = 4;
     return num_sms * occ;
 }

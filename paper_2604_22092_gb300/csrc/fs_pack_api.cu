@@ -58,18 +58,20 @@ struct fs_batch {
     fs::PackSeg* d_seg = nullptr;
     int64_t* d_thr = nullptr;
     int64_t* d_hub = nullptr;
-    int32_t* d_nseg = nullptr;
+    int32_t* d_cls = nullptr;           // [4] class boundaries of the table (see PackArgs)
     fs::PackSeg* h_seg = nullptr;       // pinned staging of the table
     int64_t* h_thr = nullptr;
     int64_t* h_hub = nullptr;
-    int32_t* h_nseg = nullptr;
+    int32_t* h_cls = nullptr;
     fs::DevCtl* d_ctl = nullptr;
     int64_t G = 0;                      // global step of the next launch
     std::vector<Member> members;
     bool dirty = true;
     cudaGraphExec_t gexec = nullptr;
     int gK = 0;
-    int grid = 0;
+    int g_classes = 0;                  // classes launched by the captured graph (bit c)
+    int classes = 0;                    // classes present in the table (bit c: R_pad = 8 << c)
+    int grid[3] = {0, 0, 0};
     bool failed = false;
 };
 
@@ -103,12 +105,12 @@ void free_batch(fs_batch* b)
     cudaFree(b->d_seg);
     cudaFree(b->d_thr);
     cudaFree(b->d_hub);
-    cudaFree(b->d_nseg);
+    cudaFree(b->d_cls);
     cudaFree(b->d_ctl);
     cudaFreeHost(b->h_seg);
     cudaFreeHost(b->h_thr);
     cudaFreeHost(b->h_hub);
-    cudaFreeHost(b->h_nseg);
+    cudaFreeHost(b->h_cls);
     if (b->own_stream && b->stream)
         cudaStreamDestroy(b->stream);
     delete b;
@@ -355,14 +357,14 @@ fs_status fs_batch_create(int32_t age_dtype, int32_t max_members, void* stream, 
     if (e == cudaSuccess) e = dev_alloc(&b->d_seg, (size_t)max_members, nullptr);
     if (e == cudaSuccess) e = dev_alloc(&b->d_thr, (size_t)max_members + 1, nullptr);
     if (e == cudaSuccess) e = dev_alloc(&b->d_hub, (size_t)max_members + 1, nullptr);
-    if (e == cudaSuccess) e = dev_alloc(&b->d_nseg, 1, nullptr);
+    if (e == cudaSuccess) e = dev_alloc(&b->d_cls, 4, nullptr);
     if (e == cudaSuccess) e = dev_alloc(&b->d_ctl, 1, nullptr);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_seg, sizeof(fs::PackSeg) * max_members);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_thr, sizeof(int64_t) * (max_members + 1));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_hub, sizeof(int64_t) * (max_members + 1));
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_nseg, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_cls, sizeof(int32_t) * 4);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ctl, 0, sizeof(fs::DevCtl), b->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_nseg, 0, sizeof(int32_t), b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_cls, 0, sizeof(int32_t) * 4, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_thr, 0, sizeof(int64_t), b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_hub, 0, sizeof(int64_t), b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -371,7 +373,8 @@ fs_status fs_batch_create(int32_t age_dtype, int32_t max_members, void* stream, 
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    b->grid = fs::pack_grid(sms);
+    for (int c = 0; c < 3; ++c)
+        b->grid[c] = fs::pack_grid(sms, c);
     *out = b;
     return FS_OK;
 }
@@ -403,25 +406,38 @@ fs_status fs_batch_add(fs_batch* b, fs_ens* e, int64_t steps, uint32_t* counts_o
     return FS_OK;
 }
 
+static int width_class(int R_pad)
+{
+    return R_pad == 8 ? 0 : R_pad == 16 ? 1 : 2;
+}
+
 static fs_status upload_table(fs_batch* b)
 {
     E_CUDA(b, cudaStreamSynchronize(b->stream));     // the staging buffers are free again
-    const int ns = (int)b->members.size();
     b->h_thr[0] = 0;
     b->h_hub[0] = 0;
-    for (int q = 0; q < ns; ++q) {
-        const Member& m = b->members[q];
-        b->h_seg[q] = segment_of(m);
-        const fs_graph* g = m.e->g;
-        b->h_thr[q + 1] = b->h_thr[q] + (int64_t)g->n_slices;
-        b->h_hub[q + 1] = b->h_hub[q] + g->n_m;
+    b->classes = 0;
+    int q = 0;
+    for (int c = 0; c < 3; ++c) {                     // rows ordered by replicate width
+        b->h_cls[c] = q;
+        for (const Member& m : b->members) {
+            if (width_class(m.e->R_pad) != c)
+                continue;
+            b->h_seg[q] = segment_of(m);
+            const fs_graph* g = m.e->g;
+            b->h_thr[q + 1] = b->h_thr[q] + (int64_t)g->n_slices;
+            b->h_hub[q + 1] = b->h_hub[q] + g->n_m;
+            b->classes |= 1 << c;
+            ++q;
+        }
     }
-    *b->h_nseg = ns;
+    b->h_cls[3] = q;
+    const int ns = q;
     if (ns > 0)
         E_CUDA(b, cudaMemcpyAsync(b->d_seg, b->h_seg, sizeof(fs::PackSeg) * ns, cudaMemcpyHostToDevice, b->stream));
     E_CUDA(b, cudaMemcpyAsync(b->d_thr, b->h_thr, sizeof(int64_t) * (ns + 1), cudaMemcpyHostToDevice, b->stream));
     E_CUDA(b, cudaMemcpyAsync(b->d_hub, b->h_hub, sizeof(int64_t) * (ns + 1), cudaMemcpyHostToDevice, b->stream));
-    E_CUDA(b, cudaMemcpyAsync(b->d_nseg, b->h_nseg, sizeof(int32_t), cudaMemcpyHostToDevice, b->stream));
+    E_CUDA(b, cudaMemcpyAsync(b->d_cls, b->h_cls, sizeof(int32_t) * 4, cudaMemcpyHostToDevice, b->stream));
     b->dirty = false;
     return FS_OK;
 }
@@ -432,10 +448,20 @@ static fs::PackArgs pack_args(const fs_batch* b, int j)
     a.seg = b->d_seg;
     a.thr_pre = b->d_thr;
     a.hub_pre = b->d_hub;
-    a.n_seg = b->d_nseg;
+    a.cls = b->d_cls;
     a.ctl = b->d_ctl;
     a.j = j;
     return a;
+}
+
+// one step of every width class present in the table
+static cudaError_t launch_classes(const fs_batch* b, int j, int classes)
+{
+    cudaError_t e = cudaSuccess;
+    for (int c = 0; c < 3 && e == cudaSuccess; ++c)
+        if (classes & (1 << c))
+            e = fs::launch_pack_step(pack_args(b, j), c, b->age_dtype, b->grid[c], b->stream);
+    return e;
 }
 
 fs_status fs_batch_run(fs_batch* b, int64_t launches, int32_t graph_steps)
@@ -454,7 +480,9 @@ fs_status fs_batch_run(fs_batch* b, int64_t launches, int32_t graph_steps)
     }
     const int64_t full = launches / K;
     const int rem = (int)(launches % K);
-    if (full > 0 && !(b->gexec && b->gK == K)) {
+    const int classes = b->classes;
+    const int n_cls = __builtin_popcount((unsigned)classes);
+    if (full > 0 && !(b->gexec && b->gK == K && b->g_classes == classes)) {
         if (b->gexec) {
             cudaGraphExecDestroy(b->gexec);
             b->gexec = nullptr;
@@ -463,7 +491,7 @@ fs_status fs_batch_run(fs_batch* b, int64_t launches, int32_t graph_steps)
         E_CUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaSuccess;
         for (int j = 0; j < K && e == cudaSuccess; ++j)
-            e = fs::launch_pack_step(pack_args(b, j), b->age_dtype, b->grid, b->stream);
+            e = launch_classes(b, j, classes);
         if (e == cudaSuccess)
             e = fs::launch_pack_advance(b->d_ctl, K, b->stream);
         cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
@@ -473,13 +501,14 @@ fs_status fs_batch_run(fs_batch* b, int64_t launches, int32_t graph_steps)
         cudaGraphDestroy(graph);
         E_CUDA(b, e);
         b->gK = K;
+        b->g_classes = classes;
     }
     for (int64_t r = 0; r < full; ++r)
         E_CUDA(b, cudaGraphLaunch(b->gexec, b->stream));
-    fs::g_launch_count += (unsigned long long)full * (K + 1);
+    fs::g_launch_count += (unsigned long long)full * ((unsigned long long)K * n_cls + 1);
     if (rem > 0) {
         for (int j = 0; j < rem; ++j)
-            E_CUDA(b, fs::launch_pack_step(pack_args(b, j), b->age_dtype, b->grid, b->stream));
+            E_CUDA(b, launch_classes(b, j, classes));
         E_CUDA(b, fs::launch_pack_advance(b->d_ctl, rem, b->stream));
     }
     b->G += launches;

@@ -88,7 +88,7 @@ def test_batch_members_join_leave_and_resume(cuda):
               W.erdos_renyi(9_000, 8, seed=13)]
     ghs = [fs.fs_graph_create(g.n, g.row_ptr, g.col_ind) for g in graphs]
     idxs = [W.index_nodes(g.n, 20, seed=21 + q) for q, g in enumerate(graphs)]
-    Rs = [8, 3, 20]
+    Rs = [12, 3, 20]          # all three replicate widths (16, 8, 32 lanes)
     params = [scenarios(R, seed0=500 + 100 * q) for q, R in enumerate(Rs)]
     ens = [fs.fs_ens_create(ghs[q], params[q], idxs[q]) for q in range(3)]
     steps = [150, 90, 120]
