@@ -272,10 +272,15 @@ fs_status fs_batch_destroy(fs_batch* b);
  * one resident graph (realisation (s, r) uses scenarios[s] with replicate
  * index scenarios[s].replicate + r), run for `steps` steps. Requests are
  * admitted first come, first served while their device memory fits the
- * budget; admitted requests join the running batch at the next quantum of
- * `quantum` launches, so work of requests that arrive while others run
- * overlaps on the device; finished requests leave the batch and free their
- * memory. Results are identical to running each realisation alone.
+ * budget and the work in flight stays under a cap; admitted requests join
+ * the running batch at the next quantum of `quantum` launches, so work of
+ * requests that arrive while others run overlaps on the device; finished
+ * requests leave the batch and free their memory. Every running request
+ * advances one step per launch, so a launch costs the sum of their sizes:
+ * the cap keeps enough work in flight to fill the GPU while letting the
+ * requests at the head of the queue finish early instead of all sharing the
+ * device until the end. Results are identical to running each realisation
+ * alone.
  * Graphs must outlive the requests that use them.
  * ------------------------------------------------------------------------- */
 typedef struct {
@@ -284,6 +289,9 @@ typedef struct {
     int32_t quantum;           /* launches between admissions and retirements; 0 = 10      */
     int32_t age_dtype;         /* age storage of every request                               */
     int32_t reserved_;         /* must be 0                                                  */
+    int64_t max_inflight;      /* cap on node x realisation updates per launch summed over
+                                  running requests; the queue head waits while admitting it
+                                  would pass the cap, unless nothing runs. 0 = 2^25, -1 = none */
 } fs_server_cfg;
 
 typedef struct {

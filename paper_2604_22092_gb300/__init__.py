@@ -283,8 +283,9 @@ def fs_batch_destroy(b: int) -> None:
 
 # --------------------------------------------------------------- serving
 def fs_server_create(hbm_budget_bytes: int = 0, max_members: int = 0, quantum: int = 0,
-                     age_dtype: int = FS_AGE_F32) -> int:
-    cfg = _abi.fs_server_cfg(int(hbm_budget_bytes), int(max_members), int(quantum), int(age_dtype), 0)
+                     age_dtype: int = FS_AGE_F32, max_inflight: int = 0) -> int:
+    cfg = _abi.fs_server_cfg(int(hbm_budget_bytes), int(max_members), int(quantum), int(age_dtype), 0,
+                             int(max_inflight))
     h = ctypes.c_void_p()
     check(load().fs_server_create(ctypes.byref(cfg), ctypes.byref(h)), "fs_server_create")
     return h.value

@@ -1,10 +1,11 @@
 // fs_server.cpp -- continuous batching of forecast ensembles (include/fs.h,
 // "Serving"). A host thread owns one batch (the device segment table) and
 // runs it in quanta of K launches; between quanta it admits queued requests
-// first come, first served while their device memory fits the budget (each
-// request becomes ensembles of at most 32 realisations that join the running
-// batch), and retires requests whose last step has been integrated. Built on
-// the public ensemble and batch entry points; no numerics of its own.
+// first come, first served while their device memory fits the budget and the
+// updates per launch of the running requests stay under the in-flight cap
+// (each request becomes ensembles of at most 32 realisations that join the
+// running batch), and retires requests whose last step has been integrated.
+// Built on the public ensemble and batch entry points; no numerics of its own.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -43,6 +44,7 @@ struct Request {
     Clock::time_point t_submit, t_done;
     bool done = false;
     fs_status status = FS_OK;
+    int64_t load() const { return n * (int64_t)params.size(); }   // node updates per launch
 };
 
 int64_t ensemble_bytes(int64_t n, int R, int age_bytes, int64_t steps)
@@ -139,18 +141,22 @@ void serve(fs_server* s)
                 break;
             while (!s->queue.empty()) {
                 Request* q = s->queue.front();
-                const int64_t members = (int64_t)s->running.size() + (int64_t)admitted.size();
                 const int64_t need_rows = ((int64_t)q->params.size() + 31) / 32;
                 if (s->used + q->bytes > s->budget)
                     break;
-                int64_t rows = 0;
-                for (Request* r : s->running)
+                int64_t rows = 0, load = 0;
+                for (Request* r : s->running) {
                     rows += (int64_t)r->ens.size();
-                for (Request* r : admitted)
+                    load += r->load();
+                }
+                for (Request* r : admitted) {
                     rows += ((int64_t)r->params.size() + 31) / 32;
+                    load += r->load();
+                }
                 if (rows + need_rows > s->cfg.max_members)
                     break;
-                (void)members;
+                if (s->cfg.max_inflight > 0 && load > 0 && load + q->load() > s->cfg.max_inflight)
+                    break;
                 s->queue.pop_front();
                 s->used += q->bytes;
                 s->st.queued -= 1;
@@ -222,8 +228,11 @@ fs_status fs_server_create(const fs_server_cfg* cfg, fs_server** out)
     if (cfg)
         c = *cfg;
     if (c.reserved_ != 0 || c.hbm_budget_bytes < 0 || c.max_members < 0 || c.quantum < 0 ||
-        c.quantum > fs::kMaxGraphSteps || c.age_dtype < FS_AGE_F32 || c.age_dtype > FS_AGE_BF16)
+        c.quantum > fs::kMaxGraphSteps || c.age_dtype < FS_AGE_F32 || c.age_dtype > FS_AGE_BF16 ||
+        c.max_inflight < -1)
         return fail(FS_EINVAL, "fs_server_create: bad configuration");
+    if (c.max_inflight == 0)
+        c.max_inflight = (int64_t)1 << 25;
     if (c.max_members == 0)
         c.max_members = 4096;
     if (c.quantum == 0)

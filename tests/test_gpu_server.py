@@ -119,3 +119,37 @@ def test_budget_queues_and_rejects(graphs):
     with pytest.raises(fs.FsError):
         fs.fs_server_submit(srv, hs[0], bad, 4, idx, 10)
     fs.fs_server_destroy(srv)
+
+
+def test_inflight_cap_admits_in_order(graphs):
+    """With a cap of 1.5 requests' worth of updates per launch, requests run
+    one at a time in submission order; one larger than the cap still runs
+    (alone), and every result equals its realisations alone."""
+    gs, hs = graphs
+    idx = W.index_nodes(gs[2].n, 12, seed=8)
+    sc = scen(2, seed=80)
+    load = gs[2].n * 2 * 8                      # n x realisations of one request
+    srv = fs.fs_server_create(quantum=4, max_inflight=int(load * 1.5))
+    ids, t_sub = [], []
+    for _ in range(3):
+        t_sub.append(time.perf_counter())
+        ids.append(fs.fs_server_submit(srv, hs[2], sc, 8, idx, 40))
+    t_sub.append(time.perf_counter())
+    big = fs.fs_server_submit(srv, hs[2], sc, 16, idx, 30)           # twice the load: over the cap
+    max_running, t0 = 0, time.time()
+    while fs.fs_server_stats_get(srv)["completed"] < 4:
+        max_running = max(max_running, fs.fs_server_stats_get(srv)["running"])
+        assert time.time() - t0 < 120
+        time.sleep(0.0005)
+    assert max_running <= 1
+    t_done = [t + fs.fs_server_poll(srv, rid)[2] for t, rid in zip(t_sub, ids + [big])]
+    assert t_done == sorted(t_done)             # first come, first served
+    c = fs.fs_server_poll(srv, big, 30, 32)[1]
+    for s in range(2):
+        for r in (0, 15):
+            np.testing.assert_array_equal(c[:, s * 16 + r, :], alone_counts(hs[2], sc[s], idx, 30, r))
+    c0 = fs.fs_server_poll(srv, ids[2], 40, 16)[1]
+    np.testing.assert_array_equal(c0[:, 9, :], alone_counts(hs[2], sc[1], idx, 40, 1))
+    with pytest.raises(fs.FsError):
+        fs.fs_server_create(max_inflight=-2)
+    fs.fs_server_destroy(srv)
