@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-served", action="store_true", help="skip the served-vs-plain block")
-    ap.add_argument("--workload", choices=["regular", "ensemble", "serving"], default="regular",
+    ap.add_argument("--workload", choices=["regular", "ensemble", "serving", "large"], default="regular",
                     help="regular: the headline line; ensemble / serving: full-size packed and served runs")
     ap.add_argument("--age", choices=["f32", "f16"], default="f32", help="age storage of ensemble/serving runs")
     ap.add_argument("--ens-graphs", type=int, default=64, help="graphs of the packed-ensemble run")
@@ -499,6 +499,94 @@ def secondary_ba(fs, torch, args, stream, flush):
             "thread_class_nodes": info["n_thread"], "merge_class_nodes": info["n_merge"]}
 
 
+def device_regular(torch, n: int, d: int, seed: int, dev):
+    """Random d-regular multigraph built on the device for N too large for the
+    host generator: configuration-model stub pairing by a seeded device
+    permutation. Node i owns stubs i*d .. i*d + d - 1, so each stub's column is
+    its partner's node and the CSR needs no sort. Self-loops and repeated edges
+    (about (d-1)/2 + (d-1)^2/4 expected in the whole graph) are kept."""
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    perm = torch.randperm(n * d, generator=gen, device=dev)
+    a, b = perm[0::2], perm[1::2]
+    col = torch.empty(n * d, dtype=torch.int32, device=dev)
+    col[a] = torch.div(b, d, rounding_mode="floor").to(torch.int32)
+    col[b] = torch.div(a, d, rounding_mode="floor").to(torch.int32)
+    del perm, a, b
+    rp = torch.arange(0, (n + 1) * d, d, dtype=torch.int64, device=dev)
+    return rp, col
+
+
+def large_bench(fs, torch, n: int, age_dtype: int, sim_steps: int, graph_steps: int, reps: int):
+    """The C1 SEIR workload on a random 10-regular graph of N = 10^7 or 10^8
+    nodes, where the step's working set is far larger than L2: ingest from the
+    device CSR + init + all steps, timed with CUDA events; the kernel-side
+    roofline uses the graph replays alone."""
+    dev = torch.device("cuda")
+    d = 10
+    rp, col = device_regular(torch, n, d, seed=0, dev=dev)
+    idx = W.index_nodes(n, 100, seed=1)
+    prm = fs.sim_params(fs.FS_SEIR, fs.law("lognormal", math.log(6.0), 0.6), 0.25, 0.1, 1,
+                        latent=fs.law("weibull", 2.0, 4.0), replicate=0, age_dtype=age_dtype)
+    opts = fs.graph_opts(device_input=True)
+    stream = torch.cuda.Stream()
+    b_age = 4 if age_dtype == fs.FS_AGE_F32 else 2
+    totals, replays, breq = [], [], []
+    counts_dev = torch.zeros((sim_steps + 1) * 4, dtype=torch.int32, device=dev)
+    for it in range(reps + 1):
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        gh = fs.fs_graph_create(n, rp, col, opts=opts, stream=stream)
+        sh = fs.fs_sim_init(gh, prm, idx, stream=stream)
+        ms = fs.fs_sim_run_timed(sh, sim_steps, graph_steps, counts_dev)
+        ev1.record(stream)
+        ev1.synchronize()
+        work = fs.fs_sim_work(sh)
+        cnt = counts_dev.view(sim_steps + 1, 4).cpu().numpy().astype(np.int64)
+        counts = fs.fs_sim_run(sh, 0)
+        gbytes = fs.fs_graph_info_get(gh)["device_bytes"]
+        fs.fs_sim_destroy(sh)
+        fs.fs_graph_destroy(gh)
+        if it == 0:
+            continue                        # warm-up: graph capture, first-touch of the pools
+        full = sim_steps // graph_steps
+        totals.append(ev0.elapsed_time(ev1))
+        replays.append(float(np.sum(ms[:full])))
+        breq.append(bytes_model(n, sim_steps, work["s_node_sum"], work["s_degree_sum"], b_age=b_age)
+                    * full * graph_steps / sim_steps)
+    assert int(counts[-1].sum()) == n
+    peak, peak_kind = measured_peak_hbm()
+    # per replay of graph_steps steps: time per step and B_req rate (S-degree sum
+    # = d x |S| on a d-regular graph)
+    phases = []
+    for r in range(sim_steps // graph_steps):
+        S = cnt[r * graph_steps:(r + 1) * graph_steps, 0]
+        b = graph_steps * n * (2 + 2 * b_age + 1 / 8) + float(S.sum()) * (4 + d * (4 + 1 / 8))
+        phases.append([r * graph_steps, round(float(ms[r]) * 1e3 / graph_steps, 1),
+                       round(b / (float(ms[r]) * 1e-3) / 1e9, 0), round(float(S.mean()) / n, 3)])
+    steps_timed = (sim_steps // graph_steps) * graph_steps
+    step_ms = float(np.mean(replays)) / steps_timed
+    per_step_bytes = float(np.mean(breq)) / steps_timed
+    dense = n * (2 + 2 * b_age + 1 / 8 + 4) + n * d * (4 + 1 / 8)
+    total_ms = float(np.mean(totals))
+    return {"workload": f"seir-regular10-n{n:.0e}-{'f32' if b_age == 4 else 'bf16'}".replace("+0", ""),
+            "n": n, "sim_steps": sim_steps, "age_storage": "f32" if b_age == 4 else "bf16",
+            "value": round(n * sim_steps / (total_ms * 1e-3) / 1e9, 3), "unit": UNIT,
+            "ms_total": round(total_ms, 2), "steps_gnups": round(n / (step_ms * 1e-3) / 1e9, 3),
+            "avg_step_us": round(step_ms * 1e3, 2),
+            "roofline": {"bound": "hbm", "achieved": round(per_step_bytes / (step_ms * 1e-3) / 1e9, 1),
+                         "peak": peak, "unit": "GB/s", "peak_source": peak_kind,
+                         "frac": round(per_step_bytes / (step_ms * 1e-3) / 1e9 / peak, 4),
+                         "frac_dense": round(dense / (step_ms * 1e-3) / 1e9 / peak, 4),
+                         "algorithmic_bytes_per_step": round(per_step_bytes),
+                         "dense_bytes_per_step": round(dense)},
+            "phases_step_us_gbs_sfrac": phases,
+            "final_counts": [int(x) for x in counts[-1]], "graph_device_bytes": int(gbytes),
+            "graph": "random 10-regular multigraph, device stub pairing (seed 0)"}
+
+
 def run_reference(args, rank, world):
     """The oracle timed on the host cores on bounded samples of the workload."""
     if rank != 0:
@@ -543,6 +631,11 @@ def run_extra(args):
     if args.workload == "ensemble":
         res = ensemble_bench(fs, torch, n_graphs=args.ens_graphs, n_lo=1e4, n_hi=2e6, steps=args.ens_steps,
                              age_dtype=age)
+    elif args.workload == "large":
+        for n, a in ((10_000_000, fs.FS_AGE_F32), (100_000_000, fs.FS_AGE_F32), (100_000_000, fs.FS_AGE_BF16)):
+            res = large_bench(fs, torch, n, a, args.sim_steps, args.graph_steps, reps=1)
+            print(json.dumps({"metric": METRIC, "impl": "flashstep", "data": "synthetic", **res}), flush=True)
+        return
     else:
         res = serving_bench(fs, torch, n_requests=200, n_pool=24, n_hi=1e6, steps=500, rep_lo=16, rep_hi=256,
                             window_s=2.0, age_dtype=age)
