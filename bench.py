@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-served", action="store_true", help="skip the served-vs-plain block")
-    ap.add_argument("--workload", choices=["regular", "ensemble", "serving", "large"], default="regular",
+    ap.add_argument("--workload", choices=["regular", "ensemble", "serving", "large", "precision"], default="regular",
                     help="regular: the headline line; ensemble / serving: full-size packed and served runs")
     ap.add_argument("--age", choices=["f32", "f16"], default="f32", help="age storage of ensemble/serving runs")
     ap.add_argument("--ens-graphs", type=int, default=64, help="graphs of the packed-ensemble run")
@@ -587,6 +587,97 @@ def large_bench(fs, torch, n: int, age_dtype: int, sim_steps: int, graph_steps: 
             "graph": "random 10-regular multigraph, device stub pairing (seed 0)"}
 
 
+def precision_runs(fs, g, idx, model, inf, lat, beta, steps, reps, index_state=None):
+    """Peak infectious fraction and attack rate of `reps` replicates under each
+    age storage (one packed batch per storage type)."""
+    n = g.n
+    gh = fs.fs_graph_create(g.n, g.row_ptr, g.col_ind)
+    peak, attack, secs = {}, {}, {}
+    for name, a in (("f32", fs.FS_AGE_F32), ("f16", fs.FS_AGE_F16), ("bf16", fs.FS_AGE_BF16)):
+        b = fs.fs_batch_create(a, (reps + 31) // 32 + 1)
+        ens, outs = [], []
+        for off in range(0, reps, 32):
+            R = min(32, reps - off)
+            prm = [fs.sim_params(model, inf, beta, 0.1, 1, latent=lat, replicate=off + q, age_dtype=a,
+                                 index_state=index_state) for q in range(R)]
+            e = fs.fs_ens_create(gh, prm, idx)
+            o = np.zeros((steps + 1, R, 4), dtype=np.uint32)
+            fs.fs_batch_add(b, e, steps, o)
+            ens.append(e)
+            outs.append(o)
+        t0 = time.perf_counter()
+        fs.fs_batch_run(b, steps + 1, 50)
+        secs[name] = time.perf_counter() - t0
+        fs.fs_batch_destroy(b)
+        for e in ens:
+            fs.fs_ens_destroy(e)
+        c = np.concatenate(outs, axis=1).astype(np.int64)          # [steps+1, reps, 4]
+        assert (c.sum(axis=2) == n).all()
+        peak[name] = c[:, :, 2].max(axis=0) / n
+        attack[name] = 1.0 - c[-1, :, 0] / n
+    fs.fs_graph_destroy(gh)
+    res = {}
+    for name in ("f32", "f16", "bf16"):
+        r = {"peak_I_mean": round(float(peak[name].mean()), 6), "attack_mean": round(float(attack[name].mean()), 6),
+             "peak_I_sd": round(float(peak[name].std(ddof=1)), 6), "attack_sd": round(float(attack[name].std(ddof=1)), 6),
+             "gnups": round(n * reps * steps / secs[name] / 1e9, 1)}
+        if name != "f32":
+            dp, da = peak[name] - peak["f32"], attack[name] - attack["f32"]
+            r["peak_I_shift"] = float(f"{dp.mean():.3g}")
+            r["peak_I_shift_se"] = float(f"{dp.std(ddof=1) / math.sqrt(reps):.3g}")
+            r["attack_shift"] = float(f"{da.mean():.3g}")
+            r["attack_shift_se"] = float(f"{da.std(ddof=1) / math.sqrt(reps):.3g}")
+        res[name] = r
+    return res
+
+
+def precision_bench(fs, torch, n: int, steps: int, reps: int):
+    """Storage precision of ages, stated per result. `reps` replicates of three
+    workloads with FP32, FP16 and BF16 age storage: C1 (SEIR, 10-regular, N,
+    beta 0.25, `steps` steps), the same at beta 0.05 (partial attack), and C0
+    (SIR, 10-regular, N = 10^4, beta 0.3, log-normal(ln 5, 0.5), 10 index
+    cases, 300 steps). Replicate r has the same random stream under every
+    storage type, so the paired differences of each replicate's peak
+    infectious fraction and attack rate isolate the effect of the storage. The
+    FP32 trajectories are the oracle's (bit-exact parity), so the shifts are
+    against the FP64 oracle at FP32 storage. Also the largest relative error of
+    the GPU's FP32 hazards against FP64 closed forms over the ages a run visits."""
+    import scipy.stats as st
+    lat, inf = fs.law("weibull", 2.0, 4.0), fs.law("lognormal", math.log(6.0), 0.6)
+    g = W.random_regular(n, 10, seed=0)
+    idx = W.index_nodes(n, 100, seed=1)
+    out = {"workload": f"age-storage-precision-{reps}replicates", "replicates": reps, "results": {}}
+    out["results"][f"C1 seir-regular10-n{n:.0e} beta0.25 {steps}steps".replace("+0", "")] = \
+        precision_runs(fs, g, idx, fs.FS_SEIR, inf, lat, 0.25, steps, reps)
+    out["results"][f"C1 seir-regular10-n{n:.0e} beta0.05 {steps}steps".replace("+0", "")] = \
+        precision_runs(fs, g, idx, fs.FS_SEIR, inf, lat, 0.05, steps, reps)
+    g0 = W.random_regular(10_000, 10, seed=0)
+    idx0 = W.index_nodes(g0.n, 10, seed=1)
+    out["results"]["C0 sir-regular10-n1e4 beta0.3 300steps"] = \
+        precision_runs(fs, g0, idx0, fs.FS_SIR, fs.law("lognormal", math.log(5.0), 0.5), None, 0.3, 300, reps)
+    # GPU FP32 hazards against FP64 closed forms at the ages of the fixed-step sequence
+    tau = (np.arange(1, 1001) * np.float32(0.1)).astype(np.float32)
+    t64 = tau.astype(np.float64)
+    refs = {"lognormal(ln 6, 0.6)": (inf, np.exp(st.lognorm.logpdf(t64, 0.6, scale=6.0)
+                                                 - st.lognorm.logsf(t64, 0.6, scale=6.0))),
+            "lognormal(ln 5, 0.5)": (fs.law("lognormal", math.log(5.0), 0.5),
+                                     np.exp(st.lognorm.logpdf(t64, 0.5, scale=5.0) - st.lognorm.logsf(t64, 0.5, scale=5.0))),
+            "weibull(2, 4)": (lat, 2.0 / 4.0 * (t64 / 4.0)),
+            "erlang(3, 0.75)": (fs.law("erlang", 0.75, k=3),
+                                np.exp(st.gamma.logpdf(t64, 3, scale=1 / 0.75) - st.gamma.logsf(t64, 3, scale=1 / 0.75)))}
+    herr = {}
+    for name, (lw, ref) in refs.items():
+        td = torch.from_numpy(tau).cuda()
+        hd = torch.empty_like(td)
+        fs.fs_eval_hazard(lw, td, hd)
+        torch.cuda.synchronize()
+        h = hd.cpu().numpy().astype(np.float64)
+        ok = ref >= 1e-30
+        herr[name] = float(np.max(np.abs(h[ok] - ref[ok]) / ref[ok]))
+    out["hazard_max_rel_err"] = {k: float(f"{v:.3g}") for k, v in herr.items()}
+    return out
+
+
 def run_reference(args, rank, world):
     """The oracle timed on the host cores on bounded samples of the workload."""
     if rank != 0:
@@ -631,6 +722,8 @@ def run_extra(args):
     if args.workload == "ensemble":
         res = ensemble_bench(fs, torch, n_graphs=args.ens_graphs, n_lo=1e4, n_hi=2e6, steps=args.ens_steps,
                              age_dtype=age)
+    elif args.workload == "precision":
+        res = precision_bench(fs, torch, n=args.n, steps=args.sim_steps, reps=1000)
     elif args.workload == "large":
         for n, a in ((10_000_000, fs.FS_AGE_F32), (100_000_000, fs.FS_AGE_F32), (100_000_000, fs.FS_AGE_BF16)):
             res = large_bench(fs, torch, n, a, args.sim_steps, args.graph_steps, reps=1)
