@@ -58,7 +58,7 @@ typedef enum {
 enum { FS_S = 0, FS_E = 1, FS_I = 2, FS_R = 3 };
 enum { FS_SIR = 0, FS_SEIR = 1 };
 enum { FS_AGE_F32 = 0, FS_AGE_F16 = 1, FS_AGE_BF16 = 2 };
-enum { FS_DISPATCH_AUTO = 0, FS_DISPATCH_THREAD = 1, FS_DISPATCH_MERGE = 2 };
+enum { FS_DISPATCH_AUTO = 0, FS_DISPATCH_THREAD = 1, FS_DISPATCH_MERGE = 2, FS_DISPATCH_TUNE = 3 };
 
 /* Holding-time law of a nodal transition (Section 5.1; hazard h = f/S).
  *   FS_LAW_EXP:       a = rate gamma                  h = gamma
@@ -96,7 +96,17 @@ typedef struct {
 /* Graph construction options (all fields may be 0 for the defaults). */
 typedef struct {
     int32_t dispatch;        /* FS_DISPATCH_*: AUTO picks the class split from the
-                                degree profile (Section 5.5 auto-dispatch)        */
+                                degree profile by a fixed rule (Section 5.5
+                                auto-dispatch); TUNE times short trial runs
+                                from an early-phase state (1% I) and from a
+                                mid-epidemic mix of states for each
+                                candidate split (thresholds 31, 63, 127, 255
+                                below d_max) and keeps the fastest (the AUTO
+                                split unless beaten by > 2%), caching the choice
+                                per degree profile
+                                (ceil log2 N, ceil log2 d_max, round d_avg) for
+                                the process; graphs with d_max <= 64 need no
+                                trial. THREAD / MERGE force one class.          */
     int32_t thread_max_deg;  /* rows of degree <= this go to the one-thread-per-node
                                 class; larger rows go to the edge-partitioned
                                 merge class. 0 = chosen by the tuner; >= 31        */
@@ -195,6 +205,13 @@ fs_status fs_sim_run_timed(fs_sim* s, int64_t steps, int32_t graph_steps, uint32
 /* Number of kernels enqueued so far by step loops of this process (graph
  * replays count their kernels). */
 fs_status fs_kernel_launches(uint64_t* count);
+
+/* Dispatch autotuner (FS_DISPATCH_TUNE): trial runs timed so far, graph
+ * creations answered from the cache, and degree profiles cached. The paper
+ * has no autotuner; its dispatch is a fixed rule on rho. */
+fs_status fs_tune_stats(int64_t* trials, int64_t* cache_hits, int64_t* profiles);
+/* Forgets every cached choice and zeroes the statistics. */
+fs_status fs_tune_reset(void);
 
 /* Host copies of the state in original node order: state uint8[n], age
  * (float / binary16 / bfloat16 bits per age_dtype)[n], step (next step

@@ -17,13 +17,13 @@ import numpy as np
 
 from . import _abi
 from ._abi import (FS_AGE_BF16, FS_AGE_F16, FS_AGE_F32, FS_DISPATCH_AUTO, FS_DISPATCH_MERGE,
-                   FS_DISPATCH_THREAD, FS_E, FS_I, FS_LAW_ERLANG, FS_LAW_EXP, FS_LAW_LOGNORMAL,
+                   FS_DISPATCH_THREAD, FS_DISPATCH_TUNE, FS_E, FS_I, FS_LAW_ERLANG, FS_LAW_EXP, FS_LAW_LOGNORMAL,
                    FS_LAW_NONE, FS_LAW_WEIBULL, FS_R, FS_S, FS_SEIR, FS_SIR, FsError, check)
 
 __all__ = [
     "fs_version", "fs_last_error", "fs_graph_create", "fs_graph_info_get", "fs_graph_destroy",
     "fs_sim_init", "fs_sim_step", "fs_sim_run", "fs_sim_run_async", "fs_sim_sync", "fs_sim_run_timed",
-    "fs_kernel_launches",
+    "fs_kernel_launches", "fs_tune_stats", "fs_tune_reset",
     "fs_sim_get_state", "fs_sim_set_state", "fs_sim_work", "fs_sim_destroy", "fs_eval_hazard",
     "fs_eval_uniforms", "fs_step_noalloc", "fs_ens_create", "fs_ens_run", "fs_ens_get_state",
     "fs_ens_destroy", "fs_batch_create", "fs_batch_add", "fs_batch_run", "fs_batch_status", "fs_batch_destroy",
@@ -31,7 +31,7 @@ __all__ = [
     "fs_server_destroy",
     "law", "sim_params", "graph_opts", "FsError", "load",
     "FS_S", "FS_E", "FS_I", "FS_R", "FS_SIR", "FS_SEIR", "FS_AGE_F32", "FS_AGE_F16", "FS_AGE_BF16",
-    "FS_DISPATCH_AUTO", "FS_DISPATCH_THREAD", "FS_DISPATCH_MERGE",
+    "FS_DISPATCH_AUTO", "FS_DISPATCH_THREAD", "FS_DISPATCH_MERGE", "FS_DISPATCH_TUNE",
 ]
 
 
@@ -167,6 +167,16 @@ def fs_sim_run_timed(s: int, steps: int, graph_steps: int = 0, counts_dev=None) 
     check(load().fs_sim_run_timed(s, int(steps), int(graph_steps), _addr(counts_dev), _addr(ms),
                                   ctypes.byref(n)), "fs_sim_run_timed")
     return ms[:n.value]
+
+
+def fs_tune_stats() -> dict:
+    t, h, p = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    check(load().fs_tune_stats(ctypes.byref(t), ctypes.byref(h), ctypes.byref(p)), "fs_tune_stats")
+    return {"trials": t.value, "cache_hits": h.value, "profiles": p.value}
+
+
+def fs_tune_reset() -> None:
+    check(load().fs_tune_reset(), "fs_tune_reset")
 
 
 def fs_kernel_launches() -> int:

@@ -17,7 +17,7 @@ STATUS_NAMES = {0: "FS_OK", 1: "FS_EINVAL", 2: "FS_ENOMEM", 3: "FS_ECUDA", 4: "F
 FS_S, FS_E, FS_I, FS_R = 0, 1, 2, 3
 FS_SIR, FS_SEIR = 0, 1
 FS_AGE_F32, FS_AGE_F16, FS_AGE_BF16 = 0, 1, 2
-FS_DISPATCH_AUTO, FS_DISPATCH_THREAD, FS_DISPATCH_MERGE = 0, 1, 2
+FS_DISPATCH_AUTO, FS_DISPATCH_THREAD, FS_DISPATCH_MERGE, FS_DISPATCH_TUNE = 0, 1, 2, 3
 FS_LAW_NONE, FS_LAW_EXP, FS_LAW_LOGNORMAL, FS_LAW_WEIBULL, FS_LAW_ERLANG = 0, 1, 2, 3, 4
 
 
@@ -95,6 +95,8 @@ PROTOTYPES = {
     "fs_batch_run": (ctypes.c_int, [VP, ctypes.c_int64, ctypes.c_int32]),
     "fs_batch_status": (ctypes.c_int, [VP, P(ctypes.c_int32), P(ctypes.c_int64)]),
     "fs_batch_destroy": (ctypes.c_int, [VP]),
+    "fs_tune_stats": (ctypes.c_int, [P(ctypes.c_int64), P(ctypes.c_int64), P(ctypes.c_int64)]),
+    "fs_tune_reset": (ctypes.c_int, []),
     "fs_server_create": (ctypes.c_int, [P(fs_server_cfg), P(VP)]),
     "fs_server_submit": (ctypes.c_int, [VP, VP, P(fs_sim_params), ctypes.c_int32, ctypes.c_int32, VP,
                                         ctypes.c_int64, ctypes.c_int64, P(ctypes.c_uint64)]),

@@ -274,8 +274,10 @@ fs_status fs_graph_create(int64_t n, const int64_t* row_ptr, const int32_t* col_
         return fail(FS_EINVAL, "n must be in [1, 2^31 - 1)");
     if (!row_ptr)
         return fail(FS_EINVAL, "row_ptr is NULL");
-    if (o.dispatch < FS_DISPATCH_AUTO || o.dispatch > FS_DISPATCH_MERGE)
+    if (o.dispatch < FS_DISPATCH_AUTO || o.dispatch > FS_DISPATCH_TUNE)
         return fail(FS_EINVAL, "unknown dispatch %d", o.dispatch);
+    if (o.dispatch == FS_DISPATCH_TUNE && o.thread_max_deg != 0)
+        return fail(FS_EINVAL, "FS_DISPATCH_TUNE chooses thread_max_deg itself (pass 0)");
     if (o.thread_max_deg != 0 && (o.thread_max_deg < 31 || o.thread_max_deg > fs::kMaxThreadDeg))
         return fail(FS_EINVAL, "thread_max_deg must be 0 or in [31, %d]", fs::kMaxThreadDeg);
     if (o.device_input != 0 && o.device_input != 1)
@@ -303,6 +305,35 @@ fs_status fs_graph_create(int64_t n, const int64_t* row_ptr, const int32_t* col_
             return fail(FS_EINVAL, "row_ptr[n] < 0");
         if (nnz > 0 && !col_ind)
             return fail(FS_EINVAL, "col_ind is NULL");
+    }
+    if (o.dispatch == FS_DISPATCH_TUNE) {
+        // the degree profile first (d_max), then the tuner builds what it needs
+        int64_t dmax = 0;
+        if (!dev_in) {
+            for (int64_t i = 0; i < n; ++i)
+                dmax = std::max(dmax, row_ptr[i + 1] - row_ptr[i]);
+        } else {
+            fs::IngestFlags* d_fl = nullptr;
+            fs::IngestFlags hf{};
+            cudaError_t e = dev_alloc(&d_fl, 1, nullptr);
+            if (e == cudaSuccess)
+                e = cudaMemsetAsync(d_fl, 0, sizeof(fs::IngestFlags), st);
+            if (e == cudaSuccess)
+                e = fs::launch_degrees(row_ptr, (int)n, fs::kMaxThreadDeg, nullptr, nullptr, d_fl, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(&hf, d_fl, sizeof(hf), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess)
+                e = cudaStreamSynchronize(st);
+            cudaFree(d_fl);
+            if (e != cudaSuccess)
+                return fail(FS_ECUDA, "degree profile: %s", cudaGetErrorString(e));
+            if (hf.error)
+                return fail(FS_EINVAL, "row_ptr is not a valid CSR row pointer");
+            dmax = hf.dmax;
+        }
+        fs_graph_opts a = o;
+        a.dispatch = FS_DISPATCH_AUTO;
+        return fsapi::tune_create(n, nnz, dmax, row_ptr, col_ind, a, stream, out);
     }
 
     fs_graph* g = new fs_graph();

@@ -29,8 +29,10 @@ __global__ void degree_kernel(const int64_t* __restrict__ row_ptr, int n, int t1
         d = (int)max((int64_t)0, min(dd, (int64_t)INT_MAX));
         k = d <= t1 ? d : t1 + 1;
         small = d <= t1;
-        deg[i] = d;
-        key[i] = (uint16_t)k;
+        if (deg) {                                   // null: only d_max and the checks
+            deg[i] = d;
+            key[i] = (uint16_t)k;
+        }
         if (i + 1 < n) {
             const int64_t dn = row_ptr[i + 2] - b;
             const int kn = (dn >= 0 && dn <= t1) ? (int)dn : t1 + 1;

@@ -1,0 +1,232 @@
+// fs_tune.cpp -- the dispatch autotuner behind fs_graph_create's
+// FS_DISPATCH_TUNE (include/fs.h). The class split of a skewed graph (which
+// rows run one lane per node in SELL-32 slices and which run edge-partitioned
+// in merge chunks, Section 5.5) is chosen by timing: every candidate
+// threshold is built and short trial runs from an early-phase state and a
+// mid-epidemic mix of states are timed through the public step loop; the
+// fastest is kept (the default split unless another beats it by more than
+// the trial's noise). Choices are cached per degree profile for
+// the life of the process. Built on the public entry points only.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "fs.h"
+#include "fs_objects.h"
+
+using fsapi::fail;
+
+namespace {
+
+using Key = std::tuple<int, int, int>;   // ceil(log2 N), ceil(log2 d_max), round(d_avg)
+
+constexpr int32_t kDefaultT1 = 63;       // the AUTO rule's threshold when d_max > 64
+
+std::mutex g_mu;
+std::map<Key, int32_t> g_cache;
+std::atomic<int64_t> g_trials{0}, g_hits{0};
+
+int ceil_log2(int64_t v)
+{
+    int l = 0;
+    while (((int64_t)1 << l) < v)
+        ++l;
+    return l;
+}
+
+fs_sim_params trial_params()
+{
+    fs_sim_params p{};
+    p.model = FS_SEIR;
+    p.age_dtype = FS_AGE_F32;
+    p.latent.kind = FS_LAW_WEIBULL;
+    p.latent.a = 2.0;
+    p.latent.b = 4.0;
+    p.infectious.kind = FS_LAW_LOGNORMAL;
+    p.infectious.a = std::log(6.0);
+    p.infectious.b = 0.6;
+    p.beta = 0.25;
+    p.dt = 0.1;
+    p.seed = 0x5eed;
+    p.index_state = FS_E;
+    return p;
+}
+
+uint64_t mix64(uint64_t i)
+{
+    uint64_t h = i * 0x9E3779B97F4A7C15ull;
+    h ^= h >> 31;
+    h *= 0xBF58476D1CE4E5B9ull;
+    h ^= h >> 29;
+    return h;
+}
+
+// time of the replays after the first of 32 steps from the given states
+fs_status timed_from(fs_graph* g, int64_t n, void* stream, const std::vector<uint8_t>& X,
+                     const std::vector<float>& A, float* ms)
+{
+    const fs_sim_params p = trial_params();
+    const int32_t first = 0;
+    fs_sim* s = nullptr;
+    fs_status st = fs_sim_init(g, &p, &first, 1, stream, &s);
+    if (st != FS_OK)
+        return st;
+    st = fs_sim_set_state(s, X.data(), A.data(), 0);
+    float r[5] = {0, 0, 0, 0, 0};
+    int64_t nr = 0;
+    if (st == FS_OK)
+        st = fs_sim_run_timed(s, 32, 8, nullptr, r, &nr);
+    fs_sim_destroy(s);
+    *ms = r[1] + r[2] + r[3];
+    return st;
+}
+
+// Trial time of one class split: SEIR from two states, each a hash of the
+// node id, for the two regimes of a run: the early phase (all S but 1% I:
+// every row is gathered) and a mid-epidemic mix (S 40%, E 15%, I 15%,
+// R 30%, E/I ages on the fixed-step age sequence up to 8 days).
+fs_status trial_ms(fs_graph* g, int64_t n, void* stream, float* ms)
+{
+    float seq[81];
+    seq[0] = 0.0f;
+    for (int k = 0; k < 80; ++k)
+        seq[k + 1] = seq[k] + 0.1f;
+    std::vector<uint8_t> X((size_t)n);
+    std::vector<float> A((size_t)n, 0.0f);
+    for (int64_t i = 0; i < n; ++i) {
+        const uint64_t h = mix64((uint64_t)i);
+        X[(size_t)i] = (h % 100u) < 1 ? FS_I : FS_S;
+        A[(size_t)i] = X[(size_t)i] == FS_I ? seq[(h >> 8) % 80u] : 0.0f;
+    }
+    float early = 0.0f, mid = 0.0f;
+    fs_status st = timed_from(g, n, stream, X, A, &early);
+    if (st != FS_OK)
+        return st;
+    for (int64_t i = 0; i < n; ++i) {
+        const uint64_t h = mix64((uint64_t)i);
+        const uint32_t u = (uint32_t)(h % 100u);
+        const uint8_t x = u < 40 ? FS_S : u < 55 ? FS_E : u < 70 ? FS_I : FS_R;
+        X[(size_t)i] = x;
+        A[(size_t)i] = (x == FS_E || x == FS_I) ? seq[(h >> 8) % 80u] : 0.0f;
+    }
+    st = timed_from(g, n, stream, X, A, &mid);
+    if (st != FS_OK)
+        return st;
+    *ms = early + mid;
+    g_trials += 1;
+    return FS_OK;
+}
+
+}  // namespace
+
+namespace fsapi {
+
+fs_status tune_create(int64_t n, int64_t nnz, int64_t dmax, const int64_t* row_ptr, const int32_t* col_ind,
+                      const fs_graph_opts& base, void* stream, fs_graph** out)
+{
+    auto build = [&](int32_t t1, fs_graph** g) {
+        fs_graph_opts o = base;
+        o.dispatch = FS_DISPATCH_AUTO;
+        o.thread_max_deg = t1;
+        return fs_graph_create(n, row_ptr, col_ind, nullptr, &o, stream, g);
+    };
+    std::vector<int32_t> cand;
+    for (int32_t t : {31, 63, 127, 255})
+        if (t < dmax && t <= fs::kMaxThreadDeg)
+            cand.push_back(t);
+    if (dmax <= 64 || cand.empty())             // one class holds every row: nothing to choose
+        return build(0, out);
+    const double d_avg = n ? (double)nnz / (double)n : 0.0;
+    const Key key{ceil_log2(n), ceil_log2(dmax), (int)std::lround(d_avg)};
+    {
+        std::lock_guard<std::mutex> lock(g_mu);
+        auto it = g_cache.find(key);
+        if (it != g_cache.end()) {
+            g_hits += 1;
+            const int32_t t1 = it->second;
+            return build(t1, out);
+        }
+    }
+    fs_graph *best_g = nullptr, *default_g = nullptr;   // default_g: the AUTO rule's split, kept aside
+    float best_ms = 0.0f, default_ms = 0.0f;
+    int32_t best = 0;
+    for (int32_t t1 : cand) {
+        fs_graph* g = nullptr;
+        fs_status st = build(t1, &g);
+        float ms = 0.0f;
+        if (st == FS_OK)
+            st = trial_ms(g, n, stream, &ms);
+        if (st != FS_OK) {                     // free each graph held, once
+            fs_graph* held[3] = {g, best_g, default_g};
+            for (int a = 0; a < 3; ++a) {
+                bool seen = held[a] == nullptr;
+                for (int b = 0; b < a; ++b)
+                    seen = seen || held[b] == held[a];
+                if (!seen)
+                    fs_graph_destroy(held[a]);
+            }
+            return st;
+        }
+        if (t1 == kDefaultT1) {
+            default_g = g;
+            default_ms = ms;
+        }
+        if (!best_g || ms < best_ms) {
+            if (best_g && best_g != default_g)
+                fs_graph_destroy(best_g);
+            best_g = g;
+            best_ms = ms;
+            best = t1;
+        } else if (g != default_g) {
+            fs_graph_destroy(g);
+        }
+    }
+    // the default split stays unless a candidate beats it by more than the
+    // trial's run-to-run noise (2%)
+    if (best != kDefaultT1 && default_g && default_ms <= best_ms * 1.02f) {
+        fs_graph_destroy(best_g);
+        best_g = default_g;
+        best = kDefaultT1;
+        default_g = nullptr;
+    }
+    if (default_g && default_g != best_g)
+        fs_graph_destroy(default_g);
+    {
+        std::lock_guard<std::mutex> lock(g_mu);
+        g_cache[key] = best;
+    }
+    *out = best_g;
+    return FS_OK;
+}
+
+}  // namespace fsapi
+
+extern "C" {
+
+fs_status fs_tune_stats(int64_t* trials, int64_t* cache_hits, int64_t* profiles)
+{
+    if (!trials || !cache_hits || !profiles)
+        return fail(FS_EINVAL, "fs_tune_stats: NULL argument");
+    std::lock_guard<std::mutex> lock(g_mu);
+    *trials = g_trials.load();
+    *cache_hits = g_hits.load();
+    *profiles = (int64_t)g_cache.size();
+    return FS_OK;
+}
+
+fs_status fs_tune_reset(void)
+{
+    std::lock_guard<std::mutex> lock(g_mu);
+    g_cache.clear();
+    g_trials = 0;
+    g_hits = 0;
+    return FS_OK;
+}
+
+}  // extern "C"
