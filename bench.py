@@ -346,7 +346,7 @@ def run_flashstep(args, rank, world, local_rank):
     d_col = torch.from_numpy(g.col_ind).to(dev)
     counts_dev = torch.zeros((args.sim_steps + 1) * 4, dtype=torch.int32, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    prm = params(fs, seed=1 + rank, replicate=0)
+    prm = params(fs, seed=replica_seed(rank), replicate=0)
     opts = fs.graph_opts(device_input=True)
 
     def one_step():
@@ -389,13 +389,8 @@ def run_flashstep(args, rank, world, local_rank):
                          * steps_in_graphs / args.sim_steps)
     clock_info = clocks.stop() if clocks else None
     launches = (fs.fs_kernel_launches() - launches0) // max(args.steps, 1)
-    total_ms = float(np.sum(times))
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    node_updates = g.n * args.sim_steps * args.steps * world
-    value = node_updates / (total_ms * 1e-3) / 1e9
+    total_ms = max_over_ranks(float(np.sum(times)), dist, dev)
+    value = whole_job_gnups(g.n, args.sim_steps, args.steps, world, total_ms)
     # roofline of the dominant kernel (the fused step): algorithmic bytes of the
     # steps / their event-timed graph replays (which include launch gaps and the
     # per-replay epilogue, so this is a lower bound on the kernel's own rate)
@@ -738,19 +733,53 @@ def run_extra(args):
     print(json.dumps({"metric": METRIC, "unit": UNIT, "impl": "flashstep", "data": "synthetic", **res}), flush=True)
 
 
+# ------------------------------------------------------------------ ranks
+def rank_setup(environ, gpus: int):
+    """(rank, world, local_rank) of this process, and the environment changes
+    it needs. Under torchrun every rank is one replica on its own GPU: that GPU
+    is made the only visible one, so that every CUDA runtime in the process
+    (torch's and the library's) addresses the same device."""
+    changes = {}
+    world = int(environ.get("WORLD_SIZE", "1"))
+    local_rank = int(environ.get("LOCAL_RANK", "0"))
+    if world > 1 and "LOCAL_RANK" in environ:
+        changes = {"CUDA_VISIBLE_DEVICES": environ["LOCAL_RANK"], "LOCAL_RANK": "0"}
+        local_rank = 0
+    rank = int(environ.get("RANK", "0"))
+    if "WORLD_SIZE" not in environ:
+        world = gpus if gpus == 1 else 1
+    return rank, world, local_rank, changes
+
+
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """The largest value over all ranks (a job lasts as long as its slowest
+    rank); the value itself when there is one rank."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gnups(n: int, sim_steps: int, bench_steps: int, world: int, total_ms: float) -> float:
+    """Node updates of all replicas (weak scaling: every rank runs the full
+    workload on its own GPU) per second of the slowest rank, in GNUPS."""
+    return n * sim_steps * bench_steps * world / (total_ms * 1e-3) / 1e9
+
+
+def replica_seed(rank: int) -> int:
+    """Philox seed of rank r's replica: distinct realisations, no exchange."""
+    return 1 + rank
+
+
 def main():
     args = parse()
     if args.workload != "regular":
         run_extra(args)
         return
-    if int(os.environ.get("WORLD_SIZE", "1")) > 1 and "LOCAL_RANK" in os.environ:
-        # one visible GPU per replica, so that every CUDA runtime in the
-        # process (torch's and the library's) addresses the same device
-        os.environ["CUDA_VISIBLE_DEVICES"] = os.environ["LOCAL_RANK"]
-        os.environ["LOCAL_RANK"] = "0"
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
-    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local_rank, changes = rank_setup(os.environ, args.gpus)
+    os.environ.update(changes)
     if args.impl == "reference":
         out = run_reference(args, rank, world)
     else:
