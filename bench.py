@@ -61,7 +61,12 @@ def parse():
     ap.add_argument("--age", choices=["f32", "f16"], default="f32", help="age storage of ensemble/serving runs")
     ap.add_argument("--ens-graphs", type=int, default=64, help="graphs of the packed-ensemble run")
     ap.add_argument("--ens-steps", type=int, default=500, help="steps of the packed-ensemble run")
+    ap.add_argument("--pressure", choices=["auto", "gather", "push"], default="auto",
+                    help="pressure form of single-realisation runs (auto = push where available)")
     return ap.parse_args()
+
+
+PRESSURE = {"auto": 0, "gather": 1, "push": 2}
 
 
 # ------------------------------------------------------------------ workload
@@ -77,9 +82,9 @@ def workload(kind: str, n: int):
     return g, idx, name
 
 
-def params(fs, seed: int, replicate: int = 0):
+def params(fs, seed: int, replicate: int = 0, pressure: int = 0):
     return fs.sim_params(fs.FS_SEIR, fs.law("lognormal", math.log(6.0), 0.6), 0.25, 0.1, seed,
-                         latent=fs.law("weibull", 2.0, 4.0), replicate=replicate)
+                         latent=fs.law("weibull", 2.0, 4.0), replicate=replicate, pressure=pressure)
 
 
 def bytes_model(n: int, steps: int, s_node_sum: int, s_degree_sum: int, b_state=1, b_age=4) -> float:
@@ -346,7 +351,7 @@ def run_flashstep(args, rank, world, local_rank):
     d_col = torch.from_numpy(g.col_ind).to(dev)
     counts_dev = torch.zeros((args.sim_steps + 1) * 4, dtype=torch.int32, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    prm = params(fs, seed=replica_seed(rank), replicate=0)
+    prm = params(fs, seed=replica_seed(rank), replicate=0, pressure=PRESSURE[args.pressure])
     opts = fs.graph_opts(device_input=True)
 
     def one_step():
@@ -467,7 +472,7 @@ def secondary_ba(fs, torch, args, stream, flush):
     dev = flush.device
     d_rp = torch.from_numpy(g.row_ptr).to(dev)
     d_col = torch.from_numpy(g.col_ind).to(dev)
-    prm = params(fs, seed=1)
+    prm = params(fs, seed=1, pressure=PRESSURE[args.pressure])
     # the class split is chosen by the autotuner (its trials run once, in the
     # first warm-up creation; later creations are answered from its cache)
     opts = fs.graph_opts(dispatch=fs.FS_DISPATCH_TUNE, device_input=True)
@@ -515,7 +520,7 @@ def device_regular(torch, n: int, d: int, seed: int, dev):
     return rp, col
 
 
-def large_bench(fs, torch, n: int, age_dtype: int, sim_steps: int, graph_steps: int, reps: int):
+def large_bench(fs, torch, n: int, age_dtype: int, sim_steps: int, graph_steps: int, reps: int, pressure: int = 0):
     """The C1 SEIR workload on a random 10-regular graph of N = 10^7 or 10^8
     nodes, where the step's working set is far larger than L2: ingest from the
     device CSR + init + all steps, timed with CUDA events; the kernel-side
@@ -525,7 +530,7 @@ def large_bench(fs, torch, n: int, age_dtype: int, sim_steps: int, graph_steps: 
     rp, col = device_regular(torch, n, d, seed=0, dev=dev)
     idx = W.index_nodes(n, 100, seed=1)
     prm = fs.sim_params(fs.FS_SEIR, fs.law("lognormal", math.log(6.0), 0.6), 0.25, 0.1, 1,
-                        latent=fs.law("weibull", 2.0, 4.0), replicate=0, age_dtype=age_dtype)
+                        latent=fs.law("weibull", 2.0, 4.0), replicate=0, age_dtype=age_dtype, pressure=pressure)
     opts = fs.graph_opts(device_input=True)
     stream = torch.cuda.Stream()
     b_age = 4 if age_dtype == fs.FS_AGE_F32 else 2
@@ -724,7 +729,8 @@ def run_extra(args):
         res = precision_bench(fs, torch, n=args.n, steps=args.sim_steps, reps=1000)
     elif args.workload == "large":
         for n, a in ((10_000_000, fs.FS_AGE_F32), (100_000_000, fs.FS_AGE_F32), (100_000_000, fs.FS_AGE_BF16)):
-            res = large_bench(fs, torch, n, a, args.sim_steps, args.graph_steps, reps=1)
+            res = large_bench(fs, torch, n, a, args.sim_steps, args.graph_steps, reps=1,
+                              pressure=PRESSURE[args.pressure])
             print(json.dumps({"metric": METRIC, "impl": "flashstep", "data": "synthetic", **res}), flush=True)
         return
     else:

@@ -59,6 +59,22 @@ enum { FS_S = 0, FS_E = 1, FS_I = 2, FS_R = 3 };
 enum { FS_SIR = 0, FS_SEIR = 1 };
 enum { FS_AGE_F32 = 0, FS_AGE_F16 = 1, FS_AGE_BF16 = 2 };
 enum { FS_DISPATCH_AUTO = 0, FS_DISPATCH_THREAD = 1, FS_DISPATCH_MERGE = 2, FS_DISPATCH_TUNE = 3 };
+/* How a realisation obtains the infection pressure of its S nodes (the count
+ * c_i of in-neighbours in I, lambda_i = beta c_i; Eq. 3 with unit weights and
+ * constant shedding), passed in fs_sim_params.flags:
+ *   FS_PRESSURE_GATHER: every step, every S node counts the I bits of its
+ *     row in an infectious bitmap (the paper's gather, Algorithm 3).
+ *   FS_PRESSURE_PUSH: every node keeps c_i; a node entering I adds 1 to the
+ *     count of each node whose row lists it, a node leaving I subtracts 1
+ *     (along the transposed CSR, built on the graph's first push-form sim).
+ *     Same integer counts, so the same trajectory bit for bit; the work per
+ *     step no longer grows with the edges of S rows. Needs every node of the
+ *     one-thread-per-node class to have in-degree <= 255 (true for every
+ *     dispatch except FS_DISPATCH_THREAD on graphs with d_max > 255).
+ *   FS_PRESSURE_AUTO (0): PUSH where it is available, else GATHER.
+ * Packed ensembles, batches and the server use the gather (AUTO or GATHER;
+ * PUSH is FS_EUNSUPPORTED there). */
+enum { FS_PRESSURE_AUTO = 0, FS_PRESSURE_GATHER = 1, FS_PRESSURE_PUSH = 2 };
 
 /* Holding-time law of a nodal transition (Section 5.1; hazard h = f/S).
  *   FS_LAW_EXP:       a = rate gamma                  h = gamma
@@ -89,7 +105,7 @@ typedef struct {
     uint64_t seed;       /* Philox key                                             */
     uint32_t replicate;  /* realisation index in the key's stream                  */
     int32_t index_state; /* compartment of the index cases: FS_E (SEIR) or FS_I    */
-    int32_t flags;       /* reserved, must be 0                                    */
+    int32_t flags;       /* FS_PRESSURE_AUTO / _GATHER / _PUSH; other values invalid */
     int32_t reserved_;   /* must be 0                                              */
 } fs_sim_params;
 
@@ -221,6 +237,9 @@ fs_status fs_sim_get_state(fs_sim* s, uint8_t* state, void* age, int64_t* step);
  * ages must be storage values of the sim's age dtype; S and R ages must be
  * 0. Synchronous. */
 fs_status fs_sim_set_state(fs_sim* s, const uint8_t* state, const void* age, int64_t step);
+
+/* The pressure form the sim runs (FS_PRESSURE_GATHER or FS_PRESSURE_PUSH). */
+fs_status fs_sim_pressure_get(const fs_sim* s, int32_t* pressure);
 
 /* Work accounting for the roofline model: the sum over all steps run so far
  * of sum_{i in S at step start} deg(i), and of |S at step start|. */

@@ -18,13 +18,15 @@ import numpy as np
 from . import _abi
 from ._abi import (FS_AGE_BF16, FS_AGE_F16, FS_AGE_F32, FS_DISPATCH_AUTO, FS_DISPATCH_MERGE,
                    FS_DISPATCH_THREAD, FS_DISPATCH_TUNE, FS_E, FS_I, FS_LAW_ERLANG, FS_LAW_EXP, FS_LAW_LOGNORMAL,
-                   FS_LAW_NONE, FS_LAW_WEIBULL, FS_R, FS_S, FS_SEIR, FS_SIR, FsError, check)
+                   FS_LAW_NONE, FS_LAW_WEIBULL, FS_PRESSURE_AUTO, FS_PRESSURE_GATHER, FS_PRESSURE_PUSH, FS_R,
+                   FS_S, FS_SEIR, FS_SIR, FsError, check)
 
 __all__ = [
     "fs_version", "fs_last_error", "fs_graph_create", "fs_graph_info_get", "fs_graph_destroy",
     "fs_sim_init", "fs_sim_step", "fs_sim_run", "fs_sim_run_async", "fs_sim_sync", "fs_sim_run_timed",
     "fs_kernel_launches", "fs_tune_stats", "fs_tune_reset",
-    "fs_sim_get_state", "fs_sim_set_state", "fs_sim_work", "fs_sim_destroy", "fs_eval_hazard",
+    "fs_sim_get_state", "fs_sim_set_state", "fs_sim_work", "fs_sim_pressure_get", "fs_sim_destroy",
+    "fs_eval_hazard",
     "fs_eval_uniforms", "fs_step_noalloc", "fs_ens_create", "fs_ens_run", "fs_ens_get_state",
     "fs_ens_destroy", "fs_batch_create", "fs_batch_add", "fs_batch_run", "fs_batch_status", "fs_batch_destroy",
     "fs_server_create", "fs_server_submit", "fs_server_poll", "fs_server_drain", "fs_server_stats_get",
@@ -32,6 +34,7 @@ __all__ = [
     "law", "sim_params", "graph_opts", "FsError", "load",
     "FS_S", "FS_E", "FS_I", "FS_R", "FS_SIR", "FS_SEIR", "FS_AGE_F32", "FS_AGE_F16", "FS_AGE_BF16",
     "FS_DISPATCH_AUTO", "FS_DISPATCH_THREAD", "FS_DISPATCH_MERGE", "FS_DISPATCH_TUNE",
+    "FS_PRESSURE_AUTO", "FS_PRESSURE_GATHER", "FS_PRESSURE_PUSH",
 ]
 
 
@@ -81,12 +84,13 @@ def lognormal_from_mean_median(mean: float, median: float) -> _abi.fs_law:
 
 def sim_params(model: int, infectious: _abi.fs_law, beta: float, dt: float, seed: int,
                latent: _abi.fs_law | None = None, replicate: int = 0, index_state: int | None = None,
-               age_dtype: int = FS_AGE_F32) -> _abi.fs_sim_params:
+               age_dtype: int = FS_AGE_F32, pressure: int = FS_PRESSURE_AUTO) -> _abi.fs_sim_params:
+    """pressure: FS_PRESSURE_AUTO / FS_PRESSURE_GATHER / FS_PRESSURE_PUSH (the flags field)."""
     if index_state is None:
         index_state = FS_E if model == FS_SEIR else FS_I
     return _abi.fs_sim_params(int(model), int(age_dtype), latent if latent is not None else law("none"),
                               infectious, float(beta), float(dt), int(seed), int(replicate),
-                              int(index_state), 0, 0)
+                              int(index_state), int(pressure), 0)
 
 
 def graph_opts(dispatch: int = FS_DISPATCH_AUTO, thread_max_deg: int = 0,
@@ -207,6 +211,13 @@ def fs_sim_work(s: int) -> dict:
     ds, sn, k = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int64()
     check(load().fs_sim_work(s, ctypes.byref(ds), ctypes.byref(sn), ctypes.byref(k)), "fs_sim_work")
     return {"s_degree_sum": ds.value, "s_node_sum": sn.value, "steps": k.value}
+
+
+def fs_sim_pressure_get(s: int) -> int:
+    """FS_PRESSURE_GATHER or FS_PRESSURE_PUSH: the form the sim runs."""
+    v = ctypes.c_int32()
+    check(load().fs_sim_pressure_get(s, ctypes.byref(v)), "fs_sim_pressure_get")
+    return v.value
 
 
 def fs_sim_destroy(s: int) -> None:

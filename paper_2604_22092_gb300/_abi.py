@@ -18,6 +18,7 @@ FS_S, FS_E, FS_I, FS_R = 0, 1, 2, 3
 FS_SIR, FS_SEIR = 0, 1
 FS_AGE_F32, FS_AGE_F16, FS_AGE_BF16 = 0, 1, 2
 FS_DISPATCH_AUTO, FS_DISPATCH_THREAD, FS_DISPATCH_MERGE, FS_DISPATCH_TUNE = 0, 1, 2, 3
+FS_PRESSURE_AUTO, FS_PRESSURE_GATHER, FS_PRESSURE_PUSH = 0, 1, 2
 FS_LAW_NONE, FS_LAW_EXP, FS_LAW_LOGNORMAL, FS_LAW_WEIBULL, FS_LAW_ERLANG = 0, 1, 2, 3, 4
 
 
@@ -81,6 +82,7 @@ PROTOTYPES = {
     "fs_sim_get_state": (ctypes.c_int, [VP, VP, VP, P(ctypes.c_int64)]),
     "fs_sim_set_state": (ctypes.c_int, [VP, VP, VP, ctypes.c_int64]),
     "fs_sim_work": (ctypes.c_int, [VP, P(ctypes.c_uint64), P(ctypes.c_uint64), P(ctypes.c_int64)]),
+    "fs_sim_pressure_get": (ctypes.c_int, [VP, P(ctypes.c_int32)]),
     "fs_sim_destroy": (ctypes.c_int, [VP]),
     "fs_eval_hazard": (ctypes.c_int, [P(fs_law), VP, VP, ctypes.c_int64, VP]),
     "fs_eval_uniforms": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64, VP, VP,

@@ -65,6 +65,8 @@ void free_graph(fs_graph* g)
     cudaFree(g->d_m_col);
     cudaFree(g->d_m_warp_row);
     cudaFree(g->d_m_chunk_last);
+    cudaFree(g->d_out_ptr);
+    cudaFree(g->d_out_col);
     delete g;
 }
 
@@ -84,6 +86,12 @@ void free_sim(fs_sim* s)
     cudaFree(s->d_deltas);
     cudaFree(s->d_ptab);
     cudaFree(s->d_ps);
+    cudaFree(s->d_cnt8);
+    cudaFree(s->d_pd16[0]);
+    cudaFree(s->d_pd16[1]);
+    cudaFree(s->d_hcnt);
+    cudaFree(s->d_pd64[0]);
+    cudaFree(s->d_pd64[1]);
     cudaFree(s->d_counts);
     if (s->own_stream && s->stream)
         cudaStreamDestroy(s->stream);
@@ -164,8 +172,10 @@ fs_status check_params(const fs_sim_params* p)
         return fail(FS_EINVAL, "beta must be finite and >= 0");
     if (!finite(p->dt) || !(p->dt > 0))
         return fail(FS_EINVAL, "dt must be finite and > 0");
-    if (p->flags != 0 || p->reserved_ != 0)
-        return fail(FS_EINVAL, "flags and reserved fields must be 0");
+    if (p->flags < FS_PRESSURE_AUTO || p->flags > FS_PRESSURE_PUSH)
+        return fail(FS_EINVAL, "flags must be FS_PRESSURE_AUTO, FS_PRESSURE_GATHER or FS_PRESSURE_PUSH");
+    if (p->reserved_ != 0)
+        return fail(FS_EINVAL, "reserved field must be 0");
     fs_status st = check_law(p->infectious, "infectious", false);
     if (st != FS_OK)
         return st;
@@ -232,7 +242,80 @@ fs::StepArgs step_args(const fs_sim* s, int j)
     a.deltas = s->d_deltas;
     a.j = j;
     a.n = (int32_t)g->n;
+    a.cnt8 = s->d_cnt8;
+    a.pd16[0] = s->d_pd16[0];
+    a.pd16[1] = s->d_pd16[1];
+    a.hcnt = s->d_hcnt;
+    a.pd64[0] = s->d_pd64[0];
+    a.pd64[1] = s->d_pd64[1];
+    a.out_ptr = g->d_out_ptr;
+    a.out_col = g->d_out_col;
     return a;
+}
+
+// the push form needs u8 counts for the whole one-thread-per-node class
+bool push_available(const fs_graph* g)
+{
+    return g->n_thr == 0 || g->t1 <= fs::kMaxThreadDeg;
+}
+
+// transposed CSR of the graph in internal ids (once per graph)
+cudaError_t ensure_out_csr(fs_graph* g, cudaStream_t st)
+{
+    if (g->d_out_ptr)
+        return cudaSuccess;
+    const int64_t n = g->n;
+    int64_t* optr = nullptr;
+    int32_t* ocol = nullptr;
+    unsigned long long* cur = nullptr;
+    int64_t bytes = 0;
+    cudaError_t e = dev_alloc(&optr, (size_t)n + 1, &bytes);
+    if (e == cudaSuccess)
+        e = dev_alloc(&ocol, (size_t)g->nnz, &bytes);
+    if (e == cudaSuccess)
+        e = dev_alloc(&cur, (size_t)n + 1, nullptr);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(cur, 0, sizeof(unsigned long long) * (n + 1), st);
+    if (e == cudaSuccess)
+        e = fs::launch_transpose(g->d_sell_off, g->d_sell_col, g->d_deg, g->n_thr, g->d_m_ptr, g->d_m_col, g->n_m,
+                                 (int)n, cur, nullptr, false, st);
+    if (e == cudaSuccess)
+        e = fs::exclusive_scan_i64(reinterpret_cast<const int64_t*>(cur), optr, n, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(cur, optr, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+        e = fs::launch_transpose(g->d_sell_off, g->d_sell_col, g->d_deg, g->n_thr, g->d_m_ptr, g->d_m_col, g->n_m,
+                                 (int)n, cur, ocol, true, st);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(st);
+    cudaFree(cur);
+    if (e != cudaSuccess) {
+        cudaFree(optr);
+        cudaFree(ocol);
+        return e;
+    }
+    g->d_out_ptr = optr;
+    g->d_out_col = ocol;
+    g->bytes += bytes;
+    return cudaSuccess;
+}
+
+// counts and pending tallies of a push-form sim from its current state
+cudaError_t push_reset(fs_sim* s)
+{
+    const fs_graph* g = s->g;
+    const size_t thr_pad = ((size_t)g->n_thr + 15) / 16 * 16;
+    cudaStream_t cs = s->stream;
+    cudaError_t e = cudaMemsetAsync(s->d_cnt8, 0, thr_pad, cs);
+    for (int q = 0; q < 2 && e == cudaSuccess; ++q)
+        e = cudaMemsetAsync(s->d_pd16[q], 0, thr_pad * sizeof(uint16_t), cs);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(s->d_hcnt, 0, sizeof(uint32_t) * std::max(g->n_m, 1), cs);
+    for (int q = 0; q < 2 && e == cudaSuccess; ++q)
+        e = cudaMemsetAsync(s->d_pd64[q], 0, sizeof(unsigned long long) * std::max(g->n_m, 1), cs);
+    if (e == cudaSuccess)
+        e = fs::launch_push_init(step_args(s, 0), cs, g->num_sms);
+    return e;
 }
 
 fs_status check_device_error(fs_sim* s)
@@ -543,9 +626,14 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
                 return fail(FS_EINVAL, "index node %d repeated", v[q]);
         }
     }
+    if (params->flags == FS_PRESSURE_PUSH && !push_available(g))
+        return fail(FS_EUNSUPPORTED, "FS_PRESSURE_PUSH needs in-degrees <= %d in the thread class (thread_max_deg %d)",
+                    fs::kMaxThreadDeg, g->t1);
     fs_sim* s = new fs_sim();
     s->g = g;
     s->p = *params;
+    s->pressure = (params->flags == FS_PRESSURE_GATHER || !push_available(g)) ? FS_PRESSURE_GATHER
+                                                                              : FS_PRESSURE_PUSH;
     s->M = to_model(*params);
     s->age_bytes = params->age_dtype == FS_AGE_F32 ? 4 : 2;
     const int64_t n = g->n;
@@ -570,8 +658,9 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
     }
     cudaStream_t cs = s->stream;
     const size_t words = ((size_t)(n >> 5) + 1 + 3) / 4 * 4;
-    S_CUDA(dev_alloc(&s->d_X, (size_t)n, nullptr));
-    S_CUDA(cudaMalloc(&s->d_A, (size_t)n * s->age_bytes));
+    const size_t n_pad = ((size_t)n + 15) / 16 * 16;   // whole 16-node groups for vector access
+    S_CUDA(dev_alloc(&s->d_X, n_pad, nullptr));
+    S_CUDA(cudaMalloc(&s->d_A, n_pad * s->age_bytes));
     S_CUDA(dev_alloc(&s->d_bm[0], words, nullptr));
     S_CUDA(dev_alloc(&s->d_bm[1], words, nullptr));
     S_CUDA(dev_alloc(&s->d_m_cnt, (size_t)std::max(g->n_m, 1), nullptr));
@@ -582,8 +671,8 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
     S_CUDA(dev_alloc(&s->d_ps, (size_t)fs::kPSTableN, nullptr));
     S_CUDA(cudaMemsetAsync(s->d_ptab, 0xff, sizeof(float2) * 2 * fs::kPTableN, cs));   // NaN ages: no entry
     S_CUDA(fs::launch_build_ptables(s->M, params->age_dtype, s->d_ptab, s->d_ps, cs));
-    S_CUDA(cudaMemsetAsync(s->d_X, 0, (size_t)n, cs));
-    S_CUDA(cudaMemsetAsync(s->d_A, 0, (size_t)n * s->age_bytes, cs));
+    S_CUDA(cudaMemsetAsync(s->d_X, 0, n_pad, cs));
+    S_CUDA(cudaMemsetAsync(s->d_A, 0, n_pad * s->age_bytes, cs));
     S_CUDA(cudaMemsetAsync(s->d_bm[0], 0, words * 4, cs));
     S_CUDA(cudaMemsetAsync(s->d_bm[1], 0, words * 4, cs));
     S_CUDA(cudaMemsetAsync(s->d_m_cnt, 0, sizeof(int32_t) * std::max(g->n_m, 1), cs));
@@ -596,6 +685,17 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
         S_CUDA(fs::launch_set_index(s->d_X, d_idx, n_index, g->d_inv, params->index_state, cs));
     }
     S_CUDA(fs::launch_refresh(s->d_X, (int)n, g->d_deg, s->d_bm[0], s->d_bm[1], s->d_ctl, cs));
+    if (s->pressure == FS_PRESSURE_PUSH) {
+        const size_t thr_pad = ((size_t)g->n_thr + 15) / 16 * 16;
+        S_CUDA(ensure_out_csr(g, cs));
+        S_CUDA(dev_alloc(&s->d_cnt8, thr_pad, nullptr));
+        S_CUDA(dev_alloc(&s->d_pd16[0], thr_pad, nullptr));
+        S_CUDA(dev_alloc(&s->d_pd16[1], thr_pad, nullptr));
+        S_CUDA(dev_alloc(&s->d_hcnt, (size_t)std::max(g->n_m, 1), nullptr));
+        S_CUDA(dev_alloc(&s->d_pd64[0], (size_t)std::max(g->n_m, 1), nullptr));
+        S_CUDA(dev_alloc(&s->d_pd64[1], (size_t)std::max(g->n_m, 1), nullptr));
+        S_CUDA(push_reset(s));
+    }
     S_CUDA(cudaStreamSynchronize(cs));
 #undef S_CUDA
     cudaFree(d_idx);
@@ -609,6 +709,8 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
 static cudaError_t launch_one_step(fs_sim* s, int j)
 {
     const fs::StepArgs a = step_args(s, j);
+    if (s->pressure == FS_PRESSURE_PUSH)
+        return fs::launch_push_step(a, s->p.age_dtype, s->stream, s->g->num_sms);
     if (s->g->smem_path)
         return fs::launch_step_smem(a, s->p.age_dtype, s->stream, s->g->num_sms);
     return fs::launch_step(a, s->p.age_dtype, s->stream, false);
@@ -869,7 +971,17 @@ fs_status fs_sim_set_state(fs_sim* s, const uint8_t* state, const void* age, int
     c.step = step;
     FS_CUDA(s, cudaMemcpy(s->d_ctl, &c, sizeof(c), cudaMemcpyHostToDevice));
     FS_CUDA(s, fs::launch_refresh(s->d_X, n, g->d_deg, s->d_bm[0], s->d_bm[1], s->d_ctl, s->stream));
+    if (s->pressure == FS_PRESSURE_PUSH)
+        FS_CUDA(s, push_reset(s));
     FS_CUDA(s, cudaStreamSynchronize(s->stream));
+    return FS_OK;
+}
+
+fs_status fs_sim_pressure_get(const fs_sim* s, int32_t* pressure)
+{
+    if (!s || !pressure)
+        return fail(FS_EINVAL, "NULL argument");
+    *pressure = s->pressure;
     return FS_OK;
 }
 

@@ -110,7 +110,20 @@ struct StepArgs {
     unsigned long long* deltas;   // [K][kDeltaFields]
     int32_t j;                    // step offset within the launch sequence
     int32_t n;
+    // push form of the pressure (fs_push.cu): per-node infectious in-neighbour
+    // counts kept up to date by +-1 pushes along the transposed CSR; pushes
+    // made at step k land in the pending words of parity k & 1
+    uint8_t* cnt8;                // [n_thr] counts of the thread class (in-degree <= 255)
+    uint16_t* pd16[2];            // [n_thr] pending pushes: +1 tally low byte, -1 tally high byte
+    uint32_t* hcnt;               // [n_m] counts of the merge class
+    unsigned long long* pd64[2];  // [n_m] pending pushes: +1 tally low word, -1 tally high word
+    const int64_t* out_ptr;       // [n + 1] transposed CSR: the nodes whose rows list node j
+    const int32_t* out_col;       // [nnz] internal ids
 };
+
+constexpr int kPushG = 8;                 // thread-class nodes per thread of the push step
+constexpr int kPushThreads = 256;
+constexpr int kPushCtasPerSm = 4;
 
 }  // namespace fs
 

@@ -33,6 +33,15 @@ cudaError_t launch_eval_hazard(const LawF& L, const float* tau, float* h, int64_
 cudaError_t launch_eval_uniforms(uint32_t key0, uint32_t key1, uint32_t rep, uint32_t step, const int32_t* nodes,
                                  float* u, int64_t n, cudaStream_t s);
 
+// fs_push.cu: one step with the pressure kept by pushes; the initial counts
+// (counts and pending tallies zeroed before); the transposed CSR of a graph
+// (fill = false: out-degrees into cursor; fill = true: rows via cursor)
+cudaError_t launch_push_step(const StepArgs& a, int age_dtype, cudaStream_t s, int num_sms);
+cudaError_t launch_push_init(const StepArgs& a, cudaStream_t s, int num_sms);
+cudaError_t launch_transpose(const int64_t* sell_off, const int32_t* sell_col, const int32_t* deg, int n_thr,
+                             const int64_t* m_ptr, const int32_t* m_col, int n_m, int n,
+                             unsigned long long* cursor, int32_t* out_col, bool fill, cudaStream_t s);
+
 // fs_pack.cu
 // one step of the segments of replicate-width class cls (R_pad = 8 << cls)
 cudaError_t launch_pack_step(const PackArgs& a, int cls, int age_dtype, int grid, cudaStream_t s);

@@ -32,6 +32,10 @@ struct fs_graph {
     uint32_t bm_bytes = 0;         // infectious bitmap bytes, rounded up to 16
     bool smem_path = false;        // bitmap small enough to be staged in shared memory
     uint32_t smem_min_s = 0;       // S count from which staging pays off
+    // transposed CSR (internal ids) for the push form of the pressure, built
+    // on the first push-form sim of the graph
+    int64_t* d_out_ptr = nullptr;  // [n + 1]
+    int32_t* d_out_col = nullptr;  // [nnz]
     int refs = 0;
     bool failed = false;
 };
@@ -50,6 +54,12 @@ struct fs_sim {
     unsigned long long* d_deltas = nullptr;
     float2* d_ptab = nullptr;
     float* d_ps = nullptr;
+    // push form of the pressure (pressure == FS_PRESSURE_PUSH)
+    int pressure = FS_PRESSURE_GATHER;
+    uint8_t* d_cnt8 = nullptr;
+    uint16_t* d_pd16[2] = {nullptr, nullptr};
+    uint32_t* d_hcnt = nullptr;
+    unsigned long long* d_pd64[2] = {nullptr, nullptr};
     uint32_t* d_counts = nullptr;
     int64_t counts_cap = 0;
     cudaGraphExec_t gexec = nullptr;

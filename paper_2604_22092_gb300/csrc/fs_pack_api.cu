@@ -177,6 +177,8 @@ fs_status fs_ens_create(fs_graph* g, const fs_sim_params* params, int32_t n_real
         fs_status st = fsapi::check_params(params + r);
         if (st != FS_OK)
             return st;
+        if (params[r].flags == FS_PRESSURE_PUSH)
+            return fail(FS_EUNSUPPORTED, "fs_ens_create: packed ensembles use the gather form of the pressure");
         if (params[r].model != params[0].model || params[r].age_dtype != params[0].age_dtype ||
             params[r].index_state != params[0].index_state)
             return fail(FS_EINVAL, "fs_ens_create: realisations must share model, age_dtype and index_state");

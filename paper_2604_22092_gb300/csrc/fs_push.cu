@@ -1,0 +1,730 @@
+// fs_push.cu -- the fused renewal step (FlashSpread, arXiv 2604.22092,
+// Algorithm 3 at a fixed step) with the infection pressure of S nodes kept up
+// to date by pushes instead of being recounted by a gather every step.
+//
+// With unit weights and constant shedding (Eq. 3 with s = 1), the pressure
+// on an S node i is beta times c_i, the number of its in-neighbours in I.
+// The gather form recounts c_i for every S node at every step, although c_i
+// only changes when an in-neighbour enters or leaves I, which each node does
+// at most once per epidemic. Here each node keeps c_i; a node that enters I
+// adds 1 to the count of every node whose row lists it (the transposed CSR,
+// built once per graph), and a node that leaves I subtracts 1. Counts are
+// integers, so they equal the gathered counts exactly, in any order.
+//
+// One launch per step stays race-free: counts are read during step k while
+// the pushes made during step k must only be seen from step k + 1 on. Pushes
+// therefore go to a pending word of parity k & 1; during step k an S node
+// adds the pending word of parity (k - 1) & 1 (the pushes of step k - 1)
+// into its count and clears it, and no thread pushes into that parity during
+// step k. A pending word holds separate +1 and -1 tallies so that atomic
+// adds never borrow across fields:
+//   thread class (in-degree <= 255): count u8; pending u16 per node, +1
+//     tally in the low byte, -1 tally in the high byte, added through the
+//     32-bit word that holds it;
+//   merge class: count u32; pending u64, +1 tally in the low 32 bits, -1
+//     tally in the high 32 bits.
+// A tally never exceeds the node's in-degree: S nodes clear theirs every
+// step, and any node receives at most one +1 and one -1 per in-neighbour
+// over a whole run.
+//
+// The step itself (probability, Philox draw, transition, renewal age,
+// counts) is the same code as the gather form's (fs_device.cuh), so results
+// are identical to it bit for bit.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "fs_device.cuh"
+#include "fs_launch.h"
+
+namespace fs {
+
+namespace {
+
+constexpr uint32_t kFull = 0xffffffffu;
+
+__device__ __noinline__ float p_direct_p(const ModelF& M, int x, float age)
+{
+    return p_of_rate(M, hazard(x == kE ? M.lat : M.inf, age));
+}
+
+// Bernoulli probability of one node this step, from the per-sim tables built
+// at init by the same FP32 code (identical bits to direct evaluation)
+__device__ __forceinline__ float node_p_push(const StepArgs& a, int x, float age, uint32_t c)
+{
+    if (x == kS) {
+        if (c == 0u)
+            return 0.0f;
+        if (c < (uint32_t)kPSTableN)
+            return __ldg(a.ps + c);
+        return p_of_rate(a.M, __fmul_rn(a.M.beta, (float)c));
+    }
+    if (x == kE || x == kI) {
+        const int n = __float2int_rn(__fmul_rn(age, a.M.inv_dt));
+        if ((unsigned)n < (unsigned)kPTableN) {
+            const float2 e = __ldg(a.ptab + (x == kI ? kPTableN : 0) + n);
+            if (e.x == age)
+                return e.y;
+        }
+        return p_direct_p(a.M, x, age);
+    }
+    return 0.0f;
+}
+
+struct PushDeltas {
+    uint32_t fS = 0, fE = 0, fI = 0, dS = 0;
+};
+
+// successor compartment and renewal age of one node after its decision
+__device__ __forceinline__ int next_state(const StepArgs& a, int x, bool fired)
+{
+    if (!fired)
+        return x;
+    return (x == kS) ? (a.M.model == kSEIR ? kE : kI) : (x + 1);
+}
+
+// +1 / -1 into the pending tally of node j (parity par)
+__device__ __forceinline__ void push_pending(const StepArgs& a, uint32_t par, uint32_t j, bool minus)
+{
+    if (j < (uint32_t)a.n_thr) {
+        unsigned int* w = reinterpret_cast<unsigned int*>(a.pd16[par]) + (j >> 1);
+        atomicAdd(w, (minus ? 0x100u : 0x1u) << ((j & 1u) << 4));
+    } else if (j < (uint32_t)a.n) {
+        atomicAdd(a.pd64[par] + (j - (uint32_t)a.n_thr), minus ? (1ull << 32) : 1ull);
+    }
+}
+
+// +1 straight into the count of node j (initial counts)
+__device__ __forceinline__ void push_count(const StepArgs& a, uint32_t j)
+{
+    if (j < (uint32_t)a.n_thr)
+        atomicAdd(reinterpret_cast<unsigned int*>(a.cnt8) + (j >> 2), 1u << ((j & 3u) << 3));
+    else if (j < (uint32_t)a.n)
+        atomicAdd(a.hcnt + (j - (uint32_t)a.n_thr), 1u);
+}
+
+template <bool INIT>
+__device__ __forceinline__ void push_one(const StepArgs& a, uint32_t par, uint32_t j, bool minus)
+{
+    if constexpr (INIT)
+        push_count(a, j);
+    else
+        push_pending(a, par, j, minus);
+}
+
+// eight ages of storage type AgeT as FP32 values
+template <typename AgeT> struct AgeVec8;
+template <> struct AgeVec8<float> {
+    static __device__ __forceinline__ void load(const float* p, float (&f)[8])
+    {
+        const float4 v0 = *reinterpret_cast<const float4*>(p), v1 = *reinterpret_cast<const float4*>(p + 4);
+        f[0] = v0.x; f[1] = v0.y; f[2] = v0.z; f[3] = v0.w;
+        f[4] = v1.x; f[5] = v1.y; f[6] = v1.z; f[7] = v1.w;
+    }
+    static __device__ __forceinline__ void store(float* p, const float (&f)[8])
+    {
+        *reinterpret_cast<float4*>(p) = make_float4(f[0], f[1], f[2], f[3]);
+        *reinterpret_cast<float4*>(p + 4) = make_float4(f[4], f[5], f[6], f[7]);
+    }
+};
+__device__ __forceinline__ __half bits_to(const __half*, unsigned short b) { return __ushort_as_half(b); }
+__device__ __forceinline__ __nv_bfloat16 bits_to(const __nv_bfloat16*, unsigned short b)
+{
+    return __ushort_as_bfloat16(b);
+}
+__device__ __forceinline__ unsigned short to_bits(__half h) { return __half_as_ushort(h); }
+__device__ __forceinline__ unsigned short to_bits(__nv_bfloat16 h) { return __bfloat16_as_ushort(h); }
+
+template <typename H> struct AgeVec8Half {
+    static __device__ __forceinline__ void load(const H* p, float (&f)[8])
+    {
+        const uint4 v = *reinterpret_cast<const uint4*>(p);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            f[2 * q] = AgeIO<H>::load(bits_to(p, (unsigned short)(w[q] & 0xffffu)));
+            f[2 * q + 1] = AgeIO<H>::load(bits_to(p, (unsigned short)(w[q] >> 16)));
+        }
+    }
+    static __device__ __forceinline__ void store(H* p, const float (&f)[8])
+    {
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            w[q] = (uint32_t)to_bits(AgeIO<H>::store(f[2 * q])) |
+                   ((uint32_t)to_bits(AgeIO<H>::store(f[2 * q + 1])) << 16);
+        *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+};
+template <> struct AgeVec8<__half> : AgeVec8Half<__half> {};
+template <> struct AgeVec8<__nv_bfloat16> : AgeVec8Half<__nv_bfloat16> {};
+
+__device__ __forceinline__ uint32_t byte_of(uint2 v, int u)
+{
+    return ((u < 4 ? v.x : v.y) >> (8 * (u & 3))) & 0xffu;
+}
+
+__device__ __forceinline__ void set_byte(uint2& v, int u, uint32_t b)
+{
+    const uint32_t sh = 8 * (u & 3), m = ~(0xffu << sh);
+    if (u < 4)
+        v.x = (v.x & m) | (b << sh);
+    else
+        v.y = (v.y & m) | (b << sh);
+}
+
+// What one lane carries from the preparation of its item to the application
+// of the Bernoulli decisions: a group of kPushG thread-class nodes or one
+// merge-class node.
+struct Item {
+    int kind;            // 0 = none, 1 = group, 2 = merge-class node
+    int base;            // first node of the item
+    int nv;              // nodes of the group inside the thread class
+    uint2 xs, xs0;       // states (kR for skipped nodes) and the bytes as loaded
+    uint2 nc;            // counts after folding in the pending tallies
+    bool anyEI, clear;   // ages were loaded; pending tallies to clear
+    float age[kPushG];
+    float p[kPushG];
+    uint32_t need;       // bit u: node base + u draws a uniform (p > 0)
+};
+
+enum { kItemNone = 0, kItemGroup = 1, kItemHub = 2 };
+
+// Eight consecutive thread-class nodes i0 .. i0+7 (i0 a multiple of 8):
+// vector loads of states, then of counts, pending tallies and ages; the
+// probability-table loads of all eight nodes issued together. Nodes at or
+// beyond n_thr (a partial last group) are treated as R.
+template <typename AgeT>
+__device__ __forceinline__ void group_prepare(const StepArgs& a, uint32_t par, int i0, Item& it)
+{
+    it.kind = kItemGroup;
+    it.base = i0;
+    it.need = 0u;
+    it.anyEI = false;
+    it.clear = false;
+    it.nv = min(kPushG, a.n_thr - i0);
+    uint2 xs = *reinterpret_cast<const uint2*>(a.X + i0);
+    it.xs0 = xs;
+    if (it.nv < kPushG) {
+#pragma unroll
+        for (int u = 0; u < kPushG; ++u)
+            if (u >= it.nv)
+                set_byte(xs, u, kR);
+    }
+    it.xs = xs;
+    it.nc = make_uint2(0u, 0u);
+#pragma unroll
+    for (int u = 0; u < kPushG; ++u) {
+        it.age[u] = 0.0f;
+        it.p[u] = 0.0f;
+    }
+    // compartments are 0..3, so a byte is R (3) in both words' AND only if
+    // it is 3 in both; S bytes are the zero bytes
+    if ((xs.x & xs.y) == 0x03030303u)
+        return;
+    const bool anyS = (__vcmpeq4(xs.x, 0u) | __vcmpeq4(xs.y, 0u)) != 0u;
+    const uint32_t ei_x = __vcmpeq4(xs.x, 0x01010101u) | __vcmpeq4(xs.x, 0x02020202u);
+    const uint32_t ei_y = __vcmpeq4(xs.y, 0x01010101u) | __vcmpeq4(xs.y, 0x02020202u);
+    it.anyEI = (ei_x | ei_y) != 0u;
+    uint2 c8 = make_uint2(0u, 0u);
+    uint4 pd = make_uint4(0u, 0u, 0u, 0u);
+    if (anyS) {
+        c8 = *reinterpret_cast<const uint2*>(a.cnt8 + i0);
+        pd = *reinterpret_cast<const uint4*>(a.pd16[par ^ 1u] + i0);
+    }
+    const AgeT* __restrict__ A = static_cast<const AgeT*>(a.A) + i0;
+    if (it.anyEI) {
+        if (it.nv == kPushG) {
+            AgeVec8<AgeT>::load(A, it.age);
+        } else {
+#pragma unroll
+            for (int u = 0; u < kPushG; ++u)
+                if (u < it.nv)
+                    it.age[u] = AgeIO<AgeT>::load(A[u]);
+        }
+    }
+    it.clear = (pd.x | pd.y | pd.z | pd.w) != 0u;
+    const uint32_t pdw[4] = {pd.x, pd.y, pd.z, pd.w};
+    // counts (thread-class counts are <= 255, inside the S table) and the
+    // table lookups, resolved after every load of this phase has been issued
+    uint2 nc = c8;
+#pragma unroll
+    for (int u = 0; u < kPushG; ++u) {
+        const int x = (int)byte_of(xs, u);
+        const bool isS = x == kS, isEI = x == kE || x == kI;
+        const uint32_t d = (pdw[u >> 1] >> ((u & 1) << 4)) & 0xffffu;
+        const uint32_t c = isS ? byte_of(c8, u) + (d & 0xffu) - (d >> 8) : 0u;
+        if (isS)
+            set_byte(nc, u, c);
+        const int n = __float2int_rn(__fmul_rn(it.age[u], a.M.inv_dt));
+        float2 e = make_float2(-1.0f, 0.0f);                  // no entry: never equals an age
+        if (isEI && (unsigned)n < (unsigned)kPTableN)
+            e = __ldg(a.ptab + (x == kI ? kPTableN : 0) + n);
+        float ps = 0.0f;
+        if (isS && c != 0u)
+            ps = __ldg(a.ps + c);
+        it.p[u] = isS ? ps : (isEI ? (e.x == it.age[u] ? e.y : -1.0f) : 0.0f);
+    }
+    it.nc = nc;
+#pragma unroll
+    for (int u = 0; u < kPushG; ++u) {
+        if (it.p[u] < 0.0f)                                   // age off the tabulated sequence
+            it.p[u] = p_direct_p(a.M, (int)byte_of(xs, u), it.age[u]);
+        if (it.p[u] > 0.0f)
+            it.need |= 1u << u;
+    }
+}
+
+// one merge-class node: its count and pending tallies are folded in here
+template <typename AgeT>
+__device__ __forceinline__ void hub_prepare(const StepArgs& a, uint32_t par, int i, Item& it)
+{
+    it.kind = kItemHub;
+    it.base = i;
+    it.need = 0u;
+    it.anyEI = false;
+    it.clear = false;
+    it.nv = 1;
+    const int x = a.X[i];
+    it.xs = make_uint2((uint32_t)x, 0u);
+    it.xs0 = it.xs;
+    it.age[0] = 0.0f;
+    it.p[0] = 0.0f;
+    if (x == kR)
+        return;
+    const int r = i - a.n_thr;
+    uint32_t c = 0u;
+    if (x == kS) {
+        unsigned long long* pr = a.pd64[par ^ 1u] + r;
+        const unsigned long long d = *pr;
+        c = a.hcnt[r];
+        if (d) {
+            c = c + (uint32_t)(d & 0xffffffffull) - (uint32_t)(d >> 32);
+            a.hcnt[r] = c;
+            *pr = 0ull;
+        }
+    }
+    if (x == kE || x == kI)
+        it.age[0] = AgeIO<AgeT>::load(static_cast<const AgeT*>(a.A)[i]);
+    it.p[0] = node_p_push(a, x, it.age[0], c);
+    it.need = it.p[0] > 0.0f ? 1u : 0u;
+}
+
+// Bernoulli decisions of a whole warp: every lane queues (original id, p) of
+// its nodes that draw, then the lanes share the queue evenly, so a warp runs
+// ceil(draws / 32) rounds of Philox instead of one round per node position
+// in which any lane draws. Every lane of the warp must call this. Returns the
+// lane's fired mask (bit u = node base + u fired).
+struct DrawQ {
+    uint32_t node[kPushThreads * kPushG];
+    float p[kPushThreads * kPushG];
+    uint8_t fired[kPushThreads * kPushG];
+};
+
+__device__ __forceinline__ uint32_t warp_draws(const StepArgs& a, uint32_t step, const Item& it, DrawQ& q)
+{
+    const int lane = threadIdx.x & 31;
+    const int wbase = (threadIdx.x >> 5) * (32 * kPushG);
+    const uint32_t cnt = (uint32_t)__popc(it.need);
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o)
+            incl += y;
+    }
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    if (total == 0u)
+        return 0u;
+    const int off = wbase + (int)(incl - cnt);
+    {
+        int j = off;
+#pragma unroll
+        for (int u = 0; u < kPushG; ++u) {
+            if ((it.need >> u) & 1u) {
+                const int node = it.base + u;
+                q.node[j] = a.perm ? (uint32_t)__ldg(a.perm + node) : (uint32_t)node;
+                q.p[j] = it.p[u];
+                ++j;
+            }
+        }
+    }
+    __syncwarp();
+    for (int e = lane; e < (int)total; e += 32) {
+        const float u = uniform24(a.M.key0, a.M.key1, a.M.rep, step, q.node[wbase + e]);
+        q.fired[wbase + e] = u < q.p[wbase + e] ? 1 : 0;
+    }
+    __syncwarp();
+    uint32_t fired = 0u;
+    int j = off;
+#pragma unroll
+    for (int u = 0; u < kPushG; ++u) {
+        if ((it.need >> u) & 1u) {
+            fired |= (uint32_t)q.fired[j] << u;
+            ++j;
+        }
+    }
+    __syncwarp();     // the queue is reused by the warp's next item
+    return fired;
+}
+
+// transitions, renewal ages, in-place stores, push events and deltas
+template <typename AgeT>
+__device__ __forceinline__ void item_apply(const StepArgs& a, uint32_t par, Item& it, uint32_t fired,
+                                           uint32_t& ev, uint32_t& neg, PushDeltas& ld)
+{
+    if (it.kind == kItemNone)
+        return;
+    const int i0 = it.base;
+    AgeT* __restrict__ A = static_cast<AgeT*>(a.A) + i0;
+    if (it.kind == kItemHub) {
+        const int x = (int)it.xs.x;
+        if (x == kR)
+            return;
+        const bool f = fired & 1u;
+        const int y = next_state(a, x, f);
+        if (y != x)
+            a.X[i0] = (uint8_t)y;
+        if (f || x == kE || x == kI)
+            A[0] = AgeIO<AgeT>::store(f ? 0.0f : __fadd_rn(it.age[0], a.M.dt));
+        if ((y == kI) != (x == kI)) {
+            ev = 1u;
+            neg = x == kI ? 1u : 0u;
+        }
+        if (f) {
+            ld.fS += x == kS;
+            ld.fE += x == kE;
+            ld.fI += x == kI;
+            if (x == kS)
+                ld.dS += (uint32_t)__ldg(a.deg + i0);
+        }
+        return;
+    }
+    const uint2 xs = it.xs;
+    if ((xs.x & xs.y) == 0x03030303u)
+        return;
+    uint2 nx = xs;
+    uint32_t firedS = 0u;
+#pragma unroll
+    for (int u = 0; u < kPushG; ++u) {
+        const int x = (int)byte_of(xs, u);
+        if (x == kR)
+            continue;
+        const bool f = (fired >> u) & 1u;
+        const int y = next_state(a, x, f);
+        it.age[u] = f ? 0.0f : ((x == kE || x == kI) ? __fadd_rn(it.age[u], a.M.dt) : 0.0f);
+        if (y != x)
+            set_byte(nx, u, (uint32_t)y);
+        if ((y == kI) != (x == kI)) {
+            ev |= 1u << u;
+            if (x == kI)
+                neg |= 1u << u;
+        }
+        if (f) {
+            ld.fS += x == kS;
+            ld.fE += x == kE;
+            ld.fI += x == kI;
+            if (x == kS)
+                firedS |= 1u << u;
+        }
+    }
+    if (firedS) {
+#pragma unroll
+        for (int u = 0; u < kPushG; ++u)
+            if ((firedS >> u) & 1u)
+                ld.dS += (uint32_t)__ldg(a.deg + i0 + u);
+    }
+    if (it.nv == kPushG) {
+        if (nx.x != it.xs0.x || nx.y != it.xs0.y)
+            *reinterpret_cast<uint2*>(a.X + i0) = nx;
+        if (it.anyEI)
+            AgeVec8<AgeT>::store(A, it.age);
+    } else {
+#pragma unroll
+        for (int u = 0; u < kPushG; ++u) {
+            if (u < it.nv) {
+                const uint32_t y = byte_of(nx, u);
+                if (y != byte_of(xs, u))
+                    a.X[i0 + u] = (uint8_t)y;
+                if (it.anyEI)
+                    A[u] = AgeIO<AgeT>::store(it.age[u]);
+            }
+        }
+    }
+    // the pending tallies just folded in are cleared for the pushes of the
+    // next step; counts and tallies of the thread class are padded to whole
+    // groups, so these stores never touch another class
+    if (it.clear) {
+        *reinterpret_cast<uint2*>(a.cnt8 + i0) = it.nc;
+        *reinterpret_cast<uint4*>(a.pd16[par ^ 1u] + i0) = make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// CTA-wide pushes. Threads append their push events (node id, bit 31 = the
+// node left I) to a shared list; per chunk of kPushThreads events one thread
+// per event reads the transposed row bounds, a block scan of the row lengths
+// flattens every event's edges into one index range, and all threads of the
+// CTA issue the column loads and atomic adds of that range together, so a
+// chunk costs two dependent memory round trips however many events it holds.
+// ---------------------------------------------------------------------------
+constexpr int kPushEvCap = kPushThreads * kPushG;   // events one item round can produce
+
+struct PushSmem {
+    uint32_t ev[kPushEvCap];                  // node | (1u << 31) when it left I
+    int64_t lo[kPushThreads];                 // first out-edge of each event of the chunk
+    int64_t off[kPushThreads + 1];            // exclusive prefix of the chunk's row lengths
+    int64_t wsum[kPushThreads / 32];
+    uint32_t nev;
+};
+
+// exclusive block scan of one int64 per thread; returns the total
+__device__ __forceinline__ int64_t block_scan_excl(int64_t v, int64_t* out, int64_t* wsum)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o)
+            x += y;
+    }
+    if (lane == 31)
+        wsum[warp] = x;
+    __syncthreads();
+    int64_t before = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < kPushThreads / 32; ++w) {
+        const int64_t t = wsum[w];
+        before += w < warp ? t : 0;
+        total += t;
+    }
+    out[tid] = before + x - v;
+    return total;
+}
+
+template <bool INIT>
+__device__ __forceinline__ void cta_push(const StepArgs& a, uint32_t par, PushSmem& sm)
+{
+    const int tid = threadIdx.x;
+    const int nev = (int)sm.nev;
+    for (int c0 = 0; c0 < nev; c0 += kPushThreads) {
+        const int e = c0 + tid;
+        int64_t lo = 0, len = 0;
+        if (e < nev) {
+            const int node = (int)(sm.ev[e] & 0x7fffffffu);
+            lo = __ldg(a.out_ptr + node);
+            len = __ldg(a.out_ptr + node + 1) - lo;
+        }
+        sm.lo[tid] = lo;
+        const int64_t total = block_scan_excl(len, sm.off, sm.wsum);
+        if (tid == 0)
+            sm.off[kPushThreads] = total;
+        __syncthreads();
+        const int ne = min(kPushThreads, nev - c0);
+        for (int64_t q = tid; q < total; q += kPushThreads) {
+            // the event whose edge range holds q: largest k with off[k] <= q
+            int l = 0, h = ne - 1;
+            while (l < h) {
+                const int m = (l + h + 1) >> 1;
+                if (sm.off[m] <= q)
+                    l = m;
+                else
+                    h = m - 1;
+            }
+            const uint32_t j = (uint32_t)__ldg(a.out_col + sm.lo[l] + (q - sm.off[l]));
+            push_one<INIT>(a, par, j, (sm.ev[c0 + l] >> 31) != 0u);
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ void append_events(PushSmem& sm, uint32_t ev, uint32_t neg, int base)
+{
+    if (ev) {
+        uint32_t pos = atomicAdd(&sm.nev, (uint32_t)__popc(ev));
+        while (ev) {
+            const int u = __ffs(ev) - 1;
+            ev &= ev - 1u;
+            sm.ev[pos++] = (uint32_t)(base + u) | (((neg >> u) & 1u) << 31);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// One whole step: items are groups of kPushG thread-class nodes, then single
+// merge-class nodes; CTAs stride over rounds of kPushThreads items and push
+// after each round. Per-step deltas as in the gather form.
+// ---------------------------------------------------------------------------
+template <typename AgeT>
+__global__ void __launch_bounds__(kPushThreads, kPushCtasPerSm) push_step_kernel(const __grid_constant__ StepArgs a)
+{
+    __shared__ unsigned long long s_delta[kDeltaFields];
+    __shared__ PushSmem sm;
+    __shared__ DrawQ dq;
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid < kDeltaFields)
+        s_delta[tid] = 0ull;
+    if (tid == 0)
+        sm.nev = 0u;
+    const int64_t k = a.ctl->step + a.j;
+    const uint32_t par = (uint32_t)(k & 1);
+    __syncthreads();
+    PushDeltas ld;
+    const int64_t n_grp = ((int64_t)a.n_thr + kPushG - 1) / kPushG;
+    const int64_t total = n_grp + a.n_m;
+    const int64_t stride = (int64_t)gridDim.x * kPushThreads;
+    for (int64_t t0 = (int64_t)blockIdx.x * kPushThreads; t0 < total; t0 += stride) {
+        const int64_t t = t0 + tid;
+        Item it;
+        it.kind = kItemNone;
+        it.base = 0;
+        it.need = 0u;
+        if (t < n_grp)
+            group_prepare<AgeT>(a, par, (int)(t * kPushG), it);
+        else if (t < total)
+            hub_prepare<AgeT>(a, par, a.n_thr + (int)(t - n_grp), it);
+        const uint32_t fired = warp_draws(a, (uint32_t)k, it, dq);
+        uint32_t ev = 0u, neg = 0u;
+        item_apply<AgeT>(a, par, it, fired, ev, neg, ld);
+        append_events(sm, ev, neg, it.base);
+        __syncthreads();
+        if (sm.nev) {            // uniform: read after the barrier
+            cta_push<false>(a, par, sm);
+            if (tid == 0)
+                sm.nev = 0u;
+            __syncthreads();
+        }
+    }
+    const uint32_t fs_ = __reduce_add_sync(kFull, ld.fS), fe = __reduce_add_sync(kFull, ld.fE);
+    const uint32_t fi = __reduce_add_sync(kFull, ld.fI), ds = __reduce_add_sync(kFull, ld.dS);
+    if (lane == 0) {
+        if (fs_) atomicAdd(&s_delta[0], (unsigned long long)fs_);
+        if (fe) atomicAdd(&s_delta[1], (unsigned long long)fe);
+        if (fi) atomicAdd(&s_delta[2], (unsigned long long)fi);
+        if (ds) atomicAdd(&s_delta[3], (unsigned long long)ds);
+    }
+    __syncthreads();
+    if (tid < kDeltaFields) {
+        const unsigned long long v = s_delta[tid];
+        if (v)
+            atomicAdd(a.deltas + (int64_t)a.j * kDeltaFields + tid, v);
+    }
+}
+
+// Initial counts (after init or set_state; counts and tallies zeroed): every
+// node in I pushes +1 straight into the counts of its out-neighbours.
+__global__ void __launch_bounds__(kPushThreads) push_init_kernel(const __grid_constant__ StepArgs a)
+{
+    __shared__ PushSmem sm;
+    const int tid = threadIdx.x;
+    if (tid == 0)
+        sm.nev = 0u;
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * kPushThreads;
+    for (int64_t t0 = (int64_t)blockIdx.x * kPushThreads; t0 < a.n; t0 += stride) {
+        const int64_t i = t0 + tid;
+        append_events(sm, (i < a.n && a.X[i] == kI) ? 1u : 0u, 0u, (int)i);
+        __syncthreads();
+        if (sm.nev) {
+            cta_push<true>(a, 0u, sm);
+            if (tid == 0)
+                sm.nev = 0u;
+            __syncthreads();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Transposed CSR of a graph in internal ids, from its SELL-32 blocks (thread
+// class: row i's entries are t < deg(i) of its lane) and merge-class CSR:
+// out_deg[j] = number of rows listing j, then (after a scan) every row i
+// appends itself to the out-row of each j it lists. The order inside an
+// out-row is unspecified; pushes commute, so it does not matter.
+// ---------------------------------------------------------------------------
+template <bool FILL>
+__global__ void transpose_kernel(const int64_t* __restrict__ sell_off, const int32_t* __restrict__ sell_col,
+                                 const int32_t* __restrict__ deg, int n_thr, const int64_t* __restrict__ m_ptr,
+                                 const int32_t* __restrict__ m_col, int n_m, int n,
+                                 unsigned long long* __restrict__ cursor, int32_t* __restrict__ out_col)
+{
+    const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    auto emit = [&](int j, int i) {
+        if ((unsigned)j >= (unsigned)n)     // padding (never inside a row)
+            return;
+        const unsigned long long pos = atomicAdd(cursor + j, 1ull);
+        if constexpr (FILL)
+            out_col[pos] = i;
+    };
+    if (gt < n_thr) {
+        const int i = (int)gt;
+        const int64_t off = sell_off[i >> 5] + (i & 31);
+        const int d = deg[i];
+        for (int t = 0; t < d; ++t)
+            emit(sell_col[off + 32 * (int64_t)t], i);
+    } else {
+        // merge-class rows: 32 consecutive threads per row, striding over it
+        const int64_t w = (gt - n_thr) >> 5;
+        const int l = (int)((gt - n_thr) & 31);
+        if (w < n_m) {
+            const int r = (int)w;
+            for (int64_t e = m_ptr[r] + l; e < m_ptr[r + 1]; e += 32)
+                emit(m_col[e], n_thr + r);
+        }
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+template <typename AgeT>
+static cudaError_t launch_push_step_t(const StepArgs& a, cudaStream_t s, int num_sms)
+{
+    const int64_t items = ((int64_t)a.n_thr + kPushG - 1) / kPushG + a.n_m;
+    const int64_t need = (items + kPushThreads - 1) / kPushThreads;
+    const int64_t cap = (int64_t)num_sms * kPushCtasPerSm;
+    const int grid = (int)std::max<int64_t>(1, std::min(need, cap));
+    push_step_kernel<AgeT><<<grid, kPushThreads, 0, s>>>(a);
+    g_launch_count += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_push_step(const StepArgs& a, int age_dtype, cudaStream_t s, int num_sms)
+{
+    switch (age_dtype) {
+    case kAgeF16: return launch_push_step_t<__half>(a, s, num_sms);
+    case kAgeBF16: return launch_push_step_t<__nv_bfloat16>(a, s, num_sms);
+    default: return launch_push_step_t<float>(a, s, num_sms);
+    }
+}
+
+cudaError_t launch_push_init(const StepArgs& a, cudaStream_t s, int num_sms)
+{
+    const int64_t need = ((int64_t)a.n + 255) / 256;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms * 8));
+    push_init_kernel<<<grid, kPushThreads, 0, s>>>(a);
+    g_launch_count += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transpose(const int64_t* sell_off, const int32_t* sell_col, const int32_t* deg, int n_thr,
+                             const int64_t* m_ptr, const int32_t* m_col, int n_m, int n,
+                             unsigned long long* cursor, int32_t* out_col, bool fill, cudaStream_t s)
+{
+    const int64_t threads = (int64_t)n_thr + (int64_t)n_m * 32;
+    if (threads == 0)
+        return cudaSuccess;
+    const unsigned blocks = (unsigned)((threads + 255) / 256);
+    if (fill)
+        transpose_kernel<true><<<blocks, 256, 0, s>>>(sell_off, sell_col, deg, n_thr, m_ptr, m_col, n_m, n, cursor,
+                                                      out_col);
+    else
+        transpose_kernel<false><<<blocks, 256, 0, s>>>(sell_off, sell_col, deg, n_thr, m_ptr, m_col, n_m, n, cursor,
+                                                       nullptr);
+    g_launch_count += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace fs

@@ -294,6 +294,10 @@ fs_status fs_server_submit(fs_server* s, fs_graph* g, const fs_sim_params* scena
             delete q;
             return st;
         }
+        if (p.flags == FS_PRESSURE_PUSH) {
+            delete q;
+            return fail(FS_EUNSUPPORTED, "fs_server_submit: served ensembles use the gather form of the pressure");
+        }
         if (sc > 0 && (p.model != scenarios[0].model || p.index_state != scenarios[0].index_state)) {
             delete q;
             return fail(FS_EINVAL, "fs_server_submit: scenarios must share model and index_state");

@@ -55,6 +55,7 @@ fs_sim_params trial_params()
     p.dt = 0.1;
     p.seed = 0x5eed;
     p.index_state = FS_E;
+    p.flags = FS_PRESSURE_GATHER;   // the class split is what the gather traverses
     return p;
 }
 
