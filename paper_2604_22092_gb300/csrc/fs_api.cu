@@ -304,7 +304,7 @@ cudaError_t ensure_out_csr(fs_graph* g, cudaStream_t st)
 cudaError_t push_reset(fs_sim* s)
 {
     const fs_graph* g = s->g;
-    const size_t thr_pad = ((size_t)g->n_thr + 15) / 16 * 16;
+    const size_t thr_pad = ((size_t)g->n_thr + 15) / 16 * 16 + 16;
     cudaStream_t cs = s->stream;
     cudaError_t e = cudaMemsetAsync(s->d_cnt8, 0, thr_pad, cs);
     for (int q = 0; q < 2 && e == cudaSuccess; ++q)
@@ -658,7 +658,9 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
     }
     cudaStream_t cs = s->stream;
     const size_t words = ((size_t)(n >> 5) + 1 + 3) / 4 * 4;
-    const size_t n_pad = ((size_t)n + 15) / 16 * 16;   // whole 16-node groups for vector access
+    // whole 16-node groups for vector access, plus 16 nodes for the push
+    // step's rounded-up L2 prefetch ranges
+    const size_t n_pad = ((size_t)n + 15) / 16 * 16 + 16;
     S_CUDA(dev_alloc(&s->d_X, n_pad, nullptr));
     S_CUDA(cudaMalloc(&s->d_A, n_pad * s->age_bytes));
     S_CUDA(dev_alloc(&s->d_bm[0], words, nullptr));
@@ -686,7 +688,7 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
     }
     S_CUDA(fs::launch_refresh(s->d_X, (int)n, g->d_deg, s->d_bm[0], s->d_bm[1], s->d_ctl, cs));
     if (s->pressure == FS_PRESSURE_PUSH) {
-        const size_t thr_pad = ((size_t)g->n_thr + 15) / 16 * 16;
+        const size_t thr_pad = ((size_t)g->n_thr + 15) / 16 * 16 + 16;
         S_CUDA(ensure_out_csr(g, cs));
         S_CUDA(dev_alloc(&s->d_cnt8, thr_pad, nullptr));
         S_CUDA(dev_alloc(&s->d_pd16[0], thr_pad, nullptr));

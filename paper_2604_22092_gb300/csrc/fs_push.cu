@@ -173,6 +173,19 @@ __device__ __forceinline__ void set_byte(uint2& v, int u, uint32_t b)
         v.y = (v.y & m) | (b << sh);
 }
 
+// Per-warp shared scratch of the step: probabilities by node slot (lane * 8 +
+// u), the queue of draws (original node id and slot), decisions by slot, and
+// the warp's push events.
+constexpr int kWarpSlots = 32 * kPushG;
+
+struct WarpScratch {
+    float p[kWarpSlots];          // p of the node in slot lane * kPushG + u
+    uint32_t qnode[kWarpSlots];   // draw queue: original node ids
+    uint16_t qslot[kWarpSlots];   // draw queue: slots
+    uint8_t fired[kWarpSlots];    // decision by slot
+    uint32_t ev[kWarpSlots];      // push events: node | (1u << 31) when it left I
+};
+
 // What one lane carries from the preparation of its item to the application
 // of the Bernoulli decisions: a group of kPushG thread-class nodes or one
 // merge-class node.
@@ -180,22 +193,91 @@ struct Item {
     int kind;            // 0 = none, 1 = group, 2 = merge-class node
     int base;            // first node of the item
     int nv;              // nodes of the group inside the thread class
-    uint2 xs, xs0;       // states (kR for skipped nodes) and the bytes as loaded
+    uint2 xs;            // states (kR for nodes outside the item)
     uint2 nc;            // counts after folding in the pending tallies
     bool anyEI, clear;   // ages were loaded; pending tallies to clear
     float age[kPushG];
-    float p[kPushG];
     uint32_t need;       // bit u: node base + u draws a uniform (p > 0)
 };
 
 enum { kItemNone = 0, kItemGroup = 1, kItemHub = 2 };
 
-// Eight consecutive thread-class nodes i0 .. i0+7 (i0 a multiple of 8):
-// vector loads of states, then of counts, pending tallies and ages; the
-// probability-table loads of all eight nodes issued together. Nodes at or
-// beyond n_thr (a partial last group) are treated as R.
+// The loads of a group that can be issued before it is processed (a round
+// ahead): its states and, while many nodes are S, its counts and pending
+// tallies. Every word read belongs to this thread's group, so no other thread
+// writes it during the step.
+struct GroupLoads {
+    uint2 xs;
+    uint2 c8;
+    uint4 pd;
+    bool have_cp;        // c8 and pd loaded
+};
+
+__device__ __forceinline__ GroupLoads group_loads(const StepArgs& a, uint32_t par, int64_t t, int64_t n_grp,
+                                                  bool spec_s)
+{
+    GroupLoads g;
+    g.xs = make_uint2(0x03030303u, 0x03030303u);
+    g.c8 = make_uint2(0u, 0u);
+    g.pd = make_uint4(0u, 0u, 0u, 0u);
+    g.have_cp = false;
+    if (t < n_grp) {
+        const int i0 = (int)(t * kPushG);
+        g.xs = *reinterpret_cast<const uint2*>(a.X + i0);
+        if (spec_s) {
+            g.c8 = *reinterpret_cast<const uint2*>(a.cnt8 + i0);
+            g.pd = *reinterpret_cast<const uint4*>(a.pd16[par ^ 1u] + i0);
+            g.have_cp = true;
+        }
+    }
+    return g;
+}
+
+// A group in which nothing can happen this step: no E or I node, and every S
+// node with count 0 and no pending push (R nodes' tallies are never read).
+// Its nodes draw nothing and keep their state, so the step skips it. Needs
+// the counts and tallies when the group has an S node.
+__device__ __forceinline__ bool group_idle(const StepArgs& a, uint32_t par, int64_t t, int64_t n_grp,
+                                           GroupLoads& gl)
+{
+    if (t >= n_grp)
+        return true;
+    const int i0 = (int)(t * kPushG);
+    uint2 xs = gl.xs;
+    const int nv = min(kPushG, a.n_thr - i0);
+    if (nv < kPushG) {
+#pragma unroll
+        for (int u = 0; u < kPushG; ++u)
+            if (u >= nv)
+                set_byte(xs, u, kR);
+    }
+    const uint32_t ei = __vcmpeq4(xs.x, 0x01010101u) | __vcmpeq4(xs.x, 0x02020202u) |
+                        __vcmpeq4(xs.y, 0x01010101u) | __vcmpeq4(xs.y, 0x02020202u);
+    if (ei)
+        return false;
+    const uint32_t sx = __vcmpeq4(xs.x, 0u), sy = __vcmpeq4(xs.y, 0u);   // 0xff per S byte
+    if ((sx | sy) == 0u)
+        return true;                               // R only
+    if (!gl.have_cp) {
+        gl.c8 = *reinterpret_cast<const uint2*>(a.cnt8 + i0);
+        gl.pd = *reinterpret_cast<const uint4*>(a.pd16[par ^ 1u] + i0);
+        gl.have_cp = true;
+    }
+    // S-byte masks spread to the 16-bit tally fields
+    const uint32_t m0 = __byte_perm(sx, 0u, 0x1100u), m1 = __byte_perm(sx, 0u, 0x3322u);
+    const uint32_t m2 = __byte_perm(sy, 0u, 0x1100u), m3 = __byte_perm(sy, 0u, 0x3322u);
+    return ((gl.c8.x & sx) | (gl.c8.y & sy) | (gl.pd.x & m0) | (gl.pd.y & m1) | (gl.pd.z & m2) |
+            (gl.pd.w & m3)) == 0u;
+}
+
+// Eight consecutive thread-class nodes i0 .. i0+7 (i0 a multiple of 8), from
+// their early loads: counts, pending tallies (unless loaded early) and ages,
+// then the probability-table loads of all eight nodes issued together; the
+// probabilities go to the lane's slots in shared memory. Nodes at or beyond
+// n_thr (a partial last group) are treated as R.
 template <typename AgeT>
-__device__ __forceinline__ void group_prepare(const StepArgs& a, uint32_t par, int i0, Item& it)
+__device__ __forceinline__ void group_prepare(const StepArgs& a, uint32_t par, int i0, const GroupLoads& gl,
+                                              Item& it, float* __restrict__ pslot)
 {
     it.kind = kItemGroup;
     it.base = i0;
@@ -203,8 +285,7 @@ __device__ __forceinline__ void group_prepare(const StepArgs& a, uint32_t par, i
     it.anyEI = false;
     it.clear = false;
     it.nv = min(kPushG, a.n_thr - i0);
-    uint2 xs = *reinterpret_cast<const uint2*>(a.X + i0);
-    it.xs0 = xs;
+    uint2 xs = gl.xs;
     if (it.nv < kPushG) {
 #pragma unroll
         for (int u = 0; u < kPushG; ++u)
@@ -214,10 +295,8 @@ __device__ __forceinline__ void group_prepare(const StepArgs& a, uint32_t par, i
     it.xs = xs;
     it.nc = make_uint2(0u, 0u);
 #pragma unroll
-    for (int u = 0; u < kPushG; ++u) {
+    for (int u = 0; u < kPushG; ++u)
         it.age[u] = 0.0f;
-        it.p[u] = 0.0f;
-    }
     // compartments are 0..3, so a byte is R (3) in both words' AND only if
     // it is 3 in both; S bytes are the zero bytes
     if ((xs.x & xs.y) == 0x03030303u)
@@ -226,12 +305,14 @@ __device__ __forceinline__ void group_prepare(const StepArgs& a, uint32_t par, i
     const uint32_t ei_x = __vcmpeq4(xs.x, 0x01010101u) | __vcmpeq4(xs.x, 0x02020202u);
     const uint32_t ei_y = __vcmpeq4(xs.y, 0x01010101u) | __vcmpeq4(xs.y, 0x02020202u);
     it.anyEI = (ei_x | ei_y) != 0u;
-    uint2 c8 = make_uint2(0u, 0u);
-    uint4 pd = make_uint4(0u, 0u, 0u, 0u);
-    if (anyS) {
+    uint2 c8 = gl.c8;
+    uint4 pd = gl.pd;
+    if (anyS && !gl.have_cp) {
         c8 = *reinterpret_cast<const uint2*>(a.cnt8 + i0);
         pd = *reinterpret_cast<const uint4*>(a.pd16[par ^ 1u] + i0);
     }
+    if (!anyS)
+        pd = make_uint4(0u, 0u, 0u, 0u);    // tallies of non-S nodes are never folded
     const AgeT* __restrict__ A = static_cast<const AgeT*>(a.A) + i0;
     if (it.anyEI) {
         if (it.nv == kPushG) {
@@ -248,6 +329,7 @@ __device__ __forceinline__ void group_prepare(const StepArgs& a, uint32_t par, i
     // counts (thread-class counts are <= 255, inside the S table) and the
     // table lookups, resolved after every load of this phase has been issued
     uint2 nc = c8;
+    float p[kPushG];
 #pragma unroll
     for (int u = 0; u < kPushG; ++u) {
         const int x = (int)byte_of(xs, u);
@@ -263,21 +345,24 @@ __device__ __forceinline__ void group_prepare(const StepArgs& a, uint32_t par, i
         float ps = 0.0f;
         if (isS && c != 0u)
             ps = __ldg(a.ps + c);
-        it.p[u] = isS ? ps : (isEI ? (e.x == it.age[u] ? e.y : -1.0f) : 0.0f);
+        p[u] = isS ? ps : (isEI ? (e.x == it.age[u] ? e.y : -1.0f) : 0.0f);
     }
     it.nc = nc;
 #pragma unroll
     for (int u = 0; u < kPushG; ++u) {
-        if (it.p[u] < 0.0f)                                   // age off the tabulated sequence
-            it.p[u] = p_direct_p(a.M, (int)byte_of(xs, u), it.age[u]);
-        if (it.p[u] > 0.0f)
+        if (p[u] < 0.0f)                                      // age off the tabulated sequence
+            p[u] = p_direct_p(a.M, (int)byte_of(xs, u), it.age[u]);
+        if (p[u] > 0.0f) {
             it.need |= 1u << u;
+            pslot[u] = p[u];
+        }
     }
 }
 
 // one merge-class node: its count and pending tallies are folded in here
 template <typename AgeT>
-__device__ __forceinline__ void hub_prepare(const StepArgs& a, uint32_t par, int i, Item& it)
+__device__ __forceinline__ void hub_prepare(const StepArgs& a, uint32_t par, int i, Item& it,
+                                            float* __restrict__ pslot)
 {
     it.kind = kItemHub;
     it.base = i;
@@ -287,9 +372,7 @@ __device__ __forceinline__ void hub_prepare(const StepArgs& a, uint32_t par, int
     it.nv = 1;
     const int x = a.X[i];
     it.xs = make_uint2((uint32_t)x, 0u);
-    it.xs0 = it.xs;
     it.age[0] = 0.0f;
-    it.p[0] = 0.0f;
     if (x == kR)
         return;
     const int r = i - a.n_thr;
@@ -306,25 +389,21 @@ __device__ __forceinline__ void hub_prepare(const StepArgs& a, uint32_t par, int
     }
     if (x == kE || x == kI)
         it.age[0] = AgeIO<AgeT>::load(static_cast<const AgeT*>(a.A)[i]);
-    it.p[0] = node_p_push(a, x, it.age[0], c);
-    it.need = it.p[0] > 0.0f ? 1u : 0u;
+    const float p = node_p_push(a, x, it.age[0], c);
+    if (p > 0.0f) {
+        it.need = 1u;
+        pslot[0] = p;
+    }
 }
 
-// Bernoulli decisions of a whole warp: every lane queues (original id, p) of
-// its nodes that draw, then the lanes share the queue evenly, so a warp runs
-// ceil(draws / 32) rounds of Philox instead of one round per node position
-// in which any lane draws. Every lane of the warp must call this. Returns the
-// lane's fired mask (bit u = node base + u fired).
-struct DrawQ {
-    uint32_t node[kPushThreads * kPushG];
-    float p[kPushThreads * kPushG];
-    uint8_t fired[kPushThreads * kPushG];
-};
-
-__device__ __forceinline__ uint32_t warp_draws(const StepArgs& a, uint32_t step, const Item& it, DrawQ& q)
+// Bernoulli decisions of a whole warp: every lane queues (original id, slot)
+// of its nodes that draw, then the lanes share the queue evenly, so a warp
+// runs ceil(draws / 32) rounds of Philox instead of one round per node
+// position in which any lane draws. Every lane of the warp must call this.
+// Returns the lane's fired mask (bit u = node base + u fired).
+__device__ __forceinline__ uint32_t warp_draws(const StepArgs& a, uint32_t step, const Item& it, WarpScratch& w)
 {
     const int lane = threadIdx.x & 31;
-    const int wbase = (threadIdx.x >> 5) * (32 * kPushG);
     const uint32_t cnt = (uint32_t)__popc(it.need);
     uint32_t incl = cnt;
 #pragma unroll
@@ -336,33 +415,31 @@ __device__ __forceinline__ uint32_t warp_draws(const StepArgs& a, uint32_t step,
     const uint32_t total = __shfl_sync(kFull, incl, 31);
     if (total == 0u)
         return 0u;
-    const int off = wbase + (int)(incl - cnt);
     {
-        int j = off;
-#pragma unroll
-        for (int u = 0; u < kPushG; ++u) {
-            if ((it.need >> u) & 1u) {
-                const int node = it.base + u;
-                q.node[j] = a.perm ? (uint32_t)__ldg(a.perm + node) : (uint32_t)node;
-                q.p[j] = it.p[u];
-                ++j;
-            }
+        int j = (int)(incl - cnt);
+        uint32_t m = it.need;
+        while (m) {
+            const int u = __ffs(m) - 1;
+            m &= m - 1u;
+            const int node = it.base + u;
+            w.qnode[j] = a.perm ? (uint32_t)__ldg(a.perm + node) : (uint32_t)node;
+            w.qslot[j] = (uint16_t)(lane * kPushG + u);
+            ++j;
         }
     }
     __syncwarp();
     for (int e = lane; e < (int)total; e += 32) {
-        const float u = uniform24(a.M.key0, a.M.key1, a.M.rep, step, q.node[wbase + e]);
-        q.fired[wbase + e] = u < q.p[wbase + e] ? 1 : 0;
+        const int sl = w.qslot[e];
+        const float u = uniform24(a.M.key0, a.M.key1, a.M.rep, step, w.qnode[e]);
+        w.fired[sl] = u < w.p[sl] ? 1 : 0;
     }
     __syncwarp();
     uint32_t fired = 0u;
-    int j = off;
-#pragma unroll
-    for (int u = 0; u < kPushG; ++u) {
-        if ((it.need >> u) & 1u) {
-            fired |= (uint32_t)q.fired[j] << u;
-            ++j;
-        }
+    uint32_t m = it.need;
+    while (m) {
+        const int u = __ffs(m) - 1;
+        m &= m - 1u;
+        fired |= (uint32_t)w.fired[lane * kPushG + u] << u;
     }
     __syncwarp();     // the queue is reused by the warp's next item
     return fired;
@@ -435,7 +512,7 @@ __device__ __forceinline__ void item_apply(const StepArgs& a, uint32_t par, Item
                 ld.dS += (uint32_t)__ldg(a.deg + i0 + u);
     }
     if (it.nv == kPushG) {
-        if (nx.x != it.xs0.x || nx.y != it.xs0.y)
+        if (nx.x != xs.x || nx.y != xs.y)
             *reinterpret_cast<uint2*>(a.X + i0) = nx;
         if (it.anyEI)
             AgeVec8<AgeT>::store(A, it.age);
@@ -461,143 +538,164 @@ __device__ __forceinline__ void item_apply(const StepArgs& a, uint32_t par, Item
 }
 
 // ---------------------------------------------------------------------------
-// CTA-wide pushes. Threads append their push events (node id, bit 31 = the
-// node left I) to a shared list; per chunk of kPushThreads events one thread
-// per event reads the transposed row bounds, a block scan of the row lengths
-// flattens every event's edges into one index range, and all threads of the
-// CTA issue the column loads and atomic adds of that range together, so a
-// chunk costs two dependent memory round trips however many events it holds.
+// Warp-wide pushes. The lanes' push events (bit u of ev: node base + u
+// entered I, or left it when bit u of neg is set) go to the warp's event
+// list; per batch of 32 events lane e reads event e's transposed row bounds,
+// a warp scan of the row lengths flattens the batch's edges into one index
+// range, and the 32 lanes stride over it, each finding its event by a binary
+// search over the lanes' offsets. A batch costs two dependent memory round
+// trips however many events it holds. Every lane of the warp must call this.
 // ---------------------------------------------------------------------------
-constexpr int kPushEvCap = kPushThreads * kPushG;   // events one item round can produce
-
-struct PushSmem {
-    uint32_t ev[kPushEvCap];                  // node | (1u << 31) when it left I
-    int64_t lo[kPushThreads];                 // first out-edge of each event of the chunk
-    int64_t off[kPushThreads + 1];            // exclusive prefix of the chunk's row lengths
-    int64_t wsum[kPushThreads / 32];
-    uint32_t nev;
-};
-
-// exclusive block scan of one int64 per thread; returns the total
-__device__ __forceinline__ int64_t block_scan_excl(int64_t v, int64_t* out, int64_t* wsum)
+template <bool INIT>
+__device__ __forceinline__ void warp_push(const StepArgs& a, uint32_t par, uint32_t ev, uint32_t neg, int base,
+                                          uint32_t* __restrict__ list)
 {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    int64_t x = v;
+    const int lane = threadIdx.x & 31;
+    const uint32_t cnt = (uint32_t)__popc(ev);
+    uint32_t incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const int64_t y = __shfl_up_sync(kFull, x, o);
+        const uint32_t y = __shfl_up_sync(kFull, incl, o);
         if (lane >= o)
-            x += y;
+            incl += y;
     }
-    if (lane == 31)
-        wsum[warp] = x;
-    __syncthreads();
-    int64_t before = 0, total = 0;
-#pragma unroll
-    for (int w = 0; w < kPushThreads / 32; ++w) {
-        const int64_t t = wsum[w];
-        before += w < warp ? t : 0;
-        total += t;
+    const int nev = (int)__shfl_sync(kFull, incl, 31);
+    if (nev == 0)
+        return;
+    {
+        int j = (int)(incl - cnt);
+        uint32_t m = ev;
+        while (m) {
+            const int u = __ffs(m) - 1;
+            m &= m - 1u;
+            list[j++] = (uint32_t)(base + u) | (((neg >> u) & 1u) << 31);
+        }
     }
-    out[tid] = before + x - v;
-    return total;
-}
-
-template <bool INIT>
-__device__ __forceinline__ void cta_push(const StepArgs& a, uint32_t par, PushSmem& sm)
-{
-    const int tid = threadIdx.x;
-    const int nev = (int)sm.nev;
-    for (int c0 = 0; c0 < nev; c0 += kPushThreads) {
-        const int e = c0 + tid;
+    __syncwarp();
+    for (int c0 = 0; c0 < nev; c0 += 32) {
+        const int e = c0 + lane;
         int64_t lo = 0, len = 0;
+        uint32_t evw = 0u;
         if (e < nev) {
-            const int node = (int)(sm.ev[e] & 0x7fffffffu);
+            evw = list[e];
+            const int node = (int)(evw & 0x7fffffffu);
             lo = __ldg(a.out_ptr + node);
             len = __ldg(a.out_ptr + node + 1) - lo;
         }
-        sm.lo[tid] = lo;
-        const int64_t total = block_scan_excl(len, sm.off, sm.wsum);
-        if (tid == 0)
-            sm.off[kPushThreads] = total;
-        __syncthreads();
-        const int ne = min(kPushThreads, nev - c0);
-        for (int64_t q = tid; q < total; q += kPushThreads) {
-            // the event whose edge range holds q: largest k with off[k] <= q
-            int l = 0, h = ne - 1;
-            while (l < h) {
-                const int m = (l + h + 1) >> 1;
-                if (sm.off[m] <= q)
-                    l = m;
-                else
-                    h = m - 1;
-            }
-            const uint32_t j = (uint32_t)__ldg(a.out_col + sm.lo[l] + (q - sm.off[l]));
-            push_one<INIT>(a, par, j, (sm.ev[c0 + l] >> 31) != 0u);
+        int64_t off = len;                          // inclusive scan of the lengths
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(kFull, off, o);
+            if (lane >= o)
+                off += y;
         }
-        __syncthreads();
+        const int64_t tot = __shfl_sync(kFull, off, 31);
+        off -= len;                                 // exclusive
+        // warp-uniform trip count: every lane takes part in every shuffle
+        for (int64_t q0 = 0; q0 < tot; q0 += 32) {
+            const int64_t q = q0 + lane;
+            // the lane (event) whose range holds q: largest l with off_l <= q
+            int l = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int64_t o = __shfl_sync(kFull, off, l + step);
+                if (o <= q)
+                    l += step;
+            }
+            const int64_t lo_l = __shfl_sync(kFull, lo, l);
+            const int64_t off_l = __shfl_sync(kFull, off, l);
+            const uint32_t ev_l = __shfl_sync(kFull, evw, l);
+            if (q < tot) {
+                const uint32_t j = (uint32_t)__ldg(a.out_col + lo_l + (q - off_l));
+                push_one<INIT>(a, par, j, (ev_l >> 31) != 0u);
+            }
+        }
     }
+    __syncwarp();     // the list is reused by the warp's next item
 }
 
-__device__ __forceinline__ void append_events(PushSmem& sm, uint32_t ev, uint32_t neg, int base)
+// Bulk prefetch of a byte range into L2 (TMA; 16-byte aligned start, size a
+// multiple of 16): a hint with no register destination.
+__device__ __forceinline__ void l2_prefetch(const void* p, uint32_t bytes)
 {
-    if (ev) {
-        uint32_t pos = atomicAdd(&sm.nev, (uint32_t)__popc(ev));
-        while (ev) {
-            const int u = __ffs(ev) - 1;
-            ev &= ev - 1u;
-            sm.ev[pos++] = (uint32_t)(base + u) | (((neg >> u) & 1u) << 31);
-        }
-    }
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
+
+constexpr int kPushPrefetchRounds = 2;     // grid-stride rounds prefetched ahead
 
 // ---------------------------------------------------------------------------
 // One whole step: items are groups of kPushG thread-class nodes, then single
-// merge-class nodes; CTAs stride over rounds of kPushThreads items and push
-// after each round. Per-step deltas as in the gather form.
+// merge-class nodes; warps stride over them (grid-stride, the next item's
+// early loads in flight while the current one is processed). Per-step deltas
+// as in the gather form.
 // ---------------------------------------------------------------------------
 template <typename AgeT>
 __global__ void __launch_bounds__(kPushThreads, kPushCtasPerSm) push_step_kernel(const __grid_constant__ StepArgs a)
 {
     __shared__ unsigned long long s_delta[kDeltaFields];
-    __shared__ PushSmem sm;
-    __shared__ DrawQ dq;
+    __shared__ WarpScratch scratch[kPushThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31;
+    WarpScratch& w = scratch[tid >> 5];
+    float* pslot = w.p + lane * kPushG;
     if (tid < kDeltaFields)
         s_delta[tid] = 0ull;
-    if (tid == 0)
-        sm.nev = 0u;
     const int64_t k = a.ctl->step + a.j;
     const uint32_t par = (uint32_t)(k & 1);
-    __syncthreads();
+    // counts and tallies are loaded a round ahead while S nodes are common
+    // (counts of the state at the start of this launch sequence)
+    const bool spec_s = (int64_t)a.ctl->counts[0] * 16 >= (int64_t)a.n;
+    const bool spec_ei = ((int64_t)a.ctl->counts[1] + a.ctl->counts[2]) * 16 >= (int64_t)a.n;
     PushDeltas ld;
     const int64_t n_grp = ((int64_t)a.n_thr + kPushG - 1) / kPushG;
     const int64_t total = n_grp + a.n_m;
     const int64_t stride = (int64_t)gridDim.x * kPushThreads;
-    for (int64_t t0 = (int64_t)blockIdx.x * kPushThreads; t0 < total; t0 += stride) {
-        const int64_t t = t0 + tid;
+    int64_t t0 = (int64_t)blockIdx.x * kPushThreads + (tid & ~31);
+    GroupLoads cur = group_loads(a, par, t0 + lane, n_grp, spec_s);
+    for (; t0 < total; t0 += stride) {
+        const int64_t t = t0 + lane;
+        // the warp's groups kPushPrefetchRounds rounds ahead go to L2 now (the
+        // arrays are padded past their last whole group by 16 elements, so the
+        // rounded-up ranges stay inside them)
+        const int64_t tp = t0 + kPushPrefetchRounds * stride;
+        if (lane == 0 && tp < n_grp) {
+            const int64_t ng = min((int64_t)32, n_grp - tp);
+            const int64_t i0 = tp * kPushG;
+            const uint32_t nb = (uint32_t)(ng * kPushG);               // bytes of one byte per node
+            l2_prefetch(a.X + i0, (nb + 15u) & ~15u);
+            if (spec_s) {
+                l2_prefetch(a.cnt8 + i0, (nb + 15u) & ~15u);
+                l2_prefetch(a.pd16[par ^ 1u] + i0, nb * 2u);
+            }
+            if (spec_ei)
+                l2_prefetch(static_cast<const AgeT*>(a.A) + i0, nb * (uint32_t)sizeof(AgeT));
+        }
+        // the next item's loads are in flight while this one is processed
+        const GroupLoads nxt = group_loads(a, par, t + stride, n_grp, spec_s);
+        // a warp whose items are all idle (and holds no merge-class node)
+        // skips the round
+        const bool idle = (t < n_grp || t >= total) && group_idle(a, par, t, n_grp, cur);
+        if (__all_sync(kFull, idle)) {
+            cur = nxt;
+            continue;
+        }
         Item it;
         it.kind = kItemNone;
         it.base = 0;
         it.need = 0u;
         if (t < n_grp)
-            group_prepare<AgeT>(a, par, (int)(t * kPushG), it);
+            group_prepare<AgeT>(a, par, (int)(t * kPushG), cur, it, pslot);
         else if (t < total)
-            hub_prepare<AgeT>(a, par, a.n_thr + (int)(t - n_grp), it);
-        const uint32_t fired = warp_draws(a, (uint32_t)k, it, dq);
+            hub_prepare<AgeT>(a, par, a.n_thr + (int)(t - n_grp), it, pslot);
+        __syncwarp();
+        const uint32_t fired = warp_draws(a, (uint32_t)k, it, w);
         uint32_t ev = 0u, neg = 0u;
         item_apply<AgeT>(a, par, it, fired, ev, neg, ld);
-        append_events(sm, ev, neg, it.base);
-        __syncthreads();
-        if (sm.nev) {            // uniform: read after the barrier
-            cta_push<false>(a, par, sm);
-            if (tid == 0)
-                sm.nev = 0u;
-            __syncthreads();
-        }
+        warp_push<false>(a, par, ev, neg, it.base, w.ev);
+        cur = nxt;
     }
     const uint32_t fs_ = __reduce_add_sync(kFull, ld.fS), fe = __reduce_add_sync(kFull, ld.fE);
     const uint32_t fi = __reduce_add_sync(kFull, ld.fI), ds = __reduce_add_sync(kFull, ld.dS);
+    __syncthreads();       // s_delta initialised
     if (lane == 0) {
         if (fs_) atomicAdd(&s_delta[0], (unsigned long long)fs_);
         if (fe) atomicAdd(&s_delta[1], (unsigned long long)fe);
@@ -616,22 +714,13 @@ __global__ void __launch_bounds__(kPushThreads, kPushCtasPerSm) push_step_kernel
 // node in I pushes +1 straight into the counts of its out-neighbours.
 __global__ void __launch_bounds__(kPushThreads) push_init_kernel(const __grid_constant__ StepArgs a)
 {
-    __shared__ PushSmem sm;
-    const int tid = threadIdx.x;
-    if (tid == 0)
-        sm.nev = 0u;
-    __syncthreads();
+    __shared__ uint32_t list[kPushThreads];
+    const int tid = threadIdx.x, lane = tid & 31;
     const int64_t stride = (int64_t)gridDim.x * kPushThreads;
-    for (int64_t t0 = (int64_t)blockIdx.x * kPushThreads; t0 < a.n; t0 += stride) {
-        const int64_t i = t0 + tid;
-        append_events(sm, (i < a.n && a.X[i] == kI) ? 1u : 0u, 0u, (int)i);
-        __syncthreads();
-        if (sm.nev) {
-            cta_push<true>(a, 0u, sm);
-            if (tid == 0)
-                sm.nev = 0u;
-            __syncthreads();
-        }
+    for (int64_t t0 = (int64_t)blockIdx.x * kPushThreads + (tid & ~31); t0 < a.n; t0 += stride) {
+        const int64_t i = t0 + lane;
+        const uint32_t ev = (i < a.n && a.X[i] == kI) ? 1u : 0u;
+        warp_push<true>(a, 0u, ev, 0u, (int)i, list + (tid & ~31));
     }
 }
 
