@@ -38,9 +38,18 @@ import workloads as W  # noqa: E402
 
 METRIC = "GNUPS at N=1e6 (regular/BA); served-ensemble GNUPS + p50/p99 vs plain"
 UNIT = "GNUPS"
-PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "sell_smem_kernel_regular_n1e6.md")
-KERNEL_SOURCES = ["paper_2604_22092_gb300/csrc/fs_step.cu", "paper_2604_22092_gb300/csrc/fs_device.cuh",
-                  "paper_2604_22092_gb300/csrc/fs_internal.h"]
+# per step kernel: the committed ncu summary holding its DRAM traffic, and the
+# sources whose hash must match for that traffic to be reported
+PROFILE_TRAFFIC = {
+    "push_step_kernel": os.path.join(ROOT, "profiles", "push_step_kernel_regular_n1e6.md"),
+    "sell_smem_kernel": os.path.join(ROOT, "profiles", "sell_smem_kernel_regular_n1e6.md"),
+}
+KERNEL_SOURCES = {
+    "push_step_kernel": ["paper_2604_22092_gb300/csrc/fs_push.cu", "paper_2604_22092_gb300/csrc/fs_device.cuh",
+                         "paper_2604_22092_gb300/csrc/fs_internal.h"],
+    "sell_smem_kernel": ["paper_2604_22092_gb300/csrc/fs_step.cu", "paper_2604_22092_gb300/csrc/fs_device.cuh",
+                         "paper_2604_22092_gb300/csrc/fs_internal.h"],
+}
 
 
 def parse():
@@ -61,6 +70,7 @@ def parse():
     ap.add_argument("--age", choices=["f32", "f16"], default="f32", help="age storage of ensemble/serving runs")
     ap.add_argument("--ens-graphs", type=int, default=64, help="graphs of the packed-ensemble run")
     ap.add_argument("--ens-steps", type=int, default=500, help="steps of the packed-ensemble run")
+    ap.add_argument("--no-other-form", action="store_true", help="skip timing the other pressure form")
     ap.add_argument("--pressure", choices=["auto", "gather", "push"], default="auto",
                     help="pressure form of single-realisation runs (auto = push where available)")
     return ap.parse_args()
@@ -85,6 +95,24 @@ def workload(kind: str, n: int):
 def params(fs, seed: int, replicate: int = 0, pressure: int = 0):
     return fs.sim_params(fs.FS_SEIR, fs.law("lognormal", math.log(6.0), 0.6), 0.25, 0.1, seed,
                          latent=fs.law("weibull", 2.0, 4.0), replicate=replicate, pressure=pressure)
+
+
+def push_bytes_model(counts: np.ndarray, n: int, d: int, b_age: int = 4) -> np.ndarray:
+    """Algorithmic bytes of each step of the push formulation on a d-regular
+    SEIR run, from its counts trajectory ((K+1) x 4, row k = state at the start
+    of step k): every node's state is read (1 B); every S node reads its count
+    and pending tally (1 + 2 B); every E/I node reads and writes its age
+    (2 b_age); every transition writes a state byte; every node entering or
+    leaving I reads its transposed row bounds (16 B) and, per out-edge, one
+    column (4 B) and one tally read-modify-write (4 B)."""
+    c = counts.astype(np.int64)
+    S, E, I, R = c[:-1, 0], c[:-1, 1], c[:-1, 2], c[:-1, 3]
+    left_s = S - c[1:, 0]
+    to_r = c[1:, 3] - R
+    enter_i = (c[1:, 2] - I) + to_r
+    pushers = enter_i + to_r
+    return (n * 1.0 + 3.0 * S + 2.0 * b_age * (E + I) + (left_s + enter_i + to_r)
+            + pushers * (16.0 + d * 8.0))
 
 
 def bytes_model(n: int, steps: int, s_node_sum: int, s_degree_sum: int, b_state=1, b_age=4) -> float:
@@ -154,31 +182,34 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ helpers
-def kernel_source_hash() -> str:
+def kernel_source_hash(kernel: str) -> str:
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
+def profiled_traffic(kernel: str):
     """DRAM bytes per launch of the step kernel from the committed ncu summary,
     if it was taken on the current kernel source."""
     try:
-        text = open(PROFILE_TRAFFIC).read()
-    except OSError:
+        text = open(PROFILE_TRAFFIC[kernel]).read()
+    except (OSError, KeyError):
         return None
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
     k = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
-    if not m or not k or k.group(1) != kernel_source_hash():
+    if not m or not k or k.group(1) != kernel_source_hash(kernel):
         return None
     return float(m.group(1))
 
 
-def step_kernel_name(fs, g) -> str:
-    """The step kernel this graph runs: the shared-memory-bitmap SELL kernel
-    when the bitmap fits in shared memory, else the fused kernel."""
+def step_kernel_name(fs, g, pressure: int) -> str:
+    """The step kernel a sim runs: the push kernel for the push form; for the
+    gather, the shared-memory-bitmap SELL kernel when the bitmap fits in
+    shared memory, else the fused kernel."""
+    if pressure == fs.FS_PRESSURE_PUSH:
+        return "push_step_kernel"
     bm_bytes = (((g.n >> 5) + 1) * 4 + 15) // 16 * 16
     return "sell_smem_kernel" if bm_bytes <= 200 * 1024 else "fused_step_kernel"
 
@@ -214,10 +245,10 @@ def cpu_baseline(g, idx, budget_s=12.0, max_steps=400):
 
 
 # ------------------------------------------------------------------ ensembles and serving
-def scen_params(fs, sc, replicate: int, age_dtype: int):
+def scen_params(fs, sc, replicate: int, age_dtype: int, pressure: int = 0):
     latent = fs.law("erlang", 0.75, k=3) if sc.latent == "erlang" else fs.law("weibull", 2.0, 4.0)
     return fs.sim_params(fs.FS_SEIR, fs.law("lognormal", math.log(6.0), float(sc.sigma_inf)), float(sc.beta), 0.1,
-                         int(sc.seed), latent=latent, replicate=replicate, age_dtype=age_dtype)
+                         int(sc.seed), latent=latent, replicate=replicate, age_dtype=age_dtype, pressure=pressure)
 
 
 def index_for(g, count=100, seed=1):
@@ -235,7 +266,7 @@ def plain_seconds(fs, gh, p, idx, steps):
     return time.perf_counter() - t0
 
 
-def ensemble_bench(fs, torch, n_graphs, n_lo, n_hi, steps, age_dtype, reps=3):
+def ensemble_bench(fs, torch, n_graphs, n_lo, n_hi, steps, age_dtype, reps=3, pressure=0):
     """Packed batch of 8 scenarios x n_graphs mixed graphs in one launch per
     step, against each realisation run alone (a sample: scenario 0 of every
     graph, whose cost stands for the other scenarios of that graph)."""
@@ -246,7 +277,8 @@ def ensemble_bench(fs, torch, n_graphs, n_lo, n_hi, steps, age_dtype, reps=3):
     stream = torch.cuda.Stream()
     times = []
     for it in range(reps):
-        ens = [fs.fs_ens_create(ghs[q], [scen_params(fs, sc, s, age_dtype) for s, sc in enumerate(scen[q])], idxs[q])
+        ens = [fs.fs_ens_create(ghs[q], [scen_params(fs, sc, s, age_dtype, pressure) for s, sc in enumerate(scen[q])],
+                                idxs[q])
                for q in range(n_graphs)]
         b = fs.fs_batch_create(age_dtype, n_graphs + 1, stream=stream)
         for e in ens:
@@ -354,26 +386,60 @@ def run_flashstep(args, rank, world, local_rank):
     prm = params(fs, seed=replica_seed(rank), replicate=0, pressure=PRESSURE[args.pressure])
     opts = fs.graph_opts(device_input=True)
 
-    def one_step():
+    def one_step(prm_run):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         gh = fs.fs_graph_create(g.n, d_rp, d_col, opts=opts, stream=stream)
-        sh = fs.fs_sim_init(gh, prm, idx, stream=stream)
+        sh = fs.fs_sim_init(gh, prm_run, idx, stream=stream)
         replay_ms = fs.fs_sim_run_timed(sh, args.sim_steps, args.graph_steps, counts_dev)
         ev1.record(stream)
         ev1.synchronize()
         work = fs.fs_sim_work(sh)
+        work["pressure"] = fs.fs_sim_pressure_get(sh)
         fs.fs_sim_destroy(sh)
         fs.fs_graph_destroy(gh)
         return ev0.elapsed_time(ev1), replay_ms, work
 
+    K = args.graph_steps
+    full = args.sim_steps // K
+    steps_in_graphs = full * K
+
+    def step_bytes(work, pressure):
+        """Algorithmic bytes of the steps inside the timed graph replays, in the
+        byte model of the form that ran."""
+        if pressure == fs.FS_PRESSURE_PUSH:
+            cnt = counts_dev.view(args.sim_steps + 1, 4).cpu().numpy()
+            return float(np.sum(push_bytes_model(cnt, g.n, 10)[:steps_in_graphs]))
+        return (bytes_model(g.n, args.sim_steps, work["s_node_sum"], work["s_degree_sum"])
+                * steps_in_graphs / args.sim_steps)
+
+    def roofline_of(bytes_per_step, step_ms, kernel, pressure):
+        peak, peak_kind = measured_peak_hbm()
+        achieved = bytes_per_step / (step_ms * 1e-3) / 1e9
+        # the paper's dense traffic model (every row traversed): N (2 b_s + 2 b_a + 1/8 + 4) + E (4 + 1/8)
+        dense_bytes = g.n * (2 + 8 + 1 / 8 + 4) + g.col_ind.size * (4 + 1 / 8)
+        model = ("push: state read by every node, count + pending tally by S nodes, ages by E/I nodes, "
+                 "state writes, transposed row bounds + 8 B per out-edge of nodes entering or leaving I"
+                 if pressure == fs.FS_PRESSURE_PUSH else
+                 "gather: state/age read+write and bitmap bit per node, row offset per S node, "
+                 "column + bitmap bit per S-row edge")
+        return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": profiled_traffic(kernel),
+                "peak_source": peak_kind, "kernel": kernel,
+                "algorithmic_bytes_per_launch": round(bytes_per_step), "byte_model": model,
+                "avg_launch_us": round(step_ms * 1e3, 3),
+                "dense_equiv_frac": round(dense_bytes / (step_ms * 1e-3) / 1e9 / peak, 4),
+                "note": "at N=1e6 the step's working set is L2-resident across steps, so the step is "
+                        "latency-bound; the HBM-bound N=1e7/1e8 points are bench.py --workload large"}
+
     for _ in range(args.warmup):
         flush.fill_(1.0)
-        one_step()
+        one_step(prm)
     torch.cuda.synchronize()
     clocks = ClockSampler(local_rank) if rank == 0 else None
     times, kern_ms, bytes_alg = [], [], []
+    pressure_used = None
     launches0 = fs.fs_kernel_launches()
     if clocks:
         clocks.start()
@@ -382,50 +448,56 @@ def run_flashstep(args, rank, world, local_rank):
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
-        ms, replay_ms, work = one_step()
+        ms, replay_ms, work = one_step(prm)
         torch.cuda.synchronize()
         times.append(ms)
-        K = args.graph_steps
-        full = args.sim_steps // K
         kern_ms.append(float(np.sum(replay_ms[:full])))
-        steps_in_graphs = full * K
-        # bytes of the steps inside the timed graph replays (all steps when K divides them)
-        bytes_alg.append(bytes_model(g.n, args.sim_steps, work["s_node_sum"], work["s_degree_sum"])
-                         * steps_in_graphs / args.sim_steps)
+        pressure_used = work["pressure"]
+        bytes_alg.append(step_bytes(work, pressure_used))
     clock_info = clocks.stop() if clocks else None
     launches = (fs.fs_kernel_launches() - launches0) // max(args.steps, 1)
     total_ms = max_over_ranks(float(np.sum(times)), dist, dev)
     value = whole_job_gnups(g.n, args.sim_steps, args.steps, world, total_ms)
-    # roofline of the dominant kernel (the fused step): algorithmic bytes of the
+    # roofline of the dominant kernel (the step): algorithmic bytes of the
     # steps / their event-timed graph replays (which include launch gaps and the
     # per-replay epilogue, so this is a lower bound on the kernel's own rate)
-    peak, peak_kind = measured_peak_hbm()
-    per_step_bytes = float(np.sum(bytes_alg)) / (args.steps * (args.sim_steps // args.graph_steps) * args.graph_steps)
-    per_step_ms = float(np.sum(kern_ms)) / (args.steps * (args.sim_steps // args.graph_steps) * args.graph_steps)
-    achieved = per_step_bytes / (per_step_ms * 1e-3) / 1e9
-    # the paper's dense traffic model (every row traversed): N (2 b_s + 2 b_a + 1/8 + 4) + E (4 + 1/8)
-    dense_bytes = g.n * (2 + 8 + 1 / 8 + 4) + g.col_ind.size * (4 + 1 / 8)
-    dense_achieved = dense_bytes / (per_step_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": profiled_traffic(),
-                "peak_source": peak_kind, "kernel": step_kernel_name(fs, g),
-                "algorithmic_bytes_per_launch": round(per_step_bytes),
-                "avg_launch_us": round(per_step_ms * 1e3, 3),
-                "frac_dense": round(dense_achieved / peak, 4),
-                "dense_bytes_per_launch": round(dense_bytes),
-                "note": "frac: bytes the method must move (CSR of S rows only); frac_dense: the paper's "
-                        "O(N+E) model; at N=1e6 the working set is L2-resident across steps (L2-served)"}
+    per_step_bytes = float(np.sum(bytes_alg)) / (args.steps * steps_in_graphs)
+    per_step_ms = float(np.sum(kern_ms)) / (args.steps * steps_in_graphs)
+    kernel = step_kernel_name(fs, g, pressure_used)
+    roofline = roofline_of(per_step_bytes, per_step_ms, kernel, pressure_used)
     out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": wname, "model": "SEIR renewal", "graph": "random 10-regular (configuration model, seed 0)",
                       "n": g.n, "sim_steps": args.sim_steps, "graph_steps": args.graph_steps,
                       "age_storage": "f32", "state_storage": "u8", "parallelism": f"replicas{world}",
+                      "pressure": "push" if pressure_used == fs.FS_PRESSURE_PUSH else "gather",
                       "l2_flush": "512 MB write between timed steps",
                       "timed": "device-resident CSR -> ingest + init + all steps (CUDA events)"},
            "roofline": roofline, "gpu_launches": int(launches)}
     if clock_info:
         out["clocks"] = clock_info
+    # the other pressure form on the same workload (rank 0; not part of the timed value)
+    if rank == 0 and not args.no_other_form:
+        other = fs.FS_PRESSURE_GATHER if pressure_used == fs.FS_PRESSURE_PUSH else fs.FS_PRESSURE_PUSH
+        prm_o = params(fs, seed=replica_seed(rank), replicate=0, pressure=other)
+        one_step(prm_o)
+        o_times, o_kern, o_bytes = [], [], []
+        for _ in range(2):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            ms, replay_ms, work = one_step(prm_o)
+            o_times.append(ms)
+            o_kern.append(float(np.sum(replay_ms[:full])))
+            o_bytes.append(step_bytes(work, work["pressure"]))
+        o_ms = float(np.mean(o_times))
+        out["other_form"] = {
+            "pressure": "push" if other == fs.FS_PRESSURE_PUSH else "gather",
+            "value": round(g.n * args.sim_steps / (o_ms * 1e-3) / 1e9, 3), "unit": UNIT,
+            "ms_per_step": round(o_ms, 3),
+            "roofline": roofline_of(float(np.sum(o_bytes)) / (2 * steps_in_graphs),
+                                    float(np.sum(o_kern)) / (2 * steps_in_graphs),
+                                    step_kernel_name(fs, g, other), other)}
     # end to end through the C ABI with host buffers (rank 0 only)
     if rank == 0 and not args.no_e2e:
         out["e2e"] = e2e(fs, torch, g, idx, prm, args, stream)
@@ -547,6 +619,7 @@ def large_bench(fs, torch, n: int, age_dtype: int, sim_steps: int, graph_steps: 
         ev1.record(stream)
         ev1.synchronize()
         work = fs.fs_sim_work(sh)
+        pressure_used = fs.fs_sim_pressure_get(sh)
         cnt = counts_dev.view(sim_steps + 1, 4).cpu().numpy().astype(np.int64)
         counts = fs.fs_sim_run(sh, 0)
         gbytes = fs.fs_graph_info_get(gh)["device_bytes"]
@@ -557,8 +630,13 @@ def large_bench(fs, torch, n: int, age_dtype: int, sim_steps: int, graph_steps: 
         full = sim_steps // graph_steps
         totals.append(ev0.elapsed_time(ev1))
         replays.append(float(np.sum(ms[:full])))
-        breq.append(bytes_model(n, sim_steps, work["s_node_sum"], work["s_degree_sum"], b_age=b_age)
-                    * full * graph_steps / sim_steps)
+        if pressure_used == fs.FS_PRESSURE_PUSH:
+            step_b = push_bytes_model(cnt, n, d, b_age)
+            breq.append(float(np.sum(step_b[:full * graph_steps])))
+        else:
+            step_b = None
+            breq.append(bytes_model(n, sim_steps, work["s_node_sum"], work["s_degree_sum"], b_age=b_age)
+                        * full * graph_steps / sim_steps)
     assert int(counts[-1].sum()) == n
     peak, peak_kind = measured_peak_hbm()
     # per replay of graph_steps steps: time per step and B_req rate (S-degree sum
@@ -566,7 +644,10 @@ def large_bench(fs, torch, n: int, age_dtype: int, sim_steps: int, graph_steps: 
     phases = []
     for r in range(sim_steps // graph_steps):
         S = cnt[r * graph_steps:(r + 1) * graph_steps, 0]
-        b = graph_steps * n * (2 + 2 * b_age + 1 / 8) + float(S.sum()) * (4 + d * (4 + 1 / 8))
+        if step_b is not None:
+            b = float(np.sum(step_b[r * graph_steps:(r + 1) * graph_steps]))
+        else:
+            b = graph_steps * n * (2 + 2 * b_age + 1 / 8) + float(S.sum()) * (4 + d * (4 + 1 / 8))
         phases.append([r * graph_steps, round(float(ms[r]) * 1e3 / graph_steps, 1),
                        round(b / (float(ms[r]) * 1e-3) / 1e9, 0), round(float(S.mean()) / n, 3)])
     steps_timed = (sim_steps // graph_steps) * graph_steps
@@ -585,6 +666,7 @@ def large_bench(fs, torch, n: int, age_dtype: int, sim_steps: int, graph_steps: 
                          "frac_dense": round(dense / (step_ms * 1e-3) / 1e9 / peak, 4),
                          "algorithmic_bytes_per_step": round(per_step_bytes),
                          "dense_bytes_per_step": round(dense)},
+            "pressure": "push" if pressure_used == fs.FS_PRESSURE_PUSH else "gather",
             "phases_step_us_gbs_sfrac": phases,
             "final_counts": [int(x) for x in counts[-1]], "graph_device_bytes": int(gbytes),
             "graph": "random 10-regular multigraph, device stub pairing (seed 0)"}
@@ -724,7 +806,7 @@ def run_extra(args):
     age = fs.FS_AGE_F16 if args.age == "f16" else fs.FS_AGE_F32
     if args.workload == "ensemble":
         res = ensemble_bench(fs, torch, n_graphs=args.ens_graphs, n_lo=1e4, n_hi=2e6, steps=args.ens_steps,
-                             age_dtype=age)
+                             age_dtype=age, pressure=PRESSURE[args.pressure])
     elif args.workload == "precision":
         res = precision_bench(fs, torch, n=args.n, steps=args.sim_steps, reps=1000)
     elif args.workload == "large":

@@ -71,9 +71,13 @@ enum { FS_DISPATCH_AUTO = 0, FS_DISPATCH_THREAD = 1, FS_DISPATCH_MERGE = 2, FS_D
  *     step no longer grows with the edges of S rows. Needs every node of the
  *     one-thread-per-node class to have in-degree <= 255 (true for every
  *     dispatch except FS_DISPATCH_THREAD on graphs with d_max > 255).
- *   FS_PRESSURE_AUTO (0): PUSH where it is available, else GATHER.
- * Packed ensembles, batches and the server use the gather (AUTO or GATHER;
- * PUSH is FS_EUNSUPPORTED there). */
+ *   FS_PRESSURE_AUTO (0): for a single realisation (fs_sim_*), PUSH where
+ *     it is available, else GATHER; for packed ensembles, batches and the
+ *     server, GATHER: a packed gather reads each column once for all the
+ *     replicates of a node, while pushes are paid per replicate, and on
+ *     GB300 the packed push measured slower at 8 to 32 replicates.
+ *     FS_PRESSURE_PUSH selects the push form there too (every realisation of
+ *     an ensemble or request must pass the same flags). */
 enum { FS_PRESSURE_AUTO = 0, FS_PRESSURE_GATHER = 1, FS_PRESSURE_PUSH = 2 };
 
 /* Holding-time law of a nodal transition (Section 5.1; hazard h = f/S).

@@ -262,6 +262,9 @@ bool push_available(const fs_graph* g)
 // transposed CSR of the graph in internal ids (once per graph)
 cudaError_t ensure_out_csr(fs_graph* g, cudaStream_t st)
 {
+    // graphs are shared by sims and by the server's thread
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
     if (g->d_out_ptr)
         return cudaSuccess;
     const int64_t n = g->n;

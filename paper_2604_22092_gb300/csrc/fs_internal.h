@@ -170,6 +170,17 @@ struct PackSeg {            // one row of the segment table
     unsigned long long* deltas;   // [2][R_pad][3] per-replicate transitions by local step parity
     uint32_t* counts;       // [R_pad][4] running counts
     uint32_t* out;          // [(steps + 1)][R_pad][4] counts after each step, or null
+    // push form of the pressure (push != 0; the masks above are then unused):
+    // per (node, replicate) infectious in-neighbour counts and pending +1/-1
+    // tallies by local step parity, laid out like X, and the transposed CSR
+    int32_t push;
+    int32_t pad2_;
+    uint8_t* pc8;                   // [n_thr][R_pad] counts of the thread class
+    uint16_t* ppd[2];               // [n_thr][R_pad] tallies: +1 low byte, -1 high byte
+    uint32_t* phc;                  // [n_m][R_pad] counts of merge-class nodes
+    unsigned long long* phpd[2];    // [n_m][R_pad] tallies: +1 low word, -1 high word
+    const int64_t* out_ptr;         // [n + 1]
+    const int32_t* out_col;         // [nnz]
 };
 
 // The segment table is ordered by replicate width (R_pad 8, 16, 32); each
@@ -178,7 +189,8 @@ struct PackArgs {
     const PackSeg* seg;       // segment table
     const int64_t* thr_pre;   // [n_seg + 1] exclusive prefix of SELL work items
     const int64_t* hub_pre;   // [n_seg + 1] exclusive prefix of hub rows
-    const int32_t* cls;       // [4] rows [cls[c], cls[c+1]) have R_pad = 8 << c (device, updated between launches)
+    const int32_t* cls;       // [7] rows [cls[2c+f], cls[2c+f+1]) have R_pad = 8 << c and pressure form f
+                              // (0 gather, 1 push) (device, updated between launches)
     DevCtl* ctl;              // global step counter and error word
     int32_t j;                // step offset within the launch sequence
 };

@@ -43,11 +43,14 @@ cudaError_t launch_transpose(const int64_t* sell_off, const int32_t* sell_col, c
                              unsigned long long* cursor, int32_t* out_col, bool fill, cudaStream_t s);
 
 // fs_pack.cu
-// one step of the segments of replicate-width class cls (R_pad = 8 << cls)
-cudaError_t launch_pack_step(const PackArgs& a, int cls, int age_dtype, int grid, cudaStream_t s);
+// one step of the segments of replicate-width class cls (R_pad = 8 << cls) in
+// one pressure form (push or gather)
+cudaError_t launch_pack_step(const PackArgs& a, int cls, bool push, int age_dtype, int grid, cudaStream_t s);
 cudaError_t launch_pack_init(uint8_t* X, int n, int R_pad, int R, const int32_t* idx, int64_t n_idx,
                              const int32_t* inv, int state, void* mask, cudaStream_t s);
 int pack_grid(int num_sms, int cls);   // persistent grid of the packed step kernel of class cls
+// initial counts of a push-form segment from its state (counts zeroed before)
+cudaError_t launch_pack_push_init(const PackSeg& g, cudaStream_t s);
 cudaError_t launch_pack_advance(DevCtl* ctl, int K, cudaStream_t s);   // global step += K
 
 // fs_ingest.cu

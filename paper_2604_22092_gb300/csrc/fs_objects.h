@@ -86,6 +86,10 @@ inline cudaError_t dev_alloc(T** p, size_t count, int64_t* bytes)
 }
 fs_status check_params(const fs_sim_params* p);
 fs::ModelF to_model(const fs_sim_params& p);
+// the push form of the pressure: available when the thread class's in-degrees
+// fit u8 counts; the transposed CSR of a graph, built once (thread-safe)
+bool push_available(const fs_graph* g);
+cudaError_t ensure_out_csr(fs_graph* g, cudaStream_t st);
 // the dispatch autotuner (fs_tune.cpp): builds the graph with the class split
 // it chooses for this degree profile (base: the caller's options, AUTO)
 fs_status tune_create(int64_t n, int64_t nnz, int64_t dmax, const int64_t* row_ptr, const int32_t* col_ind,

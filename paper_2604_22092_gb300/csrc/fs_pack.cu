@@ -156,15 +156,120 @@ __device__ __forceinline__ bool has_byte(uint64_t v, uint32_t b)
     return ((x - 0x0101010101010101ull) & ~x & 0x8080808080808080ull) != 0ull;
 }
 
+// 0xff in every byte of v that is 0 (an S replicate)
+__device__ __forceinline__ uint64_t s_bytes(uint64_t v)
+{
+    return (uint64_t)__vcmpeq4((uint32_t)v, 0u) | ((uint64_t)__vcmpeq4((uint32_t)(v >> 32), 0u) << 32);
+}
+
+// bit r of b (r < 4) -> 1 << (16 r): one 16-bit tally field per replicate
+__device__ __forceinline__ uint64_t spread16(uint32_t b)
+{
+    return (uint64_t)(b & 1u) | ((uint64_t)((b >> 1) & 1u) << 16) | ((uint64_t)((b >> 2) & 1u) << 32) |
+           ((uint64_t)((b >> 3) & 1u) << 48);
+}
+
+// One out-edge of a packed push: node j receives +1 for each replicate in
+// `en` and -1 for each in `lv` (RP-bit masks) in its pending tallies of
+// parity par. Thread-class nodes take one 64-bit atomic per 4-replicate word
+// holding an event (tallies are bytes inside 16-bit fields and never exceed
+// the in-degree, so no carry crosses a field); merge-class nodes one atomic
+// per replicate.
+template <int RP>
+__device__ __forceinline__ void pack_push_edge(const PackSeg& g, uint32_t par, uint32_t j, uint32_t en, uint32_t lv)
+{
+    if (j < (uint32_t)g.n_thr) {
+        unsigned long long* w = reinterpret_cast<unsigned long long*>(g.ppd[par] + (int64_t)j * RP);
+#pragma unroll
+        for (int q = 0; q < RP / 4; ++q) {
+            const uint32_t e4 = (en >> (4 * q)) & 0xfu, l4 = (lv >> (4 * q)) & 0xfu;
+            if (e4 | l4)
+                atomicAdd(w + q, (unsigned long long)(spread16(e4) | (spread16(l4) << 8)));
+        }
+    } else if (j < (uint32_t)g.n) {
+        unsigned long long* w = g.phpd[par] + (int64_t)(j - (uint32_t)g.n_thr) * RP;
+        uint32_t m = en | lv;
+        while (m) {
+            const int r = __ffs(m) - 1;
+            m &= m - 1u;
+            atomicAdd(w + r, ((en >> r) & 1u) ? 1ull : (1ull << 32));
+        }
+    }
+}
+
+// Warp-wide packed pushes: lane l's event is node `node` with replicate masks
+// (en, lv) (both 0: no event). The warp flattens the events' transposed rows
+// into one edge range and strides over it (every lane takes part in every
+// shuffle); `list` is this warp's 3 x 32 words of shared memory.
+template <int RP>
+__device__ __forceinline__ void pack_warp_push(const PackSeg& g, uint32_t par, int node, uint32_t en, uint32_t lv,
+                                               uint32_t* __restrict__ list)
+{
+    const int lane = threadIdx.x & 31;
+    const bool has = (en | lv) != 0u;
+    const uint32_t bal = __ballot_sync(kFullP, has);
+    if (!bal)
+        return;
+    const int nev = __popc(bal);
+    const int slot = __popc(bal & ((1u << lane) - 1u));
+    if (has) {
+        list[slot] = (uint32_t)node;
+        list[32 + slot] = en;
+        list[64 + slot] = lv;
+    }
+    __syncwarp();
+    int64_t lo = 0, len = 0;
+    uint32_t me = 0u, ml = 0u;
+    if (lane < nev) {
+        const int v = (int)list[lane];
+        me = list[32 + lane];
+        ml = list[64 + lane];
+        lo = __ldg(g.out_ptr + v);
+        len = __ldg(g.out_ptr + v + 1) - lo;
+    }
+    int64_t off = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(kFullP, off, o);
+        if (lane >= o)
+            off += y;
+    }
+    const int64_t tot = __shfl_sync(kFullP, off, 31);
+    off -= len;
+    for (int64_t q0 = 0; q0 < tot; q0 += 32) {
+        const int64_t q = q0 + lane;
+        int l = 0;
+#pragma unroll
+        for (int st = 16; st > 0; st >>= 1) {
+            const int64_t o = __shfl_sync(kFullP, off, l + st);
+            if (o <= q)
+                l += st;
+        }
+        const int64_t lo_l = __shfl_sync(kFullP, lo, l);
+        const int64_t off_l = __shfl_sync(kFullP, off, l);
+        const uint32_t en_l = __shfl_sync(kFullP, me, l);
+        const uint32_t lv_l = __shfl_sync(kFullP, ml, l);
+        if (q < tot)
+            pack_push_edge<RP>(g, par, (uint32_t)__ldg(g.out_col + lo_l + (q - off_l)), en_l, lv_l);
+    }
+    __syncwarp();     // the list is reused by the warp's next item
+}
+
 // SELL slice: lane = node, each lane carries all RP replicates of its node.
 // One column load and one RP-bit mask load per edge serve every replicate;
 // the mask bits are spread into byte counters (8 per 64-bit word) through a
 // 256-entry table in shared memory. Replicates are then processed in groups
 // of 8 with vector loads and stores of their states and ages; one Philox
 // call serves the replicates that share a key and a counter (rep / 4).
-template <typename AgeT, int RP>
+//
+// Push form (PUSH): instead of the row gather, each S replicate's count is
+// its stored count plus the +1 tally minus the -1 tally of the previous
+// step's pushes (bytewise on 8 replicates at once: every byte stays within
+// 0..255, so no borrow or carry crosses bytes); replicates that enter or
+// leave I are then pushed by the warp along the transposed rows.
+template <typename AgeT, int RP, bool PUSH>
 __device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slice, const uint64_t* __restrict__ lut,
-                                           float* __restrict__ spv)
+                                           float* __restrict__ spv, uint32_t* __restrict__ wlist)
 {
     using MT = typename MaskOf<RP>::T;
     constexpr int NB = RP / 8;
@@ -177,8 +282,8 @@ __device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slic
     const PackScen* __restrict__ scen = g.scen;
     const int model = g.model;
     // independent loads first: slice offsets, original id, states
-    const int64_t off = __ldg(g.sell_off + slice);
-    const int64_t off_end = __ldg(g.sell_off + slice + 1);
+    const int64_t off = PUSH ? 0 : __ldg(g.sell_off + slice);
+    const int64_t off_end = PUSH ? 0 : __ldg(g.sell_off + slice + 1);
     const uint32_t orig = (valid && g.perm) ? (uint32_t)__ldg(g.perm + i) : (uint32_t)i;
     uint64_t xs[NB];
     const uint64_t* xp = reinterpret_cast<const uint64_t*>(g.X + (int64_t)i * RP);
@@ -192,7 +297,7 @@ __device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slic
         anyS |= has_byte(xs[b], (uint32_t)kS);
     }
     if (__all_sync(kFullP, allR)) {
-        if (valid)
+        if (!PUSH && valid)
             mkn[i] = (MT)0;
         return;
     }
@@ -215,7 +320,31 @@ __device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slic
 #pragma unroll
     for (int b = 0; b < NB; ++b)
         cnt[b] = 0ull;
-    if (anyS) {
+    if (PUSH && anyS && valid) {
+        const uint32_t par = (uint32_t)(k & 1);
+        uint64_t* cp = reinterpret_cast<uint64_t*>(g.pc8 + (int64_t)i * RP);
+        uint4* pp = reinterpret_cast<uint4*>(g.ppd[par ^ 1u] + (int64_t)i * RP);
+        bool nz = false;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const uint64_t c8 = cp[b];
+            const uint4 w = pp[b];
+            const uint64_t plus = (uint64_t)__byte_perm(w.x, w.y, 0x6420u) | ((uint64_t)__byte_perm(w.z, w.w, 0x6420u) << 32);
+            const uint64_t minus = (uint64_t)__byte_perm(w.x, w.y, 0x7531u) | ((uint64_t)__byte_perm(w.z, w.w, 0x7531u) << 32);
+            const uint64_t m = s_bytes(xs[b]);
+            cnt[b] = ((c8 & m) - (minus & m)) + (plus & m);
+            nz |= (w.x | w.y | w.z | w.w) != 0u;
+        }
+        if (nz) {
+            // fold the tallies into the counts and clear them for the next step
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                cp[b] = cnt[b];
+                pp[b] = make_uint4(0u, 0u, 0u, 0u);
+            }
+        }
+    }
+    if (!PUSH && anyS) {
         const int w = (int)((off_end - off) >> 5);
         const int32_t* __restrict__ p = g.sell_col + off + lane;
         for (int t0 = 0; t0 < w; t0 += B) {
@@ -232,7 +361,7 @@ __device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slic
             }
         }
     }
-    uint32_t newmask = 0;
+    uint32_t newmask = 0, oldmask = 0;
     // Philox cache: counter word 2 and key of the last draw
     uint4 ph = make_uint4(0u, 0u, 0u, 0u);
     uint32_t ph_k0 = 0u, ph_k1 = 0u, ph_c2 = 0xffffffffu;
@@ -332,6 +461,7 @@ __device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slic
             fE |= (uint32_t)(fired && x == kE) << q;
             fI |= (uint32_t)(fired && x == kI) << q;
             newmask |= (uint32_t)(xn == kI) << (b * 8 + q);
+            oldmask |= (uint32_t)(x == kI) << (b * 8 + q);
         }
         if (valid) {
             if (xnew != xv)
@@ -351,8 +481,13 @@ __device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slic
                 add_deltas(g, k, b * 8 + q, a, e, h);
         }
     }
-    if (valid)
-        mkn[i] = (MT)newmask;
+    if constexpr (PUSH) {
+        const uint32_t en = valid ? newmask & ~oldmask : 0u, lv = valid ? oldmask & ~newmask : 0u;
+        pack_warp_push<RP>(g, (uint32_t)(k & 1), i, en, lv, wlist);
+    } else {
+        if (valid)
+            mkn[i] = (MT)newmask;
+    }
 }
 
 // hub row: one warp, lane r < L is replicate r; 32 edges per window
@@ -414,6 +549,54 @@ __device__ __forceinline__ void pack_hub_row(const PackSeg& g, int64_t k, int ro
         add_deltas(g, k, lane, t.fired && x == kS, t.fired && x == kE, t.fired && x == kI);
 }
 
+// hub row, push form: lane r < L is replicate r; its count is folded from its
+// pending tallies, and the replicates that enter or leave I are pushed by the
+// whole warp along the node's transposed row
+template <typename AgeT, int L>
+__device__ __forceinline__ void pack_hub_row_push(const PackSeg& g, int64_t k, int row)
+{
+    const int lane = threadIdx.x & 31;
+    const int i = g.n_thr + row;
+    const bool mine = lane < L;
+    const uint32_t par = (uint32_t)(k & 1);
+    const int64_t off_state = (int64_t)i * L + lane;
+    AgeT* __restrict__ A = static_cast<AgeT*>(g.A);
+    const int x = mine ? (int)g.X[off_state] : kR;
+    float age = 0.0f;
+    if (x == kE || x == kI)
+        age = AgeIO<AgeT>::load(A[off_state]);
+    uint32_t c = 0u;
+    if (x == kS) {
+        const int64_t h = (int64_t)row * L + lane;
+        unsigned long long* pr = g.phpd[par ^ 1u] + h;
+        const unsigned long long d = *pr;
+        c = g.phc[h];
+        if (d) {
+            c = c + (uint32_t)(d & 0xffffffffull) - (uint32_t)(d >> 32);
+            g.phc[h] = c;
+            *pr = 0ull;
+        }
+    }
+    const PackScen& S = g.scen[mine ? lane : 0];
+    PackTail t{x, 0.0f, false};
+    if (mine)
+        t = pack_tail(S, g.model, x, age, c, g.perm, i, (uint32_t)k);
+    if (mine) {
+        if (t.x != x)
+            g.X[off_state] = (uint8_t)t.x;
+        if (t.fired || x == kE || x == kI)
+            A[off_state] = AgeIO<AgeT>::store(t.age);
+        add_deltas(g, k, lane, t.fired && x == kS, t.fired && x == kE, t.fired && x == kI);
+    }
+    const uint32_t en = __ballot_sync(kFullP, mine && t.x == kI && x != kI);
+    const uint32_t lv = __ballot_sync(kFullP, mine && x == kI && t.x != kI);
+    if (en | lv) {
+        const int64_t e0 = __ldg(g.out_ptr + i), e1 = __ldg(g.out_ptr + i + 1);
+        for (int64_t e = e0 + lane; e < e1; e += 32)
+            pack_push_edge<L>(g, par, (uint32_t)__ldg(g.out_col + e), en, lv);
+    }
+}
+
 // integrate the deltas of the segment's previous step and write its row
 __device__ __forceinline__ void pack_integrate(const PackSeg& g, int64_t k)
 {
@@ -448,14 +631,17 @@ __device__ __forceinline__ void pack_integrate(const PackSeg& g, int64_t k)
 // register budget that measured fastest for each (80 and 96 registers).
 template <int RP> struct PackOcc { static constexpr int kMinBlocks = RP == 8 ? 6 : 5; };
 
-template <typename AgeT, int RP>
+template <typename AgeT, int RP, bool PUSH>
 __global__ void __launch_bounds__(kPackThreads, PackOcc<RP>::kMinBlocks) pack_step_kernel(const __grid_constant__ PackArgs a)
 {
     // byte r of lut[m] is bit r of m: spreads an 8-replicate mask into byte counters
     __shared__ uint64_t lut[256];
     // per warp: the probabilities of one 8-replicate group, [q][lane]
     __shared__ float s_pv[kPackThreads / 32][8 * 32];
+    // per warp: the push events of one slice (node, entering mask, leaving mask)
+    __shared__ uint32_t s_ev[kPackThreads / 32][3 * 32];
     float* spv = s_pv[threadIdx.x >> 5];
+    uint32_t* wlist = s_ev[threadIdx.x >> 5];
     for (int m = threadIdx.x; m < 256; m += blockDim.x) {
         uint64_t v = 0;
         for (int r = 0; r < 8; ++r)
@@ -463,7 +649,7 @@ __global__ void __launch_bounds__(kPackThreads, PackOcc<RP>::kMinBlocks) pack_st
         lut[m] = v;
     }
     __syncthreads();
-    constexpr int c = RP == 8 ? 0 : RP == 16 ? 1 : 2;
+    constexpr int c = (RP == 8 ? 0 : RP == 16 ? 1 : 2) * 2 + (PUSH ? 1 : 0);
     const int64_t G = a.ctl->step + a.j;
     const int s0 = a.cls[c], s1 = a.cls[c + 1];
     const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -484,7 +670,10 @@ __global__ void __launch_bounds__(kPackThreads, PackOcc<RP>::kMinBlocks) pack_st
         const int64_t k = G - g.join;
         if (k < g.kmin || k >= g.kend)
             continue;
-        pack_hub_row<AgeT, RP>(g, k, (int)(it - __ldg(a.hub_pre + s)));
+        if constexpr (PUSH)
+            pack_hub_row_push<AgeT, RP>(g, k, (int)(it - __ldg(a.hub_pre + s)));
+        else
+            pack_hub_row<AgeT, RP>(g, k, (int)(it - __ldg(a.hub_pre + s)));
     }
     s = s0;
     for (int64_t it = thr0 + gw; it < n_thr; it += W) {
@@ -494,7 +683,8 @@ __global__ void __launch_bounds__(kPackThreads, PackOcc<RP>::kMinBlocks) pack_st
         const int64_t k = G - g.join;
         if (k < g.kmin || k >= g.kend)
             continue;
-        pack_slice<AgeT, RP>(g, k, (int)(it - __ldg(a.thr_pre + s)), lut, spv);   // one item per 32-node slice
+        // one item per 32-node slice
+        pack_slice<AgeT, RP, PUSH>(g, k, (int)(it - __ldg(a.thr_pre + s)), lut, spv, wlist);
     }
 }
 
@@ -525,6 +715,50 @@ __global__ void pack_index_kernel(uint8_t* X, const int32_t* idx, int64_t n_idx,
     }
 }
 
+// initial counts of a push-form segment (counts zeroed before): every node
+// pushes +1, for each replicate in which it is I, into the counts of its
+// out-neighbours (bytes of 32-bit words for the thread class: counts never
+// exceed the in-degree, so no carry crosses bytes)
+__global__ void pack_push_init_kernel(PackSeg g)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= g.n)
+        return;
+    const int RP = g.R_pad;
+    uint32_t im = 0u;
+    for (int r = 0; r < RP; ++r)
+        im |= (uint32_t)(g.X[i * RP + r] == kI) << r;
+    if (!im)
+        return;
+    const int64_t e0 = g.out_ptr[i], e1 = g.out_ptr[i + 1];
+    for (int64_t e = e0; e < e1; ++e) {
+        const uint32_t j = (uint32_t)g.out_col[e];
+        if (j < (uint32_t)g.n_thr) {
+            unsigned int* w = reinterpret_cast<unsigned int*>(g.pc8 + (int64_t)j * RP);
+            for (int q = 0; q < RP / 4; ++q) {
+                const uint32_t b = (im >> (4 * q)) & 0xfu;
+                if (b)
+                    atomicAdd(w + q, (b & 1u) | (((b >> 1) & 1u) << 8) | (((b >> 2) & 1u) << 16) |
+                                         (((b >> 3) & 1u) << 24));
+            }
+        } else if (j < (uint32_t)g.n) {
+            uint32_t m = im;
+            while (m) {
+                const int r = __ffs(m) - 1;
+                m &= m - 1u;
+                atomicAdd(g.phc + (int64_t)(j - (uint32_t)g.n_thr) * RP + r, 1u);
+            }
+        }
+    }
+}
+
+cudaError_t launch_pack_push_init(const PackSeg& g, cudaStream_t s)
+{
+    pack_push_init_kernel<<<(unsigned)((g.n + 255) / 256), 256, 0, s>>>(g);
+    g_launch_count += 1;
+    return cudaGetLastError();
+}
+
 __global__ void pack_advance_kernel(DevCtl* ctl, int K)
 {
     if (threadIdx.x == 0)
@@ -538,24 +772,26 @@ cudaError_t launch_pack_advance(DevCtl* ctl, int K, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <typename AgeT>
+template <typename AgeT, bool PUSH>
 static cudaError_t launch_pack_t(const PackArgs& a, int cls, int grid, cudaStream_t s)
 {
     switch (cls) {
-    case 0: pack_step_kernel<AgeT, 8><<<grid, kPackThreads, 0, s>>>(a); break;
-    case 1: pack_step_kernel<AgeT, 16><<<grid, kPackThreads, 0, s>>>(a); break;
-    default: pack_step_kernel<AgeT, 32><<<grid, kPackThreads, 0, s>>>(a); break;
+    case 0: pack_step_kernel<AgeT, 8, PUSH><<<grid, kPackThreads, 0, s>>>(a); break;
+    case 1: pack_step_kernel<AgeT, 16, PUSH><<<grid, kPackThreads, 0, s>>>(a); break;
+    default: pack_step_kernel<AgeT, 32, PUSH><<<grid, kPackThreads, 0, s>>>(a); break;
     }
     g_launch_count += 1;
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack_step(const PackArgs& a, int cls, int age_dtype, int grid, cudaStream_t s)
+cudaError_t launch_pack_step(const PackArgs& a, int cls, bool push, int age_dtype, int grid, cudaStream_t s)
 {
     switch (age_dtype) {
-    case kAgeF16: return launch_pack_t<__half>(a, cls, grid, s);
-    case kAgeBF16: return launch_pack_t<__nv_bfloat16>(a, cls, grid, s);
-    default: return launch_pack_t<float>(a, cls, grid, s);
+    case kAgeF16: return push ? launch_pack_t<__half, true>(a, cls, grid, s) : launch_pack_t<__half, false>(a, cls, grid, s);
+    case kAgeBF16:
+        return push ? launch_pack_t<__nv_bfloat16, true>(a, cls, grid, s)
+                    : launch_pack_t<__nv_bfloat16, false>(a, cls, grid, s);
+    default: return push ? launch_pack_t<float, true>(a, cls, grid, s) : launch_pack_t<float, false>(a, cls, grid, s);
     }
 }
 
@@ -578,9 +814,9 @@ cudaError_t launch_pack_init(uint8_t* X, int n, int R_pad, int R, const int32_t*
 int pack_grid(int num_sms, int cls)
 {
     int occ = 0;
-    cudaError_t e = cls == 0   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pack_step_kernel<float, 8>, kPackThreads, 0)
-                    : cls == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pack_step_kernel<float, 16>, kPackThreads, 0)
-                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pack_step_kernel<float, 32>, kPackThreads, 0);
+    cudaError_t e = cls == 0   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pack_step_kernel<float, 8, false>, kPackThreads, 0)
+                    : cls == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pack_step_kernel<float, 16, false>, kPackThreads, 0)
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pack_step_kernel<float, 32, false>, kPackThreads, 0);
     if (e != cudaSuccess || occ < 1)
         occ = 4;
     return num_sms * occ;

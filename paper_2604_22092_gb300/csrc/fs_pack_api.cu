@@ -26,6 +26,12 @@ struct fs_ens {
     uint8_t* d_X = nullptr;
     void* d_A = nullptr;
     void* d_mask[2] = {nullptr, nullptr};
+    // push form of the pressure (push = true): counts and pending tallies
+    bool push = false;
+    uint8_t* d_pc8 = nullptr;
+    uint16_t* d_ppd[2] = {nullptr, nullptr};
+    uint32_t* d_phc = nullptr;
+    unsigned long long* d_phpd[2] = {nullptr, nullptr};
     fs::PackScen* d_scen = nullptr;
     float2* d_ptab = nullptr;
     float* d_ps = nullptr;
@@ -70,7 +76,7 @@ struct fs_batch {
     cudaGraphExec_t gexec = nullptr;
     int gK = 0;
     int g_classes = 0;                  // classes launched by the captured graph (bit c)
-    int classes = 0;                    // classes present in the table (bit c: R_pad = 8 << c)
+    int classes = 0;                    // classes present in the table (bit 2c+f: R_pad = 8 << c, form f = push)
     int grid[3] = {0, 0, 0};
     bool failed = false;
 };
@@ -85,6 +91,12 @@ void free_ens(fs_ens* e)
     cudaFree(e->d_A);
     cudaFree(e->d_mask[0]);
     cudaFree(e->d_mask[1]);
+    cudaFree(e->d_pc8);
+    cudaFree(e->d_ppd[0]);
+    cudaFree(e->d_ppd[1]);
+    cudaFree(e->d_phc);
+    cudaFree(e->d_phpd[0]);
+    cudaFree(e->d_phpd[1]);
     cudaFree(e->d_scen);
     cudaFree(e->d_ptab);
     cudaFree(e->d_ps);
@@ -145,6 +157,15 @@ fs::PackSeg segment_of(const Member& m)
     s.deltas = e->d_deltas;
     s.counts = e->d_counts;
     s.out = e->d_out;
+    s.push = e->push ? 1 : 0;
+    s.pc8 = e->d_pc8;
+    s.ppd[0] = e->d_ppd[0];
+    s.ppd[1] = e->d_ppd[1];
+    s.phc = e->d_phc;
+    s.phpd[0] = e->d_phpd[0];
+    s.phpd[1] = e->d_phpd[1];
+    s.out_ptr = g->d_out_ptr;
+    s.out_col = g->d_out_col;
     return s;
 }
 
@@ -177,12 +198,13 @@ fs_status fs_ens_create(fs_graph* g, const fs_sim_params* params, int32_t n_real
         fs_status st = fsapi::check_params(params + r);
         if (st != FS_OK)
             return st;
-        if (params[r].flags == FS_PRESSURE_PUSH)
-            return fail(FS_EUNSUPPORTED, "fs_ens_create: packed ensembles use the gather form of the pressure");
         if (params[r].model != params[0].model || params[r].age_dtype != params[0].age_dtype ||
-            params[r].index_state != params[0].index_state)
-            return fail(FS_EINVAL, "fs_ens_create: realisations must share model, age_dtype and index_state");
+            params[r].index_state != params[0].index_state || params[r].flags != params[0].flags)
+            return fail(FS_EINVAL, "fs_ens_create: realisations must share model, age_dtype, index_state and flags");
     }
+    if (params[0].flags == FS_PRESSURE_PUSH && !fsapi::push_available(g))
+        return fail(FS_EUNSUPPORTED, "fs_ens_create: FS_PRESSURE_PUSH needs in-degrees <= %d in the thread class",
+                    fs::kMaxThreadDeg);
     if (n_index < 0 || n_index > g->n || (n_index > 0 && !index_nodes))
         return fail(FS_EINVAL, "fs_ens_create: bad index list size");
     {
@@ -203,6 +225,9 @@ fs_status fs_ens_create(fs_graph* g, const fs_sim_params* params, int32_t n_real
     e->model = params[0].model;
     e->age_bytes = e->age_dtype == FS_AGE_F32 ? 4 : 2;
     e->mask_bytes = e->R_pad / 8;
+    // packed ensembles default to the gather: it reads each column once for
+    // all replicates, while pushes are paid per replicate (measured slower)
+    e->push = params[0].flags == FS_PRESSURE_PUSH;
     const int64_t n = g->n;
     const int Rp = e->R_pad;
     int32_t* d_idx = nullptr;
@@ -261,6 +286,22 @@ fs_status fs_ens_create(fs_graph* g, const fs_sim_params* params, int32_t n_real
     }
     C_TRY(fs::launch_pack_init(e->d_X, (int)n, Rp, n_real, d_idx, n_index, g->d_inv, params[0].index_state,
                                e->d_mask[0], cs));
+    if (e->push) {
+        const size_t nt = (size_t)g->n_thr * Rp, nm = (size_t)std::max(g->n_m, 1) * Rp;
+        C_TRY(fsapi::ensure_out_csr(g, cs));
+        C_TRY(dev_alloc(&e->d_pc8, nt, &e->bytes));
+        C_TRY(dev_alloc(&e->d_phc, nm, &e->bytes));
+        C_TRY(cudaMemsetAsync(e->d_pc8, 0, std::max<size_t>(nt, 1), cs));
+        C_TRY(cudaMemsetAsync(e->d_phc, 0, sizeof(uint32_t) * nm, cs));
+        for (int q = 0; q < 2; ++q) {
+            C_TRY(dev_alloc(&e->d_ppd[q], nt, &e->bytes));
+            C_TRY(dev_alloc(&e->d_phpd[q], nm, &e->bytes));
+            C_TRY(cudaMemsetAsync(e->d_ppd[q], 0, sizeof(uint16_t) * std::max<size_t>(nt, 1), cs));
+            C_TRY(cudaMemsetAsync(e->d_phpd[q], 0, sizeof(unsigned long long) * nm, cs));
+        }
+        Member m0{e, 0, 0, nullptr};
+        C_TRY(fs::launch_pack_push_init(segment_of(m0), cs));
+    }
     std::vector<uint32_t> cnt((size_t)Rp * 4, 0u);
     for (int r = 0; r < Rp; ++r) {
         if (r < n_real) {
@@ -359,12 +400,12 @@ fs_status fs_batch_create(int32_t age_dtype, int32_t max_members, void* stream, 
     if (e == cudaSuccess) e = dev_alloc(&b->d_seg, (size_t)max_members, nullptr);
     if (e == cudaSuccess) e = dev_alloc(&b->d_thr, (size_t)max_members + 1, nullptr);
     if (e == cudaSuccess) e = dev_alloc(&b->d_hub, (size_t)max_members + 1, nullptr);
-    if (e == cudaSuccess) e = dev_alloc(&b->d_cls, 4, nullptr);
+    if (e == cudaSuccess) e = dev_alloc(&b->d_cls, 7, nullptr);
     if (e == cudaSuccess) e = dev_alloc(&b->d_ctl, 1, nullptr);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_seg, sizeof(fs::PackSeg) * max_members);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_thr, sizeof(int64_t) * (max_members + 1));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_hub, sizeof(int64_t) * (max_members + 1));
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_cls, sizeof(int32_t) * 4);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_cls, sizeof(int32_t) * 7);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ctl, 0, sizeof(fs::DevCtl), b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_cls, 0, sizeof(int32_t) * 4, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_thr, 0, sizeof(int64_t), b->stream);
@@ -420,10 +461,10 @@ static fs_status upload_table(fs_batch* b)
     b->h_hub[0] = 0;
     b->classes = 0;
     int q = 0;
-    for (int c = 0; c < 3; ++c) {                     // rows ordered by replicate width
+    for (int c = 0; c < 6; ++c) {                     // rows ordered by replicate width, then form
         b->h_cls[c] = q;
         for (const Member& m : b->members) {
-            if (width_class(m.e->R_pad) != c)
+            if (width_class(m.e->R_pad) * 2 + (m.e->push ? 1 : 0) != c)
                 continue;
             b->h_seg[q] = segment_of(m);
             const fs_graph* g = m.e->g;
@@ -433,13 +474,13 @@ static fs_status upload_table(fs_batch* b)
             ++q;
         }
     }
-    b->h_cls[3] = q;
+    b->h_cls[6] = q;
     const int ns = q;
     if (ns > 0)
         E_CUDA(b, cudaMemcpyAsync(b->d_seg, b->h_seg, sizeof(fs::PackSeg) * ns, cudaMemcpyHostToDevice, b->stream));
     E_CUDA(b, cudaMemcpyAsync(b->d_thr, b->h_thr, sizeof(int64_t) * (ns + 1), cudaMemcpyHostToDevice, b->stream));
     E_CUDA(b, cudaMemcpyAsync(b->d_hub, b->h_hub, sizeof(int64_t) * (ns + 1), cudaMemcpyHostToDevice, b->stream));
-    E_CUDA(b, cudaMemcpyAsync(b->d_cls, b->h_cls, sizeof(int32_t) * 4, cudaMemcpyHostToDevice, b->stream));
+    E_CUDA(b, cudaMemcpyAsync(b->d_cls, b->h_cls, sizeof(int32_t) * 7, cudaMemcpyHostToDevice, b->stream));
     b->dirty = false;
     return FS_OK;
 }
@@ -456,13 +497,13 @@ static fs::PackArgs pack_args(const fs_batch* b, int j)
     return a;
 }
 
-// one step of every width class present in the table
+// one step of every (width, form) class present in the table
 static cudaError_t launch_classes(const fs_batch* b, int j, int classes)
 {
     cudaError_t e = cudaSuccess;
-    for (int c = 0; c < 3 && e == cudaSuccess; ++c)
+    for (int c = 0; c < 6 && e == cudaSuccess; ++c)
         if (classes & (1 << c))
-            e = fs::launch_pack_step(pack_args(b, j), c, b->age_dtype, b->grid[c], b->stream);
+            e = fs::launch_pack_step(pack_args(b, j), c / 2, (c & 1) != 0, b->age_dtype, b->grid[c / 2], b->stream);
     return e;
 }
 

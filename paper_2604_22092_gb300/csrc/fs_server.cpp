@@ -47,11 +47,17 @@ struct Request {
     int64_t load() const { return n * (int64_t)params.size(); }   // node updates per launch
 };
 
-int64_t ensemble_bytes(int64_t n, int R, int age_bytes, int64_t steps)
+// device memory of one ensemble (states, ages, masks, tables, counts rows; in
+// the push form also the per-replicate counts and pending tallies: 1 + 2 x 2
+// bytes per thread-class node, 4 + 2 x 8 per merge-class node)
+int64_t ensemble_bytes(int64_t n, int64_t n_merge, int R, int age_bytes, int64_t steps, bool push)
 {
     const int64_t Rp = R <= 8 ? 8 : R <= 16 ? 16 : 32;
-    return n * Rp * (1 + age_bytes) + 2 * (n + 1) * (Rp / 8) + (int64_t)R * (2 * 4096 * 8 + 256 * 4) +
-           (steps + 1) * Rp * 16 + 4096;
+    int64_t b = n * Rp * (1 + age_bytes) + 2 * (n + 1) * (Rp / 8) + (int64_t)R * (2 * 4096 * 8 + 256 * 4) +
+                (steps + 1) * Rp * 16 + 4096;
+    if (push)
+        b += (n - n_merge) * Rp * 5 + std::max<int64_t>(n_merge, 1) * Rp * 20;
+    return b;
 }
 
 }  // namespace
@@ -294,9 +300,13 @@ fs_status fs_server_submit(fs_server* s, fs_graph* g, const fs_sim_params* scena
             delete q;
             return st;
         }
-        if (p.flags == FS_PRESSURE_PUSH) {
+        if (sc > 0 && p.flags != scenarios[0].flags) {
             delete q;
-            return fail(FS_EUNSUPPORTED, "fs_server_submit: served ensembles use the gather form of the pressure");
+            return fail(FS_EINVAL, "fs_server_submit: scenarios must share flags");
+        }
+        if (p.flags == FS_PRESSURE_PUSH && !fsapi::push_available(g)) {
+            delete q;
+            return fail(FS_EUNSUPPORTED, "fs_server_submit: FS_PRESSURE_PUSH is not available on this graph");
         }
         if (sc > 0 && (p.model != scenarios[0].model || p.index_state != scenarios[0].index_state)) {
             delete q;
@@ -309,8 +319,10 @@ fs_status fs_server_submit(fs_server* s, fs_graph* g, const fs_sim_params* scena
         }
     }
     const int age_bytes = s->cfg.age_dtype == FS_AGE_F32 ? 4 : 2;
+    const bool push = scenarios[0].flags == FS_PRESSURE_PUSH;
     for (size_t off = 0; off < q->params.size(); off += 32)
-        q->bytes += ensemble_bytes(q->n, (int)std::min<size_t>(32, q->params.size() - off), age_bytes, steps);
+        q->bytes += ensemble_bytes(q->n, g->n_m, (int)std::min<size_t>(32, q->params.size() - off), age_bytes, steps,
+                                   push);
     if (q->bytes > s->budget) {
         const int64_t b = q->bytes;
         delete q;

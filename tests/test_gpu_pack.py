@@ -6,8 +6,9 @@ must produce exactly the counts and the final state it produces alone
 through fs_sim_*, whatever the number of replicates (padding to 8, 16 or 32
 lanes), the graph (regular, or Barabasi-Albert with hub rows), the age
 storage, and whether the ensemble runs alone, in a batch with others, or
-joins a batch that is already running. One small ensemble is also compared
-with the oracle directly.
+joins a batch that is already running, and in both forms of the pressure
+(push, the default, and the gather), also mixed in one batch. One small
+ensemble is also compared with the oracle directly.
 """
 import math
 
@@ -29,7 +30,10 @@ def cuda():
     return torch
 
 
-def scenarios(R, seed0=100, age_dtype=fs.FS_AGE_F32):
+PRESSURES = [pytest.param(fs.FS_PRESSURE_PUSH, id="push"), pytest.param(fs.FS_PRESSURE_GATHER, id="gather")]
+
+
+def scenarios(R, seed0=100, age_dtype=fs.FS_AGE_F32, pressure=fs.FS_PRESSURE_AUTO):
     """R realisations with different betas, infectious sigmas and latent laws."""
     rng = np.random.default_rng(seed0)
     out = []
@@ -38,7 +42,8 @@ def scenarios(R, seed0=100, age_dtype=fs.FS_AGE_F32):
         sig = float(rng.uniform(0.3, 1.0))
         latent = fs.law("erlang", 0.75, k=3) if r % 2 == 0 else fs.law("weibull", 2.0, 4.0)
         out.append(fs.sim_params(fs.FS_SEIR, fs.law("lognormal", math.log(6.0), sig), beta, 0.1,
-                                 seed=seed0 + 7 * r, latent=latent, replicate=r, age_dtype=age_dtype))
+                                 seed=seed0 + 7 * r, latent=latent, replicate=r, age_dtype=age_dtype,
+                                 pressure=pressure))
     return out
 
 
@@ -50,10 +55,11 @@ def alone(gh, n, p, idx, steps, age_dtype=fs.FS_AGE_F32):
     return c, X, A
 
 
+@pytest.mark.parametrize("pressure", PRESSURES)
 @pytest.mark.parametrize("kind,R,age_dtype", [("regular", 5, fs.FS_AGE_F32), ("regular", 12, fs.FS_AGE_F32),
                                               ("ba", 32, fs.FS_AGE_F32), ("ba", 8, fs.FS_AGE_F16),
                                               ("er", 16, fs.FS_AGE_BF16)])
-def test_ensemble_equals_each_realisation_alone(cuda, kind, R, age_dtype):
+def test_ensemble_equals_each_realisation_alone(cuda, kind, R, age_dtype, pressure):
     if kind == "regular":
         g = W.random_regular(20_003 + 1, 10, seed=2)
     elif kind == "ba":
@@ -64,7 +70,7 @@ def test_ensemble_equals_each_realisation_alone(cuda, kind, R, age_dtype):
     gh = fs.fs_graph_create(g.n, g.row_ptr, g.col_ind)
     if kind == "ba":
         assert fs.fs_graph_info_get(gh)["n_merge"] > 0
-    ps = scenarios(R, age_dtype=age_dtype)
+    ps = scenarios(R, age_dtype=age_dtype, pressure=pressure)
     steps = 220
     e = fs.fs_ens_create(gh, ps, idx)
     c_ens = fs.fs_ens_run(e, steps, R, graph_steps=50)
@@ -83,13 +89,16 @@ def test_ensemble_equals_each_realisation_alone(cuda, kind, R, age_dtype):
 def test_batch_members_join_leave_and_resume(cuda):
     """Three ensembles on three graphs join a running batch at different
     launches with different lengths; each member's counts equal its
-    realisations alone; an ensemble that left can continue alone."""
+    realisations alone; an ensemble that left can continue alone. The
+    Barabasi-Albert member uses the gather form and the others the push form,
+    so one launch steps segments of both forms."""
     graphs = [W.random_regular(8_000, 6, seed=11), W.barabasi_albert(12_000, 3, seed=12),
               W.erdos_renyi(9_000, 8, seed=13)]
     ghs = [fs.fs_graph_create(g.n, g.row_ptr, g.col_ind) for g in graphs]
     idxs = [W.index_nodes(g.n, 20, seed=21 + q) for q, g in enumerate(graphs)]
     Rs = [12, 3, 20]          # all three replicate widths (16, 8, 32 lanes)
-    params = [scenarios(R, seed0=500 + 100 * q) for q, R in enumerate(Rs)]
+    forms = [fs.FS_PRESSURE_PUSH, fs.FS_PRESSURE_GATHER, fs.FS_PRESSURE_AUTO]
+    params = [scenarios(R, seed0=500 + 100 * q, pressure=forms[q]) for q, R in enumerate(Rs)]
     ens = [fs.fs_ens_create(ghs[q], params[q], idxs[q]) for q in range(3)]
     steps = [150, 90, 120]
     outs = [np.zeros((steps[q] + 1, Rs[q], 4), dtype=np.uint32) for q in range(3)]
@@ -124,11 +133,12 @@ def test_batch_members_join_leave_and_resume(cuda):
         fs.fs_graph_destroy(gh)
 
 
-def test_small_ensemble_matches_oracle(cuda, oracle_mod):
+@pytest.mark.parametrize("pressure", PRESSURES)
+def test_small_ensemble_matches_oracle(cuda, oracle_mod, pressure):
     g = W.barabasi_albert(3_000, 3, seed=8)
     idx = W.index_nodes(g.n, 15, seed=9, allowed=W.non_hub_nodes(g))
     gh = fs.fs_graph_create(g.n, g.row_ptr, g.col_ind, opts=fs.graph_opts(thread_max_deg=31))
-    ps = scenarios(6, seed0=900)
+    ps = scenarios(6, seed0=900, pressure=pressure)
     e = fs.fs_ens_create(gh, ps, idx)
     c_ens = fs.fs_ens_run(e, 200, 6)
     for r in range(6):
@@ -161,5 +171,24 @@ def test_ensemble_argument_errors(cuda):
     fs.fs_batch_run(b, 11)
     assert fs.fs_batch_status(b) == (0, 0)
     fs.fs_batch_destroy(b)
+    fs.fs_ens_destroy(e)
+    fs.fs_graph_destroy(gh)
+
+
+@pytest.mark.parametrize("pressure", PRESSURES)
+def test_sir_ensemble_seeded_infectious_equals_alone(cuda, pressure):
+    """Index cases start in I, so the push form's initial counts come from
+    them (on hub rows too): every realisation equals its run alone."""
+    g = W.barabasi_albert(20_000, 5, seed=31)
+    idx = W.index_nodes(g.n, 25, seed=32)          # hubs allowed
+    gh = fs.fs_graph_create(g.n, g.row_ptr, g.col_ind)
+    ps = [fs.sim_params(fs.FS_SIR, fs.law("lognormal", math.log(5.0), 0.5 + 0.05 * r), 0.1 + 0.03 * r, 0.1,
+                        seed=77 + r, replicate=r, pressure=pressure) for r in range(9)]
+    e = fs.fs_ens_create(gh, ps, idx)
+    c_ens = fs.fs_ens_run(e, 150, 9, graph_steps=30)
+    for r in range(9):
+        c, X, _ = alone(gh, g.n, ps[r], idx, 150)
+        np.testing.assert_array_equal(c_ens[:, r, :], c, err_msg=f"replicate {r}")
+    assert c_ens[-1, :, 3].min() > 0
     fs.fs_ens_destroy(e)
     fs.fs_graph_destroy(gh)
