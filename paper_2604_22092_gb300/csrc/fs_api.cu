@@ -661,8 +661,7 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
     }
     cudaStream_t cs = s->stream;
     const size_t words = ((size_t)(n >> 5) + 1 + 3) / 4 * 4;
-    // whole 16-node groups for vector access, plus 16 nodes for the push
-    // step's rounded-up L2 prefetch ranges
+    // whole 16-node groups (+16) for the vector accesses of the push step
     const size_t n_pad = ((size_t)n + 15) / 16 * 16 + 16;
     S_CUDA(dev_alloc(&s->d_X, n_pad, nullptr));
     S_CUDA(cudaMalloc(&s->d_A, n_pad * s->age_bytes));

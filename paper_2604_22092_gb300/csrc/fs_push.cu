@@ -546,6 +546,8 @@ __device__ __forceinline__ void item_apply(const StepArgs& a, uint32_t par, Item
 // search over the lanes' offsets. A batch costs two dependent memory round
 // trips however many events it holds. Every lane of the warp must call this.
 // ---------------------------------------------------------------------------
+constexpr int64_t kPushLongRow = 128;    // rows longer than this are pushed one at a time
+
 template <bool INIT>
 __device__ __forceinline__ void warp_push(const StepArgs& a, uint32_t par, uint32_t ev, uint32_t neg, int base,
                                           uint32_t* __restrict__ list)
@@ -582,6 +584,29 @@ __device__ __forceinline__ void warp_push(const StepArgs& a, uint32_t par, uint3
             lo = __ldg(a.out_ptr + node);
             len = __ldg(a.out_ptr + node + 1) - lo;
         }
+        // long rows (hubs) one at a time, the warp striding over each with
+        // its column loads issued four ahead; they leave the flattened batch
+        uint32_t lng = __ballot_sync(kFull, len > kPushLongRow);
+        while (lng) {
+            const int l = __ffs(lng) - 1;
+            lng &= lng - 1u;
+            const int64_t lo_l = __shfl_sync(kFull, lo, l), len_l = __shfl_sync(kFull, len, l);
+            const bool minus = (__shfl_sync(kFull, evw, l) >> 31) != 0u;
+            const int32_t* __restrict__ col = a.out_col + lo_l;
+            int64_t q = lane;
+            for (; q + 96 < len_l; q += 128) {
+                const uint32_t j0 = (uint32_t)__ldg(col + q), j1 = (uint32_t)__ldg(col + q + 32);
+                const uint32_t j2 = (uint32_t)__ldg(col + q + 64), j3 = (uint32_t)__ldg(col + q + 96);
+                push_one<INIT>(a, par, j0, minus);
+                push_one<INIT>(a, par, j1, minus);
+                push_one<INIT>(a, par, j2, minus);
+                push_one<INIT>(a, par, j3, minus);
+            }
+            for (; q < len_l; q += 32)
+                push_one<INIT>(a, par, (uint32_t)__ldg(col + q), minus);
+        }
+        if (len > kPushLongRow)
+            len = 0;
         int64_t off = len;                          // inclusive scan of the lengths
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -614,22 +639,14 @@ __device__ __forceinline__ void warp_push(const StepArgs& a, uint32_t par, uint3
     __syncwarp();     // the list is reused by the warp's next item
 }
 
-// Bulk prefetch of a byte range into L2 (TMA; 16-byte aligned start, size a
-// multiple of 16): a hint with no register destination.
-__device__ __forceinline__ void l2_prefetch(const void* p, uint32_t bytes)
-{
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
-constexpr int kPushPrefetchRounds = 2;     // grid-stride rounds prefetched ahead
+constexpr int kScanRounds = 4;      // grid-stride rounds whose loads a warp issues together
 
 // ---------------------------------------------------------------------------
 // One whole step: items are groups of kPushG thread-class nodes, then single
-// merge-class nodes; warps stride over them (grid-stride, the next item's
-// early loads in flight while the current one is processed). Per-step deltas
-// as in the gather form.
+// merge-class nodes; warps stride over them (grid-stride). Per-step deltas as
+// in the gather form.
 // ---------------------------------------------------------------------------
-template <typename AgeT>
+template <typename AgeT, bool SCAN>
 __global__ void __launch_bounds__(kPushThreads, kPushCtasPerSm) push_step_kernel(const __grid_constant__ StepArgs a)
 {
     __shared__ unsigned long long s_delta[kDeltaFields];
@@ -644,54 +661,73 @@ __global__ void __launch_bounds__(kPushThreads, kPushCtasPerSm) push_step_kernel
     // counts and tallies are loaded a round ahead while S nodes are common
     // (counts of the state at the start of this launch sequence)
     const bool spec_s = (int64_t)a.ctl->counts[0] * 16 >= (int64_t)a.n;
-    const bool spec_ei = ((int64_t)a.ctl->counts[1] + a.ctl->counts[2]) * 16 >= (int64_t)a.n;
     PushDeltas ld;
     const int64_t n_grp = ((int64_t)a.n_thr + kPushG - 1) / kPushG;
     const int64_t total = n_grp + a.n_m;
     const int64_t stride = (int64_t)gridDim.x * kPushThreads;
-    int64_t t0 = (int64_t)blockIdx.x * kPushThreads + (tid & ~31);
-    GroupLoads cur = group_loads(a, par, t0 + lane, n_grp, spec_s);
-    for (; t0 < total; t0 += stride) {
-        const int64_t t = t0 + lane;
-        // the warp's groups kPushPrefetchRounds rounds ahead go to L2 now (the
-        // arrays are padded past their last whole group by 16 elements, so the
-        // rounded-up ranges stay inside them)
-        const int64_t tp = t0 + kPushPrefetchRounds * stride;
-        if (lane == 0 && tp < n_grp) {
-            const int64_t ng = min((int64_t)32, n_grp - tp);
-            const int64_t i0 = tp * kPushG;
-            const uint32_t nb = (uint32_t)(ng * kPushG);               // bytes of one byte per node
-            l2_prefetch(a.X + i0, (nb + 15u) & ~15u);
-            if (spec_s) {
-                l2_prefetch(a.cnt8 + i0, (nb + 15u) & ~15u);
-                l2_prefetch(a.pd16[par ^ 1u] + i0, nb * 2u);
-            }
-            if (spec_ei)
-                l2_prefetch(static_cast<const AgeT*>(a.A) + i0, nb * (uint32_t)sizeof(AgeT));
-        }
-        // the next item's loads are in flight while this one is processed
-        const GroupLoads nxt = group_loads(a, par, t + stride, n_grp, spec_s);
-        // a warp whose items are all idle (and holds no merge-class node)
-        // skips the round
+    // Warps take kScanRounds grid-stride rounds at a time: the loads that tell
+    // whether an item has work (states; counts and tallies while S is common)
+    // are issued for all of them together, and only the rounds in which some
+    // lane of the warp has work are processed, so a mostly idle sweep (the
+    // all-S start, the mostly-R tail) waits for memory once per kScanRounds
+    // rounds instead of once per round.
+    // One item per lane (the grid covers every item at once): no scan.
+    if constexpr (!SCAN) {
+        const int64_t t = (int64_t)blockIdx.x * kPushThreads + tid;
+        GroupLoads cur = group_loads(a, par, t, n_grp, spec_s);
         const bool idle = (t < n_grp || t >= total) && group_idle(a, par, t, n_grp, cur);
-        if (__all_sync(kFull, idle)) {
-            cur = nxt;
-            continue;
+        if (!__all_sync(kFull, idle)) {
+            Item it;
+            it.kind = kItemNone;
+            it.base = 0;
+            it.need = 0u;
+            if (t < n_grp)
+                group_prepare<AgeT>(a, par, (int)(t * kPushG), cur, it, pslot);
+            else if (t < total)
+                hub_prepare<AgeT>(a, par, a.n_thr + (int)(t - n_grp), it, pslot);
+            __syncwarp();
+            const uint32_t fired = warp_draws(a, (uint32_t)k, it, w);
+            uint32_t ev = 0u, neg = 0u;
+            item_apply<AgeT>(a, par, it, fired, ev, neg, ld);
+            warp_push<false>(a, par, ev, neg, it.base, w.ev);
         }
-        Item it;
-        it.kind = kItemNone;
-        it.base = 0;
-        it.need = 0u;
-        if (t < n_grp)
-            group_prepare<AgeT>(a, par, (int)(t * kPushG), cur, it, pslot);
-        else if (t < total)
-            hub_prepare<AgeT>(a, par, a.n_thr + (int)(t - n_grp), it, pslot);
-        __syncwarp();
-        const uint32_t fired = warp_draws(a, (uint32_t)k, it, w);
-        uint32_t ev = 0u, neg = 0u;
-        item_apply<AgeT>(a, par, it, fired, ev, neg, ld);
-        warp_push<false>(a, par, ev, neg, it.base, w.ev);
-        cur = nxt;
+    }
+    for (int64_t tb = (int64_t)blockIdx.x * kPushThreads + (tid & ~31); SCAN && tb < total;
+         tb += (int64_t)kScanRounds * stride) {
+        uint32_t busy = 0u;
+        {
+            GroupLoads gl[kScanRounds];
+#pragma unroll
+            for (int u = 0; u < kScanRounds; ++u)
+                gl[u] = group_loads(a, par, tb + u * stride + lane, n_grp, spec_s);
+#pragma unroll
+            for (int u = 0; u < kScanRounds; ++u) {
+                const int64_t t = tb + u * stride + lane;
+                const bool idle = (t < n_grp || t >= total) && group_idle(a, par, t, n_grp, gl[u]);
+                busy |= (idle ? 0u : 1u) << u;
+            }
+        }
+        uint32_t wb = __reduce_or_sync(kFull, busy);
+        while (wb) {
+            const int u = __ffs(wb) - 1;
+            wb &= wb - 1u;
+            const int64_t t = tb + u * stride + lane;
+            // reloaded: these lines were read by the scan just above
+            const GroupLoads cur = group_loads(a, par, t, n_grp, spec_s);
+            Item it;
+            it.kind = kItemNone;
+            it.base = 0;
+            it.need = 0u;
+            if (t < n_grp)
+                group_prepare<AgeT>(a, par, (int)(t * kPushG), cur, it, pslot);
+            else if (t < total)
+                hub_prepare<AgeT>(a, par, a.n_thr + (int)(t - n_grp), it, pslot);
+            __syncwarp();
+            const uint32_t fired = warp_draws(a, (uint32_t)k, it, w);
+            uint32_t ev = 0u, neg = 0u;
+            item_apply<AgeT>(a, par, it, fired, ev, neg, ld);
+            warp_push<false>(a, par, ev, neg, it.base, w.ev);
+        }
     }
     const uint32_t fs_ = __reduce_add_sync(kFull, ld.fS), fe = __reduce_add_sync(kFull, ld.fE);
     const uint32_t fi = __reduce_add_sync(kFull, ld.fI), ds = __reduce_add_sync(kFull, ld.dS);
@@ -775,7 +811,11 @@ static cudaError_t launch_push_step_t(const StepArgs& a, cudaStream_t s, int num
     const int64_t need = (items + kPushThreads - 1) / kPushThreads;
     const int64_t cap = (int64_t)num_sms * kPushCtasPerSm;
     const int grid = (int)std::max<int64_t>(1, std::min(need, cap));
-    push_step_kernel<AgeT><<<grid, kPushThreads, 0, s>>>(a);
+    // one item per lane when the grid covers them all, else the block scan
+    if (need <= cap)
+        push_step_kernel<AgeT, false><<<grid, kPushThreads, 0, s>>>(a);
+    else
+        push_step_kernel<AgeT, true><<<grid, kPushThreads, 0, s>>>(a);
     g_launch_count += 1;
     return cudaGetLastError();
 }
