@@ -76,22 +76,7 @@ void free_sim(fs_sim* s)
         return;
     if (s->gexec)
         cudaGraphExecDestroy(s->gexec);
-    cudaFree(s->d_X);
-    cudaFree(s->d_A);
-    cudaFree(s->d_bm[0]);
-    cudaFree(s->d_bm[1]);
-    cudaFree(s->d_m_cnt);
-    cudaFree(s->d_m_tkt);
-    cudaFree(s->d_ctl);
-    cudaFree(s->d_deltas);
-    cudaFree(s->d_ptab);
-    cudaFree(s->d_ps);
-    cudaFree(s->d_cnt8);
-    cudaFree(s->d_pd16[0]);
-    cudaFree(s->d_pd16[1]);
-    cudaFree(s->d_hcnt);
-    cudaFree(s->d_pd64[0]);
-    cudaFree(s->d_pd64[1]);
+    cudaFree(s->d_arena);          // every per-sim buffer but the counts output
     cudaFree(s->d_counts);
     if (s->own_stream && s->stream)
         cudaStreamDestroy(s->stream);
@@ -492,6 +477,11 @@ fs_status fs_graph_create(int64_t n, const int64_t* row_ptr, const int32_t* col_
             g->t1 = g->dmax;
             g->n_thr = ni;
             g->identity = true;
+        } else if (g->t1 >= g->dmax) {
+            // every node is in the thread class and the first pass's keys (the
+            // degrees, all <= 255) are this split's keys: no second pass
+            g->n_thr = ni;
+            g->identity = fl.unsorted == 0;
         } else {
             G_CUDA(cudaMemsetAsync(d_flags, 0, sizeof(fs::IngestFlags), st));
             G_CUDA(fs::launch_degrees(d_rp, ni, g->t1, g->d_deg, d_key, d_flags, st));
@@ -642,7 +632,6 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
     const int64_t n = g->n;
     int32_t* d_idx = nullptr;
     auto bail = [&](fs_status rc) {
-        cudaFree(d_idx);
         free_sim(s);
         return rc;
     };
@@ -663,46 +652,69 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
     const size_t words = ((size_t)(n >> 5) + 1 + 3) / 4 * 4;
     // whole 16-node groups (+16) for the vector accesses of the push step
     const size_t n_pad = ((size_t)n + 15) / 16 * 16 + 16;
-    S_CUDA(dev_alloc(&s->d_X, n_pad, nullptr));
-    S_CUDA(cudaMalloc(&s->d_A, n_pad * s->age_bytes));
-    S_CUDA(dev_alloc(&s->d_bm[0], words, nullptr));
-    S_CUDA(dev_alloc(&s->d_bm[1], words, nullptr));
-    S_CUDA(dev_alloc(&s->d_m_cnt, (size_t)std::max(g->n_m, 1), nullptr));
-    S_CUDA(dev_alloc(&s->d_m_tkt, (size_t)std::max(g->n_m, 1), nullptr));
-    S_CUDA(dev_alloc(&s->d_ctl, 1, nullptr));
-    S_CUDA(dev_alloc(&s->d_deltas, (size_t)fs::kMaxGraphSteps * fs::kDeltaFields, nullptr));
-    S_CUDA(dev_alloc(&s->d_ptab, (size_t)2 * fs::kPTableN, nullptr));
-    S_CUDA(dev_alloc(&s->d_ps, (size_t)fs::kPSTableN, nullptr));
+    const size_t thr_pad = ((size_t)g->n_thr + 15) / 16 * 16 + 16;
+    const size_t nm1 = (size_t)std::max(g->n_m, 1);
+    const bool push = s->pressure == FS_PRESSURE_PUSH;
+    // every buffer of the sim is carved from one allocation (256-byte aligned
+    // pieces), zeroed by one memset
+    size_t arena = 0;
+    auto carve = [&](size_t bytes) {
+        const size_t o = arena;
+        arena = (arena + std::max<size_t>(bytes, 1) + 255) & ~(size_t)255;
+        return o;
+    };
+    const size_t oX = carve(n_pad), oA = carve(n_pad * s->age_bytes);
+    const size_t oB0 = carve(words * 4), oB1 = carve(words * 4);
+    const size_t oMc = carve(sizeof(int32_t) * nm1), oMt = carve(sizeof(uint32_t) * nm1);
+    const size_t oCtl = carve(sizeof(fs::DevCtl));
+    const size_t oDel = carve(sizeof(unsigned long long) * fs::kMaxGraphSteps * fs::kDeltaFields);
+    const size_t oPt = carve(sizeof(float2) * 2 * fs::kPTableN), oPs = carve(sizeof(float) * fs::kPSTableN);
+    const size_t oIdx = carve(sizeof(int32_t) * (size_t)std::max<int64_t>(n_index, 1));
+    size_t oC8 = 0, oP0 = 0, oP1 = 0, oHc = 0, oH0 = 0, oH1 = 0;
+    if (push) {
+        oC8 = carve(thr_pad);
+        oP0 = carve(sizeof(uint16_t) * thr_pad);
+        oP1 = carve(sizeof(uint16_t) * thr_pad);
+        oHc = carve(sizeof(uint32_t) * nm1);
+        oH0 = carve(sizeof(unsigned long long) * nm1);
+        oH1 = carve(sizeof(unsigned long long) * nm1);
+    }
+    S_CUDA(cudaMalloc(&s->d_arena, arena));
+    char* base = static_cast<char*>(s->d_arena);
+    s->d_X = reinterpret_cast<uint8_t*>(base + oX);
+    s->d_A = base + oA;
+    s->d_bm[0] = reinterpret_cast<uint32_t*>(base + oB0);
+    s->d_bm[1] = reinterpret_cast<uint32_t*>(base + oB1);
+    s->d_m_cnt = reinterpret_cast<int32_t*>(base + oMc);
+    s->d_m_tkt = reinterpret_cast<uint32_t*>(base + oMt);
+    s->d_ctl = reinterpret_cast<fs::DevCtl*>(base + oCtl);
+    s->d_deltas = reinterpret_cast<unsigned long long*>(base + oDel);
+    s->d_ptab = reinterpret_cast<float2*>(base + oPt);
+    s->d_ps = reinterpret_cast<float*>(base + oPs);
+    d_idx = reinterpret_cast<int32_t*>(base + oIdx);
+    if (push) {
+        s->d_cnt8 = reinterpret_cast<uint8_t*>(base + oC8);
+        s->d_pd16[0] = reinterpret_cast<uint16_t*>(base + oP0);
+        s->d_pd16[1] = reinterpret_cast<uint16_t*>(base + oP1);
+        s->d_hcnt = reinterpret_cast<uint32_t*>(base + oHc);
+        s->d_pd64[0] = reinterpret_cast<unsigned long long*>(base + oH0);
+        s->d_pd64[1] = reinterpret_cast<unsigned long long*>(base + oH1);
+    }
+    // all S, ages 0, bitmaps / scratch / control / deltas / counts / tallies 0
+    S_CUDA(cudaMemsetAsync(s->d_arena, 0, arena, cs));
     S_CUDA(cudaMemsetAsync(s->d_ptab, 0xff, sizeof(float2) * 2 * fs::kPTableN, cs));   // NaN ages: no entry
     S_CUDA(fs::launch_build_ptables(s->M, params->age_dtype, s->d_ptab, s->d_ps, cs));
-    S_CUDA(cudaMemsetAsync(s->d_X, 0, n_pad, cs));
-    S_CUDA(cudaMemsetAsync(s->d_A, 0, n_pad * s->age_bytes, cs));
-    S_CUDA(cudaMemsetAsync(s->d_bm[0], 0, words * 4, cs));
-    S_CUDA(cudaMemsetAsync(s->d_bm[1], 0, words * 4, cs));
-    S_CUDA(cudaMemsetAsync(s->d_m_cnt, 0, sizeof(int32_t) * std::max(g->n_m, 1), cs));
-    S_CUDA(cudaMemsetAsync(s->d_m_tkt, 0, sizeof(uint32_t) * std::max(g->n_m, 1), cs));
-    S_CUDA(cudaMemsetAsync(s->d_ctl, 0, sizeof(fs::DevCtl), cs));
-    S_CUDA(cudaMemsetAsync(s->d_deltas, 0, sizeof(unsigned long long) * fs::kMaxGraphSteps * fs::kDeltaFields, cs));
     if (n_index > 0) {
-        S_CUDA(dev_alloc(&d_idx, (size_t)n_index, nullptr));
         S_CUDA(cudaMemcpyAsync(d_idx, index_nodes, sizeof(int32_t) * n_index, cudaMemcpyHostToDevice, cs));
         S_CUDA(fs::launch_set_index(s->d_X, d_idx, n_index, g->d_inv, params->index_state, cs));
     }
     S_CUDA(fs::launch_refresh(s->d_X, (int)n, g->d_deg, s->d_bm[0], s->d_bm[1], s->d_ctl, cs));
-    if (s->pressure == FS_PRESSURE_PUSH) {
-        const size_t thr_pad = ((size_t)g->n_thr + 15) / 16 * 16 + 16;
+    if (push) {
         S_CUDA(ensure_out_csr(g, cs));
-        S_CUDA(dev_alloc(&s->d_cnt8, thr_pad, nullptr));
-        S_CUDA(dev_alloc(&s->d_pd16[0], thr_pad, nullptr));
-        S_CUDA(dev_alloc(&s->d_pd16[1], thr_pad, nullptr));
-        S_CUDA(dev_alloc(&s->d_hcnt, (size_t)std::max(g->n_m, 1), nullptr));
-        S_CUDA(dev_alloc(&s->d_pd64[0], (size_t)std::max(g->n_m, 1), nullptr));
-        S_CUDA(dev_alloc(&s->d_pd64[1], (size_t)std::max(g->n_m, 1), nullptr));
-        S_CUDA(push_reset(s));
+        S_CUDA(fs::launch_push_init(step_args(s, 0), cs, g->num_sms));   // counts and tallies are zero
     }
     S_CUDA(cudaStreamSynchronize(cs));
 #undef S_CUDA
-    cudaFree(d_idx);
     g->refs += 1;
     *out = s;
     return FS_OK;

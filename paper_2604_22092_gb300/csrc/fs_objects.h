@@ -42,6 +42,7 @@ struct fs_graph {
 
 struct fs_sim {
     fs_graph* g = nullptr;
+    void* d_arena = nullptr;       // one allocation holding every per-sim device buffer below
     fs_sim_params p{};
     fs::ModelF M{};
     int age_bytes = 4;
