@@ -168,9 +168,10 @@ const char* fs_last_error(void);
  *   weights  must be NULL (unit edge weights; other weights: FS_EUNSUPPORTED)
  *   opts     NULL for the defaults
  *   out      receives the handle; destroy with fs_graph_destroy
- * Errors: FS_EINVAL (bad sizes, non-monotone row_ptr, col_ind out of range,
- *         checked on the host for host input and on the device for device
- *         input), FS_ENOMEM, FS_ECUDA, FS_EUNSUPPORTED.
+ * Errors: FS_EINVAL (bad sizes, row_ptr[0] != 0, non-monotone row_ptr,
+ *         col_ind out of range; row_ptr[0] and row_ptr[n] are read on the
+ *         host, the rest is checked on the device after the copy, for host
+ *         and device input alike), FS_ENOMEM, FS_ECUDA, FS_EUNSUPPORTED.
  * ------------------------------------------------------------------------- */
 fs_status fs_graph_create(int64_t n, const int64_t* row_ptr, const int32_t* col_ind,
                           const float* weights, const fs_graph_opts* opts,

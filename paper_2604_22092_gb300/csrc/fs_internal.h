@@ -97,10 +97,13 @@ struct StepArgs {
     const int32_t* perm;          // internal -> original id, null = identity
     const int32_t* deg;           // degree by internal id (work accounting of fired S nodes)
     // Bernoulli probabilities memoised per sim (bit-identical to direct
-    // evaluation): ptab[law * kPTableN + n] = (age, p) for the ages of the
-    // fixed-step sequence (law 0 = latent, 1 = infectious); ps[c] = p of an S
-    // node with c infectious in-neighbours
-    const float2* ptab;
+    // evaluation): ptab[law * kPTableN + n] = (age0, p0, age1, p1), the ages
+    // of the fixed-step sequence whose index rint(age / dt) is n (at most two
+    // distinct ages share an index: the sequence is monotone and its steps
+    // are at least half an index apart; NaN age = empty slot); law 0 =
+    // latent, 1 = infectious; ps[c] = p of an S node with c infectious
+    // in-neighbours
+    const float4* ptab;
     const float* ps;
     int32_t spw;                  // SELL slices per warp
     uint32_t bm_bytes;            // bitmap bytes copied to shared memory (multiple of 16)
@@ -140,7 +143,7 @@ constexpr int kPackThreads = 128;       // threads per block of the packed step
 
 struct __align__(16) PackScen {   // one realisation of a segment
     // what the step reads per replicate, as three 16-byte words
-    const float2* ptab;     // [2][kPTableN] memoised probabilities of its laws
+    const float4* ptab;     // [2][kPTableN] memoised probabilities of its laws (two slots per index)
     const float* ps;        // [kPSTableN]
     uint32_t key0, key1, rep;   // copies of M.key0, M.key1, M.rep (Philox key and replicate index)
     float dt;               // copy of M.dt

@@ -19,7 +19,7 @@ extern std::atomic<unsigned long long> g_launch_count;
 cudaError_t launch_step(const StepArgs& a, int age_dtype, cudaStream_t s, bool pdl);
 // one step as the shared-memory-bitmap SELL grid plus, if present, the merge grid
 cudaError_t launch_step_smem(const StepArgs& a, int age_dtype, cudaStream_t s, int num_sms);
-cudaError_t launch_build_ptables(const ModelF& M, int age_dtype, float2* tab, float* ps, cudaStream_t s);
+cudaError_t launch_build_ptables(const ModelF& M, int age_dtype, float4* tab, float* ps, cudaStream_t s);
 cudaError_t launch_run_begin(DevCtl* ctl, uint32_t* out, cudaStream_t s);
 cudaError_t launch_run_epilogue(DevCtl* ctl, unsigned long long* deltas, int K, int model, cudaStream_t s);
 cudaError_t launch_refresh(const uint8_t* X, int n, const int32_t* deg, uint32_t* bm0, uint32_t* bm1, DevCtl* ctl,

@@ -53,7 +53,7 @@ struct fs_sim {
     uint32_t* d_m_tkt = nullptr;
     fs::DevCtl* d_ctl = nullptr;
     unsigned long long* d_deltas = nullptr;
-    float2* d_ptab = nullptr;
+    float4* d_ptab = nullptr;
     float* d_ps = nullptr;
     // push form of the pressure (pressure == FS_PRESSURE_PUSH)
     int pressure = FS_PRESSURE_GATHER;

@@ -52,9 +52,11 @@ __device__ __forceinline__ float pack_p(const PackScen& S, int x, float age, uin
     if (x == kE || x == kI) {
         const int n = __float2int_rn(__fmul_rn(age, S.M.inv_dt));
         if ((unsigned)n < (unsigned)kPTableN) {
-            const float2 e = __ldg(S.ptab + (x == kI ? kPTableN : 0) + n);
+            const float4 e = __ldg(S.ptab + (x == kI ? kPTableN : 0) + n);
             if (e.x == age)
                 return e.y;
+            if (e.z == age)
+                return e.w;
         }
         return pack_p_direct(S.M, x, age);
     }
@@ -396,7 +398,7 @@ __device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slic
 #pragma unroll
         for (int h = 0; h < 8; h += 4) {
             float sp[8];                    // entries h..h+3 used
-            float2 et[8];
+            float4 et[8];
 #pragma unroll
             for (int q = h; q < h + 4; ++q) {
                 const int x = (int)((xv >> (8 * q)) & 0xffu);
@@ -404,19 +406,21 @@ __device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slic
                 const uint4 h0 = __ldg(reinterpret_cast<const uint4*>(scen + b * 8 + q));
                 const float inv_dt = __uint_as_float(__ldg(reinterpret_cast<const uint32_t*>(scen + b * 8 + q) + 9));
                 const float* ps = reinterpret_cast<const float*>(((uint64_t)h0.w << 32) | h0.z);
-                const float2* pt = reinterpret_cast<const float2*>(((uint64_t)h0.y << 32) | h0.x);
+                const float4* pt = reinterpret_cast<const float4*>(((uint64_t)h0.y << 32) | h0.x);
                 const int n = __float2int_rn(__fmul_rn(ag.v[q], inv_dt));
                 sp[q] = (x == kS && c != 0u) ? __ldg(ps + c) : 0.0f;      // c < 256 = kPSTableN
                 et[q] = ((x == kE || x == kI) && (unsigned)n < (unsigned)kPTableN)
                             ? __ldg(pt + (x == kI ? kPTableN : 0) + n)
-                            : make_float2(-1.0f, 0.0f);
+                            : make_float4(-1.0f, 0.0f, -1.0f, 0.0f);
             }
 #pragma unroll
             for (int q = h; q < h + 4; ++q) {
                 const int x = (int)((xv >> (8 * q)) & 0xffu);
                 float pq = sp[q];
                 if (x == kE || x == kI)
-                    pq = (et[q].x == ag.v[q]) ? et[q].y : pack_p_direct(scen[b * 8 + q].M, x, ag.v[q]);
+                    pq = (et[q].x == ag.v[q])   ? et[q].y
+                         : (et[q].z == ag.v[q]) ? et[q].w
+                                                : pack_p_direct(scen[b * 8 + q].M, x, ag.v[q]);
                 spv[q * 32 + lane] = pq;
                 act |= (uint32_t)(pq > 0.0f) << q;
             }

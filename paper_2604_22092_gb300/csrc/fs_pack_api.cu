@@ -33,7 +33,7 @@ struct fs_ens {
     uint32_t* d_phc = nullptr;
     unsigned long long* d_phpd[2] = {nullptr, nullptr};
     fs::PackScen* d_scen = nullptr;
-    float2* d_ptab = nullptr;
+    float4* d_ptab = nullptr;
     float* d_ps = nullptr;
     unsigned long long* d_deltas = nullptr;
     uint32_t* d_counts = nullptr;
@@ -260,7 +260,7 @@ fs_status fs_ens_create(fs_graph* g, const fs_sim_params* params, int32_t n_real
     C_TRY(dev_alloc(&e->d_counts, (size_t)Rp * 4, &e->bytes));
     C_TRY(cudaMemsetAsync(e->d_A, 0, (size_t)n * Rp * e->age_bytes, cs));
     C_TRY(cudaMemsetAsync(e->d_deltas, 0, sizeof(unsigned long long) * 2 * Rp * 3, cs));
-    C_TRY(cudaMemsetAsync(e->d_ptab, 0xff, sizeof(float2) * n_real * 2 * fs::kPTableN, cs));
+    C_TRY(cudaMemsetAsync(e->d_ptab, 0xff, sizeof(float4) * n_real * 2 * fs::kPTableN, cs));
     std::vector<fs::PackScen> scen(Rp);
     for (int r = 0; r < n_real; ++r) {
         fs::PackScen sc{};
@@ -273,7 +273,7 @@ fs_status fs_ens_create(fs_graph* g, const fs_sim_params* params, int32_t n_real
         sc.dt = sc.M.dt;
         sc.beta = sc.M.beta;
         sc.inv_dt = sc.M.inv_dt;
-        C_TRY(fs::launch_build_ptables(sc.M, e->age_dtype, const_cast<float2*>(sc.ptab), const_cast<float*>(sc.ps),
+        C_TRY(fs::launch_build_ptables(sc.M, e->age_dtype, const_cast<float4*>(sc.ptab), const_cast<float*>(sc.ps),
                                        cs));
         scen[r] = sc;
     }

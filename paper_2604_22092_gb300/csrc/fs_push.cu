@@ -62,9 +62,11 @@ __device__ __forceinline__ float node_p_push(const StepArgs& a, int x, float age
     if (x == kE || x == kI) {
         const int n = __float2int_rn(__fmul_rn(age, a.M.inv_dt));
         if ((unsigned)n < (unsigned)kPTableN) {
-            const float2 e = __ldg(a.ptab + (x == kI ? kPTableN : 0) + n);
+            const float4 e = __ldg(a.ptab + (x == kI ? kPTableN : 0) + n);
             if (e.x == age)
                 return e.y;
+            if (e.z == age)
+                return e.w;
         }
         return p_direct_p(a.M, x, age);
     }
@@ -339,13 +341,13 @@ __device__ __forceinline__ void group_prepare(const StepArgs& a, uint32_t par, i
         if (isS)
             set_byte(nc, u, c);
         const int n = __float2int_rn(__fmul_rn(it.age[u], a.M.inv_dt));
-        float2 e = make_float2(-1.0f, 0.0f);                  // no entry: never equals an age
+        float4 e = make_float4(-1.0f, 0.0f, -1.0f, 0.0f);      // no entry: never equals an age
         if (isEI && (unsigned)n < (unsigned)kPTableN)
             e = __ldg(a.ptab + (x == kI ? kPTableN : 0) + n);
         float ps = 0.0f;
         if (isS && c != 0u)
             ps = __ldg(a.ps + c);
-        p[u] = isS ? ps : (isEI ? (e.x == it.age[u] ? e.y : -1.0f) : 0.0f);
+        p[u] = isS ? ps : (isEI ? (e.x == it.age[u] ? e.y : (e.z == it.age[u] ? e.w : -1.0f)) : 0.0f);
     }
     it.nc = nc;
 #pragma unroll

@@ -53,7 +53,7 @@ struct Request {
 int64_t ensemble_bytes(int64_t n, int64_t n_merge, int R, int age_bytes, int64_t steps, bool push)
 {
     const int64_t Rp = R <= 8 ? 8 : R <= 16 ? 16 : 32;
-    int64_t b = n * Rp * (1 + age_bytes) + 2 * (n + 1) * (Rp / 8) + (int64_t)R * (2 * 4096 * 8 + 256 * 4) +
+    int64_t b = n * Rp * (1 + age_bytes) + 2 * (n + 1) * (Rp / 8) + (int64_t)R * (2 * 4096 * 16 + 256 * 4) +
                 (steps + 1) * Rp * 16 + 4096;
     if (push)
         b += (n - n_merge) * Rp * 5 + std::max<int64_t>(n_merge, 1) * Rp * 20;

@@ -65,9 +65,11 @@ __device__ __forceinline__ float node_p(const StepArgs& a, int x, float age, uin
     if (x == kE || x == kI) {
         const int n = __float2int_rn(__fmul_rn(age, a.M.inv_dt));
         if (a.ptab && (unsigned)n < (unsigned)kPTableN) {
-            const float2 e = __ldg(a.ptab + (x == kI ? kPTableN : 0) + n);
+            const float4 e = __ldg(a.ptab + (x == kI ? kPTableN : 0) + n);
             if (e.x == age)
                 return e.y;
+            if (e.z == age)
+                return e.w;
         }
         return p_direct(a.M, x, age);
     }
@@ -523,17 +525,34 @@ __global__ void __launch_bounds__(kSmemThreads, 1) sell_smem_kernel(const __grid
 
 // Memoised Bernoulli probabilities of one sim: the fixed-step age sequence
 // a_0 = 0, a_{n+1} = store(a_n + dt) is generated by one thread (it is
-// sequential), then every entry is evaluated in parallel with the step's own
-// hazard code and placed at the index the step computes from the age. Ages
-// that share an index with an earlier, different age keep the earlier one
-// (the step then evaluates them directly). Unfilled entries hold NaN ages.
-__global__ void build_ptables_kernel(ModelF M, int age_dtype, float2* __restrict__ tab, float* __restrict__ ps)
+// sequential), which also assigns each distinct age its slot at the index the
+// step computes from the age (the sequence is monotone, so the ages sharing
+// an index are consecutive; with FP16/BF16 storage two can share one, and a
+// third would be evaluated directly by the step); then every entry is
+// evaluated in parallel with the step's own hazard code. Unfilled slots hold
+// NaN ages.
+__global__ void build_ptables_kernel(ModelF M, int age_dtype, float4* __restrict__ tab, float* __restrict__ ps)
 {
     __shared__ float ages[kPTableN];
+    __shared__ signed char slot[kPTableN];    // -1: a repeated age, or beyond two per index
     if (threadIdx.x == 0) {
-        float v = 0.0f;
+        float v = 0.0f, prev = -1.0f;
+        int prev_idx = -1, used = 0;
         for (int n = 0; n < kPTableN; ++n) {
             ages[n] = v;
+            const int idx = __float2int_rn(__fmul_rn(v, M.inv_dt));
+            int sl = -1;
+            if (v != prev) {
+                if (idx != prev_idx) {
+                    sl = 0;
+                    used = 1;
+                    prev_idx = idx;
+                } else if (used < 2) {
+                    sl = used++;
+                }
+            }
+            slot[n] = (signed char)sl;
+            prev = v;
             v = age_step_stored(v, M.dt, age_dtype);
         }
     }
@@ -541,10 +560,14 @@ __global__ void build_ptables_kernel(ModelF M, int age_dtype, float2* __restrict
     for (int n = threadIdx.x; n < kPTableN; n += blockDim.x) {
         const float v = ages[n];
         const int idx = __float2int_rn(__fmul_rn(v, M.inv_dt));
-        const bool first = n == 0 || __float2int_rn(__fmul_rn(ages[n - 1], M.inv_dt)) != idx;
-        if (first && idx >= 0 && idx < kPTableN) {
-            tab[idx] = make_float2(v, p_of_rate(M, hazard(M.lat, v)));
-            tab[kPTableN + idx] = make_float2(v, p_of_rate(M, hazard(M.inf, v)));
+        const int sl = slot[n];
+        if (sl >= 0 && idx >= 0 && idx < kPTableN) {
+            float* lat = reinterpret_cast<float*>(tab + idx) + 2 * sl;
+            float* inf = reinterpret_cast<float*>(tab + kPTableN + idx) + 2 * sl;
+            lat[0] = v;
+            lat[1] = p_of_rate(M, hazard(M.lat, v));
+            inf[0] = v;
+            inf[1] = p_of_rate(M, hazard(M.inf, v));
         }
     }
     for (int c = threadIdx.x; c < kPSTableN; c += blockDim.x)
@@ -746,7 +769,7 @@ cudaError_t launch_step_smem(const StepArgs& a, int age_dtype, cudaStream_t s, i
     }
 }
 
-cudaError_t launch_build_ptables(const ModelF& M, int age_dtype, float2* tab, float* ps, cudaStream_t s)
+cudaError_t launch_build_ptables(const ModelF& M, int age_dtype, float4* tab, float* ps, cudaStream_t s)
 {
     build_ptables_kernel<<<1, 256, 0, s>>>(M, age_dtype, tab, ps);
     g_launch_count += 1;
