@@ -65,8 +65,7 @@ void free_graph(fs_graph* g)
     cudaFree(g->d_m_col);
     cudaFree(g->d_m_warp_row);
     cudaFree(g->d_m_chunk_last);
-    cudaFree(g->d_out_ptr);
-    cudaFree(g->d_out_col);
+    cudaFree(g->d_out_ptr);          // the columns share its allocation
     delete g;
 }
 
@@ -244,6 +243,29 @@ bool push_available(const fs_graph* g)
     return g->n_thr == 0 || g->t1 <= fs::kMaxThreadDeg;
 }
 
+cudaMemPool_t scratch_pool()
+{
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+        return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess)
+            return nullptr;
+        uint64_t keep = UINT64_MAX;     // keep freed memory for the next use
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        pools[dev] = pool;
+    }
+    return pools[dev];
+}
+
 // transposed CSR of the graph in internal ids (once per graph)
 cudaError_t ensure_out_csr(fs_graph* g, cudaStream_t st)
 {
@@ -256,12 +278,14 @@ cudaError_t ensure_out_csr(fs_graph* g, cudaStream_t st)
     int64_t* optr = nullptr;
     int32_t* ocol = nullptr;
     unsigned long long* cur = nullptr;
-    int64_t bytes = 0;
-    cudaError_t e = dev_alloc(&optr, (size_t)n + 1, &bytes);
-    if (e == cudaSuccess)
-        e = dev_alloc(&ocol, (size_t)g->nnz, &bytes);
-    if (e == cudaSuccess)
-        e = dev_alloc(&cur, (size_t)n + 1, nullptr);
+    // row bounds and columns in one allocation (freed through d_out_ptr)
+    const size_t ptr_bytes = ((sizeof(int64_t) * ((size_t)n + 1)) + 255) & ~(size_t)255;
+    const int64_t bytes = (int64_t)(ptr_bytes + sizeof(int32_t) * std::max<int64_t>(g->nnz, 1));
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&optr), (size_t)bytes);
+    if (e == cudaSuccess) {
+        ocol = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(optr) + ptr_bytes);
+        e = scratch_alloc(&cur, (size_t)n + 1, st);
+    }
     if (e == cudaSuccess)
         e = cudaMemsetAsync(cur, 0, sizeof(unsigned long long) * (n + 1), st);
     if (e == cudaSuccess)
@@ -276,10 +300,9 @@ cudaError_t ensure_out_csr(fs_graph* g, cudaStream_t st)
                                  (int)n, cur, ocol, true, st);
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(st);
-    cudaFree(cur);
+    scratch_free(cur, st);
     if (e != cudaSuccess) {
         cudaFree(optr);
-        cudaFree(ocol);
         return e;
     }
     g->d_out_ptr = optr;
@@ -421,9 +444,9 @@ fs_status fs_graph_create(int64_t n, const int64_t* row_ptr, const int32_t* col_
             cudaFree(d_rp);
             cudaFree(d_col);
         }
-        cudaFree(d_key);
-        cudaFree(d_flags);
-        cudaFree(d_tmp);
+        scratch_free(d_key, st);
+        scratch_free(d_flags, st);
+        scratch_free(d_tmp, st);
     };
 #define G_CUDA(expr)                                                                                  \
     do {                                                                                              \
@@ -446,8 +469,8 @@ fs_status fs_graph_create(int64_t n, const int64_t* row_ptr, const int32_t* col_
                 G_CUDA(cudaMemcpyAsync(d_col, col_ind, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, st));
         }
         G_CUDA(dev_alloc(&g->d_deg, (size_t)n, &g->bytes));
-        G_CUDA(dev_alloc(&d_key, (size_t)n, nullptr));
-        G_CUDA(dev_alloc(&d_flags, 1, nullptr));
+        G_CUDA(scratch_alloc(&d_key, (size_t)n, st));
+        G_CUDA(scratch_alloc(&d_flags, 1, st));
         // pass 1: degrees, d_max, validity
         G_CUDA(cudaMemsetAsync(d_flags, 0, sizeof(fs::IngestFlags), st));
         G_CUDA(fs::launch_degrees(d_rp, ni, fs::kMaxThreadDeg, g->d_deg, d_key, d_flags, st));
@@ -517,7 +540,7 @@ fs_status fs_graph_create(int64_t n, const int64_t* row_ptr, const int32_t* col_
             g->smem_min_s = (uint32_t)std::min<double>((double)n, 4.0 * (double)n / std::max(d_avg, 1.0));
         }
         G_CUDA(dev_alloc(&g->d_sell_off, (size_t)g->n_slices + 1, &g->bytes));
-        G_CUDA(dev_alloc(&d_tmp, (size_t)std::max(g->n_slices, g->n_m) + 1, nullptr));
+        G_CUDA(scratch_alloc(&d_tmp, (size_t)std::max(g->n_slices, g->n_m) + 1, st));
         G_CUDA(fs::launch_sell_widths(g->d_deg, g->n_thr, g->n_slices, d_tmp, st));
         G_CUDA(fs::exclusive_scan_i64(d_tmp, g->d_sell_off, g->n_slices, st));
         G_CUDA(cudaMemcpyAsync(&g->sell_entries, g->d_sell_off + g->n_slices, sizeof(int64_t),

@@ -35,7 +35,7 @@ struct fs_graph {
     // transposed CSR (internal ids) for the push form of the pressure, built
     // on the first push-form sim of the graph
     int64_t* d_out_ptr = nullptr;  // [n + 1]
-    int32_t* d_out_col = nullptr;  // [nnz]
+    int32_t* d_out_col = nullptr;  // [nnz], inside the allocation of d_out_ptr
     int refs = 0;
     bool failed = false;
 };
@@ -84,6 +84,22 @@ inline cudaError_t dev_alloc(T** p, size_t count, int64_t* bytes)
     if (e == cudaSuccess && bytes)
         *bytes += (int64_t)b;
     return e;
+}
+// stream-ordered scratch from a library-owned pool per device that keeps its
+// memory (no device-wide synchronisation on free, no re-mapping per use)
+cudaMemPool_t scratch_pool();
+template <typename T>
+inline cudaError_t scratch_alloc(T** p, size_t count, cudaStream_t s)
+{
+    cudaMemPool_t pool = scratch_pool();
+    if (!pool)
+        return cudaErrorMemoryAllocation;
+    return cudaMallocFromPoolAsync(reinterpret_cast<void**>(p), sizeof(T) * (count > 0 ? count : 1), pool, s);
+}
+inline void scratch_free(void* p, cudaStream_t s)
+{
+    if (p)
+        cudaFreeAsync(p, s);
 }
 fs_status check_params(const fs_sim_params* p);
 fs::ModelF to_model(const fs_sim_params& p);

@@ -534,25 +534,10 @@ __global__ void __launch_bounds__(kSmemThreads, 1) sell_smem_kernel(const __grid
 __global__ void build_ptables_kernel(ModelF M, int age_dtype, float4* __restrict__ tab, float* __restrict__ ps)
 {
     __shared__ float ages[kPTableN];
-    __shared__ signed char slot[kPTableN];    // -1: a repeated age, or beyond two per index
     if (threadIdx.x == 0) {
-        float v = 0.0f, prev = -1.0f;
-        int prev_idx = -1, used = 0;
+        float v = 0.0f;
         for (int n = 0; n < kPTableN; ++n) {
             ages[n] = v;
-            const int idx = __float2int_rn(__fmul_rn(v, M.inv_dt));
-            int sl = -1;
-            if (v != prev) {
-                if (idx != prev_idx) {
-                    sl = 0;
-                    used = 1;
-                    prev_idx = idx;
-                } else if (used < 2) {
-                    sl = used++;
-                }
-            }
-            slot[n] = (signed char)sl;
-            prev = v;
             v = age_step_stored(v, M.dt, age_dtype);
         }
     }
@@ -560,7 +545,17 @@ __global__ void build_ptables_kernel(ModelF M, int age_dtype, float4* __restrict
     for (int n = threadIdx.x; n < kPTableN; n += blockDim.x) {
         const float v = ages[n];
         const int idx = __float2int_rn(__fmul_rn(v, M.inv_dt));
-        const int sl = slot[n];
+        // slot = distinct earlier ages with the same index (a repeated age,
+        // one that freezes in storage, already has its slot)
+        int sl = -1;
+        if (n == 0 || ages[n - 1] != v) {
+            sl = 0;
+            for (int m = n - 1; m >= 0 && __float2int_rn(__fmul_rn(ages[m], M.inv_dt)) == idx && sl < 2; --m)
+                if (ages[m] != ages[m + 1])
+                    ++sl;
+            if (sl >= 2)
+                sl = -1;
+        }
         if (sl >= 0 && idx >= 0 && idx < kPTableN) {
             float* lat = reinterpret_cast<float*>(tab + idx) + 2 * sl;
             float* inf = reinterpret_cast<float*>(tab + kPTableN + idx) + 2 * sl;
