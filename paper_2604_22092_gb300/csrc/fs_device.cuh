@@ -170,6 +170,15 @@ __device__ __forceinline__ float age_step_stored(float age, float dt, int age_dt
     return v;
 }
 
+// Memoised probability of an E/I node of age `age` from its law's two-slot
+// table row (age0, p0, age1, p1): slot 0 is read as 8 bytes and slot 1 only
+// when slot 0 holds another age; returns -1 when neither holds `age`.
+__device__ __forceinline__ float ptab_slot1(const float4* row, float age)
+{
+    const float2 e1 = __ldg(reinterpret_cast<const float2*>(row) + 1);
+    return e1.x == age ? e1.y : -1.0f;
+}
+
 struct TailResult {
     int x;        // new compartment
     float age;    // new age (FP32 value, rounded on store by the caller)

@@ -52,11 +52,13 @@ __device__ __forceinline__ float pack_p(const PackScen& S, int x, float age, uin
     if (x == kE || x == kI) {
         const int n = __float2int_rn(__fmul_rn(age, S.M.inv_dt));
         if ((unsigned)n < (unsigned)kPTableN) {
-            const float4 e = __ldg(S.ptab + (x == kI ? kPTableN : 0) + n);
+            const float4* row = S.ptab + (x == kI ? kPTableN : 0) + n;
+            const float2 e = __ldg(reinterpret_cast<const float2*>(row));
             if (e.x == age)
                 return e.y;
-            if (e.z == age)
-                return e.w;
+            const float p1 = ptab_slot1(row, age);
+            if (p1 >= 0.0f)
+                return p1;
         }
         return pack_p_direct(S.M, x, age);
     }
@@ -346,6 +348,17 @@ __device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slic
             }
         }
     }
+    if constexpr (PUSH) {
+        // nothing can happen in a slice with no E or I replicate whose S
+        // replicates all have count 0 (their tallies are folded above): no
+        // draw, no transition, no write, no push
+        bool busy = false;
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+            busy |= cnt[b] != 0ull || has_byte(xs[b], (uint32_t)kE) || has_byte(xs[b], (uint32_t)kI);
+        if (!__any_sync(kFullP, busy))
+            return;
+    }
     if (!PUSH && anyS) {
         const int w = (int)((off_end - off) >> 5);
         const int32_t* __restrict__ p = g.sell_col + off + lane;
@@ -398,7 +411,7 @@ __device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slic
 #pragma unroll
         for (int h = 0; h < 8; h += 4) {
             float sp[8];                    // entries h..h+3 used
-            float4 et[8];
+            float2 et[8];
 #pragma unroll
             for (int q = h; q < h + 4; ++q) {
                 const int x = (int)((xv >> (8 * q)) & 0xffu);
@@ -410,17 +423,15 @@ __device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slic
                 const int n = __float2int_rn(__fmul_rn(ag.v[q], inv_dt));
                 sp[q] = (x == kS && c != 0u) ? __ldg(ps + c) : 0.0f;      // c < 256 = kPSTableN
                 et[q] = ((x == kE || x == kI) && (unsigned)n < (unsigned)kPTableN)
-                            ? __ldg(pt + (x == kI ? kPTableN : 0) + n)
-                            : make_float4(-1.0f, 0.0f, -1.0f, 0.0f);
+                            ? __ldg(reinterpret_cast<const float2*>(pt + (x == kI ? kPTableN : 0) + n))
+                            : make_float2(-1.0f, 0.0f);
             }
 #pragma unroll
             for (int q = h; q < h + 4; ++q) {
                 const int x = (int)((xv >> (8 * q)) & 0xffu);
                 float pq = sp[q];
                 if (x == kE || x == kI)
-                    pq = (et[q].x == ag.v[q])   ? et[q].y
-                         : (et[q].z == ag.v[q]) ? et[q].w
-                                                : pack_p_direct(scen[b * 8 + q].M, x, ag.v[q]);
+                    pq = (et[q].x == ag.v[q]) ? et[q].y : pack_p(scen[b * 8 + q], x, ag.v[q], 0u);
                 spv[q * 32 + lane] = pq;
                 act |= (uint32_t)(pq > 0.0f) << q;
             }

@@ -48,6 +48,19 @@ __device__ __noinline__ float p_direct_p(const ModelF& M, int x, float age)
     return p_of_rate(M, hazard(x == kE ? M.lat : M.inf, age));
 }
 
+// an E/I probability whose table slot 0 holds another age: slot 1, else
+// direct evaluation (rare; out of line)
+__device__ __noinline__ float p_table_miss(const StepArgs& a, int x, float age)
+{
+    const int n = __float2int_rn(__fmul_rn(age, a.M.inv_dt));
+    if ((unsigned)n < (unsigned)kPTableN) {
+        const float p1 = ptab_slot1(a.ptab + (x == kI ? kPTableN : 0) + n, age);
+        if (p1 >= 0.0f)
+            return p1;
+    }
+    return p_of_rate(a.M, hazard(x == kE ? a.M.lat : a.M.inf, age));
+}
+
 // Bernoulli probability of one node this step, from the per-sim tables built
 // at init by the same FP32 code (identical bits to direct evaluation)
 __device__ __forceinline__ float node_p_push(const StepArgs& a, int x, float age, uint32_t c)
@@ -62,11 +75,13 @@ __device__ __forceinline__ float node_p_push(const StepArgs& a, int x, float age
     if (x == kE || x == kI) {
         const int n = __float2int_rn(__fmul_rn(age, a.M.inv_dt));
         if ((unsigned)n < (unsigned)kPTableN) {
-            const float4 e = __ldg(a.ptab + (x == kI ? kPTableN : 0) + n);
+            const float4* row = a.ptab + (x == kI ? kPTableN : 0) + n;
+            const float2 e = __ldg(reinterpret_cast<const float2*>(row));
             if (e.x == age)
                 return e.y;
-            if (e.z == age)
-                return e.w;
+            const float p1 = ptab_slot1(row, age);
+            if (p1 >= 0.0f)
+                return p1;
         }
         return p_direct_p(a.M, x, age);
     }
@@ -341,19 +356,20 @@ __device__ __forceinline__ void group_prepare(const StepArgs& a, uint32_t par, i
         if (isS)
             set_byte(nc, u, c);
         const int n = __float2int_rn(__fmul_rn(it.age[u], a.M.inv_dt));
-        float4 e = make_float4(-1.0f, 0.0f, -1.0f, 0.0f);      // no entry: never equals an age
+        float2 e = make_float2(-1.0f, 0.0f);                  // no entry: never equals an age
         if (isEI && (unsigned)n < (unsigned)kPTableN)
-            e = __ldg(a.ptab + (x == kI ? kPTableN : 0) + n);
+            e = __ldg(reinterpret_cast<const float2*>(a.ptab + (x == kI ? kPTableN : 0) + n));
         float ps = 0.0f;
         if (isS && c != 0u)
             ps = __ldg(a.ps + c);
-        p[u] = isS ? ps : (isEI ? (e.x == it.age[u] ? e.y : (e.z == it.age[u] ? e.w : -1.0f)) : 0.0f);
+        // -1: slot 0 holds another age (slot 1 or direct evaluation below)
+        p[u] = isS ? ps : (isEI ? (e.x == it.age[u] ? e.y : -1.0f) : 0.0f);
     }
     it.nc = nc;
 #pragma unroll
     for (int u = 0; u < kPushG; ++u) {
-        if (p[u] < 0.0f)                                      // age off the tabulated sequence
-            p[u] = p_direct_p(a.M, (int)byte_of(xs, u), it.age[u]);
+        if (p[u] < 0.0f)                                      // slot 1, else off the tabulated sequence
+            p[u] = p_table_miss(a, (int)byte_of(xs, u), it.age[u]);
         if (p[u] > 0.0f) {
             it.need |= 1u << u;
             pslot[u] = p[u];

@@ -65,11 +65,13 @@ __device__ __forceinline__ float node_p(const StepArgs& a, int x, float age, uin
     if (x == kE || x == kI) {
         const int n = __float2int_rn(__fmul_rn(age, a.M.inv_dt));
         if (a.ptab && (unsigned)n < (unsigned)kPTableN) {
-            const float4 e = __ldg(a.ptab + (x == kI ? kPTableN : 0) + n);
+            const float4* row = a.ptab + (x == kI ? kPTableN : 0) + n;
+            const float2 e = __ldg(reinterpret_cast<const float2*>(row));
             if (e.x == age)
                 return e.y;
-            if (e.z == age)
-                return e.w;
+            const float p1 = ptab_slot1(row, age);
+            if (p1 >= 0.0f)
+                return p1;
         }
         return p_direct(a.M, x, age);
     }
