@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--ens-graphs", type=int, default=64, help="graphs of the packed-ensemble run")
     ap.add_argument("--ens-steps", type=int, default=500, help="steps of the packed-ensemble run")
     ap.add_argument("--no-other-form", action="store_true", help="skip timing the other pressure form")
+    ap.add_argument("--large-n", type=str, default="",
+                    help="comma-separated N of --workload large (default: 1e7 and 1e8 FP32, 1e8 BF16)")
     ap.add_argument("--pressure", choices=["auto", "gather", "push"], default="auto",
                     help="pressure form of single-realisation runs (auto = push where available)")
     return ap.parse_args()
@@ -810,7 +812,10 @@ def run_extra(args):
     elif args.workload == "precision":
         res = precision_bench(fs, torch, n=args.n, steps=args.sim_steps, reps=1000)
     elif args.workload == "large":
-        for n, a in ((10_000_000, fs.FS_AGE_F32), (100_000_000, fs.FS_AGE_F32), (100_000_000, fs.FS_AGE_BF16)):
+        sizes = ((10_000_000, fs.FS_AGE_F32), (100_000_000, fs.FS_AGE_F32), (100_000_000, fs.FS_AGE_BF16))
+        if args.large_n:
+            sizes = tuple((int(float(v)), fs.FS_AGE_F32) for v in args.large_n.split(","))
+        for n, a in sizes:
             res = large_bench(fs, torch, n, a, args.sim_steps, args.graph_steps, reps=1,
                               pressure=PRESSURE[args.pressure])
             print(json.dumps({"metric": METRIC, "impl": "flashstep", "data": "synthetic", **res}), flush=True)

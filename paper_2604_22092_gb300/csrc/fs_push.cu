@@ -657,7 +657,7 @@ __device__ __forceinline__ void warp_push(const StepArgs& a, uint32_t par, uint3
     __syncwarp();     // the list is reused by the warp's next item
 }
 
-constexpr int kScanRounds = 4;      // grid-stride rounds whose loads a warp issues together
+constexpr int kScanRounds = 3;      // grid-stride rounds whose loads a warp issues together
 
 // ---------------------------------------------------------------------------
 // One whole step: items are groups of kPushG thread-class nodes, then single
