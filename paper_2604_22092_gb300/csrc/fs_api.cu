@@ -243,29 +243,6 @@ bool push_available(const fs_graph* g)
     return g->n_thr == 0 || g->t1 <= fs::kMaxThreadDeg;
 }
 
-cudaMemPool_t scratch_pool()
-{
-    static std::mutex mu;
-    static cudaMemPool_t pools[64] = {};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
-        return nullptr;
-    std::lock_guard<std::mutex> lock(mu);
-    if (!pools[dev]) {
-        cudaMemPoolProps props{};
-        props.allocType = cudaMemAllocationTypePinned;
-        props.location.type = cudaMemLocationTypeDevice;
-        props.location.id = dev;
-        cudaMemPool_t pool = nullptr;
-        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess)
-            return nullptr;
-        uint64_t keep = UINT64_MAX;     // keep freed memory for the next use
-        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
-        pools[dev] = pool;
-    }
-    return pools[dev];
-}
-
 // transposed CSR of the graph in internal ids (once per graph)
 cudaError_t ensure_out_csr(fs_graph* g, cudaStream_t st)
 {

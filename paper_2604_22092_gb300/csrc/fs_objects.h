@@ -85,21 +85,15 @@ inline cudaError_t dev_alloc(T** p, size_t count, int64_t* bytes)
         *bytes += (int64_t)b;
     return e;
 }
-// stream-ordered scratch from a library-owned pool per device that keeps its
-// memory (no device-wide synchronisation on free, no re-mapping per use)
-cudaMemPool_t scratch_pool();
+// scratch of the ingest (freed before fs_graph_create / fs_sim_init return)
 template <typename T>
-inline cudaError_t scratch_alloc(T** p, size_t count, cudaStream_t s)
+inline cudaError_t scratch_alloc(T** p, size_t count, cudaStream_t)
 {
-    cudaMemPool_t pool = scratch_pool();
-    if (!pool)
-        return cudaErrorMemoryAllocation;
-    return cudaMallocFromPoolAsync(reinterpret_cast<void**>(p), sizeof(T) * (count > 0 ? count : 1), pool, s);
+    return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (count > 0 ? count : 1));
 }
-inline void scratch_free(void* p, cudaStream_t s)
+inline void scratch_free(void* p, cudaStream_t)
 {
-    if (p)
-        cudaFreeAsync(p, s);
+    cudaFree(p);
 }
 fs_status check_params(const fs_sim_params* p);
 fs::ModelF to_model(const fs_sim_params& p);
