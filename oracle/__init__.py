@@ -113,6 +113,12 @@ def lib():
             L.fso_run.argtypes = [ctypes.c_int64, i64p, i32p, P(Params), ctypes.c_int64,
                                   ctypes.c_int64, u8p, f32p, u32p]
             L.fso_run.restype = ctypes.c_int
+            L.fso_adaptive_dt.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+            L.fso_adaptive_dt.restype = ctypes.c_float
+            L.fso_run_adaptive.argtypes = [ctypes.c_int64, i64p, i32p, P(Params), ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_int64, ctypes.c_int64, u8p, f32p, u32p, f32p,
+                                           P(ctypes.c_double)]
+            L.fso_run_adaptive.restype = ctypes.c_int
             L.fso_exact_run.argtypes = [ctypes.c_int64, i64p, i32p, P(Params), i32p, ctypes.c_int64,
                                         ctypes.c_int32, ctypes.c_uint64, ctypes.c_int64,
                                         ctypes.c_double, u32p]
@@ -214,6 +220,31 @@ def run(row_ptr, col_ind, prm: Params, k0: int, steps: int, X, A):
     if rc:
         raise ValueError("oracle run failed")
     return cnt, X, A
+
+
+def adaptive_dt(dt_max: float, eps: float, delta: float, lambda_prev: float) -> float:
+    """Section 5.2: min(dt_max, eps / (lambda_prev + delta)) as the float ages advance by."""
+    return lib().fso_adaptive_dt(dt_max, eps, delta, lambda_prev)
+
+
+def run_adaptive(row_ptr, col_ind, prm: Params, eps: float, delta: float, k0: int, steps: int, X, A,
+                 lambda_prev: float = 0.0):
+    """Adaptive steps (prm.dt = dt_max). Returns (counts[(steps+1), 4], X, A,
+    dts[steps], lambda of the last step's largest rate)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col_ind, dtype=np.int32)
+    X = np.array(X, dtype=np.uint8, copy=True)
+    A = np.array(A, dtype=np.float32, copy=True)
+    cnt = np.zeros((steps + 1, 4), dtype=np.uint32)
+    dts = np.zeros(steps, dtype=np.float32)
+    last = ctypes.c_double(0.0)
+    rc = lib().fso_run_adaptive(X.size, _ptr(rp, ctypes.c_int64), _ptr(ci, ctypes.c_int32), ctypes.byref(prm),
+                                eps, delta, lambda_prev, k0, steps, _ptr(X, ctypes.c_uint8),
+                                _ptr(A, ctypes.c_float), _ptr(cnt, ctypes.c_uint32), _ptr(dts, ctypes.c_float),
+                                ctypes.byref(last))
+    if rc:
+        raise ValueError("oracle adaptive run failed")
+    return cnt, X, A, dts, last.value
 
 
 def exact_run(row_ptr, col_ind, prm: Params, index_nodes, index_state: int, rng_seed: int,

@@ -306,6 +306,64 @@ int fso_step(int64_t n, const int64_t* row_ptr, const int32_t* col_ind,
     return 0;
 }
 
+/* Section 5.2: dt = min(dt_max, eps / (max_i lambda_i + delta)), in double,
+ * from the rates of the previous step; the ages advance by its float value. */
+float fso_adaptive_dt(double dt_max, double eps, double delta, double lambda_prev)
+{
+    double dt = eps / (lambda_prev + delta);
+    if (dt > dt_max)
+        dt = dt_max;
+    return (float)dt;
+}
+
+int fso_run_adaptive(int64_t n, const int64_t* row_ptr, const int32_t* col_ind,
+                     const fso_params* prm, double eps, double delta, double lambda_prev,
+                     int64_t k0, int64_t steps, uint8_t* X, float* A, uint32_t* counts,
+                     float* dts, double* lambda_last)
+{
+    const size_t m = (size_t)(n > 0 ? n : 1);
+    uint8_t* X2 = (uint8_t*)malloc(m);
+    float* A2 = (float*)malloc(sizeof(float) * m);
+    double* lam = (double*)malloc(sizeof(double) * m);
+    if (!X2 || !A2 || !lam) {
+        free(X2); free(A2); free(lam);
+        return -1;
+    }
+    uint8_t* xc = X; float* ac = A;
+    uint8_t* xn = X2; float* an = A2;
+    fso_params p = *prm;
+    int rc = 0;
+    if (counts)
+        fso_counts(n, xc, counts);
+    for (int64_t s = 0; s < steps; ++s) {
+        const float dt = fso_adaptive_dt(prm->dt, eps, delta, lambda_prev);
+        p.dt = (double)dt;
+        rc = fso_step(n, row_ptr, col_ind, &p, k0 + s, xc, ac, xn, an, NULL, lam);
+        if (rc)
+            break;
+        if (dts)
+            dts[s] = dt;
+        /* the largest rate of this step sets the next step's size */
+        double mx = 0.0;
+        for (int64_t i = 0; i < n; ++i)
+            if (lam[i] > mx)
+                mx = lam[i];
+        lambda_prev = mx;
+        if (counts)
+            fso_counts(n, xn, counts + 4 * (s + 1));
+        uint8_t* tx = xc; xc = xn; xn = tx;
+        float* ta = ac; ac = an; an = ta;
+    }
+    if (lambda_last)
+        *lambda_last = lambda_prev;
+    if (xc != X) {
+        memcpy(X, xc, (size_t)n);
+        memcpy(A, ac, sizeof(float) * (size_t)n);
+    }
+    free(X2); free(A2); free(lam);
+    return rc;
+}
+
 int fso_run(int64_t n, const int64_t* row_ptr, const int32_t* col_ind,
             const fso_params* prm, int64_t k0, int64_t steps,
             uint8_t* X, float* A, uint32_t* counts)

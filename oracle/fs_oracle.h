@@ -93,6 +93,22 @@ int fso_run(int64_t n, const int64_t* row_ptr, const int32_t* col_ind,
             const fso_params* prm, int64_t k0, int64_t steps,
             uint8_t* X, float* A, uint32_t* counts);
 
+/* ---- adaptive step (Section 5.2) ----------------------------------------- */
+/* The step size of step k from the largest rate of step k-1:
+ *   dt_k = min(dt_max, eps / (lambda*_{k-1} + delta)),
+ * returned as the float value the ages advance by (lambda* = 0 before the
+ * first step gives dt_max). */
+float fso_adaptive_dt(double dt_max, double eps, double delta, double lambda_prev);
+
+/* steps adaptive steps from k0 (prm->dt = dt_max), in place on (X, A), the
+ * rates of the step before k0 summarised by lambda_prev (0 at a start):
+ * counts[(steps+1)*4] as fso_run, dts[steps] the step sizes used and
+ * *lambda_last the largest rate of the last step (any output may be NULL). */
+int fso_run_adaptive(int64_t n, const int64_t* row_ptr, const int32_t* col_ind,
+                     const fso_params* prm, double eps, double delta, double lambda_prev,
+                     int64_t k0, int64_t steps, uint8_t* X, float* A, uint32_t* counts,
+                     float* dts, double* lambda_last);
+
 /* ---- exact continuous-time simulator for tiny graphs -------------------- */
 /* Event-driven simulation of the same compartmental process without time
  * discretisation: S -> E (SIR: S -> I) at rate beta * (#infectious
