@@ -105,12 +105,24 @@ typedef struct {
     fs_law latent;       /* E -> I law (SEIR only; ignored for SIR)                */
     fs_law infectious;   /* I -> R law                                             */
     double beta;         /* hazard per infectious in-neighbour (1/day) > 0         */
-    double dt;           /* fixed step (days) > 0                                  */
+    double dt;           /* fixed step (days) > 0; with eps > 0, the cap dt_max    */
     uint64_t seed;       /* Philox key                                             */
     uint32_t replicate;  /* realisation index in the key's stream                  */
     int32_t index_state; /* compartment of the index cases: FS_E (SEIR) or FS_I    */
     int32_t flags;       /* FS_PRESSURE_AUTO / _GATHER / _PUSH; other values invalid */
     int32_t reserved_;   /* must be 0                                              */
+    /* Adaptive step (Section 5.2): with eps > 0 step k advances by
+     *   dt_k = min(dt, eps / (lambda*_{k-1} + delta))
+     * where lambda*_{k-1} is the largest rate of any node in step k-1 (S:
+     * beta x infectious in-neighbours, E/I: the hazard at the begin-of-step
+     * age) and the first step after init or set_state uses dt. Computed in
+     * FP32 on the device; ages advance by that value; hazards are evaluated
+     * directly (no memoised tables, since ages leave the fixed-step
+     * sequence). Single realisations in the push form only (GATHER, or a
+     * graph without the push form: FS_EUNSUPPORTED); packed ensembles,
+     * batches and the server need eps = 0. */
+    double eps;          /* 0: fixed step; > 0: the tolerance (the paper uses 0.01-0.05) */
+    double delta;        /* added to lambda*; 0 = 1e-12                            */
 } fs_sim_params;
 
 /* Graph construction options (all fields may be 0 for the defaults). */
@@ -242,6 +254,11 @@ fs_status fs_sim_get_state(fs_sim* s, uint8_t* state, void* age, int64_t* step);
  * ages must be storage values of the sim's age dtype; S and R ages must be
  * 0. Synchronous. */
 fs_status fs_sim_set_state(fs_sim* s, const uint8_t* state, const void* age, int64_t step);
+
+/* Simulated time: *elapsed (may be NULL) = the sum of the step sizes of the
+ * steps run since init or set_state; *next_dt (may be NULL) = the size of the
+ * next step (dt for a fixed step). Synchronous. */
+fs_status fs_sim_time(const fs_sim* s, double* elapsed, float* next_dt);
 
 /* The pressure form the sim runs (FS_PRESSURE_GATHER or FS_PRESSURE_PUSH). */
 fs_status fs_sim_pressure_get(const fs_sim* s, int32_t* pressure);

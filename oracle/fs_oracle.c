@@ -7,7 +7,9 @@
  *
  * Readings of the paper taken here (each is listed with its reason in the
  * design notes of the repository):
- *   - fixed step dt (the adaptive rule of Section 5.2 is not used);
+ *   - a fixed step dt in fso_step / fso_run; fso_run_adaptive takes the
+ *     adaptive rule of Section 5.2 with lambda* the largest per-node rate of
+ *     the previous step and dt_max at the first step;
  *   - the hazard is evaluated at the begin-of-step age (Algorithm 3);
  *   - ages of S and R nodes are held at 0; E/I ages advance by one float add
  *     of dt followed by round-to-nearest-even to the storage type (Section

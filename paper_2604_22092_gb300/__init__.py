@@ -25,7 +25,8 @@ __all__ = [
     "fs_version", "fs_last_error", "fs_graph_create", "fs_graph_info_get", "fs_graph_destroy",
     "fs_sim_init", "fs_sim_step", "fs_sim_run", "fs_sim_run_async", "fs_sim_sync", "fs_sim_run_timed",
     "fs_kernel_launches", "fs_tune_stats", "fs_tune_reset",
-    "fs_sim_get_state", "fs_sim_set_state", "fs_sim_work", "fs_sim_pressure_get", "fs_sim_destroy",
+    "fs_sim_get_state", "fs_sim_set_state", "fs_sim_work", "fs_sim_pressure_get", "fs_sim_time",
+    "fs_sim_destroy",
     "fs_eval_hazard",
     "fs_eval_uniforms", "fs_step_noalloc", "fs_ens_create", "fs_ens_run", "fs_ens_get_state",
     "fs_ens_destroy", "fs_batch_create", "fs_batch_add", "fs_batch_run", "fs_batch_status", "fs_batch_destroy",
@@ -84,13 +85,15 @@ def lognormal_from_mean_median(mean: float, median: float) -> _abi.fs_law:
 
 def sim_params(model: int, infectious: _abi.fs_law, beta: float, dt: float, seed: int,
                latent: _abi.fs_law | None = None, replicate: int = 0, index_state: int | None = None,
-               age_dtype: int = FS_AGE_F32, pressure: int = FS_PRESSURE_AUTO) -> _abi.fs_sim_params:
-    """pressure: FS_PRESSURE_AUTO / FS_PRESSURE_GATHER / FS_PRESSURE_PUSH (the flags field)."""
+               age_dtype: int = FS_AGE_F32, pressure: int = FS_PRESSURE_AUTO, eps: float = 0.0,
+               delta: float = 0.0) -> _abi.fs_sim_params:
+    """pressure: FS_PRESSURE_AUTO / FS_PRESSURE_GATHER / FS_PRESSURE_PUSH (the flags field);
+    eps > 0: adaptive step with dt as its cap (delta 0 = 1e-12)."""
     if index_state is None:
         index_state = FS_E if model == FS_SEIR else FS_I
     return _abi.fs_sim_params(int(model), int(age_dtype), latent if latent is not None else law("none"),
                               infectious, float(beta), float(dt), int(seed), int(replicate),
-                              int(index_state), int(pressure), 0)
+                              int(index_state), int(pressure), 0, float(eps), float(delta))
 
 
 def graph_opts(dispatch: int = FS_DISPATCH_AUTO, thread_max_deg: int = 0,
@@ -211,6 +214,13 @@ def fs_sim_work(s: int) -> dict:
     ds, sn, k = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int64()
     check(load().fs_sim_work(s, ctypes.byref(ds), ctypes.byref(sn), ctypes.byref(k)), "fs_sim_work")
     return {"s_degree_sum": ds.value, "s_node_sum": sn.value, "steps": k.value}
+
+
+def fs_sim_time(s: int) -> tuple[float, float]:
+    """(elapsed simulated time, size of the next step)."""
+    t, d = ctypes.c_double(), ctypes.c_float()
+    check(load().fs_sim_time(s, ctypes.byref(t), ctypes.byref(d)), "fs_sim_time")
+    return t.value, d.value
 
 
 def fs_sim_pressure_get(s: int) -> int:

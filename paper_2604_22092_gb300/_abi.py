@@ -33,7 +33,7 @@ class fs_sim_params(ctypes.Structure):
                 ("beta", ctypes.c_double), ("dt", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("replicate", ctypes.c_uint32),
                 ("index_state", ctypes.c_int32), ("flags", ctypes.c_int32),
-                ("reserved_", ctypes.c_int32)]
+                ("reserved_", ctypes.c_int32), ("eps", ctypes.c_double), ("delta", ctypes.c_double)]
 
 
 class fs_graph_opts(ctypes.Structure):
@@ -83,6 +83,7 @@ PROTOTYPES = {
     "fs_sim_set_state": (ctypes.c_int, [VP, VP, VP, ctypes.c_int64]),
     "fs_sim_work": (ctypes.c_int, [VP, P(ctypes.c_uint64), P(ctypes.c_uint64), P(ctypes.c_int64)]),
     "fs_sim_pressure_get": (ctypes.c_int, [VP, P(ctypes.c_int32)]),
+    "fs_sim_time": (ctypes.c_int, [VP, P(ctypes.c_double), P(ctypes.c_float)]),
     "fs_sim_destroy": (ctypes.c_int, [VP]),
     "fs_eval_hazard": (ctypes.c_int, [P(fs_law), VP, VP, ctypes.c_int64, VP]),
     "fs_eval_uniforms": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64, VP, VP,

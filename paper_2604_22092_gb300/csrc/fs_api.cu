@@ -160,6 +160,8 @@ fs_status check_params(const fs_sim_params* p)
         return fail(FS_EINVAL, "flags must be FS_PRESSURE_AUTO, FS_PRESSURE_GATHER or FS_PRESSURE_PUSH");
     if (p->reserved_ != 0)
         return fail(FS_EINVAL, "reserved field must be 0");
+    if (!finite(p->eps) || p->eps < 0 || !finite(p->delta) || p->delta < 0)
+        return fail(FS_EINVAL, "eps and delta must be finite and >= 0");
     fs_status st = check_law(p->infectious, "infectious", false);
     if (st != FS_OK)
         return st;
@@ -234,6 +236,9 @@ fs::StepArgs step_args(const fs_sim* s, int j)
     a.pd64[1] = s->d_pd64[1];
     a.out_ptr = g->d_out_ptr;
     a.out_col = g->d_out_col;
+    a.eps = (float)s->p.eps;
+    a.delta = (float)(s->p.delta > 0 ? s->p.delta : 1e-12);
+    a.dtrec = s->d_dtrec;
     return a;
 }
 
@@ -619,6 +624,8 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
     if (params->flags == FS_PRESSURE_PUSH && !push_available(g))
         return fail(FS_EUNSUPPORTED, "FS_PRESSURE_PUSH needs in-degrees <= %d in the thread class (thread_max_deg %d)",
                     fs::kMaxThreadDeg, g->t1);
+    if (params->eps > 0 && (params->flags == FS_PRESSURE_GATHER || !push_available(g)))
+        return fail(FS_EUNSUPPORTED, "the adaptive step (eps > 0) runs in the push form of the pressure only");
     fs_sim* s = new fs_sim();
     s->g = g;
     s->p = *params;
@@ -667,6 +674,7 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
     const size_t oDel = carve(sizeof(unsigned long long) * fs::kMaxGraphSteps * fs::kDeltaFields);
     const size_t oPt = carve(sizeof(float4) * 2 * fs::kPTableN), oPs = carve(sizeof(float) * fs::kPSTableN);
     const size_t oIdx = carve(sizeof(int32_t) * (size_t)std::max<int64_t>(n_index, 1));
+    const size_t oDt = carve(sizeof(float) * fs::kMaxGraphSteps);
     size_t oC8 = 0, oP0 = 0, oP1 = 0, oHc = 0, oH0 = 0, oH1 = 0;
     if (push) {
         oC8 = carve(thr_pad);
@@ -689,6 +697,8 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
     s->d_ptab = reinterpret_cast<float4*>(base + oPt);
     s->d_ps = reinterpret_cast<float*>(base + oPs);
     d_idx = reinterpret_cast<int32_t*>(base + oIdx);
+    if (params->eps > 0)
+        s->d_dtrec = reinterpret_cast<float*>(base + oDt);
     if (push) {
         s->d_cnt8 = reinterpret_cast<uint8_t*>(base + oC8);
         s->d_pd16[0] = reinterpret_cast<uint16_t*>(base + oP0);
@@ -722,6 +732,8 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
 static cudaError_t launch_one_step(fs_sim* s, int j)
 {
     const fs::StepArgs a = step_args(s, j);
+    if (s->pressure == FS_PRESSURE_PUSH && s->d_dtrec)
+        return fs::launch_push_step_adaptive(a, s->p.age_dtype, s->stream, s->g->num_sms);
     if (s->pressure == FS_PRESSURE_PUSH)
         return fs::launch_push_step(a, s->p.age_dtype, s->stream, s->g->num_sms);
     if (s->g->smem_path)
@@ -743,7 +755,7 @@ static fs_status ensure_graph(fs_sim* s, int K)
     for (int j = 0; j < K && e == cudaSuccess; ++j)
         e = launch_one_step(s, j);
     if (e == cudaSuccess)
-        e = fs::launch_run_epilogue(s->d_ctl, s->d_deltas, K, s->p.model, s->stream);
+        e = fs::launch_run_epilogue(s->d_ctl, s->d_deltas, K, s->p.model, s->d_dtrec, s->M.dt, s->stream);
     cudaError_t e2 = cudaStreamEndCapture(s->stream, &graph);
     FS_CUDA(s, e);
     FS_CUDA(s, e2);
@@ -785,7 +797,7 @@ static fs_status run_enqueue(fs_sim* s, int64_t steps, int32_t graph_steps, uint
     if (rem > 0) {
         for (int j = 0; j < rem; ++j)
             FS_CUDA(s, launch_one_step(s, j));
-        FS_CUDA(s, fs::launch_run_epilogue(s->d_ctl, s->d_deltas, rem, s->p.model, s->stream));
+        FS_CUDA(s, fs::launch_run_epilogue(s->d_ctl, s->d_deltas, rem, s->p.model, s->d_dtrec, s->M.dt, s->stream));
     }
     if (replay_ev)
         FS_CUDA(s, cudaEventRecord(replay_ev[full + 1], s->stream));
@@ -990,6 +1002,36 @@ fs_status fs_sim_set_state(fs_sim* s, const uint8_t* state, const void* age, int
     return FS_OK;
 }
 
+fs_status fs_sim_time(const fs_sim* s, double* elapsed, float* next_dt)
+{
+    if (!s)
+        return fail(FS_EINVAL, "sim is NULL");
+    if (s->failed)
+        return fail(FS_ESTATE, "sim is in a failed state");
+    fs::DevCtl c;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(&c, s->d_ctl, sizeof(c), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+        return fail(FS_ECUDA, "fs_sim_time: %s", cudaGetErrorString(e));
+    if (elapsed)
+        *elapsed = c.time;
+    if (next_dt) {
+        float dt = s->M.dt;
+        if (s->d_dtrec) {
+            // the device's own rule, in the same FP32 operations
+            uint32_t bits = c.lam[(c.step + 2) % 3];
+            float lp;
+            memcpy(&lp, &bits, sizeof(lp));
+            const float eps = (float)s->p.eps, delta = (float)(s->p.delta > 0 ? s->p.delta : 1e-12);
+            const float q = eps / (lp + delta);
+            dt = q < dt ? q : dt;
+        }
+        *next_dt = dt;
+    }
+    return FS_OK;
+}
+
 fs_status fs_sim_pressure_get(const fs_sim* s, int32_t* pressure)
 {
     if (!s || !pressure)
@@ -1137,6 +1179,8 @@ extern "C" fs_status fs_step_noalloc(const fs_graph* g, const fs_sim_params* par
     fs_status st = check_params(&pv);
     if (st != FS_OK)
         return st;
+    if (pv.eps > 0)
+        return fail(FS_EUNSUPPORTED, "fs_step_noalloc: one step has a fixed size (eps must be 0)");
     if (step < 0 || step >= ((int64_t)1 << 32))
         return fail(FS_EINVAL, "fs_step_noalloc: step must be in [0, 2^32)");
     if (g->n_m > kNoAllocMaxMergeRows)

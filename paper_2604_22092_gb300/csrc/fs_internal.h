@@ -62,6 +62,11 @@ struct DevCtl {
     uint32_t counts[4];           // counts of the current state
     int32_t error;                // device error word (0 = ok)
     int32_t pad_;
+    // adaptive step: the largest rate of step k goes to lam[k % 3] (FP32
+    // bits, atomic max), read by step k + 1 for its size; simulated time
+    uint32_t lam[3];
+    int32_t pad2_;
+    double time;                  // sum of the step sizes since init / set_state
 };
 
 enum { kErrNone = 0, kErrTmaTimeout = 1, kErrBadState = 2, kErrBadGraph = 3 };
@@ -122,6 +127,11 @@ struct StepArgs {
     unsigned long long* pd64[2];  // [n_m] pending pushes: +1 tally low word, -1 tally high word
     const int64_t* out_ptr;       // [n + 1] transposed CSR: the nodes whose rows list node j
     const int32_t* out_col;       // [nnz] internal ids
+    // adaptive step (push kernel's ADAPTIVE instance): dt_k = min(M.dt,
+    // eps / (lambda*_{k-1} + delta)); the size of step j of a launch
+    // sequence is recorded in dtrec[j] for the epilogue's clock
+    float eps, delta;
+    float* dtrec;                 // [kMaxGraphSteps]
 };
 
 constexpr int kPushG = 8;                 // thread-class nodes per thread of the push step

@@ -21,7 +21,11 @@ cudaError_t launch_step(const StepArgs& a, int age_dtype, cudaStream_t s, bool p
 cudaError_t launch_step_smem(const StepArgs& a, int age_dtype, cudaStream_t s, int num_sms);
 cudaError_t launch_build_ptables(const ModelF& M, int age_dtype, float4* tab, float* ps, cudaStream_t s);
 cudaError_t launch_run_begin(DevCtl* ctl, uint32_t* out, cudaStream_t s);
-cudaError_t launch_run_epilogue(DevCtl* ctl, unsigned long long* deltas, int K, int model, cudaStream_t s);
+// dtrec: the K step sizes (adaptive step) or null (every step is dt)
+cudaError_t launch_run_epilogue(DevCtl* ctl, unsigned long long* deltas, int K, int model, const float* dtrec,
+                                float dt, cudaStream_t s);
+// one step of the push form with the adaptive step
+cudaError_t launch_push_step_adaptive(const StepArgs& a, int age_dtype, cudaStream_t s, int num_sms);
 cudaError_t launch_refresh(const uint8_t* X, int n, const int32_t* deg, uint32_t* bm0, uint32_t* bm1, DevCtl* ctl,
                            cudaStream_t s);
 cudaError_t launch_set_index(uint8_t* X, const int32_t* idx, int64_t n_idx, const int32_t* inv, int state,

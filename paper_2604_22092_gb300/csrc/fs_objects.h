@@ -55,6 +55,8 @@ struct fs_sim {
     unsigned long long* d_deltas = nullptr;
     float4* d_ptab = nullptr;
     float* d_ps = nullptr;
+    // adaptive step (p.eps > 0): the step sizes of the current launch sequence
+    float* d_dtrec = nullptr;
     // push form of the pressure (pressure == FS_PRESSURE_PUSH)
     int pressure = FS_PRESSURE_GATHER;
     uint8_t* d_cnt8 = nullptr;

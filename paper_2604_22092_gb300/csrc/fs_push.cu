@@ -48,6 +48,18 @@ __device__ __noinline__ float p_direct_p(const ModelF& M, int x, float age)
     return p_of_rate(M, hazard(x == kE ? M.lat : M.inf, age));
 }
 
+// the hazard of an E or I node (adaptive step: evaluated every step; out of line)
+__device__ __noinline__ float rate_ei(const ModelF& M, int x, float age)
+{
+    return hazard(x == kE ? M.lat : M.inf, age);
+}
+
+// p = 1 - exp(-lambda dt) with the step's own size (adaptive step)
+__device__ __forceinline__ float p_of_rate_dt(float lambda, float dt)
+{
+    return lambda > 0.0f ? -expm1f(-__fmul_rn(lambda, dt)) : 0.0f;
+}
+
 // an E/I probability whose table slot 0 holds another age: slot 1, else
 // direct evaluation (rare; out of line)
 __device__ __noinline__ float p_table_miss(const StepArgs& a, int x, float age)
@@ -292,9 +304,9 @@ __device__ __forceinline__ bool group_idle(const StepArgs& a, uint32_t par, int6
 // then the probability-table loads of all eight nodes issued together; the
 // probabilities go to the lane's slots in shared memory. Nodes at or beyond
 // n_thr (a partial last group) are treated as R.
-template <typename AgeT>
+template <typename AgeT, bool ADAPTIVE>
 __device__ __forceinline__ void group_prepare(const StepArgs& a, uint32_t par, int i0, const GroupLoads& gl,
-                                              Item& it, float* __restrict__ pslot)
+                                              Item& it, float* __restrict__ pslot, float dt, float& lmax)
 {
     it.kind = kItemGroup;
     it.base = i0;
@@ -347,6 +359,35 @@ __device__ __forceinline__ void group_prepare(const StepArgs& a, uint32_t par, i
     // table lookups, resolved after every load of this phase has been issued
     uint2 nc = c8;
     float p[kPushG];
+    if constexpr (ADAPTIVE) {
+        // rates evaluated directly (ages leave the fixed-step sequence); the
+        // largest one sets the next step's size
+#pragma unroll
+        for (int u = 0; u < kPushG; ++u) {
+            const int x = (int)byte_of(xs, u);
+            const bool isS = x == kS, isEI = x == kE || x == kI;
+            const uint32_t d = (pdw[u >> 1] >> ((u & 1) << 4)) & 0xffffu;
+            const uint32_t c = isS ? byte_of(c8, u) + (d & 0xffu) - (d >> 8) : 0u;
+            if (isS)
+                set_byte(nc, u, c);
+            float lam = 0.0f;
+            if (isS && c != 0u)
+                lam = __fmul_rn(a.M.beta, (float)c);
+            else if (isEI)
+                lam = rate_ei(a.M, x, it.age[u]);
+            lmax = fmaxf(lmax, lam);
+            p[u] = p_of_rate_dt(lam, dt);
+        }
+        it.nc = nc;
+#pragma unroll
+        for (int u = 0; u < kPushG; ++u) {
+            if (p[u] > 0.0f) {
+                it.need |= 1u << u;
+                pslot[u] = p[u];
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int u = 0; u < kPushG; ++u) {
         const int x = (int)byte_of(xs, u);
@@ -378,9 +419,9 @@ __device__ __forceinline__ void group_prepare(const StepArgs& a, uint32_t par, i
 }
 
 // one merge-class node: its count and pending tallies are folded in here
-template <typename AgeT>
+template <typename AgeT, bool ADAPTIVE>
 __device__ __forceinline__ void hub_prepare(const StepArgs& a, uint32_t par, int i, Item& it,
-                                            float* __restrict__ pslot)
+                                            float* __restrict__ pslot, float dt, float& lmax)
 {
     it.kind = kItemHub;
     it.base = i;
@@ -407,7 +448,14 @@ __device__ __forceinline__ void hub_prepare(const StepArgs& a, uint32_t par, int
     }
     if (x == kE || x == kI)
         it.age[0] = AgeIO<AgeT>::load(static_cast<const AgeT*>(a.A)[i]);
-    const float p = node_p_push(a, x, it.age[0], c);
+    float p;
+    if constexpr (ADAPTIVE) {
+        const float lam = (x == kS) ? (c ? __fmul_rn(a.M.beta, (float)c) : 0.0f) : rate_ei(a.M, x, it.age[0]);
+        lmax = fmaxf(lmax, lam);
+        p = p_of_rate_dt(lam, dt);
+    } else {
+        p = node_p_push(a, x, it.age[0], c);
+    }
     if (p > 0.0f) {
         it.need = 1u;
         pslot[0] = p;
@@ -466,7 +514,7 @@ __device__ __forceinline__ uint32_t warp_draws(const StepArgs& a, uint32_t step,
 // transitions, renewal ages, in-place stores, push events and deltas
 template <typename AgeT>
 __device__ __forceinline__ void item_apply(const StepArgs& a, uint32_t par, Item& it, uint32_t fired,
-                                           uint32_t& ev, uint32_t& neg, PushDeltas& ld)
+                                           uint32_t& ev, uint32_t& neg, PushDeltas& ld, float dt)
 {
     if (it.kind == kItemNone)
         return;
@@ -481,7 +529,7 @@ __device__ __forceinline__ void item_apply(const StepArgs& a, uint32_t par, Item
         if (y != x)
             a.X[i0] = (uint8_t)y;
         if (f || x == kE || x == kI)
-            A[0] = AgeIO<AgeT>::store(f ? 0.0f : __fadd_rn(it.age[0], a.M.dt));
+            A[0] = AgeIO<AgeT>::store(f ? 0.0f : __fadd_rn(it.age[0], dt));
         if ((y == kI) != (x == kI)) {
             ev = 1u;
             neg = x == kI ? 1u : 0u;
@@ -507,7 +555,7 @@ __device__ __forceinline__ void item_apply(const StepArgs& a, uint32_t par, Item
             continue;
         const bool f = (fired >> u) & 1u;
         const int y = next_state(a, x, f);
-        it.age[u] = f ? 0.0f : ((x == kE || x == kI) ? __fadd_rn(it.age[u], a.M.dt) : 0.0f);
+        it.age[u] = f ? 0.0f : ((x == kE || x == kI) ? __fadd_rn(it.age[u], dt) : 0.0f);
         if (y != x)
             set_byte(nx, u, (uint32_t)y);
         if ((y == kI) != (x == kI)) {
@@ -664,7 +712,7 @@ constexpr int kScanRounds = 3;      // grid-stride rounds whose loads a warp iss
 // merge-class nodes; warps stride over them (grid-stride). Per-step deltas as
 // in the gather form.
 // ---------------------------------------------------------------------------
-template <typename AgeT, bool SCAN>
+template <typename AgeT, bool SCAN, bool ADAPTIVE>
 __global__ void __launch_bounds__(kPushThreads, kPushCtasPerSm) push_step_kernel(const __grid_constant__ StepArgs a)
 {
     __shared__ unsigned long long s_delta[kDeltaFields];
@@ -676,6 +724,20 @@ __global__ void __launch_bounds__(kPushThreads, kPushCtasPerSm) push_step_kernel
         s_delta[tid] = 0ull;
     const int64_t k = a.ctl->step + a.j;
     const uint32_t par = (uint32_t)(k & 1);
+    // the step's size: fixed, or (Section 5.2) min(dt_max, eps / (lambda* of
+    // the previous step + delta)); this step's largest rate goes to lam[k % 3]
+    // for the next one, lam[(k + 1) % 3] (read two steps ago) is cleared for
+    // the step after it
+    float dt = a.M.dt;
+    float lmax = 0.0f;
+    if constexpr (ADAPTIVE) {
+        const float lp = __uint_as_float(a.ctl->lam[(k + 2) % 3]);
+        dt = fminf(a.M.dt, __fdiv_rn(a.eps, __fadd_rn(lp, a.delta)));
+        if (blockIdx.x == 0 && tid == 0) {
+            a.ctl->lam[(k + 1) % 3] = 0u;
+            a.dtrec[a.j] = dt;
+        }
+    }
     // counts and tallies are loaded a round ahead while S nodes are common
     // (counts of the state at the start of this launch sequence)
     const bool spec_s = (int64_t)a.ctl->counts[0] * 16 >= (int64_t)a.n;
@@ -700,13 +762,13 @@ __global__ void __launch_bounds__(kPushThreads, kPushCtasPerSm) push_step_kernel
             it.base = 0;
             it.need = 0u;
             if (t < n_grp)
-                group_prepare<AgeT>(a, par, (int)(t * kPushG), cur, it, pslot);
+                group_prepare<AgeT, ADAPTIVE>(a, par, (int)(t * kPushG), cur, it, pslot, dt, lmax);
             else if (t < total)
-                hub_prepare<AgeT>(a, par, a.n_thr + (int)(t - n_grp), it, pslot);
+                hub_prepare<AgeT, ADAPTIVE>(a, par, a.n_thr + (int)(t - n_grp), it, pslot, dt, lmax);
             __syncwarp();
             const uint32_t fired = warp_draws(a, (uint32_t)k, it, w);
             uint32_t ev = 0u, neg = 0u;
-            item_apply<AgeT>(a, par, it, fired, ev, neg, ld);
+            item_apply<AgeT>(a, par, it, fired, ev, neg, ld, dt);
             warp_push<false>(a, par, ev, neg, it.base, w.ev);
         }
     }
@@ -737,15 +799,21 @@ __global__ void __launch_bounds__(kPushThreads, kPushCtasPerSm) push_step_kernel
             it.base = 0;
             it.need = 0u;
             if (t < n_grp)
-                group_prepare<AgeT>(a, par, (int)(t * kPushG), cur, it, pslot);
+                group_prepare<AgeT, ADAPTIVE>(a, par, (int)(t * kPushG), cur, it, pslot, dt, lmax);
             else if (t < total)
-                hub_prepare<AgeT>(a, par, a.n_thr + (int)(t - n_grp), it, pslot);
+                hub_prepare<AgeT, ADAPTIVE>(a, par, a.n_thr + (int)(t - n_grp), it, pslot, dt, lmax);
             __syncwarp();
             const uint32_t fired = warp_draws(a, (uint32_t)k, it, w);
             uint32_t ev = 0u, neg = 0u;
-            item_apply<AgeT>(a, par, it, fired, ev, neg, ld);
+            item_apply<AgeT>(a, par, it, fired, ev, neg, ld, dt);
             warp_push<false>(a, par, ev, neg, it.base, w.ev);
         }
+    }
+    if constexpr (ADAPTIVE) {
+        // rates are >= 0, so their FP32 bits order as unsigned integers
+        const uint32_t m = __reduce_max_sync(kFull, __float_as_uint(lmax));
+        if (lane == 0 && m)
+            atomicMax(&a.ctl->lam[k % 3], m);
     }
     const uint32_t fs_ = __reduce_add_sync(kFull, ld.fS), fe = __reduce_add_sync(kFull, ld.fE);
     const uint32_t fi = __reduce_add_sync(kFull, ld.fI), ds = __reduce_add_sync(kFull, ld.dS);
@@ -822,7 +890,7 @@ __global__ void transpose_kernel(const int64_t* __restrict__ sell_off, const int
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
-template <typename AgeT>
+template <typename AgeT, bool ADAPTIVE>
 static cudaError_t launch_push_step_t(const StepArgs& a, cudaStream_t s, int num_sms)
 {
     const int64_t items = ((int64_t)a.n_thr + kPushG - 1) / kPushG + a.n_m;
@@ -831,9 +899,9 @@ static cudaError_t launch_push_step_t(const StepArgs& a, cudaStream_t s, int num
     const int grid = (int)std::max<int64_t>(1, std::min(need, cap));
     // one item per lane when the grid covers them all, else the block scan
     if (need <= cap)
-        push_step_kernel<AgeT, false><<<grid, kPushThreads, 0, s>>>(a);
+        push_step_kernel<AgeT, false, ADAPTIVE><<<grid, kPushThreads, 0, s>>>(a);
     else
-        push_step_kernel<AgeT, true><<<grid, kPushThreads, 0, s>>>(a);
+        push_step_kernel<AgeT, true, ADAPTIVE><<<grid, kPushThreads, 0, s>>>(a);
     g_launch_count += 1;
     return cudaGetLastError();
 }
@@ -841,9 +909,18 @@ static cudaError_t launch_push_step_t(const StepArgs& a, cudaStream_t s, int num
 cudaError_t launch_push_step(const StepArgs& a, int age_dtype, cudaStream_t s, int num_sms)
 {
     switch (age_dtype) {
-    case kAgeF16: return launch_push_step_t<__half>(a, s, num_sms);
-    case kAgeBF16: return launch_push_step_t<__nv_bfloat16>(a, s, num_sms);
-    default: return launch_push_step_t<float>(a, s, num_sms);
+    case kAgeF16: return launch_push_step_t<__half, false>(a, s, num_sms);
+    case kAgeBF16: return launch_push_step_t<__nv_bfloat16, false>(a, s, num_sms);
+    default: return launch_push_step_t<float, false>(a, s, num_sms);
+    }
+}
+
+cudaError_t launch_push_step_adaptive(const StepArgs& a, int age_dtype, cudaStream_t s, int num_sms)
+{
+    switch (age_dtype) {
+    case kAgeF16: return launch_push_step_t<__half, true>(a, s, num_sms);
+    case kAgeBF16: return launch_push_step_t<__nv_bfloat16, true>(a, s, num_sms);
+    default: return launch_push_step_t<float, true>(a, s, num_sms);
     }
 }
 

@@ -588,7 +588,8 @@ __global__ void run_begin_kernel(DevCtl* ctl, uint32_t* out)
     }
 }
 
-__global__ void run_epilogue_kernel(DevCtl* ctl, unsigned long long* deltas, int K, int model)
+__global__ void run_epilogue_kernel(DevCtl* ctl, unsigned long long* deltas, int K, int model, const float* dtrec,
+                                    float dt)
 {
     __shared__ unsigned long long d[kMaxGraphSteps][kDeltaFields];
     for (int t = threadIdx.x; t < K * kDeltaFields; t += blockDim.x) {
@@ -623,6 +624,10 @@ __global__ void run_epilogue_kernel(DevCtl* ctl, unsigned long long* deltas, int
         ctl->ds_cur = ds;
         ctl->ds_total = dst;
         ctl->s_total = st;
+        double t = ctl->time;
+        for (int j = 0; j < K; ++j)
+            t += (double)(dtrec ? dtrec[j] : dt);
+        ctl->time = t;
         ctl->step += K;
         if (out)
             ctl->row = row + K;
@@ -780,9 +785,10 @@ cudaError_t launch_run_begin(DevCtl* ctl, uint32_t* out, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_run_epilogue(DevCtl* ctl, unsigned long long* deltas, int K, int model, cudaStream_t s)
+cudaError_t launch_run_epilogue(DevCtl* ctl, unsigned long long* deltas, int K, int model, const float* dtrec,
+                                float dt, cudaStream_t s)
 {
-    run_epilogue_kernel<<<1, 256, 0, s>>>(ctl, deltas, K, model);
+    run_epilogue_kernel<<<1, 256, 0, s>>>(ctl, deltas, K, model, dtrec, dt);
     g_launch_count += 1;
     return cudaGetLastError();
 }
