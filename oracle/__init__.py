@@ -31,6 +31,7 @@ S, E, I, R = 0, 1, 2, 3
 SIR, SEIR = 0, 1
 LAW_NONE, LAW_EXP, LAW_LOGNORMAL, LAW_WEIBULL, LAW_ERLANG = 0, 1, 2, 3, 4
 AGE_F32, AGE_F16, AGE_BF16 = 0, 1, 2
+SHED_NONE, SHED_HAZARD, SHED_DENSITY = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
@@ -58,7 +59,7 @@ class Params(ctypes.Structure):
                 ("latent", Law), ("infectious", Law),
                 ("beta", ctypes.c_double), ("dt", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("rep", ctypes.c_uint32),
-                ("pad_", ctypes.c_int32)]
+                ("shed_mode", ctypes.c_int32), ("shedding", Law)]
 
 
 def law(kind: str, a: float = 0.0, b: float = 0.0, k: int = 0) -> Law:
@@ -69,9 +70,12 @@ def law(kind: str, a: float = 0.0, b: float = 0.0, k: int = 0) -> Law:
 
 
 def params(model: int, latent: Law | None, infectious: Law, beta: float, dt: float,
-           seed: int, rep: int = 0, age_dtype: int = AGE_F32) -> Params:
+           seed: int, rep: int = 0, age_dtype: int = AGE_F32, shed_mode: int = SHED_NONE,
+           shedding: Law | None = None) -> Params:
+    """shed_mode / shedding: the shedding profile s(tau) of Eq. 8 (SHED_NONE: s = 1)."""
     return Params(model, age_dtype, latent if latent is not None else Law(0, 0, 0.0, 0.0),
-                  infectious, float(beta), float(dt), int(seed), int(rep), 0)
+                  infectious, float(beta), float(dt), int(seed), int(rep), int(shed_mode),
+                  shedding if shedding is not None else Law(0, 0, 0.0, 0.0))
 
 
 def lib():
@@ -110,6 +114,15 @@ def lib():
             L.fso_step.argtypes = [ctypes.c_int64, i64p, i32p, P(Params), ctypes.c_int64,
                                    u8p, f32p, u8p, f32p, f64p, f64p]
             L.fso_step.restype = ctypes.c_int
+            L.fso_density.argtypes = [P(Law), ctypes.c_double]
+            L.fso_density.restype = ctypes.c_double
+            L.fso_shedding.argtypes = [P(Params), ctypes.c_double]
+            L.fso_shedding.restype = ctypes.c_double
+            L.fso_infectivity.argtypes = [P(Params), ctypes.c_float]
+            L.fso_infectivity.restype = ctypes.c_float
+            L.fso_step_rho.argtypes = [ctypes.c_int64, i64p, i32p, P(Params), ctypes.c_int64,
+                                       u8p, f32p, f32p, u8p, f32p, f32p, f64p, f64p]
+            L.fso_step_rho.restype = ctypes.c_int
             L.fso_run.argtypes = [ctypes.c_int64, i64p, i32p, P(Params), ctypes.c_int64,
                                   ctypes.c_int64, u8p, f32p, u32p]
             L.fso_run.restype = ctypes.c_int
@@ -205,6 +218,44 @@ def step(row_ptr, col_ind, prm: Params, k: int, X, A, want_margin=False, want_la
     if rc:
         raise ValueError("oracle step rejected the state")
     return Xn, An, margin, lam
+
+
+def density(lw: Law, tau: float) -> float:
+    return lib().fso_density(ctypes.byref(lw), float(tau))
+
+
+def shedding(prm: Params, tau: float) -> float:
+    """s(tau) of Eq. 8."""
+    return lib().fso_shedding(ctypes.byref(prm), float(tau))
+
+
+def infectivity(prm: Params, tau: float) -> float:
+    """The stored infectivity beta s(tau) of an I node (fp32, then the storage type)."""
+    return lib().fso_infectivity(ctypes.byref(prm), float(tau))
+
+
+def step_rho(row_ptr, col_ind, prm: Params, k: int, X, A, rho_in=None):
+    """One step with the infectivity explicit: rho_in (float32[n] as stored,
+    None = computed from the ages). Returns (Xn, An, rho_next, margin, lam)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col_ind, dtype=np.int32)
+    X = np.ascontiguousarray(X, dtype=np.uint8)
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    rin = None if rho_in is None else np.ascontiguousarray(rho_in, dtype=np.float32)
+    n = X.size
+    Xn = np.empty_like(X)
+    An = np.empty_like(A)
+    rout = np.empty(n, dtype=np.float32)
+    margin = np.empty(n, dtype=np.float64)
+    lam = np.empty(n, dtype=np.float64)
+    rc = lib().fso_step_rho(n, _ptr(rp, ctypes.c_int64), _ptr(ci, ctypes.c_int32), ctypes.byref(prm), k,
+                            _ptr(X, ctypes.c_uint8), _ptr(A, ctypes.c_float),
+                            _ptr(rin, ctypes.c_float) if rin is not None else None,
+                            _ptr(Xn, ctypes.c_uint8), _ptr(An, ctypes.c_float), _ptr(rout, ctypes.c_float),
+                            _ptr(margin, ctypes.c_double), _ptr(lam, ctypes.c_double))
+    if rc:
+        raise ValueError("oracle step rejected the state or the parameters")
+    return Xn, An, rout, margin, lam
 
 
 def run(row_ptr, col_ind, prm: Params, k0: int, steps: int, X, A):

@@ -16,7 +16,11 @@
  *     5.7, "promote on load, cast on store");
  *   - the infectivity is the indicator of state I with unit edge weights
  *     (Eq. 8 with s = 1), so the pressure of an S node is beta times the
- *     integer number of infectious in-neighbours (Eq. 3);
+ *     integer number of infectious in-neighbours (Eq. 3); with a shedding
+ *     profile s(tau) (the hazard or the density of a law) the infectivity
+ *     beta s(tau) of each I node is evaluated at its begin-of-step age,
+ *     stored like an age (fp32, then the storage type), and the pressure is
+ *     the double sum of the stored values;
  *   - the paper's Triton PRNG is replaced by Philox4x32-10 keyed by
  *     (seed, replicate, step, node).
  */
@@ -135,6 +139,59 @@ double fso_hazard(const fso_law* law, double tau)
     }
 }
 
+/* Densities f(tau) of the holding-time laws, written from their textbook
+ * definitions (used as shedding profiles, Section 5.3). */
+double fso_density(const fso_law* law, double tau)
+{
+    if (tau < 0.0)
+        return 0.0;
+    switch (law->kind) {
+    case FSO_LAW_NONE:
+        return 0.0;
+    case FSO_LAW_EXP:
+        return law->a * exp(-law->a * tau);
+    case FSO_LAW_LOGNORMAL: {
+        /* f = exp(-(ln tau - mu)^2 / (2 sigma^2)) / (tau sigma sqrt(2 pi)) */
+        double mu = law->a, sigma = law->b;
+        if (!(tau > 0.0))
+            return 0.0;
+        double y = (log(tau) - mu) / sigma;
+        return exp(-0.5 * y * y) / (tau * sigma * sqrt(2.0 * M_PI));
+    }
+    case FSO_LAW_WEIBULL: {
+        /* f = (k/s) (tau/s)^(k-1) exp(-(tau/s)^k) */
+        double k = law->a, s = law->b, x = tau / s;
+        return (k / s) * pow(x, k - 1.0) * exp(-pow(x, k));
+    }
+    case FSO_LAW_ERLANG: {
+        /* f = r^k tau^(k-1) exp(-r tau) / (k-1)! */
+        int k = law->k;
+        double r = law->a;
+        double f = r * exp(-r * tau);
+        for (int n = 1; n < k; ++n)
+            f *= r * tau / (double)n;
+        return f;
+    }
+    default:
+        return NAN;
+    }
+}
+
+/* Eq. 8: rho_j = beta s(tau_j) 1{X_j = I}; s = 1 is the Markovian edge. */
+double fso_shedding(const fso_params* prm, double tau)
+{
+    switch (prm->shed_mode) {
+    case FSO_SHED_NONE:
+        return 1.0;
+    case FSO_SHED_HAZARD:
+        return fso_hazard(&prm->shedding, tau);
+    case FSO_SHED_DENSITY:
+        return fso_density(&prm->shedding, tau);
+    default:
+        return NAN;
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Storage rounding (Section 5.7, Table "mixed precision dtypes"): all math */
 /* in fp32, round-to-nearest-even on the store.                             */
@@ -219,6 +276,14 @@ float fso_age_next(float age, double dt, int32_t age_dtype)
     return fso_store_age(s, age_dtype);
 }
 
+/* Eq. 8 stored as Section 5.7 stores ages: the product beta * s(tau) in
+ * double, rounded to fp32, then to the storage type. */
+float fso_infectivity(const fso_params* prm, float tau)
+{
+    float rho32 = (float)(prm->beta * fso_shedding(prm, (double)tau));
+    return fso_store_age(rho32, prm->age_dtype);
+}
+
 /* ------------------------------------------------------------------------ */
 /* The step (Algorithm 3, fixed step; Section 3 Eqs. 1-3; Section 5.2).     */
 /* ------------------------------------------------------------------------ */
@@ -262,17 +327,36 @@ int fso_step(int64_t n, const int64_t* row_ptr, const int32_t* col_ind,
              const uint8_t* X, const float* A, uint8_t* Xn, float* An,
              double* margin, double* lambda_out)
 {
+    return fso_step_rho(n, row_ptr, col_ind, prm, k, X, A, NULL, Xn, An, NULL, margin, lambda_out);
+}
+
+int fso_step_rho(int64_t n, const int64_t* row_ptr, const int32_t* col_ind,
+                 const fso_params* prm, int64_t k,
+                 const uint8_t* X, const float* A, const float* rho_in,
+                 uint8_t* Xn, float* An, float* rho_out,
+                 double* margin, double* lambda_out)
+{
+    if (prm->shed_mode < FSO_SHED_NONE || prm->shed_mode > FSO_SHED_DENSITY)
+        return -1;
     for (int64_t i = 0; i < n; ++i) {
         int x = X[i];
         double tau = (double)A[i];
         double lambda = 0.0;
-        if (x == FSO_S) {
-            /* Eq. 3 with rho = 1{X_j = I}: integer pressure c_i */
+        if (x == FSO_S && prm->shed_mode == FSO_SHED_NONE) {
+            /* Eq. 3 with rho = beta 1{X_j = I}: integer pressure c_i */
             int64_t c = 0;
             for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
                 if (X[col_ind[e]] == FSO_I)
                     c += 1;
             lambda = prm->beta * (double)c;
+        } else if (x == FSO_S) {
+            /* Eq. 3 with the infectivity of Eq. 8: the sum of the stored
+             * rho_j of the infectious in-neighbours, in row order */
+            for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+                int32_t j = col_ind[e];
+                if (X[j] == FSO_I)
+                    lambda += rho_in ? (double)rho_in[j] : (double)fso_infectivity(prm, A[j]);
+            }
         } else if (x == FSO_E) {
             if (prm->model != FSO_SEIR)
                 return -1;
@@ -304,6 +388,10 @@ int fso_step(int64_t n, const int64_t* row_ptr, const int32_t* col_ind,
             An[i] = (x == FSO_E || x == FSO_I) ? fso_age_next(A[i], prm->dt, prm->age_dtype)
                                                : 0.0f;
         }
+        /* the next step's infectivity, from the new age (Section 5.3) */
+        if (rho_out)
+            rho_out[i] = (Xn[i] != FSO_I) ? 0.0f
+                       : (prm->shed_mode == FSO_SHED_NONE) ? (float)prm->beta : fso_infectivity(prm, An[i]);
     }
     return 0;
 }
@@ -451,6 +539,8 @@ int fso_exact_run(int64_t n, const int64_t* row_ptr, const int32_t* col_ind,
                   int64_t n_index, int32_t index_state, uint64_t rng_seed,
                   int64_t n_grid, double grid_dt, uint32_t* counts_grid)
 {
+    if (prm->shed_mode != FSO_SHED_NONE)
+        return -1;                   /* rates between events must be constant */
     int64_t nnz = row_ptr[n];
     uint8_t* X = (uint8_t*)malloc((size_t)n);
     double* t_exit = (double*)malloc(sizeof(double) * (size_t)n);

@@ -32,6 +32,8 @@ enum { FSO_SIR = 0, FSO_SEIR = 1 };
 enum { FSO_LAW_NONE = 0, FSO_LAW_EXP = 1, FSO_LAW_LOGNORMAL = 2,
        FSO_LAW_WEIBULL = 3, FSO_LAW_ERLANG = 4 };
 enum { FSO_AGE_F32 = 0, FSO_AGE_F16 = 1, FSO_AGE_BF16 = 2 };
+/* shedding profile s(tau) of the infectivity (Section 5.3, Eq. 8) */
+enum { FSO_SHED_NONE = 0, FSO_SHED_HAZARD = 1, FSO_SHED_DENSITY = 2 };
 
 /* Holding-time law.  EXP: a = rate.  LOGNORMAL: a = mu, b = sigma (log-days).
  * WEIBULL: a = shape k, b = scale s.  ERLANG: k = stages, a = rate per stage. */
@@ -50,7 +52,10 @@ typedef struct {
     double dt;              /* fixed step (days)                             */
     uint64_t seed;          /* Philox key                                    */
     uint32_t rep;           /* realisation index inside the key's stream     */
-    int32_t pad_;
+    int32_t shed_mode;      /* FSO_SHED_NONE: s = 1 (Markovian edges);
+                               FSO_SHED_HAZARD / _DENSITY: s(tau) = the hazard
+                               or the density of `shedding`                  */
+    fso_law shedding;
 } fso_params;
 
 /* ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) ------------------ */
@@ -61,6 +66,16 @@ double fso_uniform(uint64_t seed, uint32_t rep, int64_t step, int64_t node);
 /* ---- hazards in double precision (Section 5.1, Proposition 1) ----------- */
 double fso_erfcx(double z);
 double fso_hazard(const fso_law* law, double tau);
+
+/* probability density of a law (0 for FSO_LAW_NONE) */
+double fso_density(const fso_law* law, double tau);
+
+/* ---- source-node infectivity (Section 5.3, Eq. 8) ------------------------ */
+/* s(tau): 1, or the hazard / density of prm->shedding at infection age tau */
+double fso_shedding(const fso_params* prm, double tau);
+/* The stored infectivity of an I node of age tau: beta * s(tau) rounded to
+ * fp32, then to the storage type of the ages (prm->age_dtype). */
+float fso_infectivity(const fso_params* prm, float tau);
 
 /* ---- storage rounding (Section 5.7: fp32 math, cast on store) ----------- */
 uint16_t fso_f32_to_f16_bits(float x);
@@ -86,6 +101,19 @@ int fso_step(int64_t n, const int64_t* row_ptr, const int32_t* col_ind,
              const fso_params* prm, int64_t k,
              const uint8_t* X, const float* A, uint8_t* Xn, float* An,
              double* margin, double* lambda_out);
+
+/* The same step with the infectivity made explicit (shed_mode != NONE: the
+ * pressure of an S node is the sum, in double, of the stored infectivities
+ * of its infectious in-neighbours). rho_in[n]: the infectivity of every node
+ * as stored (read only where X = I), or NULL to compute it from A with
+ * fso_infectivity. rho_out[n] (may be NULL): the next step's infectivity,
+ * fso_infectivity(An) where Xn = I and 0 elsewhere. With shed_mode = NONE
+ * both are ignored (rho_out is filled with beta where Xn = I). */
+int fso_step_rho(int64_t n, const int64_t* row_ptr, const int32_t* col_ind,
+                 const fso_params* prm, int64_t k,
+                 const uint8_t* X, const float* A, const float* rho_in,
+                 uint8_t* Xn, float* An, float* rho_out,
+                 double* margin, double* lambda_out);
 
 /* steps consecutive steps k0 .. k0+steps-1, in place on (X, A);
  * counts[(steps+1)*4], row 0 = the input state. */
