@@ -65,8 +65,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-served", action="store_true", help="skip the served-vs-plain block")
-    ap.add_argument("--workload", choices=["regular", "ensemble", "serving", "large", "precision"], default="regular",
-                    help="regular: the headline line; ensemble / serving: full-size packed and served runs")
+    ap.add_argument("--workload", choices=["regular", "ensemble", "serving", "large", "precision", "shedding"],
+                    default="regular",
+                    help="regular: the headline line; ensemble / serving: full-size packed and served runs; "
+                         "shedding: constant vs age-dependent infectivity on regular d=8 and BA m=4 graphs")
     ap.add_argument("--age", choices=["f32", "f16"], default="f32", help="age storage of ensemble/serving runs")
     ap.add_argument("--ens-graphs", type=int, default=64, help="graphs of the packed-ensemble run")
     ap.add_argument("--ens-steps", type=int, default=500, help="steps of the packed-ensemble run")
@@ -800,6 +802,57 @@ def run_reference(args, rank, world):
             "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def shedding_bench(fs, torch, n: int, sim_steps: int, graph_steps: int, reps: int = 3):
+    """Cost of the age-dependent source infectivity (Eq. 8) on the step, as the
+    paper's shedding-overhead table measures it: N = 10^6, mean degree 8, a
+    regular and a Barabasi-Albert (m = 4) graph, the same SEIR model with
+    constant beta and with beta s(tau), s = the infectious hazard h_IR (and,
+    as a second profile, a log-normal shedding density). Each variant: event-
+    timed CUDA Graph replays of a full run (ingest and init untimed), median
+    of `reps`, L2 flushed before each run."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    inf, lat = fs.law("lognormal", math.log(6.0), 0.6), fs.law("weibull", 2.0, 4.0)
+    K = graph_steps
+    full = sim_steps // K
+    variants = [
+        ("constant_gather", dict(pressure=fs.FS_PRESSURE_GATHER)),
+        ("constant_push", dict(pressure=fs.FS_PRESSURE_PUSH)),
+        ("shed_hazard_IR", dict(shed_mode=fs.FS_SHED_HAZARD, shedding=inf)),
+        ("shed_density_lognormal", dict(shed_mode=fs.FS_SHED_DENSITY, shedding=fs.law("lognormal", math.log(5.0), 0.5))),
+    ]
+    graphs = [("regular-d8", W.random_regular(n, 8, seed=0)), ("ba-m4", W.barabasi_albert(n, 4, seed=0))]
+    res = {"workload": f"seir-shedding-overhead-n{n:.0e}".replace("+0", ""), "sim_steps": sim_steps,
+           "graph_steps": K, "timed": "CUDA Graph replays of the step loop (CUDA events), median of runs",
+           "graphs": {}}
+    for gname, g in graphs:
+        allowed = W.non_hub_nodes(g) if gname.startswith("ba") else None
+        idx = W.index_nodes(g.n, 100, seed=1, allowed=allowed)
+        gh = fs.fs_graph_create(g.n, g.row_ptr, g.col_ind)
+        row = {}
+        for label, kw in variants:
+            prm = fs.sim_params(fs.FS_SEIR, inf, 0.25, 0.1, 3, latent=lat, **kw)
+            times = []
+            for r in range(reps + 1):
+                flush.fill_(1.0)
+                torch.cuda.synchronize()
+                sh = fs.fs_sim_init(gh, prm, idx)
+                ms = fs.fs_sim_run_timed(sh, sim_steps, K, None)
+                c = fs.fs_sim_run(sh, 0)
+                fs.fs_sim_destroy(sh)
+                if r:
+                    times.append(float(np.sum(ms[:full])))
+            t = float(np.median(times))
+            row[label] = {"value": round(g.n * full * K / (t * 1e-3) / 1e9, 3), "unit": UNIT,
+                          "ms_per_run": round(t, 3), "final_R": int(c[-1, 3])}
+        base = row["constant_gather"]["value"]
+        for label in ("shed_hazard_IR", "shed_density_lognormal"):
+            row[label]["slowdown_vs_constant_gather_pct"] = round((base / row[label]["value"] - 1) * 100, 2)
+        res["graphs"][gname] = row
+        fs.fs_graph_destroy(gh)
+    return res
+
+
 def run_extra(args):
     """Full-size packed-ensemble or serving runs (their own JSON line)."""
     import torch
@@ -811,6 +864,8 @@ def run_extra(args):
                              age_dtype=age, pressure=PRESSURE[args.pressure])
     elif args.workload == "precision":
         res = precision_bench(fs, torch, n=args.n, steps=args.sim_steps, reps=1000)
+    elif args.workload == "shedding":
+        res = shedding_bench(fs, torch, n=args.n, sim_steps=args.sim_steps, graph_steps=args.graph_steps)
     elif args.workload == "large":
         sizes = ((10_000_000, fs.FS_AGE_F32), (100_000_000, fs.FS_AGE_F32), (100_000_000, fs.FS_AGE_BF16))
         if args.large_n:

@@ -98,6 +98,25 @@ typedef struct {
     double a, b;
 } fs_law;
 
+/* Shedding profile s(tau) of the source-node infectivity (Section 5.3,
+ * Eq. 8): an I node of infection age tau exerts beta * s(tau) on each of its
+ * out-neighbours.
+ *   FS_SHED_NONE:    s = 1 (Markovian edges; the pressure is beta x the
+ *                    number of infectious in-neighbours, an integer count)
+ *   FS_SHED_HAZARD:  s = the hazard of the `shedding` law (e.g. the
+ *                    infectious law itself: beta h_IR(tau))
+ *   FS_SHED_DENSITY: s = the density of the `shedding` law (e.g. a
+ *                    log-normal viral-load profile)
+ * With a profile, every step writes beta s(tau') of each node that is I after
+ * it (tau' its new age), FP32 rounded to the sim's age storage type, and an S
+ * node's pressure is the FP32 sum of those values over its infectious
+ * in-neighbours, in a fixed order (row order in the one-lane-per-node class;
+ * segmented warp sums folded by warp, then by chunk, in the merge class), so
+ * a run is reproducible bit for bit. Gather form only: FS_PRESSURE_PUSH, eps
+ * > 0, packed ensembles, batches, the server and fs_step_noalloc need
+ * FS_SHED_NONE (FS_EUNSUPPORTED). */
+typedef enum { FS_SHED_NONE = 0, FS_SHED_HAZARD = 1, FS_SHED_DENSITY = 2 } fs_shed_mode;
+
 /* One realisation (Section 3; Algorithm 3 with a fixed step dt). */
 typedef struct {
     int32_t model;       /* FS_SIR or FS_SEIR                                     */
@@ -110,7 +129,7 @@ typedef struct {
     uint32_t replicate;  /* realisation index in the key's stream                  */
     int32_t index_state; /* compartment of the index cases: FS_E (SEIR) or FS_I    */
     int32_t flags;       /* FS_PRESSURE_AUTO / _GATHER / _PUSH; other values invalid */
-    int32_t reserved_;   /* must be 0                                              */
+    int32_t shed_mode;   /* fs_shed_mode (0: s = 1)                                */
     /* Adaptive step (Section 5.2): with eps > 0 step k advances by
      *   dt_k = min(dt, eps / (lambda*_{k-1} + delta))
      * where lambda*_{k-1} is the largest rate of any node in step k-1 (S:
@@ -123,6 +142,7 @@ typedef struct {
      * batches and the server need eps = 0. */
     double eps;          /* 0: fixed step; > 0: the tolerance (the paper uses 0.01-0.05) */
     double delta;        /* added to lambda*; 0 = 1e-12                            */
+    fs_law shedding;     /* the law of s(tau) when shed_mode != FS_SHED_NONE       */
 } fs_sim_params;
 
 /* Graph construction options (all fields may be 0 for the defaults). */
@@ -260,6 +280,12 @@ fs_status fs_sim_set_state(fs_sim* s, const uint8_t* state, const void* age, int
  * next step (dt for a fixed step). Synchronous. */
 fs_status fs_sim_time(const fs_sim* s, double* elapsed, float* next_dt);
 
+/* The infectivity the next step reads (Eq. 8): rho[i] = beta s(tau_i) as
+ * stored (age_dtype storage: float / binary16 / bfloat16 bits, n elements,
+ * original node order) for I nodes and 0 elsewhere. Needs shed_mode !=
+ * FS_SHED_NONE (else FS_EUNSUPPORTED). Synchronous. */
+fs_status fs_sim_infectivity_get(fs_sim* s, void* rho);
+
 /* The pressure form the sim runs (FS_PRESSURE_GATHER or FS_PRESSURE_PUSH). */
 fs_status fs_sim_pressure_get(const fs_sim* s, int32_t* pressure);
 
@@ -277,6 +303,9 @@ fs_status fs_sim_destroy(fs_sim* s);
  * step, nodes_dev[i]) as a float, device arrays (asynchronous).
  * ------------------------------------------------------------------------- */
 fs_status fs_eval_hazard(const fs_law* law, const float* tau_dev, float* h_dev, int64_t n, void* stream);
+/* f_dev[i] = the probability density of `law` at tau_dev[i] in FP32 (the
+ * shedding profile of FS_SHED_DENSITY); asynchronous. */
+fs_status fs_eval_density(const fs_law* law, const float* tau_dev, float* f_dev, int64_t n, void* stream);
 fs_status fs_eval_uniforms(uint64_t seed, uint32_t replicate, int64_t step, const int32_t* nodes_dev,
                            float* u_dev, int64_t n, void* stream);
 

@@ -19,15 +19,15 @@ from . import _abi
 from ._abi import (FS_AGE_BF16, FS_AGE_F16, FS_AGE_F32, FS_DISPATCH_AUTO, FS_DISPATCH_MERGE,
                    FS_DISPATCH_THREAD, FS_DISPATCH_TUNE, FS_E, FS_I, FS_LAW_ERLANG, FS_LAW_EXP, FS_LAW_LOGNORMAL,
                    FS_LAW_NONE, FS_LAW_WEIBULL, FS_PRESSURE_AUTO, FS_PRESSURE_GATHER, FS_PRESSURE_PUSH, FS_R,
-                   FS_S, FS_SEIR, FS_SIR, FsError, check)
+                   FS_S, FS_SEIR, FS_SHED_DENSITY, FS_SHED_HAZARD, FS_SHED_NONE, FS_SIR, FsError, check)
 
 __all__ = [
     "fs_version", "fs_last_error", "fs_graph_create", "fs_graph_info_get", "fs_graph_destroy",
     "fs_sim_init", "fs_sim_step", "fs_sim_run", "fs_sim_run_async", "fs_sim_sync", "fs_sim_run_timed",
     "fs_kernel_launches", "fs_tune_stats", "fs_tune_reset",
     "fs_sim_get_state", "fs_sim_set_state", "fs_sim_work", "fs_sim_pressure_get", "fs_sim_time",
-    "fs_sim_destroy",
-    "fs_eval_hazard",
+    "fs_sim_infectivity_get", "fs_sim_destroy",
+    "fs_eval_hazard", "fs_eval_density",
     "fs_eval_uniforms", "fs_step_noalloc", "fs_ens_create", "fs_ens_run", "fs_ens_get_state",
     "fs_ens_destroy", "fs_batch_create", "fs_batch_add", "fs_batch_run", "fs_batch_status", "fs_batch_destroy",
     "fs_server_create", "fs_server_submit", "fs_server_poll", "fs_server_drain", "fs_server_stats_get",
@@ -35,7 +35,8 @@ __all__ = [
     "law", "sim_params", "graph_opts", "FsError", "load",
     "FS_S", "FS_E", "FS_I", "FS_R", "FS_SIR", "FS_SEIR", "FS_AGE_F32", "FS_AGE_F16", "FS_AGE_BF16",
     "FS_DISPATCH_AUTO", "FS_DISPATCH_THREAD", "FS_DISPATCH_MERGE", "FS_DISPATCH_TUNE",
-    "FS_PRESSURE_AUTO", "FS_PRESSURE_GATHER", "FS_PRESSURE_PUSH",
+    "FS_PRESSURE_AUTO", "FS_PRESSURE_GATHER", "FS_PRESSURE_PUSH", "FS_SHED_NONE", "FS_SHED_HAZARD",
+    "FS_SHED_DENSITY",
 ]
 
 
@@ -86,14 +87,17 @@ def lognormal_from_mean_median(mean: float, median: float) -> _abi.fs_law:
 def sim_params(model: int, infectious: _abi.fs_law, beta: float, dt: float, seed: int,
                latent: _abi.fs_law | None = None, replicate: int = 0, index_state: int | None = None,
                age_dtype: int = FS_AGE_F32, pressure: int = FS_PRESSURE_AUTO, eps: float = 0.0,
-               delta: float = 0.0) -> _abi.fs_sim_params:
+               delta: float = 0.0, shed_mode: int = FS_SHED_NONE,
+               shedding: _abi.fs_law | None = None) -> _abi.fs_sim_params:
     """pressure: FS_PRESSURE_AUTO / FS_PRESSURE_GATHER / FS_PRESSURE_PUSH (the flags field);
-    eps > 0: adaptive step with dt as its cap (delta 0 = 1e-12)."""
+    eps > 0: adaptive step with dt as its cap (delta 0 = 1e-12);
+    shed_mode / shedding: the shedding profile s(tau) of the infectivity (FS_SHED_NONE: s = 1)."""
     if index_state is None:
         index_state = FS_E if model == FS_SEIR else FS_I
     return _abi.fs_sim_params(int(model), int(age_dtype), latent if latent is not None else law("none"),
                               infectious, float(beta), float(dt), int(seed), int(replicate),
-                              int(index_state), int(pressure), 0, float(eps), float(delta))
+                              int(index_state), int(pressure), int(shed_mode), float(eps), float(delta),
+                              shedding if shedding is not None else law("none"))
 
 
 def graph_opts(dispatch: int = FS_DISPATCH_AUTO, thread_max_deg: int = 0,
@@ -223,6 +227,13 @@ def fs_sim_time(s: int) -> tuple[float, float]:
     return t.value, d.value
 
 
+def fs_sim_infectivity_get(s: int, n: int, age_dtype: int = FS_AGE_F32) -> np.ndarray:
+    """rho[n] the next step reads (float32, or the raw 16-bit storage); 0 for non-I nodes."""
+    rho = np.zeros(n, dtype=_AGE_NP[age_dtype])
+    check(load().fs_sim_infectivity_get(s, _addr(rho)), "fs_sim_infectivity_get")
+    return rho
+
+
 def fs_sim_pressure_get(s: int) -> int:
     """FS_PRESSURE_GATHER or FS_PRESSURE_PUSH: the form the sim runs."""
     v = ctypes.c_int32()
@@ -238,6 +249,12 @@ def fs_eval_hazard(lw: _abi.fs_law, tau_dev, h_dev, stream=None) -> None:
     n = tau_dev.numel()
     check(load().fs_eval_hazard(ctypes.byref(lw), _addr(tau_dev), _addr(h_dev), n, _stream(stream)),
           "fs_eval_hazard")
+
+
+def fs_eval_density(lw: _abi.fs_law, tau_dev, f_dev, stream=None) -> None:
+    n = tau_dev.numel()
+    check(load().fs_eval_density(ctypes.byref(lw), _addr(tau_dev), _addr(f_dev), n, _stream(stream)),
+          "fs_eval_density")
 
 
 def fs_eval_uniforms(seed: int, replicate: int, step: int, nodes_dev, u_dev, stream=None) -> None:

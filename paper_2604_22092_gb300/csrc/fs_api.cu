@@ -158,8 +158,13 @@ fs_status check_params(const fs_sim_params* p)
         return fail(FS_EINVAL, "dt must be finite and > 0");
     if (p->flags < FS_PRESSURE_AUTO || p->flags > FS_PRESSURE_PUSH)
         return fail(FS_EINVAL, "flags must be FS_PRESSURE_AUTO, FS_PRESSURE_GATHER or FS_PRESSURE_PUSH");
-    if (p->reserved_ != 0)
-        return fail(FS_EINVAL, "reserved field must be 0");
+    if (p->shed_mode < FS_SHED_NONE || p->shed_mode > FS_SHED_DENSITY)
+        return fail(FS_EINVAL, "shed_mode must be FS_SHED_NONE, FS_SHED_HAZARD or FS_SHED_DENSITY");
+    if (p->shed_mode != FS_SHED_NONE) {
+        fs_status st = check_law(p->shedding, "shedding", false);
+        if (st != FS_OK)
+            return st;
+    }
     if (!finite(p->eps) || p->eps < 0 || !finite(p->delta) || p->delta < 0)
         return fail(FS_EINVAL, "eps and delta must be finite and >= 0");
     fs_status st = check_law(p->infectious, "infectious", false);
@@ -238,6 +243,11 @@ fs::StepArgs step_args(const fs_sim* s, int j)
     a.out_col = g->d_out_col;
     a.eps = (float)s->p.eps;
     a.delta = (float)(s->p.delta > 0 ? s->p.delta : 1e-12);
+    a.rho[0] = s->d_rho[0];
+    a.rho[1] = s->d_rho[1];
+    a.m_part = s->d_mpart;
+    a.shed = to_lawf(s->p.shedding);
+    a.shed_mode = s->p.shed_mode;
     a.dtrec = s->d_dtrec;
     return a;
 }
@@ -624,13 +634,17 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
     if (params->flags == FS_PRESSURE_PUSH && !push_available(g))
         return fail(FS_EUNSUPPORTED, "FS_PRESSURE_PUSH needs in-degrees <= %d in the thread class (thread_max_deg %d)",
                     fs::kMaxThreadDeg, g->t1);
-    if (params->eps > 0 && (params->flags == FS_PRESSURE_GATHER || !push_available(g)))
+    const bool shed = params->shed_mode != FS_SHED_NONE;
+    if (shed && params->flags == FS_PRESSURE_PUSH)
+        return fail(FS_EUNSUPPORTED, "a shedding profile needs the gather form of the pressure (the push form "
+                                     "keeps integer infectious counts)");
+    if (params->eps > 0 && (shed || params->flags == FS_PRESSURE_GATHER || !push_available(g)))
         return fail(FS_EUNSUPPORTED, "the adaptive step (eps > 0) runs in the push form of the pressure only");
     fs_sim* s = new fs_sim();
     s->g = g;
     s->p = *params;
-    s->pressure = (params->flags == FS_PRESSURE_GATHER || !push_available(g)) ? FS_PRESSURE_GATHER
-                                                                              : FS_PRESSURE_PUSH;
+    s->pressure = (shed || params->flags == FS_PRESSURE_GATHER || !push_available(g)) ? FS_PRESSURE_GATHER
+                                                                                      : FS_PRESSURE_PUSH;
     s->M = to_model(*params);
     s->age_bytes = params->age_dtype == FS_AGE_F32 ? 4 : 2;
     const int64_t n = g->n;
@@ -675,6 +689,12 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
     const size_t oPt = carve(sizeof(float4) * 2 * fs::kPTableN), oPs = carve(sizeof(float) * fs::kPSTableN);
     const size_t oIdx = carve(sizeof(int32_t) * (size_t)std::max<int64_t>(n_index, 1));
     const size_t oDt = carve(sizeof(float) * fs::kMaxGraphSteps);
+    size_t oR0 = 0, oR1 = 0, oMp = 0;
+    if (shed) {
+        oR0 = carve(n_pad * s->age_bytes);
+        oR1 = carve(n_pad * s->age_bytes);
+        oMp = carve(sizeof(float2) * (size_t)std::max(g->n_chunks, 1));
+    }
     size_t oC8 = 0, oP0 = 0, oP1 = 0, oHc = 0, oH0 = 0, oH1 = 0;
     if (push) {
         oC8 = carve(thr_pad);
@@ -699,6 +719,11 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
     d_idx = reinterpret_cast<int32_t*>(base + oIdx);
     if (params->eps > 0)
         s->d_dtrec = reinterpret_cast<float*>(base + oDt);
+    if (shed) {
+        s->d_rho[0] = base + oR0;
+        s->d_rho[1] = base + oR1;
+        s->d_mpart = reinterpret_cast<float2*>(base + oMp);
+    }
     if (push) {
         s->d_cnt8 = reinterpret_cast<uint8_t*>(base + oC8);
         s->d_pd16[0] = reinterpret_cast<uint16_t*>(base + oP0);
@@ -716,6 +741,8 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
         S_CUDA(fs::launch_set_index(s->d_X, d_idx, n_index, g->d_inv, params->index_state, cs));
     }
     S_CUDA(fs::launch_refresh(s->d_X, (int)n, g->d_deg, s->d_bm[0], s->d_bm[1], s->d_ctl, cs));
+    if (shed)
+        S_CUDA(fs::launch_rho_init(step_args(s, 0), params->age_dtype, 0u, cs));
     if (push) {
         S_CUDA(ensure_out_csr(g, cs));
         S_CUDA(fs::launch_push_init(step_args(s, 0), cs, g->num_sms));   // counts and tallies are zero
@@ -736,7 +763,7 @@ static cudaError_t launch_one_step(fs_sim* s, int j)
         return fs::launch_push_step_adaptive(a, s->p.age_dtype, s->stream, s->g->num_sms);
     if (s->pressure == FS_PRESSURE_PUSH)
         return fs::launch_push_step(a, s->p.age_dtype, s->stream, s->g->num_sms);
-    if (s->g->smem_path)
+    if (s->g->smem_path && !s->d_rho[0])
         return fs::launch_step_smem(a, s->p.age_dtype, s->stream, s->g->num_sms);
     return fs::launch_step(a, s->p.age_dtype, s->stream, false);
 }
@@ -998,7 +1025,52 @@ fs_status fs_sim_set_state(fs_sim* s, const uint8_t* state, const void* age, int
     FS_CUDA(s, fs::launch_refresh(s->d_X, n, g->d_deg, s->d_bm[0], s->d_bm[1], s->d_ctl, s->stream));
     if (s->pressure == FS_PRESSURE_PUSH)
         FS_CUDA(s, push_reset(s));
+    if (s->d_rho[0])
+        FS_CUDA(s, fs::launch_rho_init(step_args(s, 0), s->p.age_dtype, (uint32_t)(step & 1), s->stream));
     FS_CUDA(s, cudaStreamSynchronize(s->stream));
+    return FS_OK;
+}
+
+fs_status fs_sim_infectivity_get(fs_sim* s, void* rho)
+{
+    if (!s || !rho)
+        return fail(FS_EINVAL, "NULL argument");
+    if (s->failed)
+        return fail(FS_ESTATE, "sim is in a failed state");
+    if (!s->d_rho[0])
+        return fail(FS_EUNSUPPORTED, "fs_sim_infectivity_get: the sim has no shedding profile");
+    const int64_t n = s->g->n;
+    std::vector<uint8_t> X((size_t)std::max<int64_t>(n, 1));
+    int64_t step = 0;
+    fs_status st = fs_sim_get_state(s, X.data(), nullptr, &step);
+    if (st != FS_OK)
+        return st;
+    const fs_graph* g = s->g;
+    const int eb = s->age_bytes;
+    const void* src = s->d_rho[step & 1];
+    cudaError_t e = cudaSuccess;
+    if (g->identity) {
+        e = cudaMemcpy(rho, src, (size_t)n * eb, cudaMemcpyDeviceToHost);
+    } else {
+        void* tmp = nullptr;
+        e = cudaMalloc(&tmp, (size_t)std::max<int64_t>(n, 1) * eb);
+        if (e == cudaSuccess)
+            e = fs::launch_to_original(src, tmp, eb, g->d_perm, (int)n, s->stream);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(s->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(rho, tmp, (size_t)n * eb, cudaMemcpyDeviceToHost);
+        cudaFree(tmp);
+    }
+    if (e != cudaSuccess) {
+        s->failed = true;
+        return fail(FS_ECUDA, "fs_sim_infectivity_get: %s", cudaGetErrorString(e));
+    }
+    // entries of non-I nodes are stale in the device buffer (never read)
+    unsigned char* out = static_cast<unsigned char*>(rho);
+    for (int64_t i = 0; i < n; ++i)
+        if (X[(size_t)i] != FS_I)
+            memset(out + (size_t)i * eb, 0, (size_t)eb);
     return FS_OK;
 }
 
@@ -1079,6 +1151,19 @@ fs_status fs_eval_hazard(const fs_law* law, const float* tau_dev, float* h_dev, 
     cudaError_t e = fs::launch_eval_hazard(to_lawf(*law), tau_dev, h_dev, n, (cudaStream_t)stream);
     if (e != cudaSuccess)
         return fail(FS_ECUDA, "fs_eval_hazard: %s", cudaGetErrorString(e));
+    return FS_OK;
+}
+
+fs_status fs_eval_density(const fs_law* law, const float* tau_dev, float* f_dev, int64_t n, void* stream)
+{
+    if (!law || n < 0 || (n > 0 && (!tau_dev || !f_dev)))
+        return fail(FS_EINVAL, "bad argument");
+    fs_status st = check_law(*law, "eval", false);
+    if (st != FS_OK)
+        return st;
+    cudaError_t e = fs::launch_eval_density(to_lawf(*law), tau_dev, f_dev, n, (cudaStream_t)stream);
+    if (e != cudaSuccess)
+        return fail(FS_ECUDA, "fs_eval_density: %s", cudaGetErrorString(e));
     return FS_OK;
 }
 
@@ -1181,6 +1266,8 @@ extern "C" fs_status fs_step_noalloc(const fs_graph* g, const fs_sim_params* par
         return st;
     if (pv.eps > 0)
         return fail(FS_EUNSUPPORTED, "fs_step_noalloc: one step has a fixed size (eps must be 0)");
+    if (pv.shed_mode != FS_SHED_NONE)
+        return fail(FS_EUNSUPPORTED, "fs_step_noalloc: a shedding profile needs the sim's infectivity buffers");
     if (step < 0 || step >= ((int64_t)1 << 32))
         return fail(FS_EINVAL, "fs_step_noalloc: step must be in [0, 2^32)");
     if (g->n_m > kNoAllocMaxMergeRows)

@@ -68,10 +68,9 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-__device__ __forceinline__ float hazard_lognormal(const LawF& L, float tau)
+// z = (ln tau - mu) / (sigma sqrt 2) as an unevaluated pair zh + zl (tau > 0)
+__device__ __forceinline__ void lognormal_z(const LawF& L, float tau, float& zh, float& zl)
 {
-    if (!(tau > 0.0f))
-        return 0.0f;
     constexpr float kLn2Hi = 0.693145751953125f;          // ln 2 to 16 bits (e * kLn2Hi is exact)
     constexpr float kLn2Lo = 1.4286067653302226e-06f;     // ln 2 - kLn2Hi
     int e;
@@ -90,12 +89,26 @@ __device__ __forceinline__ float hazard_lognormal(const LawF& L, float tau)
     const float z_hi = __fmul_rn(d_hi, L.p1);
     const float z_lo = __fadd_rn(__fmaf_rn(d_hi, L.p1, -z_hi),
                                  __fadd_rn(__fmul_rn(d_hi, L.p4), __fmul_rn(d_lo, L.p1)));
-    const float zh = __fadd_rn(z_hi, z_lo);
-    const float zl = __fsub_rn(z_lo, __fsub_rn(zh, z_hi));
+    zh = __fadd_rn(z_hi, z_lo);
+    zl = __fsub_rn(z_lo, __fsub_rn(zh, z_hi));
+}
+
+// e^{-z^2} for z = zh + zl, with z^2 split exactly
+__device__ __forceinline__ float exp_neg_z2(float zh, float zl)
+{
+    const float s_hi = __fmul_rn(zh, zh);
+    const float s_lo = __fadd_rn(__fmaf_rn(zh, zh, -s_hi), __fmul_rn(__fmul_rn(2.0f, zh), zl));
+    return __fmul_rn(expf(-s_hi), __fsub_rn(1.0f, s_lo));
+}
+
+__device__ __forceinline__ float hazard_lognormal(const LawF& L, float tau)
+{
+    if (!(tau > 0.0f))
+        return 0.0f;
+    float zh, zl;
+    lognormal_z(L, tau, zh, zl);
     if (zh < -2.0f) {
-        const float s_hi = __fmul_rn(zh, zh);
-        const float s_lo = __fadd_rn(__fmaf_rn(zh, zh, -s_hi), __fmul_rn(__fmul_rn(2.0f, zh), zl));
-        const float ez = __fmul_rn(expf(-s_hi), __fsub_rn(1.0f, s_lo));   // e^{-z^2}
+        const float ez = exp_neg_z2(zh, zl);
         const float erfc_z = __fsub_rn(2.0f, erfcf(-zh));
         return __fdiv_rn(__fmul_rn(L.p2, ez), __fmul_rn(tau, erfc_z));
     }
@@ -130,6 +143,45 @@ __device__ __forceinline__ float hazard(const LawF& L, float tau)
         for (int m = 1; m < L.k; ++m)
             s = __fadd_rn(1.0f, __fmul_rn(__fmul_rn((float)m, y), s));
         return __fdiv_rn(r, s);
+    }
+    default:
+        return 0.0f;
+    }
+}
+
+// Probability densities in FP32 (shedding profiles, Section 5.3), from the
+// textbook definitions:
+//   EXP        f = r e^{-r tau}
+//   LOGNORMAL  f = e^{-z^2} / (tau sigma sqrt(2 pi)), z as in the hazard
+//              (1 / (sigma sqrt(2 pi)) = p2 / 2)
+//   WEIBULL    f = (k/s) x^(k-1) e^{-x^k}, x = tau / s
+//   ERLANG     f = r (r tau)^(k-1) / (k-1)! e^{-r tau}
+__device__ __forceinline__ float density(const LawF& L, float tau)
+{
+    if (!(tau >= 0.0f))
+        return 0.0f;
+    switch (L.kind) {
+    case kLawExp:
+        return __fmul_rn(L.p0, expf(-__fmul_rn(L.p0, tau)));
+    case kLawLogNormal: {
+        if (!(tau > 0.0f))
+            return 0.0f;
+        float zh, zl;
+        lognormal_z(L, tau, zh, zl);
+        return __fdiv_rn(__fmul_rn(__fmul_rn(0.5f, L.p2), exp_neg_z2(zh, zl)), tau);
+    }
+    case kLawWeibull: {
+        const float x = __fmul_rn(tau, L.p1);
+        const float xk1 = powf(x, L.p2);                   // x^(k-1); powf(0, 0) = 1
+        return __fmul_rn(__fmul_rn(L.p0, xk1), expf(-__fmul_rn(xk1, x)));
+    }
+    case kLawErlang: {
+        const float r = L.p0;
+        const float x = __fmul_rn(r, tau);
+        float t = 1.0f;
+        for (int n = 1; n < L.k; ++n)
+            t = __fmul_rn(t, __fdiv_rn(x, (float)n));
+        return __fmul_rn(__fmul_rn(r, t), expf(-x));
     }
     default:
         return 0.0f;

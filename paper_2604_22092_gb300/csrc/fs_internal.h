@@ -132,7 +132,19 @@ struct StepArgs {
     // sequence is recorded in dtrec[j] for the epilogue's clock
     float eps, delta;
     float* dtrec;                 // [kMaxGraphSteps]
+    // source-node infectivity with a shedding profile (Eq. 8; gather kernels'
+    // SHED instances): rho[k & 1][i] = beta s(tau_i) of the nodes that are I
+    // at step k, in the storage type of the ages; entries of other nodes are
+    // stale and never read (the bitmap gates every read)
+    void* rho[2];
+    float2* m_part;               // [n_chunks] cross-chunk partial pressures: .x of the row that
+                                  // enters the chunk from the previous one, .y of the row that
+                                  // continues into the next one
+    LawF shed;                    // the law of s(tau)
+    int32_t shed_mode;            // FS_SHED_HAZARD (1) or FS_SHED_DENSITY (2); 0 = s = 1
 };
+
+enum { kShedNone = 0, kShedHazard = 1, kShedDensity = 2 };
 
 constexpr int kPushG = 8;                 // thread-class nodes per thread of the push step
 constexpr int kPushThreads = 256;

@@ -34,6 +34,9 @@ cudaError_t launch_to_original(const void* in, void* out, int elem_bytes, const 
 cudaError_t launch_from_original(const void* in, void* out, int elem_bytes, const int32_t* inv, int n,
                                  cudaStream_t s);
 cudaError_t launch_eval_hazard(const LawF& L, const float* tau, float* h, int64_t n, cudaStream_t s);
+cudaError_t launch_eval_density(const LawF& L, const float* tau, float* f, int64_t n, cudaStream_t s);
+// rho[par] of every I node from its age (a.X, a.A, a.rho, a.M.beta, a.shed*)
+cudaError_t launch_rho_init(const StepArgs& a, int age_dtype, uint32_t par, cudaStream_t s);
 cudaError_t launch_eval_uniforms(uint32_t key0, uint32_t key1, uint32_t rep, uint32_t step, const int32_t* nodes,
                                  float* u, int64_t n, cudaStream_t s);
 

@@ -57,6 +57,10 @@ struct fs_sim {
     float* d_ps = nullptr;
     // adaptive step (p.eps > 0): the step sizes of the current launch sequence
     float* d_dtrec = nullptr;
+    // shedding profile (p.shed_mode != 0): infectivity by step parity, and
+    // the merge class's cross-chunk partial pressures
+    void* d_rho[2] = {nullptr, nullptr};
+    float2* d_mpart = nullptr;
     // push form of the pressure (pressure == FS_PRESSURE_PUSH)
     int pressure = FS_PRESSURE_GATHER;
     uint8_t* d_cnt8 = nullptr;

@@ -202,8 +202,13 @@ fs_status fs_ens_create(fs_graph* g, const fs_sim_params* params, int32_t n_real
             params[r].index_state != params[0].index_state || params[r].flags != params[0].flags)
             return fail(FS_EINVAL, "fs_ens_create: realisations must share model, age_dtype, index_state and flags");
     }
-    if (params[0].eps > 0)
-        return fail(FS_EUNSUPPORTED, "fs_ens_create: packed ensembles run a fixed step (eps must be 0)");
+    for (int r = 0; r < n_real; ++r) {
+        if (params[r].eps > 0)
+            return fail(FS_EUNSUPPORTED, "fs_ens_create: packed ensembles run a fixed step (eps must be 0)");
+        if (params[r].shed_mode != FS_SHED_NONE)
+            return fail(FS_EUNSUPPORTED,
+                        "fs_ens_create: packed ensembles keep s = 1 (shed_mode must be FS_SHED_NONE)");
+    }
     if (params[0].flags == FS_PRESSURE_PUSH && !fsapi::push_available(g))
         return fail(FS_EUNSUPPORTED, "fs_ens_create: FS_PRESSURE_PUSH needs in-degrees <= %d in the thread class",
                     fs::kMaxThreadDeg);

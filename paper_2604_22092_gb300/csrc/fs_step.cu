@@ -78,12 +78,18 @@ __device__ __forceinline__ float node_p(const StepArgs& a, int x, float age, uin
     return 0.0f;
 }
 
-// Bernoulli decision and transition for one node (Algorithm 3); the original
-// id is looked up only when a uniform is needed (p > 0)
-__device__ __forceinline__ TailResult tail_at(const StepArgs& a, int x, float age, uint32_t c, int i,
-                                              uint32_t step)
+// beta s(tau) of an I node of age tau (Eq. 8), FP32; out of line (I nodes
+// only, and only in the SHED instances)
+__device__ __noinline__ float shed_rho(const StepArgs& a, float tau)
 {
-    const float p = node_p(a, x, age, c);
+    const float s = a.shed_mode == kShedHazard ? hazard(a.shed, tau) : density(a.shed, tau);
+    return __fmul_rn(a.M.beta, s);
+}
+
+// Bernoulli decision and transition for one node of probability p
+// (Algorithm 3); the original id is looked up only when a uniform is needed
+__device__ __forceinline__ TailResult tail_p(const StepArgs& a, int x, float age, float p, int i, uint32_t step)
+{
     bool fired = false;
     if (p > 0.0f)
         fired = uniform24(a.M.key0, a.M.key1, a.M.rep, step, orig_id(a.perm, i)) < p;
@@ -97,6 +103,12 @@ __device__ __forceinline__ TailResult tail_at(const StepArgs& a, int x, float ag
     }
     r.fired = fired;
     return r;
+}
+
+__device__ __forceinline__ TailResult tail_at(const StepArgs& a, int x, float age, uint32_t c, int i,
+                                              uint32_t step)
+{
+    return tail_p(a, x, age, node_p(a, x, age, c), i, step);
 }
 
 // warp-level delta accumulation into the CTA's shared counters
@@ -124,7 +136,7 @@ struct LaneDeltas {
     uint32_t fS = 0, fE = 0, fI = 0, dS = 0;
 };
 
-template <typename AgeT, bool SMEM_BM>
+template <typename AgeT, bool SMEM_BM, bool SHED = false>
 __device__ __forceinline__ void sell_slice(const StepArgs& a, uint32_t step, const uint32_t* __restrict__ bm,
                                            uint32_t* __restrict__ bmn, int slice, int x, LaneDeltas& ld,
                                            uint32_t mbar = 0u, bool* ready = nullptr)
@@ -138,6 +150,7 @@ __device__ __forceinline__ void sell_slice(const StepArgs& a, uint32_t step, con
     if (x == kE || x == kI)
         age = AgeIO<AgeT>::load(A[i]);
     uint32_t c = 0;
+    float rs = 0.0f;                             // SHED: FP32 sum of the stored rho, row order
     if (x == kS) {
         // padding entries hold the sentinel id n, whose bitmap bit is always
         // 0, so every gathered bit is added without a test
@@ -166,16 +179,31 @@ __device__ __forceinline__ void sell_slice(const StepArgs& a, uint32_t step, con
                     word = bm[jj[u] >> 5];
                 else
                     word = __ldg(bm + (jj[u] >> 5));
-                c += __funnelshift_r(word, 0u, (uint32_t)jj[u]) & 1u;   // bit jj mod 32
+                const uint32_t bit = __funnelshift_r(word, 0u, (uint32_t)jj[u]) & 1u;   // bit jj mod 32
+                if constexpr (SHED) {
+                    if (bit)
+                        rs = __fadd_rn(rs, AgeIO<AgeT>::load(static_cast<const AgeT*>(a.rho[step & 1u])[jj[u]]));
+                } else {
+                    c += bit;
+                }
             }
         }
     }
-    const TailResult r = tail_at(a, x, age, c, i, step);
+    TailResult r;
+    if constexpr (SHED)
+        r = tail_p(a, x, age, x == kS ? p_of_rate(a.M, rs) : node_p(a, x, age, 0u), i, step);
+    else
+        r = tail_at(a, x, age, c, i, step);
     if (valid) {
         if (r.x != x)
             a.X[i] = (uint8_t)r.x;
         if (r.fired || x == kE || x == kI)
             A[i] = AgeIO<AgeT>::store(r.age);
+        if constexpr (SHED) {
+            if (r.x == kI)   // the next step's infectivity, from the new age as stored
+                static_cast<AgeT*>(a.rho[(step & 1u) ^ 1u])[i] =
+                    AgeIO<AgeT>::store(shed_rho(a, AgeIO<AgeT>::load(AgeIO<AgeT>::store(r.age))));
+        }
     }
     const uint32_t word = __ballot_sync(kFull, valid && r.x == kI);
     if ((slice + 1) * 32 <= a.n_thr) {
@@ -199,7 +227,7 @@ __device__ __forceinline__ void sell_slice(const StepArgs& a, uint32_t step, con
     }
 }
 
-template <typename AgeT>
+template <typename AgeT, bool SHED>
 __device__ __forceinline__ void sell_warp(const StepArgs& a, uint32_t step, const uint32_t* __restrict__ bm,
                                           uint32_t* __restrict__ bmn, int s_begin, int s_end, LaneDeltas& ld)
 {
@@ -224,7 +252,7 @@ __device__ __forceinline__ void sell_warp(const StepArgs& a, uint32_t step, cons
                     bmn[slice] = 0u;
                 continue;
             }
-            sell_slice<AgeT, false>(a, step, bm, bmn, slice, x, ld);
+            sell_slice<AgeT, false, SHED>(a, step, bm, bmn, slice, x, ld);
         }
     }
 }
@@ -241,11 +269,20 @@ struct MergeSmem {
     unsigned long long mbar;
 };
 
-template <typename AgeT>
+// SHED: per-warp partial pressures of the rows of its 32 lanes, and the
+// first row of each warp's range (INT32_MAX: the warp has no edges)
+template <bool SHED> struct MergeShedSmem {
+    float part[kStepWarps][kWarp];
+    int32_t wrow[kStepWarps];
+};
+template <> struct MergeShedSmem<false> {};
+
+template <typename AgeT, bool SHED>
 __device__ __forceinline__ void merge_chunk(const StepArgs& a, uint32_t step, const uint32_t* __restrict__ bm,
                                             uint32_t* __restrict__ bmn, int chunk, unsigned long long* s_delta)
 {
     __shared__ __align__(128) MergeSmem sm;
+    __shared__ MergeShedSmem<SHED> sh;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t e0 = (int64_t)chunk * kMergeEPB;
     const int64_t e1 = min(e0 + (int64_t)kMergeEPB, a.e_m);
@@ -289,6 +326,11 @@ __device__ __forceinline__ void merge_chunk(const StepArgs& a, uint32_t step, co
             ok = mbar_wait(mbar, 0u, kWaitLimit);   // let an in-flight copy land before leaving
         }
         const int64_t s0 = e0 + (int64_t)warp * kMergeEdgesPerWarp;
+        if constexpr (SHED) {
+            sh.part[warp][lane] = 0.0f;
+            if (lane == 0)
+                sh.wrow[warp] = INT32_MAX;
+        }
         if (ok && s0 < e1) {
             const int64_t s1 = min(s0 + (int64_t)kMergeEdgesPerWarp, e1);
             const int rw = __ldg(a.m_warp_row + (int64_t)chunk * kStepWarps + warp);
@@ -301,6 +343,46 @@ __device__ __forceinline__ void merge_chunk(const StepArgs& a, uint32_t step, co
                 isS = sm.xs[r - R0] == kS;
             }
             const int32_t* cb = sm.col + (s0 - e0);
+            if constexpr (SHED) {
+                // each 32-edge window: lanes load the stored rho of their
+                // edge's column if it is infectious and its row is S; a
+                // segmented inclusive scan (fixed tree order) sums each row's
+                // run of lanes; the row's lane adds the run's total, window
+                // by window
+                const AgeT* __restrict__ rho = static_cast<const AgeT*>(a.rho[step & 1u]);
+                if (lane == 0)
+                    sh.wrow[warp] = rw;
+                float acc = 0.0f;
+#pragma unroll 4
+                for (int m = 0; m < kMergeWindowsPerWarp; ++m) {
+                    const int64_t base = s0 + 32 * m;
+                    const int l0 = (int)max((int64_t)0, min((int64_t)32, lo - base));
+                    const int h0 = (int)max((int64_t)0, min((int64_t)32, hi - base));
+                    uint32_t rm = 0u;
+                    if (h0 > l0)
+                        rm = ((h0 == 32) ? kFull : ((1u << h0) - 1u)) & ~((1u << l0) - 1u);
+                    const uint32_t act = __reduce_or_sync(kFull, isS ? rm : 0u);
+                    const uint32_t heads = __reduce_or_sync(kFull, h0 > l0 ? (1u << l0) : 0u);
+                    float v = 0.0f;
+                    if ((act >> lane) & 1u) {
+                        const int32_t col = cb[32 * m + lane];
+                        if ((__ldg(bm + (col >> 5)) >> (col & 31)) & 1u)
+                            v = AgeIO<AgeT>::load(rho[col]);
+                    }
+                    const uint32_t below = heads & ((lane == 31) ? kFull : ((2u << lane) - 1u));
+                    const int head = below ? 31 - __clz(below) : 0;
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const float t = __shfl_up_sync(kFull, v, d);
+                        if (lane - d >= head)
+                            v = __fadd_rn(v, t);
+                    }
+                    const float seg = __shfl_sync(kFull, v, h0 > l0 ? h0 - 1 : 0);
+                    if (isS && h0 > l0)
+                        acc = __fadd_rn(acc, seg);
+                }
+                sh.part[warp][lane] = acc;
+            } else {
             uint32_t cnt = 0;
 #pragma unroll
             for (int m = 0; m < kMergeWindowsPerWarp; ++m) {
@@ -320,6 +402,7 @@ __device__ __forceinline__ void merge_chunk(const StepArgs& a, uint32_t step, co
             }
             if (r <= R1 && isS && lo < hi && cnt)
                 atomicAdd(&sm.cnt[r - R0], cnt);
+            }
         }
     }
     __syncthreads();
@@ -332,7 +415,38 @@ __device__ __forceinline__ void merge_chunk(const StepArgs& a, uint32_t step, co
         const int x = sm.xs[tid];
         bool do_tail = false;
         uint32_t count = 0;
-        if (x == kS) {
+        float lam = 0.0f;                   // SHED: the row's pressure
+        if (x == kS && SHED) {
+            if constexpr (SHED) {
+                // this chunk's partial: the warps' partials in warp order
+                float part = 0.0f;
+                for (int w = 0; w < kStepWarps; ++w) {
+                    const int d = r - sh.wrow[w];
+                    if (d >= 0 && d < kWarp)
+                        part = __fadd_rn(part, sh.part[w][d]);
+                }
+                if (rlo >= e0 && rhi <= e1) {
+                    do_tail = true;
+                    lam = part;
+                } else {
+                    // chunk partials land in per-chunk slots; the last chunk
+                    // to arrive folds them in chunk order
+                    const int64_t cf = rlo / kMergeEPB, cl = (rhi - 1) / kMergeEPB;
+                    __stcg(reinterpret_cast<float*>(a.m_part + chunk) + (rlo < e0 ? 0 : 1), part);
+                    __threadfence();
+                    const uint32_t tk = atomicAdd(a.m_tkt + r, 1u);
+                    if (tk == (uint32_t)(cl - cf)) {
+                        __threadfence();
+                        float tot = __ldcg(reinterpret_cast<const float*>(a.m_part + cf) + 1);
+                        for (int64_t c = cf + 1; c <= cl; ++c)
+                            tot = __fadd_rn(tot, __ldcg(reinterpret_cast<const float*>(a.m_part + c)));
+                        atomicExch(a.m_tkt + r, 0u);
+                        do_tail = true;
+                        lam = tot;
+                    }
+                }
+            }
+        } else if (x == kS) {
             if (rlo >= e0 && rhi <= e1) {
                 do_tail = true;
                 count = sm.cnt[tid];
@@ -358,11 +472,20 @@ __device__ __forceinline__ void merge_chunk(const StepArgs& a, uint32_t step, co
             float age = 0.0f;
             if (x == kE || x == kI)
                 age = AgeIO<AgeT>::load(A[gi]);
-            const TailResult t = tail_at(a, x, age, count, gi, step);
+            TailResult t;
+            if constexpr (SHED)
+                t = tail_p(a, x, age, x == kS ? p_of_rate(a.M, lam) : node_p(a, x, age, 0u), gi, step);
+            else
+                t = tail_at(a, x, age, count, gi, step);
             if (t.x != x)
                 a.X[gi] = (uint8_t)t.x;
             if (t.fired || x == kE || x == kI)
                 A[gi] = AgeIO<AgeT>::store(t.age);
+            if constexpr (SHED) {
+                if (t.x == kI)
+                    static_cast<AgeT*>(a.rho[(step & 1u) ^ 1u])[gi] =
+                        AgeIO<AgeT>::store(shed_rho(a, AgeIO<AgeT>::load(AgeIO<AgeT>::store(t.age))));
+            }
             const int wofs = (gi >> 5) - ((a.m_base + R0) >> 5);
             const uint32_t bit = 1u << (gi & 31);
             if (t.x == kI)
@@ -386,7 +509,7 @@ __device__ __forceinline__ void merge_chunk(const StepArgs& a, uint32_t step, co
     }
 }
 
-template <typename AgeT, bool HAS_MERGE>
+template <typename AgeT, bool HAS_MERGE, bool SHED>
 __global__ void __launch_bounds__(kStepThreads, kStepCtasPerSm) fused_step_kernel(const __grid_constant__ StepArgs a)
 {
     // Programmatic dependent launch: this grid may start while the previous
@@ -409,13 +532,13 @@ __global__ void __launch_bounds__(kStepThreads, kStepCtasPerSm) fused_step_kerne
         merge_cta = (int)blockIdx.x < a.n_chunks;
     if (merge_cta) {
         if constexpr (HAS_MERGE)
-            merge_chunk<AgeT>(a, (uint32_t)k, bm, bmn, (int)blockIdx.x, s_delta);
+            merge_chunk<AgeT, SHED>(a, (uint32_t)k, bm, bmn, (int)blockIdx.x, s_delta);
     } else {
         const int cta = (int)blockIdx.x - (HAS_MERGE ? a.n_chunks : 0);
         const int s_begin = (cta * kStepWarps + (int)(threadIdx.x >> 5)) * a.spw;
         const int s_end = min(s_begin + a.spw, a.n_slices);
         if (s_begin < s_end)
-            sell_warp<AgeT>(a, (uint32_t)k, bm, bmn, s_begin, s_end, ld);
+            sell_warp<AgeT, SHED>(a, (uint32_t)k, bm, bmn, s_begin, s_end, ld);
         const uint32_t fs_ = __reduce_add_sync(kFull, ld.fS), fe = __reduce_add_sync(kFull, ld.fE);
         const uint32_t fi = __reduce_add_sync(kFull, ld.fI), ds = __reduce_add_sync(kFull, ld.dS);
         if ((threadIdx.x & 31) == 0) {
@@ -688,6 +811,24 @@ __global__ void from_original_kernel(const T* __restrict__ in, T* __restrict__ o
         out[inv[o]] = in[o];
 }
 
+// infectivity of the I nodes at the current step (after init or set_state)
+template <typename AgeT>
+__global__ void rho_init_kernel(const __grid_constant__ StepArgs a, uint32_t par)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.n && a.X[i] == kI) {
+        const float age = AgeIO<AgeT>::load(static_cast<const AgeT*>(a.A)[i]);
+        static_cast<AgeT*>(a.rho[par])[i] = AgeIO<AgeT>::store(shed_rho(a, age));
+    }
+}
+
+__global__ void eval_density_kernel(LawF L, const float* tau, float* f, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n)
+        f[i] = density(L, tau[i]);
+}
+
 __global__ void eval_hazard_kernel(LawF L, const float* tau, float* h, int64_t n)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -722,10 +863,13 @@ static cudaError_t launch_step_t(const StepArgs& a, cudaStream_t s, bool pdl)
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
     cudaError_t e;
+    const bool shed = a.shed_mode != kShedNone;
     if (a.n_chunks > 0)
-        e = cudaLaunchKernelEx(&cfg, fused_step_kernel<AgeT, true>, a);
+        e = shed ? cudaLaunchKernelEx(&cfg, fused_step_kernel<AgeT, true, true>, a)
+                 : cudaLaunchKernelEx(&cfg, fused_step_kernel<AgeT, true, false>, a);
     else
-        e = cudaLaunchKernelEx(&cfg, fused_step_kernel<AgeT, false>, a);
+        e = shed ? cudaLaunchKernelEx(&cfg, fused_step_kernel<AgeT, false, true>, a)
+                 : cudaLaunchKernelEx(&cfg, fused_step_kernel<AgeT, false, false>, a);
     g_launch_count += 1;
     return e;
 }
@@ -837,6 +981,30 @@ cudaError_t launch_from_original(const void* in, void* out, int elem_bytes, cons
         from_original_kernel<uint16_t><<<blocks, 256, 0, s>>>((const uint16_t*)in, (uint16_t*)out, inv, n);
     else
         from_original_kernel<uint32_t><<<blocks, 256, 0, s>>>((const uint32_t*)in, (uint32_t*)out, inv, n);
+    g_launch_count += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rho_init(const StepArgs& a, int age_dtype, uint32_t par, cudaStream_t s)
+{
+    if (a.n == 0)
+        return cudaSuccess;
+    const int blocks = (a.n + 255) / 256;
+    switch (age_dtype) {
+    case kAgeF16: rho_init_kernel<__half><<<blocks, 256, 0, s>>>(a, par); break;
+    case kAgeBF16: rho_init_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(a, par); break;
+    default: rho_init_kernel<float><<<blocks, 256, 0, s>>>(a, par); break;
+    }
+    g_launch_count += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eval_density(const LawF& L, const float* tau, float* f, int64_t n, cudaStream_t s)
+{
+    if (n == 0)
+        return cudaSuccess;
+    const int64_t blocks = (n + 255) / 256;
+    eval_density_kernel<<<(unsigned)blocks, 256, 0, s>>>(L, tau, f, n);
     g_launch_count += 1;
     return cudaGetLastError();
 }

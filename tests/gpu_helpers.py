@@ -30,7 +30,7 @@ def oracle_params(om, p) -> object:
     def lw(L):
         return om.Law(L.kind, L.k, L.a, L.b)
     return om.Params(p.model, p.age_dtype, lw(p.latent), lw(p.infectious), p.beta, p.dt, p.seed,
-                     p.replicate, 0)
+                     p.replicate, p.shed_mode, lw(p.shedding))
 
 
 class LockstepReport:
