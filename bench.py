@@ -807,7 +807,10 @@ def shedding_bench(fs, torch, n: int, sim_steps: int, graph_steps: int, reps: in
     paper's shedding-overhead table measures it: N = 10^6, mean degree 8, a
     regular and a Barabasi-Albert (m = 4) graph, the same SEIR model with
     constant beta and with beta s(tau), s = the infectious hazard h_IR (and,
-    as a second profile, a log-normal shedding density). Each variant: event-
+    as a second profile, a log-normal shedding density). A profile changes
+    the epidemic and so the work (S node-steps and S-row edges gathered are
+    reported beside each time); shed_constant_exact isolates the cost of the
+    machinery on the constant-beta trajectory. Each variant: event-
     timed CUDA Graph replays of a full run (ingest and init untimed), median
     of `reps`, L2 flushed before each run."""
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -818,6 +821,10 @@ def shedding_bench(fs, torch, n: int, sim_steps: int, graph_steps: int, reps: in
     variants = [
         ("constant_gather", dict(pressure=fs.FS_PRESSURE_GATHER)),
         ("constant_push", dict(pressure=fs.FS_PRESSURE_PUSH)),
+        # s = the hazard of Exp(2) = 2 with beta / 2: rho = beta exactly, so the
+        # trajectory (and the work) is constant_gather's, bit for bit; the
+        # difference is the cost of the infectivity machinery alone
+        ("shed_constant_exact", dict(shed_mode=fs.FS_SHED_HAZARD, shedding=fs.law("exp", 2.0))),
         ("shed_hazard_IR", dict(shed_mode=fs.FS_SHED_HAZARD, shedding=inf)),
         ("shed_density_lognormal", dict(shed_mode=fs.FS_SHED_DENSITY, shedding=fs.law("lognormal", math.log(5.0), 0.5))),
     ]
@@ -831,7 +838,8 @@ def shedding_bench(fs, torch, n: int, sim_steps: int, graph_steps: int, reps: in
         gh = fs.fs_graph_create(g.n, g.row_ptr, g.col_ind)
         row = {}
         for label, kw in variants:
-            prm = fs.sim_params(fs.FS_SEIR, inf, 0.25, 0.1, 3, latent=lat, **kw)
+            beta = 0.125 if label == "shed_constant_exact" else 0.25
+            prm = fs.sim_params(fs.FS_SEIR, inf, beta, 0.1, 3, latent=lat, **kw)
             times = []
             for r in range(reps + 1):
                 flush.fill_(1.0)
@@ -839,14 +847,16 @@ def shedding_bench(fs, torch, n: int, sim_steps: int, graph_steps: int, reps: in
                 sh = fs.fs_sim_init(gh, prm, idx)
                 ms = fs.fs_sim_run_timed(sh, sim_steps, K, None)
                 c = fs.fs_sim_run(sh, 0)
+                work = fs.fs_sim_work(sh)
                 fs.fs_sim_destroy(sh)
                 if r:
                     times.append(float(np.sum(ms[:full])))
             t = float(np.median(times))
             row[label] = {"value": round(g.n * full * K / (t * 1e-3) / 1e9, 3), "unit": UNIT,
-                          "ms_per_run": round(t, 3), "final_R": int(c[-1, 3])}
+                          "ms_per_run": round(t, 3), "final_R": int(c[-1, 3]),
+                          "s_node_steps": int(work["s_node_sum"]), "s_row_edges": int(work["s_degree_sum"])}
         base = row["constant_gather"]["value"]
-        for label in ("shed_hazard_IR", "shed_density_lognormal"):
+        for label in ("shed_constant_exact", "shed_hazard_IR", "shed_density_lognormal"):
             row[label]["slowdown_vs_constant_gather_pct"] = round((base / row[label]["value"] - 1) * 100, 2)
         res["graphs"][gname] = row
         fs.fs_graph_destroy(gh)

@@ -248,6 +248,7 @@ fs::StepArgs step_args(const fs_sim* s, int j)
     a.m_part = s->d_mpart;
     a.shed = to_lawf(s->p.shedding);
     a.shed_mode = s->p.shed_mode;
+    a.rtab = s->d_rtab;
     a.dtrec = s->d_dtrec;
     return a;
 }
@@ -689,11 +690,12 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
     const size_t oPt = carve(sizeof(float4) * 2 * fs::kPTableN), oPs = carve(sizeof(float) * fs::kPSTableN);
     const size_t oIdx = carve(sizeof(int32_t) * (size_t)std::max<int64_t>(n_index, 1));
     const size_t oDt = carve(sizeof(float) * fs::kMaxGraphSteps);
-    size_t oR0 = 0, oR1 = 0, oMp = 0;
+    size_t oR0 = 0, oR1 = 0, oMp = 0, oRt = 0;
     if (shed) {
         oR0 = carve(n_pad * s->age_bytes);
         oR1 = carve(n_pad * s->age_bytes);
         oMp = carve(sizeof(float2) * (size_t)std::max(g->n_chunks, 1));
+        oRt = carve(sizeof(float4) * fs::kPTableN);
     }
     size_t oC8 = 0, oP0 = 0, oP1 = 0, oHc = 0, oH0 = 0, oH1 = 0;
     if (push) {
@@ -723,6 +725,7 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
         s->d_rho[0] = base + oR0;
         s->d_rho[1] = base + oR1;
         s->d_mpart = reinterpret_cast<float2*>(base + oMp);
+        s->d_rtab = reinterpret_cast<float4*>(base + oRt);
     }
     if (push) {
         s->d_cnt8 = reinterpret_cast<uint8_t*>(base + oC8);
@@ -735,7 +738,10 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
     // all S, ages 0, bitmaps / scratch / control / deltas / counts / tallies 0
     S_CUDA(cudaMemsetAsync(s->d_arena, 0, arena, cs));
     S_CUDA(cudaMemsetAsync(s->d_ptab, 0xff, sizeof(float4) * 2 * fs::kPTableN, cs));   // NaN ages: no entry
-    S_CUDA(fs::launch_build_ptables(s->M, params->age_dtype, s->d_ptab, s->d_ps, cs));
+    if (shed)
+        S_CUDA(cudaMemsetAsync(s->d_rtab, 0xff, sizeof(float4) * fs::kPTableN, cs));
+    S_CUDA(fs::launch_build_ptables(s->M, params->age_dtype, s->d_ptab, s->d_ps, cs, s->d_rtab,
+                                    to_lawf(params->shedding), params->shed_mode));
     if (n_index > 0) {
         S_CUDA(cudaMemcpyAsync(d_idx, index_nodes, sizeof(int32_t) * n_index, cudaMemcpyHostToDevice, cs));
         S_CUDA(fs::launch_set_index(s->d_X, d_idx, n_index, g->d_inv, params->index_state, cs));
@@ -763,7 +769,7 @@ static cudaError_t launch_one_step(fs_sim* s, int j)
         return fs::launch_push_step_adaptive(a, s->p.age_dtype, s->stream, s->g->num_sms);
     if (s->pressure == FS_PRESSURE_PUSH)
         return fs::launch_push_step(a, s->p.age_dtype, s->stream, s->g->num_sms);
-    if (s->g->smem_path && !s->d_rho[0])
+    if (s->g->smem_path)
         return fs::launch_step_smem(a, s->p.age_dtype, s->stream, s->g->num_sms);
     return fs::launch_step(a, s->p.age_dtype, s->stream, false);
 }

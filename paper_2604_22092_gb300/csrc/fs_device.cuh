@@ -225,6 +225,14 @@ __device__ __forceinline__ float age_step_stored(float age, float dt, int age_dt
 // Memoised probability of an E/I node of age `age` from its law's two-slot
 // table row (age0, p0, age1, p1): slot 0 is read as 8 bytes and slot 1 only
 // when slot 0 holds another age; returns -1 when neither holds `age`.
+// beta s(tau) of the source-node infectivity (Eq. 8): s = the hazard
+// (mode 1) or the density (mode 2) of the shedding law
+__device__ __forceinline__ float shed_value(const LawF& L, int mode, float beta, float tau)
+{
+    const float s = mode == 1 ? hazard(L, tau) : density(L, tau);
+    return __fmul_rn(beta, s);
+}
+
 __device__ __forceinline__ float ptab_slot1(const float4* row, float age)
 {
     const float2 e1 = __ldg(reinterpret_cast<const float2*>(row) + 1);

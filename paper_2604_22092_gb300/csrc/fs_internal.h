@@ -142,6 +142,8 @@ struct StepArgs {
                                   // continues into the next one
     LawF shed;                    // the law of s(tau)
     int32_t shed_mode;            // FS_SHED_HAZARD (1) or FS_SHED_DENSITY (2); 0 = s = 1
+    const float4* rtab;           // [kPTableN] memoised beta s(age) over the fixed-step age
+                                  // sequence, two (age, value) slots per index like ptab
 };
 
 enum { kShedNone = 0, kShedHazard = 1, kShedDensity = 2 };

@@ -19,7 +19,9 @@ extern std::atomic<unsigned long long> g_launch_count;
 cudaError_t launch_step(const StepArgs& a, int age_dtype, cudaStream_t s, bool pdl);
 // one step as the shared-memory-bitmap SELL grid plus, if present, the merge grid
 cudaError_t launch_step_smem(const StepArgs& a, int age_dtype, cudaStream_t s, int num_sms);
-cudaError_t launch_build_ptables(const ModelF& M, int age_dtype, float4* tab, float* ps, cudaStream_t s);
+// rtab (optional): the memoised infectivity beta s(age) of a shedding profile
+cudaError_t launch_build_ptables(const ModelF& M, int age_dtype, float4* tab, float* ps, cudaStream_t s,
+                                 float4* rtab = nullptr, const LawF& shed = LawF{}, int shed_mode = 0);
 cudaError_t launch_run_begin(DevCtl* ctl, uint32_t* out, cudaStream_t s);
 // dtrec: the K step sizes (adaptive step) or null (every step is dt)
 cudaError_t launch_run_epilogue(DevCtl* ctl, unsigned long long* deltas, int K, int model, const float* dtrec,

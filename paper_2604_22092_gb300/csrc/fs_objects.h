@@ -61,6 +61,7 @@ struct fs_sim {
     // the merge class's cross-chunk partial pressures
     void* d_rho[2] = {nullptr, nullptr};
     float2* d_mpart = nullptr;
+    float4* d_rtab = nullptr;     // [kPTableN] memoised beta s(age)
     // push form of the pressure (pressure == FS_PRESSURE_PUSH)
     int pressure = FS_PRESSURE_GATHER;
     uint8_t* d_cnt8 = nullptr;

@@ -82,8 +82,24 @@ __device__ __forceinline__ float node_p(const StepArgs& a, int x, float age, uin
 // only, and only in the SHED instances)
 __device__ __noinline__ float shed_rho(const StepArgs& a, float tau)
 {
-    const float s = a.shed_mode == kShedHazard ? hazard(a.shed, tau) : density(a.shed, tau);
-    return __fmul_rn(a.M.beta, s);
+    return shed_value(a.shed, a.shed_mode, a.M.beta, tau);
+}
+
+// the same value from the per-sim table when the age is on the fixed-step
+// sequence (identical bits: the table is built by shed_value)
+__device__ __forceinline__ float rho_of_age(const StepArgs& a, float age)
+{
+    const int n = __float2int_rn(__fmul_rn(age, a.M.inv_dt));
+    if ((unsigned)n < (unsigned)kPTableN) {
+        const float4* row = a.rtab + n;
+        const float2 e = __ldg(reinterpret_cast<const float2*>(row));
+        if (e.x == age)
+            return e.y;
+        const float r1 = ptab_slot1(row, age);
+        if (r1 >= 0.0f)
+            return r1;
+    }
+    return shed_rho(a, age);
 }
 
 // Bernoulli decision and transition for one node of probability p
@@ -202,7 +218,7 @@ __device__ __forceinline__ void sell_slice(const StepArgs& a, uint32_t step, con
         if constexpr (SHED) {
             if (r.x == kI)   // the next step's infectivity, from the new age as stored
                 static_cast<AgeT*>(a.rho[(step & 1u) ^ 1u])[i] =
-                    AgeIO<AgeT>::store(shed_rho(a, AgeIO<AgeT>::load(AgeIO<AgeT>::store(r.age))));
+                    AgeIO<AgeT>::store(rho_of_age(a, AgeIO<AgeT>::load(AgeIO<AgeT>::store(r.age))));
         }
     }
     const uint32_t word = __ballot_sync(kFull, valid && r.x == kI);
@@ -484,7 +500,7 @@ __device__ __forceinline__ void merge_chunk(const StepArgs& a, uint32_t step, co
             if constexpr (SHED) {
                 if (t.x == kI)
                     static_cast<AgeT*>(a.rho[(step & 1u) ^ 1u])[gi] =
-                        AgeIO<AgeT>::store(shed_rho(a, AgeIO<AgeT>::load(AgeIO<AgeT>::store(t.age))));
+                        AgeIO<AgeT>::store(rho_of_age(a, AgeIO<AgeT>::load(AgeIO<AgeT>::store(t.age))));
             }
             const int wofs = (gi >> 5) - ((a.m_base + R0) >> 5);
             const uint32_t bit = 1u << (gi & 31);
@@ -565,7 +581,7 @@ __global__ void __launch_bounds__(kStepThreads, kStepCtasPerSm) fused_step_kerne
 // bitmap through the read-only path. Warps take slices round-robin and load
 // the next slice's states one iteration ahead.
 // ---------------------------------------------------------------------------
-template <typename AgeT>
+template <typename AgeT, bool SHED>
 __global__ void __launch_bounds__(kSmemThreads, 1) sell_smem_kernel(const __grid_constant__ StepArgs a)
 {
     extern __shared__ __align__(128) uint32_t sbm[];
@@ -624,9 +640,9 @@ __global__ void __launch_bounds__(kSmemThreads, 1) sell_smem_kernel(const __grid
                 continue;
             }
             if (use_smem)
-                sell_slice<AgeT, true>(a, (uint32_t)k, sbm, bmn, slice, x, ld, mb, &ready);
+                sell_slice<AgeT, true, SHED>(a, (uint32_t)k, sbm, bmn, slice, x, ld, mb, &ready);
             else
-                sell_slice<AgeT, false>(a, (uint32_t)k, bm, bmn, slice, x, ld);
+                sell_slice<AgeT, false, SHED>(a, (uint32_t)k, bm, bmn, slice, x, ld);
         }
     }
     // the copy into this CTA's shared memory must have landed before it exits
@@ -656,7 +672,8 @@ __global__ void __launch_bounds__(kSmemThreads, 1) sell_smem_kernel(const __grid
 // third would be evaluated directly by the step); then every entry is
 // evaluated in parallel with the step's own hazard code. Unfilled slots hold
 // NaN ages.
-__global__ void build_ptables_kernel(ModelF M, int age_dtype, float4* __restrict__ tab, float* __restrict__ ps)
+__global__ void build_ptables_kernel(ModelF M, int age_dtype, float4* __restrict__ tab, float* __restrict__ ps,
+                                     float4* __restrict__ rtab, LawF shed, int shed_mode)
 {
     __shared__ float ages[kPTableN];
     if (threadIdx.x == 0) {
@@ -688,6 +705,11 @@ __global__ void build_ptables_kernel(ModelF M, int age_dtype, float4* __restrict
             lat[1] = p_of_rate(M, hazard(M.lat, v));
             inf[0] = v;
             inf[1] = p_of_rate(M, hazard(M.inf, v));
+            if (rtab) {
+                float* rr = reinterpret_cast<float*>(rtab + idx) + 2 * sl;
+                rr[0] = v;
+                rr[1] = shed_value(shed, shed_mode, M.beta, v);
+            }
         }
     }
     for (int c = threadIdx.x; c < kPSTableN; c += blockDim.x)
@@ -886,16 +908,22 @@ cudaError_t launch_step(const StepArgs& a, int age_dtype, cudaStream_t s, bool p
 template <typename AgeT>
 static cudaError_t launch_step_smem_t(const StepArgs& a, cudaStream_t s, int num_sms)
 {
-    static thread_local int configured = 0;   // dynamic shared memory limit set once per thread
+    static thread_local int configured = 0;   // dynamic shared memory limits set once per thread
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(sell_smem_kernel<AgeT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kSmemBitmapMaxBytes);
+        cudaError_t e = cudaFuncSetAttribute(sell_smem_kernel<AgeT, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBitmapMaxBytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(sell_smem_kernel<AgeT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kSmemBitmapMaxBytes);
         if (e != cudaSuccess)
             return e;
         configured = 1;
     }
     const int grid = std::max(1, std::min(num_sms, (a.n_slices + 31) / 32));
-    sell_smem_kernel<AgeT><<<grid, kSmemThreads, a.bm_bytes, s>>>(a);
+    if (a.shed_mode != kShedNone)
+        sell_smem_kernel<AgeT, true><<<grid, kSmemThreads, a.bm_bytes, s>>>(a);
+    else
+        sell_smem_kernel<AgeT, false><<<grid, kSmemThreads, a.bm_bytes, s>>>(a);
     g_launch_count += 1;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || a.n_chunks == 0)
@@ -915,9 +943,10 @@ cudaError_t launch_step_smem(const StepArgs& a, int age_dtype, cudaStream_t s, i
     }
 }
 
-cudaError_t launch_build_ptables(const ModelF& M, int age_dtype, float4* tab, float* ps, cudaStream_t s)
+cudaError_t launch_build_ptables(const ModelF& M, int age_dtype, float4* tab, float* ps, cudaStream_t s,
+                                 float4* rtab, const LawF& shed, int shed_mode)
 {
-    build_ptables_kernel<<<1, 256, 0, s>>>(M, age_dtype, tab, ps);
+    build_ptables_kernel<<<1, 256, 0, s>>>(M, age_dtype, tab, ps, rtab, shed, shed_mode);
     g_launch_count += 1;
     return cudaGetLastError();
 }
