@@ -65,10 +65,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-served", action="store_true", help="skip the served-vs-plain block")
-    ap.add_argument("--workload", choices=["regular", "ensemble", "serving", "large", "precision", "shedding"],
+    ap.add_argument("--workload", choices=["regular", "ensemble", "serving", "large", "precision", "shedding",
+                                           "compaction"],
                     default="regular",
                     help="regular: the headline line; ensemble / serving: full-size packed and served runs; "
-                         "shedding: constant vs age-dependent infectivity on regular d=8 and BA m=4 graphs")
+                         "shedding: constant vs age-dependent infectivity on regular d=8 and BA m=4 graphs; "
+                         "compaction: runs with and without the active-node list on ER d=8 and BA m=4")
     ap.add_argument("--age", choices=["f32", "f16"], default="f32", help="age storage of ensemble/serving runs")
     ap.add_argument("--ens-graphs", type=int, default=64, help="graphs of the packed-ensemble run")
     ap.add_argument("--ens-steps", type=int, default=500, help="steps of the packed-ensemble run")
@@ -863,6 +865,54 @@ def shedding_bench(fs, torch, n: int, sim_steps: int, graph_steps: int, reps: in
     return res
 
 
+def compaction_bench(fs, torch, n: int, sim_steps: int, graph_steps: int, reps: int = 3):
+    """Active-node compaction (Section 5.6) as the paper's compaction table
+    measures it: N = 10^6, Erdos-Renyi mean degree 8 and Barabasi-Albert m = 4,
+    the same SEIR model, TF = sim_steps * dt, each run with and without
+    FS_ACTIVE_LIST in the gather form with every node in the one-lane-per-node
+    class (the paper's forced configuration), the gather form with the
+    automatic class split, and the push form. Event-timed CUDA Graph replays
+    (the per-window refreshes included), median of `reps`, L2 flushed."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    inf, lat = fs.law("lognormal", math.log(6.0), 0.6), fs.law("weibull", 2.0, 4.0)
+    K = graph_steps
+    full = sim_steps // K
+    res = {"workload": f"seir-compaction-n{n:.0e}".replace("+0", ""), "sim_steps": sim_steps, "graph_steps": K,
+           "timed": "CUDA Graph replays incl. refreshes (CUDA events), median of runs", "graphs": {}}
+    for gname, g in (("er-d8", W.erdos_renyi(n, 8, seed=0)), ("ba-m4", W.barabasi_albert(n, 4, seed=0))):
+        idx = W.index_nodes(g.n, 100, seed=1, allowed=W.non_hub_nodes(g) if gname.startswith("ba") else None)
+        row = {}
+        for cname, dispatch, pressure in (("gather_thread", fs.FS_DISPATCH_THREAD, fs.FS_PRESSURE_GATHER),
+                                          ("gather_auto", fs.FS_DISPATCH_AUTO, fs.FS_PRESSURE_GATHER),
+                                          ("push_auto", fs.FS_DISPATCH_AUTO, fs.FS_PRESSURE_PUSH)):
+            gh = fs.fs_graph_create(g.n, g.row_ptr, g.col_ind, opts=fs.graph_opts(dispatch, 0))
+            cell = {}
+            for label, flag in (("baseline", 0), ("compaction", fs.FS_ACTIVE_LIST)):
+                prm = fs.sim_params(fs.FS_SEIR, inf, 0.25, 0.1, 3, latent=lat, pressure=pressure | flag)
+                times = []
+                for r in range(reps + 1):
+                    flush.fill_(1.0)
+                    torch.cuda.synchronize()
+                    sh = fs.fs_sim_init(gh, prm, idx)
+                    ms = fs.fs_sim_run_timed(sh, sim_steps, K, None)
+                    c = fs.fs_sim_run(sh, 0)
+                    listed, units = fs.fs_sim_active_units(sh)
+                    fs.fs_sim_destroy(sh)
+                    if r:
+                        times.append(float(np.sum(ms[:full])))
+                t = float(np.median(times))
+                cell[label] = {"value": round(g.n * full * K / (t * 1e-3) / 1e9, 3), "unit": UNIT,
+                               "ms_per_run": round(t, 3), "final_R_frac": round(int(c[-1, 3]) / g.n, 4)}
+                if units:
+                    cell[label]["mean_units_visited_frac"] = round(listed / (units * (full + (sim_steps % K > 0))), 4)
+            cell["speedup"] = round(cell["compaction"]["value"] / cell["baseline"]["value"], 3)
+            row[cname] = cell
+            fs.fs_graph_destroy(gh)
+        res["graphs"][gname] = row
+    return res
+
+
 def run_extra(args):
     """Full-size packed-ensemble or serving runs (their own JSON line)."""
     import torch
@@ -874,6 +924,8 @@ def run_extra(args):
                              age_dtype=age, pressure=PRESSURE[args.pressure])
     elif args.workload == "precision":
         res = precision_bench(fs, torch, n=args.n, steps=args.sim_steps, reps=1000)
+    elif args.workload == "compaction":
+        res = compaction_bench(fs, torch, n=args.n, sim_steps=args.sim_steps, graph_steps=args.graph_steps)
     elif args.workload == "shedding":
         res = shedding_bench(fs, torch, n=args.n, sim_steps=args.sim_steps, graph_steps=args.graph_steps)
     elif args.workload == "large":

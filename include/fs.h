@@ -79,6 +79,20 @@ enum { FS_DISPATCH_AUTO = 0, FS_DISPATCH_THREAD = 1, FS_DISPATCH_MERGE = 2, FS_D
  *     FS_PRESSURE_PUSH selects the push form there too (every realisation of
  *     an ensemble or request must pass the same flags). */
 enum { FS_PRESSURE_AUTO = 0, FS_PRESSURE_GATHER = 1, FS_PRESSURE_PUSH = 2 };
+/* Active-node compaction (Section 5.6), a flag ORed into fs_sim_params.flags
+ * of a single realisation: at the start of every launch sequence (each CUDA
+ * Graph replay of the step loop, and the directly launched remainder) the
+ * units that still hold a non-R node are listed (SELL slices of 32 nodes in
+ * the gather form, groups of 8 nodes and merge-class nodes in the push form)
+ * and the steps of that sequence visit only them. R is absorbing, so a unit
+ * dropped at a refresh never needs a step again; units that reach R inside a
+ * sequence stay on the list until the next refresh. The list is used only
+ * once at least half the nodes are R (before that the refresh writes "all
+ * units" and returns). Trajectories are identical with and without it.
+ * Merge-class chunks of the gather form are edge-partitioned and not listed.
+ * Packed ensembles, batches, the server and fs_step_noalloc reject it. */
+#define FS_ACTIVE_LIST 0x4
+#define FS_PRESSURE_MASK 0x3
 
 /* Holding-time law of a nodal transition (Section 5.1; hazard h = f/S).
  *   FS_LAW_EXP:       a = rate gamma                  h = gamma
@@ -128,7 +142,8 @@ typedef struct {
     uint64_t seed;       /* Philox key                                             */
     uint32_t replicate;  /* realisation index in the key's stream                  */
     int32_t index_state; /* compartment of the index cases: FS_E (SEIR) or FS_I    */
-    int32_t flags;       /* FS_PRESSURE_AUTO / _GATHER / _PUSH; other values invalid */
+    int32_t flags;       /* FS_PRESSURE_AUTO / _GATHER / _PUSH, optionally | FS_ACTIVE_LIST;
+                            other bits invalid                                    */
     int32_t shed_mode;   /* fs_shed_mode (0: s = 1)                                */
     /* Adaptive step (Section 5.2): with eps > 0 step k advances by
      *   dt_k = min(dt, eps / (lambda*_{k-1} + delta))
@@ -279,6 +294,13 @@ fs_status fs_sim_set_state(fs_sim* s, const uint8_t* state, const void* age, int
  * steps run since init or set_state; *next_dt (may be NULL) = the size of the
  * next step (dt for a fixed step). Synchronous. */
 fs_status fs_sim_time(const fs_sim* s, double* elapsed, float* next_dt);
+
+/* Active-node compaction accounting (FS_ACTIVE_LIST): *listed = the sum over
+ * the launch sequences run since init or set_state of the units each one
+ * visited (all units while the list is not in use), *units = the number of
+ * units (SELL slices in the gather form, push items in the push form; 0
+ * without FS_ACTIVE_LIST). Synchronous. */
+fs_status fs_sim_active_units(const fs_sim* s, uint64_t* listed, uint64_t* units);
 
 /* The infectivity the next step reads (Eq. 8): rho[i] = beta s(tau_i) as
  * stored (age_dtype storage: float / binary16 / bfloat16 bits, n elements,

@@ -19,14 +19,15 @@ from . import _abi
 from ._abi import (FS_AGE_BF16, FS_AGE_F16, FS_AGE_F32, FS_DISPATCH_AUTO, FS_DISPATCH_MERGE,
                    FS_DISPATCH_THREAD, FS_DISPATCH_TUNE, FS_E, FS_I, FS_LAW_ERLANG, FS_LAW_EXP, FS_LAW_LOGNORMAL,
                    FS_LAW_NONE, FS_LAW_WEIBULL, FS_PRESSURE_AUTO, FS_PRESSURE_GATHER, FS_PRESSURE_PUSH, FS_R,
-                   FS_S, FS_SEIR, FS_SHED_DENSITY, FS_SHED_HAZARD, FS_SHED_NONE, FS_SIR, FsError, check)
+                   FS_S, FS_SEIR, FS_SHED_DENSITY, FS_SHED_HAZARD, FS_SHED_NONE, FS_SIR, FS_ACTIVE_LIST, FsError,
+                   check)
 
 __all__ = [
     "fs_version", "fs_last_error", "fs_graph_create", "fs_graph_info_get", "fs_graph_destroy",
     "fs_sim_init", "fs_sim_step", "fs_sim_run", "fs_sim_run_async", "fs_sim_sync", "fs_sim_run_timed",
     "fs_kernel_launches", "fs_tune_stats", "fs_tune_reset",
     "fs_sim_get_state", "fs_sim_set_state", "fs_sim_work", "fs_sim_pressure_get", "fs_sim_time",
-    "fs_sim_infectivity_get", "fs_sim_destroy",
+    "fs_sim_infectivity_get", "fs_sim_active_units", "fs_sim_destroy",
     "fs_eval_hazard", "fs_eval_density",
     "fs_eval_uniforms", "fs_step_noalloc", "fs_ens_create", "fs_ens_run", "fs_ens_get_state",
     "fs_ens_destroy", "fs_batch_create", "fs_batch_add", "fs_batch_run", "fs_batch_status", "fs_batch_destroy",
@@ -36,7 +37,7 @@ __all__ = [
     "FS_S", "FS_E", "FS_I", "FS_R", "FS_SIR", "FS_SEIR", "FS_AGE_F32", "FS_AGE_F16", "FS_AGE_BF16",
     "FS_DISPATCH_AUTO", "FS_DISPATCH_THREAD", "FS_DISPATCH_MERGE", "FS_DISPATCH_TUNE",
     "FS_PRESSURE_AUTO", "FS_PRESSURE_GATHER", "FS_PRESSURE_PUSH", "FS_SHED_NONE", "FS_SHED_HAZARD",
-    "FS_SHED_DENSITY",
+    "FS_SHED_DENSITY", "FS_ACTIVE_LIST",
 ]
 
 
@@ -89,7 +90,8 @@ def sim_params(model: int, infectious: _abi.fs_law, beta: float, dt: float, seed
                age_dtype: int = FS_AGE_F32, pressure: int = FS_PRESSURE_AUTO, eps: float = 0.0,
                delta: float = 0.0, shed_mode: int = FS_SHED_NONE,
                shedding: _abi.fs_law | None = None) -> _abi.fs_sim_params:
-    """pressure: FS_PRESSURE_AUTO / FS_PRESSURE_GATHER / FS_PRESSURE_PUSH (the flags field);
+    """pressure: FS_PRESSURE_AUTO / FS_PRESSURE_GATHER / FS_PRESSURE_PUSH, optionally
+    | FS_ACTIVE_LIST (the flags field);
     eps > 0: adaptive step with dt as its cap (delta 0 = 1e-12);
     shed_mode / shedding: the shedding profile s(tau) of the infectivity (FS_SHED_NONE: s = 1)."""
     if index_state is None:
@@ -232,6 +234,13 @@ def fs_sim_infectivity_get(s: int, n: int, age_dtype: int = FS_AGE_F32) -> np.nd
     rho = np.zeros(n, dtype=_AGE_NP[age_dtype])
     check(load().fs_sim_infectivity_get(s, _addr(rho)), "fs_sim_infectivity_get")
     return rho
+
+
+def fs_sim_active_units(s: int) -> tuple[int, int]:
+    """(units visited summed over launch sequences, units per sequence) of FS_ACTIVE_LIST."""
+    a, u = ctypes.c_uint64(), ctypes.c_uint64()
+    check(load().fs_sim_active_units(s, ctypes.byref(a), ctypes.byref(u)), "fs_sim_active_units")
+    return a.value, u.value
 
 
 def fs_sim_pressure_get(s: int) -> int:

@@ -20,6 +20,7 @@ FS_AGE_F32, FS_AGE_F16, FS_AGE_BF16 = 0, 1, 2
 FS_DISPATCH_AUTO, FS_DISPATCH_THREAD, FS_DISPATCH_MERGE, FS_DISPATCH_TUNE = 0, 1, 2, 3
 FS_PRESSURE_AUTO, FS_PRESSURE_GATHER, FS_PRESSURE_PUSH = 0, 1, 2
 FS_SHED_NONE, FS_SHED_HAZARD, FS_SHED_DENSITY = 0, 1, 2
+FS_ACTIVE_LIST = 0x4
 FS_LAW_NONE, FS_LAW_EXP, FS_LAW_LOGNORMAL, FS_LAW_WEIBULL, FS_LAW_ERLANG = 0, 1, 2, 3, 4
 
 
@@ -87,6 +88,7 @@ PROTOTYPES = {
     "fs_sim_pressure_get": (ctypes.c_int, [VP, P(ctypes.c_int32)]),
     "fs_sim_time": (ctypes.c_int, [VP, P(ctypes.c_double), P(ctypes.c_float)]),
     "fs_sim_infectivity_get": (ctypes.c_int, [VP, VP]),
+    "fs_sim_active_units": (ctypes.c_int, [VP, P(ctypes.c_uint64), P(ctypes.c_uint64)]),
     "fs_sim_destroy": (ctypes.c_int, [VP]),
     "fs_eval_hazard": (ctypes.c_int, [P(fs_law), VP, VP, ctypes.c_int64, VP]),
     "fs_eval_density": (ctypes.c_int, [P(fs_law), VP, VP, ctypes.c_int64, VP]),

@@ -156,8 +156,9 @@ fs_status check_params(const fs_sim_params* p)
         return fail(FS_EINVAL, "beta must be finite and >= 0");
     if (!finite(p->dt) || !(p->dt > 0))
         return fail(FS_EINVAL, "dt must be finite and > 0");
-    if (p->flags < FS_PRESSURE_AUTO || p->flags > FS_PRESSURE_PUSH)
-        return fail(FS_EINVAL, "flags must be FS_PRESSURE_AUTO, FS_PRESSURE_GATHER or FS_PRESSURE_PUSH");
+    if ((p->flags & ~(FS_PRESSURE_MASK | FS_ACTIVE_LIST)) != 0 || (p->flags & FS_PRESSURE_MASK) > FS_PRESSURE_PUSH)
+        return fail(FS_EINVAL, "flags must be FS_PRESSURE_AUTO, FS_PRESSURE_GATHER or FS_PRESSURE_PUSH, "
+                               "optionally with FS_ACTIVE_LIST");
     if (p->shed_mode < FS_SHED_NONE || p->shed_mode > FS_SHED_DENSITY)
         return fail(FS_EINVAL, "shed_mode must be FS_SHED_NONE, FS_SHED_HAZARD or FS_SHED_DENSITY");
     if (p->shed_mode != FS_SHED_NONE) {
@@ -249,6 +250,7 @@ fs::StepArgs step_args(const fs_sim* s, int j)
     a.shed = to_lawf(s->p.shedding);
     a.shed_mode = s->p.shed_mode;
     a.rtab = s->d_rtab;
+    a.act = s->d_act;
     a.dtrec = s->d_dtrec;
     return a;
 }
@@ -632,20 +634,21 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
                 return fail(FS_EINVAL, "index node %d repeated", v[q]);
         }
     }
-    if (params->flags == FS_PRESSURE_PUSH && !push_available(g))
+    const int pform = params->flags & FS_PRESSURE_MASK;
+    if (pform == FS_PRESSURE_PUSH && !push_available(g))
         return fail(FS_EUNSUPPORTED, "FS_PRESSURE_PUSH needs in-degrees <= %d in the thread class (thread_max_deg %d)",
                     fs::kMaxThreadDeg, g->t1);
     const bool shed = params->shed_mode != FS_SHED_NONE;
-    if (shed && params->flags == FS_PRESSURE_PUSH)
+    if (shed && pform == FS_PRESSURE_PUSH)
         return fail(FS_EUNSUPPORTED, "a shedding profile needs the gather form of the pressure (the push form "
                                      "keeps integer infectious counts)");
-    if (params->eps > 0 && (shed || params->flags == FS_PRESSURE_GATHER || !push_available(g)))
+    if (params->eps > 0 && (shed || pform == FS_PRESSURE_GATHER || !push_available(g)))
         return fail(FS_EUNSUPPORTED, "the adaptive step (eps > 0) runs in the push form of the pressure only");
     fs_sim* s = new fs_sim();
     s->g = g;
     s->p = *params;
-    s->pressure = (shed || params->flags == FS_PRESSURE_GATHER || !push_available(g)) ? FS_PRESSURE_GATHER
-                                                                                      : FS_PRESSURE_PUSH;
+    s->pressure = (shed || pform == FS_PRESSURE_GATHER || !push_available(g)) ? FS_PRESSURE_GATHER
+                                                                              : FS_PRESSURE_PUSH;
     s->M = to_model(*params);
     s->age_bytes = params->age_dtype == FS_AGE_F32 ? 4 : 2;
     const int64_t n = g->n;
@@ -690,6 +693,11 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
     const size_t oPt = carve(sizeof(float4) * 2 * fs::kPTableN), oPs = carve(sizeof(float) * fs::kPSTableN);
     const size_t oIdx = carve(sizeof(int32_t) * (size_t)std::max<int64_t>(n_index, 1));
     const size_t oDt = carve(sizeof(float) * fs::kMaxGraphSteps);
+    // active-node compaction list: one entry per push item or SELL slice
+    const bool compact = (params->flags & FS_ACTIVE_LIST) != 0;
+    const size_t n_units = push ? ((size_t)g->n_thr + fs::kPushG - 1) / fs::kPushG + (size_t)g->n_m
+                                : (size_t)g->n_slices;
+    const size_t oAct = compact ? carve(sizeof(int32_t) * (n_units + 32)) : 0;
     size_t oR0 = 0, oR1 = 0, oMp = 0, oRt = 0;
     if (shed) {
         oR0 = carve(n_pad * s->age_bytes);
@@ -721,6 +729,8 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
     d_idx = reinterpret_cast<int32_t*>(base + oIdx);
     if (params->eps > 0)
         s->d_dtrec = reinterpret_cast<float*>(base + oDt);
+    if (compact)
+        s->d_act = reinterpret_cast<int32_t*>(base + oAct);
     if (shed) {
         s->d_rho[0] = base + oR0;
         s->d_rho[1] = base + oR1;
@@ -774,6 +784,16 @@ static cudaError_t launch_one_step(fs_sim* s, int j)
     return fs::launch_step(a, s->p.age_dtype, s->stream, false);
 }
 
+// the active-node compaction refresh that opens every launch sequence
+static cudaError_t launch_compact(fs_sim* s)
+{
+    if (!s->d_act)
+        return cudaSuccess;
+    const fs::StepArgs a = step_args(s, 0);
+    return s->pressure == FS_PRESSURE_PUSH ? fs::launch_push_compact(a, s->stream, s->g->num_sms)
+                                           : fs::launch_sell_compact(a, s->stream, s->g->num_sms);
+}
+
 static fs_status ensure_graph(fs_sim* s, int K)
 {
     if (s->gexec && s->gK == K)
@@ -784,7 +804,7 @@ static fs_status ensure_graph(fs_sim* s, int K)
     }
     cudaGraph_t graph = nullptr;
     FS_CUDA(s, cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = launch_compact(s);
     for (int j = 0; j < K && e == cudaSuccess; ++j)
         e = launch_one_step(s, j);
     if (e == cudaSuccess)
@@ -823,11 +843,12 @@ static fs_status run_enqueue(fs_sim* s, int64_t steps, int32_t graph_steps, uint
                 FS_CUDA(s, cudaEventRecord(replay_ev[r], s->stream));
             FS_CUDA(s, cudaGraphLaunch(s->gexec, s->stream));
         }
-        fs::g_launch_count += (unsigned long long)full * (K + 1);
+        fs::g_launch_count += (unsigned long long)full * (K + 1 + (s->d_act ? 1 : 0));
     }
     if (replay_ev)
         FS_CUDA(s, cudaEventRecord(replay_ev[full], s->stream));
     if (rem > 0) {
+        FS_CUDA(s, launch_compact(s));
         for (int j = 0; j < rem; ++j)
             FS_CUDA(s, launch_one_step(s, j));
         FS_CUDA(s, fs::launch_run_epilogue(s->d_ctl, s->d_deltas, rem, s->p.model, s->d_dtrec, s->M.dt, s->stream));
@@ -1034,6 +1055,27 @@ fs_status fs_sim_set_state(fs_sim* s, const uint8_t* state, const void* age, int
     if (s->d_rho[0])
         FS_CUDA(s, fs::launch_rho_init(step_args(s, 0), s->p.age_dtype, (uint32_t)(step & 1), s->stream));
     FS_CUDA(s, cudaStreamSynchronize(s->stream));
+    return FS_OK;
+}
+
+fs_status fs_sim_active_units(const fs_sim* s, uint64_t* listed, uint64_t* units)
+{
+    if (!s || !listed || !units)
+        return fail(FS_EINVAL, "NULL argument");
+    if (s->failed)
+        return fail(FS_ESTATE, "sim is in a failed state");
+    fs::DevCtl c;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(&c, s->d_ctl, sizeof(c), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+        return fail(FS_ECUDA, "fs_sim_active_units: %s", cudaGetErrorString(e));
+    *listed = c.act_sum;
+    *units = 0;
+    if (s->d_act)
+        *units = s->pressure == FS_PRESSURE_PUSH
+                     ? (uint64_t)(((int64_t)s->g->n_thr + fs::kPushG - 1) / fs::kPushG + s->g->n_m)
+                     : (uint64_t)s->g->n_slices;
     return FS_OK;
 }
 
@@ -1274,6 +1316,8 @@ extern "C" fs_status fs_step_noalloc(const fs_graph* g, const fs_sim_params* par
         return fail(FS_EUNSUPPORTED, "fs_step_noalloc: one step has a fixed size (eps must be 0)");
     if (pv.shed_mode != FS_SHED_NONE)
         return fail(FS_EUNSUPPORTED, "fs_step_noalloc: a shedding profile needs the sim's infectivity buffers");
+    if (pv.flags & FS_ACTIVE_LIST)
+        return fail(FS_EUNSUPPORTED, "fs_step_noalloc: FS_ACTIVE_LIST needs the sim's launch sequences");
     if (step < 0 || step >= ((int64_t)1 << 32))
         return fail(FS_EINVAL, "fs_step_noalloc: step must be in [0, 2^32)");
     if (g->n_m > kNoAllocMaxMergeRows)

@@ -67,6 +67,10 @@ struct DevCtl {
     uint32_t lam[3];
     int32_t pad2_;
     double time;                  // sum of the step sizes since init / set_state
+    // active-node compaction: units listed by the refresh of the current
+    // launch sequence (moved into act_sum and reset to 0 by the epilogue)
+    unsigned long long n_act;
+    unsigned long long act_sum;   // sum over launch sequences of n_act
 };
 
 enum { kErrNone = 0, kErrTmaTimeout = 1, kErrBadState = 2, kErrBadGraph = 3 };
@@ -144,6 +148,10 @@ struct StepArgs {
     int32_t shed_mode;            // FS_SHED_HAZARD (1) or FS_SHED_DENSITY (2); 0 = s = 1
     const float4* rtab;           // [kPTableN] memoised beta s(age) over the fixed-step age
                                   // sequence, two (age, value) slots per index like ptab
+    // active-node compaction (null: off): the units with a non-R node at the
+    // start of the launch sequence, ctl->n_act of them (all units when
+    // n_act >= their number): SELL slices (gather) or push items
+    int32_t* act;
 };
 
 enum { kShedNone = 0, kShedHazard = 1, kShedDensity = 2 };

@@ -37,6 +37,10 @@ cudaError_t launch_from_original(const void* in, void* out, int elem_bytes, cons
                                  cudaStream_t s);
 cudaError_t launch_eval_hazard(const LawF& L, const float* tau, float* h, int64_t n, cudaStream_t s);
 cudaError_t launch_eval_density(const LawF& L, const float* tau, float* f, int64_t n, cudaStream_t s);
+// active-node compaction refreshes (a.act must be set): gather form (SELL
+// slices) and push form (push items)
+cudaError_t launch_sell_compact(const StepArgs& a, cudaStream_t s, int num_sms);
+cudaError_t launch_push_compact(const StepArgs& a, cudaStream_t s, int num_sms);
 // rho[par] of every I node from its age (a.X, a.A, a.rho, a.M.beta, a.shed*)
 cudaError_t launch_rho_init(const StepArgs& a, int age_dtype, uint32_t par, cudaStream_t s);
 cudaError_t launch_eval_uniforms(uint32_t key0, uint32_t key1, uint32_t rep, uint32_t step, const int32_t* nodes,

@@ -62,6 +62,7 @@ struct fs_sim {
     void* d_rho[2] = {nullptr, nullptr};
     float2* d_mpart = nullptr;
     float4* d_rtab = nullptr;     // [kPTableN] memoised beta s(age)
+    int32_t* d_act = nullptr;     // active-node compaction list (FS_ACTIVE_LIST)
     // push form of the pressure (pressure == FS_PRESSURE_PUSH)
     int pressure = FS_PRESSURE_GATHER;
     uint8_t* d_cnt8 = nullptr;

@@ -707,6 +707,111 @@ __device__ __forceinline__ void warp_push(const StepArgs& a, uint32_t par, uint3
 
 constexpr int kScanRounds = 3;      // grid-stride rounds whose loads a warp issues together
 
+// The item loops of one step: one item per lane (the grid covers every item
+// at once) or kScanRounds grid-stride rounds at a time. LIST: position q of
+// the sweep visits the listed item act[q] (q < n_items), else item q; a
+// compile-time choice so that the sweep without a list keeps its own register
+// allocation.
+template <typename AgeT, bool SCAN, bool ADAPTIVE, bool LIST>
+__device__ __forceinline__ void push_items(const StepArgs& a, uint32_t par, int64_t k, bool spec_s, float dt,
+                                           float& lmax, PushDeltas& ld, WarpScratch& w, float* pslot,
+                                           const int32_t* __restrict__ act, int64_t n_items)
+{
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int64_t n_grp = ((int64_t)a.n_thr + kPushG - 1) / kPushG;
+    const int64_t total = n_grp + a.n_m;
+    const int64_t stride = (int64_t)gridDim.x * kPushThreads;
+    // (item numbers fit 31 bits: at most n / kPushG + n_m < 2^31)
+    auto item_at = [&](int64_t q) -> int64_t {
+        if constexpr (!LIST)
+            return q;
+        else
+            return q < n_items ? (int64_t)__ldg(act + q) : (int64_t)INT32_MAX;
+    };
+    // Warps take kScanRounds grid-stride rounds at a time: the loads that tell
+    // whether an item has work (states; counts and tallies while S is common)
+    // are issued for all of them together, and only the rounds in which some
+    // lane of the warp has work are processed, so a mostly idle sweep (the
+    // all-S start, the mostly-R tail) waits for memory once per kScanRounds
+    // rounds instead of once per round.
+    // One item per lane (the grid covers every item at once): no scan.
+    if constexpr (!SCAN) {
+        const int64_t t = item_at((int64_t)blockIdx.x * kPushThreads + tid);
+        GroupLoads cur = group_loads(a, par, t, n_grp, spec_s);
+        const bool idle = (t < n_grp || t >= total) && group_idle(a, par, t, n_grp, cur);
+        if (!__all_sync(kFull, idle)) {
+            Item it;
+            it.kind = kItemNone;
+            it.base = 0;
+            it.need = 0u;
+            if (t < n_grp)
+                group_prepare<AgeT, ADAPTIVE>(a, par, (int)(t * kPushG), cur, it, pslot, dt, lmax);
+            else if (t < total)
+                hub_prepare<AgeT, ADAPTIVE>(a, par, a.n_thr + (int)(t - n_grp), it, pslot, dt, lmax);
+            __syncwarp();
+            const uint32_t fired = warp_draws(a, (uint32_t)k, it, w);
+            uint32_t ev = 0u, neg = 0u;
+            item_apply<AgeT>(a, par, it, fired, ev, neg, ld, dt);
+            warp_push<false>(a, par, ev, neg, it.base, w.ev);
+        }
+    }
+    for (int64_t tb = (int64_t)blockIdx.x * kPushThreads + (tid & ~31); SCAN && tb < n_items;
+         tb += (int64_t)kScanRounds * stride) {
+        uint32_t busy = 0u;
+        {
+            GroupLoads gl[kScanRounds];
+#pragma unroll
+            for (int u = 0; u < kScanRounds; ++u)
+                gl[u] = group_loads(a, par, item_at(tb + u * stride + lane), n_grp, spec_s);
+#pragma unroll
+            for (int u = 0; u < kScanRounds; ++u) {
+                const int64_t t = item_at(tb + u * stride + lane);
+                const bool idle = (t < n_grp || t >= total) && group_idle(a, par, t, n_grp, gl[u]);
+                busy |= (idle ? 0u : 1u) << u;
+            }
+        }
+        uint32_t wb = __reduce_or_sync(kFull, busy);
+        while (wb) {
+            const int u = __ffs(wb) - 1;
+            wb &= wb - 1u;
+            const int64_t t = item_at(tb + u * stride + lane);
+            // reloaded: these lines were read by the scan just above
+            const GroupLoads cur = group_loads(a, par, t, n_grp, spec_s);
+            Item it;
+            it.kind = kItemNone;
+            it.base = 0;
+            it.need = 0u;
+            if (t < n_grp)
+                group_prepare<AgeT, ADAPTIVE>(a, par, (int)(t * kPushG), cur, it, pslot, dt, lmax);
+            else if (t < total)
+                hub_prepare<AgeT, ADAPTIVE>(a, par, a.n_thr + (int)(t - n_grp), it, pslot, dt, lmax);
+            __syncwarp();
+            const uint32_t fired = warp_draws(a, (uint32_t)k, it, w);
+            uint32_t ev = 0u, neg = 0u;
+            item_apply<AgeT>(a, par, it, fired, ev, neg, ld, dt);
+            warp_push<false>(a, par, ev, neg, it.base, w.ev);
+        }
+    }
+}
+
+// The listed block-scan sweep out of line: it has its own register
+// allocation, and the sweep without a list (inlined into the kernel) keeps
+// the allocation it has alone. Results come back by value.
+struct PushSweepOut {
+    PushDeltas ld;
+    float lmax;
+};
+
+template <typename AgeT, bool SCAN, bool ADAPTIVE>
+__device__ __noinline__ PushSweepOut push_items_listed(const StepArgs& a, uint32_t par, int64_t k, bool spec_s,
+                                                        float dt, WarpScratch* w, float* pslot, int64_t n_items)
+{
+    PushSweepOut o;
+    o.lmax = 0.0f;
+    push_items<AgeT, SCAN, ADAPTIVE, true>(a, par, k, spec_s, dt, o.lmax, o.ld, *w, pslot, a.act, n_items);
+    return o;
+}
+
 // ---------------------------------------------------------------------------
 // One whole step: items are groups of kPushG thread-class nodes, then single
 // merge-class nodes; warps stride over them (grid-stride). Per-step deltas as
@@ -742,72 +847,24 @@ __global__ void __launch_bounds__(kPushThreads, kPushCtasPerSm) push_step_kernel
     // (counts of the state at the start of this launch sequence)
     const bool spec_s = (int64_t)a.ctl->counts[0] * 16 >= (int64_t)a.n;
     PushDeltas ld;
-    const int64_t n_grp = ((int64_t)a.n_thr + kPushG - 1) / kPushG;
-    const int64_t total = n_grp + a.n_m;
-    const int64_t stride = (int64_t)gridDim.x * kPushThreads;
-    // Warps take kScanRounds grid-stride rounds at a time: the loads that tell
-    // whether an item has work (states; counts and tallies while S is common)
-    // are issued for all of them together, and only the rounds in which some
-    // lane of the warp has work are processed, so a mostly idle sweep (the
-    // all-S start, the mostly-R tail) waits for memory once per kScanRounds
-    // rounds instead of once per round.
-    // One item per lane (the grid covers every item at once): no scan.
-    if constexpr (!SCAN) {
-        const int64_t t = (int64_t)blockIdx.x * kPushThreads + tid;
-        GroupLoads cur = group_loads(a, par, t, n_grp, spec_s);
-        const bool idle = (t < n_grp || t >= total) && group_idle(a, par, t, n_grp, cur);
-        if (!__all_sync(kFull, idle)) {
-            Item it;
-            it.kind = kItemNone;
-            it.base = 0;
-            it.need = 0u;
-            if (t < n_grp)
-                group_prepare<AgeT, ADAPTIVE>(a, par, (int)(t * kPushG), cur, it, pslot, dt, lmax);
-            else if (t < total)
-                hub_prepare<AgeT, ADAPTIVE>(a, par, a.n_thr + (int)(t - n_grp), it, pslot, dt, lmax);
-            __syncwarp();
-            const uint32_t fired = warp_draws(a, (uint32_t)k, it, w);
-            uint32_t ev = 0u, neg = 0u;
-            item_apply<AgeT>(a, par, it, fired, ev, neg, ld, dt);
-            warp_push<false>(a, par, ev, neg, it.base, w.ev);
+    // active-node compaction (Section 5.6): the items listed by this launch
+    // sequence's refresh, or every item
+    const int64_t total = ((int64_t)a.n_thr + kPushG - 1) / kPushG + a.n_m;
+    const int64_t na = a.act ? (int64_t)a.ctl->n_act : total;
+    if constexpr (SCAN) {
+        if (na < total) {
+            const PushSweepOut o = push_items_listed<AgeT, SCAN, ADAPTIVE>(a, par, k, spec_s, dt, &w, pslot, na);
+            ld = o.ld;
+            lmax = o.lmax;
+        } else {
+            push_items<AgeT, SCAN, ADAPTIVE, false>(a, par, k, spec_s, dt, lmax, ld, w, pslot, nullptr, total);
         }
-    }
-    for (int64_t tb = (int64_t)blockIdx.x * kPushThreads + (tid & ~31); SCAN && tb < total;
-         tb += (int64_t)kScanRounds * stride) {
-        uint32_t busy = 0u;
-        {
-            GroupLoads gl[kScanRounds];
-#pragma unroll
-            for (int u = 0; u < kScanRounds; ++u)
-                gl[u] = group_loads(a, par, tb + u * stride + lane, n_grp, spec_s);
-#pragma unroll
-            for (int u = 0; u < kScanRounds; ++u) {
-                const int64_t t = tb + u * stride + lane;
-                const bool idle = (t < n_grp || t >= total) && group_idle(a, par, t, n_grp, gl[u]);
-                busy |= (idle ? 0u : 1u) << u;
-            }
-        }
-        uint32_t wb = __reduce_or_sync(kFull, busy);
-        while (wb) {
-            const int u = __ffs(wb) - 1;
-            wb &= wb - 1u;
-            const int64_t t = tb + u * stride + lane;
-            // reloaded: these lines were read by the scan just above
-            const GroupLoads cur = group_loads(a, par, t, n_grp, spec_s);
-            Item it;
-            it.kind = kItemNone;
-            it.base = 0;
-            it.need = 0u;
-            if (t < n_grp)
-                group_prepare<AgeT, ADAPTIVE>(a, par, (int)(t * kPushG), cur, it, pslot, dt, lmax);
-            else if (t < total)
-                hub_prepare<AgeT, ADAPTIVE>(a, par, a.n_thr + (int)(t - n_grp), it, pslot, dt, lmax);
-            __syncwarp();
-            const uint32_t fired = warp_draws(a, (uint32_t)k, it, w);
-            uint32_t ev = 0u, neg = 0u;
-            item_apply<AgeT>(a, par, it, fired, ev, neg, ld, dt);
-            warp_push<false>(a, par, ev, neg, it.base, w.ev);
-        }
+    } else {
+        // one round: both sweeps inline
+        if (na < total)
+            push_items<AgeT, SCAN, ADAPTIVE, true>(a, par, k, spec_s, dt, lmax, ld, w, pslot, a.act, na);
+        else
+            push_items<AgeT, SCAN, ADAPTIVE, false>(a, par, k, spec_s, dt, lmax, ld, w, pslot, nullptr, total);
     }
     if constexpr (ADAPTIVE) {
         // rates are >= 0, so their FP32 bits order as unsigned integers
@@ -885,6 +942,49 @@ __global__ void transpose_kernel(const int64_t* __restrict__ sell_off, const int
     }
 }
 
+// Active-node compaction refresh (Section 5.6), at the start of a launch
+// sequence: lists the items (groups of kPushG thread-class nodes, merge-class
+// nodes) that still hold a non-R node. While fewer than half the nodes are R
+// it writes "all items" instead. ctl->n_act is 0 on entry (the previous
+// epilogue, init or set_state left it so).
+__global__ void push_compact_kernel(const __grid_constant__ StepArgs a)
+{
+    const int64_t n_grp = ((int64_t)a.n_thr + kPushG - 1) / kPushG;
+    const int64_t total = n_grp + a.n_m;
+    if ((int64_t)a.ctl->counts[3] * 2 < (int64_t)a.n) {
+        if (blockIdx.x == 0 && threadIdx.x == 0)
+            a.ctl->n_act = (unsigned long long)total;
+        return;
+    }
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); t0 < total; t0 += stride) {
+        const int64_t t = t0 + lane;
+        bool live = false;
+        if (t < n_grp) {
+            const int i0 = (int)(t * kPushG);
+            uint2 xs = *reinterpret_cast<const uint2*>(a.X + i0);
+            const int nv = min(kPushG, a.n_thr - i0);
+#pragma unroll
+            for (int u = 0; u < kPushG; ++u)
+                if (u >= nv)
+                    set_byte(xs, u, kR);
+            live = (xs.x & xs.y) != 0x03030303u;
+        } else if (t < total) {
+            live = a.X[a.n_thr + (int)(t - n_grp)] != kR;
+        }
+        const uint32_t b = __ballot_sync(kFull, live);
+        if (b) {
+            unsigned long long base = 0ull;
+            if (lane == 0)
+                base = atomicAdd(&a.ctl->n_act, (unsigned long long)__popc(b));
+            base = __shfl_sync(kFull, base, 0);
+            if (live)
+                a.act[base + __popc(b & ((1u << lane) - 1u))] = (int32_t)t;
+        }
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -922,6 +1022,16 @@ cudaError_t launch_push_step_adaptive(const StepArgs& a, int age_dtype, cudaStre
     case kAgeBF16: return launch_push_step_t<__nv_bfloat16, true>(a, s, num_sms);
     default: return launch_push_step_t<float, true>(a, s, num_sms);
     }
+}
+
+cudaError_t launch_push_compact(const StepArgs& a, cudaStream_t s, int num_sms)
+{
+    const int64_t items = ((int64_t)a.n_thr + kPushG - 1) / kPushG + a.n_m;
+    const int64_t need = (items + kPushThreads - 1) / kPushThreads;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms * 8));
+    push_compact_kernel<<<grid, kPushThreads, 0, s>>>(a);
+    g_launch_count += 1;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_push_init(const StepArgs& a, cudaStream_t s, int num_sms)

@@ -243,23 +243,60 @@ __device__ __forceinline__ void sell_slice(const StepArgs& a, uint32_t step, con
     }
 }
 
-template <typename AgeT, bool SHED>
+// Active-node compaction (Section 5.6): the SELL slices a step visits. With
+// a list (ctl->n_act < n_slices), position q < n_act is the listed slice
+// act[q]; without, position q is slice q. Positions past the end map to
+// n_slices.
+struct SliceMap {
+    const int32_t* act;
+    int n_items;
+    bool list;
+    // LIST is the run-time `list`, made a compile-time choice by the callers
+    // so that the path without a list keeps its own register allocation
+    template <bool LIST>
+    __device__ __forceinline__ int at(int q) const
+    {
+        if constexpr (!LIST)
+            return q;
+        else
+            return q < n_items ? __ldg(act + q) : INT32_MAX;
+    }
+};
+
+__device__ __forceinline__ SliceMap slice_map(const StepArgs& a)
+{
+    SliceMap m{a.act, a.n_slices, false};
+    if (a.act) {
+        const unsigned long long na = a.ctl->n_act;
+        if (na < (unsigned long long)a.n_slices) {
+            m.list = true;
+            m.n_items = (int)na;
+        }
+    }
+    return m;
+}
+
+template <typename AgeT, bool SHED, bool LIST>
 __device__ __forceinline__ void sell_warp(const StepArgs& a, uint32_t step, const uint32_t* __restrict__ bm,
-                                          uint32_t* __restrict__ bmn, int s_begin, int s_end, LaneDeltas& ld)
+                                          uint32_t* __restrict__ bmn, int s_begin, int s_end, LaneDeltas& ld,
+                                          const SliceMap& sm)
 {
     const int lane = threadIdx.x & 31;
     for (int s0 = s_begin; s0 < s_end; s0 += 4) {
         uint32_t xs = 0;                       // four states, one byte each
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int i = (s0 + u) * 32 + lane;
-            const uint32_t x = (s0 + u < s_end && i < a.n_thr) ? (uint32_t)a.X[i] : (uint32_t)kR;
+            const int sl = s0 + u < s_end ? sm.at<LIST>(s0 + u) : INT32_MAX;
+            const uint32_t x = (sl < a.n_slices && sl * 32 + lane < a.n_thr) ? (uint32_t)a.X[sl * 32 + lane]
+                                                                           : (uint32_t)kR;
             xs |= x << (8 * u);
         }
 #pragma unroll 1
         for (int u = 0; u < 4; ++u) {
-            const int slice = s0 + u;
-            if (slice >= s_end)
+            if (s0 + u >= s_end)
+                break;
+            const int slice = sm.at<LIST>(s0 + u);
+            if (slice >= a.n_slices)
                 break;
             const int x = (int)((xs >> (8 * u)) & 0xffu);
             // absorbed slice: every node R, next-bitmap word 0, nothing else to do
@@ -551,10 +588,15 @@ __global__ void __launch_bounds__(kStepThreads, kStepCtasPerSm) fused_step_kerne
             merge_chunk<AgeT, SHED>(a, (uint32_t)k, bm, bmn, (int)blockIdx.x, s_delta);
     } else {
         const int cta = (int)blockIdx.x - (HAS_MERGE ? a.n_chunks : 0);
+        const SliceMap smap = slice_map(a);
         const int s_begin = (cta * kStepWarps + (int)(threadIdx.x >> 5)) * a.spw;
-        const int s_end = min(s_begin + a.spw, a.n_slices);
-        if (s_begin < s_end)
-            sell_warp<AgeT, SHED>(a, (uint32_t)k, bm, bmn, s_begin, s_end, ld);
+        const int s_end = min(s_begin + a.spw, smap.n_items);
+        if (s_begin < s_end) {
+            if (smap.list)
+                sell_warp<AgeT, SHED, true>(a, (uint32_t)k, bm, bmn, s_begin, s_end, ld, smap);
+            else
+                sell_warp<AgeT, SHED, false>(a, (uint32_t)k, bm, bmn, s_begin, s_end, ld, smap);
+        }
         const uint32_t fs_ = __reduce_add_sync(kFull, ld.fS), fe = __reduce_add_sync(kFull, ld.fE);
         const uint32_t fi = __reduce_add_sync(kFull, ld.fI), ds = __reduce_add_sync(kFull, ld.dS);
         if ((threadIdx.x & 31) == 0) {
@@ -581,6 +623,54 @@ __global__ void __launch_bounds__(kStepThreads, kStepCtasPerSm) fused_step_kerne
 // bitmap through the read-only path. Warps take slices round-robin and load
 // the next slice's states one iteration ahead.
 // ---------------------------------------------------------------------------
+// the slice loop of sell_smem_kernel: warps take the slices at positions
+// first + j W round-robin (W = resident warps), the states of the next four
+// loaded one iteration ahead
+template <typename AgeT, bool SHED, bool LIST>
+__device__ __forceinline__ void smem_slices(const StepArgs& a, uint32_t step, const uint32_t* __restrict__ bm,
+                                            const uint32_t* sbm, uint32_t* __restrict__ bmn, bool use_smem,
+                                            uint32_t mb, bool& ready, LaneDeltas& ld, const SliceMap& smap)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int W = (int)gridDim.x * (kSmemThreads / 32);
+    const int first = (int)blockIdx.x * (kSmemThreads / 32) + warp;
+    // states of the slices at positions first + (4g + u) W, u = 0..3, packed
+    // one byte each
+    auto load_group = [&](int base) -> uint32_t {
+        uint32_t xs = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int sl = smap.at<LIST>(base + u * W);
+            const uint32_t x = (sl < a.n_slices && sl * 32 + lane < a.n_thr) ? (uint32_t)a.X[sl * 32 + lane]
+                                                                           : (uint32_t)kR;
+            xs |= x << (8 * u);
+        }
+        return xs;
+    };
+    uint32_t xs_next = load_group(first);
+    for (int base = first; base < smap.n_items; base += 4 * W) {
+        const uint32_t xs = xs_next;
+        if (base + 4 * W < smap.n_items)
+            xs_next = load_group(base + 4 * W);
+#pragma unroll 1
+        for (int u = 0; u < 4; ++u) {
+            const int slice = smap.at<LIST>(base + u * W);
+            if (slice >= a.n_slices)
+                break;
+            const int x = (int)((xs >> (8 * u)) & 0xffu);
+            if (__all_sync(kFull, x == kR) && (slice + 1) * 32 <= a.n_thr) {
+                if (lane == 0)
+                    bmn[slice] = 0u;
+                continue;
+            }
+            if (use_smem)
+                sell_slice<AgeT, true, SHED>(a, step, sbm, bmn, slice, x, ld, mb, &ready);
+            else
+                sell_slice<AgeT, false, SHED>(a, step, bm, bmn, slice, x, ld);
+        }
+    }
+}
+
 template <typename AgeT, bool SHED>
 __global__ void __launch_bounds__(kSmemThreads, 1) sell_smem_kernel(const __grid_constant__ StepArgs a)
 {
@@ -609,42 +699,11 @@ __global__ void __launch_bounds__(kSmemThreads, 1) sell_smem_kernel(const __grid
     __syncthreads();
     LaneDeltas ld;
     bool ready = !use_smem;
-    const int W = (int)gridDim.x * (kSmemThreads / 32);
-    const int first = (int)blockIdx.x * (kSmemThreads / 32) + warp;
-    // states of the slices first + (4g + u) W, u = 0..3, packed one byte each
-    auto load_group = [&](int base) -> uint32_t {
-        uint32_t xs = 0;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int sl = base + u * W;
-            const int i = sl * 32 + lane;
-            const uint32_t x = (sl < a.n_slices && i < a.n_thr) ? (uint32_t)a.X[i] : (uint32_t)kR;
-            xs |= x << (8 * u);
-        }
-        return xs;
-    };
-    uint32_t xs_next = load_group(first);
-    for (int base = first; base < a.n_slices; base += 4 * W) {
-        const uint32_t xs = xs_next;
-        if (base + 4 * W < a.n_slices)
-            xs_next = load_group(base + 4 * W);
-#pragma unroll 1
-        for (int u = 0; u < 4; ++u) {
-            const int slice = base + u * W;
-            if (slice >= a.n_slices)
-                break;
-            const int x = (int)((xs >> (8 * u)) & 0xffu);
-            if (__all_sync(kFull, x == kR) && (slice + 1) * 32 <= a.n_thr) {
-                if (lane == 0)
-                    bmn[slice] = 0u;
-                continue;
-            }
-            if (use_smem)
-                sell_slice<AgeT, true, SHED>(a, (uint32_t)k, sbm, bmn, slice, x, ld, mb, &ready);
-            else
-                sell_slice<AgeT, false, SHED>(a, (uint32_t)k, bm, bmn, slice, x, ld);
-        }
-    }
+    const SliceMap smap = slice_map(a);
+    if (smap.list)
+        smem_slices<AgeT, SHED, true>(a, (uint32_t)k, bm, sbm, bmn, use_smem, mb, ready, ld, smap);
+    else
+        smem_slices<AgeT, SHED, false>(a, (uint32_t)k, bm, sbm, bmn, use_smem, mb, ready, ld, smap);
     // the copy into this CTA's shared memory must have landed before it exits
     if (!ready && !mbar_wait(mb, 0u, kWaitLimit))
         record_error(a.ctl, kErrTmaTimeout);
@@ -773,6 +832,8 @@ __global__ void run_epilogue_kernel(DevCtl* ctl, unsigned long long* deltas, int
         for (int j = 0; j < K; ++j)
             t += (double)(dtrec ? dtrec[j] : dt);
         ctl->time = t;
+        ctl->act_sum += ctl->n_act;
+        ctl->n_act = 0ull;                 // the next launch sequence's refresh counts from 0
         ctl->step += K;
         if (out)
             ctl->row = row + K;
@@ -831,6 +892,50 @@ __global__ void from_original_kernel(const T* __restrict__ in, T* __restrict__ o
     const int o = blockIdx.x * blockDim.x + threadIdx.x;
     if (o < n)
         out[inv[o]] = in[o];
+}
+
+// Active-node compaction refresh (Section 5.6) for the gather form, at the
+// start of a launch sequence: lists the SELL slices that still hold a non-R
+// node (the last slice, whose bitmap word merge-class nodes may share, is
+// always listed) and clears both bitmap words of the others, which the steps
+// will no longer write (their nodes are R: no infectious bit can appear).
+// While fewer than half the nodes are R it writes "all slices" instead.
+// ctl->n_act is 0 on entry.
+__global__ void sell_compact_kernel(const __grid_constant__ StepArgs a)
+{
+    if ((int64_t)a.ctl->counts[3] * 2 < (int64_t)a.n) {
+        if (blockIdx.x == 0 && threadIdx.x == 0)
+            a.ctl->n_act = (unsigned long long)a.n_slices;
+        return;
+    }
+    const int lane = threadIdx.x & 31;
+    const int stride = (int)(gridDim.x * blockDim.x);
+    for (int t0 = (int)(blockIdx.x * blockDim.x) + (int)(threadIdx.x & ~31u); t0 < a.n_slices; t0 += stride) {
+        const int t = t0 + lane;
+        bool live = false;
+        if (t < a.n_slices) {
+            if ((t + 1) * 32 > a.n_thr) {
+                live = true;
+            } else {
+                const uint4 x0 = *reinterpret_cast<const uint4*>(a.X + (int64_t)t * 32);
+                const uint4 x1 = *reinterpret_cast<const uint4*>(a.X + (int64_t)t * 32 + 16);
+                live = (x0.x & x0.y & x0.z & x0.w & x1.x & x1.y & x1.z & x1.w) != 0x03030303u;
+                if (!live) {
+                    a.bm[0][t] = 0u;
+                    a.bm[1][t] = 0u;
+                }
+            }
+        }
+        const uint32_t b = __ballot_sync(kFull, live);
+        if (b) {
+            unsigned long long base = 0ull;
+            if (lane == 0)
+                base = atomicAdd(&a.ctl->n_act, (unsigned long long)__popc(b));
+            base = __shfl_sync(kFull, base, 0);
+            if (live)
+                a.act[base + __popc(b & ((1u << lane) - 1u))] = t;
+        }
+    }
 }
 
 // infectivity of the I nodes at the current step (after init or set_state)
@@ -1010,6 +1115,15 @@ cudaError_t launch_from_original(const void* in, void* out, int elem_bytes, cons
         from_original_kernel<uint16_t><<<blocks, 256, 0, s>>>((const uint16_t*)in, (uint16_t*)out, inv, n);
     else
         from_original_kernel<uint32_t><<<blocks, 256, 0, s>>>((const uint32_t*)in, (uint32_t*)out, inv, n);
+    g_launch_count += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sell_compact(const StepArgs& a, cudaStream_t s, int num_sms)
+{
+    const int need = (a.n_slices + 255) / 256;
+    const int grid = std::max(1, std::min(need, num_sms * 8));
+    sell_compact_kernel<<<grid, 256, 0, s>>>(a);
     g_launch_count += 1;
     return cudaGetLastError();
 }
