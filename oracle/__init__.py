@@ -28,7 +28,7 @@ _lock = threading.Lock()
 _lib = None
 
 S, E, I, R = 0, 1, 2, 3
-SIR, SEIR = 0, 1
+SIR, SEIR, SIS = 0, 1, 2
 LAW_NONE, LAW_EXP, LAW_LOGNORMAL, LAW_WEIBULL, LAW_ERLANG = 0, 1, 2, 3, 4
 AGE_F32, AGE_F16, AGE_BF16 = 0, 1, 2
 SHED_NONE, SHED_HAZARD, SHED_DENSITY = 0, 1, 2
@@ -123,6 +123,20 @@ def lib():
             L.fso_step_rho.argtypes = [ctypes.c_int64, i64p, i32p, P(Params), ctypes.c_int64,
                                        u8p, f32p, f32p, u8p, f32p, f32p, f64p, f64p]
             L.fso_step_rho.restype = ctypes.c_int
+            L.fso_markov_tau.argtypes = [ctypes.c_int64, i64p, i32p, P(Params), ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, u8p, f64p, f64p]
+            L.fso_markov_tau.restype = ctypes.c_float
+            L.fso_markov_step.argtypes = [ctypes.c_int64, i64p, i32p, P(Params), ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_float, ctypes.c_int64, u8p, f32p, u8p, f32p,
+                                          f64p, f32p]
+            L.fso_markov_step.restype = ctypes.c_int
+            L.fso_markov_run.argtypes = [ctypes.c_int64, i64p, i32p, P(Params), ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_int64, ctypes.c_int64, ctypes.c_double, u8p, f32p,
+                                         u32p, P(ctypes.c_int64)]
+            L.fso_markov_run.restype = ctypes.c_int
+            L.fso_gillespie_run.argtypes = [ctypes.c_int64, i64p, i32p, P(Params), i32p, ctypes.c_int64,
+                                            ctypes.c_int32, ctypes.c_uint64, ctypes.c_int64, ctypes.c_double, u32p]
+            L.fso_gillespie_run.restype = ctypes.c_int
             L.fso_run.argtypes = [ctypes.c_int64, i64p, i32p, P(Params), ctypes.c_int64,
                                   ctypes.c_int64, u8p, f32p, u32p]
             L.fso_run.restype = ctypes.c_int
@@ -256,6 +270,70 @@ def step_rho(row_ptr, col_ind, prm: Params, k: int, X, A, rho_in=None):
     if rc:
         raise ValueError("oracle step rejected the state or the parameters")
     return Xn, An, rout, margin, lam
+
+
+def markov_tau(row_ptr, col_ind, prm: Params, theta: float, p_max: float, tau_max: float, X):
+    """Algorithm 1's step size for state X: (tau as float, Lambda, max lambda)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col_ind, dtype=np.int32)
+    X = np.ascontiguousarray(X, dtype=np.uint8)
+    lam, lmax = ctypes.c_double(), ctypes.c_double()
+    tau = lib().fso_markov_tau(X.size, _ptr(rp, ctypes.c_int64), _ptr(ci, ctypes.c_int32), ctypes.byref(prm),
+                               theta, p_max, tau_max, _ptr(X, ctypes.c_uint8), ctypes.byref(lam),
+                               ctypes.byref(lmax))
+    return tau, lam.value, lmax.value
+
+
+def markov_step(row_ptr, col_ind, prm: Params, theta: float, p_max: float, tau_max: float, k: int, X, A,
+                tau_in: float = 0.0):
+    """One step of Algorithm 1 (tau_in > 0 overrides the rule). Returns (Xn, An, margin, tau)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col_ind, dtype=np.int32)
+    X = np.ascontiguousarray(X, dtype=np.uint8)
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    Xn = np.empty_like(X)
+    An = np.empty_like(A)
+    margin = np.empty(X.size, dtype=np.float64)
+    tau = ctypes.c_float()
+    rc = lib().fso_markov_step(X.size, _ptr(rp, ctypes.c_int64), _ptr(ci, ctypes.c_int32), ctypes.byref(prm),
+                               theta, p_max, tau_max, float(tau_in), k, _ptr(X, ctypes.c_uint8),
+                               _ptr(A, ctypes.c_float), _ptr(Xn, ctypes.c_uint8), _ptr(An, ctypes.c_float),
+                               _ptr(margin, ctypes.c_double), ctypes.byref(tau))
+    if rc:
+        raise ValueError("oracle Markov step rejected the state or the parameters")
+    return Xn, An, margin, tau.value
+
+
+def markov_run(row_ptr, col_ind, prm: Params, theta: float, p_max: float, tau_max: float, k0: int,
+               n_grid: int, grid_dt: float, X, A):
+    """Algorithm 1 steps until t = (n_grid - 1) grid_dt; returns (counts[n_grid, 4], X, A, steps)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col_ind, dtype=np.int32)
+    X = np.array(X, dtype=np.uint8, copy=True)
+    A = np.array(A, dtype=np.float32, copy=True)
+    cnt = np.zeros((n_grid, 4), dtype=np.uint32)
+    steps = ctypes.c_int64()
+    rc = lib().fso_markov_run(X.size, _ptr(rp, ctypes.c_int64), _ptr(ci, ctypes.c_int32), ctypes.byref(prm),
+                              theta, p_max, tau_max, k0, n_grid, grid_dt, _ptr(X, ctypes.c_uint8),
+                              _ptr(A, ctypes.c_float), _ptr(cnt, ctypes.c_uint32), ctypes.byref(steps))
+    if rc:
+        raise ValueError("oracle Markov run failed")
+    return cnt, X, A, steps.value
+
+
+def gillespie_run(row_ptr, col_ind, prm: Params, index_nodes, index_state: int, rng_seed: int,
+                  n_grid: int, grid_dt: float) -> np.ndarray:
+    """Exact Doob-Gillespie run; counts[n_grid, 4] at t = g * grid_dt."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col_ind, dtype=np.int32)
+    idx = np.ascontiguousarray(index_nodes, dtype=np.int32)
+    cnt = np.zeros((n_grid, 4), dtype=np.uint32)
+    rc = lib().fso_gillespie_run(rp.size - 1, _ptr(rp, ctypes.c_int64), _ptr(ci, ctypes.c_int32),
+                                 ctypes.byref(prm), _ptr(idx, ctypes.c_int32), idx.size, index_state, rng_seed,
+                                 n_grid, grid_dt, _ptr(cnt, ctypes.c_uint32))
+    if rc:
+        raise ValueError("Gillespie run failed")
+    return cnt
 
 
 def run(row_ptr, col_ind, prm: Params, k0: int, steps: int, X, A):

@@ -646,3 +646,304 @@ int fso_exact_run(int64_t n, const int64_t* row_ptr, const int32_t* col_ind,
     free(X); free(t_exit); free(c); free(out_ptr); free(out_ind); free(fill);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Markovian engine (Section 4, Algorithm 1): constant rates, tau-leaping    */
+/* with the step chosen from the total and the largest rate.               */
+/* ------------------------------------------------------------------------ */
+static int markov_params_ok(const fso_params* prm)
+{
+    if (prm->model != FSO_SIR && prm->model != FSO_SIS && prm->model != FSO_SEIR)
+        return 0;
+    if (prm->infectious.kind != FSO_LAW_EXP)
+        return 0;
+    if (prm->model == FSO_SEIR && prm->latent.kind != FSO_LAW_EXP)
+        return 0;
+    return 1;
+}
+
+/* rate of node i of state X (Eq. 3 for S with rho = beta 1{X_j = I}) */
+static double markov_rate(int64_t i, const int64_t* row_ptr, const int32_t* col_ind,
+                          const fso_params* prm, const uint8_t* X)
+{
+    switch (X[i]) {
+    case FSO_S: {
+        int64_t c = 0;
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+            if (X[col_ind[e]] == FSO_I)
+                c += 1;
+        return prm->beta * (double)c;
+    }
+    case FSO_E:
+        return prm->latent.a;
+    case FSO_I:
+        return prm->infectious.a;
+    default:
+        return 0.0;
+    }
+}
+
+float fso_markov_tau(int64_t n, const int64_t* row_ptr, const int32_t* col_ind,
+                     const fso_params* prm, double theta, double p_max, double tau_max,
+                     const uint8_t* X, double* Lambda, double* lambda_max)
+{
+    /* Lambda collected by compartment, so that its rounding is fixed:
+     * beta * (number of S-I edges) + sigma * |E| + gamma * |I| */
+    int64_t si = 0, ne = 0, ni = 0, cmax = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (X[i] == FSO_S) {
+            int64_t c = 0;
+            for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+                if (X[col_ind[e]] == FSO_I)
+                    c += 1;
+            si += c;
+            if (c > cmax)
+                cmax = c;
+        } else if (X[i] == FSO_E) {
+            ne += 1;
+        } else if (X[i] == FSO_I) {
+            ni += 1;
+        }
+    }
+    double sigma = prm->model == FSO_SEIR ? prm->latent.a : 0.0;
+    double gamma = prm->infectious.a;
+    double lam = prm->beta * (double)si + sigma * (double)ne + gamma * (double)ni;
+    double lmax = prm->beta * (double)cmax;
+    if (ne > 0 && sigma > lmax)
+        lmax = sigma;
+    if (ni > 0 && gamma > lmax)
+        lmax = gamma;
+    double tau = tau_max;
+    if (lam > 0.0 && theta * (double)n / lam < tau)
+        tau = theta * (double)n / lam;
+    if (lmax > 0.0 && p_max / lmax < tau)
+        tau = p_max / lmax;
+    if (Lambda)
+        *Lambda = lam;
+    if (lambda_max)
+        *lambda_max = lmax;
+    return (float)tau;
+}
+
+int fso_markov_step(int64_t n, const int64_t* row_ptr, const int32_t* col_ind,
+                    const fso_params* prm, double theta, double p_max, double tau_max, float tau_in,
+                    int64_t k, const uint8_t* X, const float* A, uint8_t* Xn, float* An,
+                    double* margin, float* tau_out)
+{
+    if (!markov_params_ok(prm))
+        return -1;
+    float tau = tau_in > 0.0f ? tau_in
+                              : fso_markov_tau(n, row_ptr, col_ind, prm, theta, p_max, tau_max, X, NULL, NULL);
+    if (tau_out)
+        *tau_out = tau;
+    for (int64_t i = 0; i < n; ++i) {
+        int x = X[i];
+        if (x > FSO_R || (x == FSO_E && prm->model != FSO_SEIR) || (x == FSO_R && prm->model == FSO_SIS))
+            return -1;
+        double lambda = markov_rate(i, row_ptr, col_ind, prm, X);
+        double p = (lambda > 0.0) ? -expm1(-lambda * (double)tau) : 0.0;
+        int fire = 0;
+        double mg = INFINITY;
+        if (p > 0.0) {
+            double u = fso_uniform(prm->seed, prm->rep, k, i);
+            fire = (u < p);
+            mg = u - p;
+        }
+        if (margin)
+            margin[i] = mg;
+        if (fire) {
+            int y;
+            if (x == FSO_S)
+                y = prm->model == FSO_SEIR ? FSO_E : FSO_I;
+            else if (x == FSO_E)
+                y = FSO_I;
+            else
+                y = prm->model == FSO_SIS ? FSO_S : FSO_R;
+            Xn[i] = (uint8_t)y;
+            An[i] = 0.0f;
+        } else {
+            Xn[i] = (uint8_t)x;
+            An[i] = (x == FSO_E || x == FSO_I) ? fso_age_next(A[i], (double)tau, prm->age_dtype) : 0.0f;
+        }
+    }
+    return 0;
+}
+
+/* Fenwick tree over the node rates (sums of ranges of rates; the total at
+ * the root); selection by descending the implicit tree */
+typedef struct {
+    int64_t n, top;
+    double* t;
+} fenwick;
+
+static void fw_add(fenwick* f, int64_t i, double v)
+{
+    for (int64_t j = i + 1; j <= f->n; j += j & -j)
+        f->t[j] += v;
+}
+
+static int64_t fw_find(const fenwick* f, double u)   /* smallest i with prefix(i+1) > u */
+{
+    int64_t pos = 0;
+    for (int64_t step = f->top; step > 0; step >>= 1) {
+        if (pos + step <= f->n && f->t[pos + step] <= u) {
+            pos += step;
+            u -= f->t[pos];
+        }
+    }
+    return pos < f->n ? pos : f->n - 1;
+}
+
+int fso_gillespie_run(int64_t n, const int64_t* row_ptr, const int32_t* col_ind,
+                      const fso_params* prm, const int32_t* index_nodes, int64_t n_index,
+                      int32_t index_state, uint64_t rng_seed, int64_t n_grid, double grid_dt,
+                      uint32_t* counts_grid)
+{
+    if (!markov_params_ok(prm) || n <= 0)
+        return -1;
+    int64_t nnz = row_ptr[n];
+    uint8_t* X = (uint8_t*)malloc((size_t)n);
+    int64_t* c = (int64_t*)calloc((size_t)n, sizeof(int64_t));
+    double* rate = (double*)calloc((size_t)n, sizeof(double));
+    int64_t* out_ptr = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+    int32_t* out_ind = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
+    int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+    fenwick f = { n, 1, (double*)calloc((size_t)n + 1, sizeof(double)) };
+    if (!X || !c || !rate || !out_ptr || !out_ind || !fill || !f.t) {
+        free(X); free(c); free(rate); free(out_ptr); free(out_ind); free(fill); free(f.t);
+        return -1;
+    }
+    while (f.top * 2 <= n)
+        f.top *= 2;
+    for (int64_t e = 0; e < nnz; ++e)
+        out_ptr[col_ind[e] + 1] += 1;
+    for (int64_t i = 0; i < n; ++i)
+        out_ptr[i + 1] += out_ptr[i];
+    for (int64_t i = 0; i < n; ++i)
+        fill[i] = out_ptr[i];
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+            out_ind[fill[col_ind[e]]++] = (int32_t)i;
+
+    const double sigma = prm->model == FSO_SEIR ? prm->latent.a : 0.0;
+    const double gamma = prm->infectious.a;
+    for (int64_t i = 0; i < n; ++i)
+        X[i] = FSO_S;
+    for (int64_t q = 0; q < n_index; ++q)
+        X[index_nodes[q]] = (uint8_t)index_state;
+    for (int64_t i = 0; i < n; ++i)
+        if (X[i] == FSO_I)
+            for (int64_t e = out_ptr[i]; e < out_ptr[i + 1]; ++e)
+                c[out_ind[e]] += 1;
+    /* (re)sets the rate of node i in the tree */
+#define SET_RATE(i)                                                                  \
+    do {                                                                             \
+        double r_ = X[i] == FSO_S ? prm->beta * (double)c[i]                         \
+                  : X[i] == FSO_E ? sigma : X[i] == FSO_I ? gamma : 0.0;             \
+        fw_add(&f, (i), r_ - rate[i]);                                               \
+        rate[i] = r_;                                                                \
+    } while (0)
+    for (int64_t i = 0; i < n; ++i)
+        SET_RATE(i);
+
+    sm64 g = { rng_seed };
+    uint32_t cnt[4];
+    fso_counts(n, X, cnt);
+    double t = 0.0;
+    int64_t gi = 0, events = 0;
+    for (;;) {
+        /* the tree's running sums drift by rounding; rebuild them now and then */
+        if ((events & 4095) == 0) {
+            memset(f.t, 0, sizeof(double) * ((size_t)n + 1));
+            for (int64_t i = 0; i < n; ++i)
+                fw_add(&f, i, rate[i]);
+        }
+        double total = 0.0;
+        for (int64_t step = f.top, pos = 0; step > 0; step >>= 1)
+            if (pos + step <= n) {
+                pos += step;
+                total += f.t[pos];
+            }
+        double t_ev = (total > 0.0) ? t - log(sm64_open01(&g)) / total : INFINITY;
+        while (gi < n_grid && (double)gi * grid_dt < t_ev) {
+            memcpy(counts_grid + 4 * gi, cnt, sizeof(cnt));
+            ++gi;
+        }
+        if (gi >= n_grid || !(total > 0.0))
+            break;
+        t = t_ev;
+        int64_t i = fw_find(&f, sm64_open01(&g) * total);
+        while (rate[i] <= 0.0 && i + 1 < n)          /* rounding at a boundary */
+            ++i;
+        int x = X[i];
+        int y = x == FSO_S ? (prm->model == FSO_SEIR ? FSO_E : FSO_I)
+              : x == FSO_E ? FSO_I : (prm->model == FSO_SIS ? FSO_S : FSO_R);
+        X[i] = (uint8_t)y;
+        cnt[x] -= 1;
+        cnt[y] += 1;
+        if ((x == FSO_I) != (y == FSO_I)) {
+            int64_t d = (y == FSO_I) ? 1 : -1;
+            for (int64_t e = out_ptr[i]; e < out_ptr[i + 1]; ++e) {
+                int64_t j = out_ind[e];
+                c[j] += d;
+                if (X[j] == FSO_S)
+                    SET_RATE(j);
+            }
+        }
+        SET_RATE(i);
+        ++events;
+    }
+#undef SET_RATE
+    while (gi < n_grid) {
+        memcpy(counts_grid + 4 * gi, cnt, sizeof(cnt));
+        ++gi;
+    }
+    free(X); free(c); free(rate); free(out_ptr); free(out_ind); free(fill); free(f.t);
+    return 0;
+}
+
+int fso_markov_run(int64_t n, const int64_t* row_ptr, const int32_t* col_ind,
+                   const fso_params* prm, double theta, double p_max, double tau_max,
+                   int64_t k0, int64_t n_grid, double grid_dt, uint8_t* X, float* A,
+                   uint32_t* counts_grid, int64_t* steps_out)
+{
+    const size_t m = (size_t)(n > 0 ? n : 1);
+    uint8_t* X2 = (uint8_t*)malloc(m);
+    float* A2 = (float*)malloc(sizeof(float) * m);
+    if (!X2 || !A2) {
+        free(X2); free(A2);
+        return -1;
+    }
+    uint8_t* xc = X; float* ac = A;
+    uint8_t* xn = X2; float* an = A2;
+    double t = 0.0;
+    int64_t gi = 0, k = k0;
+    int rc = 0;
+    uint32_t cnt[4];
+    fso_counts(n, xc, cnt);
+    while (gi < n_grid) {
+        while (gi < n_grid && (double)gi * grid_dt <= t) {
+            memcpy(counts_grid + 4 * gi, cnt, sizeof(cnt));
+            ++gi;
+        }
+        if (gi >= n_grid)
+            break;
+        float tau = 0.0f;
+        rc = fso_markov_step(n, row_ptr, col_ind, prm, theta, p_max, tau_max, 0.0f, k, xc, ac, xn, an, NULL, &tau);
+        if (rc)
+            break;
+        t += (double)tau;
+        ++k;
+        fso_counts(n, xn, cnt);
+        uint8_t* tx = xc; xc = xn; xn = tx;
+        float* ta = ac; ac = an; an = ta;
+    }
+    if (steps_out)
+        *steps_out = k - k0;
+    if (xc != X) {
+        memcpy(X, xc, (size_t)n);
+        memcpy(A, ac, sizeof(float) * (size_t)n);
+    }
+    free(X2); free(A2);
+    return rc;
+}

@@ -28,7 +28,7 @@ extern "C" {
 #endif
 
 enum { FSO_S = 0, FSO_E = 1, FSO_I = 2, FSO_R = 3 };
-enum { FSO_SIR = 0, FSO_SEIR = 1 };
+enum { FSO_SIR = 0, FSO_SEIR = 1, FSO_SIS = 2 };
 enum { FSO_LAW_NONE = 0, FSO_LAW_EXP = 1, FSO_LAW_LOGNORMAL = 2,
        FSO_LAW_WEIBULL = 3, FSO_LAW_ERLANG = 4 };
 enum { FSO_AGE_F32 = 0, FSO_AGE_F16 = 1, FSO_AGE_BF16 = 2 };
@@ -136,6 +136,46 @@ int fso_run_adaptive(int64_t n, const int64_t* row_ptr, const int32_t* col_ind,
                      const fso_params* prm, double eps, double delta, double lambda_prev,
                      int64_t k0, int64_t steps, uint8_t* X, float* A, uint32_t* counts,
                      float* dts, double* lambda_last);
+
+/* ---- Markovian engine (Section 4, Algorithm 1) --------------------------- */
+/* Constant rates: an S node leaves at beta * c_i (c_i = its infectious
+ * in-neighbours), E at the latent rate sigma, I at the recovery rate gamma
+ * (EXP laws in prm). SIS: I -> S; SIR: I -> R; SEIR: S -> E -> I -> R.
+ * The step size of Algorithm 1 from the rates of the current state:
+ *   Lambda = sum_i lambda_i, tau = min(theta N / Lambda, p_max / max_i
+ *   lambda_i, tau_max) (a term is skipped when its denominator is 0),
+ * in double in that order, returned as the float the ages advance by. */
+float fso_markov_tau(int64_t n, const int64_t* row_ptr, const int32_t* col_ind,
+                     const fso_params* prm, double theta, double p_max, double tau_max,
+                     const uint8_t* X, double* Lambda, double* lambda_max);
+
+/* One step k of Algorithm 1: tau from fso_markov_tau (or tau_in if > 0),
+ * p_i = 1 - exp(-lambda_i tau), Bernoulli with the step's uniforms, the
+ * transitions, renewal ages (age 0 on a transition, E/I ages + tau stored
+ * as in fso_age_next). margin as in fso_step. *tau_out = the tau used.
+ * Returns 0 or -1 (bad state or parameters). */
+int fso_markov_step(int64_t n, const int64_t* row_ptr, const int32_t* col_ind,
+                    const fso_params* prm, double theta, double p_max, double tau_max, float tau_in,
+                    int64_t k, const uint8_t* X, const float* A, uint8_t* Xn, float* An,
+                    double* margin, float* tau_out);
+
+/* Algorithm 1 steps from k0 until the time reaches t_end: counts_grid[n_grid
+ * * 4] receives the counts of the state holding at t = g * grid_dt (the
+ * state after the last step ending at or before it); in place on (X, A);
+ * *steps_out = the steps taken. */
+int fso_markov_run(int64_t n, const int64_t* row_ptr, const int32_t* col_ind,
+                   const fso_params* prm, double theta, double p_max, double tau_max,
+                   int64_t k0, int64_t n_grid, double grid_dt, uint8_t* X, float* A,
+                   uint32_t* counts_grid, int64_t* steps_out);
+
+/* Exact Doob-Gillespie direct method for the same Markovian models: the
+ * next event after Exp(Lambda), the node chosen with probability
+ * lambda_i / Lambda (a Fenwick tree over the rates), its own splitmix64
+ * stream. counts_grid[n_grid * 4]: the counts at t = g * grid_dt. */
+int fso_gillespie_run(int64_t n, const int64_t* row_ptr, const int32_t* col_ind,
+                      const fso_params* prm, const int32_t* index_nodes, int64_t n_index,
+                      int32_t index_state, uint64_t rng_seed, int64_t n_grid, double grid_dt,
+                      uint32_t* counts_grid);
 
 /* ---- exact continuous-time simulator for tiny graphs -------------------- */
 /* Event-driven simulation of the same compartmental process without time
