@@ -66,11 +66,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-served", action="store_true", help="skip the served-vs-plain block")
     ap.add_argument("--workload", choices=["regular", "ensemble", "serving", "large", "precision", "shedding",
-                                           "compaction"],
+                                           "compaction", "markov"],
                     default="regular",
                     help="regular: the headline line; ensemble / serving: full-size packed and served runs; "
                          "shedding: constant vs age-dependent infectivity on regular d=8 and BA m=4 graphs; "
-                         "compaction: runs with and without the active-node list on ER d=8 and BA m=4")
+                         "compaction: runs with and without the active-node list on ER d=8 and BA m=4; "
+                         "markov: the Markovian engine's transitions per second on ER d=8 (SIS, SIR)")
     ap.add_argument("--age", choices=["f32", "f16"], default="f32", help="age storage of ensemble/serving runs")
     ap.add_argument("--ens-graphs", type=int, default=64, help="graphs of the packed-ensemble run")
     ap.add_argument("--ens-steps", type=int, default=500, help="steps of the packed-ensemble run")
@@ -913,6 +914,49 @@ def compaction_bench(fs, torch, n: int, sim_steps: int, graph_steps: int, reps: 
     return res
 
 
+def markov_bench(fs, torch, n: int, sim_steps: int, graph_steps: int, reps: int = 3):
+    """The Markovian engine (Section 4, Algorithm 1) on the paper's
+    Markovian workload shape: Erdos-Renyi mean degree 8, beta = 0.25,
+    recovery 0.15, theta = 0.01, p_max = 0.1, tau_max = 0.1, 10 seeds per
+    10^3 nodes; SIS and SIR; `sim_steps` steps from the initial state
+    (event-timed CUDA Graph replays, ingest and init untimed, median of
+    `reps`). Transitions per second is the paper's Markovian figure
+    (1.95 * 10^7 / s at N = 10^6 on its hardware)."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    g = W.erdos_renyi(n, 8, seed=0)
+    idx = W.index_nodes(g.n, max(1, n // 100), seed=1)
+    K = graph_steps
+    full = sim_steps // K
+    gh = fs.fs_graph_create(g.n, g.row_ptr, g.col_ind)
+    res = {"workload": f"markov-er8-n{n:.0e}".replace("+0", ""), "sim_steps": full * K, "graph_steps": K,
+           "theta": 0.01, "p_max": 0.1, "tau_max": 0.1,
+           "timed": "CUDA Graph replays (3 launches per step), median of runs", "models": {}}
+    for mname, model in (("sis", fs.FS_SIS), ("sir", fs.FS_SIR)):
+        prm = fs.sim_params(model, fs.law("exp", 0.15), 0.25, 0.1, 3, theta=0.01, p_max=0.1)
+        rows = []
+        for r in range(reps + 1):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            sh = fs.fs_sim_init(gh, prm, idx)
+            ms = fs.fs_sim_run_timed(sh, full * K, K, None)
+            trans = fs.fs_sim_transitions(sh)
+            t_sim = fs.fs_sim_time(sh)[0]
+            c = fs.fs_sim_run(sh, 0)
+            fs.fs_sim_destroy(sh)
+            if r:
+                rows.append((float(np.sum(ms[:full])), trans, t_sim, c[-1]))
+        rows.sort(key=lambda x: x[0])
+        t_ms, trans, t_sim, cnt = rows[len(rows) // 2]
+        res["models"][mname] = {
+            "transitions_per_s": round(trans / (t_ms * 1e-3), 1), "transitions": int(trans),
+            "node_updates_per_s": round(g.n * full * K / (t_ms * 1e-3), 1), "ms_per_run": round(t_ms, 3),
+            "us_per_step": round(t_ms * 1e3 / (full * K), 3), "simulated_days": round(t_sim, 3),
+            "final_counts": [int(v) for v in cnt]}
+    fs.fs_graph_destroy(gh)
+    return res
+
+
 def run_extra(args):
     """Full-size packed-ensemble or serving runs (their own JSON line)."""
     import torch
@@ -924,6 +968,8 @@ def run_extra(args):
                              age_dtype=age, pressure=PRESSURE[args.pressure])
     elif args.workload == "precision":
         res = precision_bench(fs, torch, n=args.n, steps=args.sim_steps, reps=1000)
+    elif args.workload == "markov":
+        res = markov_bench(fs, torch, n=args.n, sim_steps=args.sim_steps, graph_steps=args.graph_steps)
     elif args.workload == "compaction":
         res = compaction_bench(fs, torch, n=args.n, sim_steps=args.sim_steps, graph_steps=args.graph_steps)
     elif args.workload == "shedding":

@@ -56,7 +56,7 @@ typedef enum {
 } fs_status;
 
 enum { FS_S = 0, FS_E = 1, FS_I = 2, FS_R = 3 };
-enum { FS_SIR = 0, FS_SEIR = 1 };
+enum { FS_SIR = 0, FS_SEIR = 1, FS_SIS = 2 };
 enum { FS_AGE_F32 = 0, FS_AGE_F16 = 1, FS_AGE_BF16 = 2 };
 enum { FS_DISPATCH_AUTO = 0, FS_DISPATCH_THREAD = 1, FS_DISPATCH_MERGE = 2, FS_DISPATCH_TUNE = 3 };
 /* How a realisation obtains the infection pressure of its S nodes (the count
@@ -158,6 +158,24 @@ typedef struct {
     double eps;          /* 0: fixed step; > 0: the tolerance (the paper uses 0.01-0.05) */
     double delta;        /* added to lambda*; 0 = 1e-12                            */
     fs_law shedding;     /* the law of s(tau) when shed_mode != FS_SHED_NONE       */
+    /* Markovian engine (Section 4, Algorithm 1), selected by theta > 0: all
+     * rates constant (infectious law, and latent law for SEIR, must be
+     * FS_LAW_EXP; SIS: I -> S, SIR / SEIR: I -> R); step k has the size
+     *   tau_k = min(theta N / Lambda, p_max / max_i lambda_i, dt)
+     * from the rates of the state at its start (Lambda = their sum; a term is
+     * skipped when its denominator is 0), computed in double from integer
+     * reductions (exact, schedule-independent) and applied as a float. The
+     * infection counts are exact integers kept for every node and updated
+     * after each step by +-1 along the transposed CSR from the nodes that
+     * entered or left I (Inertial Mode) or recounted from the rows (Control
+     * Mode); markov_mode picks: 0 by memory touched, 1 inertial, 2 control.
+     * Single realisations only (packed ensembles, the server and
+     * fs_step_noalloc reject it); eps, shedding and FS_ACTIVE_LIST must be
+     * off; the flags' pressure form is ignored. FS_SIS needs theta > 0. */
+    double theta;        /* 0: renewal engine; > 0: Algorithm 1 (the paper uses 0.01) */
+    double p_max;        /* largest per-step probability (0 = 0.1, the paper's)   */
+    int32_t markov_mode; /* 0 auto, 1 inertial, 2 control                          */
+    int32_t reserved2_;  /* must be 0                                              */
 } fs_sim_params;
 
 /* Graph construction options (all fields may be 0 for the defaults). */
@@ -292,7 +310,8 @@ fs_status fs_sim_set_state(fs_sim* s, const uint8_t* state, const void* age, int
 
 /* Simulated time: *elapsed (may be NULL) = the sum of the step sizes of the
  * steps run since init or set_state; *next_dt (may be NULL) = the size of the
- * next step (dt for a fixed step). Synchronous. */
+ * next step (dt for a fixed step; 0 for the Markovian engine, whose next
+ * step size depends on the rates of the state it starts from). Synchronous. */
 fs_status fs_sim_time(const fs_sim* s, double* elapsed, float* next_dt);
 
 /* Active-node compaction accounting (FS_ACTIVE_LIST): *listed = the sum over
@@ -301,6 +320,10 @@ fs_status fs_sim_time(const fs_sim* s, double* elapsed, float* next_dt);
  * units (SELL slices in the gather form, push items in the push form; 0
  * without FS_ACTIVE_LIST). Synchronous. */
 fs_status fs_sim_active_units(const fs_sim* s, uint64_t* listed, uint64_t* units);
+
+/* *total = the node transitions (S -> E/I, E -> I, I -> R/S) of the steps
+ * run since init or set_state. Synchronous. */
+fs_status fs_sim_transitions(const fs_sim* s, uint64_t* total);
 
 /* The infectivity the next step reads (Eq. 8): rho[i] = beta s(tau_i) as
  * stored (age_dtype storage: float / binary16 / bfloat16 bits, n elements,

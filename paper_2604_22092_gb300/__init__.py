@@ -19,22 +19,22 @@ from . import _abi
 from ._abi import (FS_AGE_BF16, FS_AGE_F16, FS_AGE_F32, FS_DISPATCH_AUTO, FS_DISPATCH_MERGE,
                    FS_DISPATCH_THREAD, FS_DISPATCH_TUNE, FS_E, FS_I, FS_LAW_ERLANG, FS_LAW_EXP, FS_LAW_LOGNORMAL,
                    FS_LAW_NONE, FS_LAW_WEIBULL, FS_PRESSURE_AUTO, FS_PRESSURE_GATHER, FS_PRESSURE_PUSH, FS_R,
-                   FS_S, FS_SEIR, FS_SHED_DENSITY, FS_SHED_HAZARD, FS_SHED_NONE, FS_SIR, FS_ACTIVE_LIST, FsError,
-                   check)
+                   FS_S, FS_SEIR, FS_SHED_DENSITY, FS_SHED_HAZARD, FS_SHED_NONE, FS_SIR, FS_SIS, FS_ACTIVE_LIST,
+                   FsError, check)
 
 __all__ = [
     "fs_version", "fs_last_error", "fs_graph_create", "fs_graph_info_get", "fs_graph_destroy",
     "fs_sim_init", "fs_sim_step", "fs_sim_run", "fs_sim_run_async", "fs_sim_sync", "fs_sim_run_timed",
     "fs_kernel_launches", "fs_tune_stats", "fs_tune_reset",
     "fs_sim_get_state", "fs_sim_set_state", "fs_sim_work", "fs_sim_pressure_get", "fs_sim_time",
-    "fs_sim_infectivity_get", "fs_sim_active_units", "fs_sim_destroy",
+    "fs_sim_infectivity_get", "fs_sim_active_units", "fs_sim_transitions", "fs_sim_destroy",
     "fs_eval_hazard", "fs_eval_density",
     "fs_eval_uniforms", "fs_step_noalloc", "fs_ens_create", "fs_ens_run", "fs_ens_get_state",
     "fs_ens_destroy", "fs_batch_create", "fs_batch_add", "fs_batch_run", "fs_batch_status", "fs_batch_destroy",
     "fs_server_create", "fs_server_submit", "fs_server_poll", "fs_server_drain", "fs_server_stats_get",
     "fs_server_destroy",
     "law", "sim_params", "graph_opts", "FsError", "load",
-    "FS_S", "FS_E", "FS_I", "FS_R", "FS_SIR", "FS_SEIR", "FS_AGE_F32", "FS_AGE_F16", "FS_AGE_BF16",
+    "FS_S", "FS_E", "FS_I", "FS_R", "FS_SIR", "FS_SEIR", "FS_SIS", "FS_AGE_F32", "FS_AGE_F16", "FS_AGE_BF16",
     "FS_DISPATCH_AUTO", "FS_DISPATCH_THREAD", "FS_DISPATCH_MERGE", "FS_DISPATCH_TUNE",
     "FS_PRESSURE_AUTO", "FS_PRESSURE_GATHER", "FS_PRESSURE_PUSH", "FS_SHED_NONE", "FS_SHED_HAZARD",
     "FS_SHED_DENSITY", "FS_ACTIVE_LIST",
@@ -89,17 +89,20 @@ def sim_params(model: int, infectious: _abi.fs_law, beta: float, dt: float, seed
                latent: _abi.fs_law | None = None, replicate: int = 0, index_state: int | None = None,
                age_dtype: int = FS_AGE_F32, pressure: int = FS_PRESSURE_AUTO, eps: float = 0.0,
                delta: float = 0.0, shed_mode: int = FS_SHED_NONE,
-               shedding: _abi.fs_law | None = None) -> _abi.fs_sim_params:
+               shedding: _abi.fs_law | None = None, theta: float = 0.0, p_max: float = 0.0,
+               markov_mode: int = 0) -> _abi.fs_sim_params:
     """pressure: FS_PRESSURE_AUTO / FS_PRESSURE_GATHER / FS_PRESSURE_PUSH, optionally
     | FS_ACTIVE_LIST (the flags field);
     eps > 0: adaptive step with dt as its cap (delta 0 = 1e-12);
-    shed_mode / shedding: the shedding profile s(tau) of the infectivity (FS_SHED_NONE: s = 1)."""
+    shed_mode / shedding: the shedding profile s(tau) of the infectivity (FS_SHED_NONE: s = 1);
+    theta > 0: the Markovian engine (Algorithm 1) with p_max (0 = 0.1) and dt as tau_max."""
     if index_state is None:
         index_state = FS_E if model == FS_SEIR else FS_I
     return _abi.fs_sim_params(int(model), int(age_dtype), latent if latent is not None else law("none"),
                               infectious, float(beta), float(dt), int(seed), int(replicate),
                               int(index_state), int(pressure), int(shed_mode), float(eps), float(delta),
-                              shedding if shedding is not None else law("none"))
+                              shedding if shedding is not None else law("none"), float(theta), float(p_max),
+                              int(markov_mode), 0)
 
 
 def graph_opts(dispatch: int = FS_DISPATCH_AUTO, thread_max_deg: int = 0,
@@ -241,6 +244,13 @@ def fs_sim_active_units(s: int) -> tuple[int, int]:
     a, u = ctypes.c_uint64(), ctypes.c_uint64()
     check(load().fs_sim_active_units(s, ctypes.byref(a), ctypes.byref(u)), "fs_sim_active_units")
     return a.value, u.value
+
+
+def fs_sim_transitions(s: int) -> int:
+    """Node transitions of the steps run since init or set_state."""
+    t = ctypes.c_uint64()
+    check(load().fs_sim_transitions(s, ctypes.byref(t)), "fs_sim_transitions")
+    return t.value
 
 
 def fs_sim_pressure_get(s: int) -> int:

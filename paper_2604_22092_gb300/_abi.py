@@ -15,7 +15,7 @@ FS_OK, FS_EINVAL, FS_ENOMEM, FS_ECUDA, FS_ETIMEOUT, FS_EBUSY, FS_ESTATE, FS_EUNS
 STATUS_NAMES = {0: "FS_OK", 1: "FS_EINVAL", 2: "FS_ENOMEM", 3: "FS_ECUDA", 4: "FS_ETIMEOUT",
                 5: "FS_EBUSY", 6: "FS_ESTATE", 7: "FS_EUNSUPPORTED"}
 FS_S, FS_E, FS_I, FS_R = 0, 1, 2, 3
-FS_SIR, FS_SEIR = 0, 1
+FS_SIR, FS_SEIR, FS_SIS = 0, 1, 2
 FS_AGE_F32, FS_AGE_F16, FS_AGE_BF16 = 0, 1, 2
 FS_DISPATCH_AUTO, FS_DISPATCH_THREAD, FS_DISPATCH_MERGE, FS_DISPATCH_TUNE = 0, 1, 2, 3
 FS_PRESSURE_AUTO, FS_PRESSURE_GATHER, FS_PRESSURE_PUSH = 0, 1, 2
@@ -36,7 +36,8 @@ class fs_sim_params(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("replicate", ctypes.c_uint32),
                 ("index_state", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("shed_mode", ctypes.c_int32), ("eps", ctypes.c_double), ("delta", ctypes.c_double),
-                ("shedding", fs_law)]
+                ("shedding", fs_law), ("theta", ctypes.c_double), ("p_max", ctypes.c_double),
+                ("markov_mode", ctypes.c_int32), ("reserved2_", ctypes.c_int32)]
 
 
 class fs_graph_opts(ctypes.Structure):
@@ -89,6 +90,7 @@ PROTOTYPES = {
     "fs_sim_time": (ctypes.c_int, [VP, P(ctypes.c_double), P(ctypes.c_float)]),
     "fs_sim_infectivity_get": (ctypes.c_int, [VP, VP]),
     "fs_sim_active_units": (ctypes.c_int, [VP, P(ctypes.c_uint64), P(ctypes.c_uint64)]),
+    "fs_sim_transitions": (ctypes.c_int, [VP, P(ctypes.c_uint64)]),
     "fs_sim_destroy": (ctypes.c_int, [VP]),
     "fs_eval_hazard": (ctypes.c_int, [P(fs_law), VP, VP, ctypes.c_int64, VP]),
     "fs_eval_density": (ctypes.c_int, [P(fs_law), VP, VP, ctypes.c_int64, VP]),

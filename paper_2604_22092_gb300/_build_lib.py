@@ -13,7 +13,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libflashstep.so")
 
-SOURCES = ["fs_api.cu", "fs_step.cu", "fs_push.cu", "fs_ingest.cu", "fs_pack.cu", "fs_pack_api.cu", "fs_server.cpp",
+SOURCES = ["fs_api.cu", "fs_step.cu", "fs_push.cu", "fs_markov.cu", "fs_ingest.cu", "fs_pack.cu", "fs_pack_api.cu", "fs_server.cpp",
            "fs_tune.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v",

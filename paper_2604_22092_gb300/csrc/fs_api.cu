@@ -148,8 +148,20 @@ fs_status check_params(const fs_sim_params* p)
 {
     if (!p)
         return fail(FS_EINVAL, "params is NULL");
-    if (p->model != FS_SIR && p->model != FS_SEIR)
-        return fail(FS_EINVAL, "model must be FS_SIR or FS_SEIR");
+    if (p->model != FS_SIR && p->model != FS_SEIR && p->model != FS_SIS)
+        return fail(FS_EINVAL, "model must be FS_SIR, FS_SEIR or FS_SIS");
+    if (!finite(p->theta) || p->theta < 0 || !finite(p->p_max) || p->p_max < 0 || p->p_max > 1)
+        return fail(FS_EINVAL, "theta must be finite and >= 0, p_max in [0, 1]");
+    if (p->markov_mode < 0 || p->markov_mode > 2 || p->reserved2_ != 0)
+        return fail(FS_EINVAL, "markov_mode must be 0, 1 or 2 and reserved2_ 0");
+    if (p->theta > 0) {
+        if (p->infectious.kind != FS_LAW_EXP || (p->model == FS_SEIR && p->latent.kind != FS_LAW_EXP))
+            return fail(FS_EINVAL, "the Markovian engine (theta > 0) needs FS_LAW_EXP holding times");
+        if (p->eps > 0 || p->shed_mode != FS_SHED_NONE || (p->flags & FS_ACTIVE_LIST))
+            return fail(FS_EUNSUPPORTED, "the Markovian engine runs without eps, shedding and FS_ACTIVE_LIST");
+    } else if (p->model == FS_SIS) {
+        return fail(FS_EUNSUPPORTED, "FS_SIS runs in the Markovian engine (theta > 0)");
+    }
     if (p->age_dtype < FS_AGE_F32 || p->age_dtype > FS_AGE_BF16)
         return fail(FS_EINVAL, "age_dtype must be FS_AGE_F32, FS_AGE_F16 or FS_AGE_BF16");
     if (!finite(p->beta) || p->beta < 0)
@@ -251,6 +263,17 @@ fs::StepArgs step_args(const fs_sim* s, int j)
     a.shed_mode = s->p.shed_mode;
     a.rtab = s->d_rtab;
     a.act = s->d_act;
+    a.mk_cnt = s->d_mk_cnt;
+    a.mk_ev = s->d_mk_ev;
+    a.mk_beta = s->p.beta;
+    a.mk_sigma = s->p.model == FS_SEIR ? s->p.latent.a : 0.0;
+    a.mk_gamma = s->p.infectious.a;
+    a.mk_theta = s->p.theta;
+    a.mk_p_max = s->p.p_max > 0 ? s->p.p_max : 0.1;
+    a.mk_tau_max = s->p.dt;
+    a.mk_avg_deg = g->n ? (double)g->nnz / (double)g->n : 0.0;
+    a.e_total = g->nnz;
+    a.mk_mode = s->p.markov_mode;
     a.dtrec = s->d_dtrec;
     return a;
 }
@@ -642,13 +665,15 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
     if (shed && pform == FS_PRESSURE_PUSH)
         return fail(FS_EUNSUPPORTED, "a shedding profile needs the gather form of the pressure (the push form "
                                      "keeps integer infectious counts)");
+    const bool markov = params->theta > 0;
     if (params->eps > 0 && (shed || pform == FS_PRESSURE_GATHER || !push_available(g)))
         return fail(FS_EUNSUPPORTED, "the adaptive step (eps > 0) runs in the push form of the pressure only");
     fs_sim* s = new fs_sim();
     s->g = g;
     s->p = *params;
-    s->pressure = (shed || pform == FS_PRESSURE_GATHER || !push_available(g)) ? FS_PRESSURE_GATHER
-                                                                              : FS_PRESSURE_PUSH;
+    s->pressure = (markov || shed || pform == FS_PRESSURE_GATHER || !push_available(g)) ? FS_PRESSURE_GATHER
+                                                                                        : FS_PRESSURE_PUSH;
+    s->markov = markov;
     s->M = to_model(*params);
     s->age_bytes = params->age_dtype == FS_AGE_F32 ? 4 : 2;
     const int64_t n = g->n;
@@ -693,6 +718,8 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
     const size_t oPt = carve(sizeof(float4) * 2 * fs::kPTableN), oPs = carve(sizeof(float) * fs::kPSTableN);
     const size_t oIdx = carve(sizeof(int32_t) * (size_t)std::max<int64_t>(n_index, 1));
     const size_t oDt = carve(sizeof(float) * fs::kMaxGraphSteps);
+    const size_t oMkc = markov ? carve(sizeof(uint32_t) * n_pad) : 0;
+    const size_t oMke = markov ? carve(sizeof(uint32_t) * n_pad) : 0;
     // active-node compaction list: one entry per push item or SELL slice
     const bool compact = (params->flags & FS_ACTIVE_LIST) != 0;
     const size_t n_units = push ? ((size_t)g->n_thr + fs::kPushG - 1) / fs::kPushG + (size_t)g->n_m
@@ -727,8 +754,12 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
     s->d_ptab = reinterpret_cast<float4*>(base + oPt);
     s->d_ps = reinterpret_cast<float*>(base + oPs);
     d_idx = reinterpret_cast<int32_t*>(base + oIdx);
-    if (params->eps > 0)
+    if (params->eps > 0 || markov)
         s->d_dtrec = reinterpret_cast<float*>(base + oDt);
+    if (markov) {
+        s->d_mk_cnt = reinterpret_cast<uint32_t*>(base + oMkc);
+        s->d_mk_ev = reinterpret_cast<uint32_t*>(base + oMke);
+    }
     if (compact)
         s->d_act = reinterpret_cast<int32_t*>(base + oAct);
     if (shed) {
@@ -759,6 +790,10 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
     S_CUDA(fs::launch_refresh(s->d_X, (int)n, g->d_deg, s->d_bm[0], s->d_bm[1], s->d_ctl, cs));
     if (shed)
         S_CUDA(fs::launch_rho_init(step_args(s, 0), params->age_dtype, 0u, cs));
+    if (markov) {
+        S_CUDA(ensure_out_csr(g, cs));
+        S_CUDA(fs::launch_markov_recount(step_args(s, 0), cs, g->num_sms));
+    }
     if (push) {
         S_CUDA(ensure_out_csr(g, cs));
         S_CUDA(fs::launch_push_init(step_args(s, 0), cs, g->num_sms));   // counts and tallies are zero
@@ -775,6 +810,8 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
 static cudaError_t launch_one_step(fs_sim* s, int j)
 {
     const fs::StepArgs a = step_args(s, j);
+    if (s->markov)
+        return fs::launch_markov_step(a, s->p.age_dtype, s->stream, s->g->num_sms);
     if (s->pressure == FS_PRESSURE_PUSH && s->d_dtrec)
         return fs::launch_push_step_adaptive(a, s->p.age_dtype, s->stream, s->g->num_sms);
     if (s->pressure == FS_PRESSURE_PUSH)
@@ -843,7 +880,7 @@ static fs_status run_enqueue(fs_sim* s, int64_t steps, int32_t graph_steps, uint
                 FS_CUDA(s, cudaEventRecord(replay_ev[r], s->stream));
             FS_CUDA(s, cudaGraphLaunch(s->gexec, s->stream));
         }
-        fs::g_launch_count += (unsigned long long)full * (K + 1 + (s->d_act ? 1 : 0));
+        fs::g_launch_count += (unsigned long long)full * ((s->markov ? 3 : 1) * K + 1 + (s->d_act ? 1 : 0));
     }
     if (replay_ev)
         FS_CUDA(s, cudaEventRecord(replay_ev[full], s->stream));
@@ -1017,7 +1054,7 @@ fs_status fs_sim_set_state(fs_sim* s, const uint8_t* state, const void* age, int
     const int n = (int)g->n;
     for (int64_t i = 0; i < n; ++i) {
         const int x = state[i];
-        if (x > FS_R || (s->p.model == FS_SIR && x == FS_E))
+        if (x > FS_R || (s->p.model != FS_SEIR && x == FS_E) || (s->p.model == FS_SIS && x == FS_R))
             return fail(FS_EINVAL, "state[%lld] = %d is not a compartment of the model", (long long)i, x);
         if (!age_ok(age, s->p.age_dtype, i, x == FS_S || x == FS_R))
             return fail(FS_EINVAL, "age[%lld] invalid (S/R ages must be 0; E/I ages finite and >= 0)",
@@ -1054,6 +1091,8 @@ fs_status fs_sim_set_state(fs_sim* s, const uint8_t* state, const void* age, int
         FS_CUDA(s, push_reset(s));
     if (s->d_rho[0])
         FS_CUDA(s, fs::launch_rho_init(step_args(s, 0), s->p.age_dtype, (uint32_t)(step & 1), s->stream));
+    if (s->markov)
+        FS_CUDA(s, fs::launch_markov_recount(step_args(s, 0), s->stream, s->g->num_sms));
     FS_CUDA(s, cudaStreamSynchronize(s->stream));
     return FS_OK;
 }
@@ -1076,6 +1115,22 @@ fs_status fs_sim_active_units(const fs_sim* s, uint64_t* listed, uint64_t* units
         *units = s->pressure == FS_PRESSURE_PUSH
                      ? (uint64_t)(((int64_t)s->g->n_thr + fs::kPushG - 1) / fs::kPushG + s->g->n_m)
                      : (uint64_t)s->g->n_slices;
+    return FS_OK;
+}
+
+fs_status fs_sim_transitions(const fs_sim* s, uint64_t* total)
+{
+    if (!s || !total)
+        return fail(FS_EINVAL, "NULL argument");
+    if (s->failed)
+        return fail(FS_ESTATE, "sim is in a failed state");
+    fs::DevCtl c;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(&c, s->d_ctl, sizeof(c), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+        return fail(FS_ECUDA, "fs_sim_transitions: %s", cudaGetErrorString(e));
+    *total = c.transitions;
     return FS_OK;
 }
 
@@ -1137,8 +1192,8 @@ fs_status fs_sim_time(const fs_sim* s, double* elapsed, float* next_dt)
     if (elapsed)
         *elapsed = c.time;
     if (next_dt) {
-        float dt = s->M.dt;
-        if (s->d_dtrec) {
+        float dt = s->markov ? 0.0f : s->M.dt;       // Markovian: known only from the state's rates
+        if (s->d_dtrec && !s->markov) {
             // the device's own rule, in the same FP32 operations
             uint32_t bits = c.lam[(c.step + 2) % 3];
             float lp;
@@ -1318,6 +1373,8 @@ extern "C" fs_status fs_step_noalloc(const fs_graph* g, const fs_sim_params* par
         return fail(FS_EUNSUPPORTED, "fs_step_noalloc: a shedding profile needs the sim's infectivity buffers");
     if (pv.flags & FS_ACTIVE_LIST)
         return fail(FS_EUNSUPPORTED, "fs_step_noalloc: FS_ACTIVE_LIST needs the sim's launch sequences");
+    if (pv.theta > 0)
+        return fail(FS_EUNSUPPORTED, "fs_step_noalloc: the Markovian engine needs the sim's count buffers");
     if (step < 0 || step >= ((int64_t)1 << 32))
         return fail(FS_EINVAL, "fs_step_noalloc: step must be in [0, 2^32)");
     if (g->n_m > kNoAllocMaxMergeRows)

@@ -7,7 +7,7 @@
 namespace fs {
 
 enum { kS = 0, kE = 1, kI = 2, kR = 3 };
-enum { kSIR = 0, kSEIR = 1 };
+enum { kSIR = 0, kSEIR = 1, kSIS = 2 };
 enum { kLawNone = 0, kLawExp = 1, kLawLogNormal = 2, kLawWeibull = 3, kLawErlang = 4 };
 enum { kAgeF32 = 0, kAgeF16 = 1, kAgeBF16 = 2 };
 
@@ -50,6 +50,14 @@ constexpr int kStepCtasPerSm = 5;                 // resident step CTAs per SM (
 constexpr int kSmemThreads = 1024;                // one CTA per SM holding the bitmap in shared memory
 constexpr uint32_t kSmemBitmapMaxBytes = 200u * 1024u;   // bitmap sizes staged in shared memory
 
+// Markovian engine: the integer reductions of one state's rates
+struct MarkovSums {
+    unsigned long long si;        // sum over S nodes of their infectious in-neighbours
+    unsigned long long ne, ni;    // |E|, |I|
+    unsigned int cmax;            // largest count of an S node
+    unsigned int pad_;
+};
+
 // Device-resident control block of one simulation (the persistent scalars of
 // Algorithm 2: step counter; plus running counts and work accounting).
 struct DevCtl {
@@ -71,6 +79,12 @@ struct DevCtl {
     // launch sequence (moved into act_sum and reset to 0 by the epilogue)
     unsigned long long n_act;
     unsigned long long act_sum;   // sum over launch sequences of n_act
+    // Markovian engine: rate sums of step k in mk[k & 1] (step k clears
+    // mk[(k + 1) & 1] for the next reduction); events appended by a step
+    MarkovSums mk[2];
+    unsigned int mk_nev;
+    unsigned int pad3_;
+    unsigned long long transitions;   // node transitions since init / set_state
 };
 
 enum { kErrNone = 0, kErrTmaTimeout = 1, kErrBadState = 2, kErrBadGraph = 3 };
@@ -152,6 +166,15 @@ struct StepArgs {
     // start of the launch sequence, ctl->n_act of them (all units when
     // n_act >= their number): SELL slices (gather) or push items
     int32_t* act;
+    // Markovian engine (fs_markov.cu): exact infectious in-neighbour counts of
+    // every node, the step's event list, the rates and the step-size rule
+    uint32_t* mk_cnt;             // [n]
+    uint32_t* mk_ev;              // [n] node | bit 31 when it left I
+    double mk_beta, mk_sigma, mk_gamma;
+    double mk_theta, mk_p_max, mk_tau_max;
+    double mk_avg_deg;            // edges / nodes
+    int64_t e_total;              // edges
+    int32_t mk_mode;              // influence update: 0 by cost, 1 inertial, 2 control
 };
 
 enum { kShedNone = 0, kShedHazard = 1, kShedDensity = 2 };

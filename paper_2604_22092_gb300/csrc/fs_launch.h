@@ -37,6 +37,10 @@ cudaError_t launch_from_original(const void* in, void* out, int elem_bytes, cons
                                  cudaStream_t s);
 cudaError_t launch_eval_hazard(const LawF& L, const float* tau, float* h, int64_t n, cudaStream_t s);
 cudaError_t launch_eval_density(const LawF& L, const float* tau, float* f, int64_t n, cudaStream_t s);
+// Markovian engine: one step of Algorithm 1 (three launches), and the dense
+// recount of the counts (after init or set_state)
+cudaError_t launch_markov_step(const StepArgs& a, int age_dtype, cudaStream_t s, int num_sms);
+cudaError_t launch_markov_recount(const StepArgs& a, cudaStream_t s, int num_sms);
 // active-node compaction refreshes (a.act must be set): gather form (SELL
 // slices) and push form (push items)
 cudaError_t launch_sell_compact(const StepArgs& a, cudaStream_t s, int num_sms);

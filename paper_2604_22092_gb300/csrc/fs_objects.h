@@ -63,6 +63,10 @@ struct fs_sim {
     float2* d_mpart = nullptr;
     float4* d_rtab = nullptr;     // [kPTableN] memoised beta s(age)
     int32_t* d_act = nullptr;     // active-node compaction list (FS_ACTIVE_LIST)
+    // Markovian engine (p.theta > 0): exact counts and the step's event list
+    bool markov = false;
+    uint32_t* d_mk_cnt = nullptr;
+    uint32_t* d_mk_ev = nullptr;
     // push form of the pressure (pressure == FS_PRESSURE_PUSH)
     int pressure = FS_PRESSURE_GATHER;
     uint8_t* d_cnt8 = nullptr;

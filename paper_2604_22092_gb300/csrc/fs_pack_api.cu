@@ -210,6 +210,8 @@ fs_status fs_ens_create(fs_graph* g, const fs_sim_params* params, int32_t n_real
                         "fs_ens_create: packed ensembles keep s = 1 (shed_mode must be FS_SHED_NONE)");
         if (params[r].flags & FS_ACTIVE_LIST)
             return fail(FS_EUNSUPPORTED, "fs_ens_create: FS_ACTIVE_LIST is for single realisations");
+        if (params[r].theta > 0)
+            return fail(FS_EUNSUPPORTED, "fs_ens_create: the Markovian engine is for single realisations");
     }
     if (params[0].flags == FS_PRESSURE_PUSH && !fsapi::push_available(g))
         return fail(FS_EUNSUPPORTED, "fs_ens_create: FS_PRESSURE_PUSH needs in-degrees <= %d in the thread class",

@@ -803,21 +803,26 @@ __global__ void run_epilogue_kernel(DevCtl* ctl, unsigned long long* deltas, int
     __syncthreads();
     if (threadIdx.x == 0) {
         uint32_t c0 = ctl->counts[0], c1 = ctl->counts[1], c2 = ctl->counts[2], c3 = ctl->counts[3];
-        unsigned long long ds = ctl->ds_cur, dst = ctl->ds_total, st = ctl->s_total;
+        unsigned long long ds = ctl->ds_cur, dst = ctl->ds_total, st = ctl->s_total, trans = ctl->transitions;
         uint32_t* out = ctl->out;
         const int64_t row = ctl->row;
         for (int j = 0; j < K; ++j) {
             st += c0;
             dst += ds;
             const uint32_t l = (uint32_t)d[j][0], ei = (uint32_t)d[j][1], ir = (uint32_t)d[j][2];
+            trans += (unsigned long long)l + ei + ir;
             c0 -= l;
             if (model == kSEIR) {
                 c1 += l - ei;
                 c2 += ei - ir;
+                c3 += ir;
+            } else if (model == kSIS) {           // recoveries return to S
+                c0 += ir;
+                c2 += l - ir;
             } else {
                 c2 += l - ir;
+                c3 += ir;
             }
-            c3 += ir;
             ds -= d[j][3];
             if (out) {
                 uint32_t* o = out + (row + j) * 4;
@@ -826,6 +831,7 @@ __global__ void run_epilogue_kernel(DevCtl* ctl, unsigned long long* deltas, int
         }
         ctl->counts[0] = c0; ctl->counts[1] = c1; ctl->counts[2] = c2; ctl->counts[3] = c3;
         ctl->ds_cur = ds;
+        ctl->transitions = trans;
         ctl->ds_total = dst;
         ctl->s_total = st;
         double t = ctl->time;
