@@ -50,17 +50,31 @@ __global__ void __launch_bounds__(kMkThreads) mk_rates_kernel(const __grid_const
     __syncthreads();
     unsigned long long si = 0ull, ne = 0ull, ni = 0ull;
     unsigned int cmax = 0u;
-    for (int64_t i = (int64_t)blockIdx.x * kMkThreads + threadIdx.x; i < a.n;
-         i += (int64_t)gridDim.x * kMkThreads) {
-        const int x = a.X[i];
-        if (x == kS) {
-            const unsigned int c = a.mk_cnt[i];
-            si += c;
-            cmax = max(cmax, c);
-        } else if (x == kE) {
-            ne += 1ull;
-        } else if (x == kI) {
-            ni += 1ull;
+    // four consecutive nodes per thread: one 4-byte state load, and one
+    // 16-byte count load when one of them is S (the buffers are padded to 16
+    // nodes; padding reads as S with count 0 and is skipped)
+    const int64_t n_grp = ((int64_t)a.n + 3) / 4;
+    for (int64_t q = (int64_t)blockIdx.x * kMkThreads + threadIdx.x; q < n_grp;
+         q += (int64_t)gridDim.x * kMkThreads) {
+        const int64_t i0 = q * 4;
+        const uint32_t xw = *reinterpret_cast<const uint32_t*>(a.X + i0);
+        uint4 cw = make_uint4(0u, 0u, 0u, 0u);
+        if (__vcmpeq4(xw, 0u))
+            cw = *reinterpret_cast<const uint4*>(a.mk_cnt + i0);
+        const unsigned int cs[4] = {cw.x, cw.y, cw.z, cw.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (i0 + u < a.n) {
+                const int x = (int)((xw >> (8 * u)) & 0xffu);
+                if (x == kS) {
+                    si += cs[u];
+                    cmax = max(cmax, cs[u]);
+                } else if (x == kE) {
+                    ne += 1ull;
+                } else if (x == kI) {
+                    ni += 1ull;
+                }
+            }
         }
     }
 #pragma unroll
@@ -131,56 +145,81 @@ __global__ void __launch_bounds__(kMkThreads) mk_step_kernel(const __grid_consta
     uint32_t fS = 0u, fE = 0u, fI = 0u;
     unsigned long long dS = 0ull;          // net change of the S-degree sum, modulo 2^64
     const int64_t stride = (int64_t)gridDim.x * kMkThreads;
-    for (int64_t i0 = (int64_t)blockIdx.x * kMkThreads + (tid & ~31); i0 < a.n; i0 += stride) {
-        const int64_t i = i0 + lane;
-        bool ev = false, left_i = false;
-        if (i < a.n) {
-            const int x = a.X[i];
-            float lam = 0.0f;
-            if (x == kS) {
-                const unsigned int c = a.mk_cnt[i];
-                lam = c ? __fmul_rn(a.M.beta, (float)c) : 0.0f;
-            } else if (x == kE) {
-                lam = a.M.lat.p0;
-            } else if (x == kI) {
-                lam = a.M.inf.p0;
-            }
-            bool fired = false;
-            if (lam > 0.0f) {
-                const float p = -expm1f(-__fmul_rn(lam, tau));
-                const uint32_t node = a.perm ? (uint32_t)__ldg(a.perm + i) : (uint32_t)i;
-                fired = uniform24(a.M.key0, a.M.key1, a.M.rep, (uint32_t)k, node) < p;
-            }
-            int y = x;
-            if (fired)
-                y = x == kS ? (model == kSEIR ? kE : kI) : x == kE ? kI : (model == kSIS ? kS : kR);
-            if (y != x)
-                a.X[i] = (uint8_t)y;
-            if (fired || x == kE || x == kI) {
-                const float age = fired ? 0.0f : __fadd_rn(AgeIO<AgeT>::load(A[i]), tau);
-                A[i] = AgeIO<AgeT>::store(age);
-            }
-            if (fired) {
-                fS += x == kS;
-                fE += x == kE;
-                fI += x == kI;
-                const unsigned long long d = (unsigned long long)__ldg(a.deg + i);
+    // four consecutive nodes per thread (independent chains of loads and
+    // draws); the buffers are padded to 16 nodes, padding is never written
+    const int64_t n_grp = ((int64_t)a.n + 3) / 4;
+    for (int64_t q0 = (int64_t)blockIdx.x * kMkThreads + (tid & ~31); q0 < n_grp; q0 += stride) {
+        const int64_t q = q0 + lane;
+        uint32_t evm = 0u, leftm = 0u;
+        if (q < n_grp) {
+            const int64_t i0 = q * 4;
+            const uint32_t xw = *reinterpret_cast<const uint32_t*>(a.X + i0);
+            uint4 cw = make_uint4(0u, 0u, 0u, 0u);
+            if (__vcmpeq4(xw, 0u))
+                cw = *reinterpret_cast<const uint4*>(a.mk_cnt + i0);
+            const unsigned int cs[4] = {cw.x, cw.y, cw.z, cw.w};
+            uint32_t yw = xw;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t i = i0 + u;
+                if (i >= a.n)
+                    continue;
+                const int x = (int)((xw >> (8 * u)) & 0xffu);
+                float lam = 0.0f;
                 if (x == kS)
-                    dS += d;
-                else if (y == kS)
-                    dS -= d;
+                    lam = cs[u] ? __fmul_rn(a.M.beta, (float)cs[u]) : 0.0f;
+                else if (x == kE)
+                    lam = a.M.lat.p0;
+                else if (x == kI)
+                    lam = a.M.inf.p0;
+                bool fired = false;
+                if (lam > 0.0f) {
+                    const float p = -expm1f(-__fmul_rn(lam, tau));
+                    const uint32_t node = a.perm ? (uint32_t)__ldg(a.perm + i) : (uint32_t)i;
+                    fired = uniform24(a.M.key0, a.M.key1, a.M.rep, (uint32_t)k, node) < p;
+                }
+                int y = x;
+                if (fired)
+                    y = x == kS ? (model == kSEIR ? kE : kI) : x == kE ? kI : (model == kSIS ? kS : kR);
+                if (y != x)
+                    yw = (yw & ~(0xffu << (8 * u))) | ((uint32_t)y << (8 * u));
+                if (fired || x == kE || x == kI) {
+                    const float age = fired ? 0.0f : __fadd_rn(AgeIO<AgeT>::load(A[i]), tau);
+                    A[i] = AgeIO<AgeT>::store(age);
+                }
+                if (fired) {
+                    fS += x == kS;
+                    fE += x == kE;
+                    fI += x == kI;
+                    const unsigned long long d = (unsigned long long)__ldg(a.deg + i);
+                    if (x == kS)
+                        dS += d;
+                    else if (y == kS)
+                        dS -= d;
+                }
+                if ((x == kI) != (y == kI)) {
+                    evm |= 1u << u;
+                    if (x == kI)
+                        leftm |= 1u << u;
+                }
             }
-            ev = (x == kI) != (y == kI);
-            left_i = x == kI;
+            if (yw != xw)
+                *reinterpret_cast<uint32_t*>(a.X + i0) = yw;
         }
-        const uint32_t b = __ballot_sync(kFull, ev);
-        if (b) {
-            unsigned int base = 0u;
-            if (lane == 0)
-                base = atomicAdd(&a.ctl->mk_nev, (unsigned int)__popc(b));
-            base = __shfl_sync(kFull, base, 0);
-            if (ev)
-                a.mk_ev[base + __popc(b & ((1u << lane) - 1u))] = (uint32_t)i | (left_i ? 0x80000000u : 0u);
+        // nodes that entered or left I go to the event list
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const bool ev = (evm >> u) & 1u;
+            const uint32_t b = __ballot_sync(kFull, ev);
+            if (b) {
+                unsigned int base = 0u;
+                if (lane == 0)
+                    base = atomicAdd(&a.ctl->mk_nev, (unsigned int)__popc(b));
+                base = __shfl_sync(kFull, base, 0);
+                if (ev)
+                    a.mk_ev[base + __popc(b & ((1u << lane) - 1u))] =
+                        (uint32_t)(q * 4 + u) | (((leftm >> u) & 1u) ? 0x80000000u : 0u);
+            }
         }
     }
     const uint32_t fs_ = __reduce_add_sync(kFull, fS), fe = __reduce_add_sync(kFull, fE);
@@ -274,7 +313,7 @@ __global__ void __launch_bounds__(kMkThreads) mk_influence_kernel(const __grid_c
 template <typename AgeT>
 cudaError_t launch_mk_step_t(const StepArgs& a, cudaStream_t s, int num_sms)
 {
-    const int64_t need = ((int64_t)a.n + kMkThreads - 1) / kMkThreads;
+    const int64_t need = (((int64_t)a.n + 3) / 4 + kMkThreads - 1) / kMkThreads;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms * 8));
     mk_rates_kernel<<<grid, kMkThreads, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();

@@ -79,7 +79,8 @@ def test_markov_lockstep(torch_cuda, oracle_mod, model):
     fs.fs_sim_run(s, 300, graph_steps=50, want_counts=False)
     taus2, dec2 = markov_lockstep(oracle_mod, g, p, s, 40)
     assert dec + dec2 > 100_000
-    assert taus.min() < p.dt                          # the theta or p_max term binds
+    if model != fs.FS_SEIR:      # (SEIR: few events while the index nodes are latent)
+        assert taus.min() < p.dt                      # the theta or p_max term binds
     X, _, _ = fs.fs_sim_get_state(s, g.n)
     if model == fs.FS_SIS:
         assert not (X == fs.FS_R).any() and (X == fs.FS_I).sum() > 1000
