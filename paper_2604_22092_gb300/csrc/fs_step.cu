@@ -565,10 +565,12 @@ __device__ __forceinline__ void merge_chunk(const StepArgs& a, uint32_t step, co
 template <typename AgeT, bool HAS_MERGE, bool SHED>
 __global__ void __launch_bounds__(kStepThreads, kStepCtasPerSm) fused_step_kernel(const __grid_constant__ StepArgs a)
 {
-    // Programmatic dependent launch: this grid may start while the previous
-    // step drains; nothing it reads is touched before the previous grid has
-    // completed and flushed (griddepcontrol.wait), and the next step may be
-    // scheduled as soon as every CTA of this one has started.
+    // Ready for programmatic dependent launch (launch_step's pdl flag): such a
+    // grid may start while the previous step drains, so nothing it reads is
+    // touched before that grid has completed and flushed (griddepcontrol.wait),
+    // and the next step may be scheduled once every CTA of this one has
+    // started. Without the launch attribute both instructions do nothing; the
+    // step loop launches without it (graph kernel nodes measured faster).
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
     __shared__ unsigned long long s_delta[kDeltaFields];
