@@ -129,17 +129,22 @@ template <typename AgeT>
 __global__ void __launch_bounds__(kMkThreads) mk_step_kernel(const __grid_constant__ StepArgs a)
 {
     __shared__ unsigned long long s_delta[kDeltaFields];
+    __shared__ float s_tau;
     const int tid = threadIdx.x, lane = tid & 31;
     if (tid < kDeltaFields)
         s_delta[tid] = 0ull;
     const int64_t k = a.ctl->step + a.j;
-    const MarkovSums m = a.ctl->mk[k & 1];
-    const float tau = mk_tau(a, m);
-    if (blockIdx.x == 0 && tid == 0) {
-        a.dtrec[a.j] = tau;
-        a.ctl->mk[(k + 1) & 1] = MarkovSums{};   // for the next step's reduction
+    // tau once per block: double arithmetic is slow on this part, and every
+    // thread would compute the same value
+    if (tid == 0) {
+        s_tau = mk_tau(a, a.ctl->mk[k & 1]);
+        if (blockIdx.x == 0) {
+            a.dtrec[a.j] = s_tau;
+            a.ctl->mk[(k + 1) & 1] = MarkovSums{};   // for the next step's reduction
+        }
     }
     __syncthreads();
+    const float tau = s_tau;
     AgeT* __restrict__ A = static_cast<AgeT*>(a.A);
     const int model = a.M.model;
     uint32_t fS = 0u, fE = 0u, fI = 0u;
