@@ -331,7 +331,9 @@ fs_status fs_sim_transitions(const fs_sim* s, uint64_t* total);
  * FS_SHED_NONE (else FS_EUNSUPPORTED). Synchronous. */
 fs_status fs_sim_infectivity_get(fs_sim* s, void* rho);
 
-/* The pressure form the sim runs (FS_PRESSURE_GATHER or FS_PRESSURE_PUSH). */
+/* The pressure form the sim runs (FS_PRESSURE_GATHER or FS_PRESSURE_PUSH).
+ * The Markovian engine keeps its own exact counts (updated by pushes or
+ * recounts, see markov_mode) and reports FS_PRESSURE_GATHER. */
 fs_status fs_sim_pressure_get(const fs_sim* s, int32_t* pressure);
 
 /* Work accounting for the roofline model: the sum over all steps run so far

@@ -657,7 +657,8 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
                 return fail(FS_EINVAL, "index node %d repeated", v[q]);
         }
     }
-    const int pform = params->flags & FS_PRESSURE_MASK;
+    const bool markov = params->theta > 0;    // keeps its own exact counts: the pressure form is ignored
+    const int pform = markov ? FS_PRESSURE_AUTO : (params->flags & FS_PRESSURE_MASK);
     if (pform == FS_PRESSURE_PUSH && !push_available(g))
         return fail(FS_EUNSUPPORTED, "FS_PRESSURE_PUSH needs in-degrees <= %d in the thread class (thread_max_deg %d)",
                     fs::kMaxThreadDeg, g->t1);
@@ -665,7 +666,6 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
     if (shed && pform == FS_PRESSURE_PUSH)
         return fail(FS_EUNSUPPORTED, "a shedding profile needs the gather form of the pressure (the push form "
                                      "keeps integer infectious counts)");
-    const bool markov = params->theta > 0;
     if (params->eps > 0 && (shed || pform == FS_PRESSURE_GATHER || !push_available(g)))
         return fail(FS_EUNSUPPORTED, "the adaptive step (eps > 0) runs in the push form of the pressure only");
     fs_sim* s = new fs_sim();
