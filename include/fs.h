@@ -152,9 +152,9 @@ typedef struct {
      * age) and the first step after init or set_state uses dt. Computed in
      * FP32 on the device; ages advance by that value; hazards are evaluated
      * directly (no memoised tables, since ages leave the fixed-step
-     * sequence). Single realisations in the push form only (GATHER, or a
-     * graph without the push form: FS_EUNSUPPORTED); packed ensembles,
-     * batches and the server need eps = 0. */
+     * sequence). Single realisations, in either pressure form and with or
+     * without a shedding profile; packed ensembles, batches, the server and
+     * fs_step_noalloc need eps = 0. */
     double eps;          /* 0: fixed step; > 0: the tolerance (the paper uses 0.01-0.05) */
     double delta;        /* added to lambda*; 0 = 1e-12                            */
     fs_law shedding;     /* the law of s(tau) when shed_mode != FS_SHED_NONE       */

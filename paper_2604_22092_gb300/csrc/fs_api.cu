@@ -666,8 +666,6 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
     if (shed && pform == FS_PRESSURE_PUSH)
         return fail(FS_EUNSUPPORTED, "a shedding profile needs the gather form of the pressure (the push form "
                                      "keeps integer infectious counts)");
-    if (params->eps > 0 && (shed || pform == FS_PRESSURE_GATHER || !push_available(g)))
-        return fail(FS_EUNSUPPORTED, "the adaptive step (eps > 0) runs in the push form of the pressure only");
     fs_sim* s = new fs_sim();
     s->g = g;
     s->p = *params;

@@ -211,6 +211,12 @@ __device__ __forceinline__ float p_of_rate(const ModelF& M, float lambda)
     return lambda > 0.0f ? -expm1f(-__fmul_rn(lambda, M.dt)) : 0.0f;
 }
 
+// the same with the step's own size (adaptive step)
+__device__ __forceinline__ float p_of_rate_dt(float lambda, float dt)
+{
+    return lambda > 0.0f ? -expm1f(-__fmul_rn(lambda, dt)) : 0.0f;
+}
+
 // the age after one more step in storage: one FP32 add, round to storage
 __device__ __forceinline__ float age_step_stored(float age, float dt, int age_dtype)
 {

@@ -54,11 +54,6 @@ __device__ __noinline__ float rate_ei(const ModelF& M, int x, float age)
     return hazard(x == kE ? M.lat : M.inf, age);
 }
 
-// p = 1 - exp(-lambda dt) with the step's own size (adaptive step)
-__device__ __forceinline__ float p_of_rate_dt(float lambda, float dt)
-{
-    return lambda > 0.0f ? -expm1f(-__fmul_rn(lambda, dt)) : 0.0f;
-}
 
 // an E/I probability whose table slot 0 holds another age: slot 1, else
 // direct evaluation (rare; out of line)

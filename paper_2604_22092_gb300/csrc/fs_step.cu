@@ -104,7 +104,8 @@ __device__ __forceinline__ float rho_of_age(const StepArgs& a, float age)
 
 // Bernoulli decision and transition for one node of probability p
 // (Algorithm 3); the original id is looked up only when a uniform is needed
-__device__ __forceinline__ TailResult tail_p(const StepArgs& a, int x, float age, float p, int i, uint32_t step)
+__device__ __forceinline__ TailResult tail_p_dt(const StepArgs& a, int x, float age, float p, int i, uint32_t step,
+                                                float dt)
 {
     bool fired = false;
     if (p > 0.0f)
@@ -115,10 +116,49 @@ __device__ __forceinline__ TailResult tail_p(const StepArgs& a, int x, float age
         r.age = 0.0f;
     } else {
         r.x = x;
-        r.age = (x == kE || x == kI) ? __fadd_rn(age, a.M.dt) : 0.0f;
+        r.age = (x == kE || x == kI) ? __fadd_rn(age, dt) : 0.0f;
     }
     r.fired = fired;
     return r;
+}
+
+__device__ __forceinline__ TailResult tail_p(const StepArgs& a, int x, float age, float p, int i, uint32_t step)
+{
+    return tail_p_dt(a, x, age, p, i, step, a.M.dt);
+}
+
+// the E / I rate evaluated directly (adaptive step: ages leave the fixed-step
+// sequence of the tables); out of line
+__device__ __noinline__ float hazard_of(const ModelF& M, int x, float age)
+{
+    return hazard(x == kE ? M.lat : M.inf, age);
+}
+
+// The variant bits of the gather kernels: kModeShed (source-node
+// infectivity with a shedding profile, Eq. 8) and kModeAdaptive (the step
+// size of Section 5.2 with rates evaluated directly).
+constexpr int kModeShed = 1, kModeAdaptive = 2;
+
+// the adaptive step's size for step k (every thread computes it); the first
+// thread of the grid clears the rate slot read two steps ago and records it
+__device__ __forceinline__ float adaptive_dt(const StepArgs& a, int64_t k)
+{
+    const float lp = __uint_as_float(a.ctl->lam[(k + 2) % 3]);
+    const float dt = fminf(a.M.dt, __fdiv_rn(a.eps, __fadd_rn(lp, a.delta)));
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.ctl->lam[(k + 1) % 3] = 0u;
+        a.dtrec[a.j] = dt;
+    }
+    return dt;
+}
+
+// this thread's largest rate into the step's slot (rates are >= 0, so their
+// FP32 bits order as unsigned integers); every lane of the warp calls it
+__device__ __forceinline__ void adaptive_lmax(const StepArgs& a, int64_t k, float lmax)
+{
+    const uint32_t m = __reduce_max_sync(kFull, __float_as_uint(lmax));
+    if ((threadIdx.x & 31) == 0 && m)
+        atomicMax(&a.ctl->lam[k % 3], m);
 }
 
 __device__ __forceinline__ TailResult tail_at(const StepArgs& a, int x, float age, uint32_t c, int i,
@@ -150,13 +190,15 @@ __device__ __forceinline__ void warp_deltas(unsigned long long* s_delta, bool fi
 // ---------------------------------------------------------------------------
 struct LaneDeltas {
     uint32_t fS = 0, fE = 0, fI = 0, dS = 0;
+    float lmax = 0.0f;           // adaptive step: the largest rate this lane saw
 };
 
-template <typename AgeT, bool SMEM_BM, bool SHED = false>
+template <typename AgeT, bool SMEM_BM, int MODE = 0>
 __device__ __forceinline__ void sell_slice(const StepArgs& a, uint32_t step, const uint32_t* __restrict__ bm,
                                            uint32_t* __restrict__ bmn, int slice, int x, LaneDeltas& ld,
-                                           uint32_t mbar = 0u, bool* ready = nullptr)
+                                           float dt, uint32_t mbar = 0u, bool* ready = nullptr)
 {
+    constexpr bool SHED = (MODE & kModeShed) != 0, ADPT = (MODE & kModeAdaptive) != 0;
     constexpr int B = 12;                        // column loads in flight per lane
     const int lane = threadIdx.x & 31;
     const int i = slice * 32 + lane;
@@ -206,10 +248,19 @@ __device__ __forceinline__ void sell_slice(const StepArgs& a, uint32_t step, con
         }
     }
     TailResult r;
-    if constexpr (SHED)
+    if constexpr (ADPT) {
+        float lam = 0.0f;
+        if (x == kS)
+            lam = SHED ? rs : (c ? __fmul_rn(a.M.beta, (float)c) : 0.0f);
+        else if (x == kE || x == kI)
+            lam = hazard_of(a.M, x, age);
+        ld.lmax = fmaxf(ld.lmax, lam);
+        r = tail_p_dt(a, x, age, p_of_rate_dt(lam, dt), i, step, dt);
+    } else if constexpr (SHED) {
         r = tail_p(a, x, age, x == kS ? p_of_rate(a.M, rs) : node_p(a, x, age, 0u), i, step);
-    else
+    } else {
         r = tail_at(a, x, age, c, i, step);
+    }
     if (valid) {
         if (r.x != x)
             a.X[i] = (uint8_t)r.x;
@@ -276,10 +327,10 @@ __device__ __forceinline__ SliceMap slice_map(const StepArgs& a)
     return m;
 }
 
-template <typename AgeT, bool SHED, bool LIST>
+template <typename AgeT, int MODE, bool LIST>
 __device__ __forceinline__ void sell_warp(const StepArgs& a, uint32_t step, const uint32_t* __restrict__ bm,
                                           uint32_t* __restrict__ bmn, int s_begin, int s_end, LaneDeltas& ld,
-                                          const SliceMap& sm)
+                                          const SliceMap& sm, float dt)
 {
     const int lane = threadIdx.x & 31;
     for (int s0 = s_begin; s0 < s_end; s0 += 4) {
@@ -305,7 +356,7 @@ __device__ __forceinline__ void sell_warp(const StepArgs& a, uint32_t step, cons
                     bmn[slice] = 0u;
                 continue;
             }
-            sell_slice<AgeT, false, SHED>(a, step, bm, bmn, slice, x, ld);
+            sell_slice<AgeT, false, MODE>(a, step, bm, bmn, slice, x, ld, dt);
         }
     }
 }
@@ -330,10 +381,12 @@ template <bool SHED> struct MergeShedSmem {
 };
 template <> struct MergeShedSmem<false> {};
 
-template <typename AgeT, bool SHED>
+template <typename AgeT, int MODE>
 __device__ __forceinline__ void merge_chunk(const StepArgs& a, uint32_t step, const uint32_t* __restrict__ bm,
-                                            uint32_t* __restrict__ bmn, int chunk, unsigned long long* s_delta)
+                                            uint32_t* __restrict__ bmn, int chunk, unsigned long long* s_delta,
+                                            float dt, float& lmax)
 {
+    constexpr bool SHED = (MODE & kModeShed) != 0, ADPT = (MODE & kModeAdaptive) != 0;
     __shared__ __align__(128) MergeSmem sm;
     __shared__ MergeShedSmem<SHED> sh;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -526,10 +579,19 @@ __device__ __forceinline__ void merge_chunk(const StepArgs& a, uint32_t step, co
             if (x == kE || x == kI)
                 age = AgeIO<AgeT>::load(A[gi]);
             TailResult t;
-            if constexpr (SHED)
+            if constexpr (ADPT) {
+                float rate = 0.0f;
+                if (x == kS)
+                    rate = SHED ? lam : (count ? __fmul_rn(a.M.beta, (float)count) : 0.0f);
+                else if (x == kE || x == kI)
+                    rate = hazard_of(a.M, x, age);
+                lmax = fmaxf(lmax, rate);
+                t = tail_p_dt(a, x, age, p_of_rate_dt(rate, dt), gi, step, dt);
+            } else if constexpr (SHED) {
                 t = tail_p(a, x, age, x == kS ? p_of_rate(a.M, lam) : node_p(a, x, age, 0u), gi, step);
-            else
+            } else {
                 t = tail_at(a, x, age, count, gi, step);
+            }
             if (t.x != x)
                 a.X[gi] = (uint8_t)t.x;
             if (t.fired || x == kE || x == kI)
@@ -562,7 +624,7 @@ __device__ __forceinline__ void merge_chunk(const StepArgs& a, uint32_t step, co
     }
 }
 
-template <typename AgeT, bool HAS_MERGE, bool SHED>
+template <typename AgeT, bool HAS_MERGE, int MODE>
 __global__ void __launch_bounds__(kStepThreads, kStepCtasPerSm) fused_step_kernel(const __grid_constant__ StepArgs a)
 {
     // Ready for programmatic dependent launch (launch_step's pdl flag): such a
@@ -580,6 +642,9 @@ __global__ void __launch_bounds__(kStepThreads, kStepCtasPerSm) fused_step_kerne
     const uint32_t par = (uint32_t)(k & 1);
     const uint32_t* __restrict__ bm = a.bm[par];
     uint32_t* __restrict__ bmn = a.bm[par ^ 1u];
+    float dt = a.M.dt;
+    if constexpr ((MODE & kModeAdaptive) != 0)
+        dt = adaptive_dt(a, k);
     __syncthreads();
     LaneDeltas ld;
     bool merge_cta = false;
@@ -587,7 +652,7 @@ __global__ void __launch_bounds__(kStepThreads, kStepCtasPerSm) fused_step_kerne
         merge_cta = (int)blockIdx.x < a.n_chunks;
     if (merge_cta) {
         if constexpr (HAS_MERGE)
-            merge_chunk<AgeT, SHED>(a, (uint32_t)k, bm, bmn, (int)blockIdx.x, s_delta);
+            merge_chunk<AgeT, MODE>(a, (uint32_t)k, bm, bmn, (int)blockIdx.x, s_delta, dt, ld.lmax);
     } else {
         const int cta = (int)blockIdx.x - (HAS_MERGE ? a.n_chunks : 0);
         const SliceMap smap = slice_map(a);
@@ -595,9 +660,9 @@ __global__ void __launch_bounds__(kStepThreads, kStepCtasPerSm) fused_step_kerne
         const int s_end = min(s_begin + a.spw, smap.n_items);
         if (s_begin < s_end) {
             if (smap.list)
-                sell_warp<AgeT, SHED, true>(a, (uint32_t)k, bm, bmn, s_begin, s_end, ld, smap);
+                sell_warp<AgeT, MODE, true>(a, (uint32_t)k, bm, bmn, s_begin, s_end, ld, smap, dt);
             else
-                sell_warp<AgeT, SHED, false>(a, (uint32_t)k, bm, bmn, s_begin, s_end, ld, smap);
+                sell_warp<AgeT, MODE, false>(a, (uint32_t)k, bm, bmn, s_begin, s_end, ld, smap, dt);
         }
         const uint32_t fs_ = __reduce_add_sync(kFull, ld.fS), fe = __reduce_add_sync(kFull, ld.fE);
         const uint32_t fi = __reduce_add_sync(kFull, ld.fI), ds = __reduce_add_sync(kFull, ld.dS);
@@ -608,6 +673,8 @@ __global__ void __launch_bounds__(kStepThreads, kStepCtasPerSm) fused_step_kerne
             if (ds) atomicAdd(&s_delta[3], (unsigned long long)ds);
         }
     }
+    if constexpr ((MODE & kModeAdaptive) != 0)
+        adaptive_lmax(a, k, ld.lmax);
     __syncthreads();
     if (threadIdx.x < kDeltaFields) {
         const unsigned long long v = s_delta[threadIdx.x];
@@ -628,10 +695,11 @@ __global__ void __launch_bounds__(kStepThreads, kStepCtasPerSm) fused_step_kerne
 // the slice loop of sell_smem_kernel: warps take the slices at positions
 // first + j W round-robin (W = resident warps), the states of the next four
 // loaded one iteration ahead
-template <typename AgeT, bool SHED, bool LIST>
+template <typename AgeT, int MODE, bool LIST>
 __device__ __forceinline__ void smem_slices(const StepArgs& a, uint32_t step, const uint32_t* __restrict__ bm,
                                             const uint32_t* sbm, uint32_t* __restrict__ bmn, bool use_smem,
-                                            uint32_t mb, bool& ready, LaneDeltas& ld, const SliceMap& smap)
+                                            uint32_t mb, bool& ready, LaneDeltas& ld, const SliceMap& smap,
+                                            float dt)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int W = (int)gridDim.x * (kSmemThreads / 32);
@@ -666,14 +734,14 @@ __device__ __forceinline__ void smem_slices(const StepArgs& a, uint32_t step, co
                 continue;
             }
             if (use_smem)
-                sell_slice<AgeT, true, SHED>(a, step, sbm, bmn, slice, x, ld, mb, &ready);
+                sell_slice<AgeT, true, MODE>(a, step, sbm, bmn, slice, x, ld, dt, mb, &ready);
             else
-                sell_slice<AgeT, false, SHED>(a, step, bm, bmn, slice, x, ld);
+                sell_slice<AgeT, false, MODE>(a, step, bm, bmn, slice, x, ld, dt);
         }
     }
 }
 
-template <typename AgeT, bool SHED>
+template <typename AgeT, int MODE>
 __global__ void __launch_bounds__(kSmemThreads, 1) sell_smem_kernel(const __grid_constant__ StepArgs a)
 {
     extern __shared__ __align__(128) uint32_t sbm[];
@@ -701,11 +769,16 @@ __global__ void __launch_bounds__(kSmemThreads, 1) sell_smem_kernel(const __grid
     __syncthreads();
     LaneDeltas ld;
     bool ready = !use_smem;
+    float dt = a.M.dt;
+    if constexpr ((MODE & kModeAdaptive) != 0)
+        dt = adaptive_dt(a, k);
     const SliceMap smap = slice_map(a);
     if (smap.list)
-        smem_slices<AgeT, SHED, true>(a, (uint32_t)k, bm, sbm, bmn, use_smem, mb, ready, ld, smap);
+        smem_slices<AgeT, MODE, true>(a, (uint32_t)k, bm, sbm, bmn, use_smem, mb, ready, ld, smap, dt);
     else
-        smem_slices<AgeT, SHED, false>(a, (uint32_t)k, bm, sbm, bmn, use_smem, mb, ready, ld, smap);
+        smem_slices<AgeT, MODE, false>(a, (uint32_t)k, bm, sbm, bmn, use_smem, mb, ready, ld, smap, dt);
+    if constexpr ((MODE & kModeAdaptive) != 0)
+        adaptive_lmax(a, k, ld.lmax);
     // the copy into this CTA's shared memory must have landed before it exits
     if (!ready && !mbar_wait(mb, 0u, kWaitLimit))
         record_error(a.ctl, kErrTmaTimeout);
@@ -998,13 +1071,22 @@ static cudaError_t launch_step_t(const StepArgs& a, cudaStream_t s, bool pdl)
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
     cudaError_t e;
-    const bool shed = a.shed_mode != kShedNone;
-    if (a.n_chunks > 0)
-        e = shed ? cudaLaunchKernelEx(&cfg, fused_step_kernel<AgeT, true, true>, a)
-                 : cudaLaunchKernelEx(&cfg, fused_step_kernel<AgeT, true, false>, a);
-    else
-        e = shed ? cudaLaunchKernelEx(&cfg, fused_step_kernel<AgeT, false, true>, a)
-                 : cudaLaunchKernelEx(&cfg, fused_step_kernel<AgeT, false, false>, a);
+    const int mode = (a.shed_mode != kShedNone ? kModeShed : 0) | (a.dtrec ? kModeAdaptive : 0);
+    if (a.n_chunks > 0) {
+        switch (mode) {
+        case 1: e = cudaLaunchKernelEx(&cfg, fused_step_kernel<AgeT, true, 1>, a); break;
+        case 2: e = cudaLaunchKernelEx(&cfg, fused_step_kernel<AgeT, true, 2>, a); break;
+        case 3: e = cudaLaunchKernelEx(&cfg, fused_step_kernel<AgeT, true, 3>, a); break;
+        default: e = cudaLaunchKernelEx(&cfg, fused_step_kernel<AgeT, true, 0>, a); break;
+        }
+    } else {
+        switch (mode) {
+        case 1: e = cudaLaunchKernelEx(&cfg, fused_step_kernel<AgeT, false, 1>, a); break;
+        case 2: e = cudaLaunchKernelEx(&cfg, fused_step_kernel<AgeT, false, 2>, a); break;
+        case 3: e = cudaLaunchKernelEx(&cfg, fused_step_kernel<AgeT, false, 3>, a); break;
+        default: e = cudaLaunchKernelEx(&cfg, fused_step_kernel<AgeT, false, 0>, a); break;
+        }
+    }
     g_launch_count += 1;
     return e;
 }
@@ -1023,20 +1105,22 @@ static cudaError_t launch_step_smem_t(const StepArgs& a, cudaStream_t s, int num
 {
     static thread_local int configured = 0;   // dynamic shared memory limits set once per thread
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(sell_smem_kernel<AgeT, false>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBitmapMaxBytes);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(sell_smem_kernel<AgeT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kSmemBitmapMaxBytes);
+        cudaError_t e = cudaSuccess;
+        for (auto f : {sell_smem_kernel<AgeT, 0>, sell_smem_kernel<AgeT, 1>, sell_smem_kernel<AgeT, 2>,
+                       sell_smem_kernel<AgeT, 3>})
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBitmapMaxBytes);
         if (e != cudaSuccess)
             return e;
         configured = 1;
     }
     const int grid = std::max(1, std::min(num_sms, (a.n_slices + 31) / 32));
-    if (a.shed_mode != kShedNone)
-        sell_smem_kernel<AgeT, true><<<grid, kSmemThreads, a.bm_bytes, s>>>(a);
-    else
-        sell_smem_kernel<AgeT, false><<<grid, kSmemThreads, a.bm_bytes, s>>>(a);
+    switch ((a.shed_mode != kShedNone ? kModeShed : 0) | (a.dtrec ? kModeAdaptive : 0)) {
+    case 1: sell_smem_kernel<AgeT, 1><<<grid, kSmemThreads, a.bm_bytes, s>>>(a); break;
+    case 2: sell_smem_kernel<AgeT, 2><<<grid, kSmemThreads, a.bm_bytes, s>>>(a); break;
+    case 3: sell_smem_kernel<AgeT, 3><<<grid, kSmemThreads, a.bm_bytes, s>>>(a); break;
+    default: sell_smem_kernel<AgeT, 0><<<grid, kSmemThreads, a.bm_bytes, s>>>(a); break;
+    }
     g_launch_count += 1;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || a.n_chunks == 0)

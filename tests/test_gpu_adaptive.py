@@ -13,6 +13,8 @@ in FP64. Each test checks:
     ages bit for bit wherever the state agrees;
   - the simulated clock (the FP64 sum of the step sizes).
 A tolerance eps that never binds gives the fixed-step trajectory bit for bit.
+Both pressure forms run the rule (the push kernel and the gather kernels'
+adaptive instances), also with an age-dependent infectivity.
 """
 import math
 
@@ -43,10 +45,10 @@ def sir(eps, delta=0.0, age_dtype=fs.FS_AGE_F32, seed=1, pressure=fs.FS_PRESSURE
                          pressure=pressure, eps=eps, delta=delta)
 
 
-def seir(eps, delta=0.0, age_dtype=fs.FS_AGE_F32, seed=11):
+def seir(eps, delta=0.0, age_dtype=fs.FS_AGE_F32, seed=11, pressure=fs.FS_PRESSURE_PUSH):
     return fs.sim_params(fs.FS_SEIR, fs.law("lognormal", LN6, 0.6), 0.25, 0.1, seed,
                          latent=fs.law("weibull", 2.0, 4.0), age_dtype=age_dtype,
-                         pressure=fs.FS_PRESSURE_PUSH, eps=eps, delta=delta)
+                         pressure=pressure, eps=eps, delta=delta)
 
 
 def adaptive_lockstep(om, g, params, sim, steps, lam_prev, rep):
@@ -99,15 +101,19 @@ def fp64_sum(dts):
     return t
 
 
-def test_sir_regular_adaptive_lockstep(torch_cuda, oracle_mod):
+PRESSURES = [pytest.param(fs.FS_PRESSURE_PUSH, id="push"), pytest.param(fs.FS_PRESSURE_GATHER, id="gather")]
+
+
+@pytest.mark.parametrize("pressure", PRESSURES)
+def test_sir_regular_adaptive_lockstep(torch_cuda, oracle_mod, pressure):
     """SIR on the 10-regular graph (N = 10^4): eps = 0.05 binds once the
     pressure builds up (beta c up to 3 per day), so dt_k drops below dt_max."""
     g = W.random_regular(10_000, 10, seed=0)
     idx = W.index_nodes(g.n, 10, seed=1)
-    p = sir(0.05)
+    p = sir(0.05, pressure=pressure)
     gh = fs.fs_graph_create(g.n, g.row_ptr, g.col_ind)
     s = fs.fs_sim_init(gh, p, idx)
-    assert fs.fs_sim_pressure_get(s) == fs.FS_PRESSURE_PUSH
+    assert fs.fs_sim_pressure_get(s) == pressure
     assert fs.fs_sim_time(s) == (0.0, np.float32(0.1))
     rep = LockstepReport()
     dts, lam = adaptive_lockstep(oracle_mod, g, p, s, 150, None, rep)
@@ -150,14 +156,15 @@ def test_free_run_equals_single_steps(torch_cuda):
     fs.fs_graph_destroy(gh)
 
 
+@pytest.mark.parametrize("pressure", PRESSURES)
 @pytest.mark.parametrize("age_dtype", [fs.FS_AGE_F32, fs.FS_AGE_BF16])
-def test_seir_ba_adaptive_lockstep(torch_cuda, oracle_mod, age_dtype):
+def test_seir_ba_adaptive_lockstep(torch_cuda, oracle_mod, age_dtype, pressure):
     """SEIR on a Barabasi-Albert graph (N = 50,003, m = 5): merge-class hubs
     take the per-node path; BF16 ages advance by the variable step and round
     to storage like the oracle's."""
     g = W.barabasi_albert(50_003, 5, seed=7)
     idx = W.index_nodes(g.n, 50, seed=2, allowed=W.non_hub_nodes(g))
-    p = seir(0.02, delta=1e-3, age_dtype=age_dtype)
+    p = seir(0.02, delta=1e-3, age_dtype=age_dtype, pressure=pressure)
     gh = fs.fs_graph_create(g.n, g.row_ptr, g.col_ind, opts=fs.graph_opts(fs.FS_DISPATCH_AUTO, 40))
     info = fs.fs_graph_info_get(gh)
     assert info["n_merge"] > 0
@@ -170,7 +177,8 @@ def test_seir_ba_adaptive_lockstep(torch_cuda, oracle_mod, age_dtype):
     fs.fs_graph_destroy(gh)
 
 
-def test_unbinding_eps_equals_fixed_step(torch_cuda):
+@pytest.mark.parametrize("pressure", PRESSURES)
+def test_unbinding_eps_equals_fixed_step(torch_cuda, pressure):
     """With eps / (lambda* + delta) above dt_max at every step, dt_k = dt_max
     and the adaptive kernel (direct rate evaluation) reproduces the fixed-step
     kernel (tabulated probabilities) bit for bit: the tables hold the same
@@ -178,7 +186,7 @@ def test_unbinding_eps_equals_fixed_step(torch_cuda):
     g = W.barabasi_albert(30_011, 4, seed=9)
     idx = W.index_nodes(g.n, 30, seed=3, allowed=W.non_hub_nodes(g))
     gh = fs.fs_graph_create(g.n, g.row_ptr, g.col_ind, opts=fs.graph_opts(fs.FS_DISPATCH_AUTO, 40))
-    for mk in (lambda e: sir(e, seed=21), lambda e: seir(e, seed=22)):
+    for mk in (lambda e: sir(e, seed=21, pressure=pressure), lambda e: seir(e, seed=22, pressure=pressure)):
         pa, pf = mk(1e6), mk(0.0)
         a = fs.fs_sim_init(gh, pa, idx)
         f = fs.fs_sim_init(gh, pf, idx)
@@ -223,10 +231,6 @@ def test_adaptive_argument_errors(torch_cuda):
         with pytest.raises(fs.FsError) as e:
             fs.fs_sim_init(gh, bad, [1, 2])
         assert e.value.status == 1
-    # the gather form runs a fixed step
-    with pytest.raises(fs.FsError) as e:
-        fs.fs_sim_init(gh, sir(0.05, pressure=fs.FS_PRESSURE_GATHER), [1, 2])
-    assert e.value.status == 7
     # packed ensembles run a fixed step
     with pytest.raises(fs.FsError) as e:
         fs.fs_ens_create(gh, [sir(0.05, seed=k) for k in range(4)], [1, 2])
@@ -236,5 +240,59 @@ def test_adaptive_argument_errors(torch_cuda):
     fs.fs_sim_run(s, 7, want_counts=False)
     t, dt = fs.fs_sim_time(s)
     assert dt == np.float32(0.1) and t == fp64_sum([np.float32(0.1)] * 7)
+    fs.fs_sim_destroy(s)
+    fs.fs_graph_destroy(gh)
+
+
+@pytest.mark.parametrize("graph", ["regular", "hub"])
+def test_adaptive_with_shedding_lockstep(torch_cuda, oracle_mod, graph):
+    """The paper's default renewal configuration: the adaptive step with an
+    age-dependent infectivity (gather form). Each step: dt_k against the
+    oracle's rule on its own lambda* (the S rates are the stored-rho sums),
+    then one oracle step of the GPU's dt_k fed the GPU's stored rho."""
+    from tests.test_gpu_shedding import hub_graph, rho_float
+    if graph == "regular":
+        g = W.random_regular(10_000, 10, seed=0)
+        idx = W.index_nodes(g.n, 30, seed=1)
+    else:
+        g = hub_graph(seed=17)
+        idx = W.index_nodes(g.n, 60, seed=2, allowed=W.non_hub_nodes(g))
+    p = fs.sim_params(fs.FS_SEIR, fs.law("lognormal", LN6, 0.6), 1.2, 0.1, 31, latent=fs.law("weibull", 2.0, 4.0),
+                      eps=0.03, shed_mode=fs.FS_SHED_DENSITY, shedding=fs.law("lognormal", LN6, 0.6))
+    gh = fs.fs_graph_create(g.n, g.row_ptr, g.col_ind)
+    s = fs.fs_sim_init(gh, p, idx)
+    assert fs.fs_sim_pressure_get(s) == fs.FS_PRESSURE_GATHER
+    om = oracle_mod
+    prm = oracle_params(om, p)
+    deg = np.diff(g.row_ptr)
+    lam_prev = None
+    dts = []
+    decisions = mism = 0
+    for _ in range(70):
+        X, A, k = fs.fs_sim_get_state(s, g.n)
+        rho = rho_float(fs.fs_sim_infectivity_get(s, g.n), fs.FS_AGE_F32)
+        _, dt_gpu = fs.fs_sim_time(s)
+        if lam_prev is None:
+            assert dt_gpu == np.float32(p.dt)
+        else:
+            dt_ref = om.adaptive_dt(p.dt, p.eps, 1e-12, lam_prev)
+            assert abs(dt_gpu - dt_ref) <= DT_REL * dt_ref, (k, dt_gpu, dt_ref)
+        prm.dt = float(dt_gpu)
+        Xo, Ao, _, margin, lam = om.step_rho(g.row_ptr, g.col_ind, prm, k, X, A, rho_in=rho)
+        fs.fs_sim_step(s)
+        X2, A2, _ = fs.fs_sim_get_state(s, g.n)
+        band = TIE + prm.dt * np.exp(-lam * prm.dt) * deg * 2.0 ** -24 * lam * 1.01
+        bad = X2 != Xo
+        decisions += int(np.isfinite(margin).sum())
+        if bad.any():
+            assert (np.abs(margin[bad]) < band[bad]).all(), (k, np.flatnonzero(bad)[:10])
+            mism += int(bad.sum())
+        ok = ~bad
+        assert (A2[ok].view(np.uint32) == Ao[ok].view(np.uint32)).all(), k
+        dts.append(dt_gpu)
+        lam_prev = float(lam.max())
+    assert mism <= 1e-6 * decisions and decisions > 10_000
+    assert min(dts) < p.dt
+    assert fs.fs_sim_time(s)[0] == fp64_sum(dts)
     fs.fs_sim_destroy(s)
     fs.fs_graph_destroy(gh)
