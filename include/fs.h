@@ -126,9 +126,9 @@ typedef struct {
  * node's pressure is the FP32 sum of those values over its infectious
  * in-neighbours, in a fixed order (row order in the one-lane-per-node class;
  * segmented warp sums folded by warp, then by chunk, in the merge class), so
- * a run is reproducible bit for bit. Gather form only: FS_PRESSURE_PUSH, eps
- * > 0, packed ensembles, batches, the server and fs_step_noalloc need
- * FS_SHED_NONE (FS_EUNSUPPORTED). */
+ * a run is reproducible bit for bit. Gather form only (the adaptive step,
+ * eps > 0, combines with it): FS_PRESSURE_PUSH, packed ensembles, batches,
+ * the server and fs_step_noalloc need FS_SHED_NONE (FS_EUNSUPPORTED). */
 typedef enum { FS_SHED_NONE = 0, FS_SHED_HAZARD = 1, FS_SHED_DENSITY = 2 } fs_shed_mode;
 
 /* One realisation (Section 3; Algorithm 3 with a fixed step dt). */

@@ -285,11 +285,12 @@ def test_shedding_argument_errors(torch_cuda):
         with pytest.raises(fs.FsError) as e:
             fs.fs_sim_init(gh, p, [1])
         assert e.value.status == 7
+    # the adaptive step combines with a profile (gather form)
     p = sir_shed(fs.FS_SHED_DENSITY)
     p.eps = 0.05
-    with pytest.raises(fs.FsError) as e:
-        fs.fs_sim_init(gh, p, [1])
-    assert e.value.status == 7
+    s = fs.fs_sim_init(gh, p, [1])
+    assert fs.fs_sim_pressure_get(s) == fs.FS_PRESSURE_GATHER
+    fs.fs_sim_destroy(s)
     with pytest.raises(fs.FsError) as e:
         fs.fs_ens_create(gh, [sir_shed(fs.FS_SHED_DENSITY, seed=k) for k in range(3)], [1])
     assert e.value.status == 7
