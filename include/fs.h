@@ -308,13 +308,14 @@ fs_status fs_sim_get_state(fs_sim* s, uint8_t* state, void* age, int64_t* step);
  * 0. Synchronous. */
 fs_status fs_sim_set_state(fs_sim* s, const uint8_t* state, const void* age, int64_t step);
 
-/* Simulated time: *elapsed (may be NULL) = the sum of the step sizes of the
+/* Simulated time (the clock of Algorithm 2 / Algorithm 1, Section 5.2):
+ * *elapsed (may be NULL) = the sum of the step sizes of the
  * steps run since init or set_state; *next_dt (may be NULL) = the size of the
  * next step (dt for a fixed step; 0 for the Markovian engine, whose next
  * step size depends on the rates of the state it starts from). Synchronous. */
 fs_status fs_sim_time(const fs_sim* s, double* elapsed, float* next_dt);
 
-/* Active-node compaction accounting (FS_ACTIVE_LIST): *listed = the sum over
+/* Active-node compaction accounting (FS_ACTIVE_LIST, Section 5.6): *listed = the sum over
  * the launch sequences run since init or set_state of the units each one
  * visited (all units while the list is not in use), *units = the number of
  * units (SELL slices in the gather form, push items in the push form; 0
@@ -322,7 +323,8 @@ fs_status fs_sim_time(const fs_sim* s, double* elapsed, float* next_dt);
 fs_status fs_sim_active_units(const fs_sim* s, uint64_t* listed, uint64_t* units);
 
 /* *total = the node transitions (S -> E/I, E -> I, I -> R/S) of the steps
- * run since init or set_state. Synchronous. */
+ * run since init or set_state (the Markovian engine's "events", Section 4).
+ * Synchronous. */
 fs_status fs_sim_transitions(const fs_sim* s, uint64_t* total);
 
 /* The infectivity the next step reads (Eq. 8): rho[i] = beta s(tau_i) as

@@ -22,7 +22,12 @@
  *     stored like an age (fp32, then the storage type), and the pressure is
  *     the double sum of the stored values;
  *   - the paper's Triton PRNG is replaced by Philox4x32-10 keyed by
- *     (seed, replicate, step, node).
+ *     (seed, replicate, step, node);
+ *   - the Markovian engine (Algorithm 1) takes its step size from the rates
+ *     of the state the step starts from, Lambda collected by compartment
+ *     (beta x S-I edges + sigma |E| + gamma |I|) in double, and SIS returns
+ *     recovered nodes to S; its exact reference is a Doob-Gillespie direct
+ *     method (fso_gillespie_run).
  */
 #include "fs_oracle.h"
 
