@@ -33,10 +33,11 @@ def small_graph():
     return W.csr_from_edges(5, np.array([a for a, _ in edges]), np.array([b for _, b in edges]))
 
 
-def ctmc_mean_counts(g, model, beta, gamma, index, times):
-    """Exact E[#S], E[#I], E[#R] of the Markov chain at the given times."""
+def ctmc_mean_counts(g, model, beta, gamma, index, times, sigma=0.0):
+    """Exact E[#S], E[#I], E[#R] (and E[#E] last for SEIR) of the Markov
+    chain at the given times."""
     n = g.n
-    comps = (S, I) if model == "sis" else (S, I, R)
+    comps = {"sis": (S, I), "sir": (S, I, R), "seir": (S, E, I, R)}[model]
     states = list(itertools.product(comps, repeat=n))
     pos = {s: q for q, s in enumerate(states)}
     Q = np.zeros((len(states), len(states)))
@@ -45,7 +46,9 @@ def ctmc_mean_counts(g, model, beta, gamma, index, times):
         for i in range(n):
             if s[i] == S:
                 c = sum(1 for j in g.col_ind[g.row_ptr[i]:g.row_ptr[i + 1]] if s[j] == I)
-                rate, y = beta * c, I
+                rate, y = beta * c, (E if model == "seir" else I)
+            elif s[i] == E:
+                rate, y = sigma, I
             elif s[i] == I:
                 rate, y = gamma, (S if model == "sis" else R)
             else:
@@ -57,7 +60,7 @@ def ctmc_mean_counts(g, model, beta, gamma, index, times):
                 Q[a, a] -= rate
     p0 = np.zeros(len(states))
     p0[pos[tuple(I if i in index else S for i in range(n))]] = 1.0
-    cnt = np.array([[sum(1 for x in s if x == c) for c in (S, I, R)] for s in states], dtype=float)
+    cnt = np.array([[sum(1 for x in s if x == c) for c in (S, I, R, E)] for s in states], dtype=float)
     return np.array([(p0 @ scipy.linalg.expm(Q * t)) @ cnt for t in times])
 
 
@@ -213,3 +216,26 @@ def test_papers_validation_protocol(oracle_mod, model):
     mean = tl.mean(axis=0)
     assert ((mean >= q25) & (mean <= q75)).all(), np.flatnonzero((mean < q25) | (mean > q75))
     assert exact.mean(axis=0).max() > 100          # a real outbreak (SIR peak, SIS endemic level)
+
+
+def test_seir_gillespie_and_small_steps_match_exact_chain(oracle_mod):
+    """SEIR with exponential latent and infectious periods (4^5 states)."""
+    om = oracle_mod
+    g = small_graph()
+    beta, sigma, gamma = 0.9, 0.8, 0.6
+    times = np.arange(9) * 0.5
+    exact = ctmc_mean_counts(g, "seir", beta, gamma, {0}, times, sigma=sigma)
+    prm = om.params(om.SEIR, om.law("exp", sigma), om.law("exp", gamma), beta, 0.1, 1)
+    gil = np.array([om.gillespie_run(g.row_ptr, g.col_ind, prm, [0], om.I, 3000 + r, 9, 0.5)
+                    for r in range(20_000)], dtype=float)
+    X0, A0 = om.init(g.n, [0], om.I)
+    tl = np.array([om.markov_run(g.row_ptr, g.col_ind,
+                                 om.params(om.SEIR, om.law("exp", sigma), om.law("exp", gamma), beta, 0.1, 500 + r),
+                                 1e-3, 0.005, 0.005, 0, 9, 0.5, X0, A0)[0] for r in range(4000)], dtype=float)
+    for col, c in ((1, I), (2, R), (3, E)):
+        m = gil[:, :, c].mean(axis=0)
+        se = gil[:, :, c].std(axis=0) / math.sqrt(gil.shape[0])
+        assert (np.abs(m - exact[:, col]) <= 4.5 * se + 1e-9).all(), ("gillespie", c, m, exact[:, col])
+        m = tl[:, :, c].mean(axis=0)
+        se = tl[:, :, c].std(axis=0) / math.sqrt(tl.shape[0])
+        assert (np.abs(m - exact[:, col]) <= 4.5 * se + 0.02).all(), ("tau-leap", c, m, exact[:, col])

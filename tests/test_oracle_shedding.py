@@ -194,3 +194,23 @@ def test_exact_simulator_rejects_shedding(oracle_mod):
                     shedding=om.law("lognormal", LN5, 0.5))
     with pytest.raises(ValueError):
         om.exact_run(g.row_ptr, g.col_ind, prm, [1], om.I, 5, 10, 1.0)
+
+
+def test_constant_profile_adaptive_equals_markovian_edges(oracle_mod):
+    """The adaptive step (Section 5.2) with the exact constant profile: the
+    pressure, lambda*, every dt_k and the trajectory equal the s = 1 run."""
+    om = oracle_mod
+    g = W.random_regular(2000, 8, seed=13)
+    idx = W.index_nodes(g.n, 20, seed=14)
+    lat, inf = om.law("weibull", 2.0, 4.0), om.law("lognormal", LN6, 0.6)
+    base = om.params(om.SEIR, lat, inf, 0.25, 0.1, 7)
+    shed = om.params(om.SEIR, lat, inf, 0.125, 0.1, 7, shed_mode=om.SHED_HAZARD, shedding=om.law("exp", 2.0))
+    X0, A0 = om.init(g.n, idx, om.E)
+    c1, X1, A1, d1, l1 = om.run_adaptive(g.row_ptr, g.col_ind, base, 0.03, 1e-12, 0, 400, X0, A0)
+    c2, X2, A2, d2, l2 = om.run_adaptive(g.row_ptr, g.col_ind, shed, 0.03, 1e-12, 0, 400, X0, A0)
+    assert d1.min() < 0.1 and c1[-1, 3] > 50
+    np.testing.assert_array_equal(d1, d2)
+    np.testing.assert_array_equal(c1, c2)
+    np.testing.assert_array_equal(X1, X2)
+    np.testing.assert_array_equal(A1.view(np.uint32), A2.view(np.uint32))
+    assert l1 == l2
