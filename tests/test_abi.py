@@ -54,3 +54,40 @@ def test_oracle_is_not_imported_by_the_product_package():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text
                 assert "fs_oracle" not in text, f
+
+
+# typedef name in include/fs.h -> ctypes mirror in the binding
+_STRUCTS = {"fs_law": "fs_law", "fs_sim_params": "fs_sim_params", "fs_graph_opts": "fs_graph_opts",
+            "fs_graph_info": "fs_graph_info", "fs_server_cfg": "fs_server_cfg", "fs_server_stats": "fs_server_stats"}
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every ctypes mirror has the size and field offsets the C compiler gives
+    the header's struct (checked by compiling a probe against include/fs.h)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fs.h"', "int main(void) {"]
+    for cname, pname in _STRUCTS.items():
+        cls = getattr(_abi, pname)
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "probe"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            parts = line.split()
+            got[(parts[0], parts[1])] = int(parts[2])
+    for cname, pname in _STRUCTS.items():
+        cls = getattr(_abi, pname)
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
