@@ -239,3 +239,22 @@ def test_seir_gillespie_and_small_steps_match_exact_chain(oracle_mod):
         m = tl[:, :, c].mean(axis=0)
         se = tl[:, :, c].std(axis=0) / math.sqrt(tl.shape[0])
         assert (np.abs(m - exact[:, col]) <= 4.5 * se + 0.02).all(), ("tau-leap", c, m, exact[:, col])
+
+
+def test_gillespie_agrees_with_the_event_driven_simulator(oracle_mod):
+    """SIR with exponential recovery: the Doob-Gillespie run and the oracle's
+    event-driven renewal simulator (holding times drawn at entry) simulate
+    the same process by different algorithms; their mean trajectories agree."""
+    om = oracle_mod
+    g = W.erdos_renyi(200, 6, seed=8)
+    idx = W.index_nodes(g.n, 5, seed=9)
+    prm = om.params(om.SIR, None, om.law("exp", 0.2), 0.3, 0.1, 1)
+    a = np.array([om.gillespie_run(g.row_ptr, g.col_ind, prm, idx, om.I, 11 + r, 31, 1.0)
+                  for r in range(1500)], dtype=float)
+    b = np.array([om.exact_run(g.row_ptr, g.col_ind, prm, idx, om.I, 7001 + r, 31, 1.0)
+                  for r in range(1500)], dtype=float)
+    for c in (I, R):
+        d = a[:, :, c].mean(axis=0) - b[:, :, c].mean(axis=0)
+        se = np.sqrt(a[:, :, c].var(axis=0) / a.shape[0] + b[:, :, c].var(axis=0) / b.shape[0])
+        assert (np.abs(d) <= 4.5 * se + 1e-9).all(), (c, d, se)
+    assert a[:, -1, R].mean() > 50
