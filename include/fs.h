@@ -428,6 +428,10 @@ typedef struct {
     int64_t max_inflight;      /* cap on node x realisation updates per launch summed over
                                   running requests; the queue head waits while admitting it
                                   would pass the cap, unless nothing runs. 0 = 2^25, -1 = none */
+    double wait_limit_s;       /* longest time a request may wait in the queue; a request
+                                  not admitted by then is retired alone: fs_server_poll
+                                  reports done with FS_ETIMEOUT, the others run on.
+                                  0 = no limit; must be >= 0                                  */
 } fs_server_cfg;
 
 typedef struct {
@@ -448,7 +452,8 @@ fs_status fs_server_submit(fs_server* s, fs_graph* g, const fs_sim_params* scena
                            uint64_t* request_id);
 /* *done = 1 when the request has finished; then counts_out (host uint32
  * [(steps+1)][n_scen*replicates][4], may be NULL) receives its counts and
- * *seconds (may be NULL) its time from submission to completion. */
+ * *seconds (may be NULL) its time from submission to completion. A request
+ * retired by the wait limit sets *done = 1 and returns FS_ETIMEOUT. */
 fs_status fs_server_poll(fs_server* s, uint64_t request_id, int32_t* done, uint32_t* counts_out,
                          double* seconds);
 /* Blocks until every submitted request has finished or `timeout_s` passes
@@ -468,14 +473,19 @@ fs_status fs_server_destroy(fs_server* s);
  * caller owns and passes every other buffer.
  *
  * The step's only scratch -- the merge class's cross-chunk partial counts and
- * tickets, and a 256-byte control block -- lives in one fixed array inside
- * the library, sized for at most 65,536 merge-class rows (512 KiB + 256 B,
- * held on every GPU that loads the library until the process exits). A graph
- * with more merge-class rows is rejected with FS_EINVAL.
+ * tickets, a 256-byte control block and a 1 KiB row of per-warp delta slots
+ * -- lives in one fixed array inside the library, sized for at most 65,536
+ * merge-class rows (512 KiB + 1.25 KiB, held on every GPU that loads the
+ * library until the process exits). A graph with more merge-class rows is
+ * rejected with FS_EINVAL.
  *   g               graph from fs_graph_create. The buffers below are in the
  *                   graph's internal node order, which is the caller's order
  *                   when fs_graph_info_get reports identity_layout = 1.
- *   params          the realisation, as for fs_sim_init (index_state unused)
+ *   params          the realisation, as for fs_sim_init (index_state unused).
+ *                   The pressure form in params->flags is ignored: this step
+ *                   always counts infectious neighbours by the gather over the
+ *                   bitmap (the push form keeps per-node counts, which would be
+ *                   more caller-owned state); both forms give the same counts.
  *   step            step index k (keys the uniforms), 0 <= k < 2^32
  *   state_dev       device uint8[n], read and updated in place
  *   age_dev         device ages[n] of params->age_dtype, updated in place
@@ -494,7 +504,9 @@ fs_status fs_server_destroy(fs_server* s);
  * clears what must start at zero; calls that overlap on the GPU (other
  * streams, other threads) race on it and must be serialised by the caller.
  * Errors: FS_EINVAL (NULL pointers, bad params or step, too many merge-class
- * rows), FS_ESTATE, FS_ECUDA.
+ * rows), FS_EUNSUPPORTED (eps > 0, a shedding profile, FS_ACTIVE_LIST,
+ * theta > 0, or a current device ordinal of 64 or more), FS_ESTATE (the graph
+ * is in a failed state), FS_ECUDA.
  * ------------------------------------------------------------------------- */
 fs_status fs_step_noalloc(const fs_graph* g, const fs_sim_params* params, int64_t step,
                           uint8_t* state_dev, void* age_dev, const uint32_t* bitmap_cur_dev,

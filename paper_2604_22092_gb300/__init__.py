@@ -80,11 +80,6 @@ def law(kind: str, a: float = 0.0, b: float = 0.0, k: int = 0) -> _abi.fs_law:
     return _abi.fs_law(code, int(k), float(a), float(b))
 
 
-def lognormal_from_mean_median(mean: float, median: float) -> _abi.fs_law:
-    """mu = ln(median), sigma = sqrt(2 ln(mean/median)) (the paper's parametrisation)."""
-    return law("lognormal", math.log(median), math.sqrt(2.0 * math.log(mean / median)))
-
-
 def sim_params(model: int, infectious: _abi.fs_law, beta: float, dt: float, seed: int,
                latent: _abi.fs_law | None = None, replicate: int = 0, index_state: int | None = None,
                age_dtype: int = FS_AGE_F32, pressure: int = FS_PRESSURE_AUTO, eps: float = 0.0,
@@ -350,9 +345,9 @@ def fs_batch_destroy(b: int) -> None:
 
 # --------------------------------------------------------------- serving
 def fs_server_create(hbm_budget_bytes: int = 0, max_members: int = 0, quantum: int = 0,
-                     age_dtype: int = FS_AGE_F32, max_inflight: int = 0) -> int:
+                     age_dtype: int = FS_AGE_F32, max_inflight: int = 0, wait_limit_s: float = 0.0) -> int:
     cfg = _abi.fs_server_cfg(int(hbm_budget_bytes), int(max_members), int(quantum), int(age_dtype), 0,
-                             int(max_inflight))
+                             int(max_inflight), float(wait_limit_s))
     h = ctypes.c_void_p()
     check(load().fs_server_create(ctypes.byref(cfg), ctypes.byref(h)), "fs_server_create")
     return h.value

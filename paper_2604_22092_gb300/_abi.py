@@ -57,7 +57,7 @@ class fs_graph_info(ctypes.Structure):
 class fs_server_cfg(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_members", ctypes.c_int32),
                 ("quantum", ctypes.c_int32), ("age_dtype", ctypes.c_int32), ("reserved_", ctypes.c_int32),
-                ("max_inflight", ctypes.c_int64)]
+                ("max_inflight", ctypes.c_int64), ("wait_limit_s", ctypes.c_double)]
 
 
 class fs_server_stats(ctypes.Structure):

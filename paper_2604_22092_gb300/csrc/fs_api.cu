@@ -712,7 +712,7 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
     const size_t oB0 = carve(words * 4), oB1 = carve(words * 4);
     const size_t oMc = carve(sizeof(int32_t) * nm1), oMt = carve(sizeof(uint32_t) * nm1);
     const size_t oCtl = carve(sizeof(fs::DevCtl));
-    const size_t oDel = carve(sizeof(unsigned long long) * fs::kMaxGraphSteps * fs::kDeltaFields);
+    const size_t oDel = carve(sizeof(unsigned long long) * fs::kMaxGraphSteps * fs::kDeltaRow);
     const size_t oPt = carve(sizeof(float4) * 2 * fs::kPTableN), oPs = carve(sizeof(float) * fs::kPSTableN);
     const size_t oIdx = carve(sizeof(int32_t) * (size_t)std::max<int64_t>(n_index, 1));
     const size_t oDt = carve(sizeof(float) * fs::kMaxGraphSteps);
@@ -1284,15 +1284,17 @@ fs_status fs_eval_uniforms(uint64_t seed, uint32_t replicate, int64_t step, cons
 
 // ---------------------------------------------------------------------------
 // fs_step_noalloc: one fused step that allocates nothing. Its scratch (the
-// merge class's cross-chunk partial counts and tickets, and the control block
-// the step kernel reads its step index from and writes its error word to)
-// lives in one file-scope device array, looked up once per device.
+// merge class's cross-chunk partial counts and tickets, the control block the
+// step kernel reads its step index from and writes its error word to, and the
+// step's row of delta slots) lives in one file-scope device array, looked up
+// once per device.
 // ---------------------------------------------------------------------------
 namespace {
 
 constexpr int kNoAllocMaxMergeRows = 65536;
 constexpr size_t kNoAllocCtlBytes = 256;
-constexpr size_t kNoAllocBytes = kNoAllocCtlBytes + (size_t)kNoAllocMaxMergeRows * 8;
+constexpr size_t kNoAllocSlotBytes = sizeof(unsigned long long) * fs::kDeltaRow;   // one step's delta slots
+constexpr size_t kNoAllocBytes = kNoAllocCtlBytes + kNoAllocSlotBytes + (size_t)kNoAllocMaxMergeRows * 8;
 static_assert(sizeof(fs::DevCtl) <= kNoAllocCtlBytes, "control block does not fit");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
@@ -1323,10 +1325,10 @@ fs_status noalloc_scratch_addr(unsigned char** out)
     return FS_OK;
 }
 
-// clears the scratch rows in use, sets the step index, clears the caller's
-// delta outputs (everything the step expects to start at zero)
+// clears the scratch rows in use and the delta slots, sets the step index
+// (everything the step expects to start at zero)
 __global__ void noalloc_prepare_kernel(fs::DevCtl* ctl, int32_t* cnt, uint32_t* tkt, int n_m, int64_t step,
-                                       unsigned long long* deltas)
+                                       unsigned long long* slots)
 {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     for (int64_t i = t; i < n_m; i += (int64_t)gridDim.x * blockDim.x) {
@@ -1337,14 +1339,28 @@ __global__ void noalloc_prepare_kernel(fs::DevCtl* ctl, int32_t* cnt, uint32_t* 
         ctl->step = step;
         ctl->error = 0;
     }
-    if (t < 5)
-        deltas[t] = 0ull;
+    if (t < fs::kDeltaRow)
+        slots[t] = 0ull;
 }
 
-__global__ void noalloc_finish_kernel(const fs::DevCtl* ctl, unsigned long long* deltas)
+// the step's totals (the delta slots summed) and the device error word into
+// the caller's five words; one warp, lane = slot
+__global__ void noalloc_finish_kernel(const fs::DevCtl* ctl, const unsigned long long* slots,
+                                      unsigned long long* deltas)
 {
-    if (threadIdx.x == 0)
+    static_assert(fs::kDeltaSlots == 32, "one delta slot per lane");
+    const int lane = threadIdx.x & 31;
+    unsigned long long f[fs::kDeltaFields];
+    for (int q = 0; q < fs::kDeltaFields; ++q) {
+        f[q] = slots[lane * fs::kDeltaFields + q];
+        for (int o = 16; o > 0; o >>= 1)
+            f[q] += __shfl_xor_sync(0xffffffffu, f[q], o);
+    }
+    if (lane == 0) {
+        for (int q = 0; q < fs::kDeltaFields; ++q)
+            deltas[q] = f[q];
         deltas[4] = (unsigned long long)(unsigned)ctl->error;
+    }
 }
 
 }  // namespace
@@ -1385,13 +1401,15 @@ extern "C" fs_status fs_step_noalloc(const fs_graph* g, const fs_sim_params* par
     if (st != FS_OK)
         return st;
     fs::DevCtl* ctl = reinterpret_cast<fs::DevCtl*>(base);
-    int32_t* cnt = reinterpret_cast<int32_t*>(base + kNoAllocCtlBytes);
-    uint32_t* tkt = reinterpret_cast<uint32_t*>(base + kNoAllocCtlBytes + (size_t)kNoAllocMaxMergeRows * 4);
+    unsigned long long* slots = reinterpret_cast<unsigned long long*>(base + kNoAllocCtlBytes);
+    int32_t* cnt = reinterpret_cast<int32_t*>(base + kNoAllocCtlBytes + kNoAllocSlotBytes);
+    uint32_t* tkt = reinterpret_cast<uint32_t*>(base + kNoAllocCtlBytes + kNoAllocSlotBytes +
+                                                (size_t)kNoAllocMaxMergeRows * 4);
     cudaStream_t cs = (cudaStream_t)stream;
     unsigned long long* deltas = reinterpret_cast<unsigned long long*>(deltas_dev);
 
     const int prep_blocks = std::max(1, std::min(64, (g->n_m + 255) / 256));
-    noalloc_prepare_kernel<<<prep_blocks, 256, 0, cs>>>(ctl, cnt, tkt, g->n_m, step, deltas);
+    noalloc_prepare_kernel<<<prep_blocks, 256, 0, cs>>>(ctl, cnt, tkt, g->n_m, step, slots);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return fail(FS_ECUDA, "fs_step_noalloc: prepare: %s", cudaGetErrorString(e));
@@ -1423,13 +1441,13 @@ extern "C" fs_status fs_step_noalloc(const fs_graph* g, const fs_sim_params* par
     a.deg = g->d_deg;
     a.M = to_model(pv);
     a.ctl = ctl;
-    a.deltas = deltas;
+    a.deltas = slots;
     a.j = 0;
     a.n = (int32_t)g->n;
     e = fs::launch_step(a, pv.age_dtype, cs, false);
     if (e != cudaSuccess)
         return fail(FS_ECUDA, "fs_step_noalloc: step: %s", cudaGetErrorString(e));
-    noalloc_finish_kernel<<<1, 32, 0, cs>>>(ctl, deltas);
+    noalloc_finish_kernel<<<1, 32, 0, cs>>>(ctl, slots, deltas);
     e = cudaGetLastError();
     if (e != cudaSuccess)
         return fail(FS_ECUDA, "fs_step_noalloc: finish: %s", cudaGetErrorString(e));

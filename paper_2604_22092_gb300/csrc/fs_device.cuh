@@ -228,9 +228,6 @@ __device__ __forceinline__ float age_step_stored(float age, float dt, int age_dt
     return v;
 }
 
-// Memoised probability of an E/I node of age `age` from its law's two-slot
-// table row (age0, p0, age1, p1): slot 0 is read as 8 bytes and slot 1 only
-// when slot 0 holds another age; returns -1 when neither holds `age`.
 // beta s(tau) of the source-node infectivity (Eq. 8): s = the hazard
 // (mode 1) or the density (mode 2) of the shedding law
 __device__ __forceinline__ float shed_value(const LawF& L, int mode, float beta, float tau)
@@ -239,6 +236,32 @@ __device__ __forceinline__ float shed_value(const LawF& L, int mode, float beta,
     return __fmul_rn(beta, s);
 }
 
+// Adds one warp's step totals into its delta slot of row j (every lane of the
+// warp calls this with its own counts; lanes 0..3 issue one atomic each, and
+// only for non-zero totals). No barrier: warps that finish early leave.
+__device__ __forceinline__ void warp_add_deltas(unsigned long long* deltas, int j, uint32_t fS, uint32_t fE,
+                                                uint32_t fI, unsigned long long dS)
+{
+    fS = __reduce_add_sync(0xffffffffu, fS);
+    fE = __reduce_add_sync(0xffffffffu, fE);
+    fI = __reduce_add_sync(0xffffffffu, fI);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        dS += __shfl_xor_sync(0xffffffffu, dS, o);
+    const int lane = threadIdx.x & 31;
+    if (lane < kDeltaFields) {
+        const unsigned long long v = lane == 0 ? fS : lane == 1 ? fE : lane == 2 ? fI : dS;
+        if (v) {
+            const uint32_t w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+            atomicAdd(deltas + (int64_t)j * kDeltaRow + (w & (kDeltaSlots - 1)) * kDeltaFields + lane, v);
+        }
+    }
+}
+
+// Memoised probability of an E/I node of age `age` from slot 1 of its law's
+// two-slot table row (age0, p0, age1, p1); slot 0 is read by the caller as 8
+// bytes and this is called only when slot 0 holds another age. Returns -1
+// when slot 1 does not hold `age` either.
 __device__ __forceinline__ float ptab_slot1(const float4* row, float age)
 {
     const float2 e1 = __ldg(reinterpret_cast<const float2*>(row) + 1);

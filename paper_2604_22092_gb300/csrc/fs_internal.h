@@ -91,8 +91,14 @@ enum { kErrNone = 0, kErrTmaTimeout = 1, kErrBadState = 2, kErrBadGraph = 3 };
 
 // Per-step deltas accumulated by the step kernel (atomics, skipped when 0):
 // [0] nodes that left S, [1] E -> I, [2] I -> R, [3] sum of degrees of the
-// nodes that left S.
+// nodes that left S. Each step's row is spread over kDeltaSlots slots
+// (uint64 [K][kDeltaSlots][kDeltaFields]): warp w of a step's grid adds its
+// totals into slot w mod kDeltaSlots, so that no CTA-wide reduction or
+// barrier ends the step and no word takes more than a few dozen atomics; the
+// epilogue sums the slots.
 constexpr int kDeltaFields = 4;
+constexpr int kDeltaSlots = 32;
+constexpr int kDeltaRow = kDeltaSlots * kDeltaFields;   // words per step
 
 // Everything the fused step kernel reads, passed by value.
 struct StepArgs {
@@ -133,7 +139,7 @@ struct StepArgs {
     uint32_t smem_min_s;          // stage the bitmap when at least this many nodes are S
     ModelF M;
     DevCtl* ctl;
-    unsigned long long* deltas;   // [K][kDeltaFields]
+    unsigned long long* deltas;   // [K][kDeltaSlots][kDeltaFields]
     int32_t j;                    // step offset within the launch sequence
     int32_t n;
     // push form of the pressure (fs_push.cu): per-node infectious in-neighbour

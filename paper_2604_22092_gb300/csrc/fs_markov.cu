@@ -128,11 +128,8 @@ __device__ __forceinline__ float mk_tau(const StepArgs& a, const MarkovSums& m)
 template <typename AgeT>
 __global__ void __launch_bounds__(kMkThreads) mk_step_kernel(const __grid_constant__ StepArgs a)
 {
-    __shared__ unsigned long long s_delta[kDeltaFields];
     __shared__ float s_tau;
     const int tid = threadIdx.x, lane = tid & 31;
-    if (tid < kDeltaFields)
-        s_delta[tid] = 0ull;
     const int64_t k = a.ctl->step + a.j;
     // tau once per block: double arithmetic is slow on this part, and every
     // thread would compute the same value
@@ -227,24 +224,7 @@ __global__ void __launch_bounds__(kMkThreads) mk_step_kernel(const __grid_consta
             }
         }
     }
-    const uint32_t fs_ = __reduce_add_sync(kFull, fS), fe = __reduce_add_sync(kFull, fE);
-    const uint32_t fi = __reduce_add_sync(kFull, fI);
-    unsigned long long ds = dS;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-        ds += __shfl_down_sync(kFull, ds, o);
-    if (lane == 0) {
-        if (fs_) atomicAdd(&s_delta[0], (unsigned long long)fs_);
-        if (fe) atomicAdd(&s_delta[1], (unsigned long long)fe);
-        if (fi) atomicAdd(&s_delta[2], (unsigned long long)fi);
-        if (ds) atomicAdd(&s_delta[3], ds);
-    }
-    __syncthreads();
-    if (tid < kDeltaFields) {
-        const unsigned long long v = s_delta[tid];
-        if (v)
-            atomicAdd(a.deltas + (int64_t)a.j * kDeltaFields + tid, v);
-    }
+    warp_add_deltas(a.deltas, a.j, fS, fE, fI, dS);
 }
 
 // Control Mode: every node's count recomputed from its row. Warps take

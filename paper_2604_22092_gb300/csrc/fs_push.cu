@@ -809,19 +809,16 @@ __device__ __noinline__ PushSweepOut push_items_listed(const StepArgs& a, uint32
 
 // ---------------------------------------------------------------------------
 // One whole step: items are groups of kPushG thread-class nodes, then single
-// merge-class nodes; warps stride over them (grid-stride). Per-step deltas as
-// in the gather form.
+// merge-class nodes; warps stride over them (grid-stride). Each warp adds its
+// per-step deltas into its slot and leaves (no CTA-wide barrier).
 // ---------------------------------------------------------------------------
 template <typename AgeT, bool SCAN, bool ADAPTIVE>
 __global__ void __launch_bounds__(kPushThreads, kPushCtasPerSm) push_step_kernel(const __grid_constant__ StepArgs a)
 {
-    __shared__ unsigned long long s_delta[kDeltaFields];
     __shared__ WarpScratch scratch[kPushThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31;
     WarpScratch& w = scratch[tid >> 5];
     float* pslot = w.p + lane * kPushG;
-    if (tid < kDeltaFields)
-        s_delta[tid] = 0ull;
     const int64_t k = a.ctl->step + a.j;
     const uint32_t par = (uint32_t)(k & 1);
     // the step's size: fixed, or (Section 5.2) min(dt_max, eps / (lambda* of
@@ -867,21 +864,7 @@ __global__ void __launch_bounds__(kPushThreads, kPushCtasPerSm) push_step_kernel
         if (lane == 0 && m)
             atomicMax(&a.ctl->lam[k % 3], m);
     }
-    const uint32_t fs_ = __reduce_add_sync(kFull, ld.fS), fe = __reduce_add_sync(kFull, ld.fE);
-    const uint32_t fi = __reduce_add_sync(kFull, ld.fI), ds = __reduce_add_sync(kFull, ld.dS);
-    __syncthreads();       // s_delta initialised
-    if (lane == 0) {
-        if (fs_) atomicAdd(&s_delta[0], (unsigned long long)fs_);
-        if (fe) atomicAdd(&s_delta[1], (unsigned long long)fe);
-        if (fi) atomicAdd(&s_delta[2], (unsigned long long)fi);
-        if (ds) atomicAdd(&s_delta[3], (unsigned long long)ds);
-    }
-    __syncthreads();
-    if (tid < kDeltaFields) {
-        const unsigned long long v = s_delta[tid];
-        if (v)
-            atomicAdd(a.deltas + (int64_t)a.j * kDeltaFields + tid, v);
-    }
+    warp_add_deltas(a.deltas, a.j, ld.fS, ld.fE, ld.fI, ld.dS);
 }
 
 // Initial counts (after init or set_state; counts and tallies zeroed): every

@@ -135,6 +135,32 @@ void collect(Request* q)
     }
 }
 
+// retires the queued requests that have waited longer than the wait limit
+// (FS_ETIMEOUT); they hold no device memory yet. Called with s->mu held.
+void expire_locked(fs_server* s, Clock::time_point now)
+{
+    if (s->cfg.wait_limit_s <= 0.0)
+        return;
+    const auto limit = std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(s->cfg.wait_limit_s));
+    std::deque<Request*> keep;
+    bool any = false;
+    for (Request* q : s->queue) {
+        if (now - q->t_submit > limit) {
+            q->status = FS_ETIMEOUT;
+            q->t_done = now;
+            q->done = true;
+            s->st.queued -= 1;
+            s->st.completed += 1;
+            any = true;
+        } else {
+            keep.push_back(q);
+        }
+    }
+    s->queue.swap(keep);
+    if (any)
+        s->cv.notify_all();
+}
+
 void serve(fs_server* s)
 {
     cudaSetDevice(s->device);
@@ -145,6 +171,7 @@ void serve(fs_server* s)
             std::unique_lock<std::mutex> lock(s->mu);
             if (s->stop)
                 break;
+            expire_locked(s, Clock::now());
             while (!s->queue.empty()) {
                 Request* q = s->queue.front();
                 const int64_t need_rows = ((int64_t)q->params.size() + 31) / 32;
@@ -235,7 +262,7 @@ fs_status fs_server_create(const fs_server_cfg* cfg, fs_server** out)
         c = *cfg;
     if (c.reserved_ != 0 || c.hbm_budget_bytes < 0 || c.max_members < 0 || c.quantum < 0 ||
         c.quantum > fs::kMaxGraphSteps || c.age_dtype < FS_AGE_F32 || c.age_dtype > FS_AGE_BF16 ||
-        c.max_inflight < -1)
+        c.max_inflight < -1 || !(c.wait_limit_s >= 0.0))
         return fail(FS_EINVAL, "fs_server_create: bad configuration");
     if (c.max_inflight == 0)
         c.max_inflight = (int64_t)1 << 25;

@@ -167,22 +167,6 @@ __device__ __forceinline__ TailResult tail_at(const StepArgs& a, int x, float ag
     return tail_p(a, x, age, node_p(a, x, age, c), i, step);
 }
 
-// warp-level delta accumulation into the CTA's shared counters
-__device__ __forceinline__ void warp_deltas(unsigned long long* s_delta, bool firedS, bool firedE,
-                                            bool firedI, uint32_t deg_if_firedS)
-{
-    const uint32_t a = __popc(__ballot_sync(kFull, firedS));
-    const uint32_t b = __popc(__ballot_sync(kFull, firedE));
-    const uint32_t c = __popc(__ballot_sync(kFull, firedI));
-    const uint32_t d = __reduce_add_sync(kFull, deg_if_firedS);
-    if ((threadIdx.x & 31) == 0) {
-        if (a) atomicAdd(&s_delta[0], (unsigned long long)a);
-        if (b) atomicAdd(&s_delta[1], (unsigned long long)b);
-        if (c) atomicAdd(&s_delta[2], (unsigned long long)c);
-        if (d) atomicAdd(&s_delta[3], (unsigned long long)d);
-    }
-}
-
 // ---------------------------------------------------------------------------
 // One-thread-per-node class: a warp owns `spw` consecutive 32-node SELL
 // slices; the states of four slices are loaded together so that their
@@ -383,7 +367,7 @@ template <> struct MergeShedSmem<false> {};
 
 template <typename AgeT, int MODE>
 __device__ __forceinline__ void merge_chunk(const StepArgs& a, uint32_t step, const uint32_t* __restrict__ bm,
-                                            uint32_t* __restrict__ bmn, int chunk, unsigned long long* s_delta,
+                                            uint32_t* __restrict__ bmn, int chunk,
                                             float dt, float& lmax)
 {
     constexpr bool SHED = (MODE & kModeShed) != 0, ADPT = (MODE & kModeAdaptive) != 0;
@@ -613,7 +597,7 @@ __device__ __forceinline__ void merge_chunk(const StepArgs& a, uint32_t step, co
             dS = fS ? (uint32_t)(rhi - rlo) : 0u;
         }
     }
-    warp_deltas(s_delta, fS, fE, fI, dS);
+    warp_add_deltas(a.deltas, a.j, fS, fE, fI, dS);
     __syncthreads();
     if (tid < 8) {
         const int w = ((a.m_base + R0) >> 5) + tid;
@@ -635,9 +619,6 @@ __global__ void __launch_bounds__(kStepThreads, kStepCtasPerSm) fused_step_kerne
     // step loop launches without it (graph kernel nodes measured faster).
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
-    __shared__ unsigned long long s_delta[kDeltaFields];
-    if (threadIdx.x < kDeltaFields)
-        s_delta[threadIdx.x] = 0ull;
     const int64_t k = a.ctl->step + a.j;
     const uint32_t par = (uint32_t)(k & 1);
     const uint32_t* __restrict__ bm = a.bm[par];
@@ -645,14 +626,13 @@ __global__ void __launch_bounds__(kStepThreads, kStepCtasPerSm) fused_step_kerne
     float dt = a.M.dt;
     if constexpr ((MODE & kModeAdaptive) != 0)
         dt = adaptive_dt(a, k);
-    __syncthreads();
     LaneDeltas ld;
     bool merge_cta = false;
     if constexpr (HAS_MERGE)
         merge_cta = (int)blockIdx.x < a.n_chunks;
     if (merge_cta) {
         if constexpr (HAS_MERGE)
-            merge_chunk<AgeT, MODE>(a, (uint32_t)k, bm, bmn, (int)blockIdx.x, s_delta, dt, ld.lmax);
+            merge_chunk<AgeT, MODE>(a, (uint32_t)k, bm, bmn, (int)blockIdx.x, dt, ld.lmax);
     } else {
         const int cta = (int)blockIdx.x - (HAS_MERGE ? a.n_chunks : 0);
         const SliceMap smap = slice_map(a);
@@ -664,23 +644,10 @@ __global__ void __launch_bounds__(kStepThreads, kStepCtasPerSm) fused_step_kerne
             else
                 sell_warp<AgeT, MODE, false>(a, (uint32_t)k, bm, bmn, s_begin, s_end, ld, smap, dt);
         }
-        const uint32_t fs_ = __reduce_add_sync(kFull, ld.fS), fe = __reduce_add_sync(kFull, ld.fE);
-        const uint32_t fi = __reduce_add_sync(kFull, ld.fI), ds = __reduce_add_sync(kFull, ld.dS);
-        if ((threadIdx.x & 31) == 0) {
-            if (fs_) atomicAdd(&s_delta[0], (unsigned long long)fs_);
-            if (fe) atomicAdd(&s_delta[1], (unsigned long long)fe);
-            if (fi) atomicAdd(&s_delta[2], (unsigned long long)fi);
-            if (ds) atomicAdd(&s_delta[3], (unsigned long long)ds);
-        }
+        warp_add_deltas(a.deltas, a.j, ld.fS, ld.fE, ld.fI, ld.dS);
     }
     if constexpr ((MODE & kModeAdaptive) != 0)
         adaptive_lmax(a, k, ld.lmax);
-    __syncthreads();
-    if (threadIdx.x < kDeltaFields) {
-        const unsigned long long v = s_delta[threadIdx.x];
-        if (v)
-            atomicAdd(a.deltas + (int64_t)a.j * kDeltaFields + threadIdx.x, v);
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -746,11 +713,8 @@ __global__ void __launch_bounds__(kSmemThreads, 1) sell_smem_kernel(const __grid
 {
     extern __shared__ __align__(128) uint32_t sbm[];
     __shared__ __align__(8) unsigned long long mbar;
-    __shared__ unsigned long long s_delta[kDeltaFields];
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid < kDeltaFields)
-        s_delta[tid] = 0ull;
+    const int tid = threadIdx.x;
     const int64_t k = a.ctl->step + a.j;
     const uint32_t par = (uint32_t)(k & 1);
     const uint32_t* __restrict__ bm = a.bm[par];
@@ -782,20 +746,7 @@ __global__ void __launch_bounds__(kSmemThreads, 1) sell_smem_kernel(const __grid
     // the copy into this CTA's shared memory must have landed before it exits
     if (!ready && !mbar_wait(mb, 0u, kWaitLimit))
         record_error(a.ctl, kErrTmaTimeout);
-    const uint32_t fs_ = __reduce_add_sync(kFull, ld.fS), fe = __reduce_add_sync(kFull, ld.fE);
-    const uint32_t fi = __reduce_add_sync(kFull, ld.fI), ds = __reduce_add_sync(kFull, ld.dS);
-    if (lane == 0) {
-        if (fs_) atomicAdd(&s_delta[0], (unsigned long long)fs_);
-        if (fe) atomicAdd(&s_delta[1], (unsigned long long)fe);
-        if (fi) atomicAdd(&s_delta[2], (unsigned long long)fi);
-        if (ds) atomicAdd(&s_delta[3], (unsigned long long)ds);
-    }
-    __syncthreads();
-    if (tid < kDeltaFields) {
-        const unsigned long long v = s_delta[tid];
-        if (v)
-            atomicAdd(a.deltas + (int64_t)a.j * kDeltaFields + tid, v);
-    }
+    warp_add_deltas(a.deltas, a.j, ld.fS, ld.fE, ld.fI, ld.dS);
 }
 
 // Memoised Bernoulli probabilities of one sim: the fixed-step age sequence
@@ -867,13 +818,32 @@ __global__ void run_begin_kernel(DevCtl* ctl, uint32_t* out)
     }
 }
 
+static_assert(kDeltaSlots == 32, "the epilogue sums one delta slot per lane");
+
 __global__ void run_epilogue_kernel(DevCtl* ctl, unsigned long long* deltas, int K, int model, const float* dtrec,
                                     float dt)
 {
     __shared__ unsigned long long d[kMaxGraphSteps][kDeltaFields];
-    for (int t = threadIdx.x; t < K * kDeltaFields; t += blockDim.x) {
-        d[t / kDeltaFields][t % kDeltaFields] = deltas[t];
-        deltas[t] = 0ull;
+    // warp w sums the slots of steps w, w + warps, ... (lane = slot) and
+    // clears them for the next launch sequence
+    const int lane = threadIdx.x & 31, nw = (int)(blockDim.x >> 5);
+    for (int j = (int)(threadIdx.x >> 5); j < K; j += nw) {
+        ulonglong2* row = reinterpret_cast<ulonglong2*>(deltas + (int64_t)j * kDeltaRow + lane * kDeltaFields);
+        const ulonglong2 v0 = row[0], v1 = row[1];
+        row[0] = make_ulonglong2(0ull, 0ull);
+        row[1] = make_ulonglong2(0ull, 0ull);
+        unsigned long long f[kDeltaFields] = {v0.x, v0.y, v1.x, v1.y};
+#pragma unroll
+        for (int q = 0; q < kDeltaFields; ++q) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                f[q] += __shfl_xor_sync(kFull, f[q], o);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < kDeltaFields; ++q)
+                d[j][q] = f[q];
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1158,7 +1128,7 @@ cudaError_t launch_run_begin(DevCtl* ctl, uint32_t* out, cudaStream_t s)
 cudaError_t launch_run_epilogue(DevCtl* ctl, unsigned long long* deltas, int K, int model, const float* dtrec,
                                 float dt, cudaStream_t s)
 {
-    run_epilogue_kernel<<<1, 256, 0, s>>>(ctl, deltas, K, model, dtrec, dt);
+    run_epilogue_kernel<<<1, 1024, 0, s>>>(ctl, deltas, K, model, dtrec, dt);
     g_launch_count += 1;
     return cudaGetLastError();
 }

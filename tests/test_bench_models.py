@@ -40,3 +40,28 @@ def test_pull_byte_model_by_hand():
 def test_whole_job_throughput():
     # 10^6 nodes x 1,000 steps x 5 benchmark steps x 2 replicas in 100 ms
     assert bench.whole_job_gnups(1_000_000, 1000, 5, 2, 100.0) == pytest.approx(100.0)
+
+
+def test_host_oracle_pool_steps_independent_realisations():
+    """The CPU baseline's pool: every worker is the oracle on its own
+    replicate, and its realisation equals the oracle run directly."""
+    import math
+    import oracle as om
+    import workloads as W
+    g = W.random_regular(3000, 6, seed=2)
+    idx = W.index_nodes(g.n, 30, seed=3)
+    h = bench.HostOracle(g, idx, workers=2)
+    try:
+        upd, wall, steps = h.advance(12)
+        assert steps == [12, 12] and upd == g.n * 24 and wall > 0
+        got = h.counts()
+    finally:
+        h.close()
+    for rep, (k, c) in enumerate(got):
+        prm = om.params(om.SEIR, om.law("weibull", 2.0, 4.0), om.law("lognormal", math.log(6.0), 0.6), 0.25, 0.1,
+                        seed=1, rep=rep)
+        X, A = om.init(g.n, idx, om.E)
+        ref, _, _ = om.run(g.row_ptr, g.col_ind, prm, 0, 12, X, A)
+        assert k == 12
+        assert c == ref[-1].tolist()
+    assert got[0][1] != got[1][1], "the two replicates must draw different uniforms"

@@ -6,7 +6,8 @@ belongs to their own pool. Its scratch lives in a fixed array inside the
 library. This test drives it through the C ABI on caller-owned buffers for two
 consecutive steps and checks that it produces exactly what fs_sim_step
 produces (the tolerance of the step parity tests: bit-identical states and
-ages), on a graph whose merge class uses that scratch. It sits in a file that
+ages), on a graph whose merge class uses that scratch, for each age storage
+type (FP32, and FP16 and BF16 compared as their 16-bit patterns). It sits in a file that
 pytest collects last, and must pass alone in a fresh process as well as after
 the other tests.
 """
@@ -39,7 +40,11 @@ def bitmap(X: np.ndarray) -> np.ndarray:
     return (bits.reshape(words, 32) << np.arange(32, dtype=np.uint64)).sum(axis=1).astype(np.uint32)
 
 
-def test_noalloc_step_matches_sim_step_twice():
+AGE_TORCH = {fs.FS_AGE_F32: "float32", fs.FS_AGE_F16: "float16", fs.FS_AGE_BF16: "bfloat16"}
+
+
+@pytest.mark.parametrize("age_dtype", [fs.FS_AGE_F32, fs.FS_AGE_F16, fs.FS_AGE_BF16])
+def test_noalloc_step_matches_sim_step_twice(age_dtype):
     import torch
     assert torch.cuda.is_available()
     g = degree_sorted(W.barabasi_albert(60_000, 5, seed=3))
@@ -48,23 +53,25 @@ def test_noalloc_step_matches_sim_step_twice():
     assert info["identity_layout"] == 1
     assert 0 < info["n_merge"] <= 65536 and info["merge_chunks"] > 1
     p = fs.sim_params(fs.FS_SEIR, fs.law("lognormal", math.log(6.0), 0.6), 0.25, 0.1, seed=17,
-                      latent=fs.law("weibull", 2.0, 4.0))
+                      latent=fs.law("weibull", 2.0, 4.0), age_dtype=age_dtype)
     idx = W.index_nodes(g.n, 60, seed=5, allowed=W.non_hub_nodes(g))
     sh = fs.fs_sim_init(gh, p, idx)
     fs.fs_sim_run(sh, 150, want_counts=False)            # into the growth phase
-    X0, A0, k0 = fs.fs_sim_get_state(sh, g.n)
+    X0, A0, k0 = fs.fs_sim_get_state(sh, g.n, age_dtype)
     c0 = fs.fs_sim_run(sh, 0)[0].astype(np.int64)
     ref = []
     for _ in range(2):
         c = fs.fs_sim_step(sh).astype(np.int64)
-        X, A, _ = fs.fs_sim_get_state(sh, g.n)
+        X, A, _ = fs.fs_sim_get_state(sh, g.n, age_dtype)
         ref.append((X, A, c))
     fs.fs_sim_destroy(sh)
     assert (ref[1][2] != c0).any(), "the window must contain transitions"
 
     dev = torch.device("cuda")
     dX = torch.from_numpy(X0.copy()).to(dev)
-    dA = torch.from_numpy(A0.copy()).to(dev)
+    # ages travel as their raw storage bits, then are viewed as the storage type
+    dA = torch.from_numpy(A0.copy().view(np.int32 if A0.itemsize == 4 else np.int16)).to(dev)
+    dA = dA.view(getattr(torch, AGE_TORCH[age_dtype]))
     bm = [torch.from_numpy(bitmap(X0).view(np.int32)).to(dev),
           torch.zeros((g.n >> 5) + 1, dtype=torch.int32, device=dev)]
     deltas = torch.zeros(5, dtype=torch.int64, device=dev)
@@ -76,7 +83,9 @@ def test_noalloc_step_matches_sim_step_twice():
         torch.cuda.synchronize()
         X_ref, A_ref, c_ref = ref[t]
         np.testing.assert_array_equal(dX.cpu().numpy(), X_ref)
-        np.testing.assert_array_equal(dA.cpu().numpy().view(np.uint32), A_ref.view(np.uint32))
+        bits = np.uint32 if A_ref.itemsize == 4 else np.uint16
+        got = dA.view(torch.int32 if A_ref.itemsize == 4 else torch.int16).cpu().numpy().view(bits)
+        np.testing.assert_array_equal(got, A_ref.view(bits))
         np.testing.assert_array_equal(bm[(t + 1) % 2].cpu().numpy().view(np.uint32), bitmap(X_ref))
         d = deltas.cpu().numpy()
         assert d[4] == 0
