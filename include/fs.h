@@ -464,6 +464,34 @@ fs_status fs_server_stats_get(fs_server* s, fs_server_stats* out);
 fs_status fs_server_destroy(fs_server* s);
 
 /* ---------------------------------------------------------------------------
+ * Failure-detection test hooks. The paper has no counterpart: these let the
+ * tests make the library's own bounded device waits and bounds checks fire
+ * without faulting the GPU. They affect only simulations created while the
+ * setting is in force (the setting is copied at fs_sim_init); 0 turns it off.
+ *   FS_TEST_WAIT_TIMEOUT  value = a wait limit in polls (1 .. 2^20): the
+ *                         merge-class chunks of the gather form arm their
+ *                         mbarrier but issue no bulk copy, so the bounded
+ *                         wait runs out with nothing in flight; the step then
+ *                         sets the device error word and returns, and the
+ *                         next synchronising call reports FS_ETIMEOUT (the
+ *                         simulation then answers FS_ESTATE; other handles
+ *                         and the CUDA context stay usable).
+ *   FS_TEST_BOUNDS_SHRINK value = how far below the end of the transposed
+ *                         CSR the bounds check of its column reads is put
+ *                         (the reads it rejects are still inside the buffer);
+ *                         only in the bounds-checked build (FS_DEBUG_BOUNDS),
+ *                         else FS_EUNSUPPORTED.
+ * In the bounds-checked build the step kernels check the indices of their
+ * main accesses; the first index out of range is recorded with its check's
+ * site, the access is skipped, and the call reports FS_ECUDA with "bounds
+ * check failed: site S, index I" in fs_last_error.
+ * ------------------------------------------------------------------------- */
+enum { FS_TEST_WAIT_TIMEOUT = 1, FS_TEST_BOUNDS_SHRINK = 2 };
+fs_status fs_test_inject(int32_t what, int64_t value);
+/* *enabled = 1 in the bounds-checked build, else 0. */
+fs_status fs_debug_bounds_build(int32_t* enabled);
+
+/* ---------------------------------------------------------------------------
  * fs_step_noalloc -- one fused step that allocates no device memory. The
  * paper has no counterpart: this entry point exists for callers that cannot
  * call cudaMalloc while they step -- code running inside CUDA stream capture

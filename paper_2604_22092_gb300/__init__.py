@@ -20,7 +20,7 @@ from ._abi import (FS_AGE_BF16, FS_AGE_F16, FS_AGE_F32, FS_DISPATCH_AUTO, FS_DIS
                    FS_DISPATCH_THREAD, FS_DISPATCH_TUNE, FS_E, FS_I, FS_LAW_ERLANG, FS_LAW_EXP, FS_LAW_LOGNORMAL,
                    FS_LAW_NONE, FS_LAW_WEIBULL, FS_PRESSURE_AUTO, FS_PRESSURE_GATHER, FS_PRESSURE_PUSH, FS_R,
                    FS_S, FS_SEIR, FS_SHED_DENSITY, FS_SHED_HAZARD, FS_SHED_NONE, FS_SIR, FS_SIS, FS_ACTIVE_LIST,
-                   FsError, check)
+                   FS_TEST_BOUNDS_SHRINK, FS_TEST_WAIT_TIMEOUT, FsError, check)
 
 __all__ = [
     "fs_version", "fs_last_error", "fs_graph_create", "fs_graph_info_get", "fs_graph_destroy",
@@ -32,12 +32,12 @@ __all__ = [
     "fs_eval_uniforms", "fs_step_noalloc", "fs_ens_create", "fs_ens_run", "fs_ens_get_state",
     "fs_ens_destroy", "fs_batch_create", "fs_batch_add", "fs_batch_run", "fs_batch_status", "fs_batch_destroy",
     "fs_server_create", "fs_server_submit", "fs_server_poll", "fs_server_drain", "fs_server_stats_get",
-    "fs_server_destroy",
+    "fs_server_destroy", "fs_test_inject", "fs_debug_bounds_build",
     "law", "sim_params", "graph_opts", "FsError", "load",
     "FS_S", "FS_E", "FS_I", "FS_R", "FS_SIR", "FS_SEIR", "FS_SIS", "FS_AGE_F32", "FS_AGE_F16", "FS_AGE_BF16",
     "FS_DISPATCH_AUTO", "FS_DISPATCH_THREAD", "FS_DISPATCH_MERGE", "FS_DISPATCH_TUNE",
     "FS_PRESSURE_AUTO", "FS_PRESSURE_GATHER", "FS_PRESSURE_PUSH", "FS_SHED_NONE", "FS_SHED_HAZARD",
-    "FS_SHED_DENSITY", "FS_ACTIVE_LIST",
+    "FS_SHED_DENSITY", "FS_ACTIVE_LIST", "FS_TEST_WAIT_TIMEOUT", "FS_TEST_BOUNDS_SHRINK",
 ]
 
 
@@ -285,6 +285,17 @@ def fs_step_noalloc(g: int, params: _abi.fs_sim_params, step: int, state_dev, ag
     check(load().fs_step_noalloc(g, ctypes.byref(params), int(step), _addr(state_dev), _addr(age_dev),
                                  _addr(bitmap_cur_dev), _addr(bitmap_next_dev), _addr(deltas_dev),
                                  _stream(stream)), "fs_step_noalloc")
+
+
+def fs_test_inject(what: int, value: int) -> None:
+    """Failure-detection test settings for sims created afterwards (fs.h)."""
+    check(load().fs_test_inject(int(what), int(value)), "fs_test_inject")
+
+
+def fs_debug_bounds_build() -> bool:
+    e = ctypes.c_int32()
+    check(load().fs_debug_bounds_build(ctypes.byref(e)), "fs_debug_bounds_build")
+    return bool(e.value)
 
 
 # --------------------------------------------------------------- ensembles

@@ -22,6 +22,7 @@ FS_PRESSURE_AUTO, FS_PRESSURE_GATHER, FS_PRESSURE_PUSH = 0, 1, 2
 FS_SHED_NONE, FS_SHED_HAZARD, FS_SHED_DENSITY = 0, 1, 2
 FS_ACTIVE_LIST = 0x4
 FS_LAW_NONE, FS_LAW_EXP, FS_LAW_LOGNORMAL, FS_LAW_WEIBULL, FS_LAW_ERLANG = 0, 1, 2, 3, 4
+FS_TEST_WAIT_TIMEOUT, FS_TEST_BOUNDS_SHRINK = 1, 2
 
 
 class fs_law(ctypes.Structure):
@@ -76,6 +77,8 @@ PROTOTYPES = {
     "fs_graph_create": (ctypes.c_int, [ctypes.c_int64, VP, VP, VP, P(fs_graph_opts), VP, P(VP)]),
     "fs_graph_info_get": (ctypes.c_int, [VP, P(fs_graph_info)]),
     "fs_graph_destroy": (ctypes.c_int, [VP]),
+    "fs_test_inject": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64]),
+    "fs_debug_bounds_build": (ctypes.c_int, [P(ctypes.c_int32)]),
     "fs_sim_init": (ctypes.c_int, [VP, P(fs_sim_params), VP, ctypes.c_int64, VP, P(VP)]),
     "fs_sim_step": (ctypes.c_int, [VP, VP]),
     "fs_sim_run": (ctypes.c_int, [VP, ctypes.c_int64, ctypes.c_int32, VP]),

@@ -22,6 +22,11 @@ namespace fsapi {
 
 thread_local std::string g_err;
 
+// failure-detection test settings (fs_test_inject), copied into every sim
+// created while they are set
+std::atomic<uint32_t> g_test_wait_limit{0};
+std::atomic<int64_t> g_test_bounds_shrink{0};
+
 fs_status fail(fs_status st, const char* fmt, ...)
 {
     char buf[512];
@@ -275,6 +280,13 @@ fs::StepArgs step_args(const fs_sim* s, int j)
     a.e_total = g->nnz;
     a.mk_mode = s->p.markov_mode;
     a.dtrec = s->d_dtrec;
+    a.wait_limit = s->test_wait_limit;
+    a.skip_bulk_copy = s->test_wait_limit ? 1 : 0;
+    a.x_len = (g->n + 15) / 16 * 16 + 16;
+    a.out_nnz = g->d_out_col ? g->nnz : 0;
+    a.dbg_shrink = s->test_bounds_shrink;
+    a.sell_len = g->sell_entries;
+    a.bm_words = (g->n >> 5) + 1;
     return a;
 }
 
@@ -355,6 +367,9 @@ fs_status check_device_error(fs_sim* s)
         s->failed = true;
         if (c.error == fs::kErrTmaTimeout)
             return fail(FS_ETIMEOUT, "a bounded device wait ran out (error word %d)", c.error);
+        if (c.error == fs::kErrBounds)
+            return fail(FS_ECUDA, "bounds check failed: site %d, index %lld (error word %d)", c.dbg_site,
+                        (long long)c.dbg_index, c.error);
         return fail(FS_ECUDA, "device error word %d", c.error);
     }
     return FS_OK;
@@ -669,6 +684,8 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
     fs_sim* s = new fs_sim();
     s->g = g;
     s->p = *params;
+    s->test_wait_limit = g_test_wait_limit.load();
+    s->test_bounds_shrink = g_test_bounds_shrink.load();
     s->pressure = (markov || shed || pform == FS_PRESSURE_GATHER || !push_available(g)) ? FS_PRESSURE_GATHER
                                                                                         : FS_PRESSURE_PUSH;
     s->markov = markov;
@@ -922,6 +939,40 @@ fs_status fs_sim_run_timed(fs_sim* s, int64_t steps, int32_t graph_steps, uint32
     for (auto& e : ev)
         cudaEventDestroy(e);
     return st;
+}
+
+fs_status fs_test_inject(int32_t what, int64_t value)
+{
+    g_err.clear();
+    if (what == FS_TEST_WAIT_TIMEOUT) {
+        if (value < 0 || value > (int64_t)fs::kWaitLimit)
+            return fail(FS_EINVAL, "fs_test_inject: wait limit must be in [0, %u]", fs::kWaitLimit);
+        g_test_wait_limit.store((uint32_t)value);
+        return FS_OK;
+    }
+    if (what == FS_TEST_BOUNDS_SHRINK) {
+#ifndef FS_DEBUG_BOUNDS
+        return fail(FS_EUNSUPPORTED, "fs_test_inject: bounds checks exist only in the FS_DEBUG_BOUNDS build");
+#else
+        if (value < 0)
+            return fail(FS_EINVAL, "fs_test_inject: shrink must be >= 0");
+        g_test_bounds_shrink.store(value);
+        return FS_OK;
+#endif
+    }
+    return fail(FS_EINVAL, "fs_test_inject: unknown setting %d", what);
+}
+
+fs_status fs_debug_bounds_build(int32_t* enabled)
+{
+    if (!enabled)
+        return fail(FS_EINVAL, "NULL argument");
+#ifdef FS_DEBUG_BOUNDS
+    *enabled = 1;
+#else
+    *enabled = 0;
+#endif
+    return FS_OK;
 }
 
 fs_status fs_kernel_launches(uint64_t* count)

@@ -236,6 +236,27 @@ __device__ __forceinline__ float shed_value(const LawF& L, int mode, float beta,
     return __fmul_rn(beta, s);
 }
 
+// Bounds checks of bounds-checked builds (FS_DEBUG_BOUNDS): an index at or
+// beyond its bound records kErrBounds with the index and the check's site in
+// the control block (the first one wins) and the access it guards is skipped.
+// Other builds compile every check to `true`.
+static __device__ __noinline__ bool bounds_reject(DevCtl* ctl, int site, long long idx)
+{
+    if (atomicCAS(&ctl->error, 0, kErrBounds) == 0) {
+        ctl->dbg_index = idx;
+        ctl->dbg_site = site;
+    }
+    return false;
+}
+#ifdef FS_DEBUG_BOUNDS
+#define FS_IN_BOUNDS(ctl, site, idx, bound) \
+    ((unsigned long long)(long long)(idx) < (unsigned long long)(long long)(bound) \
+         ? true                                                                         \
+         : ::fs::bounds_reject((ctl), (site), (long long)(idx)))
+#else
+#define FS_IN_BOUNDS(ctl, site, idx, bound) true
+#endif
+
 // Adds one warp's step totals into its delta slot of row j (every lane of the
 // warp calls this with its own counts; lanes 0..3 issue one atomic each, and
 // only for non-zero totals). No barrier: warps that finish early leave.

@@ -85,9 +85,24 @@ struct DevCtl {
     unsigned int mk_nev;
     unsigned int pad3_;
     unsigned long long transitions;   // node transitions since init / set_state
+    // bounds-checked builds (FS_DEBUG_BOUNDS): the first index a check
+    // rejected and the check's site number (kErrBounds in `error`)
+    long long dbg_index;
+    int32_t dbg_site;
+    int32_t pad4_;
 };
 
-enum { kErrNone = 0, kErrTmaTimeout = 1, kErrBadState = 2, kErrBadGraph = 3 };
+enum { kErrNone = 0, kErrTmaTimeout = 1, kErrBadState = 2, kErrBadGraph = 3, kErrBounds = 4 };
+
+// sites of the FS_DEBUG_BOUNDS checks (reported with the rejected index)
+enum {
+    kSiteGroup = 1,        // push step: a group's vector of node slots
+    kSiteOutPtr = 2,       // push step: a pushing node's transposed row bounds
+    kSiteOutCol = 3,       // push step: a transposed column index
+    kSitePushTarget = 4,   // push step: the node a push lands on
+    kSiteSellCol = 5,      // gather: a SELL column entry
+    kSiteBitmap = 6,       // gather: a bitmap word
+};
 
 // Per-step deltas accumulated by the step kernel (atomics, skipped when 0):
 // [0] nodes that left S, [1] E -> I, [2] I -> R, [3] sum of degrees of the
@@ -181,6 +196,21 @@ struct StepArgs {
     double mk_avg_deg;            // edges / nodes
     int64_t e_total;              // edges
     int32_t mk_mode;              // influence update: 0 by cost, 1 inertial, 2 control
+    // failure-detection tests (fs_test_inject): the bounded mbarrier waits
+    // give up after wait_limit polls (0 = kWaitLimit); with skip_bulk_copy
+    // set the merge chunks arm their barrier but issue no copy, so their
+    // waits run out with nothing in flight
+    uint32_t wait_limit;
+    int32_t skip_bulk_copy;
+    // lengths the FS_DEBUG_BOUNDS checks compare against (set in every
+    // build; read only by bounds-checked builds): node slots of X, entries
+    // of the transposed CSR (minus dbg_shrink, a test knob that puts the
+    // check's bound below the buffer's end), SELL column entries, bitmap words
+    int64_t x_len;
+    int64_t out_nnz;
+    int64_t dbg_shrink;
+    int64_t sell_len;
+    int64_t bm_words;
 };
 
 enum { kShedNone = 0, kShedHazard = 1, kShedDensity = 2 };

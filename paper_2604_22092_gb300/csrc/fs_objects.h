@@ -80,6 +80,10 @@ struct fs_sim {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     bool failed = false;
+    // failure-detection test settings in force when the sim was created
+    // (fs_test_inject): wait limit with no bulk copies, bounds-check shrink
+    uint32_t test_wait_limit = 0;
+    int64_t test_bounds_shrink = 0;
 };
 
 

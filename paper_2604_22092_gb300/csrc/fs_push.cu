@@ -43,11 +43,6 @@ namespace {
 
 constexpr uint32_t kFull = 0xffffffffu;
 
-__device__ __noinline__ float p_direct_p(const ModelF& M, int x, float age)
-{
-    return p_of_rate(M, hazard(x == kE ? M.lat : M.inf, age));
-}
-
 // the hazard of an E or I node (adaptive step: evaluated every step; out of line)
 __device__ __noinline__ float rate_ei(const ModelF& M, int x, float age)
 {
@@ -68,33 +63,6 @@ __device__ __noinline__ float p_table_miss(const StepArgs& a, int x, float age)
     return p_of_rate(a.M, hazard(x == kE ? a.M.lat : a.M.inf, age));
 }
 
-// Bernoulli probability of one node this step, from the per-sim tables built
-// at init by the same FP32 code (identical bits to direct evaluation)
-__device__ __forceinline__ float node_p_push(const StepArgs& a, int x, float age, uint32_t c)
-{
-    if (x == kS) {
-        if (c == 0u)
-            return 0.0f;
-        if (c < (uint32_t)kPSTableN)
-            return __ldg(a.ps + c);
-        return p_of_rate(a.M, __fmul_rn(a.M.beta, (float)c));
-    }
-    if (x == kE || x == kI) {
-        const int n = __float2int_rn(__fmul_rn(age, a.M.inv_dt));
-        if ((unsigned)n < (unsigned)kPTableN) {
-            const float4* row = a.ptab + (x == kI ? kPTableN : 0) + n;
-            const float2 e = __ldg(reinterpret_cast<const float2*>(row));
-            if (e.x == age)
-                return e.y;
-            const float p1 = ptab_slot1(row, age);
-            if (p1 >= 0.0f)
-                return p1;
-        }
-        return p_direct_p(a.M, x, age);
-    }
-    return 0.0f;
-}
-
 struct PushDeltas {
     uint32_t fS = 0, fE = 0, fI = 0, dS = 0;
 };
@@ -105,35 +73,6 @@ __device__ __forceinline__ int next_state(const StepArgs& a, int x, bool fired)
     if (!fired)
         return x;
     return (x == kS) ? (a.M.model == kSEIR ? kE : kI) : (x + 1);
-}
-
-// +1 / -1 into the pending tally of node j (parity par)
-__device__ __forceinline__ void push_pending(const StepArgs& a, uint32_t par, uint32_t j, bool minus)
-{
-    if (j < (uint32_t)a.n_thr) {
-        unsigned int* w = reinterpret_cast<unsigned int*>(a.pd16[par]) + (j >> 1);
-        atomicAdd(w, (minus ? 0x100u : 0x1u) << ((j & 1u) << 4));
-    } else if (j < (uint32_t)a.n) {
-        atomicAdd(a.pd64[par] + (j - (uint32_t)a.n_thr), minus ? (1ull << 32) : 1ull);
-    }
-}
-
-// +1 straight into the count of node j (initial counts)
-__device__ __forceinline__ void push_count(const StepArgs& a, uint32_t j)
-{
-    if (j < (uint32_t)a.n_thr)
-        atomicAdd(reinterpret_cast<unsigned int*>(a.cnt8) + (j >> 2), 1u << ((j & 3u) << 3));
-    else if (j < (uint32_t)a.n)
-        atomicAdd(a.hcnt + (j - (uint32_t)a.n_thr), 1u);
-}
-
-template <bool INIT>
-__device__ __forceinline__ void push_one(const StepArgs& a, uint32_t par, uint32_t j, bool minus)
-{
-    if constexpr (INIT)
-        push_count(a, j);
-    else
-        push_pending(a, par, j, minus);
 }
 
 // eight ages of storage type AgeT as FP32 values
@@ -197,31 +136,26 @@ __device__ __forceinline__ void set_byte(uint2& v, int u, uint32_t b)
         v.y = (v.y & m) | (b << sh);
 }
 
-// Per-warp shared scratch of the step: probabilities by node slot (lane * 8 +
-// u), the queue of draws (original node id and slot), decisions by slot, and
-// the warp's push events.
-constexpr int kWarpSlots = 32 * kPushG;
+// ---------------------------------------------------------------------------
+// One round of a warp: every lane holds one item, a group of kPushG
+// consecutive thread-class nodes or one merge-class node. The nodes that can
+// change this step (E and I nodes, S nodes with an infectious in-neighbour)
+// are queued in shared memory and the 32 lanes share the queue evenly, so a
+// round costs a table lookup and a Philox draw per queued node and a few
+// byte-parallel (SWAR) operations per group: classification, the fold of the
+// pending tallies and the transitions work on eight nodes at once.
+// ---------------------------------------------------------------------------
+constexpr int kWarpSlots = 32 * kPushG;       // node slots of a round: lane * kPushG + u
 
 struct WarpScratch {
-    float p[kWarpSlots];          // p of the node in slot lane * kPushG + u
-    uint32_t qnode[kWarpSlots];   // draw queue: original node ids
-    uint16_t qslot[kWarpSlots];   // draw queue: slots
-    uint8_t fired[kWarpSlots];    // decision by slot
+    uint8_t xb[kWarpSlots];       // state of the node in each slot (R for empty slots)
+    uint8_t cb[kWarpSlots];       // infectious in-neighbour count (thread class)
+    uint8_t fb[kWarpSlots];       // decision: 0xff fired, 0 not
+    uint8_t q[kWarpSlots];        // the round's queue of slots that draw
+    float age[kWarpSlots];        // age of the E/I node in each slot
+    int32_t base[32];             // first node of each lane's item
+    uint32_t hc[32];              // count of a lane's merge-class node, ~0 for a group
     uint32_t ev[kWarpSlots];      // push events: node | (1u << 31) when it left I
-};
-
-// What one lane carries from the preparation of its item to the application
-// of the Bernoulli decisions: a group of kPushG thread-class nodes or one
-// merge-class node.
-struct Item {
-    int kind;            // 0 = none, 1 = group, 2 = merge-class node
-    int base;            // first node of the item
-    int nv;              // nodes of the group inside the thread class
-    uint2 xs;            // states (kR for nodes outside the item)
-    uint2 nc;            // counts after folding in the pending tallies
-    bool anyEI, clear;   // ages were loaded; pending tallies to clear
-    float age[kPushG];
-    uint32_t need;       // bit u: node base + u draws a uniform (p > 0)
 };
 
 enum { kItemNone = 0, kItemGroup = 1, kItemHub = 2 };
@@ -245,7 +179,7 @@ __device__ __forceinline__ GroupLoads group_loads(const StepArgs& a, uint32_t pa
     g.c8 = make_uint2(0u, 0u);
     g.pd = make_uint4(0u, 0u, 0u, 0u);
     g.have_cp = false;
-    if (t < n_grp) {
+    if (t < n_grp && FS_IN_BOUNDS(a.ctl, kSiteGroup, t * kPushG + kPushG - 1, a.x_len)) {
         const int i0 = (int)(t * kPushG);
         g.xs = *reinterpret_cast<const uint2*>(a.X + i0);
         if (spec_s) {
@@ -255,6 +189,20 @@ __device__ __forceinline__ GroupLoads group_loads(const StepArgs& a, uint32_t pa
         }
     }
     return g;
+}
+
+// states of a group with the bytes of nodes at or beyond n_thr (a partial
+// last group) set to R
+__device__ __forceinline__ uint2 group_states(const StepArgs& a, int i0, uint2 xs)
+{
+    const int nv = a.n_thr - i0;
+    if (nv < kPushG) {
+#pragma unroll
+        for (int u = 0; u < kPushG; ++u)
+            if (u >= nv)
+                set_byte(xs, u, kR);
+    }
+    return xs;
 }
 
 // A group in which nothing can happen this step: no E or I node, and every S
@@ -267,14 +215,7 @@ __device__ __forceinline__ bool group_idle(const StepArgs& a, uint32_t par, int6
     if (t >= n_grp)
         return true;
     const int i0 = (int)(t * kPushG);
-    uint2 xs = gl.xs;
-    const int nv = min(kPushG, a.n_thr - i0);
-    if (nv < kPushG) {
-#pragma unroll
-        for (int u = 0; u < kPushG; ++u)
-            if (u >= nv)
-                set_byte(xs, u, kR);
-    }
+    const uint2 xs = group_states(a, i0, gl.xs);
     const uint32_t ei = __vcmpeq4(xs.x, 0x01010101u) | __vcmpeq4(xs.x, 0x02020202u) |
                         __vcmpeq4(xs.y, 0x01010101u) | __vcmpeq4(xs.y, 0x02020202u);
     if (ei)
@@ -294,178 +235,171 @@ __device__ __forceinline__ bool group_idle(const StepArgs& a, uint32_t par, int6
             (gl.pd.w & m3)) == 0u;
 }
 
-// Eight consecutive thread-class nodes i0 .. i0+7 (i0 a multiple of 8), from
-// their early loads: counts, pending tallies (unless loaded early) and ages,
-// then the probability-table loads of all eight nodes issued together; the
-// probabilities go to the lane's slots in shared memory. Nodes at or beyond
-// n_thr (a partial last group) are treated as R.
-template <typename AgeT, bool ADAPTIVE>
-__device__ __forceinline__ void group_prepare(const StepArgs& a, uint32_t par, int i0, const GroupLoads& gl,
-                                              Item& it, float* __restrict__ pslot, float dt, float& lmax)
+// bit u of the result = top bit of byte u (bytes of a __vcmpeq4-style mask:
+// 0x00 or 0xff), for the four bytes of a word
+__device__ __forceinline__ uint32_t byte_mask_bits(uint32_t m)
 {
-    it.kind = kItemGroup;
-    it.base = i0;
-    it.need = 0u;
-    it.anyEI = false;
-    it.clear = false;
-    it.nv = min(kPushG, a.n_thr - i0);
-    uint2 xs = gl.xs;
-    if (it.nv < kPushG) {
-#pragma unroll
-        for (int u = 0; u < kPushG; ++u)
-            if (u >= it.nv)
-                set_byte(xs, u, kR);
-    }
-    it.xs = xs;
-    it.nc = make_uint2(0u, 0u);
-#pragma unroll
-    for (int u = 0; u < kPushG; ++u)
-        it.age[u] = 0.0f;
-    // compartments are 0..3, so a byte is R (3) in both words' AND only if
-    // it is 3 in both; S bytes are the zero bytes
-    if ((xs.x & xs.y) == 0x03030303u)
-        return;
-    const bool anyS = (__vcmpeq4(xs.x, 0u) | __vcmpeq4(xs.y, 0u)) != 0u;
-    const uint32_t ei_x = __vcmpeq4(xs.x, 0x01010101u) | __vcmpeq4(xs.x, 0x02020202u);
-    const uint32_t ei_y = __vcmpeq4(xs.y, 0x01010101u) | __vcmpeq4(xs.y, 0x02020202u);
-    it.anyEI = (ei_x | ei_y) != 0u;
-    uint2 c8 = gl.c8;
-    uint4 pd = gl.pd;
-    if (anyS && !gl.have_cp) {
-        c8 = *reinterpret_cast<const uint2*>(a.cnt8 + i0);
-        pd = *reinterpret_cast<const uint4*>(a.pd16[par ^ 1u] + i0);
-    }
-    if (!anyS)
-        pd = make_uint4(0u, 0u, 0u, 0u);    // tallies of non-S nodes are never folded
-    const AgeT* __restrict__ A = static_cast<const AgeT*>(a.A) + i0;
-    if (it.anyEI) {
-        if (it.nv == kPushG) {
-            AgeVec8<AgeT>::load(A, it.age);
-        } else {
-#pragma unroll
-            for (int u = 0; u < kPushG; ++u)
-                if (u < it.nv)
-                    it.age[u] = AgeIO<AgeT>::load(A[u]);
-        }
-    }
-    it.clear = (pd.x | pd.y | pd.z | pd.w) != 0u;
-    const uint32_t pdw[4] = {pd.x, pd.y, pd.z, pd.w};
-    // counts (thread-class counts are <= 255, inside the S table) and the
-    // table lookups, resolved after every load of this phase has been issued
-    uint2 nc = c8;
-    float p[kPushG];
-    if constexpr (ADAPTIVE) {
-        // rates evaluated directly (ages leave the fixed-step sequence); the
-        // largest one sets the next step's size
-#pragma unroll
-        for (int u = 0; u < kPushG; ++u) {
-            const int x = (int)byte_of(xs, u);
-            const bool isS = x == kS, isEI = x == kE || x == kI;
-            const uint32_t d = (pdw[u >> 1] >> ((u & 1) << 4)) & 0xffffu;
-            const uint32_t c = isS ? byte_of(c8, u) + (d & 0xffu) - (d >> 8) : 0u;
-            if (isS)
-                set_byte(nc, u, c);
-            float lam = 0.0f;
-            if (isS && c != 0u)
-                lam = __fmul_rn(a.M.beta, (float)c);
-            else if (isEI)
-                lam = rate_ei(a.M, x, it.age[u]);
-            lmax = fmaxf(lmax, lam);
-            p[u] = p_of_rate_dt(lam, dt);
-        }
-        it.nc = nc;
-#pragma unroll
-        for (int u = 0; u < kPushG; ++u) {
-            if (p[u] > 0.0f) {
-                it.need |= 1u << u;
-                pslot[u] = p[u];
-            }
-        }
-        return;
-    }
-#pragma unroll
-    for (int u = 0; u < kPushG; ++u) {
-        const int x = (int)byte_of(xs, u);
-        const bool isS = x == kS, isEI = x == kE || x == kI;
-        const uint32_t d = (pdw[u >> 1] >> ((u & 1) << 4)) & 0xffffu;
-        const uint32_t c = isS ? byte_of(c8, u) + (d & 0xffu) - (d >> 8) : 0u;
-        if (isS)
-            set_byte(nc, u, c);
-        const int n = __float2int_rn(__fmul_rn(it.age[u], a.M.inv_dt));
-        float2 e = make_float2(-1.0f, 0.0f);                  // no entry: never equals an age
-        if (isEI && (unsigned)n < (unsigned)kPTableN)
-            e = __ldg(reinterpret_cast<const float2*>(a.ptab + (x == kI ? kPTableN : 0) + n));
-        float ps = 0.0f;
-        if (isS && c != 0u)
-            ps = __ldg(a.ps + c);
-        // -1: slot 0 holds another age (slot 1 or direct evaluation below)
-        p[u] = isS ? ps : (isEI ? (e.x == it.age[u] ? e.y : -1.0f) : 0.0f);
-    }
-    it.nc = nc;
-#pragma unroll
-    for (int u = 0; u < kPushG; ++u) {
-        if (p[u] < 0.0f)                                      // slot 1, else off the tabulated sequence
-            p[u] = p_table_miss(a, (int)byte_of(xs, u), it.age[u]);
-        if (p[u] > 0.0f) {
-            it.need |= 1u << u;
-            pslot[u] = p[u];
-        }
-    }
+    return ((m & 0x01010101u) * 0x01020408u) >> 24;
 }
 
-// one merge-class node: its count and pending tallies are folded in here
-template <typename AgeT, bool ADAPTIVE>
-__device__ __forceinline__ void hub_prepare(const StepArgs& a, uint32_t par, int i, Item& it,
-                                            float* __restrict__ pslot, float dt, float& lmax)
+__device__ __forceinline__ uint32_t byte_mask_bits(uint2 m)
 {
-    it.kind = kItemHub;
-    it.base = i;
-    it.need = 0u;
-    it.anyEI = false;
-    it.clear = false;
-    it.nv = 1;
-    const int x = a.X[i];
-    it.xs = make_uint2((uint32_t)x, 0u);
-    it.age[0] = 0.0f;
-    if (x == kR)
-        return;
-    const int r = i - a.n_thr;
-    uint32_t c = 0u;
-    if (x == kS) {
-        unsigned long long* pr = a.pd64[par ^ 1u] + r;
-        const unsigned long long d = *pr;
-        c = a.hcnt[r];
-        if (d) {
-            c = c + (uint32_t)(d & 0xffffffffull) - (uint32_t)(d >> 32);
-            a.hcnt[r] = c;
-            *pr = 0ull;
-        }
-    }
-    if (x == kE || x == kI)
-        it.age[0] = AgeIO<AgeT>::load(static_cast<const AgeT*>(a.A)[i]);
-    float p;
+    return byte_mask_bits(m.x) | (byte_mask_bits(m.y) << 4);
+}
+
+__device__ __forceinline__ uint2 vcmpeq(uint2 v, uint32_t b)
+{
+    return make_uint2(__vcmpeq4(v.x, b), __vcmpeq4(v.y, b));
+}
+
+__device__ __forceinline__ uint2 operator|(uint2 p, uint2 q) { return make_uint2(p.x | q.x, p.y | q.y); }
+__device__ __forceinline__ uint2 operator&(uint2 p, uint2 q) { return make_uint2(p.x & q.x, p.y & q.y); }
+__device__ __forceinline__ uint2 operator~(uint2 p) { return make_uint2(~p.x, ~p.y); }
+
+// Bernoulli probability (and, with ADAPTIVE, the rate into lmax) of a queued
+// node: state x, count c (S), age (E/I)
+template <bool ADAPTIVE>
+__device__ __forceinline__ float queued_p(const StepArgs& a, int x, uint32_t c, float age, float dt, float& lmax)
+{
     if constexpr (ADAPTIVE) {
-        const float lam = (x == kS) ? (c ? __fmul_rn(a.M.beta, (float)c) : 0.0f) : rate_ei(a.M, x, it.age[0]);
+        const float lam = x == kS ? __fmul_rn(a.M.beta, (float)c) : rate_ei(a.M, x, age);
         lmax = fmaxf(lmax, lam);
-        p = p_of_rate_dt(lam, dt);
+        return p_of_rate_dt(lam, dt);
     } else {
-        p = node_p_push(a, x, it.age[0], c);
-    }
-    if (p > 0.0f) {
-        it.need = 1u;
-        pslot[0] = p;
+        if (x == kS)
+            return c < (uint32_t)kPSTableN ? __ldg(a.ps + c) : p_of_rate(a.M, __fmul_rn(a.M.beta, (float)c));
+        const int n = __float2int_rn(__fmul_rn(age, a.M.inv_dt));
+        float2 e = make_float2(-1.0f, 0.0f);                  // no entry: never equals an age
+        if ((unsigned)n < (unsigned)kPTableN)
+            e = __ldg(reinterpret_cast<const float2*>(a.ptab + (x == kI ? kPTableN : 0) + n));
+        return e.x == age ? e.y : p_table_miss(a, x, age);    // slot 1, else direct evaluation
     }
 }
 
-// Bernoulli decisions of a whole warp: every lane queues (original id, slot)
-// of its nodes that draw, then the lanes share the queue evenly, so a warp
-// runs ceil(draws / 32) rounds of Philox instead of one round per node
-// position in which any lane draws. Every lane of the warp must call this.
-// Returns the lane's fired mask (bit u = node base + u fired).
-__device__ __forceinline__ uint32_t warp_draws(const StepArgs& a, uint32_t step, const Item& it, WarpScratch& w)
+// +1 / -1 into the pending tally of node j (parity par)
+__device__ __forceinline__ void push_pending(const StepArgs& a, uint32_t par, uint32_t j, bool minus)
+{
+    if (j < (uint32_t)a.n_thr) {
+        unsigned int* w = reinterpret_cast<unsigned int*>(a.pd16[par]) + (j >> 1);
+        atomicAdd(w, (minus ? 0x100u : 0x1u) << ((j & 1u) << 4));
+    } else if (j < (uint32_t)a.n) {
+        atomicAdd(a.pd64[par] + (j - (uint32_t)a.n_thr), minus ? (1ull << 32) : 1ull);
+    } else {
+        (void)FS_IN_BOUNDS(a.ctl, kSitePushTarget, j, a.n);
+    }
+}
+
+// +1 straight into the count of node j (initial counts)
+__device__ __forceinline__ void push_count(const StepArgs& a, uint32_t j)
+{
+    if (j < (uint32_t)a.n_thr)
+        atomicAdd(reinterpret_cast<unsigned int*>(a.cnt8) + (j >> 2), 1u << ((j & 3u) << 3));
+    else if (j < (uint32_t)a.n)
+        atomicAdd(a.hcnt + (j - (uint32_t)a.n_thr), 1u);
+    else
+        (void)FS_IN_BOUNDS(a.ctl, kSitePushTarget, j, a.n);
+}
+
+template <bool INIT>
+__device__ __forceinline__ void push_one(const StepArgs& a, uint32_t par, uint32_t j, bool minus)
+{
+    if constexpr (INIT)
+        push_count(a, j);
+    else
+        push_pending(a, par, j, minus);
+}
+
+template <bool INIT>
+__device__ __forceinline__ void warp_push(const StepArgs& a, uint32_t par, uint32_t ev, uint32_t neg, int base,
+                                          uint32_t* __restrict__ list);
+
+// One round of the warp (every lane calls this; item t of this lane, t >=
+// total for none; gl = the group's early loads). Returns nothing: states,
+// ages, counts and tallies are stored, pushes are made, deltas accumulated.
+template <typename AgeT, bool ADAPTIVE>
+__device__ __forceinline__ void warp_round(const StepArgs& a, uint32_t par, uint32_t step, int64_t t,
+                                           const GroupLoads& gl, int64_t n_grp, int64_t total, float dt,
+                                           float& lmax, PushDeltas& ld, WarpScratch& w)
 {
     const int lane = threadIdx.x & 31;
-    const uint32_t cnt = (uint32_t)__popc(it.need);
+    const int slot0 = lane * kPushG;
+    int kind = t < n_grp ? kItemGroup : (t < total ? kItemHub : kItemNone);
+    if (kind == kItemHub && !FS_IN_BOUNDS(a.ctl, kSiteGroup, a.n_thr + (t - n_grp), a.n))
+        kind = kItemNone;
+    uint2 xs = make_uint2(0x03030303u, 0x03030303u);   // R for empty slots
+    uint2 sM = make_uint2(0u, 0u), eM = sM, iM = sM;    // 0xff per S / E / I byte
+    uint32_t need = 0u;                                 // bit u: slot0 + u draws
+    bool clear = false;
+    uint2 nc = make_uint2(0u, 0u);
+    int base = 0;
+    uint32_t hcount = ~0u;
+    const AgeT* __restrict__ Ain = static_cast<const AgeT*>(a.A);
+    if (kind == kItemGroup) {
+        base = (int)(t * kPushG);
+        xs = group_states(a, base, gl.xs);
+        sM = vcmpeq(xs, 0u);
+        eM = vcmpeq(xs, 0x01010101u);
+        iM = vcmpeq(xs, 0x02020202u);
+        const bool anyS = (sM.x | sM.y) != 0u;
+        if (anyS) {
+            uint2 c8 = gl.c8;
+            uint4 pd = gl.pd;
+            if (!gl.have_cp) {
+                c8 = *reinterpret_cast<const uint2*>(a.cnt8 + base);
+                pd = *reinterpret_cast<const uint4*>(a.pd16[par ^ 1u] + base);
+            }
+            // fold the pending tallies (field u: +1 tally in its low byte, -1
+            // tally in its high byte) into the counts, eight at once; an S
+            // node's count is in [0, 255], so the byte-wise wrap is exact
+            const uint32_t plus0 = __byte_perm(pd.x, pd.y, 0x6420u), minus0 = __byte_perm(pd.x, pd.y, 0x7531u);
+            const uint32_t plus1 = __byte_perm(pd.z, pd.w, 0x6420u), minus1 = __byte_perm(pd.z, pd.w, 0x7531u);
+            const uint2 f = make_uint2(__vsub4(__vadd4(c8.x, plus0), minus0), __vsub4(__vadd4(c8.y, plus1), minus1));
+            nc = (f & sM) | (c8 & ~sM);               // counts of non-S nodes are left as they were
+            clear = (pd.x | pd.y | pd.z | pd.w) != 0u;
+            need = byte_mask_bits(sM & ~vcmpeq(nc, 0u));
+        }
+        const uint2 eiM = eM | iM;
+        if ((eiM.x | eiM.y) != 0u) {
+            need |= byte_mask_bits(eiM);
+            float ag[kPushG];
+            if (base + kPushG <= a.n_thr) {
+                AgeVec8<AgeT>::load(Ain + base, ag);
+            } else {
+#pragma unroll
+                for (int u = 0; u < kPushG; ++u)
+                    ag[u] = base + u < a.n_thr ? AgeIO<AgeT>::load(Ain[base + u]) : 0.0f;
+            }
+            *reinterpret_cast<float4*>(w.age + slot0) = make_float4(ag[0], ag[1], ag[2], ag[3]);
+            *reinterpret_cast<float4*>(w.age + slot0 + 4) = make_float4(ag[4], ag[5], ag[6], ag[7]);
+        }
+    } else if (kind == kItemHub) {
+        base = a.n_thr + (int)(t - n_grp);
+        const int x = a.X[base];
+        xs.x = 0x03030300u | (uint32_t)x;
+        const int r = base - a.n_thr;
+        if (x == kS) {
+            unsigned long long* pr = a.pd64[par ^ 1u] + r;
+            const unsigned long long d = *pr;
+            uint32_t c = a.hcnt[r];
+            if (d) {
+                c = c + (uint32_t)(d & 0xffffffffull) - (uint32_t)(d >> 32);
+                a.hcnt[r] = c;
+                *pr = 0ull;
+            }
+            hcount = c;
+            need = c != 0u ? 1u : 0u;
+        } else if (x == kE || x == kI) {
+            w.age[slot0] = AgeIO<AgeT>::load(Ain[base]);
+            need = 1u;
+        }
+    }
+    *reinterpret_cast<uint2*>(w.xb + slot0) = xs;
+    *reinterpret_cast<uint2*>(w.cb + slot0) = nc;
+    *reinterpret_cast<uint2*>(w.fb + slot0) = make_uint2(0u, 0u);
+    w.base[lane] = base;
+    w.hc[lane] = hcount;
+    // the queue: slots that draw, lane by lane
+    const uint32_t cnt = (uint32_t)__popc(need);
     uint32_t incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -473,129 +407,121 @@ __device__ __forceinline__ uint32_t warp_draws(const StepArgs& a, uint32_t step,
         if (lane >= o)
             incl += y;
     }
-    const uint32_t total = __shfl_sync(kFull, incl, 31);
-    if (total == 0u)
-        return 0u;
+    const int total_q = (int)__shfl_sync(kFull, incl, 31);
     {
         int j = (int)(incl - cnt);
-        uint32_t m = it.need;
+        uint32_t m = need;
         while (m) {
             const int u = __ffs(m) - 1;
             m &= m - 1u;
-            const int node = it.base + u;
-            w.qnode[j] = a.perm ? (uint32_t)__ldg(a.perm + node) : (uint32_t)node;
-            w.qslot[j] = (uint16_t)(lane * kPushG + u);
-            ++j;
+            w.q[j++] = (uint8_t)(slot0 + u);
         }
     }
     __syncwarp();
-    for (int e = lane; e < (int)total; e += 32) {
-        const int sl = w.qslot[e];
-        const float u = uniform24(a.M.key0, a.M.key1, a.M.rep, step, w.qnode[e]);
-        w.fired[sl] = u < w.p[sl] ? 1 : 0;
+    // the draws: two queued nodes per lane per pass (independent chains of
+    // table loads and Philox rounds)
+    for (int e0 = lane; e0 < total_q; e0 += 64) {
+        const int e1 = e0 + 32;
+        const bool has1 = e1 < total_q;
+        const int s0 = w.q[e0], s1 = has1 ? (int)w.q[e1] : s0;
+        const int x0 = w.xb[s0], x1 = w.xb[s1];
+        const uint32_t h0 = w.hc[s0 >> 3], h1 = w.hc[s1 >> 3];
+        const uint32_t c0 = h0 != ~0u ? h0 : (uint32_t)w.cb[s0], c1 = h1 != ~0u ? h1 : (uint32_t)w.cb[s1];
+        const int n0 = w.base[s0 >> 3] + (s0 & (kPushG - 1)), n1 = w.base[s1 >> 3] + (s1 & (kPushG - 1));
+        const uint32_t o0 = a.perm ? (uint32_t)__ldg(a.perm + n0) : (uint32_t)n0;
+        const uint32_t o1 = a.perm ? (uint32_t)__ldg(a.perm + n1) : (uint32_t)n1;
+        const float p0 = queued_p<ADAPTIVE>(a, x0, c0, w.age[s0], dt, lmax);
+        const float p1 = queued_p<ADAPTIVE>(a, x1, c1, w.age[s1], dt, lmax);
+        const float u0 = uniform24(a.M.key0, a.M.key1, a.M.rep, step, o0);
+        const float u1 = uniform24(a.M.key0, a.M.key1, a.M.rep, step, o1);
+        w.fb[s0] = u0 < p0 ? 0xffu : 0u;
+        if (has1)
+            w.fb[s1] = u1 < p1 ? 0xffu : 0u;
     }
     __syncwarp();
-    uint32_t fired = 0u;
-    uint32_t m = it.need;
-    while (m) {
-        const int u = __ffs(m) - 1;
-        m &= m - 1u;
-        fired |= (uint32_t)w.fired[lane * kPushG + u] << u;
-    }
-    __syncwarp();     // the queue is reused by the warp's next item
-    return fired;
-}
-
-// transitions, renewal ages, in-place stores, push events and deltas
-template <typename AgeT>
-__device__ __forceinline__ void item_apply(const StepArgs& a, uint32_t par, Item& it, uint32_t fired,
-                                           uint32_t& ev, uint32_t& neg, PushDeltas& ld, float dt)
-{
-    if (it.kind == kItemNone)
-        return;
-    const int i0 = it.base;
-    AgeT* __restrict__ A = static_cast<AgeT*>(a.A) + i0;
-    if (it.kind == kItemHub) {
-        const int x = (int)it.xs.x;
-        if (x == kR)
-            return;
-        const bool f = fired & 1u;
-        const int y = next_state(a, x, f);
-        if (y != x)
-            a.X[i0] = (uint8_t)y;
-        if (f || x == kE || x == kI)
-            A[0] = AgeIO<AgeT>::store(f ? 0.0f : __fadd_rn(it.age[0], dt));
-        if ((y == kI) != (x == kI)) {
-            ev = 1u;
-            neg = x == kI ? 1u : 0u;
-        }
-        if (f) {
-            ld.fS += x == kS;
-            ld.fE += x == kE;
-            ld.fI += x == kI;
-            if (x == kS)
-                ld.dS += (uint32_t)__ldg(a.deg + i0);
-        }
-        return;
-    }
-    const uint2 xs = it.xs;
-    if ((xs.x & xs.y) == 0x03030303u)
-        return;
-    uint2 nx = xs;
-    uint32_t firedS = 0u;
+    // transitions, renewal ages, in-place stores, push events and deltas
+    uint32_t ev = 0u, neg = 0u;
+    if (kind == kItemGroup) {
+        const uint2 F = *reinterpret_cast<const uint2*>(w.fb + slot0);
+        if ((F.x | F.y) != 0u) {
+            // SEIR: every firing node moves to the next compartment (+1);
+            // SIR: S -> I is +2, I -> R is +1
+            uint2 inc = F & make_uint2(0x01010101u, 0x01010101u);
+            if (a.M.model != kSEIR)
+                inc = make_uint2(inc.x + (F.x & sM.x & 0x01010101u), inc.y + (F.y & sM.y & 0x01010101u));
+            const uint2 nx = make_uint2(xs.x + inc.x, xs.y + inc.y);     // no byte carries: R never fires
+            const uint2 enterI = F & (a.M.model == kSEIR ? eM : sM);
+            ev = byte_mask_bits(enterI | (F & iM));
+            neg = byte_mask_bits(F & iM);
+            ld.fS += (uint32_t)(__popc((F & sM).x) + __popc((F & sM).y)) >> 3;
+            ld.fE += (uint32_t)(__popc((F & eM).x) + __popc((F & eM).y)) >> 3;
+            ld.fI += (uint32_t)(__popc((F & iM).x) + __popc((F & iM).y)) >> 3;
+            uint32_t fs_bits = byte_mask_bits(F & sM);
+            while (fs_bits) {
+                const int u = __ffs(fs_bits) - 1;
+                fs_bits &= fs_bits - 1u;
+                ld.dS += (uint32_t)__ldg(a.deg + base + u);
+            }
+            if (base + kPushG <= a.n_thr) {
+                *reinterpret_cast<uint2*>(a.X + base) = nx;
+            } else {
 #pragma unroll
-    for (int u = 0; u < kPushG; ++u) {
-        const int x = (int)byte_of(xs, u);
-        if (x == kR)
-            continue;
-        const bool f = (fired >> u) & 1u;
-        const int y = next_state(a, x, f);
-        it.age[u] = f ? 0.0f : ((x == kE || x == kI) ? __fadd_rn(it.age[u], dt) : 0.0f);
-        if (y != x)
-            set_byte(nx, u, (uint32_t)y);
-        if ((y == kI) != (x == kI)) {
-            ev |= 1u << u;
-            if (x == kI)
-                neg |= 1u << u;
+                for (int u = 0; u < kPushG; ++u)
+                    if (base + u < a.n_thr && byte_of(nx, u) != byte_of(xs, u))
+                        a.X[base + u] = (uint8_t)byte_of(nx, u);
+            }
         }
-        if (f) {
-            ld.fS += x == kS;
-            ld.fE += x == kE;
-            ld.fI += x == kI;
-            if (x == kS)
-                firedS |= 1u << u;
+        const uint2 eiM = eM | iM;
+        if ((eiM.x | eiM.y) != 0u) {
+            // renewal ages: 0 on firing, E/I ages advance by dt (FP32 add,
+            // rounded to storage on the store); S/R ages stay 0
+            const uint32_t fb = byte_mask_bits(F), eb = byte_mask_bits(eiM);
+            float ag[kPushG];
+#pragma unroll
+            for (int u = 0; u < kPushG; ++u) {
+                const float g = w.age[slot0 + u];
+                ag[u] = ((fb >> u) & 1u) ? 0.0f : (((eb >> u) & 1u) ? __fadd_rn(g, dt) : 0.0f);
+            }
+            AgeT* __restrict__ Aout = static_cast<AgeT*>(a.A) + base;
+            if (base + kPushG <= a.n_thr) {
+                AgeVec8<AgeT>::store(Aout, ag);
+            } else {
+#pragma unroll
+                for (int u = 0; u < kPushG; ++u)
+                    if (base + u < a.n_thr)
+                        Aout[u] = AgeIO<AgeT>::store(ag[u]);
+            }
         }
-    }
-    if (firedS) {
-#pragma unroll
-        for (int u = 0; u < kPushG; ++u)
-            if ((firedS >> u) & 1u)
-                ld.dS += (uint32_t)__ldg(a.deg + i0 + u);
-    }
-    if (it.nv == kPushG) {
-        if (nx.x != xs.x || nx.y != xs.y)
-            *reinterpret_cast<uint2*>(a.X + i0) = nx;
-        if (it.anyEI)
-            AgeVec8<AgeT>::store(A, it.age);
-    } else {
-#pragma unroll
-        for (int u = 0; u < kPushG; ++u) {
-            if (u < it.nv) {
-                const uint32_t y = byte_of(nx, u);
-                if (y != byte_of(xs, u))
-                    a.X[i0 + u] = (uint8_t)y;
-                if (it.anyEI)
-                    A[u] = AgeIO<AgeT>::store(it.age[u]);
+        // the pending tallies just folded in are cleared for the pushes of
+        // the next step; counts and tallies of the thread class are padded
+        // to whole groups, so these stores never touch another class
+        if (clear) {
+            *reinterpret_cast<uint2*>(a.cnt8 + base) = nc;
+            *reinterpret_cast<uint4*>(a.pd16[par ^ 1u] + base) = make_uint4(0u, 0u, 0u, 0u);
+        }
+    } else if (kind == kItemHub) {
+        const int x = (int)(xs.x & 0xffu);
+        if (x != kR) {
+            const bool f = w.fb[slot0] != 0u;
+            const int y = next_state(a, x, f);
+            if (y != x)
+                a.X[base] = (uint8_t)y;
+            if (f || x == kE || x == kI)
+                static_cast<AgeT*>(a.A)[base] = AgeIO<AgeT>::store(f ? 0.0f : __fadd_rn(w.age[slot0], dt));
+            if ((y == kI) != (x == kI)) {
+                ev = 1u;
+                neg = x == kI ? 1u : 0u;
+            }
+            if (f) {
+                ld.fS += x == kS;
+                ld.fE += x == kE;
+                ld.fI += x == kI;
+                if (x == kS)
+                    ld.dS += (uint32_t)__ldg(a.deg + base);
             }
         }
     }
-    // the pending tallies just folded in are cleared for the pushes of the
-    // next step; counts and tallies of the thread class are padded to whole
-    // groups, so these stores never touch another class
-    if (it.clear) {
-        *reinterpret_cast<uint2*>(a.cnt8 + i0) = it.nc;
-        *reinterpret_cast<uint4*>(a.pd16[par ^ 1u] + i0) = make_uint4(0u, 0u, 0u, 0u);
-    }
+    warp_push<false>(a, par, ev, neg, base, w.ev);
 }
 
 // ---------------------------------------------------------------------------
@@ -642,8 +568,10 @@ __device__ __forceinline__ void warp_push(const StepArgs& a, uint32_t par, uint3
         if (e < nev) {
             evw = list[e];
             const int node = (int)(evw & 0x7fffffffu);
-            lo = __ldg(a.out_ptr + node);
-            len = __ldg(a.out_ptr + node + 1) - lo;
+            if (FS_IN_BOUNDS(a.ctl, kSiteOutPtr, node, a.n)) {
+                lo = __ldg(a.out_ptr + node);
+                len = __ldg(a.out_ptr + node + 1) - lo;
+            }
         }
         // long rows (hubs) one at a time, the warp striding over each with
         // its column loads issued four ahead; they leave the flattened batch
@@ -655,6 +583,7 @@ __device__ __forceinline__ void warp_push(const StepArgs& a, uint32_t par, uint3
             const bool minus = (__shfl_sync(kFull, evw, l) >> 31) != 0u;
             const int32_t* __restrict__ col = a.out_col + lo_l;
             int64_t q = lane;
+#ifndef FS_DEBUG_BOUNDS
             for (; q + 96 < len_l; q += 128) {
                 const uint32_t j0 = (uint32_t)__ldg(col + q), j1 = (uint32_t)__ldg(col + q + 32);
                 const uint32_t j2 = (uint32_t)__ldg(col + q + 64), j3 = (uint32_t)__ldg(col + q + 96);
@@ -663,8 +592,10 @@ __device__ __forceinline__ void warp_push(const StepArgs& a, uint32_t par, uint3
                 push_one<INIT>(a, par, j2, minus);
                 push_one<INIT>(a, par, j3, minus);
             }
+#endif
             for (; q < len_l; q += 32)
-                push_one<INIT>(a, par, (uint32_t)__ldg(col + q), minus);
+                if (FS_IN_BOUNDS(a.ctl, kSiteOutCol, lo_l + q, a.out_nnz - a.dbg_shrink))
+                    push_one<INIT>(a, par, (uint32_t)__ldg(col + q), minus);
         }
         if (len > kPushLongRow)
             len = 0;
@@ -691,7 +622,7 @@ __device__ __forceinline__ void warp_push(const StepArgs& a, uint32_t par, uint3
             const int64_t lo_l = __shfl_sync(kFull, lo, l);
             const int64_t off_l = __shfl_sync(kFull, off, l);
             const uint32_t ev_l = __shfl_sync(kFull, evw, l);
-            if (q < tot) {
+            if (q < tot && FS_IN_BOUNDS(a.ctl, kSiteOutCol, lo_l + (q - off_l), a.out_nnz - a.dbg_shrink)) {
                 const uint32_t j = (uint32_t)__ldg(a.out_col + lo_l + (q - off_l));
                 push_one<INIT>(a, par, j, (ev_l >> 31) != 0u);
             }
@@ -709,7 +640,7 @@ constexpr int kScanRounds = 3;      // grid-stride rounds whose loads a warp iss
 // allocation.
 template <typename AgeT, bool SCAN, bool ADAPTIVE, bool LIST>
 __device__ __forceinline__ void push_items(const StepArgs& a, uint32_t par, int64_t k, bool spec_s, float dt,
-                                           float& lmax, PushDeltas& ld, WarpScratch& w, float* pslot,
+                                           float& lmax, PushDeltas& ld, WarpScratch& w,
                                            const int32_t* __restrict__ act, int64_t n_items)
 {
     const int tid = threadIdx.x, lane = tid & 31;
@@ -723,33 +654,20 @@ __device__ __forceinline__ void push_items(const StepArgs& a, uint32_t par, int6
         else
             return q < n_items ? (int64_t)__ldg(act + q) : (int64_t)INT32_MAX;
     };
+    // One item per lane (the grid covers every item at once): no scan.
+    if constexpr (!SCAN) {
+        const int64_t t = item_at((int64_t)blockIdx.x * kPushThreads + tid);
+        GroupLoads cur = group_loads(a, par, t, n_grp, spec_s);
+        const bool idle = (t < n_grp || t >= total) && group_idle(a, par, t, n_grp, cur);
+        if (!__all_sync(kFull, idle))
+            warp_round<AgeT, ADAPTIVE>(a, par, (uint32_t)k, t, cur, n_grp, total, dt, lmax, ld, w);
+    }
     // Warps take kScanRounds grid-stride rounds at a time: the loads that tell
     // whether an item has work (states; counts and tallies while S is common)
     // are issued for all of them together, and only the rounds in which some
     // lane of the warp has work are processed, so a mostly idle sweep (the
     // all-S start, the mostly-R tail) waits for memory once per kScanRounds
     // rounds instead of once per round.
-    // One item per lane (the grid covers every item at once): no scan.
-    if constexpr (!SCAN) {
-        const int64_t t = item_at((int64_t)blockIdx.x * kPushThreads + tid);
-        GroupLoads cur = group_loads(a, par, t, n_grp, spec_s);
-        const bool idle = (t < n_grp || t >= total) && group_idle(a, par, t, n_grp, cur);
-        if (!__all_sync(kFull, idle)) {
-            Item it;
-            it.kind = kItemNone;
-            it.base = 0;
-            it.need = 0u;
-            if (t < n_grp)
-                group_prepare<AgeT, ADAPTIVE>(a, par, (int)(t * kPushG), cur, it, pslot, dt, lmax);
-            else if (t < total)
-                hub_prepare<AgeT, ADAPTIVE>(a, par, a.n_thr + (int)(t - n_grp), it, pslot, dt, lmax);
-            __syncwarp();
-            const uint32_t fired = warp_draws(a, (uint32_t)k, it, w);
-            uint32_t ev = 0u, neg = 0u;
-            item_apply<AgeT>(a, par, it, fired, ev, neg, ld, dt);
-            warp_push<false>(a, par, ev, neg, it.base, w.ev);
-        }
-    }
     for (int64_t tb = (int64_t)blockIdx.x * kPushThreads + (tid & ~31); SCAN && tb < n_items;
          tb += (int64_t)kScanRounds * stride) {
         uint32_t busy = 0u;
@@ -772,19 +690,7 @@ __device__ __forceinline__ void push_items(const StepArgs& a, uint32_t par, int6
             const int64_t t = item_at(tb + u * stride + lane);
             // reloaded: these lines were read by the scan just above
             const GroupLoads cur = group_loads(a, par, t, n_grp, spec_s);
-            Item it;
-            it.kind = kItemNone;
-            it.base = 0;
-            it.need = 0u;
-            if (t < n_grp)
-                group_prepare<AgeT, ADAPTIVE>(a, par, (int)(t * kPushG), cur, it, pslot, dt, lmax);
-            else if (t < total)
-                hub_prepare<AgeT, ADAPTIVE>(a, par, a.n_thr + (int)(t - n_grp), it, pslot, dt, lmax);
-            __syncwarp();
-            const uint32_t fired = warp_draws(a, (uint32_t)k, it, w);
-            uint32_t ev = 0u, neg = 0u;
-            item_apply<AgeT>(a, par, it, fired, ev, neg, ld, dt);
-            warp_push<false>(a, par, ev, neg, it.base, w.ev);
+            warp_round<AgeT, ADAPTIVE>(a, par, (uint32_t)k, t, cur, n_grp, total, dt, lmax, ld, w);
         }
     }
 }
@@ -799,11 +705,11 @@ struct PushSweepOut {
 
 template <typename AgeT, bool SCAN, bool ADAPTIVE>
 __device__ __noinline__ PushSweepOut push_items_listed(const StepArgs& a, uint32_t par, int64_t k, bool spec_s,
-                                                        float dt, WarpScratch* w, float* pslot, int64_t n_items)
+                                                        float dt, WarpScratch* w, int64_t n_items)
 {
     PushSweepOut o;
     o.lmax = 0.0f;
-    push_items<AgeT, SCAN, ADAPTIVE, true>(a, par, k, spec_s, dt, o.lmax, o.ld, *w, pslot, a.act, n_items);
+    push_items<AgeT, SCAN, ADAPTIVE, true>(a, par, k, spec_s, dt, o.lmax, o.ld, *w, a.act, n_items);
     return o;
 }
 
@@ -818,7 +724,6 @@ __global__ void __launch_bounds__(kPushThreads, kPushCtasPerSm) push_step_kernel
     __shared__ WarpScratch scratch[kPushThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31;
     WarpScratch& w = scratch[tid >> 5];
-    float* pslot = w.p + lane * kPushG;
     const int64_t k = a.ctl->step + a.j;
     const uint32_t par = (uint32_t)(k & 1);
     // the step's size: fixed, or (Section 5.2) min(dt_max, eps / (lambda* of
@@ -845,18 +750,18 @@ __global__ void __launch_bounds__(kPushThreads, kPushCtasPerSm) push_step_kernel
     const int64_t na = a.act ? (int64_t)a.ctl->n_act : total;
     if constexpr (SCAN) {
         if (na < total) {
-            const PushSweepOut o = push_items_listed<AgeT, SCAN, ADAPTIVE>(a, par, k, spec_s, dt, &w, pslot, na);
+            const PushSweepOut o = push_items_listed<AgeT, SCAN, ADAPTIVE>(a, par, k, spec_s, dt, &w, na);
             ld = o.ld;
             lmax = o.lmax;
         } else {
-            push_items<AgeT, SCAN, ADAPTIVE, false>(a, par, k, spec_s, dt, lmax, ld, w, pslot, nullptr, total);
+            push_items<AgeT, SCAN, ADAPTIVE, false>(a, par, k, spec_s, dt, lmax, ld, w, nullptr, total);
         }
     } else {
         // one round: both sweeps inline
         if (na < total)
-            push_items<AgeT, SCAN, ADAPTIVE, true>(a, par, k, spec_s, dt, lmax, ld, w, pslot, a.act, na);
+            push_items<AgeT, SCAN, ADAPTIVE, true>(a, par, k, spec_s, dt, lmax, ld, w, a.act, na);
         else
-            push_items<AgeT, SCAN, ADAPTIVE, false>(a, par, k, spec_s, dt, lmax, ld, w, pslot, nullptr, total);
+            push_items<AgeT, SCAN, ADAPTIVE, false>(a, par, k, spec_s, dt, lmax, ld, w, nullptr, total);
     }
     if constexpr (ADAPTIVE) {
         // rates are >= 0, so their FP32 bits order as unsigned integers

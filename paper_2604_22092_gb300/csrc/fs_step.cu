@@ -204,20 +204,24 @@ __device__ __forceinline__ void sell_slice(const StepArgs& a, uint32_t step, con
             int32_t jj[B];
 #pragma unroll
             for (int u = 0; u < B; ++u)
-                jj[u] = (t0 + u < w) ? __ldg(p + 32 * (t0 + u)) : sentinel;
+                jj[u] = (t0 + u < w && FS_IN_BOUNDS(a.ctl, kSiteSellCol, off + lane + 32 * (int64_t)(t0 + u), a.sell_len))
+                            ? __ldg(p + 32 * (t0 + u))
+                            : sentinel;
             if constexpr (SMEM_BM) {
                 // the shared copy of the bitmap is awaited only now, after
                 // this lane's first column loads are in flight
                 if (!*ready) {
-                    if (!mbar_wait(mbar, 0u, kWaitLimit))
+                    if (!mbar_wait(mbar, 0u, a.wait_limit ? a.wait_limit : kWaitLimit))
                         record_error(a.ctl, kErrTmaTimeout);
                     *ready = true;
                 }
             }
 #pragma unroll
             for (int u = 0; u < B; ++u) {
-                uint32_t word;
-                if constexpr (SMEM_BM)
+                uint32_t word = 0u;
+                if (!FS_IN_BOUNDS(a.ctl, kSiteBitmap, jj[u] >> 5, a.bm_words))
+                    ;
+                else if constexpr (SMEM_BM)
                     word = bm[jj[u] >> 5];
                 else
                     word = __ldg(bm + (jj[u] >> 5));
@@ -403,17 +407,21 @@ __device__ __forceinline__ void merge_chunk(const StepArgs& a, uint32_t step, co
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes)
                          : "memory");
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                    smem_addr(sm.col)),
-                "l"(a.m_col + e0), "r"(bytes), "r"(mbar)
-                : "memory");
+            // (a failure-detection test sets skip_bulk_copy: the barrier then
+            // waits for bytes that never come, with no copy in flight)
+            if (!a.skip_bulk_copy)
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        smem_addr(sm.col)),
+                    "l"(a.m_col + e0), "r"(bytes), "r"(mbar)
+                    : "memory");
         }
         __syncthreads();
-        bool ok = mbar_wait(mbar, 0u, kWaitLimit);
+        const uint32_t lim = a.wait_limit ? a.wait_limit : kWaitLimit;
+        bool ok = mbar_wait(mbar, 0u, lim);
         if (!ok) {
             record_error(a.ctl, kErrTmaTimeout);
-            ok = mbar_wait(mbar, 0u, kWaitLimit);   // let an in-flight copy land before leaving
+            ok = mbar_wait(mbar, 0u, lim);          // let an in-flight copy land before leaving
         }
         const int64_t s0 = e0 + (int64_t)warp * kMergeEdgesPerWarp;
         if constexpr (SHED) {
@@ -744,7 +752,7 @@ __global__ void __launch_bounds__(kSmemThreads, 1) sell_smem_kernel(const __grid
     if constexpr ((MODE & kModeAdaptive) != 0)
         adaptive_lmax(a, k, ld.lmax);
     // the copy into this CTA's shared memory must have landed before it exits
-    if (!ready && !mbar_wait(mb, 0u, kWaitLimit))
+    if (!ready && !mbar_wait(mb, 0u, a.wait_limit ? a.wait_limit : kWaitLimit))
         record_error(a.ctl, kErrTmaTimeout);
     warp_add_deltas(a.deltas, a.j, ld.fS, ld.fE, ld.fI, ld.dS);
 }

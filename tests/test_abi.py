@@ -91,3 +91,29 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(cls), cname
         for fname, _ in cls._fields_:
             assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
+
+
+def test_bounds_checked_library_exports_the_same_boundary():
+    from paper_2604_22092_gb300 import _build_lib
+    _build_lib.build()
+    raw = ctypes.CDLL(_build_lib.LIB_BOUNDS)
+    for name in declared_entry_points():
+        assert hasattr(raw, name), name
+    e = ctypes.c_int32()
+    assert raw.fs_debug_bounds_build(ctypes.byref(e)) == 0 and e.value == 1
+
+
+def test_test_hooks_validate_their_arguments():
+    """The failure-detection settings: host-side checks only (no GPU work)."""
+    assert not fs.fs_debug_bounds_build()
+    with pytest.raises(fs.FsError) as e:
+        fs.fs_test_inject(fs.FS_TEST_BOUNDS_SHRINK, 3)     # normal build: no bounds checks
+    assert e.value.status == 7
+    with pytest.raises(fs.FsError) as e:
+        fs.fs_test_inject(fs.FS_TEST_WAIT_TIMEOUT, -1)
+    assert e.value.status == 1
+    with pytest.raises(fs.FsError) as e:
+        fs.fs_test_inject(99, 0)
+    assert e.value.status == 1
+    fs.fs_test_inject(fs.FS_TEST_WAIT_TIMEOUT, 64)
+    fs.fs_test_inject(fs.FS_TEST_WAIT_TIMEOUT, 0)

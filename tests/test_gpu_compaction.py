@@ -9,7 +9,9 @@ where half the nodes are R, so the list is in use (fs_sim_active_units shows
 fewer units visited than without it); cases cover both pressure forms, the
 shared-memory and the global-bitmap gather kernels, the push kernel's
 one-item-per-lane and block-scan instances, graph replays and directly
-launched remainders, a shedding profile and the adaptive step.
+launched remainders, a shedding profile and the adaptive step. With the list
+in use, single steps are also checked against the oracle itself (lock-step:
+each step from the GPU's own state), in both pressure forms.
 """
 import math
 
@@ -18,6 +20,7 @@ import pytest
 
 import paper_2604_22092_gb300 as fs
 import workloads as W
+from tests.gpu_helpers import lockstep
 
 pytestmark = pytest.mark.gpu
 
@@ -140,4 +143,26 @@ def test_compaction_argument_errors(torch_cuda):
     with pytest.raises(fs.FsError) as e:
         fs.fs_ens_create(gh, [seir(fs.FS_PRESSURE_AUTO | fs.FS_ACTIVE_LIST, seed=k) for k in range(3)], [1])
     assert e.value.status == 7
+    fs.fs_graph_destroy(gh)
+
+
+@pytest.mark.parametrize("pressure", [fs.FS_PRESSURE_GATHER, fs.FS_PRESSURE_PUSH], ids=["gather", "push"])
+def test_listed_steps_lockstep_with_oracle(torch_cuda, oracle_mod, pressure):
+    """Past the point where half the nodes are R (step ~260 here; the oracle's
+    own run has R = 39,931 of 50,003 at step 300), every single step opens a
+    launch sequence whose refresh lists the live units, and the listed sweep's
+    next state equals the oracle's step from the same state."""
+    g = W.barabasi_albert(50_003, 4, seed=7)
+    idx = W.index_nodes(g.n, 50, seed=2, allowed=W.non_hub_nodes(g))
+    p = seir(pressure | fs.FS_ACTIVE_LIST)
+    gh = fs.fs_graph_create(g.n, g.row_ptr, g.col_ind)
+    s = fs.fs_sim_init(gh, p, idx)
+    c = fs.fs_sim_run(s, 280, graph_steps=50)
+    assert c[-1, 3] * 2 > g.n
+    l0, u = fs.fs_sim_active_units(s)
+    rep = lockstep(oracle_mod, g, p, s, 40)
+    l1, _ = fs.fs_sim_active_units(s)
+    assert rep.decisions > 100_000
+    assert l1 - l0 < 40 * u, "the refreshes of the 40 single steps must list fewer than all units"
+    fs.fs_sim_destroy(s)
     fs.fs_graph_destroy(gh)

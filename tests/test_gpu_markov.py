@@ -79,8 +79,11 @@ def test_markov_lockstep(torch_cuda, oracle_mod, model):
     fs.fs_sim_run(s, 300, graph_steps=50, want_counts=False)
     taus2, dec2 = markov_lockstep(oracle_mod, g, p, s, 40)
     assert dec + dec2 > 100_000
-    if model != fs.FS_SEIR:      # (SEIR: few events while the index nodes are latent)
-        assert taus.min() < p.dt                      # the theta or p_max term binds
+    # the theta or p_max term of Algorithm 1 binds (SEIR: only once the index
+    # nodes' latent phase is over, so in the second window, steps 360-400,
+    # where the oracle's own run takes tau down to 1/15)
+    binding = taus2 if model == fs.FS_SEIR else taus
+    assert binding.min() < p.dt
     X, _, _ = fs.fs_sim_get_state(s, g.n)
     if model == fs.FS_SIS:
         assert not (X == fs.FS_R).any() and (X == fs.FS_I).sum() > 1000

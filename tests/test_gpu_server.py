@@ -2,7 +2,8 @@
 join the running batch, and every request's counts equal its realisations
 run alone through fs_sim_*. Also: a short request submitted after a long one
 finishes first (their work overlaps on the device), admission by the device
-memory budget queues what does not fit and rejects what never can.
+memory budget queues what does not fit and rejects what never can, and
+served realisations on each graph family equal the oracle's own runs.
 """
 import math
 import time
@@ -12,6 +13,7 @@ import pytest
 
 import paper_2604_22092_gb300 as fs
 import workloads as W
+from tests.gpu_helpers import TIE, oracle_params
 
 pytestmark = pytest.mark.gpu
 
@@ -152,4 +154,62 @@ def test_inflight_cap_admits_in_order(graphs):
     np.testing.assert_array_equal(c0[:, 9, :], alone_counts(hs[2], sc[1], idx, 40, 1))
     with pytest.raises(fs.FsError):
         fs.fs_server_create(max_inflight=-2)
+    fs.fs_server_destroy(srv)
+
+
+def oracle_counts(om, g, p, idx, steps):
+    """The oracle's free run of one realisation: per-step counts (row k = the
+    state after k steps), and per step the smallest |u - p| over its Bernoulli
+    decisions."""
+    prm = oracle_params(om, p)
+    X, A = om.init(g.n, idx, p.index_state)
+    out = [om.counts(X)]
+    closest = np.full(steps, np.inf)
+    for k in range(steps):
+        X, A, margin, _ = om.step(g.row_ptr, g.col_ind, prm, k, X, A, want_margin=True)
+        m = np.abs(margin[np.isfinite(margin)])
+        if m.size:
+            closest[k] = float(m.min())
+        out.append(om.counts(X))
+    return np.array(out, dtype=np.uint32), closest
+
+
+def test_served_realisations_equal_the_oracle(graphs, oracle_mod):
+    """Every realisation of a request served in a mix of three requests (one
+    per graph family: random regular, Barabasi-Albert, Erdos-Renyi; two
+    scenarios x two replicates each) equals the oracle's free run of the same
+    (seed, replicate) step by step. The FP32 decision may differ from the
+    oracle's FP64 one only at a near tie (|u - p| < 1e-6), after which the two
+    trajectories legitimately part: so a realisation that differs must first
+    differ right after a step in which the oracle had such a decision, and
+    most realisations must match over the whole run."""
+    gs, hs = graphs
+    srv = fs.fs_server_create(quantum=6)
+    steps, reps = 150, 2
+    reqs = []
+    for gi in range(3):
+        idx = W.index_nodes(gs[gi].n, 30, seed=90 + gi)
+        sc = scen(2, seed=95 + gi)
+        reqs.append((fs.fs_server_submit(srv, hs[gi], sc, reps, idx, steps), gi, sc, idx))
+    fs.fs_server_drain(srv, 120)
+    full = parted = 0
+    for rid, gi, sc, idx in reqs:
+        done, c, _ = fs.fs_server_poll(srv, rid, steps, len(sc) * reps)
+        assert done
+        for si, p in enumerate(sc):
+            for r in range(reps):
+                q = fs.sim_params(p.model, p.infectious, p.beta, p.dt, p.seed, latent=p.latent,
+                                  replicate=p.replicate + r, age_dtype=p.age_dtype)
+                ref, closest = oracle_counts(oracle_mod, gs[gi], q, idx, steps)
+                assert ref[-1, 3] > 0, "the realisation must have an epidemic"
+                rows = np.flatnonzero((c[:, si * reps + r, :] != ref).any(axis=1))
+                if rows.size == 0:
+                    full += 1
+                    continue
+                k = int(rows[0])
+                assert k >= 1 and closest[k - 1] < TIE, (
+                    f"graph {gi} scenario {si} replicate {r}: counts first differ at row {k} "
+                    f"({c[k, si * reps + r].tolist()} vs {ref[k].tolist()}) without a near tie in step {k - 1}")
+                parted += 1
+    assert full >= 10 and parted <= 2, (full, parted)
     fs.fs_server_destroy(srv)
