@@ -55,7 +55,7 @@ KERNEL_SOURCES = {
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["flashstep", "reference"], default="flashstep")
     ap.add_argument("--n", type=int, default=1_000_000, help="nodes (the headline workload uses 10^6)")
@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-served", action="store_true", help="skip the served-vs-plain block")
+    ap.add_argument("--no-large", action="store_true", help="skip the N=1e8 block")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the 64-graph packed-ensemble block")
     ap.add_argument("--workload", choices=["regular", "ensemble", "serving", "large", "precision", "shedding",
                                            "compaction", "markov"],
                     default="regular",
@@ -147,7 +149,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, FileNotFoundError):
             self.proc = None
             return
@@ -365,11 +367,40 @@ def plain_seconds(fs, gh, p, idx, steps):
     return time.perf_counter() - t0
 
 
-def ensemble_bench(fs, torch, n_graphs, n_lo, n_hi, steps, age_dtype, reps=3, pressure=0):
+def _gen_mixed(job):
+    """One graph of the mixed family, written to .npy files (a spawned worker)."""
+    q, n_lo, n_hi, seed, path = job
+    g = W.mixed_graph(q, n_lo, n_hi, seed=seed)
+    np.save(os.path.join(path, f"rp{q}.npy"), g.row_ptr)
+    np.save(os.path.join(path, f"ci{q}.npy"), g.col_ind)
+    return q, g.n, g.name
+
+
+def mixed_graphs(n_graphs: int, n_lo: float, n_hi: float, seed: int):
+    """The mixed graph family (workloads.mixed_graph), generated on every host
+    core at once by spawned workers (the same graphs as a serial loop)."""
+    import multiprocessing as mp
+    import shutil
+    import tempfile
+    tmp = tempfile.mkdtemp(prefix="fs_mixed_")
+    try:
+        with mp.get_context("spawn").Pool(max(1, min(host_cores(), n_graphs))) as pool:
+            done = pool.map(_gen_mixed, [(q, n_lo, n_hi, seed, tmp) for q in range(n_graphs)], chunksize=1)
+        graphs = []
+        for q, n, name in sorted(done):
+            graphs.append(W.Graph(n, np.load(os.path.join(tmp, f"rp{q}.npy")),
+                                  np.load(os.path.join(tmp, f"ci{q}.npy")), name))
+        return graphs
+    finally:
+        shutil.rmtree(tmp, ignore_errors=True)
+
+
+def ensemble_bench(fs, torch, n_graphs, n_lo, n_hi, steps, age_dtype, reps=3, pressure=0, graphs=None):
     """Packed batch of 8 scenarios x n_graphs mixed graphs in one launch per
-    step, against each realisation run alone (a sample: scenario 0 of every
-    graph, whose cost stands for the other scenarios of that graph)."""
-    graphs = [W.mixed_graph(q, n_lo, n_hi, seed=2026) for q in range(n_graphs)]
+    step, against every one of those realisations run alone through the plain
+    one-run-per-launch engine (fs_sim_run, CUDA Graph step loop), back to back."""
+    if graphs is None:
+        graphs = mixed_graphs(n_graphs, n_lo, n_hi, seed=2026)
     ghs = [fs.fs_graph_create(g.n, g.row_ptr, g.col_ind) for g in graphs]
     idxs = [index_for(g, seed=q + 1) for q, g in enumerate(graphs)]
     scen = [W.scenarios(8, seed=1000 + q) for q in range(n_graphs)]
@@ -394,19 +425,26 @@ def ensemble_bench(fs, torch, n_graphs, n_lo, n_hi, steps, age_dtype, reps=3, pr
             fs.fs_ens_destroy(e)
     served_s = float(np.median(times))
     updates = sum(g.n for g in graphs) * 8 * steps
-    for warm in (True, False):   # the first pass captures each sim's graph and warms caches
-        plain = [plain_seconds(fs, ghs[q], scen_params(fs, scen[q][0], 0, age_dtype), idxs[q], steps)
-                 for q in range(n_graphs)]
-    plain_s = 8 * float(np.sum(plain))
+    # the plain engine: every realisation alone, one after the other (a first
+    # pass over scenario 0 of each graph warms the step code and the caches)
+    for q in range(n_graphs):
+        plain_seconds(fs, ghs[q], scen_params(fs, scen[q][0], 0, age_dtype), idxs[q], steps)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for q in range(n_graphs):
+        for s_, sc in enumerate(scen[q]):
+            plain_seconds(fs, ghs[q], scen_params(fs, sc, s_, age_dtype), idxs[q], steps)
+    plain_s = time.perf_counter() - t0
     for gh in ghs:
         fs.fs_graph_destroy(gh)
     return {"workload": f"packed-{n_graphs}graphs-x8scen-n{n_lo:.0e}-{n_hi:.0e}-{steps}steps".replace("+0", ""),
             "realisations": 8 * n_graphs, "nodes_total": int(sum(g.n for g in graphs)),
             "age_storage": "f16" if age_dtype == fs.FS_AGE_F16 else "f32",
             "served_gnups": round(updates / served_s / 1e9, 3), "served_seconds": round(served_s, 4),
-            "plain_gnups": round(updates / plain_s / 1e9, 3), "plain_seconds_estimated": round(plain_s, 3),
+            "plain_gnups": round(updates / plain_s / 1e9, 3), "plain_seconds": round(plain_s, 3),
             "speedup": round(plain_s / served_s, 2),
-            "plain_sample": "scenario 0 of every graph run alone through fs_sim_run, x8 for the other scenarios"}
+            "plain_engine": "every realisation run alone through fs_sim_run (init + CUDA Graph step loop + "
+                            "counts read back), back to back, host wall clock"}
 
 
 def serving_bench(fs, torch, n_requests, n_pool, n_hi, steps, rep_lo, rep_hi, window_s, age_dtype):
@@ -532,16 +570,18 @@ def run_flashstep(args, rank, world, local_rank):
                 "note": "at N=1e6 the step's working set is L2-resident across steps, so the step is "
                         "latency-bound; the HBM-bound N=1e7/1e8 points are bench.py --workload large"}
 
+    # the clock sampler starts before the warm-up, so that its own start-up
+    # (nvidia-smi loading NVML) does not fall into the timed steps
+    clocks = ClockSampler(local_rank) if rank == 0 else None
+    if clocks:
+        clocks.start()
     for _ in range(args.warmup):
         flush.fill_(1.0)
         one_step(prm)
     torch.cuda.synchronize()
-    clocks = ClockSampler(local_rank) if rank == 0 else None
     times, kern_ms, bytes_alg = [], [], []
     pressure_used = None
     launches0 = fs.fs_kernel_launches()
-    if clocks:
-        clocks.start()
     for _ in range(args.steps):
         flush.fill_(1.0)
         torch.cuda.synchronize()
@@ -602,6 +642,30 @@ def run_flashstep(args, rank, world, local_rank):
         out["e2e"] = e2e(fs, torch, g, idx, prm, args, stream)
     if rank == 0 and not args.no_secondary:
         out["secondary"] = secondary_ba(fs, torch, args, stream, flush)
+    # the HBM-bound points: N = 10^8, FP32 and BF16 ages, whole job (rank 0)
+    if rank == 0 and not args.no_large:
+        out["large"] = []
+        for a in (fs.FS_AGE_F32, fs.FS_AGE_BF16):
+            cs = ClockSampler(local_rank)
+            cs.start()
+            r = large_bench(fs, torch, 100_000_000, a, args.sim_steps, args.graph_steps, reps=1,
+                            pressure=PRESSURE[args.pressure])
+            r.pop("phases_step_us_gbs_sfrac", None)
+            r["clocks"] = cs.stop()
+            out["large"].append(r)
+    # the 64-graph x 8-scenario packed ensemble against every realisation run
+    # alone, FP32 and FP16 ages (rank 0)
+    if rank == 0 and not args.no_ensemble:
+        graphs = mixed_graphs(args.ens_graphs, 1e4, 2e6, seed=2026)
+        out["ensemble"] = []
+        for a in (fs.FS_AGE_F32, fs.FS_AGE_F16):
+            cs = ClockSampler(local_rank)
+            cs.start()
+            r = ensemble_bench(fs, torch, n_graphs=args.ens_graphs, n_lo=1e4, n_hi=2e6, steps=args.ens_steps,
+                               age_dtype=a, graphs=graphs)
+            r["clocks"] = cs.stop()
+            out["ensemble"].append(r)
+        del graphs
     if rank == 0 and not args.no_served:
         out["served"] = serving_bench(fs, torch, n_requests=24, n_pool=8, n_hi=2e5, steps=200, rep_lo=16,
                                       rep_hi=64, window_s=0.25, age_dtype=fs.FS_AGE_F32)

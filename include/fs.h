@@ -464,6 +464,34 @@ fs_status fs_server_stats_get(fs_server* s, fs_server_stats* out);
 fs_status fs_server_destroy(fs_server* s);
 
 /* ---------------------------------------------------------------------------
+ * Device memory. Graphs, simulations, ensembles, batches and their scratch
+ * take device memory from the library's allocator. By default it keeps the
+ * blocks that are freed (after a device-wide synchronisation, so no launched
+ * work still uses them) and hands them out again for the same size, so that
+ * objects created and destroyed in a loop do not pay for cudaMalloc and
+ * cudaFree each time; when the device runs out of memory the cache is
+ * released and the allocation retried. (The paper's engine allocates through
+ * PyTorch; this boundary has no PyTorch types.)
+ *   fs_set_allocator      routes every later allocation to alloc(bytes, ctx)
+ *                         (it must return device memory of the current device,
+ *                         aligned to at least 256 bytes, or NULL when out of
+ *                         memory) and its release to free_fn(ptr, ctx), called
+ *                         after a device-wide synchronisation; the library
+ *                         then caches nothing. NULL, NULL restores the
+ *                         library's own allocator. A block is always released
+ *                         through the functions that allocated it. Both
+ *                         functions or neither, else FS_EINVAL.
+ *   fs_release_cached_memory  frees the cached blocks of the current device.
+ *   fs_cached_memory      bytes cached and blocks in use on the current device
+ *                         (the library's own allocator only).
+ * ------------------------------------------------------------------------- */
+typedef void* (*fs_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*fs_free_fn)(void* ptr, void* ctx);
+fs_status fs_set_allocator(fs_alloc_fn alloc, fs_free_fn free_fn, void* ctx);
+fs_status fs_release_cached_memory(void);
+fs_status fs_cached_memory(uint64_t* cached_bytes, uint64_t* live_blocks);
+
+/* ---------------------------------------------------------------------------
  * Failure-detection test hooks. The paper has no counterpart: these let the
  * tests make the library's own bounded device waits and bounds checks fire
  * without faulting the GPU. They affect only simulations created while the

@@ -32,7 +32,8 @@ __all__ = [
     "fs_eval_uniforms", "fs_step_noalloc", "fs_ens_create", "fs_ens_run", "fs_ens_get_state",
     "fs_ens_destroy", "fs_batch_create", "fs_batch_add", "fs_batch_run", "fs_batch_status", "fs_batch_destroy",
     "fs_server_create", "fs_server_submit", "fs_server_poll", "fs_server_drain", "fs_server_stats_get",
-    "fs_server_destroy", "fs_test_inject", "fs_debug_bounds_build",
+    "fs_server_destroy", "fs_test_inject", "fs_debug_bounds_build", "fs_set_allocator",
+    "fs_release_cached_memory", "fs_cached_memory",
     "law", "sim_params", "graph_opts", "FsError", "load",
     "FS_S", "FS_E", "FS_I", "FS_R", "FS_SIR", "FS_SEIR", "FS_SIS", "FS_AGE_F32", "FS_AGE_F16", "FS_AGE_BF16",
     "FS_DISPATCH_AUTO", "FS_DISPATCH_THREAD", "FS_DISPATCH_MERGE", "FS_DISPATCH_TUNE",
@@ -285,6 +286,35 @@ def fs_step_noalloc(g: int, params: _abi.fs_sim_params, step: int, state_dev, ag
     check(load().fs_step_noalloc(g, ctypes.byref(params), int(step), _addr(state_dev), _addr(age_dev),
                                  _addr(bitmap_cur_dev), _addr(bitmap_next_dev), _addr(deltas_dev),
                                  _stream(stream)), "fs_step_noalloc")
+
+
+_ALLOCATOR = None    # the C function pointers of the installed allocator, kept alive
+
+
+def fs_set_allocator(alloc=None, free=None) -> None:
+    """Route the library's device allocations to alloc(bytes) -> address (0
+    when out of memory) and free(address); None, None restores the library's
+    own caching allocator."""
+    global _ALLOCATOR
+    if (alloc is None) != (free is None):
+        raise ValueError("give both functions or neither")
+    if alloc is None:
+        fa, ff = _abi.ALLOC_FN(), _abi.FREE_FN()
+    else:
+        fa = _abi.ALLOC_FN(lambda nbytes, ctx: int(alloc(int(nbytes)) or 0))
+        ff = _abi.FREE_FN(lambda ptr, ctx: free(int(ptr)))
+    check(load().fs_set_allocator(fa, ff, None), "fs_set_allocator")
+    _ALLOCATOR = (fa, ff) if alloc is not None else None
+
+
+def fs_release_cached_memory() -> None:
+    check(load().fs_release_cached_memory(), "fs_release_cached_memory")
+
+
+def fs_cached_memory() -> dict:
+    c, b = ctypes.c_uint64(), ctypes.c_uint64()
+    check(load().fs_cached_memory(ctypes.byref(c), ctypes.byref(b)), "fs_cached_memory")
+    return {"cached_bytes": c.value, "live_blocks": b.value}
 
 
 def fs_test_inject(what: int, value: int) -> None:

@@ -69,6 +69,9 @@ class fs_server_stats(ctypes.Structure):
 
 VP = ctypes.c_void_p
 P = ctypes.POINTER
+# fs_alloc_fn / fs_free_fn
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
 # name -> (restype, argtypes); the exported C ABI
 PROTOTYPES = {
@@ -78,6 +81,9 @@ PROTOTYPES = {
     "fs_graph_info_get": (ctypes.c_int, [VP, P(fs_graph_info)]),
     "fs_graph_destroy": (ctypes.c_int, [VP]),
     "fs_test_inject": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64]),
+    "fs_set_allocator": (ctypes.c_int, [ALLOC_FN, FREE_FN, VP]),
+    "fs_release_cached_memory": (ctypes.c_int, []),
+    "fs_cached_memory": (ctypes.c_int, [P(ctypes.c_uint64), P(ctypes.c_uint64)]),
     "fs_debug_bounds_build": (ctypes.c_int, [P(ctypes.c_int32)]),
     "fs_sim_init": (ctypes.c_int, [VP, P(fs_sim_params), VP, ctypes.c_int64, VP, P(VP)]),
     "fs_sim_step": (ctypes.c_int, [VP, VP]),

@@ -20,7 +20,7 @@ LIB_BOUNDS = os.path.join(OUT_DIR, "libflashstep_bounds.so")
 LIB = LIB_BOUNDS if os.environ.get("FLASHSTEP_DEBUG_BOUNDS") == "1" else LIB_NORMAL
 
 SOURCES = ["fs_api.cu", "fs_step.cu", "fs_push.cu", "fs_markov.cu", "fs_ingest.cu", "fs_pack.cu", "fs_pack_api.cu", "fs_server.cpp",
-           "fs_tune.cpp"]
+           "fs_tune.cpp", "fs_alloc.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
               "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

@@ -61,16 +61,16 @@ void free_graph(fs_graph* g)
 {
     if (!g)
         return;
-    cudaFree(g->d_perm);
-    cudaFree(g->d_inv);
-    cudaFree(g->d_deg);
-    cudaFree(g->d_sell_off);
-    cudaFree(g->d_sell_col);
-    cudaFree(g->d_m_ptr);
-    cudaFree(g->d_m_col);
-    cudaFree(g->d_m_warp_row);
-    cudaFree(g->d_m_chunk_last);
-    cudaFree(g->d_out_ptr);          // the columns share its allocation
+    fs::dfree(g->d_perm);
+    fs::dfree(g->d_inv);
+    fs::dfree(g->d_deg);
+    fs::dfree(g->d_sell_off);
+    fs::dfree(g->d_sell_col);
+    fs::dfree(g->d_m_ptr);
+    fs::dfree(g->d_m_col);
+    fs::dfree(g->d_m_warp_row);
+    fs::dfree(g->d_m_chunk_last);
+    fs::dfree(g->d_out_ptr);          // the columns share its allocation
     delete g;
 }
 
@@ -80,8 +80,8 @@ void free_sim(fs_sim* s)
         return;
     if (s->gexec)
         cudaGraphExecDestroy(s->gexec);
-    cudaFree(s->d_arena);          // every per-sim buffer but the counts output
-    cudaFree(s->d_counts);
+    fs::dfree(s->d_arena);          // every per-sim buffer but the counts output
+    fs::dfree(s->d_counts);
     if (s->own_stream && s->stream)
         cudaStreamDestroy(s->stream);
     delete s;
@@ -311,7 +311,7 @@ cudaError_t ensure_out_csr(fs_graph* g, cudaStream_t st)
     // row bounds and columns in one allocation (freed through d_out_ptr)
     const size_t ptr_bytes = ((sizeof(int64_t) * ((size_t)n + 1)) + 255) & ~(size_t)255;
     const int64_t bytes = (int64_t)(ptr_bytes + sizeof(int32_t) * std::max<int64_t>(g->nnz, 1));
-    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&optr), (size_t)bytes);
+    cudaError_t e = fs::dmalloc(reinterpret_cast<void**>(&optr), (size_t)bytes);
     if (e == cudaSuccess) {
         ocol = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(optr) + ptr_bytes);
         e = scratch_alloc(&cur, (size_t)n + 1, st);
@@ -332,7 +332,7 @@ cudaError_t ensure_out_csr(fs_graph* g, cudaStream_t st)
         e = cudaStreamSynchronize(st);
     scratch_free(cur, st);
     if (e != cudaSuccess) {
-        cudaFree(optr);
+        fs::dfree(optr);
         return e;
     }
     g->d_out_ptr = optr;
@@ -449,7 +449,7 @@ fs_status fs_graph_create(int64_t n, const int64_t* row_ptr, const int32_t* col_
                 e = cudaMemcpyAsync(&hf, d_fl, sizeof(hf), cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess)
                 e = cudaStreamSynchronize(st);
-            cudaFree(d_fl);
+            fs::dfree(d_fl);
             if (e != cudaSuccess)
                 return fail(FS_ECUDA, "degree profile: %s", cudaGetErrorString(e));
             if (hf.error)
@@ -474,8 +474,8 @@ fs_status fs_graph_create(int64_t n, const int64_t* row_ptr, const int32_t* col_
     fs::IngestFlags fl{};
     auto cleanup = [&]() {
         if (!dev_in) {
-            cudaFree(d_rp);
-            cudaFree(d_col);
+            fs::dfree(d_rp);
+            fs::dfree(d_col);
         }
         scratch_free(d_key, st);
         scratch_free(d_flags, st);
@@ -551,7 +551,7 @@ fs_status fs_graph_create(int64_t n, const int64_t* row_ptr, const int32_t* col_
             G_CUDA(dev_alloc(&deg_int, (size_t)n, nullptr));
             G_CUDA(fs::stable_sort_by_key(d_key, g->d_deg, ni, g->t1 + 2, g->d_perm, g->d_inv, deg_int, st));
             G_CUDA(cudaStreamSynchronize(st));
-            cudaFree(g->d_deg);
+            fs::dfree(g->d_deg);
             g->d_deg = deg_int;
         }
         // SELL-32 blocks of the thread class; slices per warp so that the
@@ -756,7 +756,7 @@ fs_status fs_sim_init(fs_graph* g, const fs_sim_params* params, const int32_t* i
         oH0 = carve(sizeof(unsigned long long) * nm1);
         oH1 = carve(sizeof(unsigned long long) * nm1);
     }
-    S_CUDA(cudaMalloc(&s->d_arena, arena));
+    S_CUDA(fs::dmalloc(&s->d_arena, arena));
     char* base = static_cast<char*>(s->d_arena);
     s->d_X = reinterpret_cast<uint8_t*>(base + oX);
     s->d_A = base + oA;
@@ -1005,10 +1005,10 @@ fs_status fs_sim_run(fs_sim* s, int64_t steps, int32_t graph_steps, uint32_t* co
     if (counts_out) {
         const int64_t need = (steps + 1) * 4;
         if (need > s->counts_cap) {
-            cudaFree(s->d_counts);
+            fs::dfree(s->d_counts);
             s->d_counts = nullptr;
             s->counts_cap = 0;
-            FS_CUDA(s, cudaMalloc(&s->d_counts, sizeof(uint32_t) * need));
+            FS_CUDA(s, fs::dmalloc(&s->d_counts, sizeof(uint32_t) * need));
             s->counts_cap = need;
         }
         dc = s->d_counts;
@@ -1049,7 +1049,7 @@ fs_status fs_sim_get_state(fs_sim* s, uint8_t* state, void* age, int64_t* step)
         return FS_OK;
     void* tmp = nullptr;
     if (!g->identity)
-        FS_CUDA(s, cudaMalloc(&tmp, (size_t)n * 4));
+        FS_CUDA(s, fs::dmalloc(&tmp, (size_t)n * 4));
     fs_status rc = FS_OK;
     auto copy_out = [&](const void* dsrc, void* hdst, int eb) -> cudaError_t {
         if (g->identity)
@@ -1070,7 +1070,7 @@ fs_status fs_sim_get_state(fs_sim* s, uint8_t* state, void* age, int64_t* step)
         s->failed = true;
         rc = fail(FS_ECUDA, "get_state: %s", cudaGetErrorString(e));
     }
-    cudaFree(tmp);
+    fs::dfree(tmp);
     return rc;
 }
 
@@ -1112,7 +1112,7 @@ fs_status fs_sim_set_state(fs_sim* s, const uint8_t* state, const void* age, int
     FS_CUDA(s, cudaStreamSynchronize(s->stream));
     void* tmp = nullptr;
     if (!g->identity)
-        FS_CUDA(s, cudaMalloc(&tmp, (size_t)n * 4));
+        FS_CUDA(s, fs::dmalloc(&tmp, (size_t)n * 4));
     cudaError_t e = cudaSuccess;
     auto copy_in = [&](const void* hsrc, void* ddst, int eb) -> cudaError_t {
         if (g->identity)
@@ -1127,7 +1127,7 @@ fs_status fs_sim_set_state(fs_sim* s, const uint8_t* state, const void* age, int
     e = copy_in(state, s->d_X, 1);
     if (e == cudaSuccess)
         e = copy_in(age, s->d_A, s->age_bytes);
-    cudaFree(tmp);
+    fs::dfree(tmp);
     if (e != cudaSuccess) {
         s->failed = true;
         return fail(FS_ECUDA, "set_state: %s", cudaGetErrorString(e));
@@ -1205,14 +1205,14 @@ fs_status fs_sim_infectivity_get(fs_sim* s, void* rho)
         e = cudaMemcpy(rho, src, (size_t)n * eb, cudaMemcpyDeviceToHost);
     } else {
         void* tmp = nullptr;
-        e = cudaMalloc(&tmp, (size_t)std::max<int64_t>(n, 1) * eb);
+        e = fs::dmalloc(&tmp, (size_t)std::max<int64_t>(n, 1) * eb);
         if (e == cudaSuccess)
             e = fs::launch_to_original(src, tmp, eb, g->d_perm, (int)n, s->stream);
         if (e == cudaSuccess)
             e = cudaStreamSynchronize(s->stream);
         if (e == cudaSuccess)
             e = cudaMemcpy(rho, tmp, (size_t)n * eb, cudaMemcpyDeviceToHost);
-        cudaFree(tmp);
+        fs::dfree(tmp);
     }
     if (e != cudaSuccess) {
         s->failed = true;

@@ -10,6 +10,19 @@
 #include "fs.h"
 #include "fs_internal.h"
 
+namespace fs {
+// device memory of the library (fs_alloc.cpp): freed blocks are cached by
+// size and handed out again, or every block comes from the caller's
+// allocator (fs_set_allocator)
+cudaError_t dmalloc_raw(void** p, size_t bytes);
+cudaError_t dfree(void* p);
+template <class T>
+inline cudaError_t dmalloc(T** p, size_t bytes)
+{
+    return dmalloc_raw(reinterpret_cast<void**>(p), bytes);
+}
+}  // namespace fs
+
 struct fs_graph {
     int64_t n = 0, nnz = 0;
     int32_t dmax = 0;
@@ -96,7 +109,7 @@ template <typename T>
 inline cudaError_t dev_alloc(T** p, size_t count, int64_t* bytes)
 {
     const size_t b = sizeof(T) * (count > 0 ? count : 1);
-    cudaError_t e = cudaMalloc((void**)p, b);
+    cudaError_t e = fs::dmalloc((void**)p, b);
     if (e == cudaSuccess && bytes)
         *bytes += (int64_t)b;
     return e;
@@ -105,11 +118,11 @@ inline cudaError_t dev_alloc(T** p, size_t count, int64_t* bytes)
 template <typename T>
 inline cudaError_t scratch_alloc(T** p, size_t count, cudaStream_t)
 {
-    return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (count > 0 ? count : 1));
+    return fs::dmalloc(reinterpret_cast<void**>(p), sizeof(T) * (count > 0 ? count : 1));
 }
 inline void scratch_free(void* p, cudaStream_t)
 {
-    cudaFree(p);
+    fs::dfree(p);
 }
 fs_status check_params(const fs_sim_params* p);
 fs::ModelF to_model(const fs_sim_params& p);

@@ -87,22 +87,22 @@ void free_ens(fs_ens* e)
 {
     if (!e)
         return;
-    cudaFree(e->d_X);
-    cudaFree(e->d_A);
-    cudaFree(e->d_mask[0]);
-    cudaFree(e->d_mask[1]);
-    cudaFree(e->d_pc8);
-    cudaFree(e->d_ppd[0]);
-    cudaFree(e->d_ppd[1]);
-    cudaFree(e->d_phc);
-    cudaFree(e->d_phpd[0]);
-    cudaFree(e->d_phpd[1]);
-    cudaFree(e->d_scen);
-    cudaFree(e->d_ptab);
-    cudaFree(e->d_ps);
-    cudaFree(e->d_deltas);
-    cudaFree(e->d_counts);
-    cudaFree(e->d_out);
+    fs::dfree(e->d_X);
+    fs::dfree(e->d_A);
+    fs::dfree(e->d_mask[0]);
+    fs::dfree(e->d_mask[1]);
+    fs::dfree(e->d_pc8);
+    fs::dfree(e->d_ppd[0]);
+    fs::dfree(e->d_ppd[1]);
+    fs::dfree(e->d_phc);
+    fs::dfree(e->d_phpd[0]);
+    fs::dfree(e->d_phpd[1]);
+    fs::dfree(e->d_scen);
+    fs::dfree(e->d_ptab);
+    fs::dfree(e->d_ps);
+    fs::dfree(e->d_deltas);
+    fs::dfree(e->d_counts);
+    fs::dfree(e->d_out);
     if (e->stream)
         cudaStreamDestroy(e->stream);
     delete e;
@@ -114,11 +114,11 @@ void free_batch(fs_batch* b)
         return;
     if (b->gexec)
         cudaGraphExecDestroy(b->gexec);
-    cudaFree(b->d_seg);
-    cudaFree(b->d_thr);
-    cudaFree(b->d_hub);
-    cudaFree(b->d_cls);
-    cudaFree(b->d_ctl);
+    fs::dfree(b->d_seg);
+    fs::dfree(b->d_thr);
+    fs::dfree(b->d_hub);
+    fs::dfree(b->d_cls);
+    fs::dfree(b->d_ctl);
     cudaFreeHost(b->h_seg);
     cudaFreeHost(b->h_thr);
     cudaFreeHost(b->h_hub);
@@ -243,7 +243,7 @@ fs_status fs_ens_create(fs_graph* g, const fs_sim_params* params, int32_t n_real
     const int Rp = e->R_pad;
     int32_t* d_idx = nullptr;
     auto bail = [&](fs_status st) {
-        cudaFree(d_idx);
+        fs::dfree(d_idx);
         free_ens(e);
         return st;
     };
@@ -257,10 +257,10 @@ fs_status fs_ens_create(fs_graph* g, const fs_sim_params* params, int32_t n_real
     C_TRY(cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking));
     cudaStream_t cs = e->stream;
     C_TRY(dev_alloc(&e->d_X, (size_t)n * Rp, &e->bytes));
-    C_TRY(cudaMalloc(&e->d_A, (size_t)n * Rp * e->age_bytes));
+    C_TRY(fs::dmalloc(&e->d_A, (size_t)n * Rp * e->age_bytes));
     e->bytes += (int64_t)n * Rp * e->age_bytes;
     for (int q = 0; q < 2; ++q) {
-        C_TRY(cudaMalloc(&e->d_mask[q], (size_t)(n + 1) * e->mask_bytes));
+        C_TRY(fs::dmalloc(&e->d_mask[q], (size_t)(n + 1) * e->mask_bytes));
         e->bytes += (int64_t)(n + 1) * e->mask_bytes;
         C_TRY(cudaMemsetAsync(e->d_mask[q], 0, (size_t)(n + 1) * e->mask_bytes, cs));
     }
@@ -325,7 +325,7 @@ fs_status fs_ens_create(fs_graph* g, const fs_sim_params* params, int32_t n_real
     C_TRY(cudaMemcpyAsync(e->d_counts, cnt.data(), sizeof(uint32_t) * Rp * 4, cudaMemcpyHostToDevice, cs));
     C_TRY(cudaStreamSynchronize(cs));
 #undef C_TRY
-    cudaFree(d_idx);
+    fs::dfree(d_idx);
     g->refs += 1;
     *out = e;
     return FS_OK;
@@ -449,7 +449,7 @@ fs_status fs_batch_add(fs_batch* b, fs_ens* e, int64_t steps, uint32_t* counts_o
         return fail(FS_ENOMEM, "fs_batch_add: the batch is full (%d members)", b->cap);
     if (counts_out) {
         const size_t bytes = sizeof(uint32_t) * (size_t)(steps + 1) * e->R_pad * 4;
-        E_CUDA(e, cudaMalloc(&e->d_out, bytes));
+        E_CUDA(e, fs::dmalloc(&e->d_out, bytes));
         E_CUDA(e, cudaStreamSynchronize(e->stream));
         E_CUDA(e, cudaMemcpyAsync(e->d_out, e->d_counts, sizeof(uint32_t) * e->R_pad * 4, cudaMemcpyDeviceToDevice,
                                   b->stream));
@@ -588,7 +588,7 @@ fs_status fs_batch_run(fs_batch* b, int64_t launches, int32_t graph_steps)
                     memcpy(m.host_out + row * e->R * 4, tmp.data() + row * e->R_pad * 4,
                            sizeof(uint32_t) * e->R * 4);
             }
-            cudaFree(e->d_out);
+            fs::dfree(e->d_out);
             e->d_out = nullptr;
             e->steps_done += m.steps;
             e->batch = nullptr;
@@ -622,7 +622,7 @@ fs_status fs_batch_destroy(fs_batch* b)
         return fail(FS_EINVAL, "fs_batch_destroy: NULL batch");
     cudaStreamSynchronize(b->stream);
     for (const Member& m : b->members) {
-        cudaFree(m.e->d_out);
+        fs::dfree(m.e->d_out);
         m.e->d_out = nullptr;
         m.e->batch = nullptr;
     }

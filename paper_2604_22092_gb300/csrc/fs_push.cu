@@ -146,6 +146,9 @@ __device__ __forceinline__ void set_byte(uint2& v, int u, uint32_t b)
 // pending tallies and the transitions work on eight nodes at once.
 // ---------------------------------------------------------------------------
 constexpr int kWarpSlots = 32 * kPushG;       // node slots of a round: lane * kPushG + u
+// queued nodes a lane draws for at once (2 measured faster than 3 or 4,
+// which need more registers than the 64 a thread has)
+constexpr int kDrawsPerPass = 2;
 
 struct WarpScratch {
     uint8_t xb[kWarpSlots];       // state of the node in each slot (R for empty slots)
@@ -418,25 +421,30 @@ __device__ __forceinline__ void warp_round(const StepArgs& a, uint32_t par, uint
         }
     }
     __syncwarp();
-    // the draws: two queued nodes per lane per pass (independent chains of
-    // table loads and Philox rounds)
-    for (int e0 = lane; e0 < total_q; e0 += 64) {
-        const int e1 = e0 + 32;
-        const bool has1 = e1 < total_q;
-        const int s0 = w.q[e0], s1 = has1 ? (int)w.q[e1] : s0;
-        const int x0 = w.xb[s0], x1 = w.xb[s1];
-        const uint32_t h0 = w.hc[s0 >> 3], h1 = w.hc[s1 >> 3];
-        const uint32_t c0 = h0 != ~0u ? h0 : (uint32_t)w.cb[s0], c1 = h1 != ~0u ? h1 : (uint32_t)w.cb[s1];
-        const int n0 = w.base[s0 >> 3] + (s0 & (kPushG - 1)), n1 = w.base[s1 >> 3] + (s1 & (kPushG - 1));
-        const uint32_t o0 = a.perm ? (uint32_t)__ldg(a.perm + n0) : (uint32_t)n0;
-        const uint32_t o1 = a.perm ? (uint32_t)__ldg(a.perm + n1) : (uint32_t)n1;
-        const float p0 = queued_p<ADAPTIVE>(a, x0, c0, w.age[s0], dt, lmax);
-        const float p1 = queued_p<ADAPTIVE>(a, x1, c1, w.age[s1], dt, lmax);
-        const float u0 = uniform24(a.M.key0, a.M.key1, a.M.rep, step, o0);
-        const float u1 = uniform24(a.M.key0, a.M.key1, a.M.rep, step, o1);
-        w.fb[s0] = u0 < p0 ? 0xffu : 0u;
-        if (has1)
-            w.fb[s1] = u1 < p1 ? 0xffu : 0u;
+    // the draws: kDrawsPerPass queued nodes per lane per pass (independent
+    // chains of table loads and Philox rounds; a pass's missing entries
+    // repeat its first one and store nothing)
+    for (int e0 = lane; e0 < total_q; e0 += 32 * kDrawsPerPass) {
+        int sl[kDrawsPerPass];
+        float pr[kDrawsPerPass], ur[kDrawsPerPass];
+        sl[0] = w.q[e0];
+#pragma unroll
+        for (int d = 1; d < kDrawsPerPass; ++d)
+            sl[d] = e0 + 32 * d < total_q ? (int)w.q[e0 + 32 * d] : sl[0];
+#pragma unroll
+        for (int d = 0; d < kDrawsPerPass; ++d) {
+            const int s_ = sl[d];
+            const uint32_t h = w.hc[s_ >> 3];
+            const uint32_t c = h != ~0u ? h : (uint32_t)w.cb[s_];
+            const int node = w.base[s_ >> 3] + (s_ & (kPushG - 1));
+            const uint32_t orig = a.perm ? (uint32_t)__ldg(a.perm + node) : (uint32_t)node;
+            pr[d] = queued_p<ADAPTIVE>(a, w.xb[s_], c, w.age[s_], dt, lmax);
+            ur[d] = uniform24(a.M.key0, a.M.key1, a.M.rep, step, orig);
+        }
+#pragma unroll
+        for (int d = 0; d < kDrawsPerPass; ++d)
+            if (d == 0 || e0 + 32 * d < total_q)
+                w.fb[sl[d]] = ur[d] < pr[d] ? 0xffu : 0u;
     }
     __syncwarp();
     // transitions, renewal ages, in-place stores, push events and deltas

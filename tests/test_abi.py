@@ -117,3 +117,12 @@ def test_test_hooks_validate_their_arguments():
     assert e.value.status == 1
     fs.fs_test_inject(fs.FS_TEST_WAIT_TIMEOUT, 64)
     fs.fs_test_inject(fs.FS_TEST_WAIT_TIMEOUT, 0)
+
+
+def test_allocator_entry_points_validate_their_arguments():
+    """fs_set_allocator with one function but not the other is refused; the
+    cache query works without a GPU (nothing cached)."""
+    L = fs.load()
+    fa = _abi.ALLOC_FN(lambda n, ctx: 0)
+    assert L.fs_set_allocator(fa, _abi.FREE_FN(), None) == 1
+    assert L.fs_set_allocator(_abi.ALLOC_FN(), _abi.FREE_FN(), None) == 0
