@@ -259,6 +259,216 @@ __device__ __forceinline__ void pack_warp_push(const PackSeg& g, uint32_t par, i
     __syncwarp();     // the list is reused by the warp's next item
 }
 
+// bytes of v equal to b -> 0xff (per byte, b < 256)
+__device__ __forceinline__ uint64_t eq_bytes(uint64_t v, uint32_t b)
+{
+    const uint32_t bb = b * 0x01010101u;
+    return (uint64_t)__vcmpeq4((uint32_t)v, bb) | ((uint64_t)__vcmpeq4((uint32_t)(v >> 32), bb) << 32);
+}
+
+// bit q of the result = top bit of byte q (bytes 0x00 or 0xff)
+__device__ __forceinline__ uint32_t bytes_to_bits(uint64_t m)
+{
+    const uint32_t lo = (((uint32_t)m & 0x01010101u) * 0x01020408u) >> 24;
+    const uint32_t hi = (((uint32_t)(m >> 32) & 0x01010101u) * 0x01020408u) >> 24;
+    return lo | (hi << 4);
+}
+
+// What a packed warp keeps in shared memory while it processes one group of
+// 8 replicates of its 32 nodes: per node slot (lane * 8 + q) the state, the
+// count, the age and the decision; the queue of draw units; the replicates'
+// scenario headers (probability tables, Philox key, replicate, step size)
+// and the lanes' original node ids.
+struct PackWarp {
+    uint8_t xb[256];
+    uint8_t cb[256];
+    uint8_t fb[256];
+    float age[256];
+    uint16_t q[256];           // draw unit: lane | quad << 5 | replicate mask << 6
+    uint32_t orig[32];
+    // scenario headers of the segment the warp works on (cached across its
+    // items): the first 48 bytes of the PackScen of replicate r, and bit j of
+    // share = replicates 4j .. 4j+3 share key and Philox counter word
+    uint4 sc[kPackMaxR][3];
+    const PackScen* sc_src;
+    uint32_t share;
+};
+
+// the warp's scenario-header cache holds segment g's (loaded when the warp
+// moves to another segment; every lane calls this)
+__device__ __forceinline__ void pack_headers(const PackSeg& g, PackWarp& w)
+{
+    if (w.sc_src == g.scen)
+        return;
+    const int lane = threadIdx.x & 31;
+    uint4 h1 = make_uint4(0u, 0u, 0u, 0u);
+    if (lane < g.R_pad) {
+        const uint4* src = reinterpret_cast<const uint4*>(g.scen + lane);
+        w.sc[lane][0] = __ldg(src);
+        h1 = __ldg(src + 1);
+        w.sc[lane][1] = h1;
+        w.sc[lane][2] = __ldg(src + 2);
+    }
+    const int lead = lane & ~3;
+    const uint32_t k0 = __shfl_sync(kFullP, h1.x, lead), k1 = __shfl_sync(kFullP, h1.y, lead);
+    const uint32_t c2 = __shfl_sync(kFullP, h1.z >> 2, lead);
+    const uint32_t same = __ballot_sync(kFullP, lane < g.R_pad && h1.x == k0 && h1.y == k1 && (h1.z >> 2) == c2);
+    uint32_t share = 0u;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        share |= ((same >> (4 * j)) & 0xfu) == 0xfu ? (1u << j) : 0u;
+    if (lane == 0) {
+        w.share = share;
+        w.sc_src = g.scen;
+    }
+    __syncwarp();
+}
+
+// Bernoulli probability of replicate q of a slot from its scenario header
+// (tables; a miss -- an age off the tabulated sequence -- evaluates the law)
+__device__ __forceinline__ float pack_p_hdr(const PackWarp& w, const PackScen& S, int r, int x, float age,
+                                            uint32_t c)
+{
+    if (x == kS) {
+        const float* ps = reinterpret_cast<const float*>(((uint64_t)w.sc[r][0].w << 32) | w.sc[r][0].z);
+        return __ldg(ps + c);                    // c in 1..255 (thread-class in-degrees are <= 255)
+    }
+    const float4* pt = reinterpret_cast<const float4*>(((uint64_t)w.sc[r][0].y << 32) | w.sc[r][0].x);
+    const float inv_dt = __uint_as_float(w.sc[r][2].y);
+    const int n = __float2int_rn(__fmul_rn(age, inv_dt));
+    if ((unsigned)n < (unsigned)kPTableN) {
+        const float2 e = __ldg(reinterpret_cast<const float2*>(pt + (x == kI ? kPTableN : 0) + n));
+        if (e.x == age)
+            return e.y;
+    }
+    return pack_p(S, x, age, 0u);              // slot 1, else direct evaluation (rare)
+}
+
+// One group of 8 replicates (b) of the warp's 32 nodes: classification of
+// the group's states and counts eight replicates at a time, a queue of draw
+// units shared by the warp's lanes (one Philox call serves the replicates of
+// a quad that share key and counter), then transitions, ages and the
+// per-replicate transition counts. Every lane calls this.
+template <typename AgeT>
+__device__ __forceinline__ void pack_group(const PackSeg& g, int64_t k, int b, bool valid, uint64_t xv, uint64_t cb,
+                                           AgeT* __restrict__ Ag, uint8_t* __restrict__ Xg, PackWarp& w,
+                                           uint32_t& newmask, uint32_t& oldmask, const AgeVec8<AgeT>* pre)
+{
+    const int lane = threadIdx.x & 31;
+    const int slot0 = lane * 8;
+    __syncwarp();                  // the previous group has finished with w
+    const uint64_t sM = eq_bytes(xv, kS), eM = eq_bytes(xv, kE), iM = eq_bytes(xv, kI);
+    const uint64_t eiM = eM | iM;
+    uint32_t need = bytes_to_bits(eiM) | bytes_to_bits(sM & ~eq_bytes(cb, 0u));
+    if (!valid)
+        need = 0u;
+    // quads of the group's replicates that share key and Philox counter
+    // word (rep >> 2) draw once
+    const uint32_t share = (w.share >> (2 * b)) & 3u;
+    const bool anyEI = valid && eiM != 0ull;
+    if (anyEI) {
+        AgeVec8<AgeT> ag;
+        if (pre)
+            ag = *pre;
+        else
+            ag.load(Ag);
+        *reinterpret_cast<float4*>(w.age + slot0) = make_float4(ag.v[0], ag.v[1], ag.v[2], ag.v[3]);
+        *reinterpret_cast<float4*>(w.age + slot0 + 4) = make_float4(ag.v[4], ag.v[5], ag.v[6], ag.v[7]);
+    }
+    *reinterpret_cast<uint64_t*>(w.xb + slot0) = xv;
+    *reinterpret_cast<uint64_t*>(w.cb + slot0) = cb;
+    *reinterpret_cast<uint64_t*>(w.fb + slot0) = 0ull;
+    // draw units of this lane: a shared quad's needing replicates together,
+    // else one unit per needing replicate
+    const uint32_t m0 = need & 0xfu, m1 = need >> 4;
+    const int nu = (m0 ? ((share & 1u) ? 1 : __popc(m0)) : 0) + (m1 ? ((share & 2u) ? 1 : __popc(m1)) : 0);
+    uint32_t incl = (uint32_t)nu;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFullP, incl, o);
+        if (lane >= o)
+            incl += y;
+    }
+    const int total = (int)__shfl_sync(kFullP, incl, 31);
+    {
+        int at = (int)incl - nu;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            uint32_t m = j ? m1 : m0;
+            if (!m)
+                continue;
+            if ((share >> j) & 1u) {
+                w.q[at++] = (uint16_t)((uint32_t)lane | ((uint32_t)j << 5) | (m << 6));
+            } else {
+                while (m) {
+                    const uint32_t bit = m & (0u - m);
+                    m ^= bit;
+                    w.q[at++] = (uint16_t)((uint32_t)lane | ((uint32_t)j << 5) | (bit << 6));
+                }
+            }
+        }
+    }
+    __syncwarp();
+    for (int e = lane; e < total; e += 32) {
+        const uint32_t unit = w.q[e];
+        const int L = (int)(unit & 31u), quad = (int)((unit >> 5) & 1u);
+        uint32_t m = unit >> 6;
+        const int q0 = quad * 4 + __ffs(m) - 1;
+        const uint4 h1 = w.sc[b * 8 + q0][1];
+        const uint4 ph = philox4x32_10(make_uint4(w.orig[L], (uint32_t)k, h1.z >> 2, 0u), h1.x, h1.y);
+        while (m) {
+            const int i = __ffs(m) - 1;
+            m &= m - 1u;
+            const int q = quad * 4 + i, s_ = L * 8 + q;
+            const float p = pack_p_hdr(w, g.scen[b * 8 + q], b * 8 + q, w.xb[s_], w.age[s_], (uint32_t)w.cb[s_]);
+            const uint32_t sel = w.sc[b * 8 + q][1].z & 3u;
+            const uint32_t word = sel == 0 ? ph.x : sel == 1 ? ph.y : sel == 2 ? ph.z : ph.w;
+            w.fb[s_] = (float)(word >> 8) * 5.9604644775390625e-08f < p ? 0xffu : 0u;
+        }
+    }
+    __syncwarp();
+    // transitions: every firing replicate moves on (SEIR: +1; SIR: S -> I is
+    // +2, I -> R +1); ages restart at 0 on firing, else E/I ages advance by
+    // their scenario's step
+    const uint64_t F = valid ? *reinterpret_cast<const uint64_t*>(w.fb + slot0) : 0ull;
+    uint64_t inc = F & 0x0101010101010101ull;
+    if (g.model != kSEIR)
+        inc += F & sM & 0x0101010101010101ull;
+    const uint64_t xn = xv + inc;                       // no byte carries: R never fires
+    if (valid && F)
+        *reinterpret_cast<uint64_t*>(Xg) = xn;
+    if (anyEI) {
+        const uint32_t fb = bytes_to_bits(F), eb = bytes_to_bits(eiM);
+        AgeVec8<AgeT> ag;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const float dtq = __uint_as_float(w.sc[b * 8 + q][1].w);
+            ag.v[q] = ((fb >> q) & 1u) ? 0.0f : (((eb >> q) & 1u) ? __fadd_rn(w.age[slot0 + q], dtq) : 0.0f);
+        }
+        ag.store(Ag);
+    }
+    newmask |= bytes_to_bits(eq_bytes(xn, kI)) << (b * 8);
+    oldmask |= bytes_to_bits(iM) << (b * 8);
+    // per-replicate transitions of this group, summed over the warp: the
+    // fired masks (0xff bytes) become 0/1 bytes, and one warp sum per word
+    // adds four replicates' counts at once (at most 32 per byte, no carry)
+    const uint64_t one = 0x0101010101010101ull;
+    const uint64_t tS = F & sM & one, tE = F & eM & one, tI = F & iM & one;
+    if (!__any_sync(kFullP, (tS | tE | tI) != 0ull))
+        return;
+    const uint32_t s0 = __reduce_add_sync(kFullP, (uint32_t)tS), s1 = __reduce_add_sync(kFullP, (uint32_t)(tS >> 32));
+    const uint32_t s2 = __reduce_add_sync(kFullP, (uint32_t)tE), s3 = __reduce_add_sync(kFullP, (uint32_t)(tE >> 32));
+    const uint32_t s4 = __reduce_add_sync(kFullP, (uint32_t)tI), s5 = __reduce_add_sync(kFullP, (uint32_t)(tI >> 32));
+    // lane f * 8 + q adds field f (S ->, E -> I, I -> R) of replicate b * 8 + q
+    if (lane < 24) {
+        const int f = lane >> 3, q = lane & 7;
+        const uint32_t word = f == 0 ? (q < 4 ? s0 : s1) : f == 1 ? (q < 4 ? s2 : s3) : (q < 4 ? s4 : s5);
+        const uint32_t v = (word >> (8 * (q & 3))) & 0xffu;
+        if (v)
+            atomicAdd(g.deltas + ((k & 1) * g.R_pad + b * 8 + q) * 3 + f, (unsigned long long)v);
+    }
+}
+
 // SELL slice: lane = node, each lane carries all RP replicates of its node.
 // One column load and one RP-bit mask load per edge serve every replicate;
 // the mask bits are spread into byte counters (8 per 64-bit word) through a
@@ -271,9 +481,33 @@ __device__ __forceinline__ void pack_warp_push(const PackSeg& g, uint32_t par, i
 // step's pushes (bytewise on 8 replicates at once: every byte stays within
 // 0..255, so no borrow or carry crosses bytes); replicates that enter or
 // leave I are then pushed by the warp along the transposed rows.
+// The loads of a slice that need nothing else: its SELL offsets, the lane's
+// original node id and its replicates' states. The kernel issues them one
+// item ahead, while the warp processes the previous slice.
+template <int RP> struct SliceLoads {
+    int64_t off, off_end;
+    uint32_t orig;
+    uint64_t xs[RP / 8];
+};
+
+template <int RP, bool PUSH>
+__device__ __forceinline__ void slice_loads(const PackSeg& g, int slice, SliceLoads<RP>& L)
+{
+    const int i = slice * 32 + (threadIdx.x & 31);
+    const bool valid = i < g.n_thr;
+    L.off = PUSH ? 0 : __ldg(g.sell_off + slice);
+    L.off_end = PUSH ? 0 : __ldg(g.sell_off + slice + 1);
+    L.orig = (valid && g.perm) ? (uint32_t)__ldg(g.perm + i) : (uint32_t)i;
+    const uint64_t* xp = reinterpret_cast<const uint64_t*>(g.X + (int64_t)i * RP);
+#pragma unroll
+    for (int b = 0; b < RP / 8; ++b)
+        L.xs[b] = valid ? xp[b] : 0x0303030303030303ull;
+}
+
 template <typename AgeT, int RP, bool PUSH>
-__device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slice, const uint64_t* __restrict__ lut,
-                                           float* __restrict__ spv, uint32_t* __restrict__ wlist)
+__device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slice, const SliceLoads<RP>& L,
+                                           const uint64_t* __restrict__ lut, PackWarp& pw,
+                                           uint32_t* __restrict__ wlist)
 {
     using MT = typename MaskOf<RP>::T;
     constexpr int NB = RP / 8;
@@ -283,17 +517,12 @@ __device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slic
     const bool valid = i < g.n_thr;
     const MT* __restrict__ mk = static_cast<const MT*>(g.mask[k & 1]);
     MT* __restrict__ mkn = static_cast<MT*>(g.mask[(k + 1) & 1]);
-    const PackScen* __restrict__ scen = g.scen;
-    const int model = g.model;
-    // independent loads first: slice offsets, original id, states
-    const int64_t off = PUSH ? 0 : __ldg(g.sell_off + slice);
-    const int64_t off_end = PUSH ? 0 : __ldg(g.sell_off + slice + 1);
-    const uint32_t orig = (valid && g.perm) ? (uint32_t)__ldg(g.perm + i) : (uint32_t)i;
+    const int64_t off = L.off, off_end = L.off_end;
+    const uint32_t orig = L.orig;
     uint64_t xs[NB];
-    const uint64_t* xp = reinterpret_cast<const uint64_t*>(g.X + (int64_t)i * RP);
 #pragma unroll
     for (int b = 0; b < NB; ++b)
-        xs[b] = valid ? xp[b] : 0x0303030303030303ull;
+        xs[b] = L.xs[b];
     bool allR = true, anyS = false;
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
@@ -305,21 +534,18 @@ __device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slic
             mkn[i] = (MT)0;
         return;
     }
-    AgeT* __restrict__ Abase = static_cast<AgeT*>(g.A) + (int64_t)i * RP;
-    uint8_t* Xb = g.X + (int64_t)i * RP;
     // ages are read and written only for groups holding an E or I
     // replicate: the age slot of S and R replicates is always 0, and a
-    // transition from S leaves it at 0. The first group's ages are issued
-    // before the neighbour gather so that the two overlap.
-    bool ageful = valid && (has_byte(xs[0], (uint32_t)kE) || has_byte(xs[0], (uint32_t)kI));
-    AgeVec8<AgeT> ag;
-    if (ageful)
-        ag.load(Abase);
-    else {
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-            ag.v[q] = 0.0f;
-    }
+    // transition from S leaves it at 0
+    AgeT* __restrict__ Abase = static_cast<AgeT*>(g.A) + (int64_t)i * RP;
+    uint8_t* Xb = g.X + (int64_t)i * RP;
+    // the first group's ages are issued before the neighbour gather so that
+    // the two overlap
+    AgeVec8<AgeT> ag0;
+    const bool ei0 = valid && (has_byte(xs[0], (uint32_t)kE) || has_byte(xs[0], (uint32_t)kI));
+    if (ei0)
+        ag0.load(Abase);
+    pack_headers(g, pw);
     uint64_t cnt[NB];
 #pragma unroll
     for (int b = 0; b < NB; ++b)
@@ -377,124 +603,14 @@ __device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slic
         }
     }
     uint32_t newmask = 0, oldmask = 0;
-    // Philox cache: counter word 2 and key of the last draw
-    uint4 ph = make_uint4(0u, 0u, 0u, 0u);
-    uint32_t ph_k0 = 0u, ph_k1 = 0u, ph_c2 = 0xffffffffu;
-    bool ph_ok = false;
-    // groups are taken from xs[0] / cnt[0], the arrays shifted down after each
-    // one (static indices keep them in registers)
-#pragma unroll 1
+    __syncwarp();                  // the warp's previous item has finished with pw
+    pw.orig[lane] = orig;
+#pragma unroll
     for (int b = 0; b < NB; ++b) {
         if (b * 8 >= g.R)
             break;
-        const uint64_t xv = xs[0];
-        const uint64_t cb = cnt[0];
-#pragma unroll
-        for (int t = 0; t + 1 < NB; ++t) {
-            xs[t] = xs[t + 1];
-            cnt[t] = cnt[t + 1];
-        }
-        if (b > 0) {
-            ageful = valid && (has_byte(xv, (uint32_t)kE) || has_byte(xv, (uint32_t)kI));
-            if (ageful)
-                ag.load(Abase + b * 8);
-            else {
-#pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    ag.v[q] = 0.0f;
-            }
-        }
-        // probabilities of the 8 replicates: table loads are issued four at a
-        // time, then resolved (a miss falls back to direct evaluation); they
-        // go to this lane's column of spv, and bit q of act marks p > 0
-        uint32_t act = 0;
-#pragma unroll
-        for (int h = 0; h < 8; h += 4) {
-            float sp[8];                    // entries h..h+3 used
-            float2 et[8];
-#pragma unroll
-            for (int q = h; q < h + 4; ++q) {
-                const int x = (int)((xv >> (8 * q)) & 0xffu);
-                const uint32_t c = (uint32_t)((cb >> (8 * q)) & 0xffu);
-                const uint4 h0 = __ldg(reinterpret_cast<const uint4*>(scen + b * 8 + q));
-                const float inv_dt = __uint_as_float(__ldg(reinterpret_cast<const uint32_t*>(scen + b * 8 + q) + 9));
-                const float* ps = reinterpret_cast<const float*>(((uint64_t)h0.w << 32) | h0.z);
-                const float4* pt = reinterpret_cast<const float4*>(((uint64_t)h0.y << 32) | h0.x);
-                const int n = __float2int_rn(__fmul_rn(ag.v[q], inv_dt));
-                sp[q] = (x == kS && c != 0u) ? __ldg(ps + c) : 0.0f;      // c < 256 = kPSTableN
-                et[q] = ((x == kE || x == kI) && (unsigned)n < (unsigned)kPTableN)
-                            ? __ldg(reinterpret_cast<const float2*>(pt + (x == kI ? kPTableN : 0) + n))
-                            : make_float2(-1.0f, 0.0f);
-            }
-#pragma unroll
-            for (int q = h; q < h + 4; ++q) {
-                const int x = (int)((xv >> (8 * q)) & 0xffu);
-                float pq = sp[q];
-                if (x == kE || x == kI)
-                    pq = (et[q].x == ag.v[q]) ? et[q].y : pack_p(scen[b * 8 + q], x, ag.v[q], 0u);
-                spv[q * 32 + lane] = pq;
-                act |= (uint32_t)(pq > 0.0f) << q;
-            }
-        }
-        // E and I replicates age by their dt (one that fires restarts at 0 below)
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int x = (int)((xv >> (8 * q)) & 0xffu);
-            if (x == kE || x == kI)
-                ag.v[q] = __fadd_rn(ag.v[q], __uint_as_float(__ldg(reinterpret_cast<const uint32_t*>(scen + b * 8 + q) + 7)));
-        }
-        // uniforms only for the replicates with p > 0; bit q of F: fired
-        uint32_t F = 0;
-        for (uint32_t todo = act; todo != 0u; todo &= todo - 1u) {
-            const int q = __ffs(todo) - 1;
-            const uint4 h1 = __ldg(reinterpret_cast<const uint4*>(scen + b * 8 + q) + 1);   // key0, key1, rep, dt
-            const uint32_t k0 = h1.x, k1 = h1.y, rep = h1.z;
-            if (!ph_ok || k0 != ph_k0 || k1 != ph_k1 || (rep >> 2) != ph_c2) {
-                ph = philox4x32_10(make_uint4(orig, (uint32_t)k, rep >> 2, 0u), k0, k1);
-                ph_k0 = k0;
-                ph_k1 = k1;
-                ph_c2 = rep >> 2;
-                ph_ok = true;
-            }
-            const uint32_t sel = rep & 3u;
-            const uint32_t word = sel == 0 ? ph.x : sel == 1 ? ph.y : sel == 2 ? ph.z : ph.w;
-            F |= (uint32_t)((float)(word >> 8) * 5.9604644775390625e-08f < spv[q * 32 + lane]) << q;
-        }
-        // transitions: S -> E (SEIR) or I (SIR), E -> I, I -> R
-        uint64_t xnew = xv;
-        uint32_t fS = 0, fE = 0, fI = 0;     // bit q: replicate b*8+q fired from S / E / I
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int x = (int)((xv >> (8 * q)) & 0xffu);
-            const bool fired = (F >> q) & 1u;
-            const int xn = !fired ? x : (x == kS) ? (model == kSEIR ? kE : kI) : (x + 1);
-            if (fired) {
-                ag.v[q] = 0.0f;
-                xnew = (xnew & ~(0xffull << (8 * q))) | ((uint64_t)xn << (8 * q));
-            }
-            fS |= (uint32_t)(fired && x == kS) << q;
-            fE |= (uint32_t)(fired && x == kE) << q;
-            fI |= (uint32_t)(fired && x == kI) << q;
-            newmask |= (uint32_t)(xn == kI) << (b * 8 + q);
-            oldmask |= (uint32_t)(x == kI) << (b * 8 + q);
-        }
-        if (valid) {
-            if (xnew != xv)
-                reinterpret_cast<uint64_t*>(Xb)[b] = xnew;
-            if (ageful)
-                ag.store(Abase + b * 8);
-        }
-        // per-replicate transitions of this group, summed over the warp
-        if (!__any_sync(kFullP, (fS | fE | fI) != 0u))
-            continue;
-#pragma unroll 1
-        for (int q = 0; q < 8; ++q) {
-            const uint32_t a = __popc(__ballot_sync(kFullP, (fS >> q) & 1u));
-            const uint32_t e = __popc(__ballot_sync(kFullP, (fE >> q) & 1u));
-            const uint32_t h = __popc(__ballot_sync(kFullP, (fI >> q) & 1u));
-            if (lane == 0 && (a | e | h))
-                add_deltas(g, k, b * 8 + q, a, e, h);
-        }
+        pack_group<AgeT>(g, k, b, valid, xs[b], cnt[b], Abase + b * 8, Xb + b * 8, pw, newmask, oldmask,
+                         b == 0 && ei0 ? &ag0 : nullptr);
     }
     if constexpr (PUSH) {
         const uint32_t en = valid ? newmask & ~oldmask : 0u, lv = valid ? oldmask & ~newmask : 0u;
@@ -644,18 +760,24 @@ __device__ __forceinline__ void pack_integrate(const PackSeg& g, int64_t k)
 
 // Minimum resident blocks per SM of the packed step, by replicate width: the
 // register budget that measured fastest for each (80 and 96 registers).
-template <int RP> struct PackOcc { static constexpr int kMinBlocks = RP == 8 ? 6 : 5; };
+#ifndef FS_PACK_MIN_BLOCKS8
+#define FS_PACK_MIN_BLOCKS8 6
+#endif
+template <int RP> struct PackOcc { static constexpr int kMinBlocks = RP == 8 ? FS_PACK_MIN_BLOCKS8 : 5; };
 
 template <typename AgeT, int RP, bool PUSH>
 __global__ void __launch_bounds__(kPackThreads, PackOcc<RP>::kMinBlocks) pack_step_kernel(const __grid_constant__ PackArgs a)
 {
     // byte r of lut[m] is bit r of m: spreads an 8-replicate mask into byte counters
     __shared__ uint64_t lut[256];
-    // per warp: the probabilities of one 8-replicate group, [q][lane]
-    __shared__ float s_pv[kPackThreads / 32][8 * 32];
+    // per warp: one 8-replicate group of its slice (states, counts, ages,
+    // decisions, the draw queue, the replicates' scenario headers)
+    __shared__ PackWarp s_pw[kPackThreads / 32];
     // per warp: the push events of one slice (node, entering mask, leaving mask)
     __shared__ uint32_t s_ev[kPackThreads / 32][3 * 32];
-    float* spv = s_pv[threadIdx.x >> 5];
+    PackWarp& pw = s_pw[threadIdx.x >> 5];
+    if ((threadIdx.x & 31) == 0)
+        pw.sc_src = nullptr;
     uint32_t* wlist = s_ev[threadIdx.x >> 5];
     for (int m = threadIdx.x; m < 256; m += blockDim.x) {
         uint64_t v = 0;
@@ -690,16 +812,31 @@ __global__ void __launch_bounds__(kPackThreads, PackOcc<RP>::kMinBlocks) pack_st
         else
             pack_hub_row<AgeT, RP>(g, k, (int)(it - __ldg(a.hub_pre + s)));
     }
+    // one item per 32-node slice; the next item's independent loads are
+    // issued before the current one is processed
     s = s0;
-    for (int64_t it = thr0 + gw; it < n_thr; it += W) {
+    int64_t it = thr0 + gw;
+    SliceLoads<RP> cur;
+    if (it < n_thr) {
         while (__ldg(a.thr_pre + s + 1) <= it)
             ++s;
-        const PackSeg& g = a.seg[s];
+        slice_loads<RP, PUSH>(a.seg[s], (int)(it - __ldg(a.thr_pre + s)), cur);
+    }
+    while (it < n_thr) {
+        const int sc = s;
+        const int64_t ic = it;
+        it += W;
+        SliceLoads<RP> nxt;
+        if (it < n_thr) {
+            while (__ldg(a.thr_pre + s + 1) <= it)
+                ++s;
+            slice_loads<RP, PUSH>(a.seg[s], (int)(it - __ldg(a.thr_pre + s)), nxt);
+        }
+        const PackSeg& g = a.seg[sc];
         const int64_t k = G - g.join;
-        if (k < g.kmin || k >= g.kend)
-            continue;
-        // one item per 32-node slice
-        pack_slice<AgeT, RP, PUSH>(g, k, (int)(it - __ldg(a.thr_pre + s)), lut, spv, wlist);
+        if (k >= g.kmin && k < g.kend)
+            pack_slice<AgeT, RP, PUSH>(g, k, (int)(ic - __ldg(a.thr_pre + sc)), cur, lut, pw, wlist);
+        cur = nxt;
     }
 }
 
