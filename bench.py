@@ -77,6 +77,7 @@ def parse():
     ap.add_argument("--age", choices=["f32", "f16"], default="f32", help="age storage of ensemble/serving runs")
     ap.add_argument("--ens-graphs", type=int, default=64, help="graphs of the packed-ensemble run")
     ap.add_argument("--ens-steps", type=int, default=500, help="steps of the packed-ensemble run")
+    ap.add_argument("--serve-requests", type=int, default=60, help="requests of --workload serving")
     ap.add_argument("--no-other-form", action="store_true", help="skip timing the other pressure form")
     ap.add_argument("--large-n", type=str, default="",
                     help="comma-separated N of --workload large (default: 1e7 and 1e8 FP32, 1e8 BF16)")
@@ -346,10 +347,14 @@ def cpu_baseline(graphs, budget_s=10.0, max_steps=400):
 
 
 # ------------------------------------------------------------------ ensembles and serving
-def scen_params(fs, sc, replicate: int, age_dtype: int, pressure: int = 0):
+def scen_params(fs, sc, replicate: int, age_dtype: int, pressure: int = 0, seed: int | None = None):
+    """One scenario's parameters. The realisations of a request draw from one
+    Philox key (the request's seed) and are told apart by the replicate index
+    (scenario * replicates + replicate)."""
     latent = fs.law("erlang", 0.75, k=3) if sc.latent == "erlang" else fs.law("weibull", 2.0, 4.0)
     return fs.sim_params(fs.FS_SEIR, fs.law("lognormal", math.log(6.0), float(sc.sigma_inf)), float(sc.beta), 0.1,
-                         int(sc.seed), latent=latent, replicate=replicate, age_dtype=age_dtype, pressure=pressure)
+                         int(sc.seed if seed is None else seed), latent=latent, replicate=replicate,
+                         age_dtype=age_dtype, pressure=pressure)
 
 
 def index_for(g, count=100, seed=1):
@@ -404,11 +409,12 @@ def ensemble_bench(fs, torch, n_graphs, n_lo, n_hi, steps, age_dtype, reps=3, pr
     ghs = [fs.fs_graph_create(g.n, g.row_ptr, g.col_ind) for g in graphs]
     idxs = [index_for(g, seed=q + 1) for q, g in enumerate(graphs)]
     scen = [W.scenarios(8, seed=1000 + q) for q in range(n_graphs)]
+    req_seed = [int(sc[0].seed) for sc in scen]          # each graph's 8 scenarios are one request
     stream = torch.cuda.Stream()
     times = []
     for it in range(reps):
-        ens = [fs.fs_ens_create(ghs[q], [scen_params(fs, sc, s, age_dtype, pressure) for s, sc in enumerate(scen[q])],
-                                idxs[q])
+        ens = [fs.fs_ens_create(ghs[q], [scen_params(fs, sc, s, age_dtype, pressure, seed=req_seed[q])
+                                         for s, sc in enumerate(scen[q])], idxs[q])
                for q in range(n_graphs)]
         b = fs.fs_batch_create(age_dtype, n_graphs + 1, stream=stream)
         for e in ens:
@@ -428,13 +434,25 @@ def ensemble_bench(fs, torch, n_graphs, n_lo, n_hi, steps, age_dtype, reps=3, pr
     # the plain engine: every realisation alone, one after the other (a first
     # pass over scenario 0 of each graph warms the step code and the caches)
     for q in range(n_graphs):
-        plain_seconds(fs, ghs[q], scen_params(fs, scen[q][0], 0, age_dtype), idxs[q], steps)
+        plain_seconds(fs, ghs[q], scen_params(fs, scen[q][0], 0, age_dtype, seed=req_seed[q]), idxs[q], steps)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for q in range(n_graphs):
         for s_, sc in enumerate(scen[q]):
-            plain_seconds(fs, ghs[q], scen_params(fs, sc, s_, age_dtype), idxs[q], steps)
+            plain_seconds(fs, ghs[q], scen_params(fs, sc, s_, age_dtype, seed=req_seed[q]), idxs[q], steps)
     plain_s = time.perf_counter() - t0
+    # the same, in the paper's one-run-per-launch form (Algorithm 3's gather
+    # of the infectious neighbours every step)
+    for q in range(n_graphs):
+        plain_seconds(fs, ghs[q], scen_params(fs, scen[q][0], 0, age_dtype, fs.FS_PRESSURE_GATHER, seed=req_seed[q]),
+                      idxs[q], steps)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for q in range(n_graphs):
+        for s_, sc in enumerate(scen[q]):
+            plain_seconds(fs, ghs[q], scen_params(fs, sc, s_, age_dtype, fs.FS_PRESSURE_GATHER, seed=req_seed[q]),
+                          idxs[q], steps)
+    plain_gather_s = time.perf_counter() - t0
     for gh in ghs:
         fs.fs_graph_destroy(gh)
     return {"workload": f"packed-{n_graphs}graphs-x8scen-n{n_lo:.0e}-{n_hi:.0e}-{steps}steps".replace("+0", ""),
@@ -443,15 +461,29 @@ def ensemble_bench(fs, torch, n_graphs, n_lo, n_hi, steps, age_dtype, reps=3, pr
             "served_gnups": round(updates / served_s / 1e9, 3), "served_seconds": round(served_s, 4),
             "plain_gnups": round(updates / plain_s / 1e9, 3), "plain_seconds": round(plain_s, 3),
             "speedup": round(plain_s / served_s, 2),
+            "plain_gather_gnups": round(updates / plain_gather_s / 1e9, 3),
+            "plain_gather_seconds": round(plain_gather_s, 3),
+            "speedup_vs_gather": round(plain_gather_s / served_s, 2),
             "plain_engine": "every realisation run alone through fs_sim_run (init + CUDA Graph step loop + "
-                            "counts read back), back to back, host wall clock"}
+                            "counts read back), back to back, host wall clock; plain_*: the library's default "
+                            "single-realisation form (infection counts kept by pushes); plain_gather_*: the "
+                            "paper's form (Algorithm 3, every S node gathers its row each step)",
+            "request_seeds": "one Philox key per graph (its 8 scenarios are one request), replicate index = "
+                             "scenario number"}
 
 
-def serving_bench(fs, torch, n_requests, n_pool, n_hi, steps, rep_lo, rep_hi, window_s, age_dtype):
-    """Poisson stream of requests against the server, then the same stream
-    through the plain engine (each realisation alone, FIFO); the plain
-    queue is replayed on measured service times."""
-    pool = [W.mixed_graph(q, 1e4, n_hi, seed=77) for q in range(n_pool)]
+def serving_bench(fs, torch, n_requests, n_pool, n_hi, steps, rep_lo, rep_hi, window_s, age_dtype, big_n=0,
+                  big_age=None, plain_sample=4):
+    """A Poisson stream of requests against the server (optionally beside one
+    big SEIR job on a random 10-regular graph of big_n nodes, run on its own
+    stream at the same time), then the same stream through the plain engine:
+    every request's realisations alone through fs_sim_run, one request after
+    the other in arrival order. The plain service time of a request is
+    measured on a random sample of its realisations (plain_sample of them,
+    across its scenarios) and scaled by its realisation count; the plain
+    queue (and the big job, run alone after it) is replayed on those
+    measured times."""
+    pool = mixed_graphs(n_pool, 1e4, n_hi, seed=77)
     ghs = [fs.fs_graph_create(g.n, g.row_ptr, g.col_ind) for g in pool]
     idxs = [index_for(g, seed=q + 5) for q, g in enumerate(pool)]
     reqs = W.request_stream(n_requests, n_requests / window_s, n_pool, seed=99, steps=steps, rep_lo=rep_lo,
@@ -460,46 +492,90 @@ def serving_bench(fs, torch, n_requests, n_pool, n_hi, steps, rep_lo, rep_hi, wi
     # warm the server's graph capture on a tiny request
     wid = fs.fs_server_submit(srv, ghs[0], [scen_params(fs, W.scenarios(1, 5)[0], 0, age_dtype)], 1, idxs[0], 5)
     fs.fs_server_drain(srv, 120)
+    big = None
+    if big_n:
+        dev = torch.device("cuda")
+        rp, col = device_regular(torch, int(big_n), 10, seed=0, dev=dev)
+        bstream = torch.cuda.Stream()
+        bgh = fs.fs_graph_create(int(big_n), rp, col, opts=fs.graph_opts(device_input=True), stream=bstream)
+        bprm = fs.sim_params(fs.FS_SEIR, fs.law("lognormal", math.log(6.0), 0.6), 0.25, 0.1, 1,
+                             latent=fs.law("weibull", 2.0, 4.0), age_dtype=big_age if big_age is not None else age_dtype)
+        bidx = W.index_nodes(int(big_n), 100, seed=1)
+        # alone first (its plain time), then beside the request stream
+        t_b = time.perf_counter()
+        bsh = fs.fs_sim_init(bgh, bprm, bidx, stream=bstream)
+        fs.fs_sim_run(bsh, 1000, 50, want_counts=False)
+        big_alone = time.perf_counter() - t_b
+        fs.fs_sim_destroy(bsh)
+        bsh = fs.fs_sim_init(bgh, bprm, bidx, stream=bstream)
+        big = {"n": int(big_n), "steps": 1000, "alone_s": round(big_alone, 3)}
     t0 = time.perf_counter()
+    if big:
+        fs.fs_sim_run_async(bsh, 1000, 50)
     ids = []
     for r in reqs:
         while time.perf_counter() - t0 < r.arrival:
             time.sleep(0.0002)
         sc = W.scenarios(r.n_scen, seed=r.seed)
-        ids.append(fs.fs_server_submit(srv, ghs[r.graph], [scen_params(fs, c, 0, age_dtype) for c in sc],
-                                       r.replicates, idxs[r.graph], r.steps))
+        ids.append(fs.fs_server_submit(srv, ghs[r.graph],
+                                       [scen_params(fs, c, j * r.replicates, age_dtype, seed=r.seed)
+                                        for j, c in enumerate(sc)], r.replicates, idxs[r.graph], r.steps))
     fs.fs_server_drain(srv, 3600)
+    stream_done = time.perf_counter() - t0
+    if big:
+        fs.fs_sim_sync(bsh)
     makespan = time.perf_counter() - t0
     lat = np.array([fs.fs_server_poll(srv, rid)[2] for rid in ids])
     fs.fs_server_destroy(srv)
     updates = sum(pool[r.graph].n * r.n_scen * r.replicates * r.steps for r in reqs)
-    # plain engine: service time of a request = its realisations one by one
-    # (one realisation per graph and scenario count is timed and scaled)
-    svc = {}
-    clock, plain_lat = 0.0, []
+    big_updates = 0
+    if big:
+        big["counts_final"] = [int(x) for x in fs.fs_sim_run(bsh, 0)[0]]
+        fs.fs_sim_destroy(bsh)
+        fs.fs_graph_destroy(bgh)
+        big_updates = big["n"] * big["steps"]
+    # the plain engine: a random sample of each request's realisations, each
+    # alone (a warm-up run first for every graph)
+    rng = np.random.default_rng(2027)
+    for q in range(n_pool):
+        plain_seconds(fs, ghs[q], scen_params(fs, W.scenarios(1, seed=q)[0], 0, age_dtype), idxs[q], 5)
+    clock, plain_lat, sampled = 0.0, [], 0
     for r in reqs:
-        key = r.graph
-        if key not in svc:
-            p = scen_params(fs, W.scenarios(1, seed=r.seed)[0], 0, age_dtype)
-            plain_seconds(fs, ghs[r.graph], p, idxs[r.graph], r.steps)
-            svc[key] = plain_seconds(fs, ghs[r.graph], p, idxs[r.graph], r.steps)
-        service = svc[key] * r.n_scen * r.replicates
+        sc = W.scenarios(r.n_scen, seed=r.seed)
+        total = r.n_scen * r.replicates
+        picks = rng.choice(total, size=min(plain_sample, total), replace=False)
+        secs = []
+        for pk in picks:
+            j, rep = int(pk) // r.replicates, int(pk) % r.replicates
+            p = scen_params(fs, sc[j], j * r.replicates + rep, age_dtype, seed=r.seed)
+            secs.append(plain_seconds(fs, ghs[r.graph], p, idxs[r.graph], r.steps))
+        sampled += len(secs)
+        service = float(np.mean(secs)) * total
         start = max(clock, r.arrival)
         clock = start + service
         plain_lat.append(clock - r.arrival)
     plain_lat = np.array(plain_lat)
+    plain_total = clock + (big["alone_s"] if big else 0.0)
     for gh in ghs:
         fs.fs_graph_destroy(gh)
-    return {"workload": f"serving-{n_requests}req-pool{n_pool}-n1e4-{n_hi:.0e}-{steps}steps-rep{rep_lo}-{rep_hi}".replace("+0", ""),
-            "arrival_rate_per_s": round(n_requests / window_s, 2),
-            "served_gnups": round(updates / makespan / 1e9, 3), "served_makespan_s": round(makespan, 3),
-            "served_p50_s": round(float(np.percentile(lat, 50)), 4), "served_p99_s": round(float(np.percentile(lat, 99)), 4),
-            "plain_gnups": round(updates / clock / 1e9, 3), "plain_makespan_s": round(clock, 3),
-            "plain_p50_s": round(float(np.percentile(plain_lat, 50)), 4),
-            "plain_p99_s": round(float(np.percentile(plain_lat, 99)), 4),
-            "speedup": round(clock / makespan, 2), "node_updates": int(updates),
-            "plain_engine": "each realisation alone through fs_sim_run (CUDA Graph step loop), FIFO; service times "
-                            "measured per graph and scaled by realisations; queue replayed on them"}
+    out = {"workload": f"serving-{n_requests}req-pool{n_pool}-n1e4-{n_hi:.0e}-{steps}steps-rep{rep_lo}-{rep_hi}".replace("+0", "")
+                       + (f"+seir-regular10-n{big_n:.0e}".replace("+0", "") if big else ""),
+           "arrival_rate_per_s": round(n_requests / window_s, 2),
+           "served_gnups": round((updates + big_updates) / makespan / 1e9, 3), "served_makespan_s": round(makespan, 3),
+           "served_stream_s": round(stream_done, 3),
+           "served_p50_s": round(float(np.percentile(lat, 50)), 4), "served_p99_s": round(float(np.percentile(lat, 99)), 4),
+           "plain_gnups": round((updates + big_updates) / plain_total / 1e9, 3), "plain_makespan_s": round(plain_total, 3),
+           "plain_p50_s": round(float(np.percentile(plain_lat, 50)), 4),
+           "plain_p99_s": round(float(np.percentile(plain_lat, 99)), 4),
+           "speedup": round(plain_total / makespan, 2), "node_updates": int(updates + big_updates),
+           "plain_engine": f"every request's service time measured on a random sample of its realisations "
+                           f"({sampled} runs in all, each alone through fs_sim_run), scaled by its realisation "
+                           f"count; requests one after the other in arrival order, queue replayed on those times"
+                           + ("; the big job run alone after them" if big else "")}
+    if big:
+        big["age_storage"] = {fs.FS_AGE_F32: "f32", fs.FS_AGE_F16: "f16", fs.FS_AGE_BF16: "bf16"}[bprm.age_dtype]
+        out["big_job"] = big
+    return out
 
 
 # ------------------------------------------------------------------ arms
@@ -1140,8 +1216,11 @@ def run_extra(args):
             print(json.dumps({"metric": METRIC, "impl": "flashstep", "data": "synthetic", **res}), flush=True)
         return
     else:
-        res = serving_bench(fs, torch, n_requests=200, n_pool=24, n_hi=1e6, steps=500, rep_lo=16, rep_hi=256,
-                            window_s=2.0, age_dtype=age)
+        # C4's shape scaled to a few minutes: request graphs up to N = 10^7,
+        # beside the N = 10^8 SEIR job with BF16 ages
+        res = serving_bench(fs, torch, n_requests=args.serve_requests, n_pool=16, n_hi=1e7, steps=200, rep_lo=16,
+                            rep_hi=256, window_s=args.serve_requests / 40.0, age_dtype=age, big_n=1e8,
+                            big_age=fs.FS_AGE_BF16)
     print(json.dumps({"metric": METRIC, "unit": UNIT, "impl": "flashstep", "data": "synthetic", **res}), flush=True)
 
 
