@@ -153,8 +153,10 @@ typedef struct {
      * FP32 on the device; ages advance by that value; hazards are evaluated
      * directly (no memoised tables, since ages leave the fixed-step
      * sequence). Single realisations, in either pressure form and with or
-     * without a shedding profile; packed ensembles, batches, the server and
-     * fs_step_noalloc need eps = 0. */
+     * without a shedding profile; packed ensembles, batches and the server
+     * (each realisation with its own step size and clock, fs_ens_time; every
+     * realisation of an ensemble or request adaptive, or none);
+     * fs_step_noalloc needs eps = 0. */
     double eps;          /* 0: fixed step; > 0: the tolerance (the paper uses 0.01-0.05) */
     double delta;        /* added to lambda*; 0 = 1e-12                            */
     fs_law shedding;     /* the law of s(tau) when shed_mode != FS_SHED_NONE       */
@@ -375,7 +377,11 @@ typedef struct fs_batch fs_batch;
 
 /* params[n_real]: every entry must share model, age_dtype and index_state;
  * the index nodes (host int32[n_index], distinct original ids) are the same
- * for every realisation. Errors: FS_EINVAL, FS_ENOMEM, FS_ECUDA. */
+ * for every realisation. Either every realisation takes the adaptive step
+ * (eps > 0, Section 5.2; each replicate then has its own step size and
+ * clock: its trajectory is the one it has alone through fs_sim_*) or none.
+ * Errors: FS_EINVAL, FS_ENOMEM, FS_ECUDA, FS_EUNSUPPORTED (a shedding
+ * profile, FS_ACTIVE_LIST, theta > 0). */
 fs_status fs_ens_create(fs_graph* g, const fs_sim_params* params, int32_t n_real, const int32_t* index_nodes,
                         int64_t n_index, fs_ens** out);
 /* Runs the ensemble alone for `steps` steps (a batch of one).
@@ -384,6 +390,10 @@ fs_status fs_ens_run(fs_ens* e, int64_t steps, int32_t graph_steps, uint32_t* co
 /* Host copies of realisation r's state (original node order) and the number
  * of steps the ensemble has run. Synchronous. */
 fs_status fs_ens_get_state(fs_ens* e, int32_t r, uint8_t* state, void* age, int64_t* step);
+/* Per realisation r < n_real (host arrays, each may be NULL): the simulated
+ * time its steps have covered, and the size of its next step (the adaptive
+ * rule, Section 5.2; the fixed dt otherwise). Synchronous. */
+fs_status fs_ens_time(fs_ens* e, double* elapsed, float* next_dt);
 /* FS_EBUSY while the ensemble is a live member of a batch. */
 fs_status fs_ens_destroy(fs_ens* e);
 

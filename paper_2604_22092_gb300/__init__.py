@@ -29,7 +29,7 @@ __all__ = [
     "fs_sim_get_state", "fs_sim_set_state", "fs_sim_work", "fs_sim_pressure_get", "fs_sim_time",
     "fs_sim_infectivity_get", "fs_sim_active_units", "fs_sim_transitions", "fs_sim_destroy",
     "fs_eval_hazard", "fs_eval_density",
-    "fs_eval_uniforms", "fs_step_noalloc", "fs_ens_create", "fs_ens_run", "fs_ens_get_state",
+    "fs_eval_uniforms", "fs_step_noalloc", "fs_ens_create", "fs_ens_run", "fs_ens_get_state", "fs_ens_time",
     "fs_ens_destroy", "fs_batch_create", "fs_batch_add", "fs_batch_run", "fs_batch_status", "fs_batch_destroy",
     "fs_server_create", "fs_server_submit", "fs_server_poll", "fs_server_drain", "fs_server_stats_get",
     "fs_server_destroy", "fs_test_inject", "fs_debug_bounds_build", "fs_set_allocator",
@@ -329,6 +329,14 @@ def fs_debug_bounds_build() -> bool:
 
 
 # --------------------------------------------------------------- ensembles
+def fs_ens_time(e: int, n_real: int) -> tuple[np.ndarray, np.ndarray]:
+    """(simulated time covered, size of the next step) of every realisation."""
+    t = np.zeros(n_real, dtype=np.float64)
+    d = np.zeros(n_real, dtype=np.float32)
+    check(load().fs_ens_time(e, _addr(t), _addr(d)), "fs_ens_time")
+    return t, d
+
+
 def fs_ens_create(g: int, params, index_nodes) -> int:
     """params: a sequence of fs_sim_params (1..32 realisations of graph g)."""
     arr = (_abi.fs_sim_params * len(params))(*params)

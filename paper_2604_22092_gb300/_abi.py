@@ -82,6 +82,7 @@ PROTOTYPES = {
     "fs_graph_destroy": (ctypes.c_int, [VP]),
     "fs_test_inject": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64]),
     "fs_set_allocator": (ctypes.c_int, [ALLOC_FN, FREE_FN, VP]),
+    "fs_ens_time": (ctypes.c_int, [VP, VP, VP]),
     "fs_release_cached_memory": (ctypes.c_int, []),
     "fs_cached_memory": (ctypes.c_int, [P(ctypes.c_uint64), P(ctypes.c_uint64)]),
     "fs_debug_bounds_build": (ctypes.c_int, [P(ctypes.c_int32)]),

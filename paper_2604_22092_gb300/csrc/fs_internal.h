@@ -242,7 +242,7 @@ struct __align__(16) PackScen {   // one realisation of a segment
     uint32_t key0, key1, rep;   // copies of M.key0, M.key1, M.rep (Philox key and replicate index)
     float dt;               // copy of M.dt
     float beta, inv_dt;     // copies of M.beta, M.inv_dt
-    int32_t pad_[2];
+    float eps, delta;       // adaptive step (eps > 0): dt_k = min(dt, eps / (lambda*_{k-1} + delta))
     ModelF M;               // all parameters (direct evaluation when a table misses)
 };
 
@@ -278,6 +278,13 @@ struct PackSeg {            // one row of the segment table
     unsigned long long* phpd[2];    // [n_m][R_pad] tallies: +1 low word, -1 high word
     const int64_t* out_ptr;         // [n + 1]
     const int32_t* out_col;         // [nnz]
+    // adaptive step (every realisation of the segment has eps > 0; null =
+    // fixed step): lam[(k % 3) * R_pad + r] = the largest rate of replicate r
+    // in step k (FP32 bits, atomic max); step k reads slot (k + 2) % 3 for its
+    // size, the launch of step k clears slot (k + 1) % 3; time[r] = replicate
+    // r's simulated clock
+    uint32_t* lam;
+    double* time;
 };
 
 // The segment table is ordered by replicate width (R_pad 8, 16, 32); each

@@ -94,6 +94,49 @@ __device__ __forceinline__ PackTail pack_tail(const PackScen& S, int model, int 
     return t;
 }
 
+// Adaptive step (Section 5.2) of one replicate: the step's size from the
+// largest rate of the previous step (FP32, the single-realisation step's
+// operations), and the rate of an E or I replicate (evaluated directly: ages
+// leave the fixed-step sequence, so the probability tables do not apply)
+__device__ __forceinline__ float pack_dt_of(uint32_t lam_bits, float eps, float delta, float dt_max)
+{
+    return fminf(dt_max, __fdiv_rn(eps, __fadd_rn(__uint_as_float(lam_bits), delta)));
+}
+
+__device__ __noinline__ float pack_rate_ei(const ModelF& M, int x, float age)
+{
+    return hazard(x == kE ? M.lat : M.inf, age);
+}
+
+// pack_tail with the adaptive step of replicate r (segment g.lam != null):
+// its rate goes into the step's maximum, its size comes from the previous one
+__device__ __forceinline__ PackTail pack_tail_adaptive(const PackSeg& g, int64_t k, int r, int x, float age,
+                                                       uint32_t c, int i)
+{
+    const PackScen& S = g.scen[r];
+    const float lam = x == kS ? (c ? __fmul_rn(S.M.beta, (float)c) : 0.0f)
+                              : ((x == kE || x == kI) ? pack_rate_ei(S.M, x, age) : 0.0f);
+    if (lam > 0.0f)
+        atomicMax(g.lam + (k % 3) * g.R_pad + r, __float_as_uint(lam));
+    const float dt = pack_dt_of(__ldg(g.lam + ((k + 2) % 3) * g.R_pad + r), S.eps, S.delta, S.M.dt);
+    const float p = p_of_rate_dt(lam, dt);
+    bool fired = false;
+    if (p > 0.0f) {
+        const uint32_t orig = g.perm ? (uint32_t)__ldg(g.perm + i) : (uint32_t)i;
+        fired = uniform24(S.M.key0, S.M.key1, S.M.rep, (uint32_t)k, orig) < p;
+    }
+    PackTail t;
+    if (fired) {
+        t.x = (x == kS) ? (g.model == kSEIR ? kE : kI) : (x + 1);
+        t.age = 0.0f;
+    } else {
+        t.x = x;
+        t.age = (x == kE || x == kI) ? __fadd_rn(age, dt) : 0.0f;
+    }
+    t.fired = fired;
+    return t;
+}
+
 // per-replicate transitions of this step: [S->, E->I, I->R]
 __device__ __forceinline__ void add_deltas(const PackSeg& g, int64_t k, int r, uint32_t dS, uint32_t dE,
                                            uint32_t dI)
@@ -292,14 +335,31 @@ struct PackWarp {
     uint4 sc[kPackMaxR][3];
     const PackScen* sc_src;
     uint32_t share;
+    // adaptive segments: this step's size per replicate, and the warp's
+    // running maximum of each replicate's rates, added into lam_out (the
+    // segment's slot for this step) when the warp moves on
+    float dtk[kPackMaxR];
+    uint32_t lmx[kPackMaxR];
+    uint32_t* lam_out;
 };
+
+// the warp's running maxima into the segment's slot (every lane calls this)
+__device__ __forceinline__ void pack_flush_lmax(PackWarp& w)
+{
+    __syncwarp();
+    const int lane = threadIdx.x & 31;
+    if (w.lam_out && w.lmx[lane])
+        atomicMax(w.lam_out + lane, w.lmx[lane]);
+    __syncwarp();
+}
 
 // the warp's scenario-header cache holds segment g's (loaded when the warp
 // moves to another segment; every lane calls this)
-__device__ __forceinline__ void pack_headers(const PackSeg& g, PackWarp& w)
+__device__ __forceinline__ void pack_headers(const PackSeg& g, int64_t k, PackWarp& w)
 {
     if (w.sc_src == g.scen)
         return;
+    pack_flush_lmax(w);
     const int lane = threadIdx.x & 31;
     uint4 h1 = make_uint4(0u, 0u, 0u, 0u);
     if (lane < g.R_pad) {
@@ -307,8 +367,15 @@ __device__ __forceinline__ void pack_headers(const PackSeg& g, PackWarp& w)
         w.sc[lane][0] = __ldg(src);
         h1 = __ldg(src + 1);
         w.sc[lane][1] = h1;
-        w.sc[lane][2] = __ldg(src + 2);
+        const uint4 h2 = __ldg(src + 2);
+        w.sc[lane][2] = h2;
+        if (g.lam)
+            w.dtk[lane] = pack_dt_of(__ldg(g.lam + ((k + 2) % 3) * g.R_pad + lane), __uint_as_float(h2.z),
+                                     __uint_as_float(h2.w), __uint_as_float(h1.w));
     }
+    w.lmx[lane] = 0u;
+    if (lane == 0)
+        w.lam_out = g.lam ? g.lam + (k % 3) * g.R_pad : nullptr;
     const int lead = lane & ~3;
     const uint32_t k0 = __shfl_sync(kFullP, h1.x, lead), k1 = __shfl_sync(kFullP, h1.y, lead);
     const uint32_t c2 = __shfl_sync(kFullP, h1.z >> 2, lead);
@@ -420,7 +487,17 @@ __device__ __forceinline__ void pack_group(const PackSeg& g, int64_t k, int b, b
             const int i = __ffs(m) - 1;
             m &= m - 1u;
             const int q = quad * 4 + i, s_ = L * 8 + q;
-            const float p = pack_p_hdr(w, g.scen[b * 8 + q], b * 8 + q, w.xb[s_], w.age[s_], (uint32_t)w.cb[s_]);
+            float p;
+            if (g.lam) {
+                const int x = w.xb[s_];
+                const float lam = x == kS ? __fmul_rn(__uint_as_float(w.sc[b * 8 + q][2].x), (float)w.cb[s_])
+                                          : pack_rate_ei(g.scen[b * 8 + q].M, x, w.age[s_]);
+                if (lam > 0.0f)
+                    atomicMax(&w.lmx[b * 8 + q], __float_as_uint(lam));
+                p = p_of_rate_dt(lam, w.dtk[b * 8 + q]);
+            } else {
+                p = pack_p_hdr(w, g.scen[b * 8 + q], b * 8 + q, w.xb[s_], w.age[s_], (uint32_t)w.cb[s_]);
+            }
             const uint32_t sel = w.sc[b * 8 + q][1].z & 3u;
             const uint32_t word = sel == 0 ? ph.x : sel == 1 ? ph.y : sel == 2 ? ph.z : ph.w;
             w.fb[s_] = (float)(word >> 8) * 5.9604644775390625e-08f < p ? 0xffu : 0u;
@@ -442,7 +519,7 @@ __device__ __forceinline__ void pack_group(const PackSeg& g, int64_t k, int b, b
         AgeVec8<AgeT> ag;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            const float dtq = __uint_as_float(w.sc[b * 8 + q][1].w);
+            const float dtq = g.lam ? w.dtk[b * 8 + q] : __uint_as_float(w.sc[b * 8 + q][1].w);
             ag.v[q] = ((fb >> q) & 1u) ? 0.0f : (((eb >> q) & 1u) ? __fadd_rn(w.age[slot0 + q], dtq) : 0.0f);
         }
         ag.store(Ag);
@@ -545,7 +622,7 @@ __device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slic
     const bool ei0 = valid && (has_byte(xs[0], (uint32_t)kE) || has_byte(xs[0], (uint32_t)kI));
     if (ei0)
         ag0.load(Abase);
-    pack_headers(g, pw);
+    pack_headers(g, k, pw);
     uint64_t cnt[NB];
 #pragma unroll
     for (int b = 0; b < NB; ++b)
@@ -666,7 +743,7 @@ __device__ __forceinline__ void pack_hub_row(const PackSeg& g, int64_t k, int ro
     const PackScen& S = g.scen[mine ? lane : 0];
     PackTail t{x, 0.0f, false};
     if (mine)
-        t = pack_tail(S, g.model, x, age, c, g.perm, i, (uint32_t)k);
+        t = g.lam ? pack_tail_adaptive(g, k, lane, x, age, c, i) : pack_tail(S, g.model, x, age, c, g.perm, i, (uint32_t)k);
     if (mine) {
         if (t.x != x)
             g.X[off_state] = (uint8_t)t.x;
@@ -711,7 +788,7 @@ __device__ __forceinline__ void pack_hub_row_push(const PackSeg& g, int64_t k, i
     const PackScen& S = g.scen[mine ? lane : 0];
     PackTail t{x, 0.0f, false};
     if (mine)
-        t = pack_tail(S, g.model, x, age, c, g.perm, i, (uint32_t)k);
+        t = g.lam ? pack_tail_adaptive(g, k, lane, x, age, c, i) : pack_tail(S, g.model, x, age, c, g.perm, i, (uint32_t)k);
     if (mine) {
         if (t.x != x)
             g.X[off_state] = (uint8_t)t.x;
@@ -754,6 +831,14 @@ __device__ __forceinline__ void pack_integrate(const PackSeg& g, int64_t k)
         uint32_t* o = g.out + ((k - g.kmin) * g.R_pad + lane) * 4;
         o[0] = c0; o[1] = c1; o[2] = c2; o[3] = c3;
     }
+    if (g.lam) {
+        // the previous step's size (from the rates of the step before it)
+        // into the replicate's clock; that slot then takes step k + 1's rates
+        uint32_t* slot = g.lam + ((k + 1) % 3) * g.R_pad + lane;
+        const PackScen& S = g.scen[lane];
+        g.time[lane] += (double)pack_dt_of(*slot, S.eps, S.delta, S.M.dt);
+        *slot = 0u;
+    }
 }
 
 }  // namespace
@@ -776,8 +861,10 @@ __global__ void __launch_bounds__(kPackThreads, PackOcc<RP>::kMinBlocks) pack_st
     // per warp: the push events of one slice (node, entering mask, leaving mask)
     __shared__ uint32_t s_ev[kPackThreads / 32][3 * 32];
     PackWarp& pw = s_pw[threadIdx.x >> 5];
-    if ((threadIdx.x & 31) == 0)
+    if ((threadIdx.x & 31) == 0) {
         pw.sc_src = nullptr;
+        pw.lam_out = nullptr;
+    }
     uint32_t* wlist = s_ev[threadIdx.x >> 5];
     for (int m = threadIdx.x; m < 256; m += blockDim.x) {
         uint64_t v = 0;
@@ -838,6 +925,7 @@ __global__ void __launch_bounds__(kPackThreads, PackOcc<RP>::kMinBlocks) pack_st
             pack_slice<AgeT, RP, PUSH>(g, k, (int)(ic - __ldg(a.thr_pre + sc)), cur, lut, pw, wlist);
         cur = nxt;
     }
+    pack_flush_lmax(pw);
 }
 
 // initial packed state of a segment: replicates r < R start in S with the

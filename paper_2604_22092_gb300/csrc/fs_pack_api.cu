@@ -33,6 +33,11 @@ struct fs_ens {
     uint32_t* d_phc = nullptr;
     unsigned long long* d_phpd[2] = {nullptr, nullptr};
     fs::PackScen* d_scen = nullptr;
+    // adaptive step (every realisation has eps > 0): the rate ring and the
+    // per-replicate clocks
+    uint32_t* d_lam = nullptr;
+    double* d_time = nullptr;
+    std::vector<fs::PackScen> h_scen;
     float4* d_ptab = nullptr;
     float* d_ps = nullptr;
     unsigned long long* d_deltas = nullptr;
@@ -103,6 +108,8 @@ void free_ens(fs_ens* e)
     fs::dfree(e->d_deltas);
     fs::dfree(e->d_counts);
     fs::dfree(e->d_out);
+    fs::dfree(e->d_lam);
+    fs::dfree(e->d_time);
     if (e->stream)
         cudaStreamDestroy(e->stream);
     delete e;
@@ -166,6 +173,8 @@ fs::PackSeg segment_of(const Member& m)
     s.phpd[1] = e->d_phpd[1];
     s.out_ptr = g->d_out_ptr;
     s.out_col = g->d_out_col;
+    s.lam = e->d_lam;
+    s.time = e->d_time;
     return s;
 }
 
@@ -203,8 +212,8 @@ fs_status fs_ens_create(fs_graph* g, const fs_sim_params* params, int32_t n_real
             return fail(FS_EINVAL, "fs_ens_create: realisations must share model, age_dtype, index_state and flags");
     }
     for (int r = 0; r < n_real; ++r) {
-        if (params[r].eps > 0)
-            return fail(FS_EUNSUPPORTED, "fs_ens_create: packed ensembles run a fixed step (eps must be 0)");
+        if ((params[r].eps > 0) != (params[0].eps > 0))
+            return fail(FS_EINVAL, "fs_ens_create: every realisation takes the adaptive step (eps > 0) or none");
         if (params[r].shed_mode != FS_SHED_NONE)
             return fail(FS_EUNSUPPORTED,
                         "fs_ens_create: packed ensembles keep s = 1 (shed_mode must be FS_SHED_NONE)");
@@ -284,6 +293,8 @@ fs_status fs_ens_create(fs_graph* g, const fs_sim_params* params, int32_t n_real
         sc.dt = sc.M.dt;
         sc.beta = sc.M.beta;
         sc.inv_dt = sc.M.inv_dt;
+        sc.eps = (float)params[r].eps;
+        sc.delta = (float)(params[r].delta > 0 ? params[r].delta : 1e-12);
         C_TRY(fs::launch_build_ptables(sc.M, e->age_dtype, const_cast<float4*>(sc.ptab), const_cast<float*>(sc.ps),
                                        cs));
         scen[r] = sc;
@@ -291,6 +302,13 @@ fs_status fs_ens_create(fs_graph* g, const fs_sim_params* params, int32_t n_real
     for (int r = n_real; r < Rp; ++r)
         scen[r] = scen[0];                       // padding replicates never draw
     C_TRY(cudaMemcpyAsync(e->d_scen, scen.data(), sizeof(fs::PackScen) * Rp, cudaMemcpyHostToDevice, cs));
+    e->h_scen = scen;
+    if (params[0].eps > 0) {
+        C_TRY(dev_alloc(&e->d_lam, (size_t)3 * Rp, &e->bytes));
+        C_TRY(dev_alloc(&e->d_time, (size_t)Rp, &e->bytes));
+        C_TRY(cudaMemsetAsync(e->d_lam, 0, sizeof(uint32_t) * 3 * Rp, cs));
+        C_TRY(cudaMemsetAsync(e->d_time, 0, sizeof(double) * Rp, cs));
+    }
     if (n_index > 0) {
         C_TRY(dev_alloc(&d_idx, (size_t)n_index, nullptr));
         C_TRY(cudaMemcpyAsync(d_idx, index_nodes, sizeof(int32_t) * n_index, cudaMemcpyHostToDevice, cs));
@@ -369,6 +387,45 @@ fs_status fs_ens_get_state(fs_ens* e, int32_t r, uint8_t* state, void* age, int6
         E_CUDA(e, fetch(e->d_X, state, 1));
     if (age)
         E_CUDA(e, fetch(e->d_A, age, e->age_bytes));
+    return FS_OK;
+}
+
+fs_status fs_ens_time(fs_ens* e, double* elapsed, float* next_dt)
+{
+    if (!e)
+        return fail(FS_EINVAL, "fs_ens_time: NULL ensemble");
+    if (e->failed)
+        return fail(FS_ESTATE, "fs_ens_time: ensemble is in a failed state");
+    if (e->batch)
+        E_CUDA(e, cudaStreamSynchronize(e->batch->stream));
+    E_CUDA(e, cudaStreamSynchronize(e->stream));
+    const int Rp = e->R_pad;
+    std::vector<double> t((size_t)Rp, 0.0);
+    std::vector<uint32_t> lam((size_t)3 * Rp, 0u);
+    if (e->d_time) {
+        E_CUDA(e, cudaMemcpy(t.data(), e->d_time, sizeof(double) * Rp, cudaMemcpyDeviceToHost));
+        E_CUDA(e, cudaMemcpy(lam.data(), e->d_lam, sizeof(uint32_t) * 3 * Rp, cudaMemcpyDeviceToHost));
+    }
+    for (int r = 0; r < e->R; ++r) {
+        const fs::PackScen& S = e->h_scen[(size_t)r];
+        if (!e->d_time) {
+            // fixed step: every step has the same size
+            if (elapsed)
+                elapsed[r] = (double)e->steps_done * (double)S.M.dt;
+            if (next_dt)
+                next_dt[r] = S.M.dt;
+            continue;
+        }
+        if (elapsed)
+            elapsed[r] = t[(size_t)r];
+        if (next_dt) {
+            // the same FP32 operations as the step: min(dt, eps / (lambda* + delta))
+            float lp;
+            const uint32_t bits = lam[(size_t)((e->steps_done + 2) % 3) * Rp + r];
+            memcpy(&lp, &bits, sizeof(lp));
+            next_dt[r] = std::min(S.M.dt, S.eps / (lp + S.delta));
+        }
+    }
     return FS_OK;
 }
 

@@ -331,10 +331,14 @@ fs_status fs_server_submit(fs_server* s, fs_graph* g, const fs_sim_params* scena
             delete q;
             return fail(FS_EINVAL, "fs_server_submit: scenarios must share flags");
         }
-        if (p.eps > 0 || p.shed_mode != FS_SHED_NONE || (p.flags & FS_ACTIVE_LIST) || p.theta > 0) {
+        if (p.shed_mode != FS_SHED_NONE || (p.flags & FS_ACTIVE_LIST) || p.theta > 0) {
             delete q;
-            return fail(FS_EUNSUPPORTED, "fs_server_submit: served ensembles run a fixed step with s = 1 "
-                                         "(eps 0, FS_SHED_NONE)");
+            return fail(FS_EUNSUPPORTED, "fs_server_submit: served ensembles keep s = 1 (FS_SHED_NONE), no active "
+                                         "list, the renewal engine");
+        }
+        if (sc > 0 && (p.eps > 0) != (scenarios[0].eps > 0)) {
+            delete q;
+            return fail(FS_EINVAL, "fs_server_submit: every scenario takes the adaptive step (eps > 0) or none");
         }
         if (p.flags == FS_PRESSURE_PUSH && !fsapi::push_available(g)) {
             delete q;
