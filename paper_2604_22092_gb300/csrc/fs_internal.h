@@ -293,8 +293,9 @@ struct PackArgs {
     const PackSeg* seg;       // segment table
     const int64_t* thr_pre;   // [n_seg + 1] exclusive prefix of SELL work items
     const int64_t* hub_pre;   // [n_seg + 1] exclusive prefix of hub rows
-    const int32_t* cls;       // [7] rows [cls[2c+f], cls[2c+f+1]) have R_pad = 8 << c and pressure form f
-                              // (0 gather, 1 push) (device, updated between launches)
+    const int32_t* cls;       // [13] rows [cls[i], cls[i+1]) with i = (2c + f) * 2 + d have R_pad = 8 << c,
+                              // pressure form f (0 gather, 1 push) and step d (0 fixed, 1 adaptive)
+                              // (device, updated between launches)
     DevCtl* ctl;              // global step counter and error word
     int32_t j;                // step offset within the launch sequence
 };

@@ -355,11 +355,13 @@ __device__ __forceinline__ void pack_flush_lmax(PackWarp& w)
 
 // the warp's scenario-header cache holds segment g's (loaded when the warp
 // moves to another segment; every lane calls this)
+template <bool ADAPTIVE>
 __device__ __forceinline__ void pack_headers(const PackSeg& g, int64_t k, PackWarp& w)
 {
     if (w.sc_src == g.scen)
         return;
-    pack_flush_lmax(w);
+    if constexpr (ADAPTIVE)
+        pack_flush_lmax(w);
     const int lane = threadIdx.x & 31;
     uint4 h1 = make_uint4(0u, 0u, 0u, 0u);
     if (lane < g.R_pad) {
@@ -369,13 +371,15 @@ __device__ __forceinline__ void pack_headers(const PackSeg& g, int64_t k, PackWa
         w.sc[lane][1] = h1;
         const uint4 h2 = __ldg(src + 2);
         w.sc[lane][2] = h2;
-        if (g.lam)
+        if constexpr (ADAPTIVE)
             w.dtk[lane] = pack_dt_of(__ldg(g.lam + ((k + 2) % 3) * g.R_pad + lane), __uint_as_float(h2.z),
                                      __uint_as_float(h2.w), __uint_as_float(h1.w));
     }
-    w.lmx[lane] = 0u;
-    if (lane == 0)
-        w.lam_out = g.lam ? g.lam + (k % 3) * g.R_pad : nullptr;
+    if constexpr (ADAPTIVE) {
+        w.lmx[lane] = 0u;
+        if (lane == 0)
+            w.lam_out = g.lam + (k % 3) * g.R_pad;
+    }
     const int lead = lane & ~3;
     const uint32_t k0 = __shfl_sync(kFullP, h1.x, lead), k1 = __shfl_sync(kFullP, h1.y, lead);
     const uint32_t c2 = __shfl_sync(kFullP, h1.z >> 2, lead);
@@ -416,7 +420,7 @@ __device__ __forceinline__ float pack_p_hdr(const PackWarp& w, const PackScen& S
 // units shared by the warp's lanes (one Philox call serves the replicates of
 // a quad that share key and counter), then transitions, ages and the
 // per-replicate transition counts. Every lane calls this.
-template <typename AgeT>
+template <typename AgeT, bool ADAPTIVE>
 __device__ __forceinline__ void pack_group(const PackSeg& g, int64_t k, int b, bool valid, uint64_t xv, uint64_t cb,
                                            AgeT* __restrict__ Ag, uint8_t* __restrict__ Xg, PackWarp& w,
                                            uint32_t& newmask, uint32_t& oldmask, const AgeVec8<AgeT>* pre)
@@ -488,7 +492,7 @@ __device__ __forceinline__ void pack_group(const PackSeg& g, int64_t k, int b, b
             m &= m - 1u;
             const int q = quad * 4 + i, s_ = L * 8 + q;
             float p;
-            if (g.lam) {
+            if constexpr (ADAPTIVE) {
                 const int x = w.xb[s_];
                 const float lam = x == kS ? __fmul_rn(__uint_as_float(w.sc[b * 8 + q][2].x), (float)w.cb[s_])
                                           : pack_rate_ei(g.scen[b * 8 + q].M, x, w.age[s_]);
@@ -519,7 +523,7 @@ __device__ __forceinline__ void pack_group(const PackSeg& g, int64_t k, int b, b
         AgeVec8<AgeT> ag;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            const float dtq = g.lam ? w.dtk[b * 8 + q] : __uint_as_float(w.sc[b * 8 + q][1].w);
+            const float dtq = ADAPTIVE ? w.dtk[b * 8 + q] : __uint_as_float(w.sc[b * 8 + q][1].w);
             ag.v[q] = ((fb >> q) & 1u) ? 0.0f : (((eb >> q) & 1u) ? __fadd_rn(w.age[slot0 + q], dtq) : 0.0f);
         }
         ag.store(Ag);
@@ -581,7 +585,7 @@ __device__ __forceinline__ void slice_loads(const PackSeg& g, int slice, SliceLo
         L.xs[b] = valid ? xp[b] : 0x0303030303030303ull;
 }
 
-template <typename AgeT, int RP, bool PUSH>
+template <typename AgeT, int RP, bool PUSH, bool ADAPTIVE>
 __device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slice, const SliceLoads<RP>& L,
                                            const uint64_t* __restrict__ lut, PackWarp& pw,
                                            uint32_t* __restrict__ wlist)
@@ -622,7 +626,7 @@ __device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slic
     const bool ei0 = valid && (has_byte(xs[0], (uint32_t)kE) || has_byte(xs[0], (uint32_t)kI));
     if (ei0)
         ag0.load(Abase);
-    pack_headers(g, k, pw);
+    pack_headers<ADAPTIVE>(g, k, pw);
     uint64_t cnt[NB];
 #pragma unroll
     for (int b = 0; b < NB; ++b)
@@ -686,7 +690,7 @@ __device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slic
     for (int b = 0; b < NB; ++b) {
         if (b * 8 >= g.R)
             break;
-        pack_group<AgeT>(g, k, b, valid, xs[b], cnt[b], Abase + b * 8, Xb + b * 8, pw, newmask, oldmask,
+        pack_group<AgeT, ADAPTIVE>(g, k, b, valid, xs[b], cnt[b], Abase + b * 8, Xb + b * 8, pw, newmask, oldmask,
                          b == 0 && ei0 ? &ag0 : nullptr);
     }
     if constexpr (PUSH) {
@@ -699,7 +703,7 @@ __device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slic
 }
 
 // hub row: one warp, lane r < L is replicate r; 32 edges per window
-template <typename AgeT, int L>
+template <typename AgeT, int L, bool ADAPTIVE>
 __device__ __forceinline__ void pack_hub_row(const PackSeg& g, int64_t k, int row)
 {
     using MT = typename MaskOf<L>::T;
@@ -743,7 +747,7 @@ __device__ __forceinline__ void pack_hub_row(const PackSeg& g, int64_t k, int ro
     const PackScen& S = g.scen[mine ? lane : 0];
     PackTail t{x, 0.0f, false};
     if (mine)
-        t = g.lam ? pack_tail_adaptive(g, k, lane, x, age, c, i) : pack_tail(S, g.model, x, age, c, g.perm, i, (uint32_t)k);
+        t = ADAPTIVE ? pack_tail_adaptive(g, k, lane, x, age, c, i) : pack_tail(S, g.model, x, age, c, g.perm, i, (uint32_t)k);
     if (mine) {
         if (t.x != x)
             g.X[off_state] = (uint8_t)t.x;
@@ -760,7 +764,7 @@ __device__ __forceinline__ void pack_hub_row(const PackSeg& g, int64_t k, int ro
 // hub row, push form: lane r < L is replicate r; its count is folded from its
 // pending tallies, and the replicates that enter or leave I are pushed by the
 // whole warp along the node's transposed row
-template <typename AgeT, int L>
+template <typename AgeT, int L, bool ADAPTIVE>
 __device__ __forceinline__ void pack_hub_row_push(const PackSeg& g, int64_t k, int row)
 {
     const int lane = threadIdx.x & 31;
@@ -788,7 +792,7 @@ __device__ __forceinline__ void pack_hub_row_push(const PackSeg& g, int64_t k, i
     const PackScen& S = g.scen[mine ? lane : 0];
     PackTail t{x, 0.0f, false};
     if (mine)
-        t = g.lam ? pack_tail_adaptive(g, k, lane, x, age, c, i) : pack_tail(S, g.model, x, age, c, g.perm, i, (uint32_t)k);
+        t = ADAPTIVE ? pack_tail_adaptive(g, k, lane, x, age, c, i) : pack_tail(S, g.model, x, age, c, g.perm, i, (uint32_t)k);
     if (mine) {
         if (t.x != x)
             g.X[off_state] = (uint8_t)t.x;
@@ -850,7 +854,7 @@ __device__ __forceinline__ void pack_integrate(const PackSeg& g, int64_t k)
 #endif
 template <int RP> struct PackOcc { static constexpr int kMinBlocks = RP == 8 ? FS_PACK_MIN_BLOCKS8 : 5; };
 
-template <typename AgeT, int RP, bool PUSH>
+template <typename AgeT, int RP, bool PUSH, bool ADAPTIVE>
 __global__ void __launch_bounds__(kPackThreads, PackOcc<RP>::kMinBlocks) pack_step_kernel(const __grid_constant__ PackArgs a)
 {
     // byte r of lut[m] is bit r of m: spreads an 8-replicate mask into byte counters
@@ -873,7 +877,7 @@ __global__ void __launch_bounds__(kPackThreads, PackOcc<RP>::kMinBlocks) pack_st
         lut[m] = v;
     }
     __syncthreads();
-    constexpr int c = (RP == 8 ? 0 : RP == 16 ? 1 : 2) * 2 + (PUSH ? 1 : 0);
+    constexpr int c = ((RP == 8 ? 0 : RP == 16 ? 1 : 2) * 2 + (PUSH ? 1 : 0)) * 2 + (ADAPTIVE ? 1 : 0);
     const int64_t G = a.ctl->step + a.j;
     const int s0 = a.cls[c], s1 = a.cls[c + 1];
     const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -895,9 +899,9 @@ __global__ void __launch_bounds__(kPackThreads, PackOcc<RP>::kMinBlocks) pack_st
         if (k < g.kmin || k >= g.kend)
             continue;
         if constexpr (PUSH)
-            pack_hub_row_push<AgeT, RP>(g, k, (int)(it - __ldg(a.hub_pre + s)));
+            pack_hub_row_push<AgeT, RP, ADAPTIVE>(g, k, (int)(it - __ldg(a.hub_pre + s)));
         else
-            pack_hub_row<AgeT, RP>(g, k, (int)(it - __ldg(a.hub_pre + s)));
+            pack_hub_row<AgeT, RP, ADAPTIVE>(g, k, (int)(it - __ldg(a.hub_pre + s)));
     }
     // one item per 32-node slice; the next item's independent loads are
     // issued before the current one is processed
@@ -922,10 +926,11 @@ __global__ void __launch_bounds__(kPackThreads, PackOcc<RP>::kMinBlocks) pack_st
         const PackSeg& g = a.seg[sc];
         const int64_t k = G - g.join;
         if (k >= g.kmin && k < g.kend)
-            pack_slice<AgeT, RP, PUSH>(g, k, (int)(ic - __ldg(a.thr_pre + sc)), cur, lut, pw, wlist);
+            pack_slice<AgeT, RP, PUSH, ADAPTIVE>(g, k, (int)(ic - __ldg(a.thr_pre + sc)), cur, lut, pw, wlist);
         cur = nxt;
     }
-    pack_flush_lmax(pw);
+    if constexpr (ADAPTIVE)
+        pack_flush_lmax(pw);
 }
 
 // initial packed state of a segment: replicates r < R start in S with the
@@ -1012,26 +1017,33 @@ cudaError_t launch_pack_advance(DevCtl* ctl, int K, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <typename AgeT, bool PUSH>
+template <typename AgeT, bool PUSH, bool ADAPTIVE>
 static cudaError_t launch_pack_t(const PackArgs& a, int cls, int grid, cudaStream_t s)
 {
     switch (cls) {
-    case 0: pack_step_kernel<AgeT, 8, PUSH><<<grid, kPackThreads, 0, s>>>(a); break;
-    case 1: pack_step_kernel<AgeT, 16, PUSH><<<grid, kPackThreads, 0, s>>>(a); break;
-    default: pack_step_kernel<AgeT, 32, PUSH><<<grid, kPackThreads, 0, s>>>(a); break;
+    case 0: pack_step_kernel<AgeT, 8, PUSH, ADAPTIVE><<<grid, kPackThreads, 0, s>>>(a); break;
+    case 1: pack_step_kernel<AgeT, 16, PUSH, ADAPTIVE><<<grid, kPackThreads, 0, s>>>(a); break;
+    default: pack_step_kernel<AgeT, 32, PUSH, ADAPTIVE><<<grid, kPackThreads, 0, s>>>(a); break;
     }
     g_launch_count += 1;
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack_step(const PackArgs& a, int cls, bool push, int age_dtype, int grid, cudaStream_t s)
+template <typename AgeT>
+static cudaError_t launch_pack_a(const PackArgs& a, int cls, bool push, bool adaptive, int grid, cudaStream_t s)
+{
+    if (push)
+        return adaptive ? launch_pack_t<AgeT, true, true>(a, cls, grid, s) : launch_pack_t<AgeT, true, false>(a, cls, grid, s);
+    return adaptive ? launch_pack_t<AgeT, false, true>(a, cls, grid, s) : launch_pack_t<AgeT, false, false>(a, cls, grid, s);
+}
+
+cudaError_t launch_pack_step(const PackArgs& a, int cls, bool push, bool adaptive, int age_dtype, int grid,
+                             cudaStream_t s)
 {
     switch (age_dtype) {
-    case kAgeF16: return push ? launch_pack_t<__half, true>(a, cls, grid, s) : launch_pack_t<__half, false>(a, cls, grid, s);
-    case kAgeBF16:
-        return push ? launch_pack_t<__nv_bfloat16, true>(a, cls, grid, s)
-                    : launch_pack_t<__nv_bfloat16, false>(a, cls, grid, s);
-    default: return push ? launch_pack_t<float, true>(a, cls, grid, s) : launch_pack_t<float, false>(a, cls, grid, s);
+    case kAgeF16: return launch_pack_a<__half>(a, cls, push, adaptive, grid, s);
+    case kAgeBF16: return launch_pack_a<__nv_bfloat16>(a, cls, push, adaptive, grid, s);
+    default: return launch_pack_a<float>(a, cls, push, adaptive, grid, s);
     }
 }
 
@@ -1054,9 +1066,9 @@ cudaError_t launch_pack_init(uint8_t* X, int n, int R_pad, int R, const int32_t*
 int pack_grid(int num_sms, int cls)
 {
     int occ = 0;
-    cudaError_t e = cls == 0   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pack_step_kernel<float, 8, false>, kPackThreads, 0)
-                    : cls == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pack_step_kernel<float, 16, false>, kPackThreads, 0)
-                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pack_step_kernel<float, 32, false>, kPackThreads, 0);
+    cudaError_t e = cls == 0   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pack_step_kernel<float, 8, false, false>, kPackThreads, 0)
+                    : cls == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pack_step_kernel<float, 16, false, false>, kPackThreads, 0)
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pack_step_kernel<float, 32, false, false>, kPackThreads, 0);
     if (e != cudaSuccess || occ < 1)
         occ = 4;
     return num_sms * occ;

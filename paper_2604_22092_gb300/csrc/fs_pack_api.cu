@@ -69,7 +69,7 @@ struct fs_batch {
     fs::PackSeg* d_seg = nullptr;
     int64_t* d_thr = nullptr;
     int64_t* d_hub = nullptr;
-    int32_t* d_cls = nullptr;           // [4] class boundaries of the table (see PackArgs)
+    int32_t* d_cls = nullptr;           // [13] class boundaries of the table (see PackArgs)
     fs::PackSeg* h_seg = nullptr;       // pinned staging of the table
     int64_t* h_thr = nullptr;
     int64_t* h_hub = nullptr;
@@ -81,7 +81,8 @@ struct fs_batch {
     cudaGraphExec_t gexec = nullptr;
     int gK = 0;
     int g_classes = 0;                  // classes launched by the captured graph (bit c)
-    int classes = 0;                    // classes present in the table (bit 2c+f: R_pad = 8 << c, form f = push)
+    int classes = 0;                    // classes present in the table (bit (2c+f)*2+d: R_pad = 8 << c, form f = push,
+                                        // step d = adaptive)
     int grid[3] = {0, 0, 0};
     bool failed = false;
 };
@@ -468,14 +469,14 @@ fs_status fs_batch_create(int32_t age_dtype, int32_t max_members, void* stream, 
     if (e == cudaSuccess) e = dev_alloc(&b->d_seg, (size_t)max_members, nullptr);
     if (e == cudaSuccess) e = dev_alloc(&b->d_thr, (size_t)max_members + 1, nullptr);
     if (e == cudaSuccess) e = dev_alloc(&b->d_hub, (size_t)max_members + 1, nullptr);
-    if (e == cudaSuccess) e = dev_alloc(&b->d_cls, 7, nullptr);
+    if (e == cudaSuccess) e = dev_alloc(&b->d_cls, 13, nullptr);
     if (e == cudaSuccess) e = dev_alloc(&b->d_ctl, 1, nullptr);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_seg, sizeof(fs::PackSeg) * max_members);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_thr, sizeof(int64_t) * (max_members + 1));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_hub, sizeof(int64_t) * (max_members + 1));
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_cls, sizeof(int32_t) * 7);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_cls, sizeof(int32_t) * 13);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ctl, 0, sizeof(fs::DevCtl), b->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_cls, 0, sizeof(int32_t) * 4, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_cls, 0, sizeof(int32_t) * 13, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_thr, 0, sizeof(int64_t), b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_hub, 0, sizeof(int64_t), b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -529,10 +530,10 @@ static fs_status upload_table(fs_batch* b)
     b->h_hub[0] = 0;
     b->classes = 0;
     int q = 0;
-    for (int c = 0; c < 6; ++c) {                     // rows ordered by replicate width, then form
+    for (int c = 0; c < 12; ++c) {                    // rows ordered by replicate width, form, step
         b->h_cls[c] = q;
         for (const Member& m : b->members) {
-            if (width_class(m.e->R_pad) * 2 + (m.e->push ? 1 : 0) != c)
+            if ((width_class(m.e->R_pad) * 2 + (m.e->push ? 1 : 0)) * 2 + (m.e->d_lam ? 1 : 0) != c)
                 continue;
             b->h_seg[q] = segment_of(m);
             const fs_graph* g = m.e->g;
@@ -542,13 +543,13 @@ static fs_status upload_table(fs_batch* b)
             ++q;
         }
     }
-    b->h_cls[6] = q;
+    b->h_cls[12] = q;
     const int ns = q;
     if (ns > 0)
         E_CUDA(b, cudaMemcpyAsync(b->d_seg, b->h_seg, sizeof(fs::PackSeg) * ns, cudaMemcpyHostToDevice, b->stream));
     E_CUDA(b, cudaMemcpyAsync(b->d_thr, b->h_thr, sizeof(int64_t) * (ns + 1), cudaMemcpyHostToDevice, b->stream));
     E_CUDA(b, cudaMemcpyAsync(b->d_hub, b->h_hub, sizeof(int64_t) * (ns + 1), cudaMemcpyHostToDevice, b->stream));
-    E_CUDA(b, cudaMemcpyAsync(b->d_cls, b->h_cls, sizeof(int32_t) * 7, cudaMemcpyHostToDevice, b->stream));
+    E_CUDA(b, cudaMemcpyAsync(b->d_cls, b->h_cls, sizeof(int32_t) * 13, cudaMemcpyHostToDevice, b->stream));
     b->dirty = false;
     return FS_OK;
 }
@@ -565,13 +566,14 @@ static fs::PackArgs pack_args(const fs_batch* b, int j)
     return a;
 }
 
-// one step of every (width, form) class present in the table
+// one step of every (width, form, step) class present in the table
 static cudaError_t launch_classes(const fs_batch* b, int j, int classes)
 {
     cudaError_t e = cudaSuccess;
-    for (int c = 0; c < 6 && e == cudaSuccess; ++c)
+    for (int c = 0; c < 12 && e == cudaSuccess; ++c)
         if (classes & (1 << c))
-            e = fs::launch_pack_step(pack_args(b, j), c / 2, (c & 1) != 0, b->age_dtype, b->grid[c / 2], b->stream);
+            e = fs::launch_pack_step(pack_args(b, j), c / 4, ((c >> 1) & 1) != 0, (c & 1) != 0, b->age_dtype,
+                                     b->grid[c / 4], b->stream);
     return e;
 }
 

@@ -231,10 +231,11 @@ def test_adaptive_argument_errors(torch_cuda):
         with pytest.raises(fs.FsError) as e:
             fs.fs_sim_init(gh, bad, [1, 2])
         assert e.value.status == 1
-    # packed ensembles run a fixed step
+    # a packed ensemble takes the adaptive step in every realisation or in none
     with pytest.raises(fs.FsError) as e:
-        fs.fs_ens_create(gh, [sir(0.05, seed=k) for k in range(4)], [1, 2])
-    assert e.value.status == 7
+        fs.fs_ens_create(gh, [sir(0.05 if k else 0.0, seed=k) for k in range(4)], [1, 2])
+    assert e.value.status == 1
+    fs.fs_ens_destroy(fs.fs_ens_create(gh, [sir(0.05, seed=k) for k in range(4)], [1, 2]))
     # a fixed-step sim reports dt and the FP64 sum of its steps
     s = fs.fs_sim_init(gh, sir(0.0), [1, 2])
     fs.fs_sim_run(s, 7, want_counts=False)

@@ -144,3 +144,34 @@ def test_served_adaptive_request_equals_alone(ba):
                 np.testing.assert_array_equal(c[:, j * 3 + r, :], ref, err_msg=f"scenario {j} replicate {r}")
     finally:
         fs.fs_server_destroy(srv)
+
+
+def test_batch_mixes_fixed_and_adaptive_ensembles(ba):
+    """One segment table holding fixed-step and adaptive ensembles of both
+    pressure forms: each kind runs its own kernel instance, and every
+    realisation still equals its run alone."""
+    g, gh, idx = ba
+    steps = 200
+    kinds = [(fs.FS_PRESSURE_GATHER, 0.0), (fs.FS_PRESSURE_PUSH, 0.0),
+             (fs.FS_PRESSURE_GATHER, 0.03), (fs.FS_PRESSURE_PUSH, 0.03)]
+    sets = [[seir(0.2 + 0.05 * r, seed=300 + j, replicate=r, eps=eps, pressure=pr) for r in range(6)]
+            for j, (pr, eps) in enumerate(kinds)]
+    ens = [fs.fs_ens_create(gh, ps, idx) for ps in sets]
+    b = fs.fs_batch_create(fs.FS_AGE_F32, len(ens))
+    try:
+        outs = [np.zeros((steps + 1, 6, 4), dtype=np.uint32) for _ in ens]
+        for e, o in zip(ens, outs):
+            fs.fs_batch_add(b, e, steps, o)
+        fs.fs_batch_run(b, steps + 1, 50)
+        for j, ps in enumerate(sets):
+            for r, p in enumerate(ps):
+                s = fs.fs_sim_init(gh, p, idx)
+                ref = fs.fs_sim_run(s, steps)
+                fs.fs_sim_destroy(s)
+                np.testing.assert_array_equal(outs[j][:, r, :], ref, err_msg=f"kind {kinds[j]} realisation {r}")
+        t, _ = fs.fs_ens_time(ens[3], 6)
+        assert (t < steps * 0.1 - 1e-9).any()
+    finally:
+        fs.fs_batch_destroy(b)
+        for e in ens:
+            fs.fs_ens_destroy(e)
