@@ -1093,6 +1093,37 @@ def shedding_bench(fs, torch, n: int, sim_steps: int, graph_steps: int, reps: in
         base = row["constant_gather"]["value"]
         for label in ("shed_constant_exact", "shed_hazard_IR", "shed_density_lognormal"):
             row[label]["slowdown_vs_constant_gather_pct"] = round((base / row[label]["value"] - 1) * 100, 2)
+        # the s = h_IR profile in a packed ensemble of 8 replicates against the
+        # same 8 realisations run alone (host wall clock around the synchronous
+        # run calls; ensemble and sims created outside the timed region)
+        prms = [fs.sim_params(fs.FS_SEIR, inf, 0.25, 0.1, 3, latent=lat, replicate=r,
+                              pressure=fs.FS_PRESSURE_GATHER, shed_mode=fs.FS_SHED_HAZARD, shedding=inf)
+                for r in range(8)]
+        t_pack, t_alone = [], []
+        for r in range(reps + 1):
+            e = fs.fs_ens_create(gh, prms, idx)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fs.fs_ens_run(e, sim_steps, 8, K, want_counts=False)
+            t1 = time.perf_counter()
+            fs.fs_ens_destroy(e)
+            alone = 0.0
+            for p_ in prms:
+                sh = fs.fs_sim_init(gh, p_, idx)
+                torch.cuda.synchronize()
+                t2 = time.perf_counter()
+                fs.fs_sim_run(sh, sim_steps, graph_steps=K)
+                alone += time.perf_counter() - t2
+                fs.fs_sim_destroy(sh)
+            if r:
+                t_pack.append(t1 - t0)
+                t_alone.append(alone)
+        tp, ta = float(np.median(t_pack)), float(np.median(t_alone))
+        row["packed_shed_hazard_IR_x8"] = {
+            "value": round(8 * g.n * sim_steps / tp / 1e9, 3), "unit": UNIT, "seconds": round(tp, 4),
+            "alone_value": round(8 * g.n * sim_steps / ta / 1e9, 3), "alone_seconds": round(ta, 4),
+            "speedup": round(ta / tp, 2),
+            "timed": "8 replicates packed (fs_ens_run) vs each run alone (fs_sim_run), host wall clock"}
         res["graphs"][gname] = row
         fs.fs_graph_destroy(gh)
     return res

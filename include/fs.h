@@ -127,8 +127,13 @@ typedef struct {
  * in-neighbours, in a fixed order (row order in the one-lane-per-node class;
  * segmented warp sums folded by warp, then by chunk, in the merge class), so
  * a run is reproducible bit for bit. Gather form only (the adaptive step,
- * eps > 0, combines with it): FS_PRESSURE_PUSH, packed ensembles, batches,
- * the server and fs_step_noalloc need FS_SHED_NONE (FS_EUNSUPPORTED). */
+ * eps > 0, combines with it): FS_PRESSURE_PUSH and fs_step_noalloc need
+ * FS_SHED_NONE (FS_EUNSUPPORTED). Packed ensembles, batches and the server
+ * take it in the gather form when every realisation of the ensemble (or
+ * request) has a profile: each replicate keeps its own infectivities and
+ * sums them in the same order as alone (row order; in the merge class the
+ * windows, warp ranges and chunks of the single-realisation kernel), so its
+ * trajectory is the one it has alone. */
 typedef enum { FS_SHED_NONE = 0, FS_SHED_HAZARD = 1, FS_SHED_DENSITY = 2 } fs_shed_mode;
 
 /* One realisation (Section 3; Algorithm 3 with a fixed step dt). */
@@ -379,9 +384,11 @@ typedef struct fs_batch fs_batch;
  * the index nodes (host int32[n_index], distinct original ids) are the same
  * for every realisation. Either every realisation takes the adaptive step
  * (eps > 0, Section 5.2; each replicate then has its own step size and
- * clock: its trajectory is the one it has alone through fs_sim_*) or none.
- * Errors: FS_EINVAL, FS_ENOMEM, FS_ECUDA, FS_EUNSUPPORTED (a shedding
- * profile, FS_ACTIVE_LIST, theta > 0). */
+ * clock: its trajectory is the one it has alone through fs_sim_*) or none;
+ * likewise every realisation has a shedding profile (Section 5.3, each its
+ * own law, gather form) or none.
+ * Errors: FS_EINVAL, FS_ENOMEM, FS_ECUDA, FS_EUNSUPPORTED (FS_ACTIVE_LIST,
+ * theta > 0, a shedding profile with FS_PRESSURE_PUSH). */
 fs_status fs_ens_create(fs_graph* g, const fs_sim_params* params, int32_t n_real, const int32_t* index_nodes,
                         int64_t n_index, fs_ens** out);
 /* Runs the ensemble alone for `steps` steps (a batch of one).
@@ -455,8 +462,12 @@ typedef struct {
 typedef struct fs_server fs_server;
 
 fs_status fs_server_create(const fs_server_cfg* cfg, fs_server** out);
-/* Validates and queues a request (host arrays are copied). FS_EINVAL for bad
- * arguments, FS_ENOMEM if the request alone exceeds the budget. */
+/* Validates and queues a request (host arrays are copied). Scenarios share
+ * model, index_state and flags; every scenario takes the adaptive step or
+ * none, and every scenario has a shedding profile (gather form) or none.
+ * FS_EINVAL for bad arguments, FS_ENOMEM if the request alone exceeds the
+ * budget, FS_EUNSUPPORTED for FS_ACTIVE_LIST, theta > 0, or a shedding
+ * profile with FS_PRESSURE_PUSH. */
 fs_status fs_server_submit(fs_server* s, fs_graph* g, const fs_sim_params* scenarios, int32_t n_scen,
                            int32_t replicates, const int32_t* index_nodes, int64_t n_index, int64_t steps,
                            uint64_t* request_id);

@@ -233,6 +233,7 @@ namespace fs {
 // through a device segment table.
 // ---------------------------------------------------------------------------
 constexpr int kPackMaxR = 32;
+constexpr int kPackClasses = 18;        // 3 replicate widths x 3 pressure forms x 2 step rules
 constexpr int kPackThreads = 128;       // threads per block of the packed step
 
 struct __align__(16) PackScen {   // one realisation of a segment
@@ -244,6 +245,12 @@ struct __align__(16) PackScen {   // one realisation of a segment
     float beta, inv_dt;     // copies of M.beta, M.inv_dt
     float eps, delta;       // adaptive step (eps > 0): dt_k = min(dt, eps / (lambda*_{k-1} + delta))
     ModelF M;               // all parameters (direct evaluation when a table misses)
+    // shedding profile (Section 5.3, Eq. 8; segments with shed != 0):
+    // rtab[kPTableN] memoises beta s(age) over the fixed-step age sequence
+    const float4* rtab;
+    LawF shed;
+    int32_t shed_mode;
+    int32_t pad_;
 };
 
 struct PackSeg {            // one row of the segment table
@@ -285,6 +292,14 @@ struct PackSeg {            // one row of the segment table
     // r's simulated clock
     uint32_t* lam;
     double* time;
+    // shedding profile (gather form; shed != 0): rho[par][i * R_pad + r] =
+    // beta s(tau) of replicate r of node i while it is I (storage type of the
+    // ages; read only where the infectious mask has the replicate's bit), by
+    // local step parity; S replicates sum the rho of their infectious
+    // in-neighbours in FP32
+    void* rho[2];
+    int32_t shed;
+    int32_t pad3_;
 };
 
 // The segment table is ordered by replicate width (R_pad 8, 16, 32); each
@@ -293,8 +308,9 @@ struct PackArgs {
     const PackSeg* seg;       // segment table
     const int64_t* thr_pre;   // [n_seg + 1] exclusive prefix of SELL work items
     const int64_t* hub_pre;   // [n_seg + 1] exclusive prefix of hub rows
-    const int32_t* cls;       // [13] rows [cls[i], cls[i+1]) with i = (2c + f) * 2 + d have R_pad = 8 << c,
-                              // pressure form f (0 gather, 1 push) and step d (0 fixed, 1 adaptive)
+    const int32_t* cls;       // [kPackClasses + 1] rows [cls[i], cls[i+1]) with i = (3c + f) * 2 + d have
+                              // R_pad = 8 << c, pressure form f (0 gather, 1 push, 2 gather with a
+                              // shedding profile) and step d (0 fixed, 1 adaptive)
                               // (device, updated between launches)
     DevCtl* ctl;              // global step counter and error word
     int32_t j;                // step offset within the launch sequence

@@ -61,14 +61,16 @@ cudaError_t launch_transpose(const int64_t* sell_off, const int32_t* sell_col, c
 
 // fs_pack.cu
 // one step of the segments of replicate-width class cls (R_pad = 8 << cls) in
-// one pressure form (push or gather)
-cudaError_t launch_pack_step(const PackArgs& a, int cls, bool push, bool adaptive, int age_dtype, int grid,
+// one pressure form (0 gather, 1 push, 2 gather with a shedding profile)
+cudaError_t launch_pack_step(const PackArgs& a, int cls, int form, bool adaptive, int age_dtype, int grid,
                              cudaStream_t s);
 cudaError_t launch_pack_init(uint8_t* X, int n, int R_pad, int R, const int32_t* idx, int64_t n_idx,
                              const int32_t* inv, int state, void* mask, cudaStream_t s);
 int pack_grid(int num_sms, int cls);   // persistent grid of the packed step kernel of class cls
 // initial counts of a push-form segment from its state (counts zeroed before)
 cudaError_t launch_pack_push_init(const PackSeg& g, cudaStream_t s);
+// rho[par] of the replicates that start in I (shedding profile)
+cudaError_t launch_pack_rho_init(const PackSeg& g, int age_dtype, uint32_t par, cudaStream_t s);
 cudaError_t launch_pack_advance(DevCtl* ctl, int K, cudaStream_t s);   // global step += K
 
 // fs_ingest.cu

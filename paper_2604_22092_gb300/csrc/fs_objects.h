@@ -126,6 +126,7 @@ inline void scratch_free(void* p, cudaStream_t)
 }
 fs_status check_params(const fs_sim_params* p);
 fs::ModelF to_model(const fs_sim_params& p);
+fs::LawF to_lawf(const fs_law& L);
 // the push form of the pressure: available when the thread class's in-degrees
 // fit u8 counts; the transposed CSR of a graph, built once (thread-safe)
 bool push_available(const fs_graph* g);

@@ -73,10 +73,9 @@ struct PackTail {
 
 // the original id is read only when a uniform is drawn (p > 0 implies a
 // valid node: padding and absorbed lanes have p = 0)
-__device__ __forceinline__ PackTail pack_tail(const PackScen& S, int model, int x, float age, uint32_t c,
-                                              const int32_t* perm, int i, uint32_t step)
+__device__ __forceinline__ PackTail pack_tail_p(const PackScen& S, int model, int x, float age, float p,
+                                                const int32_t* perm, int i, uint32_t step)
 {
-    const float p = pack_p(S, x, age, c);
     bool fired = false;
     if (p > 0.0f) {
         const uint32_t orig = perm ? (uint32_t)__ldg(perm + i) : (uint32_t)i;
@@ -92,6 +91,12 @@ __device__ __forceinline__ PackTail pack_tail(const PackScen& S, int model, int 
     }
     t.fired = fired;
     return t;
+}
+
+__device__ __forceinline__ PackTail pack_tail(const PackScen& S, int model, int x, float age, uint32_t c,
+                                              const int32_t* perm, int i, uint32_t step)
+{
+    return pack_tail_p(S, model, x, age, pack_p(S, x, age, c), perm, i, step);
 }
 
 // Adaptive step (Section 5.2) of one replicate: the step's size from the
@@ -110,12 +115,12 @@ __device__ __noinline__ float pack_rate_ei(const ModelF& M, int x, float age)
 
 // pack_tail with the adaptive step of replicate r (segment g.lam != null):
 // its rate goes into the step's maximum, its size comes from the previous one
-__device__ __forceinline__ PackTail pack_tail_adaptive(const PackSeg& g, int64_t k, int r, int x, float age,
-                                                       uint32_t c, int i)
+// (s_rate: the rate of an S replicate)
+__device__ __forceinline__ PackTail pack_tail_adaptive_rate(const PackSeg& g, int64_t k, int r, int x, float age,
+                                                            float s_rate, int i)
 {
     const PackScen& S = g.scen[r];
-    const float lam = x == kS ? (c ? __fmul_rn(S.M.beta, (float)c) : 0.0f)
-                              : ((x == kE || x == kI) ? pack_rate_ei(S.M, x, age) : 0.0f);
+    const float lam = x == kS ? s_rate : ((x == kE || x == kI) ? pack_rate_ei(S.M, x, age) : 0.0f);
     if (lam > 0.0f)
         atomicMax(g.lam + (k % 3) * g.R_pad + r, __float_as_uint(lam));
     const float dt = pack_dt_of(__ldg(g.lam + ((k + 2) % 3) * g.R_pad + r), S.eps, S.delta, S.M.dt);
@@ -135,6 +140,39 @@ __device__ __forceinline__ PackTail pack_tail_adaptive(const PackSeg& g, int64_t
     }
     t.fired = fired;
     return t;
+}
+
+__device__ __forceinline__ PackTail pack_tail_adaptive(const PackSeg& g, int64_t k, int r, int x, float age,
+                                                       uint32_t c, int i)
+{
+    return pack_tail_adaptive_rate(g, k, r, x, age, c ? __fmul_rn(g.scen[r].M.beta, (float)c) : 0.0f, i);
+}
+
+// beta s(tau) of an I replicate of new age `age` (FP32, before storage
+// rounding) under its scenario's shedding profile (Section 5.3, Eq. 8): the
+// age as stored, looked up in the scenario's memoised table when it lies on
+// the fixed-step sequence, else evaluated (the single-realisation step's
+// operations, so the stored bits are the same)
+__device__ __noinline__ float pack_shed_direct(const PackScen& S, float tau)
+{
+    return shed_value(S.shed, S.shed_mode, S.M.beta, tau);
+}
+
+template <typename AgeT>
+__device__ __forceinline__ float pack_rho_of(const PackScen& S, float age)
+{
+    const float a = AgeIO<AgeT>::load(AgeIO<AgeT>::store(age));
+    const int n = __float2int_rn(__fmul_rn(a, S.M.inv_dt));
+    if ((unsigned)n < (unsigned)kPTableN) {
+        const float4* row = S.rtab + n;
+        const float2 e = __ldg(reinterpret_cast<const float2*>(row));
+        if (e.x == a)
+            return e.y;
+        const float r1 = ptab_slot1(row, a);
+        if (r1 >= 0.0f)
+            return r1;
+    }
+    return pack_shed_direct(S, a);
 }
 
 // per-replicate transitions of this step: [S->, E->I, I->R]
@@ -420,17 +458,31 @@ __device__ __forceinline__ float pack_p_hdr(const PackWarp& w, const PackScen& S
 // units shared by the warp's lanes (one Philox call serves the replicates of
 // a quad that share key and counter), then transitions, ages and the
 // per-replicate transition counts. Every lane calls this.
-template <typename AgeT, bool ADAPTIVE>
+template <typename AgeT, bool ADAPTIVE, bool SHED>
 __device__ __forceinline__ void pack_group(const PackSeg& g, int64_t k, int b, bool valid, uint64_t xv, uint64_t cb,
                                            AgeT* __restrict__ Ag, uint8_t* __restrict__ Xg, PackWarp& w,
-                                           uint32_t& newmask, uint32_t& oldmask, const AgeVec8<AgeT>* pre)
+                                           uint32_t& newmask, uint32_t& oldmask, const AgeVec8<AgeT>* pre,
+                                           const float* __restrict__ rsw, AgeT* __restrict__ Rg)
 {
     const int lane = threadIdx.x & 31;
     const int slot0 = lane * 8;
     __syncwarp();                  // the previous group has finished with w
     const uint64_t sM = eq_bytes(xv, kS), eM = eq_bytes(xv, kE), iM = eq_bytes(xv, kI);
     const uint64_t eiM = eM | iM;
-    uint32_t need = bytes_to_bits(eiM) | bytes_to_bits(sM & ~eq_bytes(cb, 0u));
+    uint32_t need;
+    if constexpr (SHED) {
+        // S replicates under pressure: a positive FP32 sum of infectivities
+        // (rsw[r * 32 + lane] = replicate r's sum, this lane's node)
+        const uint32_t sb = bytes_to_bits(sM);
+        uint32_t sp = 0u;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (((sb >> q) & 1u) && rsw[(b * 8 + q) * 32 + lane] > 0.0f)
+                sp |= 1u << q;
+        need = bytes_to_bits(eiM) | sp;
+    } else {
+        need = bytes_to_bits(eiM) | bytes_to_bits(sM & ~eq_bytes(cb, 0u));
+    }
     if (!valid)
         need = 0u;
     // quads of the group's replicates that share key and Philox counter
@@ -494,11 +546,17 @@ __device__ __forceinline__ void pack_group(const PackSeg& g, int64_t k, int b, b
             float p;
             if constexpr (ADAPTIVE) {
                 const int x = w.xb[s_];
-                const float lam = x == kS ? __fmul_rn(__uint_as_float(w.sc[b * 8 + q][2].x), (float)w.cb[s_])
-                                          : pack_rate_ei(g.scen[b * 8 + q].M, x, w.age[s_]);
+                float lam;
+                if (x == kS)
+                    lam = SHED ? rsw[(b * 8 + q) * 32 + L]
+                               : __fmul_rn(__uint_as_float(w.sc[b * 8 + q][2].x), (float)w.cb[s_]);
+                else
+                    lam = pack_rate_ei(g.scen[b * 8 + q].M, x, w.age[s_]);
                 if (lam > 0.0f)
                     atomicMax(&w.lmx[b * 8 + q], __float_as_uint(lam));
                 p = p_of_rate_dt(lam, w.dtk[b * 8 + q]);
+            } else if (SHED && w.xb[s_] == kS) {
+                p = p_of_rate_dt(rsw[(b * 8 + q) * 32 + L], __uint_as_float(w.sc[b * 8 + q][1].w));
             } else {
                 p = pack_p_hdr(w, g.scen[b * 8 + q], b * 8 + q, w.xb[s_], w.age[s_], (uint32_t)w.cb[s_]);
             }
@@ -530,6 +588,25 @@ __device__ __forceinline__ void pack_group(const PackSeg& g, int64_t k, int b, b
     }
     newmask |= bytes_to_bits(eq_bytes(xn, kI)) << (b * 8);
     oldmask |= bytes_to_bits(iM) << (b * 8);
+    if constexpr (SHED) {
+        // the next step's infectivity of the replicates now in I, from their
+        // new ages as stored (the others are never read: their mask bit is 0)
+        const uint32_t inb = valid ? bytes_to_bits(eq_bytes(xn, kI)) : 0u;
+        if (inb) {
+            const uint32_t fb = bytes_to_bits(F);
+            AgeVec8<AgeT> rv;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                rv.v[q] = 0.0f;
+                if ((inb >> q) & 1u) {
+                    const float dtq = ADAPTIVE ? w.dtk[b * 8 + q] : __uint_as_float(w.sc[b * 8 + q][1].w);
+                    const float na = ((fb >> q) & 1u) ? 0.0f : __fadd_rn(w.age[slot0 + q], dtq);
+                    rv.v[q] = pack_rho_of<AgeT>(g.scen[b * 8 + q], na);
+                }
+            }
+            rv.store(Rg);
+        }
+    }
     // per-replicate transitions of this group, summed over the warp: the
     // fired masks (0xff bytes) become 0/1 bytes, and one warp sum per word
     // adds four replicates' counts at once (at most 32 per byte, no carry)
@@ -585,10 +662,10 @@ __device__ __forceinline__ void slice_loads(const PackSeg& g, int slice, SliceLo
         L.xs[b] = valid ? xp[b] : 0x0303030303030303ull;
 }
 
-template <typename AgeT, int RP, bool PUSH, bool ADAPTIVE>
+template <typename AgeT, int RP, bool PUSH, bool ADAPTIVE, bool SHED>
 __device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slice, const SliceLoads<RP>& L,
                                            const uint64_t* __restrict__ lut, PackWarp& pw,
-                                           uint32_t* __restrict__ wlist)
+                                           uint32_t* __restrict__ wlist, float* __restrict__ rsw)
 {
     using MT = typename MaskOf<RP>::T;
     constexpr int NB = RP / 8;
@@ -666,7 +743,37 @@ __device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slic
         if (!__any_sync(kFullP, busy))
             return;
     }
-    if (!PUSH && anyS) {
+    if (SHED && anyS) {
+        // Eq. 3 with the infectivities of Eq. 8: each S replicate r sums, in
+        // FP32 and in row order, the stored rho of the in-neighbours whose
+        // replicate r is infectious (the single-realisation step's order)
+#pragma unroll
+        for (int r = 0; r < RP; ++r)
+            rsw[r * 32 + lane] = 0.0f;
+        uint32_t sbits = 0u;
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+            sbits |= bytes_to_bits(s_bytes(xs[b])) << (8 * b);
+        const AgeT* __restrict__ rho = static_cast<const AgeT*>(g.rho[k & 1]);
+        const int w = (int)((off_end - off) >> 5);
+        const int32_t* __restrict__ p = g.sell_col + off + lane;
+        for (int t0 = 0; t0 < w; t0 += B) {
+            int32_t jj[B];
+#pragma unroll
+            for (int u = 0; u < B; ++u)
+                jj[u] = (t0 + u < w) ? __ldg(p + 32 * (t0 + u)) : g.sentinel;
+#pragma unroll
+            for (int u = 0; u < B; ++u) {
+                uint32_t hit = (uint32_t)__ldg(mk + jj[u]) & sbits;   // the sentinel's mask is always 0
+                while (hit) {
+                    const int r = __ffs(hit) - 1;
+                    hit &= hit - 1u;
+                    rsw[r * 32 + lane] = __fadd_rn(rsw[r * 32 + lane],
+                                                   AgeIO<AgeT>::load(rho[(int64_t)jj[u] * RP + r]));
+                }
+            }
+        }
+    } else if (!PUSH && anyS) {
         const int w = (int)((off_end - off) >> 5);
         const int32_t* __restrict__ p = g.sell_col + off + lane;
         for (int t0 = 0; t0 < w; t0 += B) {
@@ -690,8 +797,10 @@ __device__ __forceinline__ void pack_slice(const PackSeg& g, int64_t k, int slic
     for (int b = 0; b < NB; ++b) {
         if (b * 8 >= g.R)
             break;
-        pack_group<AgeT, ADAPTIVE>(g, k, b, valid, xs[b], cnt[b], Abase + b * 8, Xb + b * 8, pw, newmask, oldmask,
-                         b == 0 && ei0 ? &ag0 : nullptr);
+        pack_group<AgeT, ADAPTIVE, SHED>(g, k, b, valid, xs[b], cnt[b], Abase + b * 8, Xb + b * 8, pw, newmask,
+                                         oldmask, b == 0 && ei0 ? &ag0 : nullptr, rsw,
+                                         SHED ? static_cast<AgeT*>(g.rho[(k + 1) & 1]) + (int64_t)i * RP + b * 8
+                                              : nullptr);
     }
     if constexpr (PUSH) {
         const uint32_t en = valid ? newmask & ~oldmask : 0u, lv = valid ? oldmask & ~newmask : 0u;
@@ -753,6 +862,102 @@ __device__ __forceinline__ void pack_hub_row(const PackSeg& g, int64_t k, int ro
             g.X[off_state] = (uint8_t)t.x;
         if (t.fired || x == kE || x == kI)
             A[off_state] = AgeIO<AgeT>::store(t.age);
+    }
+    const uint32_t b = __ballot_sync(kFullP, mine && t.x == kI);
+    if (lane == 0)
+        mkn[i] = (MT)b;
+    if (mine)
+        add_deltas(g, k, lane, t.fired && x == kS, t.fired && x == kE, t.fired && x == kI);
+}
+
+// hub row with a shedding profile: lane r < L is replicate r. Each S
+// replicate's pressure is the FP32 sum of the stored rho of its infectious
+// in-neighbours, summed in the order of the single-realisation merge kernel,
+// so that a packed replicate keeps the bits it has alone: the row's edges go
+// in 32-edge windows aligned to the merge CSR (a segmented scan of fixed tree
+// shape inside each window), windows fold in order within each
+// kMergeEdgesPerWarp-edge warp range, warp ranges within each kMergeEPB-edge
+// chunk, and chunks in order.
+template <typename AgeT, int L, bool ADAPTIVE>
+__device__ __forceinline__ void pack_hub_row_shed(const PackSeg& g, int64_t k, int row)
+{
+    using MT = typename MaskOf<L>::T;
+    const int lane = threadIdx.x & 31;
+    const int i = g.n_thr + row;
+    const bool mine = lane < L;
+    const int64_t off_state = (int64_t)i * L + lane;
+    AgeT* __restrict__ A = static_cast<AgeT*>(g.A);
+    const MT* __restrict__ mk = static_cast<const MT*>(g.mask[k & 1]);
+    MT* __restrict__ mkn = static_cast<MT*>(g.mask[(k + 1) & 1]);
+    const AgeT* __restrict__ rho = static_cast<const AgeT*>(g.rho[k & 1]);
+    const int x = mine ? (int)g.X[off_state] : kR;
+    float age = 0.0f;
+    if (x == kE || x == kI)
+        age = AgeIO<AgeT>::load(A[off_state]);
+    const uint32_t sm = __ballot_sync(kFullP, x == kS);
+    float lam = 0.0f;                       // lane r: replicate r's pressure
+    if (sm) {
+        const int64_t e0 = __ldg(g.m_ptr + row), e1 = __ldg(g.m_ptr + row + 1);
+        float accW = 0.0f, accC = 0.0f;
+        int64_t curW = -1, curC = -1;
+        bool started = false;
+        for (int64_t wb = e0 & ~(int64_t)31; wb < e1; wb += 32) {
+            const int64_t ws = wb / kMergeEdgesPerWarp, wc = wb / kMergeEPB;
+            if (ws != curW) {
+                if (curW >= 0)
+                    accC = __fadd_rn(accC, accW);
+                accW = 0.0f;
+                curW = ws;
+                if (wc != curC) {
+                    if (curC >= 0) {
+                        lam = started ? __fadd_rn(lam, accC) : accC;
+                        started = true;
+                    }
+                    accC = 0.0f;
+                    curC = wc;
+                }
+            }
+            const int l0 = (int)max((int64_t)0, e0 - wb), h0 = (int)min((int64_t)32, e1 - wb);
+            const int64_t e = wb + lane;
+            const bool in = lane >= l0 && lane < h0;
+            const int32_t col = in ? __ldg(g.m_col + e) : g.sentinel;
+            const uint32_t m = (uint32_t)__ldg(mk + col);      // the sentinel's mask is always 0
+            uint32_t todo = sm;
+            while (todo) {
+                const int rr = __ffs(todo) - 1;
+                todo &= todo - 1u;
+                float v = ((m >> rr) & 1u) ? AgeIO<AgeT>::load(rho[(int64_t)col * L + rr]) : 0.0f;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const float t = __shfl_up_sync(kFullP, v, d);
+                    if (lane - d >= l0)
+                        v = __fadd_rn(v, t);
+                }
+                const float seg = __shfl_sync(kFullP, v, h0 - 1);
+                if (lane == rr)
+                    accW = __fadd_rn(accW, seg);
+            }
+        }
+        accC = __fadd_rn(accC, accW);
+        lam = started ? __fadd_rn(lam, accC) : accC;
+    }
+    const PackScen& S = g.scen[mine ? lane : 0];
+    PackTail t{x, 0.0f, false};
+    if (mine) {
+        if constexpr (ADAPTIVE) {
+            t = pack_tail_adaptive_rate(g, k, lane, x, age, x == kS ? lam : 0.0f, i);
+        } else {
+            const float p = x == kS ? p_of_rate(S.M, lam) : pack_p(S, x, age, 0u);
+            t = pack_tail_p(S, g.model, x, age, p, g.perm, i, (uint32_t)k);
+        }
+    }
+    if (mine) {
+        if (t.x != x)
+            g.X[off_state] = (uint8_t)t.x;
+        if (t.fired || x == kE || x == kI)
+            A[off_state] = AgeIO<AgeT>::store(t.age);
+        if (t.x == kI)
+            static_cast<AgeT*>(g.rho[(k + 1) & 1])[off_state] = AgeIO<AgeT>::store(pack_rho_of<AgeT>(S, t.age));
     }
     const uint32_t b = __ballot_sync(kFullP, mine && t.x == kI);
     if (lane == 0)
@@ -854,9 +1059,14 @@ __device__ __forceinline__ void pack_integrate(const PackSeg& g, int64_t k)
 #endif
 template <int RP> struct PackOcc { static constexpr int kMinBlocks = RP == 8 ? FS_PACK_MIN_BLOCKS8 : 5; };
 
-template <typename AgeT, int RP, bool PUSH, bool ADAPTIVE>
+template <typename AgeT, int RP, int FORM, bool ADAPTIVE>
 __global__ void __launch_bounds__(kPackThreads, PackOcc<RP>::kMinBlocks) pack_step_kernel(const __grid_constant__ PackArgs a)
 {
+    // pressure form: 0 gather, 1 push, 2 gather with a shedding profile
+    constexpr bool PUSH = FORM == 1, SHED = FORM == 2;
+    // per warp, with a shedding profile: the FP32 pressure of every (replicate,
+    // node) of its slice, [RP][32]
+    __shared__ float s_rs[SHED ? (kPackThreads / 32) * RP * 32 : 1];
     // byte r of lut[m] is bit r of m: spreads an 8-replicate mask into byte counters
     __shared__ uint64_t lut[256];
     // per warp: one 8-replicate group of its slice (states, counts, ages,
@@ -870,6 +1080,7 @@ __global__ void __launch_bounds__(kPackThreads, PackOcc<RP>::kMinBlocks) pack_st
         pw.lam_out = nullptr;
     }
     uint32_t* wlist = s_ev[threadIdx.x >> 5];
+    float* rsw = SHED ? s_rs + (threadIdx.x >> 5) * RP * 32 : nullptr;
     for (int m = threadIdx.x; m < 256; m += blockDim.x) {
         uint64_t v = 0;
         for (int r = 0; r < 8; ++r)
@@ -877,7 +1088,7 @@ __global__ void __launch_bounds__(kPackThreads, PackOcc<RP>::kMinBlocks) pack_st
         lut[m] = v;
     }
     __syncthreads();
-    constexpr int c = ((RP == 8 ? 0 : RP == 16 ? 1 : 2) * 2 + (PUSH ? 1 : 0)) * 2 + (ADAPTIVE ? 1 : 0);
+    constexpr int c = ((RP == 8 ? 0 : RP == 16 ? 1 : 2) * 3 + FORM) * 2 + (ADAPTIVE ? 1 : 0);
     const int64_t G = a.ctl->step + a.j;
     const int s0 = a.cls[c], s1 = a.cls[c + 1];
     const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -900,6 +1111,8 @@ __global__ void __launch_bounds__(kPackThreads, PackOcc<RP>::kMinBlocks) pack_st
             continue;
         if constexpr (PUSH)
             pack_hub_row_push<AgeT, RP, ADAPTIVE>(g, k, (int)(it - __ldg(a.hub_pre + s)));
+        else if constexpr (SHED)
+            pack_hub_row_shed<AgeT, RP, ADAPTIVE>(g, k, (int)(it - __ldg(a.hub_pre + s)));
         else
             pack_hub_row<AgeT, RP, ADAPTIVE>(g, k, (int)(it - __ldg(a.hub_pre + s)));
     }
@@ -926,7 +1139,8 @@ __global__ void __launch_bounds__(kPackThreads, PackOcc<RP>::kMinBlocks) pack_st
         const PackSeg& g = a.seg[sc];
         const int64_t k = G - g.join;
         if (k >= g.kmin && k < g.kend)
-            pack_slice<AgeT, RP, PUSH, ADAPTIVE>(g, k, (int)(ic - __ldg(a.thr_pre + sc)), cur, lut, pw, wlist);
+            pack_slice<AgeT, RP, PUSH, ADAPTIVE, SHED>(g, k, (int)(ic - __ldg(a.thr_pre + sc)), cur, lut, pw, wlist,
+                                                       rsw);
         cur = nxt;
     }
     if constexpr (ADAPTIVE)
@@ -1017,34 +1231,68 @@ cudaError_t launch_pack_advance(DevCtl* ctl, int K, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <typename AgeT, bool PUSH, bool ADAPTIVE>
+template <typename AgeT, int FORM, bool ADAPTIVE>
 static cudaError_t launch_pack_t(const PackArgs& a, int cls, int grid, cudaStream_t s)
 {
     switch (cls) {
-    case 0: pack_step_kernel<AgeT, 8, PUSH, ADAPTIVE><<<grid, kPackThreads, 0, s>>>(a); break;
-    case 1: pack_step_kernel<AgeT, 16, PUSH, ADAPTIVE><<<grid, kPackThreads, 0, s>>>(a); break;
-    default: pack_step_kernel<AgeT, 32, PUSH, ADAPTIVE><<<grid, kPackThreads, 0, s>>>(a); break;
+    case 0: pack_step_kernel<AgeT, 8, FORM, ADAPTIVE><<<grid, kPackThreads, 0, s>>>(a); break;
+    case 1: pack_step_kernel<AgeT, 16, FORM, ADAPTIVE><<<grid, kPackThreads, 0, s>>>(a); break;
+    default: pack_step_kernel<AgeT, 32, FORM, ADAPTIVE><<<grid, kPackThreads, 0, s>>>(a); break;
     }
     g_launch_count += 1;
     return cudaGetLastError();
 }
 
-template <typename AgeT>
-static cudaError_t launch_pack_a(const PackArgs& a, int cls, bool push, bool adaptive, int grid, cudaStream_t s)
+template <typename AgeT, int FORM>
+static cudaError_t launch_pack_f(const PackArgs& a, int cls, bool adaptive, int grid, cudaStream_t s)
 {
-    if (push)
-        return adaptive ? launch_pack_t<AgeT, true, true>(a, cls, grid, s) : launch_pack_t<AgeT, true, false>(a, cls, grid, s);
-    return adaptive ? launch_pack_t<AgeT, false, true>(a, cls, grid, s) : launch_pack_t<AgeT, false, false>(a, cls, grid, s);
+    return adaptive ? launch_pack_t<AgeT, FORM, true>(a, cls, grid, s) : launch_pack_t<AgeT, FORM, false>(a, cls, grid, s);
 }
 
-cudaError_t launch_pack_step(const PackArgs& a, int cls, bool push, bool adaptive, int age_dtype, int grid,
+template <typename AgeT>
+static cudaError_t launch_pack_a(const PackArgs& a, int cls, int form, bool adaptive, int grid, cudaStream_t s)
+{
+    switch (form) {
+    case 1: return launch_pack_f<AgeT, 1>(a, cls, adaptive, grid, s);
+    case 2: return launch_pack_f<AgeT, 2>(a, cls, adaptive, grid, s);
+    default: return launch_pack_f<AgeT, 0>(a, cls, adaptive, grid, s);
+    }
+}
+
+cudaError_t launch_pack_step(const PackArgs& a, int cls, int form, bool adaptive, int age_dtype, int grid,
                              cudaStream_t s)
 {
     switch (age_dtype) {
-    case kAgeF16: return launch_pack_a<__half>(a, cls, push, adaptive, grid, s);
-    case kAgeBF16: return launch_pack_a<__nv_bfloat16>(a, cls, push, adaptive, grid, s);
-    default: return launch_pack_a<float>(a, cls, push, adaptive, grid, s);
+    case kAgeF16: return launch_pack_a<__half>(a, cls, form, adaptive, grid, s);
+    case kAgeBF16: return launch_pack_a<__nv_bfloat16>(a, cls, form, adaptive, grid, s);
+    default: return launch_pack_a<float>(a, cls, form, adaptive, grid, s);
     }
+}
+
+// initial infectivity of a segment with a shedding profile: replicates that
+// start in I (index nodes with index_state I) get beta s(0) in rho[par]
+template <typename AgeT>
+__global__ void pack_rho_init_kernel(PackSeg g, uint32_t par)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)g.n * g.R_pad)
+        return;
+    const int r = (int)(t % g.R_pad);
+    if (r < g.R && g.X[t] == kI)
+        static_cast<AgeT*>(g.rho[par])[t] = AgeIO<AgeT>::store(pack_rho_of<AgeT>(g.scen[r], 0.0f));
+}
+
+cudaError_t launch_pack_rho_init(const PackSeg& g, int age_dtype, uint32_t par, cudaStream_t s)
+{
+    const int64_t total = (int64_t)g.n * g.R_pad;
+    const unsigned blocks = (unsigned)((total + 255) / 256);
+    switch (age_dtype) {
+    case kAgeF16: pack_rho_init_kernel<__half><<<blocks, 256, 0, s>>>(g, par); break;
+    case kAgeBF16: pack_rho_init_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(g, par); break;
+    default: pack_rho_init_kernel<float><<<blocks, 256, 0, s>>>(g, par); break;
+    }
+    g_launch_count += 1;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pack_init(uint8_t* X, int n, int R_pad, int R, const int32_t* idx, int64_t n_idx,
@@ -1066,9 +1314,9 @@ cudaError_t launch_pack_init(uint8_t* X, int n, int R_pad, int R, const int32_t*
 int pack_grid(int num_sms, int cls)
 {
     int occ = 0;
-    cudaError_t e = cls == 0   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pack_step_kernel<float, 8, false, false>, kPackThreads, 0)
-                    : cls == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pack_step_kernel<float, 16, false, false>, kPackThreads, 0)
-                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pack_step_kernel<float, 32, false, false>, kPackThreads, 0);
+    cudaError_t e = cls == 0   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pack_step_kernel<float, 8, 0, false>, kPackThreads, 0)
+                    : cls == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pack_step_kernel<float, 16, 0, false>, kPackThreads, 0)
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pack_step_kernel<float, 32, 0, false>, kPackThreads, 0);
     if (e != cudaSuccess || occ < 1)
         occ = 4;
     return num_sms * occ;

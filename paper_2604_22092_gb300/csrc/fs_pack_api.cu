@@ -37,6 +37,12 @@ struct fs_ens {
     // per-replicate clocks
     uint32_t* d_lam = nullptr;
     double* d_time = nullptr;
+    // shedding profile (every realisation has one, gather form): the
+    // infectivity of each (node, replicate) by local step parity and each
+    // scenario's memoised beta s(age) table
+    bool shed = false;
+    void* d_rho[2] = {nullptr, nullptr};
+    float4* d_rtab = nullptr;
     std::vector<fs::PackScen> h_scen;
     float4* d_ptab = nullptr;
     float* d_ps = nullptr;
@@ -69,7 +75,7 @@ struct fs_batch {
     fs::PackSeg* d_seg = nullptr;
     int64_t* d_thr = nullptr;
     int64_t* d_hub = nullptr;
-    int32_t* d_cls = nullptr;           // [13] class boundaries of the table (see PackArgs)
+    int32_t* d_cls = nullptr;           // [kPackClasses + 1] class boundaries of the table (see PackArgs)
     fs::PackSeg* h_seg = nullptr;       // pinned staging of the table
     int64_t* h_thr = nullptr;
     int64_t* h_hub = nullptr;
@@ -81,8 +87,8 @@ struct fs_batch {
     cudaGraphExec_t gexec = nullptr;
     int gK = 0;
     int g_classes = 0;                  // classes launched by the captured graph (bit c)
-    int classes = 0;                    // classes present in the table (bit (2c+f)*2+d: R_pad = 8 << c, form f = push,
-                                        // step d = adaptive)
+    int classes = 0;                    // classes present in the table (bit (3c+f)*2+d: R_pad = 8 << c, form f
+                                        // (0 gather, 1 push, 2 gather with shedding), step d = adaptive)
     int grid[3] = {0, 0, 0};
     bool failed = false;
 };
@@ -111,6 +117,9 @@ void free_ens(fs_ens* e)
     fs::dfree(e->d_out);
     fs::dfree(e->d_lam);
     fs::dfree(e->d_time);
+    fs::dfree(e->d_rho[0]);
+    fs::dfree(e->d_rho[1]);
+    fs::dfree(e->d_rtab);
     if (e->stream)
         cudaStreamDestroy(e->stream);
     delete e;
@@ -176,6 +185,9 @@ fs::PackSeg segment_of(const Member& m)
     s.out_col = g->d_out_col;
     s.lam = e->d_lam;
     s.time = e->d_time;
+    s.shed = e->shed ? 1 : 0;
+    s.rho[0] = e->d_rho[0];
+    s.rho[1] = e->d_rho[1];
     return s;
 }
 
@@ -215,14 +227,15 @@ fs_status fs_ens_create(fs_graph* g, const fs_sim_params* params, int32_t n_real
     for (int r = 0; r < n_real; ++r) {
         if ((params[r].eps > 0) != (params[0].eps > 0))
             return fail(FS_EINVAL, "fs_ens_create: every realisation takes the adaptive step (eps > 0) or none");
-        if (params[r].shed_mode != FS_SHED_NONE)
-            return fail(FS_EUNSUPPORTED,
-                        "fs_ens_create: packed ensembles keep s = 1 (shed_mode must be FS_SHED_NONE)");
+        if ((params[r].shed_mode != FS_SHED_NONE) != (params[0].shed_mode != FS_SHED_NONE))
+            return fail(FS_EINVAL, "fs_ens_create: every realisation has a shedding profile or none");
         if (params[r].flags & FS_ACTIVE_LIST)
             return fail(FS_EUNSUPPORTED, "fs_ens_create: FS_ACTIVE_LIST is for single realisations");
         if (params[r].theta > 0)
             return fail(FS_EUNSUPPORTED, "fs_ens_create: the Markovian engine is for single realisations");
     }
+    if (params[0].shed_mode != FS_SHED_NONE && params[0].flags == FS_PRESSURE_PUSH)
+        return fail(FS_EUNSUPPORTED, "fs_ens_create: a shedding profile needs the gather form of the pressure");
     if (params[0].flags == FS_PRESSURE_PUSH && !fsapi::push_available(g))
         return fail(FS_EUNSUPPORTED, "fs_ens_create: FS_PRESSURE_PUSH needs in-degrees <= %d in the thread class",
                     fs::kMaxThreadDeg);
@@ -249,6 +262,7 @@ fs_status fs_ens_create(fs_graph* g, const fs_sim_params* params, int32_t n_real
     // packed ensembles default to the gather: it reads each column once for
     // all replicates, while pushes are paid per replicate (measured slower)
     e->push = params[0].flags == FS_PRESSURE_PUSH;
+    e->shed = params[0].shed_mode != FS_SHED_NONE;
     const int64_t n = g->n;
     const int Rp = e->R_pad;
     int32_t* d_idx = nullptr;
@@ -282,6 +296,14 @@ fs_status fs_ens_create(fs_graph* g, const fs_sim_params* params, int32_t n_real
     C_TRY(cudaMemsetAsync(e->d_A, 0, (size_t)n * Rp * e->age_bytes, cs));
     C_TRY(cudaMemsetAsync(e->d_deltas, 0, sizeof(unsigned long long) * 2 * Rp * 3, cs));
     C_TRY(cudaMemsetAsync(e->d_ptab, 0xff, sizeof(float4) * n_real * 2 * fs::kPTableN, cs));
+    if (e->shed) {
+        for (int q = 0; q < 2; ++q) {
+            C_TRY(fs::dmalloc(&e->d_rho[q], (size_t)n * Rp * e->age_bytes));
+            e->bytes += (int64_t)n * Rp * e->age_bytes;
+        }
+        C_TRY(dev_alloc(&e->d_rtab, (size_t)n_real * fs::kPTableN, &e->bytes));
+        C_TRY(cudaMemsetAsync(e->d_rtab, 0xff, sizeof(float4) * n_real * fs::kPTableN, cs));
+    }
     std::vector<fs::PackScen> scen(Rp);
     for (int r = 0; r < n_real; ++r) {
         fs::PackScen sc{};
@@ -296,8 +318,13 @@ fs_status fs_ens_create(fs_graph* g, const fs_sim_params* params, int32_t n_real
         sc.inv_dt = sc.M.inv_dt;
         sc.eps = (float)params[r].eps;
         sc.delta = (float)(params[r].delta > 0 ? params[r].delta : 1e-12);
+        if (e->shed) {
+            sc.rtab = e->d_rtab + (size_t)r * fs::kPTableN;
+            sc.shed = fsapi::to_lawf(params[r].shedding);
+            sc.shed_mode = params[r].shed_mode;
+        }
         C_TRY(fs::launch_build_ptables(sc.M, e->age_dtype, const_cast<float4*>(sc.ptab), const_cast<float*>(sc.ps),
-                                       cs));
+                                       cs, const_cast<float4*>(sc.rtab), sc.shed, sc.shed_mode));
         scen[r] = sc;
     }
     for (int r = n_real; r < Rp; ++r)
@@ -331,6 +358,10 @@ fs_status fs_ens_create(fs_graph* g, const fs_sim_params* params, int32_t n_real
         }
         Member m0{e, 0, 0, nullptr};
         C_TRY(fs::launch_pack_push_init(segment_of(m0), cs));
+    }
+    if (e->shed && n_index > 0 && params[0].index_state == FS_I) {
+        Member m0{e, 0, 0, nullptr};
+        C_TRY(fs::launch_pack_rho_init(segment_of(m0), e->age_dtype, 0u, cs));
     }
     std::vector<uint32_t> cnt((size_t)Rp * 4, 0u);
     for (int r = 0; r < Rp; ++r) {
@@ -469,14 +500,14 @@ fs_status fs_batch_create(int32_t age_dtype, int32_t max_members, void* stream, 
     if (e == cudaSuccess) e = dev_alloc(&b->d_seg, (size_t)max_members, nullptr);
     if (e == cudaSuccess) e = dev_alloc(&b->d_thr, (size_t)max_members + 1, nullptr);
     if (e == cudaSuccess) e = dev_alloc(&b->d_hub, (size_t)max_members + 1, nullptr);
-    if (e == cudaSuccess) e = dev_alloc(&b->d_cls, 13, nullptr);
+    if (e == cudaSuccess) e = dev_alloc(&b->d_cls, fs::kPackClasses + 1, nullptr);
     if (e == cudaSuccess) e = dev_alloc(&b->d_ctl, 1, nullptr);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_seg, sizeof(fs::PackSeg) * max_members);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_thr, sizeof(int64_t) * (max_members + 1));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_hub, sizeof(int64_t) * (max_members + 1));
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_cls, sizeof(int32_t) * 13);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_cls, sizeof(int32_t) * (fs::kPackClasses + 1));
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ctl, 0, sizeof(fs::DevCtl), b->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_cls, 0, sizeof(int32_t) * 13, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_cls, 0, sizeof(int32_t) * (fs::kPackClasses + 1), b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_thr, 0, sizeof(int64_t), b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_hub, 0, sizeof(int64_t), b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -530,10 +561,11 @@ static fs_status upload_table(fs_batch* b)
     b->h_hub[0] = 0;
     b->classes = 0;
     int q = 0;
-    for (int c = 0; c < 12; ++c) {                    // rows ordered by replicate width, form, step
+    for (int c = 0; c < fs::kPackClasses; ++c) {      // rows ordered by replicate width, form, step
         b->h_cls[c] = q;
         for (const Member& m : b->members) {
-            if ((width_class(m.e->R_pad) * 2 + (m.e->push ? 1 : 0)) * 2 + (m.e->d_lam ? 1 : 0) != c)
+            const int form = m.e->push ? 1 : m.e->shed ? 2 : 0;
+            if ((width_class(m.e->R_pad) * 3 + form) * 2 + (m.e->d_lam ? 1 : 0) != c)
                 continue;
             b->h_seg[q] = segment_of(m);
             const fs_graph* g = m.e->g;
@@ -543,13 +575,14 @@ static fs_status upload_table(fs_batch* b)
             ++q;
         }
     }
-    b->h_cls[12] = q;
+    b->h_cls[fs::kPackClasses] = q;
     const int ns = q;
     if (ns > 0)
         E_CUDA(b, cudaMemcpyAsync(b->d_seg, b->h_seg, sizeof(fs::PackSeg) * ns, cudaMemcpyHostToDevice, b->stream));
     E_CUDA(b, cudaMemcpyAsync(b->d_thr, b->h_thr, sizeof(int64_t) * (ns + 1), cudaMemcpyHostToDevice, b->stream));
     E_CUDA(b, cudaMemcpyAsync(b->d_hub, b->h_hub, sizeof(int64_t) * (ns + 1), cudaMemcpyHostToDevice, b->stream));
-    E_CUDA(b, cudaMemcpyAsync(b->d_cls, b->h_cls, sizeof(int32_t) * 13, cudaMemcpyHostToDevice, b->stream));
+    E_CUDA(b, cudaMemcpyAsync(b->d_cls, b->h_cls, sizeof(int32_t) * (fs::kPackClasses + 1), cudaMemcpyHostToDevice,
+                              b->stream));
     b->dirty = false;
     return FS_OK;
 }
@@ -570,10 +603,10 @@ static fs::PackArgs pack_args(const fs_batch* b, int j)
 static cudaError_t launch_classes(const fs_batch* b, int j, int classes)
 {
     cudaError_t e = cudaSuccess;
-    for (int c = 0; c < 12 && e == cudaSuccess; ++c)
+    for (int c = 0; c < fs::kPackClasses && e == cudaSuccess; ++c)
         if (classes & (1 << c))
-            e = fs::launch_pack_step(pack_args(b, j), c / 4, ((c >> 1) & 1) != 0, (c & 1) != 0, b->age_dtype,
-                                     b->grid[c / 4], b->stream);
+            e = fs::launch_pack_step(pack_args(b, j), c / 6, (c / 2) % 3, (c & 1) != 0, b->age_dtype, b->grid[c / 6],
+                                     b->stream);
     return e;
 }
 

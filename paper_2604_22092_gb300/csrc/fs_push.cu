@@ -78,6 +78,19 @@ __device__ __forceinline__ int next_state(const StepArgs& a, int x, bool fired)
 // eight ages of storage type AgeT as FP32 values
 template <typename AgeT> struct AgeVec8;
 template <> struct AgeVec8<float> {
+    // the 32 bytes of eight ages as two 16-byte words (loaded ahead of use)
+    static __device__ __forceinline__ void raw(const float* p, uint4& r0, uint4& r1)
+    {
+        r0 = *reinterpret_cast<const uint4*>(p);
+        r1 = *reinterpret_cast<const uint4*>(p + 4);
+    }
+    static __device__ __forceinline__ void from_raw(uint4 r0, uint4 r1, float (&f)[8])
+    {
+        f[0] = __uint_as_float(r0.x); f[1] = __uint_as_float(r0.y);
+        f[2] = __uint_as_float(r0.z); f[3] = __uint_as_float(r0.w);
+        f[4] = __uint_as_float(r1.x); f[5] = __uint_as_float(r1.y);
+        f[6] = __uint_as_float(r1.z); f[7] = __uint_as_float(r1.w);
+    }
     static __device__ __forceinline__ void load(const float* p, float (&f)[8])
     {
         const float4 v0 = *reinterpret_cast<const float4*>(p), v1 = *reinterpret_cast<const float4*>(p + 4);
@@ -99,15 +112,25 @@ __device__ __forceinline__ unsigned short to_bits(__half h) { return __half_as_u
 __device__ __forceinline__ unsigned short to_bits(__nv_bfloat16 h) { return __bfloat16_as_ushort(h); }
 
 template <typename H> struct AgeVec8Half {
-    static __device__ __forceinline__ void load(const H* p, float (&f)[8])
+    static __device__ __forceinline__ void raw(const H* p, uint4& r0, uint4& r1)
     {
-        const uint4 v = *reinterpret_cast<const uint4*>(p);
+        r0 = *reinterpret_cast<const uint4*>(p);
+        r1 = make_uint4(0u, 0u, 0u, 0u);
+    }
+    static __device__ __forceinline__ void from_raw(uint4 v, uint4, float (&f)[8])
+    {
+        const H* tag = nullptr;
         const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            f[2 * q] = AgeIO<H>::load(bits_to(p, (unsigned short)(w[q] & 0xffffu)));
-            f[2 * q + 1] = AgeIO<H>::load(bits_to(p, (unsigned short)(w[q] >> 16)));
+            f[2 * q] = AgeIO<H>::load(bits_to(tag, (unsigned short)(w[q] & 0xffffu)));
+            f[2 * q + 1] = AgeIO<H>::load(bits_to(tag, (unsigned short)(w[q] >> 16)));
         }
+    }
+    static __device__ __forceinline__ void load(const H* p, float (&f)[8])
+    {
+        const uint4 v = *reinterpret_cast<const uint4*>(p);
+        from_raw(v, v, f);
     }
     static __device__ __forceinline__ void store(H* p, const float (&f)[8])
     {
@@ -158,7 +181,7 @@ struct WarpScratch {
     float age[kWarpSlots];        // age of the E/I node in each slot
     int32_t base[32];             // first node of each lane's item
     uint32_t hc[32];              // count of a lane's merge-class node, ~0 for a group
-    uint32_t ev[kWarpSlots];      // push events: node | (1u << 31) when it left I
+    uint32_t ev[kWarpSlots + 32]; // deferred push events: node | (1u << 31) when it left I
 };
 
 enum { kItemNone = 0, kItemGroup = 1, kItemHub = 2 };
@@ -172,6 +195,13 @@ struct GroupLoads {
     uint2 c8;
     uint4 pd;
     bool have_cp;        // c8 and pd loaded
+};
+
+// The ages of a group loaded together with its states while E and I nodes
+// are common (raw storage words; ag1 unused for 16-bit ages)
+struct GroupAges {
+    uint4 ag0, ag1;
+    bool have;
 };
 
 __device__ __forceinline__ GroupLoads group_loads(const StepArgs& a, uint32_t par, int64_t t, int64_t n_grp,
@@ -190,6 +220,22 @@ __device__ __forceinline__ GroupLoads group_loads(const StepArgs& a, uint32_t pa
             g.pd = *reinterpret_cast<const uint4*>(a.pd16[par ^ 1u] + i0);
             g.have_cp = true;
         }
+    }
+    return g;
+}
+
+// ages of a whole group (thread class, every node below n_thr) when spec_ei
+template <typename AgeT>
+__device__ __forceinline__ GroupAges group_ages(const StepArgs& a, int64_t t, int64_t n_grp, bool spec_ei)
+{
+    GroupAges g;
+    g.ag0 = make_uint4(0u, 0u, 0u, 0u);
+    g.ag1 = g.ag0;
+    g.have = false;
+    if (spec_ei && t < n_grp && (t + 1) * kPushG <= (int64_t)a.n_thr &&
+        FS_IN_BOUNDS(a.ctl, kSiteGroup, t * kPushG + kPushG - 1, a.x_len)) {
+        AgeVec8<AgeT>::raw(static_cast<const AgeT*>(a.A) + t * kPushG, g.ag0, g.ag1);
+        g.have = true;
     }
     return g;
 }
@@ -315,14 +361,16 @@ __device__ __forceinline__ void push_one(const StepArgs& a, uint32_t par, uint32
 template <bool INIT>
 __device__ __forceinline__ void warp_push(const StepArgs& a, uint32_t par, uint32_t ev, uint32_t neg, int base,
                                           uint32_t* __restrict__ list);
+__device__ __forceinline__ void warp_push_defer(const StepArgs& a, uint32_t par, uint32_t ev, uint32_t neg,
+                                                int base, uint32_t* __restrict__ list, int& pend);
 
 // One round of the warp (every lane calls this; item t of this lane, t >=
 // total for none; gl = the group's early loads). Returns nothing: states,
 // ages, counts and tallies are stored, pushes are made, deltas accumulated.
-template <typename AgeT, bool ADAPTIVE>
+template <typename AgeT, bool ADAPTIVE, bool DEFER>
 __device__ __forceinline__ void warp_round(const StepArgs& a, uint32_t par, uint32_t step, int64_t t,
-                                           const GroupLoads& gl, int64_t n_grp, int64_t total, float dt,
-                                           float& lmax, PushDeltas& ld, WarpScratch& w)
+                                           const GroupLoads& gl, const GroupAges& ga, int64_t n_grp, int64_t total,
+                                           float dt, float& lmax, PushDeltas& ld, WarpScratch& w, int& pend)
 {
     const int lane = threadIdx.x & 31;
     const int slot0 = lane * kPushG;
@@ -365,7 +413,9 @@ __device__ __forceinline__ void warp_round(const StepArgs& a, uint32_t par, uint
         if ((eiM.x | eiM.y) != 0u) {
             need |= byte_mask_bits(eiM);
             float ag[kPushG];
-            if (base + kPushG <= a.n_thr) {
+            if (ga.have) {
+                AgeVec8<AgeT>::from_raw(ga.ag0, ga.ag1, ag);
+            } else if (base + kPushG <= a.n_thr) {
                 AgeVec8<AgeT>::load(Ain + base, ag);
             } else {
 #pragma unroll
@@ -529,23 +579,31 @@ __device__ __forceinline__ void warp_round(const StepArgs& a, uint32_t par, uint
             }
         }
     }
-    warp_push<false>(a, par, ev, neg, base, w.ev);
+    if constexpr (DEFER)
+        warp_push_defer(a, par, ev, neg, base, w.ev, pend);
+    else
+        warp_push<false>(a, par, ev, neg, base, w.ev);
 }
 
 // ---------------------------------------------------------------------------
 // Warp-wide pushes. The lanes' push events (bit u of ev: node base + u
-// entered I, or left it when bit u of neg is set) go to the warp's event
-// list; per batch of 32 events lane e reads event e's transposed row bounds,
-// a warp scan of the row lengths flattens the batch's edges into one index
-// range, and the 32 lanes stride over it, each finding its event by a binary
-// search over the lanes' offsets. A batch costs two dependent memory round
-// trips however many events it holds. Every lane of the warp must call this.
+// entered I, or left it when bit u of neg is set) are appended to the warp's
+// event list; per batch of 32 events lane e reads event e's transposed row
+// bounds, a warp scan of the row lengths flattens the batch's edges into one
+// index range, and the 32 lanes stride over it, each finding its event by a
+// binary search over the lanes' offsets. A batch costs two dependent memory
+// round trips however many events it holds, so a warp that sweeps several
+// rounds in one step (large graphs) defers its events until a batch is full
+// or its sweep ends: a round with a few events then waits for no push at
+// all. Pushes made later in the same step are equivalent: they go to the
+// tallies of this step's parity, which are read only by the next step.
+// Every lane of the warp must call these.
 // ---------------------------------------------------------------------------
 constexpr int64_t kPushLongRow = 128;    // rows longer than this are pushed one at a time
 
-template <bool INIT>
-__device__ __forceinline__ void warp_push(const StepArgs& a, uint32_t par, uint32_t ev, uint32_t neg, int base,
-                                          uint32_t* __restrict__ list)
+// appends the lanes' events at list[pend ..]; returns the new length
+__device__ __forceinline__ int warp_events_append(uint32_t ev, uint32_t neg, int base, uint32_t* __restrict__ list,
+                                                  int pend)
 {
     const int lane = threadIdx.x & 31;
     const uint32_t cnt = (uint32_t)__popc(ev);
@@ -557,10 +615,8 @@ __device__ __forceinline__ void warp_push(const StepArgs& a, uint32_t par, uint3
             incl += y;
     }
     const int nev = (int)__shfl_sync(kFull, incl, 31);
-    if (nev == 0)
-        return;
-    {
-        int j = (int)(incl - cnt);
+    if (nev) {
+        int j = pend + (int)(incl - cnt);
         uint32_t m = ev;
         while (m) {
             const int u = __ffs(m) - 1;
@@ -568,12 +624,21 @@ __device__ __forceinline__ void warp_push(const StepArgs& a, uint32_t par, uint3
             list[j++] = (uint32_t)(base + u) | (((neg >> u) & 1u) << 31);
         }
     }
+    return pend + nev;
+}
+
+// the pushes of events list[0 .. nproc)
+template <bool INIT>
+__device__ __forceinline__ void warp_push_events(const StepArgs& a, uint32_t par, const uint32_t* __restrict__ list,
+                                                 int nproc)
+{
+    const int lane = threadIdx.x & 31;
     __syncwarp();
-    for (int c0 = 0; c0 < nev; c0 += 32) {
+    for (int c0 = 0; c0 < nproc; c0 += 32) {
         const int e = c0 + lane;
         int64_t lo = 0, len = 0;
         uint32_t evw = 0u;
-        if (e < nev) {
+        if (e < nproc) {
             evw = list[e];
             const int node = (int)(evw & 0x7fffffffu);
             if (FS_IN_BOUNDS(a.ctl, kSiteOutPtr, node, a.n)) {
@@ -636,7 +701,48 @@ __device__ __forceinline__ void warp_push(const StepArgs& a, uint32_t par, uint3
             }
         }
     }
-    __syncwarp();     // the list is reused by the warp's next item
+    __syncwarp();     // the list is rewritten by the warp's next append
+}
+
+// all the lanes' events at once (initial counts)
+template <bool INIT>
+__device__ __forceinline__ void warp_push(const StepArgs& a, uint32_t par, uint32_t ev, uint32_t neg, int base,
+                                          uint32_t* __restrict__ list)
+{
+    const int nev = warp_events_append(ev, neg, base, list, 0);
+    if (nev)
+        warp_push_events<INIT>(a, par, list, nev);
+}
+
+// the step's events: appended, and pushed in whole batches of 32 once at
+// least one is full; the rest (fewer than 32) move to the front of the list.
+// The list holds pend (< 32) + one round's events (at most kWarpSlots).
+__device__ __forceinline__ void warp_push_defer(const StepArgs& a, uint32_t par, uint32_t ev, uint32_t neg,
+                                                int base, uint32_t* __restrict__ list, int& pend)
+{
+    pend = warp_events_append(ev, neg, base, list, pend);
+    if (pend < 32)
+        return;
+    const int full = pend & ~31, rest = pend & 31;
+    warp_push_events<false>(a, par, list, full);
+    const int lane = threadIdx.x & 31;
+    uint32_t v = 0u;
+    if (lane < rest)
+        v = list[full + lane];
+    __syncwarp();
+    if (lane < rest)
+        list[lane] = v;
+    __syncwarp();
+    pend = rest;
+}
+
+// the events still deferred when the warp's sweep ends
+__device__ __forceinline__ void warp_push_drain(const StepArgs& a, uint32_t par, uint32_t* __restrict__ list,
+                                                int& pend)
+{
+    if (pend)
+        warp_push_events<false>(a, par, list, pend);
+    pend = 0;
 }
 
 constexpr int kScanRounds = 3;      // grid-stride rounds whose loads a warp issues together
@@ -647,8 +753,8 @@ constexpr int kScanRounds = 3;      // grid-stride rounds whose loads a warp iss
 // compile-time choice so that the sweep without a list keeps its own register
 // allocation.
 template <typename AgeT, bool SCAN, bool ADAPTIVE, bool LIST>
-__device__ __forceinline__ void push_items(const StepArgs& a, uint32_t par, int64_t k, bool spec_s, float dt,
-                                           float& lmax, PushDeltas& ld, WarpScratch& w,
+__device__ __forceinline__ void push_items(const StepArgs& a, uint32_t par, int64_t k, bool spec_s, bool spec_ei,
+                                           float dt, float& lmax, PushDeltas& ld, WarpScratch& w, int& pend,
                                            const int32_t* __restrict__ act, int64_t n_items)
 {
     const int tid = threadIdx.x, lane = tid & 31;
@@ -666,9 +772,10 @@ __device__ __forceinline__ void push_items(const StepArgs& a, uint32_t par, int6
     if constexpr (!SCAN) {
         const int64_t t = item_at((int64_t)blockIdx.x * kPushThreads + tid);
         GroupLoads cur = group_loads(a, par, t, n_grp, spec_s);
+        const GroupAges ga = group_ages<AgeT>(a, t, n_grp, false);
         const bool idle = (t < n_grp || t >= total) && group_idle(a, par, t, n_grp, cur);
         if (!__all_sync(kFull, idle))
-            warp_round<AgeT, ADAPTIVE>(a, par, (uint32_t)k, t, cur, n_grp, total, dt, lmax, ld, w);
+            warp_round<AgeT, ADAPTIVE, false>(a, par, (uint32_t)k, t, cur, ga, n_grp, total, dt, lmax, ld, w, pend);
     }
     // Warps take kScanRounds grid-stride rounds at a time: the loads that tell
     // whether an item has work (states; counts and tallies while S is common)
@@ -696,9 +803,11 @@ __device__ __forceinline__ void push_items(const StepArgs& a, uint32_t par, int6
             const int u = __ffs(wb) - 1;
             wb &= wb - 1u;
             const int64_t t = item_at(tb + u * stride + lane);
-            // reloaded: these lines were read by the scan just above
+            // reloaded: these lines were read by the scan just above (the
+            // ages, while E/I nodes are common, are issued with them)
             const GroupLoads cur = group_loads(a, par, t, n_grp, spec_s);
-            warp_round<AgeT, ADAPTIVE>(a, par, (uint32_t)k, t, cur, n_grp, total, dt, lmax, ld, w);
+            const GroupAges ga = group_ages<AgeT>(a, t, n_grp, spec_ei);
+            warp_round<AgeT, ADAPTIVE, true>(a, par, (uint32_t)k, t, cur, ga, n_grp, total, dt, lmax, ld, w, pend);
         }
     }
 }
@@ -709,15 +818,18 @@ __device__ __forceinline__ void push_items(const StepArgs& a, uint32_t par, int6
 struct PushSweepOut {
     PushDeltas ld;
     float lmax;
+    int pend;
 };
 
 template <typename AgeT, bool SCAN, bool ADAPTIVE>
 __device__ __noinline__ PushSweepOut push_items_listed(const StepArgs& a, uint32_t par, int64_t k, bool spec_s,
-                                                        float dt, WarpScratch* w, int64_t n_items)
+                                                        bool spec_ei, float dt, WarpScratch* w, int64_t n_items)
 {
     PushSweepOut o;
     o.lmax = 0.0f;
-    push_items<AgeT, SCAN, ADAPTIVE, true>(a, par, k, spec_s, dt, o.lmax, o.ld, *w, a.act, n_items);
+    o.pend = 0;
+    push_items<AgeT, SCAN, ADAPTIVE, true>(a, par, k, spec_s, spec_ei, dt, o.lmax, o.ld, *w, o.pend, a.act,
+                                           n_items);
     return o;
 }
 
@@ -751,26 +863,35 @@ __global__ void __launch_bounds__(kPushThreads, kPushCtasPerSm) push_step_kernel
     // counts and tallies are loaded a round ahead while S nodes are common
     // (counts of the state at the start of this launch sequence)
     const bool spec_s = (int64_t)a.ctl->counts[0] * 16 >= (int64_t)a.n;
+    // in the multi-round sweep, ages are loaded with the states while at
+    // least a quarter of the nodes are E or I (then about nine groups in ten
+    // hold one)
+    const bool spec_ei = ((int64_t)a.ctl->counts[1] + (int64_t)a.ctl->counts[2]) * 4 >= (int64_t)a.n;
     PushDeltas ld;
+    int pend = 0;             // deferred push events in w.ev
     // active-node compaction (Section 5.6): the items listed by this launch
     // sequence's refresh, or every item
     const int64_t total = ((int64_t)a.n_thr + kPushG - 1) / kPushG + a.n_m;
     const int64_t na = a.act ? (int64_t)a.ctl->n_act : total;
     if constexpr (SCAN) {
         if (na < total) {
-            const PushSweepOut o = push_items_listed<AgeT, SCAN, ADAPTIVE>(a, par, k, spec_s, dt, &w, na);
+            const PushSweepOut o = push_items_listed<AgeT, SCAN, ADAPTIVE>(a, par, k, spec_s, spec_ei, dt, &w, na);
             ld = o.ld;
             lmax = o.lmax;
+            pend = o.pend;
         } else {
-            push_items<AgeT, SCAN, ADAPTIVE, false>(a, par, k, spec_s, dt, lmax, ld, w, nullptr, total);
+            push_items<AgeT, SCAN, ADAPTIVE, false>(a, par, k, spec_s, spec_ei, dt, lmax, ld, w, pend, nullptr,
+                                                    total);
         }
     } else {
         // one round: both sweeps inline
         if (na < total)
-            push_items<AgeT, SCAN, ADAPTIVE, true>(a, par, k, spec_s, dt, lmax, ld, w, a.act, na);
+            push_items<AgeT, SCAN, ADAPTIVE, true>(a, par, k, spec_s, spec_ei, dt, lmax, ld, w, pend, a.act, na);
         else
-            push_items<AgeT, SCAN, ADAPTIVE, false>(a, par, k, spec_s, dt, lmax, ld, w, nullptr, total);
+            push_items<AgeT, SCAN, ADAPTIVE, false>(a, par, k, spec_s, spec_ei, dt, lmax, ld, w, pend, nullptr,
+                                                    total);
     }
+    warp_push_drain(a, par, w.ev, pend);
     if constexpr (ADAPTIVE) {
         // rates are >= 0, so their FP32 bits order as unsigned integers
         const uint32_t m = __reduce_max_sync(kFull, __float_as_uint(lmax));

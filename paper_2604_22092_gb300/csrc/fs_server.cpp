@@ -49,14 +49,18 @@ struct Request {
 
 // device memory of one ensemble (states, ages, masks, tables, counts rows; in
 // the push form also the per-replicate counts and pending tallies: 1 + 2 x 2
-// bytes per thread-class node, 4 + 2 x 8 per merge-class node)
-int64_t ensemble_bytes(int64_t n, int64_t n_merge, int R, int age_bytes, int64_t steps, bool push)
+// bytes per thread-class node, 4 + 2 x 8 per merge-class node; with a
+// shedding profile two infectivity buffers like the ages and one more table
+// per realisation)
+int64_t ensemble_bytes(int64_t n, int64_t n_merge, int R, int age_bytes, int64_t steps, bool push, bool shed)
 {
     const int64_t Rp = R <= 8 ? 8 : R <= 16 ? 16 : 32;
     int64_t b = n * Rp * (1 + age_bytes) + 2 * (n + 1) * (Rp / 8) + (int64_t)R * (2 * 4096 * 16 + 256 * 4) +
                 (steps + 1) * Rp * 16 + 4096;
     if (push)
         b += (n - n_merge) * Rp * 5 + std::max<int64_t>(n_merge, 1) * Rp * 20;
+    if (shed)
+        b += 2 * n * Rp * age_bytes + (int64_t)R * 4096 * 16;
     return b;
 }
 
@@ -331,10 +335,18 @@ fs_status fs_server_submit(fs_server* s, fs_graph* g, const fs_sim_params* scena
             delete q;
             return fail(FS_EINVAL, "fs_server_submit: scenarios must share flags");
         }
-        if (p.shed_mode != FS_SHED_NONE || (p.flags & FS_ACTIVE_LIST) || p.theta > 0) {
+        if ((p.flags & FS_ACTIVE_LIST) || p.theta > 0) {
             delete q;
-            return fail(FS_EUNSUPPORTED, "fs_server_submit: served ensembles keep s = 1 (FS_SHED_NONE), no active "
-                                         "list, the renewal engine");
+            return fail(FS_EUNSUPPORTED, "fs_server_submit: served ensembles run the renewal engine without an "
+                                         "active list");
+        }
+        if (p.shed_mode != FS_SHED_NONE && p.flags == FS_PRESSURE_PUSH) {
+            delete q;
+            return fail(FS_EUNSUPPORTED, "fs_server_submit: a shedding profile needs the gather form");
+        }
+        if (sc > 0 && (p.shed_mode != FS_SHED_NONE) != (scenarios[0].shed_mode != FS_SHED_NONE)) {
+            delete q;
+            return fail(FS_EINVAL, "fs_server_submit: every scenario has a shedding profile or none");
         }
         if (sc > 0 && (p.eps > 0) != (scenarios[0].eps > 0)) {
             delete q;
@@ -356,9 +368,10 @@ fs_status fs_server_submit(fs_server* s, fs_graph* g, const fs_sim_params* scena
     }
     const int age_bytes = s->cfg.age_dtype == FS_AGE_F32 ? 4 : 2;
     const bool push = scenarios[0].flags == FS_PRESSURE_PUSH;
+    const bool shed = scenarios[0].shed_mode != FS_SHED_NONE;
     for (size_t off = 0; off < q->params.size(); off += 32)
         q->bytes += ensemble_bytes(q->n, g->n_m, (int)std::min<size_t>(32, q->params.size() - off), age_bytes, steps,
-                                   push);
+                                   push, shed);
     if (q->bytes > s->budget) {
         const int64_t b = q->bytes;
         delete q;

@@ -291,8 +291,14 @@ def test_shedding_argument_errors(torch_cuda):
     s = fs.fs_sim_init(gh, p, [1])
     assert fs.fs_sim_pressure_get(s) == fs.FS_PRESSURE_GATHER
     fs.fs_sim_destroy(s)
+    # packed ensembles take profiles in the gather form, not in the push form
+    ens = fs.fs_ens_create(gh, [sir_shed(fs.FS_SHED_DENSITY, seed=k) for k in range(3)], [1])
+    fs.fs_ens_destroy(ens)
+    pp = [sir_shed(fs.FS_SHED_DENSITY, seed=k) for k in range(3)]
+    for q in pp:
+        q.flags = fs.FS_PRESSURE_PUSH
     with pytest.raises(fs.FsError) as e:
-        fs.fs_ens_create(gh, [sir_shed(fs.FS_SHED_DENSITY, seed=k) for k in range(3)], [1])
+        fs.fs_ens_create(gh, pp, [1])
     assert e.value.status == 7
     s = fs.fs_sim_init(gh, fs.sim_params(fs.FS_SIR, fs.law("exp", 0.2), 0.3, 0.1, 1), [1])
     with pytest.raises(fs.FsError) as e:
