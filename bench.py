@@ -627,7 +627,16 @@ def run_flashstep(args, rank, world, local_rank):
         return (bytes_model(g.n, args.sim_steps, work["s_node_sum"], work["s_degree_sum"])
                 * steps_in_graphs / args.sim_steps)
 
-    def roofline_of(bytes_per_step, step_ms, kernel, pressure):
+    def breq_of_run():
+        """B_req (the required bytes of the pull formulation, N (2 b_s + 2 b_a
+        + 1/8) + |S_k| (4 + d (4 + 1/8)) on the d-regular headline graph) of
+        the steps inside the timed replays, from the run's counts trajectory."""
+        d = g.col_ind.size / g.n
+        cnt = counts_dev.view(args.sim_steps + 1, 4).cpu().numpy().astype(np.int64)
+        S = cnt[:steps_in_graphs, 0].astype(np.float64)
+        return float(np.sum(g.n * (2 + 8 + 1 / 8) + S * (4 + d * (4 + 1 / 8))))
+
+    def roofline_of(bytes_per_step, step_ms, kernel, pressure, breq_per_step=None):
         peak, peak_kind = measured_peak_hbm()
         achieved = bytes_per_step / (step_ms * 1e-3) / 1e9
         # the paper's dense traffic model (every row traversed): N (2 b_s + 2 b_a + 1/8 + 4) + E (4 + 1/8)
@@ -637,8 +646,14 @@ def run_flashstep(args, rank, world, local_rank):
                  if pressure == fs.FS_PRESSURE_PUSH else
                  "gather: state/age read+write and bitmap bit per node, row offset per S node, "
                  "column + bitmap bit per S-row edge")
+        extra = {}
+        if breq_per_step is not None:
+            # the same trajectory's B_req (the gather's required bytes) over the
+            # push step's time: the byte figure the two forms share
+            extra = {"breq_equiv_frac": round(breq_per_step / (step_ms * 1e-3) / 1e9 / peak, 4),
+                     "breq_bytes_per_step": round(breq_per_step)}
         return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": profiled_traffic(kernel),
+                "frac": round(achieved / peak, 4), "traffic": profiled_traffic(kernel), **extra,
                 "peak_source": peak_kind, "kernel": kernel,
                 "algorithmic_bytes_per_launch": round(bytes_per_step), "byte_model": model,
                 "avg_launch_us": round(step_ms * 1e3, 3),
@@ -655,7 +670,7 @@ def run_flashstep(args, rank, world, local_rank):
         flush.fill_(1.0)
         one_step(prm)
     torch.cuda.synchronize()
-    times, kern_ms, bytes_alg = [], [], []
+    times, kern_ms, bytes_alg, breq_alg = [], [], [], []
     pressure_used = None
     launches0 = fs.fs_kernel_launches()
     for _ in range(args.steps):
@@ -669,6 +684,8 @@ def run_flashstep(args, rank, world, local_rank):
         kern_ms.append(float(np.sum(replay_ms[:full])))
         pressure_used = work["pressure"]
         bytes_alg.append(step_bytes(work, pressure_used))
+        if pressure_used == fs.FS_PRESSURE_PUSH:
+            breq_alg.append(breq_of_run())
     clock_info = clocks.stop() if clocks else None
     launches = (fs.fs_kernel_launches() - launches0) // max(args.steps, 1)
     total_ms = max_over_ranks(float(np.sum(times)), dist, dev)
@@ -679,7 +696,8 @@ def run_flashstep(args, rank, world, local_rank):
     per_step_bytes = float(np.sum(bytes_alg)) / (args.steps * steps_in_graphs)
     per_step_ms = float(np.sum(kern_ms)) / (args.steps * steps_in_graphs)
     kernel = step_kernel_name(fs, g, pressure_used)
-    roofline = roofline_of(per_step_bytes, per_step_ms, kernel, pressure_used)
+    roofline = roofline_of(per_step_bytes, per_step_ms, kernel, pressure_used,
+                           float(np.sum(breq_alg)) / (args.steps * steps_in_graphs) if breq_alg else None)
     out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
