@@ -216,7 +216,7 @@ typedef struct {
     int32_t thread_max_deg;   /* class threshold in use                            */
     int32_t identity_layout;  /* 1 when internal ids equal original ids            */
     int64_t device_bytes;     /* device memory held by the graph                   */
-} fs_graph_info;
+} fs_graph_info_t;
 
 typedef struct fs_graph fs_graph;
 typedef struct fs_sim fs_sim;
@@ -248,7 +248,11 @@ const char* fs_last_error(void);
 fs_status fs_graph_create(int64_t n, const int64_t* row_ptr, const int32_t* col_ind,
                           const float* weights, const fs_graph_opts* opts,
                           void* stream, fs_graph** out);
-fs_status fs_graph_info_get(const fs_graph* g, fs_graph_info* out);
+/* The graph's sizes, degree profile and the class split in use (Section
+ * 5.5: d_max, rho = d_max / d_avg). fs_graph_info_get is the same call.
+ * Errors: FS_EINVAL (NULL argument). */
+fs_status fs_graph_info(const fs_graph* g, fs_graph_info_t* out);
+fs_status fs_graph_info_get(const fs_graph* g, fs_graph_info_t* out);
 /* FS_EBUSY while a simulation created on the graph is alive. */
 fs_status fs_graph_destroy(fs_graph* g);
 

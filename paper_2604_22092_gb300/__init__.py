@@ -23,7 +23,7 @@ from ._abi import (FS_AGE_BF16, FS_AGE_F16, FS_AGE_F32, FS_DISPATCH_AUTO, FS_DIS
                    FS_TEST_BOUNDS_SHRINK, FS_TEST_WAIT_TIMEOUT, FsError, check)
 
 __all__ = [
-    "fs_version", "fs_last_error", "fs_graph_create", "fs_graph_info_get", "fs_graph_destroy",
+    "fs_version", "fs_last_error", "fs_graph_create", "fs_graph_info", "fs_graph_info_get", "fs_graph_destroy",
     "fs_sim_init", "fs_sim_step", "fs_sim_run", "fs_sim_run_async", "fs_sim_sync", "fs_sim_run_timed",
     "fs_kernel_launches", "fs_tune_stats", "fs_tune_reset",
     "fs_sim_get_state", "fs_sim_set_state", "fs_sim_work", "fs_sim_pressure_get", "fs_sim_time",
@@ -129,6 +129,12 @@ def fs_graph_create(n: int, row_ptr, col_ind, weights=None, opts: _abi.fs_graph_
                            ctypes.byref(h))
     check(st, "fs_graph_create")
     return h.value
+
+
+def fs_graph_info(g: int) -> dict:
+    info = _abi.fs_graph_info()
+    check(load().fs_graph_info(g, ctypes.byref(info)), "fs_graph_info")
+    return {name: getattr(info, name) for name, _ in info._fields_}
 
 
 def fs_graph_info_get(g: int) -> dict:

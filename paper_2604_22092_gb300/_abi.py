@@ -78,6 +78,7 @@ PROTOTYPES = {
     "fs_version": (ctypes.c_char_p, []),
     "fs_last_error": (ctypes.c_char_p, []),
     "fs_graph_create": (ctypes.c_int, [ctypes.c_int64, VP, VP, VP, P(fs_graph_opts), VP, P(VP)]),
+    "fs_graph_info": (ctypes.c_int, [VP, P(fs_graph_info)]),
     "fs_graph_info_get": (ctypes.c_int, [VP, P(fs_graph_info)]),
     "fs_graph_destroy": (ctypes.c_int, [VP]),
     "fs_test_inject": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64]),

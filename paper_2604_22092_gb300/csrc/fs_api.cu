@@ -617,11 +617,11 @@ done:
     return FS_OK;
 }
 
-fs_status fs_graph_info_get(const fs_graph* g, fs_graph_info* out)
+fs_status fs_graph_info(const fs_graph* g, fs_graph_info_t* out)
 {
     if (!g || !out)
         return fail(FS_EINVAL, "NULL argument");
-    fs_graph_info i{};
+    fs_graph_info_t i{};
     i.n = g->n;
     i.nnz = g->nnz;
     i.d_max = g->dmax;
@@ -636,6 +636,11 @@ fs_status fs_graph_info_get(const fs_graph* g, fs_graph_info* out)
     i.device_bytes = g->bytes;
     *out = i;
     return FS_OK;
+}
+
+fs_status fs_graph_info_get(const fs_graph* g, fs_graph_info_t* out)
+{
+    return fs_graph_info(g, out);
 }
 
 fs_status fs_graph_destroy(fs_graph* g)

@@ -309,7 +309,7 @@ fs_status fs_server_submit(fs_server* s, fs_graph* g, const fs_sim_params* scena
         return fail(FS_EINVAL, "fs_server_submit: bad n_scen or replicates");
     if (steps < 0 || steps >= ((int64_t)1 << 31))
         return fail(FS_EINVAL, "fs_server_submit: bad steps");
-    fs_graph_info info{};
+    fs_graph_info_t info{};
     fs_status st = fs_graph_info_get(g, &info);
     if (st != FS_OK)
         return st;

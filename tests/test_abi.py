@@ -58,7 +58,7 @@ def test_oracle_is_not_imported_by_the_product_package():
 
 # typedef name in include/fs.h -> ctypes mirror in the binding
 _STRUCTS = {"fs_law": "fs_law", "fs_sim_params": "fs_sim_params", "fs_graph_opts": "fs_graph_opts",
-            "fs_graph_info": "fs_graph_info", "fs_server_cfg": "fs_server_cfg", "fs_server_stats": "fs_server_stats"}
+            "fs_graph_info_t": "fs_graph_info", "fs_server_cfg": "fs_server_cfg", "fs_server_stats": "fs_server_stats"}
 
 
 def test_struct_layouts_match_the_header(tmp_path):
