@@ -72,12 +72,14 @@ enum { FS_DISPATCH_AUTO = 0, FS_DISPATCH_THREAD = 1, FS_DISPATCH_MERGE = 2, FS_D
  *     one-thread-per-node class to have in-degree <= 255 (true for every
  *     dispatch except FS_DISPATCH_THREAD on graphs with d_max > 255).
  *   FS_PRESSURE_AUTO (0): for a single realisation (fs_sim_*), PUSH where
- *     it is available, else GATHER; for packed ensembles, batches and the
- *     server, GATHER: a packed gather reads each column once for all the
- *     replicates of a node, while pushes are paid per replicate, and on
- *     GB300 the packed push measured slower at 8 to 32 replicates.
- *     FS_PRESSURE_PUSH selects the push form there too (every realisation of
- *     an ensemble or request must pass the same flags). */
+ *     it is available, else GATHER; for a packed ensemble (also in batches
+ *     and the server), PUSH where it is available for ensembles of up to 8
+ *     realisations and GATHER for 9 to 32: a packed gather reads each column
+ *     once for all the replicates of a node while pushes are paid per
+ *     replicate, and on GB300 the gather measured faster at 16 and 32
+ *     replicate lanes, the push at 8. A shedding profile always takes
+ *     GATHER. FS_PRESSURE_PUSH / _GATHER force a form there too (every
+ *     realisation of an ensemble or request must pass the same flags). */
 enum { FS_PRESSURE_AUTO = 0, FS_PRESSURE_GATHER = 1, FS_PRESSURE_PUSH = 2 };
 /* Active-node compaction (Section 5.6), a flag ORed into fs_sim_params.flags
  * of a single realisation: at the start of every launch sequence (each CUDA

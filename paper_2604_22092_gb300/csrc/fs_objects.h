@@ -130,6 +130,8 @@ fs::LawF to_lawf(const fs_law& L);
 // the push form of the pressure: available when the thread class's in-degrees
 // fit u8 counts; the transposed CSR of a graph, built once (thread-safe)
 bool push_available(const fs_graph* g);
+// the pressure form of a packed ensemble of n_real realisations (fs_pack_api.cu)
+bool packed_push(const fs_graph* g, const fs_sim_params& p0, int n_real);
 cudaError_t ensure_out_csr(fs_graph* g, cudaStream_t st);
 // the dispatch autotuner (fs_tune.cpp): builds the graph with the class split
 // it chooses for this degree profile (base: the caller's options, AUTO)

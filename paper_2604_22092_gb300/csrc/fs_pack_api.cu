@@ -193,6 +193,24 @@ fs::PackSeg segment_of(const Member& m)
 
 }  // namespace
 
+namespace fsapi {
+
+// FS_PRESSURE_AUTO for a packed ensemble: the push form at 8 replicate lanes,
+// the gather at 16 and 32, where a gather's column and mask reads serve more
+// replicates than its pushes cost (measured on GB300, 400-step SEIR runs,
+// packed gather / push GNUPS: ER d = 8, N = 10^6: 119 / 156 at 8 lanes,
+// 148 / 127 at 16, 151 / 136 at 32; BA m = 4: 108 / 113, 119 / 103,
+// 119 / 108; regular d = 10, N = 3 x 10^5: 85 / 107, 108 / 118, 116 / 111).
+// A shedding profile needs the gather.
+bool packed_push(const fs_graph* g, const fs_sim_params& p0, int n_real)
+{
+    if (p0.flags == FS_PRESSURE_PUSH)
+        return true;
+    return p0.flags == FS_PRESSURE_AUTO && p0.shed_mode == FS_SHED_NONE && n_real <= 8 && push_available(g);
+}
+
+}  // namespace fsapi
+
 #define E_CUDA(obj, expr)                                                                                    \
     do {                                                                                                     \
         cudaError_t e_ = (expr);                                                                             \
@@ -259,9 +277,7 @@ fs_status fs_ens_create(fs_graph* g, const fs_sim_params* params, int32_t n_real
     e->model = params[0].model;
     e->age_bytes = e->age_dtype == FS_AGE_F32 ? 4 : 2;
     e->mask_bytes = e->R_pad / 8;
-    // packed ensembles default to the gather: it reads each column once for
-    // all replicates, while pushes are paid per replicate (measured slower)
-    e->push = params[0].flags == FS_PRESSURE_PUSH;
+    e->push = fsapi::packed_push(g, params[0], n_real);
     e->shed = params[0].shed_mode != FS_SHED_NONE;
     const int64_t n = g->n;
     const int Rp = e->R_pad;

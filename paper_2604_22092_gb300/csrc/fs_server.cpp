@@ -367,11 +367,11 @@ fs_status fs_server_submit(fs_server* s, fs_graph* g, const fs_sim_params* scena
         }
     }
     const int age_bytes = s->cfg.age_dtype == FS_AGE_F32 ? 4 : 2;
-    const bool push = scenarios[0].flags == FS_PRESSURE_PUSH;
     const bool shed = scenarios[0].shed_mode != FS_SHED_NONE;
-    for (size_t off = 0; off < q->params.size(); off += 32)
-        q->bytes += ensemble_bytes(q->n, g->n_m, (int)std::min<size_t>(32, q->params.size() - off), age_bytes, steps,
-                                   push, shed);
+    for (size_t off = 0; off < q->params.size(); off += 32) {
+        const int R = (int)std::min<size_t>(32, q->params.size() - off);
+        q->bytes += ensemble_bytes(q->n, g->n_m, R, age_bytes, steps, fsapi::packed_push(g, scenarios[0], R), shed);
+    }
     if (q->bytes > s->budget) {
         const int64_t b = q->bytes;
         delete q;

@@ -7,7 +7,7 @@ through fs_sim_*, whatever the number of replicates (padding to 8, 16 or 32
 lanes), the graph (regular, or Barabasi-Albert with hub rows), the age
 storage, and whether the ensemble runs alone, in a batch with others, or
 joins a batch that is already running, and in both forms of the pressure
-(push, the default, and the gather), also mixed in one batch. One small
+(push and gather), also mixed in one batch. One small
 ensemble is also compared with the oracle directly.
 """
 import math
@@ -89,9 +89,10 @@ def test_ensemble_equals_each_realisation_alone(cuda, kind, R, age_dtype, pressu
 def test_batch_members_join_leave_and_resume(cuda):
     """Three ensembles on three graphs join a running batch at different
     launches with different lengths; each member's counts equal its
-    realisations alone; an ensemble that left can continue alone. The
-    Barabasi-Albert member uses the gather form and the others the push form,
-    so one launch steps segments of both forms."""
+    realisations alone; an ensemble that left can continue alone. The first
+    member pushes, the Barabasi-Albert member gathers and the third takes the
+    default form (the gather at 32 replicate lanes), so one launch steps
+    segments of both forms."""
     graphs = [W.random_regular(8_000, 6, seed=11), W.barabasi_albert(12_000, 3, seed=12),
               W.erdos_renyi(9_000, 8, seed=13)]
     ghs = [fs.fs_graph_create(g.n, g.row_ptr, g.col_ind) for g in graphs]
