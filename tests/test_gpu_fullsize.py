@@ -42,6 +42,7 @@ def test_full_size_sampled_lockstep(oracle_mod, kind):
     d_col = torch.from_numpy(g.col_ind).cuda()
     gh = fs.fs_graph_create(n, d_rp, d_col, opts=fs.graph_opts(device_input=True))
     info = fs.fs_graph_info_get(gh)
+    assert fs.fs_graph_info(gh) == info
     if kind == "ba":
         assert info["n_merge"] > 0 and info["d_max"] > 1000
     p = seir()
