@@ -125,6 +125,14 @@ def push_bytes_model(counts: np.ndarray, n: int, d: int, b_age: int = 4) -> np.n
             + pushers * (16.0 + d * 8.0))
 
 
+def breq_regular(counts: np.ndarray, n: int, d: float, b_age: int = 4) -> float:
+    """B_req (the pull formulation's required bytes, bytes_model) of the steps
+    whose start states are rows 0 .. K-1 of a (K+1) x 4 counts trajectory on a
+    d-regular graph, where every S node's row holds d edges."""
+    S = counts[:-1, 0].astype(np.float64)
+    return bytes_model(n, S.size, float(S.sum()), float(d * S.sum()), b_age=b_age)
+
+
 def bytes_model(n: int, steps: int, s_node_sum: int, s_degree_sum: int, b_state=1, b_age=4) -> float:
     """Algorithmic bytes of `steps` steps of the pull formulation: every node
     reads and writes its state and age and writes its bitmap bit; every S node
@@ -628,13 +636,8 @@ def run_flashstep(args, rank, world, local_rank):
                 * steps_in_graphs / args.sim_steps)
 
     def breq_of_run():
-        """B_req (the required bytes of the pull formulation, N (2 b_s + 2 b_a
-        + 1/8) + |S_k| (4 + d (4 + 1/8)) on the d-regular headline graph) of
-        the steps inside the timed replays, from the run's counts trajectory."""
-        d = g.col_ind.size / g.n
-        cnt = counts_dev.view(args.sim_steps + 1, 4).cpu().numpy().astype(np.int64)
-        S = cnt[:steps_in_graphs, 0].astype(np.float64)
-        return float(np.sum(g.n * (2 + 8 + 1 / 8) + S * (4 + d * (4 + 1 / 8))))
+        cnt = counts_dev.view(args.sim_steps + 1, 4).cpu().numpy()
+        return breq_regular(cnt[:steps_in_graphs + 1], g.n, g.col_ind.size / g.n)
 
     def roofline_of(bytes_per_step, step_ms, kernel, pressure, breq_per_step=None):
         peak, peak_kind = measured_peak_hbm()

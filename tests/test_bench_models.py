@@ -65,3 +65,12 @@ def test_host_oracle_pool_steps_independent_realisations():
         assert k == 12
         assert c == ref[-1].tolist()
     assert got[0][1] != got[1][1], "the two replicates must draw different uniforms"
+
+
+def test_breq_of_a_push_trajectory():
+    # 3 steps on a 10-regular graph of 100 nodes: S at the start of each step
+    # 90, 80, 75 (row 3 is the state after the last step)
+    counts = np.array([[90, 5, 5, 0], [80, 10, 8, 2], [75, 10, 10, 5], [70, 9, 11, 10]], dtype=np.uint32)
+    got = bench.breq_regular(counts, 100, 10)
+    s = 90 + 80 + 75
+    assert got == pytest.approx(3 * 100 * (2 + 8 + 0.125) + 4 * s + 4.125 * 10 * s)
