@@ -407,6 +407,9 @@ fs_status fs_ens_get_state(fs_ens* e, int32_t r, uint8_t* state, void* age, int6
  * time its steps have covered, and the size of its next step (the adaptive
  * rule, Section 5.2; the fixed dt otherwise). Synchronous. */
 fs_status fs_ens_time(fs_ens* e, double* elapsed, float* next_dt);
+/* *pressure = FS_PRESSURE_GATHER or FS_PRESSURE_PUSH: the form the
+ * ensemble runs (FS_PRESSURE_AUTO resolves by replicate width). */
+fs_status fs_ens_pressure_get(const fs_ens* e, int32_t* pressure);
 /* FS_EBUSY while the ensemble is a live member of a batch. */
 fs_status fs_ens_destroy(fs_ens* e);
 

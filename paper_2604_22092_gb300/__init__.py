@@ -26,7 +26,7 @@ __all__ = [
     "fs_version", "fs_last_error", "fs_graph_create", "fs_graph_info", "fs_graph_info_get", "fs_graph_destroy",
     "fs_sim_init", "fs_sim_step", "fs_sim_run", "fs_sim_run_async", "fs_sim_sync", "fs_sim_run_timed",
     "fs_kernel_launches", "fs_tune_stats", "fs_tune_reset",
-    "fs_sim_get_state", "fs_sim_set_state", "fs_sim_work", "fs_sim_pressure_get", "fs_sim_time",
+    "fs_sim_get_state", "fs_sim_set_state", "fs_sim_work", "fs_sim_pressure_get", "fs_ens_pressure_get", "fs_sim_time",
     "fs_sim_infectivity_get", "fs_sim_active_units", "fs_sim_transitions", "fs_sim_destroy",
     "fs_eval_hazard", "fs_eval_density",
     "fs_eval_uniforms", "fs_step_noalloc", "fs_ens_create", "fs_ens_run", "fs_ens_get_state", "fs_ens_time",
@@ -253,6 +253,13 @@ def fs_sim_transitions(s: int) -> int:
     t = ctypes.c_uint64()
     check(load().fs_sim_transitions(s, ctypes.byref(t)), "fs_sim_transitions")
     return t.value
+
+
+def fs_ens_pressure_get(e: int) -> int:
+    """FS_PRESSURE_GATHER or FS_PRESSURE_PUSH: the form the ensemble runs."""
+    v = ctypes.c_int32()
+    check(load().fs_ens_pressure_get(e, ctypes.byref(v)), "fs_ens_pressure_get")
+    return v.value
 
 
 def fs_sim_pressure_get(s: int) -> int:

@@ -98,6 +98,7 @@ PROTOTYPES = {
     "fs_sim_set_state": (ctypes.c_int, [VP, VP, VP, ctypes.c_int64]),
     "fs_sim_work": (ctypes.c_int, [VP, P(ctypes.c_uint64), P(ctypes.c_uint64), P(ctypes.c_int64)]),
     "fs_sim_pressure_get": (ctypes.c_int, [VP, P(ctypes.c_int32)]),
+    "fs_ens_pressure_get": (ctypes.c_int, [VP, P(ctypes.c_int32)]),
     "fs_sim_time": (ctypes.c_int, [VP, P(ctypes.c_double), P(ctypes.c_float)]),
     "fs_sim_infectivity_get": (ctypes.c_int, [VP, VP]),
     "fs_sim_active_units": (ctypes.c_int, [VP, P(ctypes.c_uint64), P(ctypes.c_uint64)]),

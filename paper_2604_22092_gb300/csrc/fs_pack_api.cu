@@ -438,6 +438,14 @@ fs_status fs_ens_get_state(fs_ens* e, int32_t r, uint8_t* state, void* age, int6
     return FS_OK;
 }
 
+fs_status fs_ens_pressure_get(const fs_ens* e, int32_t* pressure)
+{
+    if (!e || !pressure)
+        return fail(FS_EINVAL, "fs_ens_pressure_get: NULL argument");
+    *pressure = e->push ? FS_PRESSURE_PUSH : FS_PRESSURE_GATHER;
+    return FS_OK;
+}
+
 fs_status fs_ens_time(fs_ens* e, double* elapsed, float* next_dt)
 {
     if (!e)

@@ -193,3 +193,27 @@ def test_sir_ensemble_seeded_infectious_equals_alone(cuda, pressure):
     assert c_ens[-1, :, 3].min() > 0
     fs.fs_ens_destroy(e)
     fs.fs_graph_destroy(gh)
+
+
+def test_default_form_follows_replicate_width():
+    """FS_PRESSURE_AUTO gives a packed ensemble the push form at up to 8
+    realisations (8 replicate lanes) and the gather above; explicit flags and
+    a shedding profile (gather only) decide it otherwise."""
+    import torch
+    assert torch.cuda.is_available()
+    g = W.random_regular(4_000, 6, seed=31)
+    gh = fs.fs_graph_create(g.n, g.row_ptr, g.col_ind)
+    idx = W.index_nodes(g.n, 10, seed=32)
+    cases = [(scenarios(5), fs.FS_PRESSURE_PUSH), (scenarios(8), fs.FS_PRESSURE_PUSH),
+             (scenarios(12), fs.FS_PRESSURE_GATHER), (scenarios(5, pressure=fs.FS_PRESSURE_GATHER), fs.FS_PRESSURE_GATHER),
+             (scenarios(20, pressure=fs.FS_PRESSURE_PUSH), fs.FS_PRESSURE_PUSH)]
+    shed = scenarios(3)
+    for p in shed:
+        p.shed_mode = fs.FS_SHED_HAZARD
+        p.shedding = fs.law("exp", 1.0)
+    cases.append((shed, fs.FS_PRESSURE_GATHER))
+    for params, form in cases:
+        e = fs.fs_ens_create(gh, params, idx)
+        assert fs.fs_ens_pressure_get(e) == form, (len(params), params[0].flags, form)
+        fs.fs_ens_destroy(e)
+    fs.fs_graph_destroy(gh)
