@@ -481,16 +481,16 @@ def ensemble_bench(fs, torch, n_graphs, n_lo, n_hi, steps, age_dtype, reps=3, pr
 
 
 def serving_bench(fs, torch, n_requests, n_pool, n_hi, steps, rep_lo, rep_hi, window_s, age_dtype, big_n=0,
-                  big_age=None, plain_sample=4):
+                  big_age=None, plain_sample=0):
     """A Poisson stream of requests against the server (optionally beside one
     big SEIR job on a random 10-regular graph of big_n nodes, run on its own
     stream at the same time), then the same stream through the plain engine:
     every request's realisations alone through fs_sim_run, one request after
-    the other in arrival order. The plain service time of a request is
-    measured on a random sample of its realisations (plain_sample of them,
-    across its scenarios) and scaled by its realisation count; the plain
-    queue (and the big job, run alone after it) is replayed on those
-    measured times."""
+    the other in arrival order. The plain service time of a request is the
+    sum of the measured run times of all its realisations (plain_sample = 0)
+    or the mean over a random sample of plain_sample of them times its
+    realisation count; the plain queue (and the big job, run alone after it)
+    is replayed on those measured times against the arrival times."""
     pool = mixed_graphs(n_pool, 1e4, n_hi, seed=77)
     ghs = [fs.fs_graph_create(g.n, g.row_ptr, g.col_ind) for g in pool]
     idxs = [index_for(g, seed=q + 5) for q, g in enumerate(pool)]
@@ -551,14 +551,15 @@ def serving_bench(fs, torch, n_requests, n_pool, n_hi, steps, rep_lo, rep_hi, wi
     for r in reqs:
         sc = W.scenarios(r.n_scen, seed=r.seed)
         total = r.n_scen * r.replicates
-        picks = rng.choice(total, size=min(plain_sample, total), replace=False)
+        every = plain_sample <= 0 or plain_sample >= total
+        picks = np.arange(total) if every else rng.choice(total, size=plain_sample, replace=False)
         secs = []
         for pk in picks:
             j, rep = int(pk) // r.replicates, int(pk) % r.replicates
             p = scen_params(fs, sc[j], j * r.replicates + rep, age_dtype, seed=r.seed)
             secs.append(plain_seconds(fs, ghs[r.graph], p, idxs[r.graph], r.steps))
         sampled += len(secs)
-        service = float(np.mean(secs)) * total
+        service = float(np.sum(secs)) if every else float(np.mean(secs)) * total
         start = max(clock, r.arrival)
         clock = start + service
         plain_lat.append(clock - r.arrival)
@@ -576,9 +577,13 @@ def serving_bench(fs, torch, n_requests, n_pool, n_hi, steps, rep_lo, rep_hi, wi
            "plain_p50_s": round(float(np.percentile(plain_lat, 50)), 4),
            "plain_p99_s": round(float(np.percentile(plain_lat, 99)), 4),
            "speedup": round(plain_total / makespan, 2), "node_updates": int(updates + big_updates),
-           "plain_engine": f"every request's service time measured on a random sample of its realisations "
-                           f"({sampled} runs in all, each alone through fs_sim_run), scaled by its realisation "
-                           f"count; requests one after the other in arrival order, queue replayed on those times"
+           "plain_engine": (f"every realisation of every request run alone through fs_sim_run ({sampled} runs), "
+                            f"each request's service time their sum"
+                            if plain_sample <= 0 else
+                            f"every request's service time measured on a random sample of its realisations "
+                            f"({sampled} runs in all, each alone through fs_sim_run), scaled by its realisation "
+                            f"count")
+                           + "; requests one after the other in arrival order, queue replayed on those times"
                            + ("; the big job run alone after them" if big else "")}
     if big:
         big["age_storage"] = {fs.FS_AGE_F32: "f32", fs.FS_AGE_F16: "f16", fs.FS_AGE_BF16: "bf16"}[bprm.age_dtype]
