@@ -695,7 +695,10 @@ def run_flashstep(args, rank, world, local_rank):
         if pressure_used == fs.FS_PRESSURE_PUSH:
             breq_alg.append(breq_of_run())
     clock_info = clocks.stop() if clocks else None
-    launches = (fs.fs_kernel_launches() - launches0) // max(args.steps, 1)
+    # the library's kernel launches inside the timed region (all K benchmark
+    # steps; graph replays count their kernel nodes), and per benchmark step
+    launches_total = fs.fs_kernel_launches() - launches0
+    launches = launches_total // max(args.steps, 1)
     total_ms = max_over_ranks(float(np.sum(times)), dist, dev)
     value = whole_job_gnups(g.n, args.sim_steps, args.steps, world, total_ms)
     # roofline of the dominant kernel (the step): algorithmic bytes of the
@@ -715,7 +718,8 @@ def run_flashstep(args, rank, world, local_rank):
                       "pressure": "push" if pressure_used == fs.FS_PRESSURE_PUSH else "gather",
                       "l2_flush": "512 MB write between timed steps",
                       "timed": "device-resident CSR -> ingest + init + all steps (CUDA events)"},
-           "roofline": roofline, "gpu_launches": int(launches)}
+           "roofline": roofline, "gpu_launches": int(launches_total),
+           "gpu_launches_per_step": int(launches)}
     if clock_info:
         out["clocks"] = clock_info
     # the other pressure form on the same workload (rank 0; not part of the timed value)
